@@ -1,0 +1,217 @@
+"""ctypes wrapper of the C oracle (test infrastructure only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "h2oracle.c")
+_SO = os.path.join(_HERE, "libh2oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KIND_LAPLACE = 0
+KIND_POLY = 1
+
+
+def build_library(force: bool = False) -> str:
+    """Compile h2oracle.c with gcc (FP64, OpenMP, no FMA contraction)."""
+    with _lock:
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            tmp = _SO + f".{os.getpid()}.tmp"
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                   _SRC, "-o", tmp, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build_library()
+    lib = C.CDLL(_SO)
+    dp = C.POINTER(C.c_double)
+    ip64 = C.POINTER(C.c_int64)
+    ip32 = C.POINTER(C.c_int32)
+    u8p = C.POINTER(C.c_uint8)
+    lib.or_build.restype = C.c_void_p
+    lib.or_build.argtypes = [dp, C.c_int64, ip32, C.c_int64, C.c_int, C.c_double, C.c_int, C.c_int,
+                             C.c_int, C.c_int, C.c_int]
+    lib.or_free.argtypes = [C.c_void_p]
+    lib.or_info.argtypes = [C.c_void_p, ip64]
+    lib.or_tree.argtypes = [C.c_void_p, ip64, ip64, ip64, dp, dp, dp]
+    lib.or_blocks.argtypes = [C.c_void_p, ip32, ip32, u8p]
+    lib.or_V.argtypes = [C.c_void_p, dp]
+    lib.or_E.argtypes = [C.c_void_p, C.c_int64, dp]
+    lib.or_S.argtypes = [C.c_void_p, C.c_int64, C.c_int64, dp]
+    lib.or_lagrange.argtypes = [C.c_void_p, C.c_int64, C.c_int, dp, C.c_int64, dp]
+    lib.or_entry.restype = C.c_double
+    lib.or_entry.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int]
+    lib.or_pair_quad.restype = C.c_double
+    lib.or_pair_quad.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.or_dense.argtypes = [C.c_void_p, dp]
+    lib.or_matvec.restype = C.c_int
+    lib.or_matvec.argtypes = [C.c_void_p, dp, dp, C.c_int, dp, dp]
+    lib.or_matvec_rows.restype = C.c_int
+    lib.or_matvec_rows.argtypes = [C.c_void_p, dp, C.c_int, ip64, C.c_int64, dp]
+    lib.or_gmres.restype = C.c_int
+    lib.or_gmres.argtypes = [C.c_void_p, dp, dp, C.c_int, C.c_double, C.c_int, C.c_int,
+                             C.POINTER(C.c_int), dp]
+    lib.or_gauss01.argtypes = [C.c_int, dp, dp]
+    lib.or_threads.restype = C.c_int
+    lib.or_set_threads.argtypes = [C.c_int]
+    _lib = lib
+    return lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def gauss01(n: int):
+    """Gauss-Legendre nodes and weights on [0, 1] from the oracle."""
+    lib = _load()
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib.or_gauss01(n, _p(x, C.c_double), _p(w, C.c_double))
+    return x, w
+
+
+def pair_quad(T1, T2, mode: int, q: int, kind: int = KIND_LAPLACE, m: int = 1) -> float:
+    """Reference-domain integral of the kernel over T1 x T2 (no 4|T1||T2| factor).
+
+    mode 0 regular, 1 identical (T1 only), 2 common edge T1[0]T1[1] = T2[0]T2[1],
+    3 common vertex T1[0] = T2[0]."""
+    lib = _load()
+    a = np.ascontiguousarray(T1, dtype=np.float64).reshape(9)
+    b = np.ascontiguousarray(T2, dtype=np.float64).reshape(9)
+    return lib.or_pair_quad(_p(a, C.c_double), _p(b, C.c_double), mode, q, kind, m)
+
+
+def threads() -> int:
+    return _load().or_threads()
+
+
+def set_threads(n: int) -> None:
+    _load().or_set_threads(n)
+
+
+class Oracle:
+    """The oracle's H² approximation of one mesh (Section 2 of the paper)."""
+
+    def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, quad_order=3,
+                 kind=KIND_LAPLACE, store_near=True, with_bases=True):
+        lib = _load()
+        self._lib = lib
+        self.vert = np.ascontiguousarray(vert, dtype=np.float64)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.n = int(self.tri.shape[0])
+        self.m = int(order)
+        self.k = self.m ** 3
+        h = lib.or_build(_p(self.vert, C.c_double), self.vert.shape[0], _p(self.tri, C.c_int32), self.n,
+                         int(leaf_size), float(eta), self.m, int(quad_order), int(kind), int(store_near),
+                         int(with_bases))
+        if not h:
+            raise ValueError("oracle: invalid arguments")
+        self._h = C.c_void_p(h)
+        info = np.zeros(7, dtype=np.int64)
+        lib.or_info(self._h, _p(info, C.c_int64))
+        (self.depth, self.nclu, self.nblk, self.nadm, self.nnear, self.near_entries, _) = (int(v) for v in info)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.or_free(h)
+            self._h = None
+
+    # ---- structure ----
+    def tree(self):
+        nc = self.nclu
+        idx = np.zeros(self.n, dtype=np.int64)
+        first = np.zeros(nc, dtype=np.int64)
+        size = np.zeros(nc, dtype=np.int64)
+        lo = np.zeros((nc, 3))
+        hi = np.zeros((nc, 3))
+        pts = np.zeros((nc, 3, self.m))
+        self._lib.or_tree(self._h, _p(idx, C.c_int64), _p(first, C.c_int64), _p(size, C.c_int64),
+                          _p(lo, C.c_double), _p(hi, C.c_double), _p(pts, C.c_double))
+        return dict(idx=idx, first=first, size=size, lo=lo, hi=hi, pts=pts)
+
+    def blocks(self):
+        t = np.zeros(self.nblk, dtype=np.int32)
+        s = np.zeros(self.nblk, dtype=np.int32)
+        a = np.zeros(self.nblk, dtype=np.uint8)
+        self._lib.or_blocks(self._h, _p(t, C.c_int32), _p(s, C.c_int32), _p(a, C.c_uint8))
+        return t, s, a.astype(bool)
+
+    def V(self):
+        v = np.zeros((self.n, self.k))
+        self._lib.or_V(self._h, _p(v, C.c_double))
+        return v
+
+    def E(self, c: int):
+        e = np.zeros((self.k, self.k))
+        self._lib.or_E(self._h, int(c), _p(e, C.c_double))
+        return e
+
+    def S(self, t: int, s: int):
+        out = np.zeros((self.k, self.k))
+        self._lib.or_S(self._h, int(t), int(s), _p(out, C.c_double))
+        return out
+
+    def lagrange(self, c: int, nu: int, x):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros(x.shape[0])
+        self._lib.or_lagrange(self._h, int(c), int(nu), _p(x, C.c_double), x.shape[0], _p(out, C.c_double))
+        return out
+
+    def entry(self, i: int, j: int, q: int | None = None) -> float:
+        return self._lib.or_entry(self._h, int(i), int(j), int(q if q is not None else 3))
+
+    def dense(self):
+        g = np.zeros((self.n, self.n), order="F")
+        self._lib.or_dense(self._h, _p(g, C.c_double))
+        return g
+
+    # ---- products and solves ----
+    def matvec(self, x, coeffs: bool = False):
+        x = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(self.n, -1))
+        nrhs = x.shape[1]
+        y = np.zeros((self.n, nrhs), order="F")
+        if coeffs:
+            xh = np.zeros((self.nclu, self.k, nrhs))
+            yh = np.zeros((self.nclu, self.k, nrhs))
+            rc = self._lib.or_matvec(self._h, _p(x, C.c_double), _p(y, C.c_double), nrhs,
+                                     _p(xh, C.c_double), _p(yh, C.c_double))
+        else:
+            rc = self._lib.or_matvec(self._h, _p(x, C.c_double), _p(y, C.c_double), nrhs, None, None)
+        if rc:
+            raise RuntimeError("oracle built without bases")
+        return (y, xh, yh) if coeffs else y
+
+    def matvec_rows(self, x, rows):
+        x = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(self.n, -1))
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        nrhs = x.shape[1]
+        out = np.zeros((rows.shape[0], nrhs), order="F")
+        rc = self._lib.or_matvec_rows(self._h, _p(x, C.c_double), nrhs, _p(rows, C.c_int64), rows.shape[0],
+                                      _p(out, C.c_double))
+        if rc:
+            raise RuntimeError("oracle built without bases")
+        return out
+
+    def gmres(self, b, rtol=1e-8, restart=30, maxit=1000):
+        b = np.asfortranarray(np.asarray(b, dtype=np.float64).reshape(self.n, -1))
+        nrhs = b.shape[1]
+        z = np.zeros((self.n, nrhs), order="F")
+        iters = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs)
+        self._lib.or_gmres(self._h, _p(b, C.c_double), _p(z, C.c_double), nrhs, float(rtol), int(restart),
+                           int(maxit), iters.ctypes.data_as(C.POINTER(C.c_int)), _p(rel, C.c_double))
+        return z, iters, rel

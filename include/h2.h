@@ -1,0 +1,187 @@
+/*
+ * h2.h -- C ABI of libh2: the H^2-matrix approximation of the Galerkin
+ * single-layer matrix (Laplace kernel, piecewise-constant basis on flat
+ * triangles) and its matrix-vector product on one NVIDIA GB300 GPU.
+ *
+ * The operation follows Boerm, "Distributed H^2-matrices for boundary element
+ * methods", Section 2: the matrix G of Eq. (3) is approximated on admissible
+ * blocks (Eq. (8)) by V_t S_ts W_s^T (Eq. (7)) with interpolation bases
+ * (Eq. (6a-c)) and nested transfer matrices (Eqs. (9), (10)); the product runs
+ * as forward transformation (Algorithm 1), interaction (Algorithm 3) and
+ * backward transformation (Algorithm 2).  Test and trial bases coincide
+ * (piecewise constants on one mesh), so W = V and F = E.
+ *
+ * Conventions for every entry point:
+ *   - The return value is an h2_status; H2_OK is 0.  No call aborts, exits
+ *     or traps the GPU.  h2_last_error() gives a message for the calling
+ *     thread's most recent failure.
+ *   - The library copies every host array it is given and keeps no caller
+ *     pointer.  Handles own all device memory they allocate.
+ *   - Vectors are column-major n x nrhs arrays (leading dimension n) in the
+ *     caller's triangle order.
+ *   - A handle is not thread-safe; use one handle per host thread or
+ *     serialise calls.
+ */
+#ifndef H2_H
+#define H2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct h2_ctx *h2_handle;
+typedef struct h2_plan_ctx *h2_plan;
+
+enum h2_status {
+  H2_OK = 0,
+  H2_EINVAL = 1,   /* invalid argument (sizes, pointers, options) */
+  H2_ENOMEM = 2,   /* device or host allocation failed */
+  H2_ECUDA = 3,    /* a CUDA runtime call failed; see h2_last_error() */
+  H2_ENOCONV = 4,  /* iterative solve stopped at maxit; best iterate written */
+  H2_ETIMEOUT = 5, /* a bounded device wait ran out */
+  H2_PENDING = 6,  /* asynchronous result not ready yet */
+  H2_EBUSY = 7     /* resource in use */
+};
+
+/* arithmetic of the stored representation and of the product */
+enum h2_prec { H2_F64 = 0, H2_F32 = 1 };
+
+typedef struct h2_options {
+  int prec;          /* enum h2_prec; default H2_F64 */
+  int quad_order;    /* Gauss points per coordinate of the nearfield quadrature; default 3 */
+  int device;        /* CUDA device ordinal; default 0 */
+  void *stream;      /* cudaStream_t used by every call on the handle; NULL = the legacy default stream */
+  int reserved[8];   /* must be zero */
+} h2_options;
+
+/* Statistics of a built matrix (h2_info). */
+typedef struct h2_stats {
+  int64_t n;              /* triangles = degrees of freedom */
+  int64_t depth;          /* leaf level of the cluster tree (root = level 0) */
+  int64_t clusters;       /* 2^(depth+1) - 1 */
+  int64_t leaf_max;       /* largest leaf, the padded leaf height */
+  int64_t order;          /* interpolation points per axis m */
+  int64_t rank;           /* k = m^3 */
+  int64_t adm_blocks;     /* admissible leaves of the block tree */
+  int64_t near_blocks;    /* inadmissible leaves */
+  int64_t near_entries;   /* sum over inadmissible leaves of |t| |s| */
+  int64_t first_adm_level;/* smallest level holding an admissible block */
+  int64_t device_bytes;   /* device memory held by the handle (without work buffers) */
+  int64_t prec;           /* enum h2_prec */
+} h2_stats;
+
+/* Per right-hand side result of h2_solve. */
+typedef struct h2_solve_info {
+  int iters;          /* GMRES iterations (matrix-vector products in the Arnoldi process) */
+  int status;         /* H2_OK or H2_ENOCONV */
+  double relres;      /* true relative residual |b - G~ z| / |b| of the returned z */
+} h2_solve_info;
+
+/* Fill *opt with the defaults (FP64, quadrature order 3, device 0, default stream). */
+int h2_options_default(h2_options *opt);
+
+/* ---------------------------------------------------------------------------
+ * Host-only planning: cluster tree (Definition 1), block tree (Eq. (8)),
+ * interpolation points, leaf bases V (Eq. (6a)) and transfer factors (Eq. (9)).
+ * Needs no GPU.
+ *
+ * vert: nv x 3 row-major coordinates; tri: nt x 3 row-major 0-based vertex
+ * indices.  leaf_size >= 2, eta > 0, 1 <= order <= 6.
+ * Errors: H2_EINVAL for bad sizes, NULL pointers or out-of-range vertex
+ * indices; H2_ENOMEM.
+ * ------------------------------------------------------------------------- */
+int h2_plan_create(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta,
+                   int order, h2_plan *out);
+int h2_plan_destroy(h2_plan p);
+
+/* Query items of a plan.  Each call copies into caller memory of the size
+ * given; pass NULL to skip an item.
+ *   counts[8]  : n, depth, clusters, leaf_max, adm_blocks, near_blocks, near_entries, first_adm_level
+ *   perm[n]    : perm[p] = triangle index of degree of freedom p in cluster order
+ *   first[clusters], size[clusters] : index range of each cluster in cluster order
+ *   lo[clusters*3], hi[clusters*3]  : cluster boxes
+ *   adm_t/adm_s[adm_blocks]   : admissible blocks (row cluster, column cluster), sorted by (t, s)
+ *   near_t/near_s[near_blocks]: inadmissible blocks (cluster indices), sorted by (t, s)
+ *   V[n*k]     : leaf basis rows in cluster order (row p belongs to DoF p), Eq. (6a)
+ *   E[clusters*3*m*m] : per cluster and axis the m x m factor E_d[j'][j] of
+ *                the transfer matrix E_c = E_x (x) E_y (x) E_z, Eq. (9); root zero. */
+int h2_plan_counts(h2_plan p, int64_t *counts);
+int h2_plan_tree(h2_plan p, int64_t *perm, int64_t *first, int64_t *size, double *lo, double *hi);
+int h2_plan_blocks(h2_plan p, int32_t *adm_t, int32_t *adm_s, int32_t *near_t, int32_t *near_s);
+int h2_plan_bases(h2_plan p, double *V, double *E);
+
+/* ---------------------------------------------------------------------------
+ * Build the H^2 matrix on the device: plan as above, coupling matrices
+ * S_ts = g(xi_t, xi_s) (Eq. (6c)) and Sauter-Schwab nearfield entries of
+ * Eq. (3), stored in opt->prec.  opt may be NULL (defaults).
+ * Errors: H2_EINVAL, H2_ENOMEM (device memory), H2_ECUDA.
+ * ------------------------------------------------------------------------- */
+int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
+             const h2_options *opt, h2_handle *out);
+int h2_destroy(h2_handle h);
+int h2_info(h2_handle h, h2_stats *out);
+
+/* y = G~ x (overwrites y) for nrhs right-hand sides, Section 2 (the
+ * paper's y <- y + G x with y cleared first).  x, y: DEVICE pointers to
+ * column-major n x nrhs arrays of the handle's precision (double for H2_F64,
+ * float for H2_F32); they must not overlap.  Asynchronous on the handle's
+ * stream.  1 <= nrhs <= 64.
+ * Errors: H2_EINVAL (NULL, nrhs out of range), H2_ENOMEM (work buffers),
+ * H2_ECUDA (launch failure). */
+int h2_matvec(h2_handle h, const void *x, void *y, int nrhs);
+
+/* The same product with HOST double arrays whatever the handle's precision:
+ * copies x to the device, multiplies, copies y back and synchronises the
+ * stream. */
+int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs);
+
+/* Coefficients of the last product (diagnostics): which = 0 gives x^ after
+ * the forward transformation, 1 gives y^ after the interaction and the
+ * downward transfer (as used by the leaf backward step).  out: HOST double
+ * array [clusters][k][nrhs] of the last product's nrhs. */
+int h2_coefficients(h2_handle h, int which, double *out);
+
+/* Solve G~ z = b by restarted GMRES(restart) per column, z0 = 0, in FP64
+ * arithmetic around the handle's product.  b, z: column-major n x nrhs
+ * double arrays, both on the host or both on the device (detected).  A
+ * column stops when its true relative residual |b - G~ z| / |b| <= rtol or
+ * after maxit iterations (status H2_ENOCONV, best iterate written).  info
+ * (host, nrhs entries) may be NULL.  Returns H2_OK when every column
+ * converged, H2_ENOCONV otherwise. */
+int h2_solve(h2_handle h, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
+             h2_solve_info *info);
+
+/* Phases of the product, in launch order (h2_phase_times). */
+enum h2_phase {
+  H2_PH_PERMUTE_IN = 0,  /* caller order -> leaf-padded cluster order */
+  H2_PH_LEAF_FORWARD,    /* x^ = V^T x on the leaves (Algorithm 1) */
+  H2_PH_UPWARD,          /* x^_parent = sum E^T x^_child (Algorithm 1, Eq. (10)) */
+  H2_PH_COUPLING,        /* y^_t = sum S_ts x^_s (Algorithm 3, Eq. (6c)) */
+  H2_PH_DOWNWARD,        /* y^_child += E y^_parent (Algorithm 2) */
+  H2_PH_LEAF_NEAR,       /* y = V y^ + nearfield (Algorithms 2 and 3) */
+  H2_PH_PERMUTE_OUT,     /* cluster order -> caller order */
+  H2_NPHASE
+};
+
+/* Enable (1) or disable (0) per-phase timing: while enabled every product
+ * records CUDA events around each phase on the handle's stream.  Enabling
+ * clears the accumulated times. */
+int h2_profile(h2_handle h, int enable);
+
+/* Accumulated device time in milliseconds (ms[H2_NPHASE]) and kernel
+ * launches (launches[H2_NPHASE]) per phase since profiling was enabled,
+ * and the number of products timed (*products).  Synchronises the stream.
+ * Any output pointer may be NULL. */
+int h2_phase_times(h2_handle h, double *ms, int64_t *launches, int64_t *products);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *h2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2_H */

@@ -1,0 +1,263 @@
+"""ctypes binding of libh2 (include/h2.h): argument marshalling only.
+
+Every computation runs in the compiled library; if libh2.so is missing the
+calls raise instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ENOCONV, H2_ETIMEOUT, H2_PENDING, H2_EBUSY = range(8)
+H2_F64, H2_F32 = 0, 1
+PREC = {"f64": H2_F64, "f32": H2_F32}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class H2Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libh2 status {status}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("prec", C.c_int), ("quad_order", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
+                ("reserved", C.c_int * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in
+                ("n", "depth", "clusters", "leaf_max", "order", "rank", "adm_blocks", "near_blocks",
+                 "near_entries", "first_adm_level", "device_bytes", "prec")]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("relres", C.c_double)]
+
+
+EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_counts", "h2_plan_tree",
+            "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec",
+            "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_profile", "h2_phase_times", "h2_last_error"]
+PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libh2.so (built by ``__graft_entry__.build()`` / ``_build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libh2.so not found at {_build.LIB}: run __graft_entry__.build() first")
+        lib = C.CDLL(_build.LIB)
+        vp, dp, i64p, i32p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+        sig = {
+            "h2_options_default": (C.c_int, [C.POINTER(Options)]),
+            "h2_plan_create": (C.c_int, [dp, C.c_int64, i32p, C.c_int64, C.c_int, C.c_double, C.c_int,
+                                         C.POINTER(vp)]),
+            "h2_plan_destroy": (C.c_int, [vp]),
+            "h2_plan_counts": (C.c_int, [vp, i64p]),
+            "h2_plan_tree": (C.c_int, [vp, i64p, i64p, i64p, dp, dp]),
+            "h2_plan_blocks": (C.c_int, [vp, i32p, i32p, i32p, i32p]),
+            "h2_plan_bases": (C.c_int, [vp, dp, dp]),
+            "h2_build": (C.c_int, [dp, C.c_int64, i32p, C.c_int64, C.c_int, C.c_double, C.c_int,
+                                   C.POINTER(Options), C.POINTER(vp)]),
+            "h2_destroy": (C.c_int, [vp]),
+            "h2_info": (C.c_int, [vp, C.POINTER(Stats)]),
+            "h2_matvec": (C.c_int, [vp, vp, vp, C.c_int]),
+            "h2_matvec_host": (C.c_int, [vp, dp, dp, C.c_int]),
+            "h2_coefficients": (C.c_int, [vp, C.c_int, dp]),
+            "h2_solve": (C.c_int, [vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(SolveInfo)]),
+            "h2_profile": (C.c_int, [vp, C.c_int]),
+            "h2_phase_times": (C.c_int, [vp, dp, i64p, i64p]),
+            "h2_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status):
+    if status != H2_OK:
+        raise H2Error(status, load().h2_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _mesh(vert, tri):
+    v = np.ascontiguousarray(vert, dtype=np.float64)
+    t = np.ascontiguousarray(tri, dtype=np.int32)
+    if v.ndim != 2 or v.shape[1] != 3 or t.ndim != 2 or t.shape[1] != 3:
+        raise ValueError("vert must be (nv, 3) and tri (nt, 3)")
+    return v, t
+
+
+class Plan:
+    """Host-only planning (trees, blocks, V, transfer factors); needs no GPU."""
+
+    def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3):
+        lib = load()
+        v, t = _mesh(vert, tri)
+        h = C.c_void_p()
+        _check(lib.h2_plan_create(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
+                                  int(leaf_size), float(eta), int(order), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.m = int(order)
+        self.k = self.m ** 3
+        cnt = np.zeros(8, dtype=np.int64)
+        _check(lib.h2_plan_counts(h, cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+        (self.n, self.depth, self.nclu, self.leaf_max, self.nadm, self.nnear, self.near_entries,
+         self.first_adm_level) = (int(x) for x in cnt)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.h2_plan_destroy(h)
+            self._h = None
+
+    def tree(self):
+        i64 = lambda n: np.zeros(n, dtype=np.int64)
+        perm, first, size = i64(self.n), i64(self.nclu), i64(self.nclu)
+        lo, hi = np.zeros((self.nclu, 3)), np.zeros((self.nclu, 3))
+        p64 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int64))
+        _check(self._lib.h2_plan_tree(self._h, p64(perm), p64(first), p64(size), _dp(lo), _dp(hi)))
+        return dict(perm=perm, first=first, size=size, lo=lo, hi=hi)
+
+    def blocks(self):
+        i32 = lambda n: np.zeros(n, dtype=np.int32)
+        at, as_, nt, ns = i32(self.nadm), i32(self.nadm), i32(self.nnear), i32(self.nnear)
+        p32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        _check(self._lib.h2_plan_blocks(self._h, p32(at), p32(as_), p32(nt), p32(ns)))
+        return (at, as_), (nt, ns)
+
+    def bases(self):
+        V = np.zeros((self.n, self.k))
+        E = np.zeros((self.nclu, 3, self.m, self.m))
+        _check(self._lib.h2_plan_bases(self._h, _dp(V), _dp(E)))
+        return V, E
+
+
+def colmajor(t):
+    """A column-major (n, nrhs) view of a torch tensor (copies if needed)."""
+    if t.dim() == 1:
+        t = t[:, None]
+    if t.stride(0) == 1 and (t.shape[1] == 1 or t.stride(1) == t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+class H2Matrix:
+    """An H² matrix of one mesh on one GPU (see include/h2.h)."""
+
+    def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, prec="f64", quad_order=3, device=0,
+                 stream=None):
+        lib = load()
+        v, t = _mesh(vert, tri)
+        opt = Options()
+        _check(lib.h2_options_default(C.byref(opt)))
+        opt.prec = PREC[prec]
+        opt.quad_order = int(quad_order)
+        opt.device = int(device)
+        opt.stream = stream
+        h = C.c_void_p()
+        _check(lib.h2_build(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
+                            int(leaf_size), float(eta), int(order), C.byref(opt), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.prec = prec
+        self.n = int(t.shape[0])
+        self.device = int(device)
+        st = Stats()
+        _check(lib.h2_info(h, C.byref(st)))
+        self.stats = {f: int(getattr(st, f)) for f, _ in Stats._fields_}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.h2_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def matvec(self, x, y):
+        """y = G~ x on the device; x, y column-major CUDA tensors (n, nrhs) of the handle's dtype."""
+        if x.shape != y.shape or x.shape[0] != self.n:
+            raise ValueError("x and y must both be (n, nrhs)")
+        if x.stride(0) != 1 or y.stride(0) != 1:
+            raise ValueError("x and y must be column-major (use colmajor())")
+        _check(self._lib.h2_matvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.shape[1])))
+        return y
+
+    def profile(self, enable=True):
+        """Start (or stop) per-phase CUDA-event timing on the handle's stream."""
+        _check(self._lib.h2_profile(self._h, 1 if enable else 0))
+
+    def phase_times(self):
+        """{phase: (ms total, kernel launches)} since profile(True), and the products timed."""
+        ms = np.zeros(len(PHASES))
+        ln = np.zeros(len(PHASES), dtype=np.int64)
+        pr = np.zeros(1, dtype=np.int64)
+        _check(self._lib.h2_phase_times(self._h, _dp(ms), ln.ctypes.data_as(C.POINTER(C.c_int64)),
+                                        pr.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {p: (float(a), int(b)) for p, a, b in zip(PHASES, ms, ln)}, int(pr[0])
+
+    def matvec_host(self, x):
+        """y = G~ x from host FP64 arrays (numpy, or pinned torch CPU tensors given as (x, y))."""
+        if isinstance(x, tuple):
+            xt, yt = x
+            _check(self._lib.h2_matvec_host(self._h, C.cast(C.c_void_p(xt.data_ptr()), C.POINTER(C.c_double)),
+                                            C.cast(C.c_void_p(yt.data_ptr()), C.POINTER(C.c_double)),
+                                            int(xt.shape[1])))
+            return yt
+        x = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(self.n, -1))
+        y = np.zeros_like(x, order="F")
+        _check(self._lib.h2_matvec_host(self._h, _dp(x), _dp(y), int(x.shape[1])))
+        return y
+
+    def coefficients(self, which, nrhs):
+        out = np.zeros((self.stats["clusters"], self.stats["rank"], nrhs))
+        _check(self._lib.h2_coefficients(self._h, int(which), _dp(out)))
+        return out
+
+    def solve(self, b, rtol=1e-8, restart=30, maxit=1000):
+        """GMRES(restart) solve; b numpy (host) or column-major CUDA tensor (device)."""
+        nrhs = b.shape[1] if b.ndim == 2 else 1
+        info = (SolveInfo * nrhs)()
+        if isinstance(b, np.ndarray):
+            bb = np.asfortranarray(np.asarray(b, dtype=np.float64).reshape(self.n, -1))
+            z = np.zeros_like(bb, order="F")
+            st = self._lib.h2_solve(self._h, bb.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p), nrhs,
+                                    float(rtol), int(restart), int(maxit), info)
+        else:
+            import torch
+            bb = colmajor(b)
+            z = colmajor(torch.zeros_like(bb))
+            st = self._lib.h2_solve(self._h, C.c_void_p(bb.data_ptr()), C.c_void_p(z.data_ptr()), nrhs,
+                                    float(rtol), int(restart), int(maxit), info)
+        if st not in (H2_OK, H2_ENOCONV):
+            _check(st)
+        it = np.array([i.iters for i in info])
+        rel = np.array([i.relres for i in info])
+        return z, it, rel, st

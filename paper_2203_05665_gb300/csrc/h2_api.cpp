@@ -1,0 +1,307 @@
+// C ABI of libh2 (declared in include/h2.h): argument checking, handles,
+// error reporting, host <-> device staging.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "h2_internal.hpp"
+
+struct h2_ctx : h2::Ctx {};
+struct h2_plan_ctx {
+  h2::Plan plan;
+};
+
+namespace h2 {
+
+static thread_local std::string g_last_error;
+
+int fail(int status, const std::string &msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? H2_ENOMEM : H2_ECUDA;
+}
+
+static void free_dev(Dev &d) {
+  void *ptrs[] = {d.pad_src, d.V,    d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
+                  d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  d = Dev();
+}
+
+}  // namespace h2
+
+using namespace h2;
+
+extern "C" {
+
+const char *h2_last_error(void) { return g_last_error.c_str(); }
+
+int h2_options_default(h2_options *opt) {
+  if (!opt) return fail(H2_EINVAL, "opt is NULL");
+  std::memset(opt, 0, sizeof(*opt));
+  opt->prec = H2_F64;
+  opt->quad_order = 3;
+  opt->device = 0;
+  opt->stream = nullptr;
+  return H2_OK;
+}
+
+int h2_plan_create(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta,
+                   int order, h2_plan *out) {
+  if (!out) return fail(H2_EINVAL, "out is NULL");
+  *out = nullptr;
+  h2_plan_ctx *p = new (std::nothrow) h2_plan_ctx();
+  if (!p) return fail(H2_ENOMEM, "plan");
+  int rc;
+  try {
+    rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, true, p->plan);
+  } catch (const std::bad_alloc &) {
+    rc = fail(H2_ENOMEM, "host allocation in planning");
+  }
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return H2_OK;
+}
+
+int h2_plan_destroy(h2_plan p) {
+  delete p;
+  return H2_OK;
+}
+
+int h2_plan_counts(h2_plan pp, int64_t *counts) {
+  if (!pp || !counts) return fail(H2_EINVAL, "NULL argument");
+  const Plan &p = pp->plan;
+  counts[0] = p.n;
+  counts[1] = p.depth;
+  counts[2] = p.nclu;
+  counts[3] = p.lmax;
+  counts[4] = (int64_t)p.adm_col.size();
+  counts[5] = (int64_t)p.near_col.size();
+  counts[6] = p.near_entries;
+  counts[7] = p.first_adm_level;
+  return H2_OK;
+}
+
+int h2_plan_tree(h2_plan pp, int64_t *perm, int64_t *first, int64_t *size, double *lo, double *hi) {
+  if (!pp) return fail(H2_EINVAL, "NULL plan");
+  const Plan &p = pp->plan;
+  if (perm) std::memcpy(perm, p.perm.data(), p.n * 8);
+  if (first) std::memcpy(first, p.first.data(), p.nclu * 8);
+  if (size) std::memcpy(size, p.size.data(), p.nclu * 8);
+  if (lo) std::memcpy(lo, p.lo.data(), p.nclu * 24);
+  if (hi) std::memcpy(hi, p.hi.data(), p.nclu * 24);
+  return H2_OK;
+}
+
+int h2_plan_blocks(h2_plan pp, int32_t *adm_t, int32_t *adm_s, int32_t *near_t, int32_t *near_s) {
+  if (!pp) return fail(H2_EINVAL, "NULL plan");
+  const Plan &p = pp->plan;
+  for (int64_t t = 0; t < p.nclu; ++t)
+    for (int64_t e = p.adm_ptr[t]; e < p.adm_ptr[t + 1]; ++e) {
+      if (adm_t) adm_t[e] = (int32_t)t;
+      if (adm_s) adm_s[e] = p.adm_col[e];
+    }
+  for (int64_t j = 0; j < p.nleaf; ++j)
+    for (int64_t e = p.near_ptr[j]; e < p.near_ptr[j + 1]; ++e) {
+      if (near_t) near_t[e] = (int32_t)(p.leaf0 + j);
+      if (near_s) near_s[e] = (int32_t)(p.leaf0 + p.near_col[e]);
+    }
+  return H2_OK;
+}
+
+int h2_plan_bases(h2_plan pp, double *V, double *E) {
+  if (!pp) return fail(H2_EINVAL, "NULL plan");
+  const Plan &p = pp->plan;
+  if (V) std::memcpy(V, p.V.data(), p.V.size() * 8);
+  if (E) std::memcpy(E, p.Ef.data(), p.Ef.size() * 8);
+  return H2_OK;
+}
+
+int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
+             const h2_options *opt, h2_handle *out) {
+  if (!out) return fail(H2_EINVAL, "out is NULL");
+  *out = nullptr;
+  h2_options o;
+  h2_options_default(&o);
+  if (opt) o = *opt;
+  if (o.prec != H2_F64 && o.prec != H2_F32) return fail(H2_EINVAL, "prec must be H2_F64 or H2_F32");
+  for (int r : o.reserved)
+    if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
+  int ndev = 0;
+  H2_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (o.device < 0 || o.device >= ndev) return fail(H2_EINVAL, "device ordinal out of range");
+  H2_CUDA_TRY(cudaSetDevice(o.device));
+  h2_ctx *c = new (std::nothrow) h2_ctx();
+  if (!c) return fail(H2_ENOMEM, "handle");
+  c->device = o.device;
+  c->stream = (cudaStream_t)o.stream;
+  c->quad_order = o.quad_order;
+  c->d.prec = o.prec;
+  int rc;
+  try {
+    rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, true, c->plan);
+    if (!rc) rc = device_build(*c);
+  } catch (const std::bad_alloc &) {
+    rc = fail(H2_ENOMEM, "host allocation in set-up");
+  }
+  if (rc) {
+    free_dev(c->d);
+    delete c;
+    return rc;
+  }
+  // the host copy of V is not needed after the upload
+  std::vector<double>().swap(c->plan.V);
+  *out = c;
+  return H2_OK;
+}
+
+static void drop_events(Prof &p) {
+  for (auto e : p.ev) cudaEventDestroy(e);
+  p.ev.clear();
+}
+
+int h2_destroy(h2_handle h) {
+  if (!h) return H2_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  drop_events(h->prof);
+  free_dev(h->d);
+  delete h;
+  return H2_OK;
+}
+
+int h2_info(h2_handle h, h2_stats *out) {
+  if (!h || !out) return fail(H2_EINVAL, "NULL argument");
+  const Plan &p = h->plan;
+  out->n = p.n;
+  out->depth = p.depth;
+  out->clusters = p.nclu;
+  out->leaf_max = p.lmax;
+  out->order = p.m;
+  out->rank = p.k;
+  out->adm_blocks = (int64_t)p.adm_col.size();
+  out->near_blocks = (int64_t)p.near_col.size();
+  out->near_entries = p.near_entries;
+  out->first_adm_level = p.first_adm_level;
+  out->device_bytes = h->d.bytes;
+  out->prec = h->d.prec;
+  return H2_OK;
+}
+
+int h2_profile(h2_handle h, int enable) {
+  if (!h) return fail(H2_EINVAL, "NULL handle");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  drop_events(h->prof);
+  h->prof.on = enable != 0;
+  h->prof.launches.assign(H2_NPHASE, 0);
+  h->prof.products = 0;
+  for (double &v : h->prof.ms) v = 0.0;
+  return H2_OK;
+}
+
+int h2_phase_times(h2_handle h, double *ms, int64_t *launches, int64_t *products) {
+  if (!h) return fail(H2_EINVAL, "NULL handle");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  Prof &p = h->prof;
+  const size_t per = H2_NPHASE + 1;
+  for (size_t b = 0; b + per <= p.ev.size(); b += per)
+    for (int i = 0; i < H2_NPHASE; ++i) {
+      float t = 0;
+      H2_CUDA_TRY(cudaEventElapsedTime(&t, p.ev[b + i], p.ev[b + i + 1]));
+      p.ms[i] += t;
+    }
+  drop_events(p);
+  if (ms)
+    for (int i = 0; i < H2_NPHASE; ++i) ms[i] = p.ms[i];
+  if (launches)
+    for (int i = 0; i < H2_NPHASE; ++i) launches[i] = i < (int)p.launches.size() ? p.launches[i] : 0;
+  if (products) *products = p.products;
+  return H2_OK;
+}
+
+int h2_matvec(h2_handle h, const void *x, void *y, int nrhs) {
+  if (!h || !x || !y) return fail(H2_EINVAL, "NULL argument");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  return run_matvec(*h, x, y, nrhs, false);
+}
+
+int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs) {
+  if (!h || !x || !y) return fail(H2_EINVAL, "NULL argument");
+  if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  int rc = ensure_work(*h, nrhs);
+  if (rc) return rc;
+  size_t bytes = (size_t)h->d.n * nrhs * 8;
+  H2_CUDA_TRY(cudaMemcpyAsync(h->d.io_x, x, bytes, cudaMemcpyHostToDevice, h->stream));
+  if ((rc = run_matvec(*h, h->d.io_x, h->d.io_y, nrhs, true))) return rc;
+  H2_CUDA_TRY(cudaMemcpyAsync(y, h->d.io_y, bytes, cudaMemcpyDeviceToHost, h->stream));
+  H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return H2_OK;
+}
+
+int h2_coefficients(h2_handle h, int which, double *out) {
+  if (!h || !out || (which != 0 && which != 1)) return fail(H2_EINVAL, "bad argument");
+  if (h->d.last_nrhs < 1) return fail(H2_EINVAL, "no product has run on this handle");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const Dev &d = h->d;
+  // the work buffers are laid out for cap_nrhs; the last product used last_nrhs
+  size_t cnt = (size_t)d.nclu * d.k * d.last_nrhs;
+  const void *src = which == 0 ? d.xhat : d.yhat;
+  if (d.prec == H2_F64) {
+    H2_CUDA_TRY(cudaMemcpy(out, src, cnt * 8, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(cnt);
+    H2_CUDA_TRY(cudaMemcpy(tmp.data(), src, cnt * 4, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < cnt; ++i) out[i] = tmp[i];
+  }
+  return H2_OK;
+}
+
+int h2_solve(h2_handle h, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
+             h2_solve_info *info) {
+  if (!h || !b || !z) return fail(H2_EINVAL, "NULL argument");
+  if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");
+  if (restart < 1 || restart > 200 || maxit < 1 || !(rtol > 0.0)) return fail(H2_EINVAL, "bad solver parameters");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  cudaPointerAttributes ab{}, az{};
+  H2_CUDA_TRY(cudaPointerGetAttributes(&ab, b));
+  H2_CUDA_TRY(cudaPointerGetAttributes(&az, z));
+  bool db = ab.type == cudaMemoryTypeDevice || ab.type == cudaMemoryTypeManaged;
+  bool dz = az.type == cudaMemoryTypeDevice || az.type == cudaMemoryTypeManaged;
+  if (db != dz) return fail(H2_EINVAL, "b and z must both be host or both be device arrays");
+  if (db) return run_gmres(*h, b, z, nrhs, rtol, restart, maxit, info);
+  size_t bytes = (size_t)h->d.n * nrhs * 8;
+  double *db_ = nullptr, *dz_ = nullptr;
+  if (cudaMalloc(&db_, bytes) != cudaSuccess || cudaMalloc(&dz_, bytes) != cudaSuccess) {
+    cudaFree(db_);
+    cudaGetLastError();
+    return fail(H2_ENOMEM, "solve staging buffers");
+  }
+  int rc = H2_OK;
+  cudaError_t e = cudaMemcpyAsync(db_, b, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) rc = cuda_fail(e, "copy b");
+  if (!rc || rc == H2_ENOCONV) rc = run_gmres(*h, db_, dz_, nrhs, rtol, restart, maxit, info);
+  if (!rc || rc == H2_ENOCONV) {
+    e = cudaMemcpyAsync(z, dz_, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy z");
+  }
+  cudaFree(db_);
+  cudaFree(dz_);
+  return rc;
+}
+
+}  // extern "C"

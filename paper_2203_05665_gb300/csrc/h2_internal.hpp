@@ -1,0 +1,113 @@
+// Internal declarations of libh2 (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/h2.h"
+
+namespace h2 {
+
+// Sets the calling thread's error message and returns the status.
+int fail(int status, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define H2_CUDA_TRY(call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return ::h2::cuda_fail(e_, #call); \
+  } while (0)
+
+// Gauss-Legendre nodes and weights on [0,1] (Newton on the Legendre recurrence).
+void gauss_legendre01(int q, std::vector<double> &x, std::vector<double> &w);
+
+// Host-side plan: cluster tree (Definition 1 with median bisection), block
+// tree (Eq. (8)), Chebyshev points, leaf bases V (Eq. (6a)) and the factors
+// of the transfer matrices (Eq. (9)).
+struct Plan {
+  int64_t n = 0, nv = 0;
+  std::vector<double> vert;    // nv x 3
+  std::vector<int32_t> tri;    // n x 3
+  std::vector<double> area;    // n
+  std::vector<double> cen;     // n x 3
+  int leaf = 0, m = 0, k = 0, depth = 0;
+  double eta = 0;
+  int64_t nclu = 0, nleaf = 0, lmax = 0, leaf0 = 0;
+  std::vector<int64_t> perm;   // cluster order -> triangle
+  std::vector<int64_t> first, size;
+  std::vector<double> lo, hi;  // nclu x 3
+  std::vector<double> cheb;    // nclu x 3 x m
+  // admissible blocks in CSR by row cluster (columns sorted)
+  std::vector<int64_t> adm_ptr;   // nclu + 1
+  std::vector<int32_t> adm_col;
+  // inadmissible blocks in CSR by row leaf (leaf-local indices, sorted)
+  std::vector<int64_t> near_ptr;  // nleaf + 1
+  std::vector<int32_t> near_col;
+  int first_adm_level = 0;
+  int64_t near_entries = 0;
+  std::vector<double> V;       // n x k, cluster order
+  std::vector<double> Ef;      // nclu x 3 x m x m
+};
+
+int make_plan(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
+              bool with_bases, Plan &p);
+
+// Device representation of one H^2 matrix.
+struct Dev {
+  int prec = H2_F64;
+  size_t esize = 8;
+  int m = 0, k = 0, depth = 0, first_adm_level = 0;
+  int64_t n = 0, nclu = 0, nleaf = 0, lmax = 0, npad = 0;
+  int64_t nadm = 0, nnear = 0;
+  int32_t *pad_src = nullptr;   // npad: original triangle index of padded DoF, or -1
+  void *V = nullptr;            // nleaf x lmax x k
+  void *Ef = nullptr;           // nclu x 3 x m x m
+  void *S = nullptr;            // nadm x k x k (row nu, column mu)
+  void *near = nullptr;         // nnear x lmax x lmax (row r, column c)
+  int64_t *adm_ptr = nullptr;   // nclu + 1
+  int32_t *adm_col = nullptr;
+  int64_t *near_ptr = nullptr;  // nleaf + 1
+  int32_t *near_col = nullptr;  // leaf-local
+  double *cheb = nullptr;       // nclu x 3 x m (FP64 always)
+  // work buffers for up to cap_nrhs right-hand sides
+  int cap_nrhs = 0;
+  void *xpad = nullptr, *ypad = nullptr, *xhat = nullptr, *yhat = nullptr;
+  double *io_x = nullptr, *io_y = nullptr;   // FP64 staging for host / solver I/O
+  int last_nrhs = 0;
+  int64_t bytes = 0;
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;      // (H2_NPHASE + 1) events per recorded product
+  std::vector<int64_t> launches;    // per phase, accumulated
+  int64_t products = 0;
+  double ms[H2_NPHASE] = {0};
+};
+
+struct Ctx {
+  Prof prof;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int quad_order = 3;
+  Plan plan;
+  Dev d;
+};
+
+// device allocation helper (tracks bytes)
+int dev_alloc(Dev &d, void **ptr, size_t bytes);
+int ensure_work(Ctx &c, int nrhs);
+
+// build steps on the device (h2_setup.cu)
+int device_build(Ctx &c);
+// y = G~ x with device arrays of the handle's precision (h2_matvec.cu);
+// if x64/y64 are given instead the product reads/writes FP64 arrays.
+int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64);
+// GMRES (h2_solve.cu); b, z device FP64 arrays
+int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
+              h2_solve_info *info);
+
+}  // namespace h2

@@ -1,0 +1,394 @@
+// Device-side set-up of the H^2 matrix: coupling matrices (Eq. (6c)) and
+// Sauter-Schwab nearfield entries of the Galerkin matrix (Eq. (3)).
+//
+// Quadrature conventions (shared with nothing; restated from the published
+// Sauter-Schwab method):
+//   reference triangle {0 <= t <= s <= 1}, map A + s (B - A) + t (C - B),
+//   Jacobian 2|T|; regular pairs: collapsed Gauss (s, t) = (u, u v) with
+//   weight u and q points per direction, vertices in mesh order; pairs that
+//   share vertices: q^4 Gauss points on [0,1]^4 over the method's regions,
+//   canonical vertex order (identical: smallest id first, cyclic; edge:
+//   smaller shared id, larger shared id, other; vertex: shared, then the
+//   triangle's cyclic successors).  Each entry is evaluated with the
+//   smaller triangle index as test triangle, so G is symmetric bit for bit.
+#include <cstdio>
+#include <vector>
+
+#include "h2_internal.hpp"
+
+namespace h2 {
+
+namespace {
+
+constexpr int kMaxQ = 16;
+__constant__ double c_gx[kMaxQ];
+__constant__ double c_gw[kMaxQ];
+
+constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
+
+__device__ __forceinline__ double green(const double *x, const double *y) {
+  double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  return kInv4Pi / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+__device__ __forceinline__ void tri_point(const double *A, const double *B, const double *C, double s, double t,
+                                          double *x) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = A[d] + s * (B[d] - A[d]) + t * (C[d] - B[d]);
+}
+
+// ---------------------------------------------------------------- coupling
+template <class T>
+__global__ void k_coupling_fill(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+                                const double *__restrict__ cheb, int m, int64_t nblk, T *__restrict__ S) {
+  const int k = m * m * m;
+  const int64_t total = nblk * k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / (k * k);
+    int rem = (int)(e - b * k * k);
+    int nu = rem / k, mu = rem - nu * k;
+    int64_t t = row[b], s = col[b];
+    double x[3], y[3];
+    x[0] = cheb[(3 * t + 0) * m + nu % m];
+    x[1] = cheb[(3 * t + 1) * m + (nu / m) % m];
+    x[2] = cheb[(3 * t + 2) * m + nu / (m * m)];
+    y[0] = cheb[(3 * s + 0) * m + mu % m];
+    y[1] = cheb[(3 * s + 1) * m + (mu / m) % m];
+    y[2] = cheb[(3 * s + 2) * m + mu / (m * m)];
+    S[e] = (T)green(x, y);
+  }
+}
+
+// ---------------------------------------------------------------- nearfield
+struct Geo {
+  const double *vert;
+  const int32_t *tri;
+  const double *area;
+  const int32_t *pad_src;
+  const int32_t *blk_row;   // row leaf of each near block
+  const int32_t *blk_col;   // column leaf of each near block
+  int64_t lmax;
+};
+
+__device__ __forceinline__ int shared_count(const int32_t *a, const int32_t *b) {
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c += (a[i] == b[j]);
+  return c;
+}
+
+// Regular entries; entries whose triangles share a vertex are listed for the
+// singular pass and left for it.
+template <class T>
+__global__ void k_near_regular(Geo g, int64_t nblk, int q, T *__restrict__ near, int64_t *__restrict__ sing,
+                               unsigned long long *__restrict__ nsing, int64_t sing_cap) {
+  const int64_t L = g.lmax, per = L * L, total = nblk * per;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / per;
+    int rc = (int)(e - b * per);
+    int r = rc / (int)L, c = rc - r * (int)L;
+    int32_t i = g.pad_src[g.blk_row[b] * L + r], j = g.pad_src[g.blk_col[b] * L + c];
+    if (i < 0 || j < 0) { near[e] = (T)0; continue; }
+    if (i > j) { int32_t t = i; i = j; j = t; }
+    int32_t ti[3] = {g.tri[3 * i], g.tri[3 * i + 1], g.tri[3 * i + 2]};
+    int32_t tj[3] = {g.tri[3 * j], g.tri[3 * j + 1], g.tri[3 * j + 2]};
+    if (shared_count(ti, tj) > 0) {
+      unsigned long long slot = atomicAdd(nsing, 1ull);
+      if ((int64_t)slot < sing_cap) sing[slot] = e;
+      near[e] = (T)0;
+      continue;
+    }
+    const double *A1 = g.vert + 3 * ti[0], *B1 = g.vert + 3 * ti[1], *C1 = g.vert + 3 * ti[2];
+    const double *A2 = g.vert + 3 * tj[0], *B2 = g.vert + 3 * tj[1], *C2 = g.vert + 3 * tj[2];
+    double acc = 0.0;
+    for (int a = 0; a < q; ++a)
+      for (int bb = 0; bb < q; ++bb) {
+        double x[3];
+        tri_point(A1, B1, C1, c_gx[a], c_gx[a] * c_gx[bb], x);
+        double wx = c_gw[a] * c_gw[bb] * c_gx[a];
+        double inner = 0.0;
+        for (int cc = 0; cc < q; ++cc)
+          for (int dd = 0; dd < q; ++dd) {
+            double y[3];
+            tri_point(A2, B2, C2, c_gx[cc], c_gx[cc] * c_gx[dd], y);
+            inner += c_gw[cc] * c_gw[dd] * c_gx[cc] * green(x, y);
+          }
+        acc += wx * inner;
+      }
+    near[e] = (T)(4.0 * g.area[i] * g.area[j] * acc);
+  }
+}
+
+// Region r of the singular rules at (xi, e1, e2, e3): reference points of the
+// test triangle (x1, x2) and of the trial triangle (y1, y2), and the weight.
+// kind 3 = identical (6 regions), 2 = common edge (5), 1 = common vertex (2).
+__device__ __forceinline__ double sing_region(int kind, int r, double xi, double e1, double e2, double e3,
+                                              double *p) {
+  if (kind == 3) {
+    double w = xi * xi * xi * e1 * e1 * e2;
+    double a = xi, b = xi * (1 - e1 + e1 * e2), c = xi * (1 - e1 * e2 * e3), d = xi * (1 - e1);
+    double f = xi * e1 * (1 - e2 + e2 * e3), g = xi * (1 - e1 * e2), hh = xi * e1 * (1 - e2);
+    double u = xi * e1 * (1 - e2 * e3);
+    switch (r) {
+      case 0: p[0] = a; p[1] = b; p[2] = c; p[3] = d; break;
+      case 1: p[0] = c; p[1] = d; p[2] = a; p[3] = b; break;
+      case 2: p[0] = a; p[1] = f; p[2] = g; p[3] = hh; break;
+      case 3: p[0] = g; p[1] = hh; p[2] = a; p[3] = f; break;
+      case 4: p[0] = c; p[1] = u; p[2] = a; p[3] = hh; break;
+      default: p[0] = a; p[1] = hh; p[2] = c; p[3] = u; break;
+    }
+    return w;
+  }
+  if (kind == 2) {
+    double w1 = xi * xi * xi * e1 * e1;
+    switch (r) {
+      case 0: p[0] = xi; p[1] = xi * e1 * e3; p[2] = xi * (1 - e1 * e2); p[3] = xi * e1 * (1 - e2); return w1;
+      case 1: p[0] = xi; p[1] = xi * e1; p[2] = xi * (1 - e1 * e2 * e3); p[3] = xi * e1 * e2 * (1 - e3); return w1 * e2;
+      case 2: p[0] = xi * (1 - e1 * e2); p[1] = xi * e1 * (1 - e2); p[2] = xi; p[3] = xi * e1 * e2 * e3; return w1 * e2;
+      case 3: p[0] = xi * (1 - e1 * e2 * e3); p[1] = xi * e1 * e2 * (1 - e3); p[2] = xi; p[3] = xi * e1; return w1 * e2;
+      default: p[0] = xi * (1 - e1 * e2 * e3); p[1] = xi * e1 * (1 - e2 * e3); p[2] = xi; p[3] = xi * e1 * e2; return w1 * e2;
+    }
+  }
+  double w = xi * xi * xi * e2;
+  if (r == 0) { p[0] = xi; p[1] = xi * e1; p[2] = xi * e2; p[3] = xi * e2 * e3; }
+  else { p[0] = xi * e2; p[1] = xi * e2 * e3; p[2] = xi; p[3] = xi * e1; }
+  return w;
+}
+
+template <class T>
+__global__ void k_near_singular(Geo g, const int64_t *__restrict__ sing, int64_t nsing, int q, T *__restrict__ near) {
+  const int64_t L = g.lmax, per = L * L;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsing; s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = sing[s];
+    int64_t b = e / per;
+    int rc = (int)(e - b * per);
+    int r = rc / (int)L, c = rc - r * (int)L;
+    int32_t i = g.pad_src[g.blk_row[b] * L + r], j = g.pad_src[g.blk_col[b] * L + c];
+    if (i > j) { int32_t t = i; i = j; j = t; }
+    int32_t ti[3] = {g.tri[3 * i], g.tri[3 * i + 1], g.tri[3 * i + 2]};
+    int32_t tj[3] = {g.tri[3 * j], g.tri[3 * j + 1], g.tri[3 * j + 2]};
+    int ns = shared_count(ti, tj);
+    int32_t P[3], Q[3];   // canonical local vertex orders
+    if (ns >= 3) {
+      int a = 0;
+      if (ti[1] < ti[a]) a = 1;
+      if (ti[2] < ti[a]) a = 2;
+      for (int v = 0; v < 3; ++v) P[v] = Q[v] = ti[(a + v) % 3];
+    } else if (ns == 2) {
+      int32_t s0 = -1, s1 = -1, oi = -1, oj = -1;
+      for (int v = 0; v < 3; ++v) {
+        bool in = (ti[v] == tj[0]) || (ti[v] == tj[1]) || (ti[v] == tj[2]);
+        if (in) { if (s0 < 0) s0 = ti[v]; else s1 = ti[v]; } else oi = ti[v];
+        bool inj = (tj[v] == ti[0]) || (tj[v] == ti[1]) || (tj[v] == ti[2]);
+        if (!inj) oj = tj[v];
+      }
+      int32_t lo_ = s0 < s1 ? s0 : s1, hi_ = s0 < s1 ? s1 : s0;
+      P[0] = lo_; P[1] = hi_; P[2] = oi;
+      Q[0] = lo_; Q[1] = hi_; Q[2] = oj;
+    } else {
+      int a = 0, bb = 0;
+      for (int u = 0; u < 3; ++u)
+        for (int v = 0; v < 3; ++v)
+          if (ti[u] == tj[v]) { a = u; bb = v; }
+      for (int v = 0; v < 3; ++v) { P[v] = ti[(a + v) % 3]; Q[v] = tj[(bb + v) % 3]; }
+    }
+    const double *A1 = g.vert + 3 * P[0], *B1 = g.vert + 3 * P[1], *C1 = g.vert + 3 * P[2];
+    const double *A2 = g.vert + 3 * Q[0], *B2 = g.vert + 3 * Q[1], *C2 = g.vert + 3 * Q[2];
+    int kind = ns >= 3 ? 3 : ns;
+    int nreg = kind == 3 ? 6 : (kind == 2 ? 5 : 2);
+    double acc = 0.0;
+    for (int i0 = 0; i0 < q; ++i0)
+      for (int i1 = 0; i1 < q; ++i1)
+        for (int i2 = 0; i2 < q; ++i2)
+          for (int i3 = 0; i3 < q; ++i3) {
+            double part = 0.0;
+            for (int rg = 0; rg < nreg; ++rg) {
+              double pr[4];
+              double w = sing_region(kind, rg, c_gx[i0], c_gx[i1], c_gx[i2], c_gx[i3], pr);
+              double x[3], y[3];
+              tri_point(A1, B1, C1, pr[0], pr[1], x);
+              tri_point(A2, B2, C2, pr[2], pr[3], y);
+              part += w * green(x, y);
+            }
+            acc += c_gw[i0] * c_gw[i1] * c_gw[i2] * c_gw[i3] * part;
+          }
+    near[e] = (T)(4.0 * g.area[i] * g.area[j] * acc);
+  }
+}
+
+template <class T>
+__global__ void k_convert(const double *__restrict__ src, T *__restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 64) g = 152 * 64;
+  return (int)g;
+}
+
+template <class T>
+int upload_converted(Dev &d, void **dst, const std::vector<double> &src, cudaStream_t st) {
+  int rc = dev_alloc(d, dst, src.size() * sizeof(T));
+  if (rc) return rc;
+  if (src.empty()) return H2_OK;
+  double *tmp = nullptr;
+  H2_CUDA_TRY(cudaMalloc(&tmp, src.size() * sizeof(double)));
+  cudaError_t e = cudaMemcpyAsync(tmp, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_convert<T><<<grid_for((int64_t)src.size(), 256), 256, 0, st>>>(tmp, (T *)*dst, (int64_t)src.size());
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "upload");
+  return H2_OK;
+}
+
+template <class T>
+int build_typed(Ctx &c) {
+  Plan &p = c.plan;
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  const int m = p.m, k = p.k;
+  const int64_t L = p.lmax;
+
+  // padded DoF layout: leaf j owns rows [j L, j L + size_j)
+  std::vector<int32_t> pad(d.npad, -1);
+  for (int64_t j = 0; j < p.nleaf; ++j) {
+    int64_t c0 = p.leaf0 + j;
+    for (int64_t r = 0; r < p.size[c0]; ++r) pad[j * L + r] = (int32_t)p.perm[p.first[c0] + r];
+  }
+  // V padded to L rows per leaf
+  std::vector<double> Vp((size_t)d.npad * k, 0.0);
+  for (int64_t j = 0; j < p.nleaf; ++j) {
+    int64_t c0 = p.leaf0 + j;
+    for (int64_t r = 0; r < p.size[c0]; ++r)
+      for (int nu = 0; nu < k; ++nu) Vp[(j * L + r) * k + nu] = p.V[(p.first[c0] + r) * k + nu];
+  }
+  int rc;
+  if ((rc = dev_alloc(d, (void **)&d.pad_src, pad.size() * 4))) return rc;
+  H2_CUDA_TRY(cudaMemcpyAsync(d.pad_src, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, st));
+  if ((rc = upload_converted<T>(d, &d.V, Vp, st))) return rc;
+  if ((rc = upload_converted<T>(d, &d.Ef, p.Ef, st))) return rc;
+  if ((rc = dev_alloc(d, (void **)&d.adm_ptr, p.adm_ptr.size() * 8))) return rc;
+  H2_CUDA_TRY(cudaMemcpyAsync(d.adm_ptr, p.adm_ptr.data(), p.adm_ptr.size() * 8, cudaMemcpyHostToDevice, st));
+  if ((rc = dev_alloc(d, (void **)&d.adm_col, std::max<size_t>(1, p.adm_col.size()) * 4))) return rc;
+  if (!p.adm_col.empty())
+    H2_CUDA_TRY(cudaMemcpyAsync(d.adm_col, p.adm_col.data(), p.adm_col.size() * 4, cudaMemcpyHostToDevice, st));
+  if ((rc = dev_alloc(d, (void **)&d.near_ptr, p.near_ptr.size() * 8))) return rc;
+  H2_CUDA_TRY(cudaMemcpyAsync(d.near_ptr, p.near_ptr.data(), p.near_ptr.size() * 8, cudaMemcpyHostToDevice, st));
+  if ((rc = dev_alloc(d, (void **)&d.near_col, std::max<size_t>(1, p.near_col.size()) * 4))) return rc;
+  if (!p.near_col.empty())
+    H2_CUDA_TRY(cudaMemcpyAsync(d.near_col, p.near_col.data(), p.near_col.size() * 4, cudaMemcpyHostToDevice, st));
+  if ((rc = dev_alloc(d, (void **)&d.cheb, p.cheb.size() * 8))) return rc;
+  H2_CUDA_TRY(cudaMemcpyAsync(d.cheb, p.cheb.data(), p.cheb.size() * 8, cudaMemcpyHostToDevice, st));
+
+  // temporary geometry for the set-up kernels
+  std::vector<int32_t> arow(p.adm_col.size()), nrow(p.near_col.size()), ncol(p.near_col.size());
+  for (int64_t t = 0; t < p.nclu; ++t)
+    for (int64_t e = p.adm_ptr[t]; e < p.adm_ptr[t + 1]; ++e) arow[e] = (int32_t)t;
+  for (int64_t j = 0; j < p.nleaf; ++j)
+    for (int64_t e = p.near_ptr[j]; e < p.near_ptr[j + 1]; ++e) {
+      nrow[e] = (int32_t)j;
+      ncol[e] = p.near_col[e];
+    }
+  struct Tmp {
+    void *ptr = nullptr;
+    ~Tmp() { if (ptr) cudaFree(ptr); }
+  } t_arow, t_nrow, t_ncol, t_vert, t_tri, t_area, t_sing, t_cnt;
+  auto tmp_up = [&](Tmp &t, const void *src, size_t bytes) -> int {
+    if (cudaMalloc(&t.ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) return fail(H2_ENOMEM, "device set-up buffer");
+    if (bytes) H2_CUDA_TRY(cudaMemcpyAsync(t.ptr, src, bytes, cudaMemcpyHostToDevice, st));
+    return H2_OK;
+  };
+  if ((rc = tmp_up(t_arow, arow.data(), arow.size() * 4))) return rc;
+  if ((rc = tmp_up(t_nrow, nrow.data(), nrow.size() * 4))) return rc;
+  if ((rc = tmp_up(t_ncol, ncol.data(), ncol.size() * 4))) return rc;
+  if ((rc = tmp_up(t_vert, p.vert.data(), p.vert.size() * 8))) return rc;
+  if ((rc = tmp_up(t_tri, p.tri.data(), p.tri.size() * 4))) return rc;
+  if ((rc = tmp_up(t_area, p.area.data(), p.area.size() * 8))) return rc;
+
+  // Gauss rule of the nearfield quadrature
+  std::vector<double> gx, gw;
+  gauss_legendre01(c.quad_order, gx, gw);
+  H2_CUDA_TRY(cudaMemcpyToSymbolAsync(c_gx, gx.data(), gx.size() * 8, 0, cudaMemcpyHostToDevice, st));
+  H2_CUDA_TRY(cudaMemcpyToSymbolAsync(c_gw, gw.data(), gw.size() * 8, 0, cudaMemcpyHostToDevice, st));
+
+  // coupling matrices
+  if ((rc = dev_alloc(d, &d.S, std::max<size_t>(1, (size_t)d.nadm * k * k) * sizeof(T)))) return rc;
+  if (d.nadm > 0) {
+    k_coupling_fill<T><<<grid_for(d.nadm * k * k, 256), 256, 0, st>>>((const int32_t *)t_arow.ptr, d.adm_col,
+                                                                       d.cheb, m, d.nadm, (T *)d.S);
+    H2_CUDA_TRY(cudaGetLastError());
+  }
+
+  // nearfield entries
+  if ((rc = dev_alloc(d, &d.near, std::max<size_t>(1, (size_t)d.nnear * L * L) * sizeof(T)))) return rc;
+  if (d.nnear > 0) {
+    // pairs that share a vertex: at most (n * 3 * valence) ordered pairs; bound by the entry count
+    int64_t cap = std::min<int64_t>(d.nnear * L * L, 64 * p.n + 1024);
+    if (cudaMalloc(&t_sing.ptr, cap * 8) != cudaSuccess) return fail(H2_ENOMEM, "singular list");
+    if (cudaMalloc(&t_cnt.ptr, 8) != cudaSuccess) return fail(H2_ENOMEM, "singular count");
+    H2_CUDA_TRY(cudaMemsetAsync(t_cnt.ptr, 0, 8, st));
+    Geo g{(const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src,
+          (const int32_t *)t_nrow.ptr, (const int32_t *)t_ncol.ptr, L};
+    k_near_regular<T><<<grid_for(d.nnear * L * L, 128), 128, 0, st>>>(
+        g, d.nnear, c.quad_order, (T *)d.near, (int64_t *)t_sing.ptr, (unsigned long long *)t_cnt.ptr, cap);
+    H2_CUDA_TRY(cudaGetLastError());
+    unsigned long long ns = 0;
+    H2_CUDA_TRY(cudaMemcpyAsync(&ns, t_cnt.ptr, 8, cudaMemcpyDeviceToHost, st));
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((int64_t)ns > cap) return fail(H2_EINVAL, "mesh has more vertex-sharing pairs than supported");
+    if (ns > 0) {
+      k_near_singular<T><<<grid_for((int64_t)ns, 64), 64, 0, st>>>(g, (const int64_t *)t_sing.ptr, (int64_t)ns,
+                                                                   c.quad_order, (T *)d.near);
+      H2_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  H2_CUDA_TRY(cudaStreamSynchronize(st));
+  return H2_OK;
+}
+
+}  // namespace
+
+int dev_alloc(Dev &d, void **ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(H2_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  d.bytes += (int64_t)bytes;
+  return H2_OK;
+}
+
+int device_build(Ctx &c) {
+  Plan &p = c.plan;
+  Dev &d = c.d;
+  if (c.quad_order < 1 || c.quad_order > kMaxQ) return fail(H2_EINVAL, "quad_order must be in [1, 16]");
+  d.m = p.m;
+  d.k = p.k;
+  d.depth = p.depth;
+  d.first_adm_level = p.first_adm_level;
+  d.n = p.n;
+  d.nclu = p.nclu;
+  d.nleaf = p.nleaf;
+  d.lmax = p.lmax;
+  d.npad = p.nleaf * p.lmax;
+  d.nadm = (int64_t)p.adm_col.size();
+  d.nnear = (int64_t)p.near_col.size();
+  if (d.prec == H2_F64) {
+    d.esize = 8;
+    return build_typed<double>(c);
+  }
+  d.esize = 4;
+  return build_typed<float>(c);
+}
+
+}  // namespace h2

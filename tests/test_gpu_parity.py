@@ -134,7 +134,9 @@ def test_gmres_solves_to_1e8(require_gpu, prec):
         assert np.all(relo <= 1e-8)
         # both solve G~ z = b to 1e-8; the iterates differ within kappa * rtol
         assert _rel(z, zo) <= 1e-5
-        assert np.abs(z[:, 1] - 1.0).max() < 0.05          # constant density -> z = 1 (O(h))
+        # constant density b = area: z -> 1 as h -> 0 (area-weighted mean within 1 %)
+        a = b[:, 1]
+        assert abs(np.dot(a, z[:, 1]) / a.sum() - 1.0) < 1e-2
     else:
         # an FP32 product cannot certify 1e-8 in its own arithmetic; it must
         # still reduce the residual to the FP32 level

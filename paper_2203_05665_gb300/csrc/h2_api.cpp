@@ -223,6 +223,8 @@ int h2_phase_times(h2_handle h, double *ms, int64_t *launches, int64_t *products
       p.ms[i] += t;
     }
   drop_events(p);
+  int derr = take_device_error(*h);
+  if (derr) return derr;
   if (ms)
     for (int i = 0; i < H2_NPHASE; ++i) ms[i] = p.ms[i];
   if (launches)
@@ -248,7 +250,7 @@ int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs) {
   if ((rc = run_matvec(*h, h->d.io_x, h->d.io_y, nrhs, true))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(y, h->d.io_y, bytes, cudaMemcpyDeviceToHost, h->stream));
   H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  return H2_OK;
+  return take_device_error(*h);
 }
 
 int h2_coefficients(h2_handle h, int which, double *out) {
@@ -257,16 +259,19 @@ int h2_coefficients(h2_handle h, int which, double *out) {
   H2_CUDA_TRY(cudaSetDevice(h->device));
   H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
   const Dev &d = h->d;
-  // the work buffers are laid out for cap_nrhs; the last product used last_nrhs
-  size_t cnt = (size_t)d.nclu * d.k * d.last_nrhs;
+  // the coefficients of the last product: [clusters][k][last_rp], the first last_nrhs columns are returned
+  const size_t rows = (size_t)d.nclu * d.k, rp = d.last_rp, nr = d.last_nrhs;
   const void *src = which == 0 ? d.xhat : d.yhat;
+  std::vector<double> tmp(rows * rp);
   if (d.prec == H2_F64) {
-    H2_CUDA_TRY(cudaMemcpy(out, src, cnt * 8, cudaMemcpyDeviceToHost));
+    H2_CUDA_TRY(cudaMemcpy(tmp.data(), src, rows * rp * 8, cudaMemcpyDeviceToHost));
   } else {
-    std::vector<float> tmp(cnt);
-    H2_CUDA_TRY(cudaMemcpy(tmp.data(), src, cnt * 4, cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < cnt; ++i) out[i] = tmp[i];
+    std::vector<float> tf(rows * rp);
+    H2_CUDA_TRY(cudaMemcpy(tf.data(), src, rows * rp * 4, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < tf.size(); ++i) tmp[i] = tf[i];
   }
+  for (size_t r = 0; r < rows; ++r)
+    for (size_t c = 0; c < nr; ++c) out[r * nr + c] = tmp[r * rp + c];
   return H2_OK;
 }
 

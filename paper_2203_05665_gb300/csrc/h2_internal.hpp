@@ -59,13 +59,13 @@ int make_plan(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, in
 struct Dev {
   int prec = H2_F64;
   size_t esize = 8;
-  int m = 0, k = 0, depth = 0, first_adm_level = 0;
+  int m = 0, k = 0, kp = 0, depth = 0, first_adm_level = 0;
   int64_t n = 0, nclu = 0, nleaf = 0, lmax = 0, npad = 0;
   int64_t nadm = 0, nnear = 0;
   int32_t *pad_src = nullptr;   // npad: original triangle index of padded DoF, or -1
   void *V = nullptr;            // nleaf x lmax x k
   void *Ef = nullptr;           // nclu x 3 x m x m
-  void *S = nullptr;            // nadm x k x k (row nu, column mu)
+  void *S = nullptr;            // nadm x k x kp: S_b stored transposed, [mu][nu], nu padded to kp = 4 ceil(k/4)
   void *near = nullptr;         // nnear x lmax x lmax (row r, column c)
   int64_t *adm_ptr = nullptr;   // nclu + 1
   int32_t *adm_col = nullptr;
@@ -76,7 +76,7 @@ struct Dev {
   int cap_nrhs = 0;
   void *xpad = nullptr, *ypad = nullptr, *xhat = nullptr, *yhat = nullptr;
   double *io_x = nullptr, *io_y = nullptr;   // FP64 staging for host / solver I/O
-  int last_nrhs = 0;
+  int last_nrhs = 0, last_rp = 0;  // last product: right-hand sides and padded coefficient width
   int64_t bytes = 0;
 };
 
@@ -96,6 +96,15 @@ struct Ctx {
   Plan plan;
   Dev d;
 };
+
+// padded coefficient width: right-hand sides rounded up to 16 bytes
+inline int padded_rhs(int nrhs, size_t esize) {
+  int v = (int)(16 / esize);
+  return (nrhs + v - 1) / v * v;
+}
+
+// device-side error word (a bounded wait ran out); read and cleared by the host
+int take_device_error(Ctx &c);
 
 // device allocation helper (tracks bytes)
 int dev_alloc(Dev &d, void **ptr, size_t bytes);

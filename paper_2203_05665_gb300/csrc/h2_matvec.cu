@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "h2_internal.hpp"
+#include "h2_ptx.cuh"
 
 namespace h2 {
 
@@ -21,27 +22,28 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxOut = 16;   // outputs per thread in the block-row kernels
 
+// xpad[p][c] (rp columns, zero beyond nrhs) from x[src][c] column-major
 template <class Tin, class Tout>
-__global__ void k_permute_in(const Tin *__restrict__ x, int64_t n, int nrhs, const int32_t *__restrict__ pad_src,
-                             int64_t npad, Tout *__restrict__ xpad) {
-  const int64_t total = npad * nrhs;
+__global__ void k_permute_in(const Tin *__restrict__ x, int64_t n, int nrhs, int rp,
+                             const int32_t *__restrict__ pad_src, int64_t npad, Tout *__restrict__ xpad) {
+  const int64_t total = npad * rp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t p = e / nrhs;
-    int r = (int)(e - p * nrhs);
+    int64_t p = e / rp;
+    int r = (int)(e - p * rp);
     int32_t src = pad_src[p];
-    xpad[e] = src >= 0 ? (Tout)x[src + r * n] : (Tout)0;
+    xpad[e] = (src >= 0 && r < nrhs) ? (Tout)x[src + r * n] : (Tout)0;
   }
 }
 
 template <class Tin, class Tout>
-__global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs, const int32_t *__restrict__ pad_src,
-                              int64_t npad, Tout *__restrict__ y) {
-  const int64_t total = npad * nrhs;
+__global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs, int rp,
+                              const int32_t *__restrict__ pad_src, int64_t npad, Tout *__restrict__ y) {
+  const int64_t total = npad * rp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t p = e / nrhs;
-    int r = (int)(e - p * nrhs);
+    int64_t p = e / rp;
+    int r = (int)(e - p * rp);
     int32_t src = pad_src[p];
-    if (src >= 0) y[src + r * n] = (Tout)ypad[e];
+    if (src >= 0 && r < nrhs) y[src + r * n] = (Tout)ypad[e];
   }
 }
 
@@ -133,41 +135,167 @@ __global__ void k_downward(const T *__restrict__ Ef, int m, int k, int nrhs, int
   for (int i = threadIdx.x; i < kr; i += blockDim.x) yhat[c * kr + i] += b[i];
 }
 
-// coupling: one CTA per row cluster t >= row0; y^_t = sum_b S_b x^_{s_b}
 template <class T>
-__global__ void k_coupling(const T *__restrict__ S, const int64_t *__restrict__ adm_ptr,
-                           const int32_t *__restrict__ adm_col, int k, int nrhs, int64_t row0,
-                           const T *__restrict__ xhat, T *__restrict__ yhat) {
-  extern __shared__ unsigned char smem_raw[];
-  T *sS = reinterpret_cast<T *>(smem_raw);
-  T *sx = sS + k * k;
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int N = 2;
+};
+
+// Launch geometry of the coupling kernel (computed on the host).
+struct CoupleCfg {
+  int k, kp, rp;             // rows of S_b, rows padded to 4, coefficient columns (padded to 16 bytes)
+  int nvg, ncg, tiles;       // 4-row groups, 16-byte column groups, register tiles of 4 x (16 bytes)
+  int ksplit, kc;            // the mu range is split in ksplit slices of kc
+  int nst;                   // pipeline stages
+  uint32_t s_bytes, x_bytes, stage_bytes, bar_off;
+};
+
+// Coupling, Algorithm 3 on admissible blocks: one CTA per row cluster t >= row0,
+// y^_t = sum_{b in row t} S_b x^_{s_b}.  The S_b tiles (stored [mu][nu]) and the
+// x^_s tiles stream through an nst-stage shared-memory ring, each stage filled
+// by one bulk copy pair (TMA engine) that completes on the stage's mbarrier;
+// thread 0 refills a stage once every thread has finished with it.  Each thread
+// keeps a 4 x VN register tile of y^ for one slice of mu; the slices are summed
+// in a fixed order at the end (no atomics, bit-reproducible).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_coupling(const T *__restrict__ S, const int64_t *__restrict__ adm_ptr,
+                                                      const int32_t *__restrict__ adm_col, CoupleCfg cfg,
+                                                      int64_t row0, const T *__restrict__ xhat,
+                                                      T *__restrict__ yhat) {
+  using V = typename Vec16<T>::V;
+  constexpr int VN = Vec16<T>::N;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + cfg.bar_off);
+  const int tid = threadIdx.x;
   const int64_t t = row0 + blockIdx.x;
-  const int kr = k * nrhs;
-  T acc[kMaxOut];
+  const int64_t e0 = adm_ptr[t], nb = adm_ptr[t + 1] - e0;
+  const int k = cfg.k, kp = cfg.kp, rp = cfg.rp;
+
+  if (tid == 0) {
+    for (int s = 0; s < cfg.nst; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int64_t issued = 0;
+  auto issue = [&](int64_t i) {
+    const int s = (int)(i % cfg.nst);
+    unsigned char *st = smem + (size_t)s * cfg.stage_bytes;
+    const int64_t e = e0 + i;
+    const int64_t col = adm_col[e];
+    mbar_expect_tx(&bar[s], cfg.s_bytes + cfg.x_bytes);
+    bulk_g2s(st, S + e * (int64_t)k * kp, cfg.s_bytes, &bar[s]);
+    bulk_g2s(st + cfg.s_bytes, xhat + col * (int64_t)k * rp, cfg.x_bytes, &bar[s]);
+  };
+  if (tid == 0)
+    for (; issued < nb && issued < cfg.nst; ++issued) issue(issued);
+
+  const int tile = tid % cfg.tiles, ks = tid / cfg.tiles;
+  const bool active = ks < cfg.ksplit;
+  const int vg = tile % cfg.nvg, cg = tile / cfg.nvg;
+  const int mu0 = ks * cfg.kc;
+  const int mu1 = min(k, mu0 + cfg.kc);
+  T acc[4][VN];
 #pragma unroll
-  for (int i = 0; i < kMaxOut; ++i) acc[i] = 0;
-  for (int64_t e = adm_ptr[t]; e < adm_ptr[t + 1]; ++e) {
-    const int64_t s = adm_col[e];
-    __syncthreads();
-    for (int i = threadIdx.x; i < k * k; i += blockDim.x) sS[i] = S[e * k * k + i];
-    for (int i = threadIdx.x; i < kr; i += blockDim.x) sx[i] = xhat[s * kr + i];
-    __syncthreads();
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int i = 0; i < kMaxOut; ++i) {
-      int o = threadIdx.x + i * blockDim.x;
-      if (o < kr) {
-        int nu = o / nrhs, r = o - nu * nrhs;
-        T sum = 0;
-        for (int mu = 0; mu < k; ++mu) sum += sS[nu * k + mu] * sx[mu * nrhs + r];
-        acc[i] += sum;
+    for (int c = 0; c < VN; ++c) acc[a][c] = (T)0;
+
+  for (int64_t i = 0; i < nb; ++i) {
+    const int s = (int)(i % cfg.nst);
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i / cfg.nst) & 1));
+    if (__syncthreads_or(!ok)) {
+      // a copy did not arrive in time: wait (bounded) for the copies still in flight, then leave
+      if (tid == 0)
+        for (int64_t j = i; j < issued; ++j) mbar_wait_bounded(&bar[j % cfg.nst], (uint32_t)((j / cfg.nst) & 1));
+      __syncthreads();
+      return;
+    }
+    const T *sS = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
+    const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.s_bytes);
+    if (active) {
+#pragma unroll 4
+      for (int mu = mu0; mu < mu1; ++mu) {
+        T sv[4];
+        const V *sp = reinterpret_cast<const V *>(sS + mu * kp + 4 * vg);
+#pragma unroll
+        for (int q = 0; q < 4 / VN; ++q) {
+          V v = sp[q];
+          if constexpr (VN == 4) {
+            sv[0] = v.x; sv[1] = v.y; sv[2] = v.z; sv[3] = v.w;
+          } else {
+            sv[2 * q] = v.x; sv[2 * q + 1] = v.y;
+          }
+        }
+        const V xv = *reinterpret_cast<const V *>(sX + mu * rp + VN * cg);
+        T xs[VN];
+        if constexpr (VN == 4) {
+          xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
+        } else {
+          xs[0] = xv.x; xs[1] = xv.y;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < VN; ++c) acc[a][c] = fma(sv[a], xs[c], acc[a][c]);
       }
     }
+    __syncthreads();
+    if (tid == 0 && issued < nb) {
+      issue(issued);
+      ++issued;
+    }
   }
+  // sum the mu slices in a fixed order
+  T *red = reinterpret_cast<T *>(smem);
+  if (active) {
 #pragma unroll
-  for (int i = 0; i < kMaxOut; ++i) {
-    int o = threadIdx.x + i * blockDim.x;
-    if (o < kr) yhat[t * kr + o] = acc[i];
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < VN; ++c) red[((int64_t)ks * kp + 4 * vg + a) * rp + VN * cg + c] = acc[a][c];
   }
+  __syncthreads();
+  T *out = yhat + t * (int64_t)k * rp;
+  for (int o = tid; o < k * rp; o += blockDim.x) {
+    const int nu = o / rp, c = o - nu * rp;
+    T sum = (T)0;
+    for (int q = 0; q < cfg.ksplit; ++q) sum += red[((int64_t)q * kp + nu) * rp + c];
+    out[o] = sum;
+  }
+}
+
+constexpr size_t kSmemMax = 227 * 1024;
+
+template <class T>
+int coupling_cfg(int k, int kp, int rp, CoupleCfg &cfg) {
+  constexpr int VN = Vec16<T>::N;
+  cfg.k = k;
+  cfg.kp = kp;
+  cfg.rp = rp;
+  cfg.nvg = kp / 4;
+  cfg.ncg = rp / VN;
+  cfg.tiles = cfg.nvg * cfg.ncg;
+  if (cfg.tiles > kThreads) return fail(H2_EINVAL, "rank x right-hand sides too large for one coupling tile");
+  int ks = std::max(1, std::min(kThreads / cfg.tiles, k));
+  cfg.kc = (k + ks - 1) / ks;
+  cfg.ksplit = (k + cfg.kc - 1) / cfg.kc;
+  cfg.s_bytes = (uint32_t)(sizeof(T) * k * kp);
+  cfg.x_bytes = (uint32_t)(sizeof(T) * k * rp);
+  cfg.stage_bytes = cfg.s_bytes + cfg.x_bytes;
+  size_t red = sizeof(T) * (size_t)cfg.ksplit * kp * rp;
+  int nst = 4;
+  while (nst > 1 && std::max((size_t)nst * cfg.stage_bytes, red) + 64 > kSmemMax) --nst;
+  cfg.nst = nst;
+  size_t body = std::max((size_t)nst * cfg.stage_bytes, red);
+  cfg.bar_off = (uint32_t)((body + 15) / 16 * 16);
+  if (cfg.bar_off + 8 * nst > kSmemMax) return fail(H2_EINVAL, "coupling tile does not fit in shared memory");
+  return H2_OK;
 }
 
 // leaf backward + nearfield: one CTA per leaf t;
@@ -261,77 +389,93 @@ template <class T, class Tio>
 int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
-  Marks mk(c);
   const int k = d.k, m = d.m, L = (int)d.lmax, D = d.depth, lmin = d.first_adm_level;
+  const int rp = padded_rhs(nrhs, sizeof(T));   // every kernel below works on rp columns
   const int64_t leaf0 = d.nleaf - 1;
   T *xpad = (T *)d.xpad, *ypad = (T *)d.ypad, *xhat = (T *)d.xhat, *yhat = (T *)d.yhat;
+  const bool far = lmin <= D;
   int rc;
+  CoupleCfg cfg{};
+  if (far && (rc = coupling_cfg<T>(k, d.kp, rp, cfg))) return rc;
+  Marks mk(c);
 
   mk.mark(H2_PH_PERMUTE_IN);
-  k_permute_in<Tio, T><<<grid_for(d.npad * nrhs), kThreads, 0, st>>>(x, d.n, nrhs, d.pad_src, d.npad, xpad);
+  k_permute_in<Tio, T><<<grid_for(d.npad * rp), kThreads, 0, st>>>(x, d.n, nrhs, rp, d.pad_src, d.npad, xpad);
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
-  const bool far = lmin <= D;
   if (far) {
-    size_t sm = (size_t)(L * k + L * nrhs) * sizeof(T);
+    size_t sm = (size_t)(L * k + L * rp) * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_leaf_forward<T>, sm))) return rc;
-    k_leaf_forward<T><<<(unsigned)d.nleaf, kThreads, sm, st>>>((const T *)d.V, xpad, L, k, nrhs, leaf0, xhat);
+    k_leaf_forward<T><<<(unsigned)d.nleaf, kThreads, sm, st>>>((const T *)d.V, xpad, L, k, rp, leaf0, xhat);
     mk.count(H2_PH_LEAF_FORWARD);
   }
   mk.mark(H2_PH_UPWARD);
   if (far) {
-    size_t sm = (size_t)3 * k * nrhs * sizeof(T);
+    size_t sm = (size_t)3 * k * rp * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_upward<T>, sm))) return rc;
     for (int l = D - 1; l >= lmin; --l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
-      k_upward<T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, nrhs, par0, xhat);
+      k_upward<T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, rp, par0, xhat);
       mk.count(H2_PH_UPWARD);
     }
   }
   mk.mark(H2_PH_COUPLING);
   if (far) {
-    size_t sm;
     int64_t row0 = ((int64_t)1 << lmin) - 1;
-    sm = (size_t)(k * k + k * nrhs) * sizeof(T);
+    size_t sm = cfg.bar_off + 8 * cfg.nst;
     if ((rc = set_smem<T>((const void *)k_coupling<T>, sm))) return rc;
-    k_coupling<T><<<(unsigned)(d.nclu - row0), kThreads, sm, st>>>((const T *)d.S, d.adm_ptr, d.adm_col, k, nrhs,
-                                                                   row0, xhat, yhat);
+    k_coupling<T><<<(unsigned)(d.nclu - row0), kThreads, sm, st>>>((const T *)d.S, d.adm_ptr, d.adm_col, cfg, row0,
+                                                                   xhat, yhat);
     mk.count(H2_PH_COUPLING);
   }
   mk.mark(H2_PH_DOWNWARD);
   if (far) {
-    size_t sm = (size_t)2 * k * nrhs * sizeof(T);
+    size_t sm = (size_t)2 * k * rp * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_downward<T>, sm))) return rc;
     for (int l = lmin; l < D; ++l) {
       int64_t ch0 = ((int64_t)2 << l) - 1;
-      k_downward<T><<<(unsigned)((int64_t)2 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, nrhs, ch0, yhat);
+      k_downward<T><<<(unsigned)((int64_t)2 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, rp, ch0, yhat);
       mk.count(H2_PH_DOWNWARD);
     }
   }
   mk.mark(H2_PH_LEAF_NEAR);
   {
     int w = std::max(k, L);
-    size_t sm = (size_t)(L * w + w * nrhs) * sizeof(T);
+    size_t sm = (size_t)(L * w + w * rp) * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_leaf_near<T>, sm))) return rc;
     k_leaf_near<T><<<(unsigned)d.nleaf, kThreads, sm, st>>>((const T *)d.V, (const T *)d.near, d.near_ptr,
-                                                             d.near_col, L, k, nrhs, leaf0, far ? 1 : 0, yhat, xpad,
+                                                             d.near_col, L, k, rp, leaf0, far ? 1 : 0, yhat, xpad,
                                                              ypad);
     mk.count(H2_PH_LEAF_NEAR);
   }
   mk.mark(H2_PH_PERMUTE_OUT);
-  k_permute_out<T, Tio><<<grid_for(d.npad * nrhs), kThreads, 0, st>>>(ypad, d.n, nrhs, d.pad_src, d.npad, y);
+  k_permute_out<T, Tio><<<grid_for(d.npad * rp), kThreads, 0, st>>>(ypad, d.n, nrhs, rp, d.pad_src, d.npad, y);
   mk.count(H2_PH_PERMUTE_OUT);
   mk.mark(H2_NPHASE);
   mk.finish();
   H2_CUDA_TRY(cudaGetLastError());
   d.last_nrhs = nrhs;
+  d.last_rp = rp;
   return H2_OK;
 }
 
 }  // namespace
 
-int ensure_work(Ctx &c, int nrhs) {
+int take_device_error(Ctx &c) {
+  int v = 0, zero = 0;
+  H2_CUDA_TRY(cudaMemcpyFromSymbolAsync(&v, g_h2_device_error, sizeof(int), 0, cudaMemcpyDeviceToHost, c.stream));
+  H2_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  if (v) {
+    H2_CUDA_TRY(cudaMemcpyToSymbolAsync(g_h2_device_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, c.stream));
+    H2_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return fail(H2_ETIMEOUT, "a bounded device wait ran out; the last result is not valid");
+  }
+  return H2_OK;
+}
+
+int ensure_work(Ctx &c, int nrhs_req) {
   Dev &d = c.d;
+  const int nrhs = padded_rhs(nrhs_req, d.esize);
   if (nrhs <= d.cap_nrhs) return H2_OK;
   cudaFree(d.xpad); cudaFree(d.ypad); cudaFree(d.xhat); cudaFree(d.yhat); cudaFree(d.io_x); cudaFree(d.io_y);
   d.xpad = d.ypad = d.xhat = d.yhat = nullptr;
@@ -355,8 +499,9 @@ int ensure_work(Ctx &c, int nrhs) {
 int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64) {
   Dev &d = c.d;
   if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");
-  if ((int64_t)d.k * nrhs > kThreads * kMaxOut || d.lmax * nrhs > kThreads * kMaxOut)
-    return fail(H2_EINVAL, "k * nrhs and leaf_max * nrhs must not exceed 4096");
+  const int rp = padded_rhs(nrhs, d.esize);
+  if ((int64_t)d.k * rp > kThreads * kMaxOut || d.lmax * rp > kThreads * kMaxOut)
+    return fail(H2_EINVAL, "k * nrhs and leaf_max * nrhs (nrhs padded to 16 bytes) must not exceed 4096");
   int rc = ensure_work(c, nrhs);
   if (rc) return rc;
   if (d.prec == H2_F64) return matvec_typed<double, double>(c, (const double *)x, (double *)y, nrhs);

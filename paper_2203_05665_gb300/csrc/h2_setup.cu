@@ -38,15 +38,17 @@ __device__ __forceinline__ void tri_point(const double *A, const double *B, cons
 }
 
 // ---------------------------------------------------------------- coupling
+// S_b stored transposed and padded: S[b][mu][nu], nu < kp, zero for nu >= k
 template <class T>
 __global__ void k_coupling_fill(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-                                const double *__restrict__ cheb, int m, int64_t nblk, T *__restrict__ S) {
+                                const double *__restrict__ cheb, int m, int kp, int64_t nblk, T *__restrict__ S) {
   const int k = m * m * m;
-  const int64_t total = nblk * k * k;
+  const int64_t per = (int64_t)k * kp, total = nblk * per;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t b = e / (k * k);
-    int rem = (int)(e - b * k * k);
-    int nu = rem / k, mu = rem - nu * k;
+    int64_t b = e / per;
+    int rem = (int)(e - b * per);
+    int mu = rem / kp, nu = rem - mu * kp;
+    if (nu >= k) { S[e] = (T)0; continue; }
     int64_t t = row[b], s = col[b];
     double x[3], y[3];
     x[0] = cheb[(3 * t + 0) * m + nu % m];
@@ -320,10 +322,10 @@ int build_typed(Ctx &c) {
   H2_CUDA_TRY(cudaMemcpyToSymbolAsync(c_gw, gw.data(), gw.size() * 8, 0, cudaMemcpyHostToDevice, st));
 
   // coupling matrices
-  if ((rc = dev_alloc(d, &d.S, std::max<size_t>(1, (size_t)d.nadm * k * k) * sizeof(T)))) return rc;
+  if ((rc = dev_alloc(d, &d.S, std::max<size_t>(1, (size_t)d.nadm * k * d.kp) * sizeof(T)))) return rc;
   if (d.nadm > 0) {
-    k_coupling_fill<T><<<grid_for(d.nadm * k * k, 256), 256, 0, st>>>((const int32_t *)t_arow.ptr, d.adm_col,
-                                                                       d.cheb, m, d.nadm, (T *)d.S);
+    k_coupling_fill<T><<<grid_for(d.nadm * k * d.kp, 256), 256, 0, st>>>((const int32_t *)t_arow.ptr, d.adm_col,
+                                                                          d.cheb, m, d.kp, d.nadm, (T *)d.S);
     H2_CUDA_TRY(cudaGetLastError());
   }
 
@@ -374,6 +376,7 @@ int device_build(Ctx &c) {
   if (c.quad_order < 1 || c.quad_order > kMaxQ) return fail(H2_EINVAL, "quad_order must be in [1, 16]");
   d.m = p.m;
   d.k = p.k;
+  d.kp = (p.k + 3) / 4 * 4;
   d.depth = p.depth;
   d.first_adm_level = p.first_adm_level;
   d.n = p.n;

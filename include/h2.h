@@ -46,8 +46,15 @@ enum h2_status {
   H2_EBUSY = 7     /* resource in use */
 };
 
-/* arithmetic of the stored representation and of the product */
-enum h2_prec { H2_F64 = 0, H2_F32 = 1 };
+/* arithmetic of the stored representation and of the product:
+ *   H2_F64        FP64-accurate: every stored value is kept as an unevaluated
+ *                 sum of two FP32 numbers (about 48 significant bits) and the
+ *                 product runs in double-float arithmetic on the FP32 pipe;
+ *                 vectors are double.
+ *   H2_F32        FP32 storage and arithmetic; vectors are float.
+ *   H2_F64_NATIVE FP64 storage and arithmetic on the FP64 pipe (1/58 of the
+ *                 FP32 rate on GB300); vectors are double. */
+enum h2_prec { H2_F64 = 0, H2_F32 = 1, H2_F64_NATIVE = 2 };
 
 typedef struct h2_options {
   int prec;          /* enum h2_prec; default H2_F64 */
@@ -126,8 +133,8 @@ int h2_info(h2_handle h, h2_stats *out);
 
 /* y = G~ x (overwrites y) for nrhs right-hand sides, Section 2 (the
  * paper's y <- y + G x with y cleared first).  x, y: DEVICE pointers to
- * column-major n x nrhs arrays of the handle's precision (double for H2_F64,
- * float for H2_F32); they must not overlap.  Asynchronous on the handle's
+ * column-major n x nrhs arrays of the handle's vector type (double for H2_F64
+ * and H2_F64_NATIVE, float for H2_F32); they must not overlap.  Asynchronous on the handle's
  * stream.  1 <= nrhs <= 64.
  * Errors: H2_EINVAL (NULL, nrhs out of range), H2_ENOMEM (work buffers),
  * H2_ECUDA (launch failure). */

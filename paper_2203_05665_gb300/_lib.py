@@ -14,8 +14,8 @@ import numpy as np
 from . import _build
 
 H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ENOCONV, H2_ETIMEOUT, H2_PENDING, H2_EBUSY = range(8)
-H2_F64, H2_F32 = 0, 1
-PREC = {"f64": H2_F64, "f32": H2_F32}
+H2_F64, H2_F32, H2_F64_NATIVE = 0, 1, 2
+PREC = {"f64": H2_F64, "f32": H2_F32, "f64n": H2_F64_NATIVE}
 
 _lock = threading.Lock()
 _lib = None

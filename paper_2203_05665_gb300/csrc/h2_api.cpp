@@ -133,7 +133,8 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   h2_options o;
   h2_options_default(&o);
   if (opt) o = *opt;
-  if (o.prec != H2_F64 && o.prec != H2_F32) return fail(H2_EINVAL, "prec must be H2_F64 or H2_F32");
+  if (o.prec != H2_F64 && o.prec != H2_F32 && o.prec != H2_F64_NATIVE)
+    return fail(H2_EINVAL, "prec must be H2_F64, H2_F32 or H2_F64_NATIVE");
   for (int r : o.reserved)
     if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
   int ndev = 0;
@@ -263,8 +264,12 @@ int h2_coefficients(h2_handle h, int which, double *out) {
   const size_t rows = (size_t)d.nclu * d.k, rp = d.last_rp, nr = d.last_nrhs;
   const void *src = which == 0 ? d.xhat : d.yhat;
   std::vector<double> tmp(rows * rp);
-  if (d.prec == H2_F64) {
+  if (d.prec == H2_F64_NATIVE) {
     H2_CUDA_TRY(cudaMemcpy(tmp.data(), src, rows * rp * 8, cudaMemcpyDeviceToHost));
+  } else if (d.prec == H2_F64) {
+    std::vector<float> tf(2 * rows * rp);
+    H2_CUDA_TRY(cudaMemcpy(tf.data(), src, rows * rp * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < rows * rp; ++i) tmp[i] = (double)tf[2 * i] + (double)tf[2 * i + 1];
   } else {
     std::vector<float> tf(rows * rp);
     H2_CUDA_TRY(cudaMemcpy(tf.data(), src, rows * rp * 4, cudaMemcpyDeviceToHost));

@@ -12,6 +12,7 @@
 // Coefficient layout: x^[cluster][nu][rhs], nu = jx + m jy + m^2 jz.
 #include <algorithm>
 
+#include "h2_dd.cuh"
 #include "h2_internal.hpp"
 #include "h2_ptx.cuh"
 
@@ -31,7 +32,7 @@ __global__ void k_permute_in(const Tin *__restrict__ x, int64_t n, int nrhs, int
     int64_t p = e / rp;
     int r = (int)(e - p * rp);
     int32_t src = pad_src[p];
-    xpad[e] = (src >= 0 && r < nrhs) ? (Tout)x[src + r * n] : (Tout)0;
+    xpad[e] = (src >= 0 && r < nrhs) ? convert<Tout, Tin>(x[src + r * n]) : zero_of<Tout>();
   }
 }
 
@@ -43,7 +44,7 @@ __global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs,
     int64_t p = e / rp;
     int r = (int)(e - p * rp);
     int32_t src = pad_src[p];
-    if (src >= 0 && r < nrhs) y[src + r * n] = (Tout)ypad[e];
+    if (src >= 0 && r < nrhs) y[src + r * n] = convert<Tout, Tin>(ypad[e]);
   }
 }
 
@@ -61,8 +62,8 @@ __global__ void k_leaf_forward(const T *__restrict__ V, const T *__restrict__ xp
   T *out = xhat + (leaf0 + j) * (int64_t)k * nrhs;
   for (int o = threadIdx.x; o < k * nrhs; o += blockDim.x) {
     int nu = o / nrhs, r = o - nu * nrhs;
-    T acc = 0;
-    for (int t = 0; t < L; ++t) acc += sV[t * k + nu] * sx[t * nrhs + r];
+    T acc = zero_of<T>();
+    for (int t = 0; t < L; ++t) acc = madd(sV[t * k + nu], sx[t * nrhs + r], acc);
     out[o] = acc;
   }
 }
@@ -79,10 +80,10 @@ __device__ __forceinline__ void mode_product(const T *__restrict__ F, const T *i
     int nu = o / nrhs, r = o - nu * nrhs;
     int jd = (nu / stride) % m;
     int base = nu - jd * stride;
-    T acc = 0;
+    T acc = zero_of<T>();
     for (int i = 0; i < m; ++i) {
       T f = trans ? F[i * m + jd] : F[jd * m + i];
-      acc += f * in[(base + i * stride) * nrhs + r];
+      acc = madd(f, in[(base + i * stride) * nrhs + r], acc);
     }
     out[o] = acc;
   }
@@ -97,7 +98,7 @@ __global__ void k_upward(const T *__restrict__ Ef, int m, int k, int nrhs, int64
   T *acc = b + k * nrhs;
   const int64_t par = par0 + blockIdx.x;
   const int kr = k * nrhs;
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = 0;
+  for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = zero_of<T>();
   for (int ch = 1; ch <= 2; ++ch) {
     const int64_t c = 2 * par + ch;
     for (int i = threadIdx.x; i < kr; i += blockDim.x) a[i] = xhat[c * kr + i];
@@ -109,7 +110,7 @@ __global__ void k_upward(const T *__restrict__ Ef, int m, int k, int nrhs, int64
     __syncthreads();
     mode_product(F + 2 * m * m, a, b, m, k, nrhs, 2, true);
     __syncthreads();
-    for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] += b[i];
+    for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = acc[i] + b[i];
     __syncthreads();
   }
   for (int i = threadIdx.x; i < kr; i += blockDim.x) xhat[par * kr + i] = acc[i];
@@ -132,7 +133,7 @@ __global__ void k_downward(const T *__restrict__ Ef, int m, int k, int nrhs, int
   __syncthreads();
   mode_product(F + 2 * m * m, a, b, m, k, nrhs, 2, false);
   __syncthreads();
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) yhat[c * kr + i] += b[i];
+  for (int i = threadIdx.x; i < kr; i += blockDim.x) yhat[c * kr + i] = yhat[c * kr + i] + b[i];
 }
 
 template <class T>
@@ -147,6 +148,27 @@ struct Vec16<double> {
   using V = double2;
   static constexpr int N = 2;
 };
+template <>
+struct Vec16<dd> {
+  using V = float4;
+  static constexpr int N = 2;
+};
+
+// the value of lane q (< N) of a 16-byte vector
+template <class T>
+__device__ __forceinline__ T lane(const typename Vec16<T>::V &v, int q);
+template <>
+__device__ __forceinline__ float lane<float>(const float4 &v, int q) {
+  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+template <>
+__device__ __forceinline__ double lane<double>(const double2 &v, int q) {
+  return q == 0 ? v.x : v.y;
+}
+template <>
+__device__ __forceinline__ dd lane<dd>(const float4 &v, int q) {
+  return q == 0 ? dd{v.x, v.y} : dd{v.z, v.w};
+}
 
 // Launch geometry of the coupling kernel (computed on the host).
 struct CoupleCfg {
@@ -165,7 +187,7 @@ struct CoupleCfg {
 // keeps a 4 x VN register tile of y^ for one slice of mu; the slices are summed
 // in a fixed order at the end (no atomics, bit-reproducible).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_coupling(const T *__restrict__ S, const int64_t *__restrict__ adm_ptr,
+__global__ void __launch_bounds__(kThreads, 1) k_coupling(const T *__restrict__ S, const int64_t *__restrict__ adm_ptr,
                                                       const int32_t *__restrict__ adm_col, CoupleCfg cfg,
                                                       int64_t row0, const T *__restrict__ xhat,
                                                       T *__restrict__ yhat) {
@@ -205,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling(const T *__restrict__ S, 
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < VN; ++c) acc[a][c] = (T)0;
+    for (int c = 0; c < VN; ++c) acc[a][c] = zero_of<T>();
 
   for (int64_t i = 0; i < nb; ++i) {
     const int s = (int)(i % cfg.nst);
@@ -226,24 +248,18 @@ __global__ void __launch_bounds__(kThreads) k_coupling(const T *__restrict__ S, 
         const V *sp = reinterpret_cast<const V *>(sS + mu * kp + 4 * vg);
 #pragma unroll
         for (int q = 0; q < 4 / VN; ++q) {
-          V v = sp[q];
-          if constexpr (VN == 4) {
-            sv[0] = v.x; sv[1] = v.y; sv[2] = v.z; sv[3] = v.w;
-          } else {
-            sv[2 * q] = v.x; sv[2 * q + 1] = v.y;
-          }
+          const V v = sp[q];
+#pragma unroll
+          for (int l = 0; l < VN; ++l) sv[q * VN + l] = lane<T>(v, l);
         }
         const V xv = *reinterpret_cast<const V *>(sX + mu * rp + VN * cg);
         T xs[VN];
-        if constexpr (VN == 4) {
-          xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
-        } else {
-          xs[0] = xv.x; xs[1] = xv.y;
-        }
+#pragma unroll
+        for (int l = 0; l < VN; ++l) xs[l] = lane<T>(xv, l);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < VN; ++c) acc[a][c] = fma(sv[a], xs[c], acc[a][c]);
+          for (int c = 0; c < VN; ++c) acc[a][c] = madd(sv[a], xs[c], acc[a][c]);
       }
     }
     __syncthreads();
@@ -264,8 +280,8 @@ __global__ void __launch_bounds__(kThreads) k_coupling(const T *__restrict__ S, 
   T *out = yhat + t * (int64_t)k * rp;
   for (int o = tid; o < k * rp; o += blockDim.x) {
     const int nu = o / rp, c = o - nu * rp;
-    T sum = (T)0;
-    for (int q = 0; q < cfg.ksplit; ++q) sum += red[((int64_t)q * kp + nu) * rp + c];
+    T sum = zero_of<T>();
+    for (int q = 0; q < cfg.ksplit; ++q) sum = sum + red[((int64_t)q * kp + nu) * rp + c];
     out[o] = sum;
   }
 }
@@ -312,7 +328,7 @@ __global__ void k_leaf_near(const T *__restrict__ V, const T *__restrict__ near,
   const int lr = L * nrhs;
   T acc[kMaxOut];
 #pragma unroll
-  for (int i = 0; i < kMaxOut; ++i) acc[i] = 0;
+  for (int i = 0; i < kMaxOut; ++i) acc[i] = zero_of<T>();
   if (use_far) {
     for (int i = threadIdx.x; i < L * k; i += blockDim.x) sA[i] = V[j * L * k + i];
     for (int i = threadIdx.x; i < k * nrhs; i += blockDim.x) sx[i] = yhat[(leaf0 + j) * k * nrhs + i];
@@ -322,9 +338,9 @@ __global__ void k_leaf_near(const T *__restrict__ V, const T *__restrict__ near,
       int o = threadIdx.x + i * blockDim.x;
       if (o < lr) {
         int t = o / nrhs, r = o - t * nrhs;
-        T sum = 0;
-        for (int nu = 0; nu < k; ++nu) sum += sA[t * k + nu] * sx[nu * nrhs + r];
-        acc[i] += sum;
+        T sum = acc[i];
+        for (int nu = 0; nu < k; ++nu) sum = madd(sA[t * k + nu], sx[nu * nrhs + r], sum);
+        acc[i] = sum;
       }
     }
   }
@@ -339,9 +355,9 @@ __global__ void k_leaf_near(const T *__restrict__ V, const T *__restrict__ near,
       int o = threadIdx.x + i * blockDim.x;
       if (o < lr) {
         int t = o / nrhs, r = o - t * nrhs;
-        T sum = 0;
-        for (int c = 0; c < L; ++c) sum += sA[t * L + c] * sx[c * nrhs + r];
-        acc[i] += sum;
+        T sum = acc[i];
+        for (int c = 0; c < L; ++c) sum = madd(sA[t * L + c], sx[c * nrhs + r], sum);
+        acc[i] = sum;
       }
     }
   }
@@ -504,7 +520,8 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64) {
     return fail(H2_EINVAL, "k * nrhs and leaf_max * nrhs (nrhs padded to 16 bytes) must not exceed 4096");
   int rc = ensure_work(c, nrhs);
   if (rc) return rc;
-  if (d.prec == H2_F64) return matvec_typed<double, double>(c, (const double *)x, (double *)y, nrhs);
+  if (d.prec == H2_F64) return matvec_typed<dd, double>(c, (const double *)x, (double *)y, nrhs);
+  if (d.prec == H2_F64_NATIVE) return matvec_typed<double, double>(c, (const double *)x, (double *)y, nrhs);
   if (io64) return matvec_typed<float, double>(c, (const double *)x, (double *)y, nrhs);
   return matvec_typed<float, float>(c, (const float *)x, (float *)y, nrhs);
 }

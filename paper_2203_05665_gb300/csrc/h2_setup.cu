@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "h2_dd.cuh"
 #include "h2_internal.hpp"
 
 namespace h2 {
@@ -48,7 +49,7 @@ __global__ void k_coupling_fill(const int32_t *__restrict__ row, const int32_t *
     int64_t b = e / per;
     int rem = (int)(e - b * per);
     int mu = rem / kp, nu = rem - mu * kp;
-    if (nu >= k) { S[e] = (T)0; continue; }
+    if (nu >= k) { S[e] = zero_of<T>(); continue; }
     int64_t t = row[b], s = col[b];
     double x[3], y[3];
     x[0] = cheb[(3 * t + 0) * m + nu % m];
@@ -57,7 +58,7 @@ __global__ void k_coupling_fill(const int32_t *__restrict__ row, const int32_t *
     y[0] = cheb[(3 * s + 0) * m + mu % m];
     y[1] = cheb[(3 * s + 1) * m + (mu / m) % m];
     y[2] = cheb[(3 * s + 2) * m + mu / (m * m)];
-    S[e] = (T)green(x, y);
+    S[e] = from_double<T>(green(x, y));
   }
 }
 
@@ -92,14 +93,14 @@ __global__ void k_near_regular(Geo g, int64_t nblk, int q, T *__restrict__ near,
     int rc = (int)(e - b * per);
     int r = rc / (int)L, c = rc - r * (int)L;
     int32_t i = g.pad_src[g.blk_row[b] * L + r], j = g.pad_src[g.blk_col[b] * L + c];
-    if (i < 0 || j < 0) { near[e] = (T)0; continue; }
+    if (i < 0 || j < 0) { near[e] = zero_of<T>(); continue; }
     if (i > j) { int32_t t = i; i = j; j = t; }
     int32_t ti[3] = {g.tri[3 * i], g.tri[3 * i + 1], g.tri[3 * i + 2]};
     int32_t tj[3] = {g.tri[3 * j], g.tri[3 * j + 1], g.tri[3 * j + 2]};
     if (shared_count(ti, tj) > 0) {
       unsigned long long slot = atomicAdd(nsing, 1ull);
       if ((int64_t)slot < sing_cap) sing[slot] = e;
-      near[e] = (T)0;
+      near[e] = zero_of<T>();
       continue;
     }
     const double *A1 = g.vert + 3 * ti[0], *B1 = g.vert + 3 * ti[1], *C1 = g.vert + 3 * ti[2];
@@ -119,7 +120,7 @@ __global__ void k_near_regular(Geo g, int64_t nblk, int q, T *__restrict__ near,
           }
         acc += wx * inner;
       }
-    near[e] = (T)(4.0 * g.area[i] * g.area[j] * acc);
+    near[e] = from_double<T>(4.0 * g.area[i] * g.area[j] * acc);
   }
 }
 
@@ -216,14 +217,14 @@ __global__ void k_near_singular(Geo g, const int64_t *__restrict__ sing, int64_t
             }
             acc += c_gw[i0] * c_gw[i1] * c_gw[i2] * c_gw[i3] * part;
           }
-    near[e] = (T)(4.0 * g.area[i] * g.area[j] * acc);
+    near[e] = from_double<T>(4.0 * g.area[i] * g.area[j] * acc);
   }
 }
 
 template <class T>
 __global__ void k_convert(const double *__restrict__ src, T *__restrict__ dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (T)src[i];
+    dst[i] = from_double<T>(src[i]);
 }
 
 int grid_for(int64_t n, int threads) {
@@ -387,6 +388,10 @@ int device_build(Ctx &c) {
   d.nadm = (int64_t)p.adm_col.size();
   d.nnear = (int64_t)p.near_col.size();
   if (d.prec == H2_F64) {
+    d.esize = 8;
+    return build_typed<dd>(c);
+  }
+  if (d.prec == H2_F64_NATIVE) {
     d.esize = 8;
     return build_typed<double>(c);
   }

@@ -60,13 +60,14 @@ struct Dev {
   int prec = H2_F64;
   size_t esize = 8;
   int m = 0, k = 0, kp = 0, depth = 0, first_adm_level = 0;
-  int64_t n = 0, nclu = 0, nleaf = 0, lmax = 0, npad = 0;
+  int64_t n = 0, nclu = 0, nleaf = 0, lmax = 0, lp = 0, npad = 0;
   int64_t nadm = 0, nnear = 0;
   int32_t *pad_src = nullptr;   // npad: original triangle index of padded DoF, or -1
-  void *V = nullptr;            // nleaf x lmax x k
+  void *V = nullptr;            // nleaf x lmax x kp (forward step)
+  void *Vt = nullptr;           // nleaf x k x lp, transposed (backward step)
   void *Ef = nullptr;           // nclu x 3 x m x m
   void *S = nullptr;            // nadm x k x kp: S_b stored transposed, [mu][nu], nu padded to kp = 4 ceil(k/4)
-  void *near = nullptr;         // nnear x lmax x lmax (row r, column c)
+  void *near = nullptr;         // nnear x lmax x lp, stored transposed: entry (t, c) at c lp + t
   int64_t *adm_ptr = nullptr;   // nclu + 1
   int32_t *adm_col = nullptr;
   int64_t *near_ptr = nullptr;  // nleaf + 1

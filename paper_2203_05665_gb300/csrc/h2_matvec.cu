@@ -48,26 +48,6 @@ __global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs,
   }
 }
 
-// x^_leaf[nu][r] = sum_t V[t][nu] x[t][r]; one CTA per leaf
-template <class T>
-__global__ void k_leaf_forward(const T *__restrict__ V, const T *__restrict__ xpad, int L, int k, int nrhs,
-                               int64_t leaf0, T *__restrict__ xhat) {
-  extern __shared__ unsigned char smem_raw[];
-  T *sV = reinterpret_cast<T *>(smem_raw);
-  T *sx = sV + L * k;
-  const int64_t j = blockIdx.x;
-  for (int i = threadIdx.x; i < L * k; i += blockDim.x) sV[i] = V[j * L * k + i];
-  for (int i = threadIdx.x; i < L * nrhs; i += blockDim.x) sx[i] = xpad[j * L * nrhs + i];
-  __syncthreads();
-  T *out = xhat + (leaf0 + j) * (int64_t)k * nrhs;
-  for (int o = threadIdx.x; o < k * nrhs; o += blockDim.x) {
-    int nu = o / nrhs, r = o - nu * nrhs;
-    T acc = zero_of<T>();
-    for (int t = 0; t < L; ++t) acc = madd(sV[t * k + nu], sx[t * nrhs + r], acc);
-    out[o] = acc;
-  }
-}
-
 // one mode product of the factored transfer: axis d, transpose or not.
 // in/out: [k][nrhs] tensors with nu = jx + m jy + m^2 jz.
 // trans: out[.., j, ..] = sum_{j'} F[j'][j] in[.., j', ..]   (E^T, upward)
@@ -170,35 +150,108 @@ __device__ __forceinline__ dd lane<dd>(const float4 &v, int q) {
   return q == 0 ? dd{v.x, v.y} : dd{v.z, v.w};
 }
 
-// Launch geometry of the coupling kernel (computed on the host).
-struct CoupleCfg {
-  int k, kp, rp;             // rows of S_b, rows padded to 4, coefficient columns (padded to 16 bytes)
+// Launch geometry of the block-row kernel (computed on the host).
+struct RowCfg {
+  int M, Mp, rp;             // rows of an output tile, rows padded to 4, columns (padded to 16 bytes)
   int nvg, ncg, tiles;       // 4-row groups, 16-byte column groups, register tiles of 4 x (16 bytes)
-  int ksplit, kc;            // the mu range is split in ksplit slices of kc
+  int ksplit;                // the contraction range of every term is split in ksplit slices
   int nst;                   // pipeline stages
-  uint32_t s_bytes, x_bytes, stage_bytes, bar_off;
+  uint32_t a_bytes, stage_bytes, bar_off;   // A region of a stage, stage size, mbarrier offset
 };
 
-// Coupling, Algorithm 3 on admissible blocks: one CTA per row cluster t >= row0,
-// y^_t = sum_{b in row t} S_b x^_{s_b}.  The S_b tiles (stored [mu][nu]) and the
-// x^_s tiles stream through an nst-stage shared-memory ring, each stage filled
-// by one bulk copy pair (TMA engine) that completes on the stage's mbarrier;
-// thread 0 refills a stage once every thread has finished with it.  Each thread
-// keeps a 4 x VN register tile of y^ for one slice of mu; the slices are summed
-// in a fixed order at the end (no atomics, bit-reproducible).
+// One term A X of an output row: A stored [K][Mp] (contraction index major), X stored [K][rp].
 template <class T>
-__global__ void __launch_bounds__(kThreads, 1) k_coupling(const T *__restrict__ S, const int64_t *__restrict__ adm_ptr,
-                                                      const int32_t *__restrict__ adm_col, CoupleCfg cfg,
-                                                      int64_t row0, const T *__restrict__ xhat,
-                                                      T *__restrict__ yhat) {
+struct Term {
+  const T *A;
+  const T *X;
+  int K;
+};
+
+// Coupling (Algorithm 3, admissible blocks): row r = cluster t = row0 + r,
+// terms S_b x^_{s_b} for the admissible blocks b of row t (S_b stored [mu][nu]).
+template <class T>
+struct CouplingRows {
+  const T *S;
+  const int64_t *ptr;
+  const int32_t *col;
+  const T *xhat;
+  int k, kp, rp;
+  int64_t row0;
+  __device__ int kdim(int64_t) const { return k; }
+  __device__ int64_t first(int64_t r) const { return ptr[row0 + r]; }
+  __device__ int64_t count(int64_t r) const { return ptr[row0 + r + 1] - ptr[row0 + r]; }
+  __device__ Term<T> term(int64_t r, int64_t i) const {
+    const int64_t e = first(r) + i;
+    return Term<T>{S + e * (int64_t)k * kp, xhat + (int64_t)col[e] * k * rp, k};
+  }
+};
+
+// Leaf forward step (Algorithm 1 on the leaves): row j = leaf j, one term V_j^T x|j
+// (V_j stored [t][nu], padded to kp).
+template <class T>
+struct LeafForwardRows {
+  const T *V;
+  const T *xpad;
+  int L, kp, rp;
+  __device__ int kdim(int64_t) const { return L; }
+  __device__ int64_t count(int64_t) const { return 1; }
+  __device__ Term<T> term(int64_t r, int64_t) const {
+    return Term<T>{V + r * (int64_t)L * kp, xpad + r * (int64_t)L * rp, L};
+  }
+};
+
+// Leaf backward step (Algorithm 2 on the leaves): row j = leaf j, one term
+// V_j y^_j (V_j stored transposed [nu][t], padded to Lp).
+template <class T>
+struct LeafBackwardRows {
+  const T *Vt;
+  const T *yhat;
+  int k, Lp, rp;
+  int64_t leaf0;
+  __device__ int kdim(int64_t) const { return k; }
+  __device__ int64_t count(int64_t) const { return 1; }
+  __device__ Term<T> term(int64_t r, int64_t) const {
+    return Term<T>{Vt + r * (int64_t)k * Lp, yhat + (leaf0 + r) * (int64_t)k * rp, k};
+  }
+};
+
+// Nearfield (Algorithm 3, inadmissible blocks): row j = leaf j, terms G_b x|s_b
+// for the inadmissible blocks b of row j (G_b stored transposed [c][t]).
+template <class T>
+struct NearRows {
+  const T *near;
+  const int64_t *ptr;
+  const int32_t *col;
+  const T *xpad;
+  int L, Lp, rp;
+  __device__ int kdim(int64_t) const { return L; }
+  __device__ int64_t count(int64_t r) const { return ptr[r + 1] - ptr[r]; }
+  __device__ Term<T> term(int64_t r, int64_t i) const {
+    const int64_t e = ptr[r] + i;
+    return Term<T>{near + e * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
+  }
+};
+
+// Block-row product: output tile out_r (M x rp) = sum over the row's terms of
+// A_i X_i, one CTA per row.  The A and X tiles stream through an nst-stage
+// shared-memory ring, each stage filled by one bulk-copy pair (TMA engine)
+// that completes on the stage's mbarrier; thread 0 refills a stage once every
+// thread is done with it.  Each thread keeps a 4 x (16 bytes) register tile
+// of the output for one slice of the contraction index; the slices are summed
+// in a fixed order at the end (no atomics: results are bit-reproducible).
+// Used for the coupling (rows = clusters), the leaf forward step, the leaf
+// backward step and the nearfield (rows = leaves); with accumulate the tile
+// is added to out instead of overwriting it.
+template <class T, class Rows>
+__global__ void __launch_bounds__(kThreads, 1) k_blockrow(Rows rows, RowCfg cfg, int accumulate, T *__restrict__ out) {
   using V = typename Vec16<T>::V;
   constexpr int VN = Vec16<T>::N;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + cfg.bar_off);
   const int tid = threadIdx.x;
-  const int64_t t = row0 + blockIdx.x;
-  const int64_t e0 = adm_ptr[t], nb = adm_ptr[t + 1] - e0;
-  const int k = cfg.k, kp = cfg.kp, rp = cfg.rp;
+  const int64_t r = blockIdx.x;
+  const int64_t nb = rows.count(r);
+  const int Mp = cfg.Mp, rp = cfg.rp;
 
   if (tid == 0) {
     for (int s = 0; s < cfg.nst; ++s) mbar_init(&bar[s], 1);
@@ -209,11 +262,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_coupling(const T *__restrict__ 
   auto issue = [&](int64_t i) {
     const int s = (int)(i % cfg.nst);
     unsigned char *st = smem + (size_t)s * cfg.stage_bytes;
-    const int64_t e = e0 + i;
-    const int64_t col = adm_col[e];
-    mbar_expect_tx(&bar[s], cfg.s_bytes + cfg.x_bytes);
-    bulk_g2s(st, S + e * (int64_t)k * kp, cfg.s_bytes, &bar[s]);
-    bulk_g2s(st + cfg.s_bytes, xhat + col * (int64_t)k * rp, cfg.x_bytes, &bar[s]);
+    const Term<T> tm = rows.term(r, i);
+    const uint32_t ab = (uint32_t)(sizeof(T) * tm.K * Mp), xb = (uint32_t)(sizeof(T) * tm.K * rp);
+    mbar_expect_tx(&bar[s], ab + xb);
+    bulk_g2s(st, tm.A, ab, &bar[s]);
+    bulk_g2s(st + cfg.a_bytes, tm.X, xb, &bar[s]);
   };
   if (tid == 0)
     for (; issued < nb && issued < cfg.nst; ++issued) issue(issued);
@@ -221,8 +274,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_coupling(const T *__restrict__ 
   const int tile = tid % cfg.tiles, ks = tid / cfg.tiles;
   const bool active = ks < cfg.ksplit;
   const int vg = tile % cfg.nvg, cg = tile / cfg.nvg;
-  const int mu0 = ks * cfg.kc;
-  const int mu1 = min(k, mu0 + cfg.kc);
   T acc[4][VN];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -239,18 +290,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_coupling(const T *__restrict__ 
       __syncthreads();
       return;
     }
-    const T *sS = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
-    const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.s_bytes);
+    const T *sA = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
+    const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
     if (active) {
+      const int K = rows.kdim(i);
+      const int kc = (K + cfg.ksplit - 1) / cfg.ksplit;
+      const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
 #pragma unroll 4
       for (int mu = mu0; mu < mu1; ++mu) {
-        T sv[4];
-        const V *sp = reinterpret_cast<const V *>(sS + mu * kp + 4 * vg);
+        T av[4];
+        const V *ap = reinterpret_cast<const V *>(sA + mu * Mp + 4 * vg);
 #pragma unroll
         for (int q = 0; q < 4 / VN; ++q) {
-          const V v = sp[q];
+          const V v = ap[q];
 #pragma unroll
-          for (int l = 0; l < VN; ++l) sv[q * VN + l] = lane<T>(v, l);
+          for (int l = 0; l < VN; ++l) av[q * VN + l] = lane<T>(v, l);
         }
         const V xv = *reinterpret_cast<const V *>(sX + mu * rp + VN * cg);
         T xs[VN];
@@ -259,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_coupling(const T *__restrict__ 
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < VN; ++c) acc[a][c] = madd(sv[a], xs[c], acc[a][c]);
+          for (int c = 0; c < VN; ++c) acc[a][c] = madd(av[a], xs[c], acc[a][c]);
       }
     }
     __syncthreads();
@@ -268,104 +322,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_coupling(const T *__restrict__ 
       ++issued;
     }
   }
-  // sum the mu slices in a fixed order
+  // sum the slices in a fixed order
   T *red = reinterpret_cast<T *>(smem);
   if (active) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int c = 0; c < VN; ++c) red[((int64_t)ks * kp + 4 * vg + a) * rp + VN * cg + c] = acc[a][c];
+      for (int c = 0; c < VN; ++c) red[((int64_t)ks * Mp + 4 * vg + a) * rp + VN * cg + c] = acc[a][c];
   }
   __syncthreads();
-  T *out = yhat + t * (int64_t)k * rp;
-  for (int o = tid; o < k * rp; o += blockDim.x) {
-    const int nu = o / rp, c = o - nu * rp;
-    T sum = zero_of<T>();
-    for (int q = 0; q < cfg.ksplit; ++q) sum = sum + red[((int64_t)q * kp + nu) * rp + c];
-    out[o] = sum;
+  T *o = out + r * (int64_t)cfg.M * rp;
+  for (int q = tid; q < cfg.M * rp; q += blockDim.x) {
+    const int nu = q / rp, c = q - nu * rp;
+    T sum = accumulate ? o[q] : zero_of<T>();
+    for (int z = 0; z < cfg.ksplit; ++z) sum = sum + red[((int64_t)z * Mp + nu) * rp + c];
+    o[q] = sum;
   }
 }
 
 constexpr size_t kSmemMax = 227 * 1024;
 
+// geometry for output tiles M x rp and contraction lengths up to Kmax;
+// threads: the number of threads the kernel is launched with
 template <class T>
-int coupling_cfg(int k, int kp, int rp, CoupleCfg &cfg) {
+int row_cfg(int M, int Mp, int rp, int Kmax, int threads, RowCfg &cfg) {
   constexpr int VN = Vec16<T>::N;
-  cfg.k = k;
-  cfg.kp = kp;
+  cfg.M = M;
+  cfg.Mp = Mp;
   cfg.rp = rp;
-  cfg.nvg = kp / 4;
+  cfg.nvg = Mp / 4;
   cfg.ncg = rp / VN;
   cfg.tiles = cfg.nvg * cfg.ncg;
-  if (cfg.tiles > kThreads) return fail(H2_EINVAL, "rank x right-hand sides too large for one coupling tile");
-  int ks = std::max(1, std::min(kThreads / cfg.tiles, k));
-  cfg.kc = (k + ks - 1) / ks;
-  cfg.ksplit = (k + cfg.kc - 1) / cfg.kc;
-  cfg.s_bytes = (uint32_t)(sizeof(T) * k * kp);
-  cfg.x_bytes = (uint32_t)(sizeof(T) * k * rp);
-  cfg.stage_bytes = cfg.s_bytes + cfg.x_bytes;
-  size_t red = sizeof(T) * (size_t)cfg.ksplit * kp * rp;
-  int nst = 4;
+  if (cfg.tiles > threads) return fail(H2_EINVAL, "tile rows x right-hand sides too large for one CTA");
+  cfg.ksplit = std::max(1, std::min(threads / cfg.tiles, Kmax));
+  cfg.a_bytes = (uint32_t)(sizeof(T) * Kmax * Mp);
+  cfg.stage_bytes = cfg.a_bytes + (uint32_t)(sizeof(T) * Kmax * rp);
+  size_t red = sizeof(T) * (size_t)cfg.ksplit * Mp * rp;
+  // stages: up to 6, sized so that 512 threads per SM stay resident when possible
+  const size_t budget = kSmemMax / (512 / threads) - 64;
+  int nst = (int)std::min<size_t>(6, budget / cfg.stage_bytes);
+  if (nst < 2) {
+    nst = 6;
+    while (nst > 1 && std::max((size_t)nst * cfg.stage_bytes, red) + 64 > kSmemMax) --nst;
+  }
   while (nst > 1 && std::max((size_t)nst * cfg.stage_bytes, red) + 64 > kSmemMax) --nst;
   cfg.nst = nst;
   size_t body = std::max((size_t)nst * cfg.stage_bytes, red);
   cfg.bar_off = (uint32_t)((body + 15) / 16 * 16);
-  if (cfg.bar_off + 8 * nst > kSmemMax) return fail(H2_EINVAL, "coupling tile does not fit in shared memory");
+  if (cfg.bar_off + 8 * nst > kSmemMax) return fail(H2_EINVAL, "block-row tile does not fit in shared memory");
   return H2_OK;
 }
 
-// leaf backward + nearfield: one CTA per leaf t;
-// y|t = V_t y^_t + sum_b G_b x|s_b
-template <class T>
-__global__ void k_leaf_near(const T *__restrict__ V, const T *__restrict__ near, const int64_t *__restrict__ near_ptr,
-                            const int32_t *__restrict__ near_col, int L, int k, int nrhs, int64_t leaf0,
-                            int use_far, const T *__restrict__ yhat, const T *__restrict__ xpad,
-                            T *__restrict__ ypad) {
-  extern __shared__ unsigned char smem_raw[];
-  T *sA = reinterpret_cast<T *>(smem_raw);         // up to L x max(k, L)
-  T *sx = sA + L * (k > L ? k : L);                // up to max(k, L) x nrhs
-  const int64_t j = blockIdx.x;
-  const int lr = L * nrhs;
-  T acc[kMaxOut];
-#pragma unroll
-  for (int i = 0; i < kMaxOut; ++i) acc[i] = zero_of<T>();
-  if (use_far) {
-    for (int i = threadIdx.x; i < L * k; i += blockDim.x) sA[i] = V[j * L * k + i];
-    for (int i = threadIdx.x; i < k * nrhs; i += blockDim.x) sx[i] = yhat[(leaf0 + j) * k * nrhs + i];
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kMaxOut; ++i) {
-      int o = threadIdx.x + i * blockDim.x;
-      if (o < lr) {
-        int t = o / nrhs, r = o - t * nrhs;
-        T sum = acc[i];
-        for (int nu = 0; nu < k; ++nu) sum = madd(sA[t * k + nu], sx[nu * nrhs + r], sum);
-        acc[i] = sum;
-      }
-    }
-  }
-  for (int64_t e = near_ptr[j]; e < near_ptr[j + 1]; ++e) {
-    const int64_t s = near_col[e];
-    __syncthreads();
-    for (int i = threadIdx.x; i < L * L; i += blockDim.x) sA[i] = near[e * L * L + i];
-    for (int i = threadIdx.x; i < lr; i += blockDim.x) sx[i] = xpad[s * lr + i];
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kMaxOut; ++i) {
-      int o = threadIdx.x + i * blockDim.x;
-      if (o < lr) {
-        int t = o / nrhs, r = o - t * nrhs;
-        T sum = acc[i];
-        for (int c = 0; c < L; ++c) sum = madd(sA[t * L + c], sx[c * nrhs + r], sum);
-        acc[i] = sum;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < kMaxOut; ++i) {
-    int o = threadIdx.x + i * blockDim.x;
-    if (o < lr) ypad[j * lr + o] = acc[i];
-  }
+// threads per CTA: enough slices of the contraction for about 8 steps each
+inline int row_threads(int Mp, int rp, int Kmax, size_t esize) {
+  const int tiles = (Mp / 4) * (rp / (int)(16 / esize));
+  const int want = tiles * std::max(1, Kmax / 8);
+  for (int t : {64, 128})
+    if (want <= t) return t;
+  return 256;
 }
 
 int grid_for(int64_t n) {
@@ -401,18 +415,36 @@ struct Marks {
   }
 };
 
+template <class T, class Rows>
+int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int64_t nrows, int accumulate, T *out,
+                cudaStream_t st) {
+  if (nrows <= 0) return H2_OK;
+  size_t sm = cfg.bar_off + 8 * cfg.nst;
+  int rc;
+  if ((rc = set_smem<T>((const void *)k_blockrow<T, Rows>, sm))) return rc;
+  k_blockrow<T, Rows><<<(unsigned)nrows, threads, sm, st>>>(rows, cfg, accumulate, out);
+  return H2_OK;
+}
+
 template <class T, class Tio>
 int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
-  const int k = d.k, m = d.m, L = (int)d.lmax, D = d.depth, lmin = d.first_adm_level;
+  const int k = d.k, kp = d.kp, m = d.m, L = (int)d.lmax, Lp = (int)d.lp, D = d.depth, lmin = d.first_adm_level;
   const int rp = padded_rhs(nrhs, sizeof(T));   // every kernel below works on rp columns
   const int64_t leaf0 = d.nleaf - 1;
   T *xpad = (T *)d.xpad, *ypad = (T *)d.ypad, *xhat = (T *)d.xhat, *yhat = (T *)d.yhat;
   const bool far = lmin <= D;
   int rc;
-  CoupleCfg cfg{};
-  if (far && (rc = coupling_cfg<T>(k, d.kp, rp, cfg))) return rc;
+  RowCfg cf_fwd{}, cf_cpl{}, cf_back{}, cf_near{};
+  const int t_fwd = row_threads(kp, rp, L, sizeof(T)), t_cpl = row_threads(kp, rp, k, sizeof(T));
+  const int t_back = row_threads(Lp, rp, k, sizeof(T)), t_near = row_threads(Lp, rp, L, sizeof(T));
+  if (far) {
+    if ((rc = row_cfg<T>(k, kp, rp, L, t_fwd, cf_fwd))) return rc;
+    if ((rc = row_cfg<T>(k, kp, rp, k, t_cpl, cf_cpl))) return rc;
+    if ((rc = row_cfg<T>(L, Lp, rp, k, t_back, cf_back))) return rc;
+  }
+  if ((rc = row_cfg<T>(L, Lp, rp, L, t_near, cf_near))) return rc;
   Marks mk(c);
 
   mk.mark(H2_PH_PERMUTE_IN);
@@ -420,9 +452,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
   if (far) {
-    size_t sm = (size_t)(L * k + L * rp) * sizeof(T);
-    if ((rc = set_smem<T>((const void *)k_leaf_forward<T>, sm))) return rc;
-    k_leaf_forward<T><<<(unsigned)d.nleaf, kThreads, sm, st>>>((const T *)d.V, xpad, L, k, rp, leaf0, xhat);
+    LeafForwardRows<T> rows{(const T *)d.V, xpad, L, kp, rp};
+    if ((rc = launch_rows<T>(rows, cf_fwd, t_fwd, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
     mk.count(H2_PH_LEAF_FORWARD);
   }
   mk.mark(H2_PH_UPWARD);
@@ -438,10 +469,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.mark(H2_PH_COUPLING);
   if (far) {
     int64_t row0 = ((int64_t)1 << lmin) - 1;
-    size_t sm = cfg.bar_off + 8 * cfg.nst;
-    if ((rc = set_smem<T>((const void *)k_coupling<T>, sm))) return rc;
-    k_coupling<T><<<(unsigned)(d.nclu - row0), kThreads, sm, st>>>((const T *)d.S, d.adm_ptr, d.adm_col, cfg, row0,
-                                                                   xhat, yhat);
+    CouplingRows<T> rows{(const T *)d.S, d.adm_ptr, d.adm_col, xhat, k, kp, rp, row0};
+    if ((rc = launch_rows<T>(rows, cf_cpl, t_cpl, d.nclu - row0, 0, yhat + row0 * (int64_t)k * rp, st))) return rc;
     mk.count(H2_PH_COUPLING);
   }
   mk.mark(H2_PH_DOWNWARD);
@@ -455,13 +484,14 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     }
   }
   mk.mark(H2_PH_LEAF_NEAR);
+  if (far) {
+    LeafBackwardRows<T> rows{(const T *)d.Vt, yhat, k, Lp, rp, leaf0};
+    if ((rc = launch_rows<T>(rows, cf_back, t_back, d.nleaf, 0, ypad, st))) return rc;
+    mk.count(H2_PH_LEAF_NEAR);
+  }
   {
-    int w = std::max(k, L);
-    size_t sm = (size_t)(L * w + w * rp) * sizeof(T);
-    if ((rc = set_smem<T>((const void *)k_leaf_near<T>, sm))) return rc;
-    k_leaf_near<T><<<(unsigned)d.nleaf, kThreads, sm, st>>>((const T *)d.V, (const T *)d.near, d.near_ptr,
-                                                             d.near_col, L, k, rp, leaf0, far ? 1 : 0, yhat, xpad,
-                                                             ypad);
+    NearRows<T> rows{(const T *)d.near, d.near_ptr, d.near_col, xpad, L, Lp, rp};
+    if ((rc = launch_rows<T>(rows, cf_near, t_near, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
   mk.mark(H2_PH_PERMUTE_OUT);

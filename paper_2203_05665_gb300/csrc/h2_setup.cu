@@ -70,8 +70,19 @@ struct Geo {
   const int32_t *pad_src;
   const int32_t *blk_row;   // row leaf of each near block
   const int32_t *blk_col;   // column leaf of each near block
-  int64_t lmax;
+  int64_t lmax, lp;         // leaf height and its padding to a multiple of 4
 };
+
+// Nearfield block layout: entry (t, c) of block b (test triangle t of the
+// row leaf, trial triangle c of the column leaf) at b L Lp + c Lp + t,
+// i.e. stored transposed with the row index padded to Lp; padding is zero.
+__device__ __forceinline__ void near_decode(const Geo &g, int64_t e, int64_t &b, int &t, int &c) {
+  const int64_t per = g.lmax * g.lp;
+  b = e / per;
+  const int rc = (int)(e - b * per);
+  c = rc / (int)g.lp;
+  t = rc - c * (int)g.lp;
+}
 
 __device__ __forceinline__ int shared_count(const int32_t *a, const int32_t *b) {
   int c = 0;
@@ -87,12 +98,12 @@ __device__ __forceinline__ int shared_count(const int32_t *a, const int32_t *b) 
 template <class T>
 __global__ void k_near_regular(Geo g, int64_t nblk, int q, T *__restrict__ near, int64_t *__restrict__ sing,
                                unsigned long long *__restrict__ nsing, int64_t sing_cap) {
-  const int64_t L = g.lmax, per = L * L, total = nblk * per;
+  const int64_t L = g.lmax, total = nblk * L * g.lp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t b = e / per;
-    int rc = (int)(e - b * per);
-    int r = rc / (int)L, c = rc - r * (int)L;
-    int32_t i = g.pad_src[g.blk_row[b] * L + r], j = g.pad_src[g.blk_col[b] * L + c];
+    int64_t b;
+    int r, c;
+    near_decode(g, e, b, r, c);
+    int32_t i = r < L ? g.pad_src[g.blk_row[b] * L + r] : -1, j = g.pad_src[g.blk_col[b] * L + c];
     if (i < 0 || j < 0) { near[e] = zero_of<T>(); continue; }
     if (i > j) { int32_t t = i; i = j; j = t; }
     int32_t ti[3] = {g.tri[3 * i], g.tri[3 * i + 1], g.tri[3 * i + 2]};
@@ -162,12 +173,12 @@ __device__ __forceinline__ double sing_region(int kind, int r, double xi, double
 
 template <class T>
 __global__ void k_near_singular(Geo g, const int64_t *__restrict__ sing, int64_t nsing, int q, T *__restrict__ near) {
-  const int64_t L = g.lmax, per = L * L;
+  const int64_t L = g.lmax;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsing; s += (int64_t)gridDim.x * blockDim.x) {
     int64_t e = sing[s];
-    int64_t b = e / per;
-    int rc = (int)(e - b * per);
-    int r = rc / (int)L, c = rc - r * (int)L;
+    int64_t b;
+    int r, c;
+    near_decode(g, e, b, r, c);
     int32_t i = g.pad_src[g.blk_row[b] * L + r], j = g.pad_src[g.blk_col[b] * L + c];
     if (i > j) { int32_t t = i; i = j; j = t; }
     int32_t ti[3] = {g.tri[3 * i], g.tri[3 * i + 1], g.tri[3 * i + 2]};
@@ -266,17 +277,24 @@ int build_typed(Ctx &c) {
     int64_t c0 = p.leaf0 + j;
     for (int64_t r = 0; r < p.size[c0]; ++r) pad[j * L + r] = (int32_t)p.perm[p.first[c0] + r];
   }
-  // V padded to L rows per leaf
-  std::vector<double> Vp((size_t)d.npad * k, 0.0);
+  // V per leaf in two layouts: [L][kp] for the forward step (x^ = V^T x) and
+  // transposed [k][Lp] for the backward step (y = V y^); padding is zero
+  const int64_t kp = d.kp, Lp = d.lp;
+  std::vector<double> Vp((size_t)p.nleaf * L * kp, 0.0), Vt((size_t)p.nleaf * k * Lp, 0.0);
   for (int64_t j = 0; j < p.nleaf; ++j) {
     int64_t c0 = p.leaf0 + j;
     for (int64_t r = 0; r < p.size[c0]; ++r)
-      for (int nu = 0; nu < k; ++nu) Vp[(j * L + r) * k + nu] = p.V[(p.first[c0] + r) * k + nu];
+      for (int nu = 0; nu < k; ++nu) {
+        double v = p.V[(p.first[c0] + r) * k + nu];
+        Vp[(j * L + r) * kp + nu] = v;
+        Vt[(j * k + nu) * Lp + r] = v;
+      }
   }
   int rc;
   if ((rc = dev_alloc(d, (void **)&d.pad_src, pad.size() * 4))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(d.pad_src, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, st));
   if ((rc = upload_converted<T>(d, &d.V, Vp, st))) return rc;
+  if ((rc = upload_converted<T>(d, &d.Vt, Vt, st))) return rc;
   if ((rc = upload_converted<T>(d, &d.Ef, p.Ef, st))) return rc;
   if ((rc = dev_alloc(d, (void **)&d.adm_ptr, p.adm_ptr.size() * 8))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(d.adm_ptr, p.adm_ptr.data(), p.adm_ptr.size() * 8, cudaMemcpyHostToDevice, st));
@@ -331,16 +349,16 @@ int build_typed(Ctx &c) {
   }
 
   // nearfield entries
-  if ((rc = dev_alloc(d, &d.near, std::max<size_t>(1, (size_t)d.nnear * L * L) * sizeof(T)))) return rc;
+  if ((rc = dev_alloc(d, &d.near, std::max<size_t>(1, (size_t)d.nnear * L * Lp) * sizeof(T)))) return rc;
   if (d.nnear > 0) {
     // pairs that share a vertex: at most (n * 3 * valence) ordered pairs; bound by the entry count
-    int64_t cap = std::min<int64_t>(d.nnear * L * L, 64 * p.n + 1024);
+    int64_t cap = std::min<int64_t>(d.nnear * L * Lp, 64 * p.n + 1024);
     if (cudaMalloc(&t_sing.ptr, cap * 8) != cudaSuccess) return fail(H2_ENOMEM, "singular list");
     if (cudaMalloc(&t_cnt.ptr, 8) != cudaSuccess) return fail(H2_ENOMEM, "singular count");
     H2_CUDA_TRY(cudaMemsetAsync(t_cnt.ptr, 0, 8, st));
     Geo g{(const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src,
-          (const int32_t *)t_nrow.ptr, (const int32_t *)t_ncol.ptr, L};
-    k_near_regular<T><<<grid_for(d.nnear * L * L, 128), 128, 0, st>>>(
+          (const int32_t *)t_nrow.ptr, (const int32_t *)t_ncol.ptr, L, Lp};
+    k_near_regular<T><<<grid_for(d.nnear * L * Lp, 128), 128, 0, st>>>(
         g, d.nnear, c.quad_order, (T *)d.near, (int64_t *)t_sing.ptr, (unsigned long long *)t_cnt.ptr, cap);
     H2_CUDA_TRY(cudaGetLastError());
     unsigned long long ns = 0;
@@ -385,6 +403,7 @@ int device_build(Ctx &c) {
   d.nleaf = p.nleaf;
   d.lmax = p.lmax;
   d.npad = p.nleaf * p.lmax;
+  d.lp = (p.lmax + 3) / 4 * 4;
   d.nadm = (int64_t)p.adm_col.size();
   d.nnear = (int64_t)p.near_col.size();
   if (d.prec == H2_F64) {

@@ -48,47 +48,59 @@ __global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs,
   }
 }
 
-// one mode product of the factored transfer: axis d, transpose or not.
-// in/out: [k][nrhs] tensors with nu = jx + m jy + m^2 jz.
-// trans: out[.., j, ..] = sum_{j'} F[j'][j] in[.., j', ..]   (E^T, upward)
-// plain: out[.., j', ..] = sum_{j} F[j'][j] in[.., j, ..]    (E, downward)
+// One mode product of the factored transfer on a [k][rp] coefficient tensor
+// (nu = jx + m jy + m^2 jz): every thread owns one fibre along axis d for one
+// column, reads its m entries once and writes m results.
+//   trans: out[.., j, ..] = sum_{j'} F[j'][j] in[.., j', ..]   (E^T, upward)
+//   plain: out[.., j', ..] = sum_{j} F[j'][j] in[.., j, ..]    (E, downward)
+constexpr int kMaxM = 5;
+
 template <class T>
-__device__ __forceinline__ void mode_product(const T *__restrict__ F, const T *in, T *out, int m, int k, int nrhs,
-                                             int d, bool trans) {
+__device__ __forceinline__ void mode_fibres(const T *F, const T *in, T *out, int m, int k, int rp, int d, bool trans) {
   const int stride = d == 0 ? 1 : (d == 1 ? m : m * m);
-  for (int o = threadIdx.x; o < k * nrhs; o += blockDim.x) {
-    int nu = o / nrhs, r = o - nu * nrhs;
-    int jd = (nu / stride) % m;
-    int base = nu - jd * stride;
-    T acc = zero_of<T>();
-    for (int i = 0; i < m; ++i) {
-      T f = trans ? F[i * m + jd] : F[jd * m + i];
-      acc = madd(f, in[(base + i * stride) * nrhs + r], acc);
+  const int items = (k / m) * rp;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int c = it % rp, f = it / rp;
+    const int lo = f % stride, hi = f / stride;
+    const int base = lo + hi * stride * m;
+    T v[kMaxM];
+#pragma unroll
+    for (int i = 0; i < kMaxM; ++i)
+      if (i < m) v[i] = in[(base + i * stride) * rp + c];
+#pragma unroll
+    for (int j = 0; j < kMaxM; ++j) {
+      if (j >= m) break;
+      T acc = zero_of<T>();
+#pragma unroll
+      for (int i = 0; i < kMaxM; ++i)
+        if (i < m) acc = madd(trans ? F[i * m + j] : F[j * m + i], v[i], acc);
+      out[(base + j * stride) * rp + c] = acc;
     }
-    out[o] = acc;
   }
 }
 
-// upward: parents of level l; x^_parent = sum_children E_c^T x^_c
+// upward step for the parents of level l (Algorithm 1): x^_p = sum_children E_c^T x^_c
 template <class T>
-__global__ void k_upward(const T *__restrict__ Ef, int m, int k, int nrhs, int64_t par0, T *__restrict__ xhat) {
-  extern __shared__ unsigned char smem_raw[];
+__global__ void k_upward(const T *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ xhat) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kr = k * rp, mm = m * m;
   T *a = reinterpret_cast<T *>(smem_raw);
-  T *b = a + k * nrhs;
-  T *acc = b + k * nrhs;
+  T *b = a + kr;
+  T *acc = b + kr;
+  T *F = acc + kr;   // 2 children x 3 axes x m x m
   const int64_t par = par0 + blockIdx.x;
-  const int kr = k * nrhs;
+  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = Ef[(2 * par + 1) * 3 * mm + i];
   for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = zero_of<T>();
-  for (int ch = 1; ch <= 2; ++ch) {
-    const int64_t c = 2 * par + ch;
+  for (int ch = 0; ch < 2; ++ch) {
+    const int64_t c = 2 * par + 1 + ch;
     for (int i = threadIdx.x; i < kr; i += blockDim.x) a[i] = xhat[c * kr + i];
     __syncthreads();
-    const T *F = Ef + c * 3 * m * m;
-    mode_product(F + 0 * m * m, a, b, m, k, nrhs, 0, true);
+    const T *Fc = F + ch * 3 * mm;
+    mode_fibres(Fc, a, b, m, k, rp, 0, true);
     __syncthreads();
-    mode_product(F + 1 * m * m, b, a, m, k, nrhs, 1, true);
+    mode_fibres(Fc + mm, b, a, m, k, rp, 1, true);
     __syncthreads();
-    mode_product(F + 2 * m * m, a, b, m, k, nrhs, 2, true);
+    mode_fibres(Fc + 2 * mm, a, b, m, k, rp, 2, true);
     __syncthreads();
     for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = acc[i] + b[i];
     __syncthreads();
@@ -96,24 +108,32 @@ __global__ void k_upward(const T *__restrict__ Ef, int m, int k, int nrhs, int64
   for (int i = threadIdx.x; i < kr; i += blockDim.x) xhat[par * kr + i] = acc[i];
 }
 
-// downward: children of level l+1; y^_c += E_c y^_parent
+// downward step for the children of level l+1 (Algorithm 2): y^_c += E_c y^_parent;
+// one CTA per parent of level l handles both children
 template <class T>
-__global__ void k_downward(const T *__restrict__ Ef, int m, int k, int nrhs, int64_t ch0, T *__restrict__ yhat) {
-  extern __shared__ unsigned char smem_raw[];
-  T *a = reinterpret_cast<T *>(smem_raw);
-  T *b = a + k * nrhs;
-  const int64_t c = ch0 + blockIdx.x, par = (c - 1) / 2;
-  const int kr = k * nrhs;
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) a[i] = yhat[par * kr + i];
+__global__ void k_downward(const T *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ yhat) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kr = k * rp, mm = m * m;
+  T *p = reinterpret_cast<T *>(smem_raw);
+  T *a = p + kr;
+  T *b = a + kr;
+  T *F = b + kr;
+  const int64_t par = par0 + blockIdx.x;
+  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = Ef[(2 * par + 1) * 3 * mm + i];
+  for (int i = threadIdx.x; i < kr; i += blockDim.x) p[i] = yhat[par * kr + i];
   __syncthreads();
-  const T *F = Ef + c * 3 * m * m;
-  mode_product(F + 0 * m * m, a, b, m, k, nrhs, 0, false);
-  __syncthreads();
-  mode_product(F + 1 * m * m, b, a, m, k, nrhs, 1, false);
-  __syncthreads();
-  mode_product(F + 2 * m * m, a, b, m, k, nrhs, 2, false);
-  __syncthreads();
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) yhat[c * kr + i] = yhat[c * kr + i] + b[i];
+  for (int ch = 0; ch < 2; ++ch) {
+    const int64_t c = 2 * par + 1 + ch;
+    const T *Fc = F + ch * 3 * mm;
+    mode_fibres(Fc, p, a, m, k, rp, 0, false);
+    __syncthreads();
+    mode_fibres(Fc + mm, a, b, m, k, rp, 1, false);
+    __syncthreads();
+    mode_fibres(Fc + 2 * mm, b, a, m, k, rp, 2, false);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kr; i += blockDim.x) yhat[c * kr + i] = yhat[c * kr + i] + a[i];
+    __syncthreads();
+  }
 }
 
 template <class T>
@@ -153,7 +173,7 @@ __device__ __forceinline__ dd lane<dd>(const float4 &v, int q) {
 // Launch geometry of the block-row kernel (computed on the host).
 struct RowCfg {
   int M, Mp, rp;             // rows of an output tile, rows padded to 4, columns (padded to 16 bytes)
-  int nvg, ncg, tiles;       // 4-row groups, 16-byte column groups, register tiles of 4 x (16 bytes)
+  int nvg, ncg, tiles;       // row groups (4 R rows), 16-byte column groups, register tiles of 4 R x (16 bytes)
   int ksplit;                // the contraction range of every term is split in ksplit slices
   int nst;                   // pipeline stages
   uint32_t a_bytes, stage_bytes, bar_off;   // A region of a stage, stage size, mbarrier offset
@@ -233,7 +253,9 @@ struct NearRows {
 };
 
 // Block-row product: output tile out_r (M x rp) = sum over the row's terms of
-// A_i X_i, one CTA per row.  The A and X tiles stream through an nst-stage
+// A_i X_i, one CTA per row.  A thread's register tile holds R groups of 4 rows
+// (rows g Mp/R + 4 vg + a, so that the lanes of a warp read contiguous
+// 16-byte pieces of one A row) times one 16-byte group of columns.  The A and X tiles stream through an nst-stage
 // shared-memory ring, each stage filled by one bulk-copy pair (TMA engine)
 // that completes on the stage's mbarrier; thread 0 refills a stage once every
 // thread is done with it.  Each thread keeps a 4 x (16 bytes) register tile
@@ -242,7 +264,7 @@ struct NearRows {
 // Used for the coupling (rows = clusters), the leaf forward step, the leaf
 // backward step and the nearfield (rows = leaves); with accumulate the tile
 // is added to out instead of overwriting it.
-template <class T, class Rows>
+template <class T, int R, class Rows>
 __global__ void __launch_bounds__(kThreads, 1) k_blockrow(Rows rows, RowCfg cfg, int accumulate, T *__restrict__ out) {
   using V = typename Vec16<T>::V;
   constexpr int VN = Vec16<T>::N;
@@ -274,9 +296,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_blockrow(Rows rows, RowCfg cfg,
   const int tile = tid % cfg.tiles, ks = tid / cfg.tiles;
   const bool active = ks < cfg.ksplit;
   const int vg = tile % cfg.nvg, cg = tile / cfg.nvg;
-  T acc[4][VN];
+  const int gstride = Mp / R;
+  T acc[4 * R][VN];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4 * R; ++a)
 #pragma unroll
     for (int c = 0; c < VN; ++c) acc[a][c] = zero_of<T>();
 
@@ -296,22 +319,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_blockrow(Rows rows, RowCfg cfg,
       const int K = rows.kdim(i);
       const int kc = (K + cfg.ksplit - 1) / cfg.ksplit;
       const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
-#pragma unroll 4
+#pragma unroll 2
       for (int mu = mu0; mu < mu1; ++mu) {
-        T av[4];
-        const V *ap = reinterpret_cast<const V *>(sA + mu * Mp + 4 * vg);
+        T av[4 * R];
 #pragma unroll
-        for (int q = 0; q < 4 / VN; ++q) {
-          const V v = ap[q];
+        for (int g = 0; g < R; ++g) {
+          const V *ap = reinterpret_cast<const V *>(sA + mu * Mp + g * gstride + 4 * vg);
 #pragma unroll
-          for (int l = 0; l < VN; ++l) av[q * VN + l] = lane<T>(v, l);
+          for (int q = 0; q < 4 / VN; ++q) {
+            const V v = ap[q];
+#pragma unroll
+            for (int l = 0; l < VN; ++l) av[4 * g + q * VN + l] = lane<T>(v, l);
+          }
         }
         const V xv = *reinterpret_cast<const V *>(sX + mu * rp + VN * cg);
         T xs[VN];
 #pragma unroll
         for (int l = 0; l < VN; ++l) xs[l] = lane<T>(xv, l);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4 * R; ++a)
 #pragma unroll
           for (int c = 0; c < VN; ++c) acc[a][c] = madd(av[a], xs[c], acc[a][c]);
       }
@@ -326,9 +352,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_blockrow(Rows rows, RowCfg cfg,
   T *red = reinterpret_cast<T *>(smem);
   if (active) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4 * R; ++a)
 #pragma unroll
-      for (int c = 0; c < VN; ++c) red[((int64_t)ks * Mp + 4 * vg + a) * rp + VN * cg + c] = acc[a][c];
+      for (int c = 0; c < VN; ++c)
+        red[((int64_t)ks * Mp + (a / 4) * gstride + 4 * vg + (a % 4)) * rp + VN * cg + c] = acc[a][c];
   }
   __syncthreads();
   T *o = out + r * (int64_t)cfg.M * rp;
@@ -345,12 +372,12 @@ constexpr size_t kSmemMax = 227 * 1024;
 // geometry for output tiles M x rp and contraction lengths up to Kmax;
 // threads: the number of threads the kernel is launched with
 template <class T>
-int row_cfg(int M, int Mp, int rp, int Kmax, int threads, RowCfg &cfg) {
+int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, RowCfg &cfg) {
   constexpr int VN = Vec16<T>::N;
   cfg.M = M;
   cfg.Mp = Mp;
   cfg.rp = rp;
-  cfg.nvg = Mp / 4;
+  cfg.nvg = Mp / (4 * R);
   cfg.ncg = rp / VN;
   cfg.tiles = cfg.nvg * cfg.ncg;
   if (cfg.tiles > threads) return fail(H2_EINVAL, "tile rows x right-hand sides too large for one CTA");
@@ -373,9 +400,15 @@ int row_cfg(int M, int Mp, int rp, int Kmax, int threads, RowCfg &cfg) {
   return H2_OK;
 }
 
+// row groups per register tile: two for FP32 when the rows split evenly
+template <class T>
+inline int row_groups(int Mp) {
+  return (sizeof(T) == 4 && Mp % 8 == 0) ? 2 : 1;
+}
+
 // threads per CTA: enough slices of the contraction for about 8 steps each
-inline int row_threads(int Mp, int rp, int Kmax, size_t esize) {
-  const int tiles = (Mp / 4) * (rp / (int)(16 / esize));
+inline int row_threads(int Mp, int rp, int Kmax, size_t esize, int R) {
+  const int tiles = (Mp / (4 * R)) * (rp / (int)(16 / esize));
   const int want = tiles * std::max(1, Kmax / 8);
   for (int t : {64, 128})
     if (want <= t) return t;
@@ -416,13 +449,18 @@ struct Marks {
 };
 
 template <class T, class Rows>
-int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int64_t nrows, int accumulate, T *out,
+int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int R, int64_t nrows, int accumulate, T *out,
                 cudaStream_t st) {
   if (nrows <= 0) return H2_OK;
   size_t sm = cfg.bar_off + 8 * cfg.nst;
   int rc;
-  if ((rc = set_smem<T>((const void *)k_blockrow<T, Rows>, sm))) return rc;
-  k_blockrow<T, Rows><<<(unsigned)nrows, threads, sm, st>>>(rows, cfg, accumulate, out);
+  if (R == 2) {
+    if ((rc = set_smem<T>((const void *)k_blockrow<T, 2, Rows>, sm))) return rc;
+    k_blockrow<T, 2, Rows><<<(unsigned)nrows, threads, sm, st>>>(rows, cfg, accumulate, out);
+  } else {
+    if ((rc = set_smem<T>((const void *)k_blockrow<T, 1, Rows>, sm))) return rc;
+    k_blockrow<T, 1, Rows><<<(unsigned)nrows, threads, sm, st>>>(rows, cfg, accumulate, out);
+  }
   return H2_OK;
 }
 
@@ -437,14 +475,15 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   const bool far = lmin <= D;
   int rc;
   RowCfg cf_fwd{}, cf_cpl{}, cf_back{}, cf_near{};
-  const int t_fwd = row_threads(kp, rp, L, sizeof(T)), t_cpl = row_threads(kp, rp, k, sizeof(T));
-  const int t_back = row_threads(Lp, rp, k, sizeof(T)), t_near = row_threads(Lp, rp, L, sizeof(T));
+  const int Rk = row_groups<T>(kp), RL = row_groups<T>(Lp);
+  const int t_fwd = row_threads(kp, rp, L, sizeof(T), Rk), t_cpl = row_threads(kp, rp, k, sizeof(T), Rk);
+  const int t_back = row_threads(Lp, rp, k, sizeof(T), RL), t_near = row_threads(Lp, rp, L, sizeof(T), RL);
   if (far) {
-    if ((rc = row_cfg<T>(k, kp, rp, L, t_fwd, cf_fwd))) return rc;
-    if ((rc = row_cfg<T>(k, kp, rp, k, t_cpl, cf_cpl))) return rc;
-    if ((rc = row_cfg<T>(L, Lp, rp, k, t_back, cf_back))) return rc;
+    if ((rc = row_cfg<T>(k, kp, rp, L, t_fwd, Rk, cf_fwd))) return rc;
+    if ((rc = row_cfg<T>(k, kp, rp, k, t_cpl, Rk, cf_cpl))) return rc;
+    if ((rc = row_cfg<T>(L, Lp, rp, k, t_back, RL, cf_back))) return rc;
   }
-  if ((rc = row_cfg<T>(L, Lp, rp, L, t_near, cf_near))) return rc;
+  if ((rc = row_cfg<T>(L, Lp, rp, L, t_near, RL, cf_near))) return rc;
   Marks mk(c);
 
   mk.mark(H2_PH_PERMUTE_IN);
@@ -453,12 +492,12 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.mark(H2_PH_LEAF_FORWARD);
   if (far) {
     LeafForwardRows<T> rows{(const T *)d.V, xpad, L, kp, rp};
-    if ((rc = launch_rows<T>(rows, cf_fwd, t_fwd, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
+    if ((rc = launch_rows<T>(rows, cf_fwd, t_fwd, Rk, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
     mk.count(H2_PH_LEAF_FORWARD);
   }
   mk.mark(H2_PH_UPWARD);
   if (far) {
-    size_t sm = (size_t)3 * k * rp * sizeof(T);
+    size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_upward<T>, sm))) return rc;
     for (int l = D - 1; l >= lmin; --l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
@@ -470,28 +509,28 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   if (far) {
     int64_t row0 = ((int64_t)1 << lmin) - 1;
     CouplingRows<T> rows{(const T *)d.S, d.adm_ptr, d.adm_col, xhat, k, kp, rp, row0};
-    if ((rc = launch_rows<T>(rows, cf_cpl, t_cpl, d.nclu - row0, 0, yhat + row0 * (int64_t)k * rp, st))) return rc;
+    if ((rc = launch_rows<T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, yhat + row0 * (int64_t)k * rp, st))) return rc;
     mk.count(H2_PH_COUPLING);
   }
   mk.mark(H2_PH_DOWNWARD);
   if (far) {
-    size_t sm = (size_t)2 * k * rp * sizeof(T);
+    size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_downward<T>, sm))) return rc;
     for (int l = lmin; l < D; ++l) {
-      int64_t ch0 = ((int64_t)2 << l) - 1;
-      k_downward<T><<<(unsigned)((int64_t)2 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, rp, ch0, yhat);
+      int64_t par0 = ((int64_t)1 << l) - 1;
+      k_downward<T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, rp, par0, yhat);
       mk.count(H2_PH_DOWNWARD);
     }
   }
   mk.mark(H2_PH_LEAF_NEAR);
   if (far) {
     LeafBackwardRows<T> rows{(const T *)d.Vt, yhat, k, Lp, rp, leaf0};
-    if ((rc = launch_rows<T>(rows, cf_back, t_back, d.nleaf, 0, ypad, st))) return rc;
+    if ((rc = launch_rows<T>(rows, cf_back, t_back, RL, d.nleaf, 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
   {
     NearRows<T> rows{(const T *)d.near, d.near_ptr, d.near_col, xpad, L, Lp, rp};
-    if ((rc = launch_rows<T>(rows, cf_near, t_near, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
+    if ((rc = launch_rows<T>(rows, cf_near, t_near, RL, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
   mk.mark(H2_PH_PERMUTE_OUT);

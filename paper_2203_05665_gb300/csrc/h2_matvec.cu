@@ -187,8 +187,13 @@ struct Term {
   int K;
 };
 
-// Coupling (Algorithm 3, admissible blocks): row r = cluster t = row0 + r,
-// terms S_b x^_{s_b} for the admissible blocks b of row t (S_b stored [mu][nu]).
+// Row sources of the block-row kernel.  Every row has count(r) terms; the
+// terms of all rows form one flat sequence (first(r) = flat index of row r's
+// first term, first(nrows) = total), term(e) gives the tiles of flat term e
+// and kdim(e) its contraction length.
+
+// Coupling (Algorithm 3, admissible blocks): row r = cluster row0 + r, terms
+// S_b x^_{s_b} for the admissible blocks b of that row (S_b stored [mu][nu]).
 template <class T>
 struct CouplingRows {
   const T *S;
@@ -198,25 +203,24 @@ struct CouplingRows {
   int k, kp, rp;
   int64_t row0;
   __device__ int kdim(int64_t) const { return k; }
-  __device__ int64_t first(int64_t r) const { return ptr[row0 + r]; }
-  __device__ int64_t count(int64_t r) const { return ptr[row0 + r + 1] - ptr[row0 + r]; }
-  __device__ Term<T> term(int64_t r, int64_t i) const {
-    const int64_t e = first(r) + i;
-    return Term<T>{S + e * (int64_t)k * kp, xhat + (int64_t)col[e] * k * rp, k};
+  __device__ int64_t first(int64_t r) const { return ptr[row0 + r] - ptr[row0]; }
+  __device__ Term<T> term(int64_t e) const {
+    const int64_t b = ptr[row0] + e;
+    return Term<T>{S + b * (int64_t)k * kp, xhat + (int64_t)col[b] * k * rp, k};
   }
 };
 
-// Leaf forward step (Algorithm 1 on the leaves): row j = leaf j, one term V_j^T x|j
-// (V_j stored [t][nu], padded to kp).
+// Leaf forward step (Algorithm 1 on the leaves): row j = leaf j, one term
+// V_j^T x|j (V_j stored [t][nu], padded to kp).
 template <class T>
 struct LeafForwardRows {
   const T *V;
   const T *xpad;
   int L, kp, rp;
   __device__ int kdim(int64_t) const { return L; }
-  __device__ int64_t count(int64_t) const { return 1; }
-  __device__ Term<T> term(int64_t r, int64_t) const {
-    return Term<T>{V + r * (int64_t)L * kp, xpad + r * (int64_t)L * rp, L};
+  __device__ int64_t first(int64_t r) const { return r; }
+  __device__ Term<T> term(int64_t e) const {
+    return Term<T>{V + e * (int64_t)L * kp, xpad + e * (int64_t)L * rp, L};
   }
 };
 
@@ -229,9 +233,9 @@ struct LeafBackwardRows {
   int k, Lp, rp;
   int64_t leaf0;
   __device__ int kdim(int64_t) const { return k; }
-  __device__ int64_t count(int64_t) const { return 1; }
-  __device__ Term<T> term(int64_t r, int64_t) const {
-    return Term<T>{Vt + r * (int64_t)k * Lp, yhat + (leaf0 + r) * (int64_t)k * rp, k};
+  __device__ int64_t first(int64_t r) const { return r; }
+  __device__ Term<T> term(int64_t e) const {
+    return Term<T>{Vt + e * (int64_t)k * Lp, yhat + (leaf0 + e) * (int64_t)k * rp, k};
   }
 };
 
@@ -245,125 +249,149 @@ struct NearRows {
   const T *xpad;
   int L, Lp, rp;
   __device__ int kdim(int64_t) const { return L; }
-  __device__ int64_t count(int64_t r) const { return ptr[r + 1] - ptr[r]; }
-  __device__ Term<T> term(int64_t r, int64_t i) const {
-    const int64_t e = ptr[r] + i;
+  __device__ int64_t first(int64_t r) const { return ptr[r]; }
+  __device__ Term<T> term(int64_t e) const {
     return Term<T>{near + e * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
   }
 };
 
-// Block-row product: output tile out_r (M x rp) = sum over the row's terms of
-// A_i X_i, one CTA per row.  A thread's register tile holds R groups of 4 rows
-// (rows g Mp/R + 4 vg + a, so that the lanes of a warp read contiguous
-// 16-byte pieces of one A row) times one 16-byte group of columns.  The A and X tiles stream through an nst-stage
-// shared-memory ring, each stage filled by one bulk-copy pair (TMA engine)
-// that completes on the stage's mbarrier; thread 0 refills a stage once every
-// thread is done with it.  Each thread keeps a 4 x (16 bytes) register tile
-// of the output for one slice of the contraction index; the slices are summed
-// in a fixed order at the end (no atomics: results are bit-reproducible).
-// Used for the coupling (rows = clusters), the leaf forward step, the leaf
-// backward step and the nearfield (rows = leaves); with accumulate the tile
-// is added to out instead of overwriting it.
+// Block-row product, persistent: output tile out_r (M x rp) = sum over the
+// terms of row r of A X.  Each CTA takes a contiguous range of rows holding
+// about 1/gridDim of all terms and streams their A and X tiles through an
+// nst-stage shared-memory ring, each stage filled by one bulk-copy pair (TMA
+// engine) that completes on the stage's mbarrier; thread 0 refills a stage
+// once every thread is done with it, so the ring runs on across row
+// boundaries.  A thread's register tile holds R groups of 4 rows (rows
+// g Mp/R + 4 vg + a, so that the lanes of a warp read contiguous 16-byte pieces
+// of one A row) times one 16-byte group of columns, for one slice of the
+// contraction index; at the end of a row the slices are summed in a fixed
+// order (no atomics: results are bit-reproducible).  With accumulate the row
+// is added to out instead of overwriting it.  Used for the coupling (rows =
+// clusters), the leaf forward and backward steps and the nearfield (rows =
+// leaves).
 template <class T, int R, class Rows>
-__global__ void __launch_bounds__(kThreads, 1) k_blockrow(Rows rows, RowCfg cfg, int accumulate, T *__restrict__ out) {
+__global__ void __launch_bounds__(kThreads, 1)
+    k_blockrow(Rows rows, RowCfg cfg, int64_t nrows, int accumulate, T *__restrict__ out) {
   using V = typename Vec16<T>::V;
   constexpr int VN = Vec16<T>::N;
   extern __shared__ __align__(128) unsigned char smem[];
+  T *red = reinterpret_cast<T *>(smem + (size_t)cfg.nst * cfg.stage_bytes);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + cfg.bar_off);
   const int tid = threadIdx.x;
-  const int64_t r = blockIdx.x;
-  const int64_t nb = rows.count(r);
   const int Mp = cfg.Mp, rp = cfg.rp;
+
+  // rows of this CTA: from the first row whose terms start at or after its share
+  const int64_t total = rows.first(nrows);
+  auto row_at = [&](int64_t w) -> int64_t {
+    if (w >= (int64_t)gridDim.x) return nrows;
+    const int64_t target = total * w / gridDim.x;
+    int64_t lo = 0, hi = nrows;  // smallest r with first(r) >= target
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (rows.first(mid) >= target) hi = mid;
+      else lo = mid + 1;
+    }
+    return lo;
+  };
+  const int64_t r_begin = blockIdx.x == 0 ? 0 : row_at(blockIdx.x);
+  const int64_t r_end = row_at(blockIdx.x + 1);
+  const int64_t e_begin = rows.first(r_begin), e_end = rows.first(r_end);
 
   if (tid == 0) {
     for (int s = 0; s < cfg.nst; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  int64_t issued = 0;
-  auto issue = [&](int64_t i) {
+  int64_t e_issue = e_begin;   // next term to load (thread 0)
+  auto issue = [&]() {
+    const int64_t i = e_issue - e_begin;
     const int s = (int)(i % cfg.nst);
     unsigned char *st = smem + (size_t)s * cfg.stage_bytes;
-    const Term<T> tm = rows.term(r, i);
+    const Term<T> tm = rows.term(e_issue);
     const uint32_t ab = (uint32_t)(sizeof(T) * tm.K * Mp), xb = (uint32_t)(sizeof(T) * tm.K * rp);
     mbar_expect_tx(&bar[s], ab + xb);
     bulk_g2s(st, tm.A, ab, &bar[s]);
     bulk_g2s(st + cfg.a_bytes, tm.X, xb, &bar[s]);
+    ++e_issue;
   };
   if (tid == 0)
-    for (; issued < nb && issued < cfg.nst; ++issued) issue(issued);
+    while (e_issue < e_end && e_issue - e_begin < cfg.nst) issue();
 
   const int tile = tid % cfg.tiles, ks = tid / cfg.tiles;
   const bool active = ks < cfg.ksplit;
   const int vg = tile % cfg.nvg, cg = tile / cfg.nvg;
   const int gstride = Mp / R;
-  T acc[4 * R][VN];
-#pragma unroll
-  for (int a = 0; a < 4 * R; ++a)
-#pragma unroll
-    for (int c = 0; c < VN; ++c) acc[a][c] = zero_of<T>();
-
-  for (int64_t i = 0; i < nb; ++i) {
-    const int s = (int)(i % cfg.nst);
-    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i / cfg.nst) & 1));
-    if (__syncthreads_or(!ok)) {
-      // a copy did not arrive in time: wait (bounded) for the copies still in flight, then leave
-      if (tid == 0)
-        for (int64_t j = i; j < issued; ++j) mbar_wait_bounded(&bar[j % cfg.nst], (uint32_t)((j / cfg.nst) & 1));
-      __syncthreads();
-      return;
-    }
-    const T *sA = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
-    const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
-    if (active) {
-      const int K = rows.kdim(i);
-      const int kc = (K + cfg.ksplit - 1) / cfg.ksplit;
-      const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
-#pragma unroll 2
-      for (int mu = mu0; mu < mu1; ++mu) {
-        T av[4 * R];
-#pragma unroll
-        for (int g = 0; g < R; ++g) {
-          const V *ap = reinterpret_cast<const V *>(sA + mu * Mp + g * gstride + 4 * vg);
-#pragma unroll
-          for (int q = 0; q < 4 / VN; ++q) {
-            const V v = ap[q];
-#pragma unroll
-            for (int l = 0; l < VN; ++l) av[4 * g + q * VN + l] = lane<T>(v, l);
-          }
-        }
-        const V xv = *reinterpret_cast<const V *>(sX + mu * rp + VN * cg);
-        T xs[VN];
-#pragma unroll
-        for (int l = 0; l < VN; ++l) xs[l] = lane<T>(xv, l);
-#pragma unroll
-        for (int a = 0; a < 4 * R; ++a)
-#pragma unroll
-          for (int c = 0; c < VN; ++c) acc[a][c] = madd(av[a], xs[c], acc[a][c]);
-      }
-    }
-    __syncthreads();
-    if (tid == 0 && issued < nb) {
-      issue(issued);
-      ++issued;
-    }
-  }
-  // sum the slices in a fixed order
-  T *red = reinterpret_cast<T *>(smem);
-  if (active) {
+  int64_t e = e_begin;
+  for (int64_t r = r_begin; r < r_end; ++r) {
+    T acc[4 * R][VN];
 #pragma unroll
     for (int a = 0; a < 4 * R; ++a)
 #pragma unroll
-      for (int c = 0; c < VN; ++c)
-        red[((int64_t)ks * Mp + (a / 4) * gstride + 4 * vg + (a % 4)) * rp + VN * cg + c] = acc[a][c];
-  }
-  __syncthreads();
-  T *o = out + r * (int64_t)cfg.M * rp;
-  for (int q = tid; q < cfg.M * rp; q += blockDim.x) {
-    const int nu = q / rp, c = q - nu * rp;
-    T sum = accumulate ? o[q] : zero_of<T>();
-    for (int z = 0; z < cfg.ksplit; ++z) sum = sum + red[((int64_t)z * Mp + nu) * rp + c];
-    o[q] = sum;
+      for (int c = 0; c < VN; ++c) acc[a][c] = zero_of<T>();
+    const int64_t e_row_end = rows.first(r + 1);
+    for (; e < e_row_end; ++e) {
+      const int64_t i = e - e_begin;
+      const int s = (int)(i % cfg.nst);
+      const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i / cfg.nst) & 1));
+      if (__syncthreads_or(!ok)) {
+        // a copy did not arrive in time: wait (bounded) for the copies still in flight, then leave
+        if (tid == 0)
+          for (int64_t j = e; j < e_issue; ++j) {
+            const int64_t ij = j - e_begin;
+            mbar_wait_bounded(&bar[ij % cfg.nst], (uint32_t)((ij / cfg.nst) & 1));
+          }
+        __syncthreads();
+        return;
+      }
+      const T *sA = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
+      const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
+      if (active) {
+        const int K = rows.kdim(e);
+        const int kc = (K + cfg.ksplit - 1) / cfg.ksplit;
+        const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
+#pragma unroll 2
+        for (int mu = mu0; mu < mu1; ++mu) {
+          T av[4 * R];
+#pragma unroll
+          for (int g = 0; g < R; ++g) {
+            const V *ap = reinterpret_cast<const V *>(sA + mu * Mp + g * gstride + 4 * vg);
+#pragma unroll
+            for (int q = 0; q < 4 / VN; ++q) {
+              const V v = ap[q];
+#pragma unroll
+              for (int l = 0; l < VN; ++l) av[4 * g + q * VN + l] = lane<T>(v, l);
+            }
+          }
+          const V xv = *reinterpret_cast<const V *>(sX + mu * rp + VN * cg);
+          T xs[VN];
+#pragma unroll
+          for (int l = 0; l < VN; ++l) xs[l] = lane<T>(xv, l);
+#pragma unroll
+          for (int a = 0; a < 4 * R; ++a)
+#pragma unroll
+            for (int c = 0; c < VN; ++c) acc[a][c] = madd(av[a], xs[c], acc[a][c]);
+        }
+      }
+      __syncthreads();
+      if (tid == 0 && e_issue < e_end) issue();
+    }
+    // end of row r: sum the slices in a fixed order
+    if (active) {
+#pragma unroll
+      for (int a = 0; a < 4 * R; ++a)
+#pragma unroll
+        for (int c = 0; c < VN; ++c)
+          red[((int64_t)ks * Mp + (a / 4) * gstride + 4 * vg + (a % 4)) * rp + VN * cg + c] = acc[a][c];
+    }
+    __syncthreads();
+    T *o = out + r * (int64_t)cfg.M * rp;
+    for (int q = tid; q < cfg.M * rp; q += blockDim.x) {
+      const int nu = q / rp, c = q - nu * rp;
+      T sum = accumulate ? o[q] : zero_of<T>();
+      for (int z = 0; z < cfg.ksplit; ++z) sum = sum + red[((int64_t)z * Mp + nu) * rp + c];
+      o[q] = sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -384,17 +412,14 @@ int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, RowCfg &cfg) {
   cfg.ksplit = std::max(1, std::min(threads / cfg.tiles, Kmax));
   cfg.a_bytes = (uint32_t)(sizeof(T) * Kmax * Mp);
   cfg.stage_bytes = cfg.a_bytes + (uint32_t)(sizeof(T) * Kmax * rp);
-  size_t red = sizeof(T) * (size_t)cfg.ksplit * Mp * rp;
+  const size_t red = sizeof(T) * (size_t)cfg.ksplit * Mp * rp;   // slice sums, after the ring
   // stages: up to 6, sized so that 512 threads per SM stay resident when possible
-  const size_t budget = kSmemMax / (512 / threads) - 64;
-  int nst = (int)std::min<size_t>(6, budget / cfg.stage_bytes);
-  if (nst < 2) {
-    nst = 6;
-    while (nst > 1 && std::max((size_t)nst * cfg.stage_bytes, red) + 64 > kSmemMax) --nst;
-  }
-  while (nst > 1 && std::max((size_t)nst * cfg.stage_bytes, red) + 64 > kSmemMax) --nst;
+  const size_t budget = kSmemMax / (512 / threads);
+  int nst = 6;
+  while (nst > 2 && (size_t)nst * cfg.stage_bytes + red + 64 > budget) --nst;
+  while (nst > 1 && (size_t)nst * cfg.stage_bytes + red + 64 > kSmemMax) --nst;
   cfg.nst = nst;
-  size_t body = std::max((size_t)nst * cfg.stage_bytes, red);
+  const size_t body = (size_t)nst * cfg.stage_bytes + red;
   cfg.bar_off = (uint32_t)((body + 15) / 16 * 16);
   if (cfg.bar_off + 8 * nst > kSmemMax) return fail(H2_EINVAL, "block-row tile does not fit in shared memory");
   return H2_OK;
@@ -448,20 +473,30 @@ struct Marks {
   }
 };
 
+// persistent launch: as many CTAs as stay resident, at most one per row
+template <class T, int R, class Rows>
+int launch_rows_r(const Rows &rows, const RowCfg &cfg, int threads, int64_t nrows, int accumulate, T *out,
+                  cudaStream_t st) {
+  const void *fn = (const void *)k_blockrow<T, R, Rows>;
+  const size_t sm = cfg.bar_off + 8 * cfg.nst;
+  int rc;
+  if ((rc = set_smem<T>(fn, sm))) return rc;
+  int per_sm = 0, dev = 0, sms = 0;
+  H2_CUDA_TRY(cudaGetDevice(&dev));
+  H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  H2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm));
+  if (per_sm < 1) return fail(H2_EINVAL, "block-row kernel cannot be resident");
+  const int64_t grid = std::min<int64_t>(nrows, (int64_t)per_sm * sms);
+  k_blockrow<T, R, Rows><<<(unsigned)grid, threads, sm, st>>>(rows, cfg, nrows, accumulate, out);
+  return H2_OK;
+}
+
 template <class T, class Rows>
 int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int R, int64_t nrows, int accumulate, T *out,
                 cudaStream_t st) {
   if (nrows <= 0) return H2_OK;
-  size_t sm = cfg.bar_off + 8 * cfg.nst;
-  int rc;
-  if (R == 2) {
-    if ((rc = set_smem<T>((const void *)k_blockrow<T, 2, Rows>, sm))) return rc;
-    k_blockrow<T, 2, Rows><<<(unsigned)nrows, threads, sm, st>>>(rows, cfg, accumulate, out);
-  } else {
-    if ((rc = set_smem<T>((const void *)k_blockrow<T, 1, Rows>, sm))) return rc;
-    k_blockrow<T, 1, Rows><<<(unsigned)nrows, threads, sm, st>>>(rows, cfg, accumulate, out);
-  }
-  return H2_OK;
+  if (R == 2) return launch_rows_r<T, 2>(rows, cfg, threads, nrows, accumulate, out, st);
+  return launch_rows_r<T, 1>(rows, cfg, threads, nrows, accumulate, out, st);
 }
 
 template <class T, class Tio>

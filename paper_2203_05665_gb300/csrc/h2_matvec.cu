@@ -255,29 +255,34 @@ struct NearRows {
   }
 };
 
-// Block-row product, persistent: output tile out_r (M x rp) = sum over the
-// terms of row r of A X.  Each CTA takes a contiguous range of rows holding
-// about 1/gridDim of all terms and streams their A and X tiles through an
-// nst-stage shared-memory ring, each stage filled by one bulk-copy pair (TMA
-// engine) that completes on the stage's mbarrier; thread 0 refills a stage
-// once every thread is done with it, so the ring runs on across row
-// boundaries.  A thread's register tile holds R groups of 4 rows (rows
-// g Mp/R + 4 vg + a, so that the lanes of a warp read contiguous 16-byte pieces
-// of one A row) times one 16-byte group of columns, for one slice of the
-// contraction index; at the end of a row the slices are summed in a fixed
-// order (no atomics: results are bit-reproducible).  With accumulate the row
-// is added to out instead of overwriting it.  Used for the coupling (rows =
-// clusters), the leaf forward and backward steps and the nearfield (rows =
-// leaves).
+// Block-row product, persistent and warp-specialised: output tile out_r
+// (M x rp) = sum over the terms of row r of A X.  Each CTA takes a contiguous
+// range of rows holding about 1/gridDim of all terms.  The last warp is the
+// producer: one lane streams the A and X tiles of the CTA's terms through an
+// nst-stage shared-memory ring with bulk copies (TMA engine), each stage
+// completing on its "full" mbarrier, and refills a stage once every consumer
+// warp has released it on its "empty" mbarrier.  The other warps consume:
+// a thread's register tile holds R groups of 4 rows (rows g Mp/R + 4 vg + a,
+// so that the lanes of a warp read contiguous 16-byte pieces of one A row)
+// times one 16-byte group of columns, for one slice of the contraction
+// index; at the end of a row the slices are summed in a fixed order (no
+// atomics: results are bit-reproducible).  With accumulate the row is added
+// to out instead of overwriting it.  Every wait is bounded; a timeout raises
+// the device error word and all warps leave after the copies in flight have
+// landed.  Used for the coupling (rows = clusters), the leaf forward and
+// backward steps and the nearfield (rows = leaves).
 template <class T, int R, class Rows>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads + 32, 1)
     k_blockrow(Rows rows, RowCfg cfg, int64_t nrows, int accumulate, T *__restrict__ out) {
   using V = typename Vec16<T>::V;
   constexpr int VN = Vec16<T>::N;
   extern __shared__ __align__(128) unsigned char smem[];
   T *red = reinterpret_cast<T *>(smem + (size_t)cfg.nst * cfg.stage_bytes);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + cfg.bar_off);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + cfg.bar_off);
+  uint64_t *empty = full + cfg.nst;
+  volatile int *abort = reinterpret_cast<volatile int *>(empty + cfg.nst);
   const int tid = threadIdx.x;
+  const int ncons = blockDim.x - 32, nwc = ncons / 32;
   const int Mp = cfg.Mp, rp = cfg.rp;
 
   // rows of this CTA: from the first row whose terms start at or after its share
@@ -298,29 +303,48 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t e_begin = rows.first(r_begin), e_end = rows.first(r_end);
 
   if (tid == 0) {
-    for (int s = 0; s < cfg.nst; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < cfg.nst; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], nwc);
+    }
+    *abort = 0;
     mbar_fence_init();
   }
   __syncthreads();
-  int64_t e_issue = e_begin;   // next term to load (thread 0)
-  auto issue = [&]() {
-    const int64_t i = e_issue - e_begin;
-    const int s = (int)(i % cfg.nst);
-    unsigned char *st = smem + (size_t)s * cfg.stage_bytes;
-    const Term<T> tm = rows.term(e_issue);
-    const uint32_t ab = (uint32_t)(sizeof(T) * tm.K * Mp), xb = (uint32_t)(sizeof(T) * tm.K * rp);
-    mbar_expect_tx(&bar[s], ab + xb);
-    bulk_g2s(st, tm.A, ab, &bar[s]);
-    bulk_g2s(st + cfg.a_bytes, tm.X, xb, &bar[s]);
-    ++e_issue;
-  };
-  if (tid == 0)
-    while (e_issue < e_end && e_issue - e_begin < cfg.nst) issue();
 
+  if (tid >= ncons) {
+    // ---------------- producer warp ----------------
+    if (tid == ncons) {
+      int64_t e = e_begin;
+      for (; e < e_end; ++e) {
+        const int64_t i = e - e_begin;
+        const int s = (int)(i % cfg.nst);
+        if (i >= cfg.nst && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / cfg.nst - 1) & 1), abort)) break;
+        unsigned char *st = smem + (size_t)s * cfg.stage_bytes;
+        const Term<T> tm = rows.term(e);
+        const uint32_t ab = (uint32_t)(sizeof(T) * tm.K * Mp), xb = (uint32_t)(sizeof(T) * tm.K * rp);
+        mbar_expect_tx(&full[s], ab + xb);
+        bulk_g2s(st, tm.A, ab, &full[s]);
+        bulk_g2s(st + cfg.a_bytes, tm.X, xb, &full[s]);
+      }
+      if (*abort) {
+        // let the copies in flight land before the CTA leaves (bounded)
+        const int64_t j0 = e - cfg.nst > e_begin ? e - cfg.nst : e_begin;
+        for (int64_t j = j0; j < e; ++j) {
+          const int64_t ij = j - e_begin;
+          mbar_wait_bounded(&full[ij % cfg.nst], (uint32_t)((ij / cfg.nst) & 1));
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumer warps ----------------
   const int tile = tid % cfg.tiles, ks = tid / cfg.tiles;
   const bool active = ks < cfg.ksplit;
   const int vg = tile % cfg.nvg, cg = tile / cfg.nvg;
   const int gstride = Mp / R;
+  const int lane_id = tid & 31;
   int64_t e = e_begin;
   for (int64_t r = r_begin; r < r_end; ++r) {
     T acc[4 * R][VN];
@@ -332,20 +356,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (; e < e_row_end; ++e) {
       const int64_t i = e - e_begin;
       const int s = (int)(i % cfg.nst);
-      const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i / cfg.nst) & 1));
-      if (__syncthreads_or(!ok)) {
-        // a copy did not arrive in time: wait (bounded) for the copies still in flight, then leave
-        if (tid == 0)
-          for (int64_t j = e; j < e_issue; ++j) {
-            const int64_t ij = j - e_begin;
-            mbar_wait_bounded(&bar[ij % cfg.nst], (uint32_t)((ij / cfg.nst) & 1));
-          }
-        __syncthreads();
-        return;
-      }
-      const T *sA = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
-      const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
-      if (active) {
+      // every consumer thread waits (also idle ones), so that no warp releases a
+      // stage it has not seen filled
+      const bool ready = !*abort && mbar_wait_or_abort(&full[s], (uint32_t)((i / cfg.nst) & 1), abort);
+      if (ready && active) {
+        const T *sA = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
+        const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
         const int K = rows.kdim(e);
         const int kc = (K + cfg.ksplit - 1) / cfg.ksplit;
         const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
@@ -372,10 +388,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = 0; c < VN; ++c) acc[a][c] = madd(av[a], xs[c], acc[a][c]);
         }
       }
-      __syncthreads();
-      if (tid == 0 && e_issue < e_end) issue();
+      __syncwarp();
+      if (lane_id == 0) mbar_arrive(&empty[s]);
     }
-    // end of row r: sum the slices in a fixed order
+    // end of row r: agree on abort, then sum the slices in a fixed order
+    if (named_sync_or(ncons, *abort)) return;
     if (active) {
 #pragma unroll
       for (int a = 0; a < 4 * R; ++a)
@@ -383,15 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < VN; ++c)
           red[((int64_t)ks * Mp + (a / 4) * gstride + 4 * vg + (a % 4)) * rp + VN * cg + c] = acc[a][c];
     }
-    __syncthreads();
+    named_sync(ncons);
     T *o = out + r * (int64_t)cfg.M * rp;
-    for (int q = tid; q < cfg.M * rp; q += blockDim.x) {
+    for (int q = tid; q < cfg.M * rp; q += ncons) {
       const int nu = q / rp, c = q - nu * rp;
       T sum = accumulate ? o[q] : zero_of<T>();
       for (int z = 0; z < cfg.ksplit; ++z) sum = sum + red[((int64_t)z * Mp + nu) * rp + c];
       o[q] = sum;
     }
-    __syncthreads();
+    named_sync(ncons);
   }
 }
 
@@ -413,15 +430,15 @@ int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, RowCfg &cfg) {
   cfg.a_bytes = (uint32_t)(sizeof(T) * Kmax * Mp);
   cfg.stage_bytes = cfg.a_bytes + (uint32_t)(sizeof(T) * Kmax * rp);
   const size_t red = sizeof(T) * (size_t)cfg.ksplit * Mp * rp;   // slice sums, after the ring
-  // stages: up to 6, sized so that 512 threads per SM stay resident when possible
+  // stages: up to 8, sized so that 512 consumer threads per SM stay resident when possible
   const size_t budget = kSmemMax / (512 / threads);
-  int nst = 6;
-  while (nst > 2 && (size_t)nst * cfg.stage_bytes + red + 64 > budget) --nst;
-  while (nst > 1 && (size_t)nst * cfg.stage_bytes + red + 64 > kSmemMax) --nst;
+  int nst = 8;
+  while (nst > 2 && (size_t)nst * cfg.stage_bytes + red + 128 > budget) --nst;
+  while (nst > 1 && (size_t)nst * cfg.stage_bytes + red + 128 > kSmemMax) --nst;
   cfg.nst = nst;
   const size_t body = (size_t)nst * cfg.stage_bytes + red;
   cfg.bar_off = (uint32_t)((body + 15) / 16 * 16);
-  if (cfg.bar_off + 8 * nst > kSmemMax) return fail(H2_EINVAL, "block-row tile does not fit in shared memory");
+  if (cfg.bar_off + 16 * nst + 16 > kSmemMax) return fail(H2_EINVAL, "block-row tile does not fit in shared memory");
   return H2_OK;
 }
 
@@ -478,7 +495,8 @@ template <class T, int R, class Rows>
 int launch_rows_r(const Rows &rows, const RowCfg &cfg, int threads, int64_t nrows, int accumulate, T *out,
                   cudaStream_t st) {
   const void *fn = (const void *)k_blockrow<T, R, Rows>;
-  const size_t sm = cfg.bar_off + 8 * cfg.nst;
+  const size_t sm = cfg.bar_off + 16 * cfg.nst + 16;
+  threads += 32;   // the producer warp
   int rc;
   if ((rc = set_smem<T>(fn, sm))) return rc;
   int per_sm = 0, dev = 0, sms = 0;

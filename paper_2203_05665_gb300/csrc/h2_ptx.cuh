@@ -43,10 +43,46 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Wait for the phase of the given parity with an iteration limit; returns
 // false (and raises the device error word) if the limit runs out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 26); ++it)
+  for (uint32_t it = 0; it < (1u << 22); ++it)
     if (mbar_try_wait(bar, parity)) return true;
   atomicExch(&g_h2_device_error, 1);
   return false;
+}
+
+// The same, also giving up as soon as *abort (shared memory) is set by
+// another thread; a timeout sets *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  atomicExch(&g_h2_device_error, 1);
+  *abort = 1;
+  return false;
+}
+
+// plain arrival (no transaction bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// named barrier 1 over the first nthreads threads of the CTA
+__device__ __forceinline__ void named_sync(uint32_t nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// named barrier 1 with an OR reduction of flag over the first nthreads threads
+__device__ __forceinline__ bool named_sync_or(uint32_t nthreads, int flag) {
+  uint32_t res;
+  asm volatile(
+      "{\n\t.reg .pred q, p;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(res)
+      : "r"(flag), "r"(nthreads)
+      : "memory");
+  return res != 0;
 }
 
 // bytes must be a multiple of 16; both addresses 16-byte aligned

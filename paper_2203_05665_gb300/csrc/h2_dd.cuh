@@ -70,6 +70,30 @@ __device__ __forceinline__ dd madd(dd a, dd b, dd c) {
   return quick_norm(s, t);
 }
 
+// Accumulation inside one block of a contraction: acc += a b without the
+// final renormalisation (12 FP32 instructions for dd; the low word collects
+// the exact rounding errors of the high sums and the product errors); call
+// acc_norm once the block is done.
+__device__ __forceinline__ void acc_fma(float &acc, float a, float b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void acc_fma(double &acc, double a, double b) { acc = ::fma(a, b, acc); }
+__device__ __forceinline__ void acc_fma(dd &acc, dd a, dd b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float s, t;
+  two_sum(acc.hi, p, s, t);
+  acc.hi = s;
+  acc.lo += t + e;
+}
+__device__ __forceinline__ void acc_norm(float &) {}
+__device__ __forceinline__ void acc_norm(double &) {}
+__device__ __forceinline__ void acc_norm(dd &a) {
+  float s, e;
+  two_sum(a.hi, a.lo, s, e);
+  a = dd{s, e};
+}
+
 // conversions used by the templated kernels
 template <class T>
 __host__ __device__ __forceinline__ T from_double(double v) {

@@ -272,7 +272,7 @@ struct NearRows {
 // landed.  Used for the coupling (rows = clusters), the leaf forward and
 // backward steps and the nearfield (rows = leaves).
 template <class T, int R, class Rows>
-__global__ void __launch_bounds__(kThreads + 32, 1)
+__global__ void __launch_bounds__(kThreads + 32, 2)
     k_blockrow(Rows rows, RowCfg cfg, int64_t nrows, int accumulate, T *__restrict__ out) {
   using V = typename Vec16<T>::V;
   constexpr int VN = Vec16<T>::N;
@@ -385,8 +385,12 @@ __global__ void __launch_bounds__(kThreads + 32, 1)
 #pragma unroll
           for (int a = 0; a < 4 * R; ++a)
 #pragma unroll
-            for (int c = 0; c < VN; ++c) acc[a][c] = madd(av[a], xs[c], acc[a][c]);
+            for (int c = 0; c < VN; ++c) acc_fma(acc[a][c], av[a], xs[c]);
         }
+#pragma unroll
+        for (int a = 0; a < 4 * R; ++a)
+#pragma unroll
+          for (int c = 0; c < VN; ++c) acc_norm(acc[a][c]);
       }
       __syncwarp();
       if (lane_id == 0) mbar_arrive(&empty[s]);

@@ -161,6 +161,19 @@ int h2_coefficients(h2_handle h, int which, double *out);
 int h2_solve(h2_handle h, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
              h2_solve_info *info);
 
+/* Mixed-precision iterative refinement around GMRES (GMRES-IR): the outer
+ * residual r = b - G~ z is formed with handle hi (e.g. H2_F64), the
+ * correction solves G~ d = r by GMRES(restart) with handle lo (e.g. H2_F32)
+ * to the relative tolerance inner_rtol, z += d, until |r| <= rtol |b| per
+ * column or maxit_outer refinement steps.  The paper names Krylov solvers for
+ * Gz = b (Section 1) without fixing one; the refinement scheme is Carson and
+ * Higham's GMRES-IR.  hi and lo must be built from the same mesh and tree
+ * parameters on one device; b, z as for h2_solve.  info[c].iters counts the
+ * inner GMRES iterations over all refinement steps, info[c].relres is the
+ * residual with hi.  Returns H2_OK or H2_ENOCONV (best iterate written). */
+int h2_solve_ir(h2_handle hi, h2_handle lo, const double *b, double *z, int nrhs, double rtol, double inner_rtol,
+                int restart, int maxit_inner, int maxit_outer, h2_solve_info *info);
+
 /* Phases of the product, in launch order (h2_phase_times). */
 enum h2_phase {
   H2_PH_PERMUTE_IN = 0,  /* caller order -> leaf-padded cluster order */

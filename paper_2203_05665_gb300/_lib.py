@@ -44,7 +44,8 @@ class SolveInfo(C.Structure):
 
 EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_counts", "h2_plan_tree",
             "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec",
-            "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_profile", "h2_phase_times", "h2_last_error"]
+            "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
+            "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -79,6 +80,8 @@ def load():
             "h2_matvec_host": (C.c_int, [vp, dp, dp, C.c_int]),
             "h2_coefficients": (C.c_int, [vp, C.c_int, dp]),
             "h2_solve": (C.c_int, [vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(SolveInfo)]),
+            "h2_solve_ir": (C.c_int, [vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                                      C.POINTER(SolveInfo)]),
             "h2_profile": (C.c_int, [vp, C.c_int]),
             "h2_phase_times": (C.c_int, [vp, dp, i64p, i64p]),
             "h2_last_error": (C.c_char_p, []),
@@ -261,3 +264,16 @@ class H2Matrix:
         it = np.array([i.iters for i in info])
         rel = np.array([i.relres for i in info])
         return z, it, rel, st
+
+    def solve_ir(self, lo, b, rtol=1e-8, inner_rtol=1e-4, restart=30, maxit_inner=1000, maxit_outer=50):
+        """GMRES-IR: residuals with this handle, inner GMRES with handle lo (numpy b, host)."""
+        nrhs = b.shape[1] if b.ndim == 2 else 1
+        info = (SolveInfo * nrhs)()
+        bb = np.asfortranarray(np.asarray(b, dtype=np.float64).reshape(self.n, -1))
+        z = np.zeros_like(bb, order="F")
+        st = self._lib.h2_solve_ir(self._h, lo._h, bb.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p),
+                                   nrhs, float(rtol), float(inner_rtol), int(restart), int(maxit_inner),
+                                   int(maxit_outer), info)
+        if st not in (H2_OK, H2_ENOCONV):
+            _check(st)
+        return z, np.array([i.iters for i in info]), np.array([i.relres for i in info]), st

@@ -176,6 +176,7 @@ int h2_destroy(h2_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   drop_events(h->prof);
+  free_gmres_work(h->gw);
   free_dev(h->d);
   delete h;
   return H2_OK;
@@ -307,6 +308,47 @@ int h2_solve(h2_handle h, const double *b, double *z, int nrhs, double rtol, int
   if (!rc || rc == H2_ENOCONV) {
     e = cudaMemcpyAsync(z, dz_, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy z");
+  }
+  cudaFree(db_);
+  cudaFree(dz_);
+  return rc;
+}
+
+int h2_solve_ir(h2_handle hi, h2_handle lo, const double *b, double *z, int nrhs, double rtol, double inner_rtol,
+                int restart, int maxit_inner, int maxit_outer, h2_solve_info *info) {
+  if (!hi || !lo || !b || !z) return fail(H2_EINVAL, "NULL argument");
+  if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");
+  if (restart < 1 || restart > 200 || maxit_inner < 1 || maxit_outer < 1 || !(rtol > 0.0) || !(inner_rtol > 0.0) ||
+      !(inner_rtol < 1.0))
+    return fail(H2_EINVAL, "bad solver parameters");
+  if (hi->device != lo->device) return fail(H2_EINVAL, "both handles must live on one device");
+  if (hi->plan.n != lo->plan.n || hi->plan.nclu != lo->plan.nclu || hi->plan.adm_col.size() != lo->plan.adm_col.size() ||
+      hi->plan.near_col.size() != lo->plan.near_col.size())
+    return fail(H2_EINVAL, "the two handles must represent the same matrix structure");
+  H2_CUDA_TRY(cudaSetDevice(hi->device));
+  cudaPointerAttributes ab{}, az{};
+  H2_CUDA_TRY(cudaPointerGetAttributes(&ab, b));
+  H2_CUDA_TRY(cudaPointerGetAttributes(&az, z));
+  bool db = ab.type == cudaMemoryTypeDevice || ab.type == cudaMemoryTypeManaged;
+  bool dz = az.type == cudaMemoryTypeDevice || az.type == cudaMemoryTypeManaged;
+  if (db != dz) return fail(H2_EINVAL, "b and z must both be host or both be device arrays");
+  if (db) return run_gmres_ir(*hi, *lo, b, z, nrhs, rtol, inner_rtol, restart, maxit_inner, maxit_outer, info);
+  size_t bytes = (size_t)hi->d.n * nrhs * 8;
+  double *db_ = nullptr, *dz_ = nullptr;
+  if (cudaMalloc(&db_, bytes) != cudaSuccess || cudaMalloc(&dz_, bytes) != cudaSuccess) {
+    cudaFree(db_);
+    cudaGetLastError();
+    return fail(H2_ENOMEM, "solve staging buffers");
+  }
+  int rc = H2_OK;
+  cudaError_t e = cudaMemcpyAsync(db_, b, bytes, cudaMemcpyHostToDevice, hi->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(hi->stream);
+  if (e != cudaSuccess) rc = cuda_fail(e, "copy b");
+  if (!rc) rc = run_gmres_ir(*hi, *lo, db_, dz_, nrhs, rtol, inner_rtol, restart, maxit_inner, maxit_outer, info);
+  if (!rc || rc == H2_ENOCONV) {
+    e = cudaMemcpyAsync(z, dz_, bytes, cudaMemcpyDeviceToHost, hi->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(hi->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "copy z");
   }
   cudaFree(db_);

@@ -89,7 +89,18 @@ struct Prof {
   double ms[H2_NPHASE] = {0};
 };
 
+// GMRES work space kept on the handle (grown on demand, freed with it)
+struct GmresWork {
+  int cols = 0, restart = 0;
+  double *Vb = nullptr, *W = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *hn = nullptr, *resid = nullptr, *yv = nullptr, *bn = nullptr;
+  double *r = nullptr, *d = nullptr, *Az = nullptr;   // refinement vectors
+  int *active = nullptr, *jc = nullptr;
+};
+void free_gmres_work(GmresWork &w);
+
 struct Ctx {
+  GmresWork gw;
   Prof prof;
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -119,5 +130,8 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64);
 // GMRES (h2_solve.cu); b, z device FP64 arrays
 int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
               h2_solve_info *info);
+// GMRES-IR: outer residuals with hi, inner GMRES with lo (same mesh and tree)
+int run_gmres_ir(Ctx &hi, Ctx &lo, const double *b, double *z, int nrhs, double rtol, double inner_rtol,
+                 int restart, int maxit_inner, int maxit_outer, h2_solve_info *info);
 
 }  // namespace h2

@@ -133,30 +133,50 @@ int grid1(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
-struct DBuf {
-  double *p = nullptr;
-  ~DBuf() { if (p) cudaFree(p); }
-  int alloc(size_t n) {
-    if (cudaMalloc(&p, std::max<size_t>(n, 1) * 8) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(H2_ENOMEM, "GMRES work space");
-    }
-    return H2_OK;
-  }
-};
-struct IBuf {
-  int *p = nullptr;
-  ~IBuf() { if (p) cudaFree(p); }
-  int alloc(size_t n) {
-    if (cudaMalloc(&p, std::max<size_t>(n, 1) * 4) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(H2_ENOMEM, "GMRES work space");
-    }
-    return H2_OK;
-  }
-};
-
 }  // namespace
+
+void free_gmres_work(GmresWork &w) {
+  double *dp[] = {w.Vb, w.W, w.H, w.cs, w.sn, w.g, w.h1, w.h2, w.hn, w.resid, w.yv, w.bn, w.r, w.d, w.Az};
+  for (double *p : dp)
+    if (p) cudaFree(p);
+  if (w.active) cudaFree(w.active);
+  if (w.jc) cudaFree(w.jc);
+  w = GmresWork();
+}
+
+static int ensure_gmres_work(Ctx &c, int nrhs, int restart) {
+  GmresWork &w = c.gw;
+  if (nrhs <= w.cols && restart <= w.restart) return H2_OK;
+  const int cols = std::max(nrhs, w.cols), mr = std::max(restart, w.restart);
+  free_gmres_work(w);
+  const size_t n = (size_t)c.d.n, tot = n * cols;
+  bool ok = true;
+  auto al = [&](double **p, size_t cnt) { ok = ok && cudaMalloc(p, std::max<size_t>(cnt, 1) * 8) == cudaSuccess; };
+  al(&w.Vb, (size_t)(mr + 1) * tot);
+  al(&w.W, tot);
+  al(&w.H, (size_t)(mr + 1) * mr * cols);
+  al(&w.cs, (size_t)mr * cols);
+  al(&w.sn, (size_t)mr * cols);
+  al(&w.g, (size_t)(mr + 1) * cols);
+  al(&w.h1, (size_t)(mr + 1) * cols);
+  al(&w.h2, (size_t)(mr + 1) * cols);
+  al(&w.hn, cols);
+  al(&w.resid, cols);
+  al(&w.yv, (size_t)mr * cols);
+  al(&w.bn, cols);
+  al(&w.r, tot);
+  al(&w.d, tot);
+  al(&w.Az, tot);
+  ok = ok && cudaMalloc(&w.active, cols * 4) == cudaSuccess && cudaMalloc(&w.jc, cols * 4) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_gmres_work(w);
+    return fail(H2_ENOMEM, "GMRES work space");
+  }
+  w.cols = cols;
+  w.restart = mr;
+  return H2_OK;
+}
 
 int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
               h2_solve_info *info) {
@@ -164,14 +184,16 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
   const int mr = restart;
   cudaStream_t st = c.stream;
   int rc;
-  DBuf Vb, W, H, cs, sn, g, h1, h2b, hn, resid, yv, bn;
-  IBuf active, jc;
-  if ((rc = Vb.alloc((size_t)(mr + 1) * tot)) || (rc = W.alloc(tot)) || (rc = H.alloc((size_t)(mr + 1) * mr * nrhs)) ||
-      (rc = cs.alloc(mr * nrhs)) || (rc = sn.alloc(mr * nrhs)) || (rc = g.alloc((mr + 1) * nrhs)) ||
-      (rc = h1.alloc((mr + 1) * nrhs)) || (rc = h2b.alloc((mr + 1) * nrhs)) || (rc = hn.alloc(nrhs)) ||
-      (rc = resid.alloc(nrhs)) || (rc = yv.alloc(mr * nrhs)) || (rc = bn.alloc(nrhs)) ||
-      (rc = active.alloc(nrhs)) || (rc = jc.alloc(nrhs)))
-    return rc;
+  if ((rc = ensure_gmres_work(c, nrhs, restart))) return rc;
+  struct P {
+    double *p;
+  };
+  GmresWork &w = c.gw;
+  P Vb{w.Vb}, W{w.W}, H{w.H}, cs{w.cs}, sn{w.sn}, g{w.g}, h1{w.h1}, h2b{w.h2}, hn{w.hn}, resid{w.resid}, yv{w.yv},
+      bn{w.bn};
+  struct I {
+    int *p;
+  } active{w.active}, jc{w.jc};
 
   std::vector<double> h_bn(nrhs), h_rn(nrhs), h_res(nrhs), h_g0((mr + 1) * nrhs, 0.0);
   std::vector<int> h_active(nrhs, 1), h_jc(nrhs, 0), h_iters(nrhs, 0), h_done(nrhs, 0);
@@ -260,7 +282,83 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
     }
   }
   if (status != H2_OK) fail(H2_ENOCONV, "GMRES reached maxit before the residual target");
-  return status;
+  int derr = take_device_error(c);
+  return derr ? derr : status;
+}
+
+__global__ void k_axpy_cols(const double *__restrict__ d, int64_t total, double *__restrict__ z) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    z[e] += d[e];
+}
+
+__global__ void k_mask_cols(const int *__restrict__ keep, int64_t n, int64_t total, double *__restrict__ v) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    if (!keep[e / n]) v[e] = 0.0;
+}
+
+// Mixed-precision iterative refinement around GMRES (GMRES-IR, Carson and
+// Higham 2018): z = 0; repeat r = b - G~_hi z (hi arithmetic), solve
+// G~_lo d = r by GMRES(restart) to inner_rtol, z += d; until |r| <= rtol |b|
+// per column.  The Krylov arithmetic is FP64 throughout.
+int run_gmres_ir(Ctx &hi, Ctx &lo, const double *b, double *z, int nrhs, double rtol, double inner_rtol,
+                 int restart, int maxit_inner, int maxit_outer, h2_solve_info *info) {
+  const int64_t n = hi.d.n, tot = n * nrhs;
+  cudaStream_t st = hi.stream;
+  int rc;
+  if ((rc = ensure_gmres_work(hi, nrhs, 1))) return rc;
+  double *r = hi.gw.r, *d = hi.gw.d, *Az = hi.gw.Az, *nrm = hi.gw.hn;
+  int *keep = hi.gw.active;
+  std::vector<double> h_bn(nrhs), h_rn(nrhs), h_res(nrhs, 1.0);
+  std::vector<int> h_keep(nrhs, 1), h_iters(nrhs, 0), h_outer(nrhs, 0);
+  std::vector<h2_solve_info> inner(nrhs);
+  k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(b, b, n, nrhs, nrm);
+  k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(nrm, nrhs);
+  H2_CUDA_TRY(cudaMemcpyAsync(h_bn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, st));
+  H2_CUDA_TRY(cudaMemsetAsync(z, 0, tot * 8, st));
+  H2_CUDA_TRY(cudaMemcpyAsync(r, b, tot * 8, cudaMemcpyDeviceToDevice, st));
+  H2_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int outer = 0;; ++outer) {
+    // residual norms and convergence per column
+    k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(r, r, n, nrhs, nrm);
+    k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(nrm, nrhs);
+    H2_CUDA_TRY(cudaMemcpyAsync(h_rn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, st));
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int col = 0; col < nrhs; ++col) {
+      h_res[col] = h_bn[col] > 0 ? h_rn[col] / h_bn[col] : 0.0;
+      h_keep[col] = h_res[col] > rtol && outer < maxit_outer;
+      any = any || h_keep[col];
+    }
+    if (!any) break;
+    H2_CUDA_TRY(cudaMemcpyAsync(keep, h_keep.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
+    k_mask_cols<<<grid1(tot), kT, 0, st>>>(keep, n, tot, r);
+    // inner solve in the low precision (its own stream is the lo handle's)
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    rc = run_gmres(lo, r, d, nrhs, inner_rtol, restart, maxit_inner, inner.data());
+    if (rc != H2_OK && rc != H2_ENOCONV) return rc;
+    H2_CUDA_TRY(cudaStreamSynchronize(lo.stream));
+    for (int col = 0; col < nrhs; ++col)
+      if (h_keep[col]) {
+        h_iters[col] += inner[col].iters;
+        h_outer[col]++;
+      }
+    k_axpy_cols<<<grid1(tot), kT, 0, st>>>(d, tot, z);
+    if ((rc = run_matvec(hi, z, Az, nrhs, true))) return rc;
+    k_residual<<<grid1(tot), kT, 0, st>>>(b, Az, tot, r);
+  }
+  int status = H2_OK;
+  for (int col = 0; col < nrhs; ++col) {
+    bool ok = h_res[col] <= rtol;
+    if (!ok) status = H2_ENOCONV;
+    if (info) {
+      info[col].iters = h_iters[col];
+      info[col].relres = h_res[col];
+      info[col].status = ok ? H2_OK : H2_ENOCONV;
+    }
+  }
+  if (status != H2_OK) fail(H2_ENOCONV, "refinement reached its step limit before the residual target");
+  int derr = take_device_error(hi);
+  return derr ? derr : status;
 }
 
 }  // namespace h2

@@ -177,3 +177,20 @@ def _full_oracle():
         v, f = I.icosphere(7)
         _full["o"] = oracle.Oracle(v, f, leaf_size=32, eta=2.0, order=4, store_near=False)
     return _full["o"]
+
+
+def test_gmres_ir_reaches_1e8(require_gpu):
+    """Mixed precision: FP32 inner GMRES(30), FP64-accurate residuals."""
+    v, f, o = _oracle("ico4_m3")
+    hi = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec="f64")
+    lo = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec="f32")
+    b = np.concatenate([I.uniform_rhs(f.shape[0], 2, 1003), _areas(v, f)[:, None]], axis=1)
+    z, it, rel, st = hi.solve_ir(lo, b, rtol=1e-8, inner_rtol=1e-4, restart=30)
+    assert st == 0 and np.all(rel <= 1e-8) and np.all(it > 0)
+    r = b - o.matvec(z)
+    assert np.all(np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0) <= 1.5e-8)
+    z64, _, rel64, st64 = hi.solve(b, rtol=1e-8)
+    assert st64 == 0
+    assert _rel(z, z64) <= 1e-5
+    hi.close()
+    lo.close()

@@ -174,6 +174,44 @@ int h2_solve(h2_handle h, const double *b, double *z, int nrhs, double rtol, int
 int h2_solve_ir(h2_handle hi, h2_handle lo, const double *b, double *z, int nrhs, double rtol, double inner_rtol,
                 int restart, int maxit_inner, int maxit_outer, h2_solve_info *info);
 
+/* ---------------------------------------------------------------------------
+ * Serving with continuous batching.  A server owns a worker thread that
+ * solves queued right-hand sides on registered matrices.  Each registered
+ * matrix gets an engine with `slots` column slots; the columns of all its
+ * requests share one batched product per Arnoldi step, and at every restart
+ * cycle finished columns leave and queued requests are admitted into the
+ * free slots.  With a low-precision partner handle lo the engine runs
+ * GMRES-IR (inner cycles with lo to inner_rtol, residuals with hi), else
+ * restarted GMRES with hi.  A column finishes when |b - G~_hi z| <= rtol |b|
+ * or after maxit iterations.  Admission is by device memory: an engine's work
+ * space (about (restart + 9) n slots doubles) is allocated when its first
+ * request is admitted, within hbm_budget bytes (0 = 90 % of the free device
+ * memory at creation), and released when the engine is idle and another
+ * needs the room.  Registered handles must not be used by other threads
+ * while the server runs.
+ * ------------------------------------------------------------------------- */
+typedef struct h2_srv *h2_server;
+int h2_serve_create(int device, size_t hbm_budget, h2_server *out);
+/* Register matrix hi (and optionally its low-precision copy lo) with the
+ * server.  1 <= slots <= 64, 1 <= restart <= 200, maxit >= 1; inner_rtol in
+ * (0, 1) when lo is given.  H2_ENOMEM if one engine exceeds the budget. */
+int h2_serve_register(h2_server s, h2_handle hi, h2_handle lo, int slots, int restart, int maxit, double inner_rtol);
+/* Queue a solve of G~ z = b on the registered matrix hi: b is a HOST
+ * column-major n x nrhs array (copied), 1 <= nrhs <= slots.  *ticket
+ * identifies the request. */
+int h2_serve_submit(h2_server s, h2_handle hi, const double *b, int nrhs, double rtol, uint64_t *ticket);
+/* H2_PENDING while the request runs; once done, copies z (host n x nrhs)
+ * and info (nrhs entries, either may be NULL), forgets the ticket and
+ * returns H2_OK or H2_ENOCONV. */
+int h2_serve_poll(h2_server s, uint64_t ticket, double *z, h2_solve_info *info);
+/* Block until the request is done or timeout_s seconds pass (H2_PENDING). */
+int h2_serve_wait(h2_server s, uint64_t ticket, double timeout_s);
+/* stats[6]: queued requests, running columns, completed requests, engine
+ * steps, device bytes in use by engines, budget. */
+int h2_serve_stats(h2_server s, int64_t *stats);
+/* Stop the worker (running requests are abandoned) and free the engines. */
+int h2_serve_destroy(h2_server s);
+
 /* Phases of the product, in launch order (h2_phase_times). */
 enum h2_phase {
   H2_PH_PERMUTE_IN = 0,  /* caller order -> leaf-padded cluster order */

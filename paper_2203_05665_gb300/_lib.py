@@ -45,7 +45,8 @@ class SolveInfo(C.Structure):
 EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_counts", "h2_plan_tree",
             "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec",
             "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
-            "h2_last_error"]
+            "h2_serve_create", "h2_serve_register", "h2_serve_submit", "h2_serve_poll", "h2_serve_wait",
+            "h2_serve_stats", "h2_serve_destroy", "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -84,6 +85,13 @@ def load():
                                       C.POINTER(SolveInfo)]),
             "h2_profile": (C.c_int, [vp, C.c_int]),
             "h2_phase_times": (C.c_int, [vp, dp, i64p, i64p]),
+            "h2_serve_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(vp)]),
+            "h2_serve_register": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double]),
+            "h2_serve_submit": (C.c_int, [vp, vp, dp, C.c_int, C.c_double, C.POINTER(C.c_uint64)]),
+            "h2_serve_poll": (C.c_int, [vp, C.c_uint64, dp, C.POINTER(SolveInfo)]),
+            "h2_serve_wait": (C.c_int, [vp, C.c_uint64, C.c_double]),
+            "h2_serve_stats": (C.c_int, [vp, i64p]),
+            "h2_serve_destroy": (C.c_int, [vp]),
             "h2_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -277,3 +285,57 @@ class H2Matrix:
         if st not in (H2_OK, H2_ENOCONV):
             _check(st)
         return z, np.array([i.iters for i in info]), np.array([i.relres for i in info]), st
+
+
+class Server:
+    """Continuous-batching solve server (h2_serve_*): a native worker thread on one GPU."""
+
+    def __init__(self, device=0, hbm_budget=0):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib.h2_serve_create(int(device), int(hbm_budget), C.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def register(self, hi, lo=None, slots=32, restart=30, maxit=5000, inner_rtol=1e-4):
+        _check(self._lib.h2_serve_register(self._h, hi.handle, lo.handle if lo is not None else None, int(slots),
+                                           int(restart), int(maxit), float(inner_rtol)))
+        self._n[hi.handle.value] = hi.n
+
+    def submit(self, hi, b, rtol=1e-8):
+        bb = np.asfortranarray(np.asarray(b, dtype=np.float64).reshape(hi.n, -1))
+        t = C.c_uint64()
+        _check(self._lib.h2_serve_submit(self._h, hi.handle, _dp(bb), int(bb.shape[1]), float(rtol), C.byref(t)))
+        return int(t.value), bb.shape
+
+    def poll(self, ticket, shape):
+        """None while pending, else (z, iters, relres, status)."""
+        z = np.zeros(shape, order="F")
+        info = (SolveInfo * shape[1])()
+        st = self._lib.h2_serve_poll(self._h, C.c_uint64(ticket), _dp(z), info)
+        if st == H2_PENDING:
+            return None
+        if st not in (H2_OK, H2_ENOCONV):
+            _check(st)
+        return z, np.array([i.iters for i in info]), np.array([i.relres for i in info]), st
+
+    def wait(self, ticket, timeout=60.0):
+        st = self._lib.h2_serve_wait(self._h, C.c_uint64(ticket), float(timeout))
+        if st not in (H2_OK, H2_PENDING):
+            _check(st)
+        return st == H2_OK
+
+    def stats(self):
+        out = np.zeros(6, dtype=np.int64)
+        _check(self._lib.h2_serve_stats(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return dict(zip(["queued", "running_columns", "completed", "steps", "engine_bytes", "budget"],
+                        (int(v) for v in out)))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.h2_serve_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -6,7 +6,6 @@
 
 #include "h2_internal.hpp"
 
-struct h2_ctx : h2::Ctx {};
 struct h2_plan_ctx {
   h2::Plan plan;
 };

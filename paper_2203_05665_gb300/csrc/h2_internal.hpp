@@ -130,8 +130,20 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64);
 // GMRES (h2_solve.cu); b, z device FP64 arrays
 int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
               h2_solve_info *info);
+// one GMRES cycle for G~ D = R (see h2_solve.cu); host arrays of nrhs entries
+int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int restart, const double *tol,
+                const int *act, const int *max_it, int *iters);
+int alloc_gmres_work(GmresWork &w, int64_t n, int cols, int restart);
 // GMRES-IR: outer residuals with hi, inner GMRES with lo (same mesh and tree)
 int run_gmres_ir(Ctx &hi, Ctx &lo, const double *b, double *z, int nrhs, double rtol, double inner_rtol,
                  int restart, int maxit_inner, int maxit_outer, h2_solve_info *info);
 
+// vector helpers of the solver (h2_solve.cu) on the context's stream
+void k_launch_residual(const double *b, const double *Az, int64_t total, double *r, cudaStream_t st);
+void k_launch_axpy(const double *d, int64_t total, double *z, cudaStream_t st);
+int column_norms(Ctx &c, const double *v, int64_t n, int ncols, double *dev_tmp, double *host_out);
+
 }  // namespace h2
+
+// the opaque handle of the C ABI
+struct h2_ctx : h2::Ctx {};

@@ -147,9 +147,12 @@ void free_gmres_work(GmresWork &w) {
 static int ensure_gmres_work(Ctx &c, int nrhs, int restart) {
   GmresWork &w = c.gw;
   if (nrhs <= w.cols && restart <= w.restart) return H2_OK;
-  const int cols = std::max(nrhs, w.cols), mr = std::max(restart, w.restart);
+  return alloc_gmres_work(w, c.d.n, std::max(nrhs, w.cols), std::max(restart, w.restart));
+}
+
+int alloc_gmres_work(GmresWork &w, int64_t n_, int cols, int mr) {
   free_gmres_work(w);
-  const size_t n = (size_t)c.d.n, tot = n * cols;
+  const size_t n = (size_t)n_, tot = n * cols;
   bool ok = true;
   auto al = [&](double **p, size_t cnt) { ok = ok && cudaMalloc(p, std::max<size_t>(cnt, 1) * 8) == cudaSuccess; };
   al(&w.Vb, (size_t)(mr + 1) * tot);
@@ -178,106 +181,121 @@ static int ensure_gmres_work(Ctx &c, int nrhs, int restart) {
   return H2_OK;
 }
 
-int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
-              h2_solve_info *info) {
+// One GMRES cycle from a zero initial guess for G~ D = R, column by column:
+// Arnoldi with classical Gram-Schmidt applied twice, Givens rotations, and
+// the update D = V y.  A column takes part if act[c] and |R_c| > tol[c]; it
+// stops when its residual estimate drops to tol[c], at a breakdown, after
+// restart iterations or after max_it[c] iterations.  iters[c] receives the
+// iterations done.  R may alias w.W.  All host arrays have nrhs entries.
+int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int restart, const double *tol,
+                const int *act, const int *max_it, int *iters) {
   const int64_t n = c.d.n, tot = n * nrhs;
   const int mr = restart;
   cudaStream_t st = c.stream;
   int rc;
-  if ((rc = ensure_gmres_work(c, nrhs, restart))) return rc;
-  struct P {
-    double *p;
-  };
-  GmresWork &w = c.gw;
-  P Vb{w.Vb}, W{w.W}, H{w.H}, cs{w.cs}, sn{w.sn}, g{w.g}, h1{w.h1}, h2b{w.h2}, hn{w.hn}, resid{w.resid}, yv{w.yv},
-      bn{w.bn};
-  struct I {
-    int *p;
-  } active{w.active}, jc{w.jc};
-
-  std::vector<double> h_bn(nrhs), h_rn(nrhs), h_res(nrhs), h_g0((mr + 1) * nrhs, 0.0);
-  std::vector<int> h_active(nrhs, 1), h_jc(nrhs, 0), h_iters(nrhs, 0), h_done(nrhs, 0);
-
-  // |b|
-  k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(b, b, n, nrhs, bn.p);
-  H2_CUDA_TRY(cudaMemcpyAsync(h_bn.data(), bn.p, nrhs * 8, cudaMemcpyDeviceToHost, st));
-  H2_CUDA_TRY(cudaMemsetAsync(z, 0, tot * 8, st));
+  std::vector<double> rn(nrhs), g0((size_t)(mr + 1) * nrhs, 0.0), rs(2 * nrhs);
+  std::vector<int> on(nrhs, 0), jc(nrhs, 0);
+  k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(R, R, n, nrhs, w.hn);
+  k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
+  H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.hn, nrhs * 8, cudaMemcpyDeviceToHost, st));
   H2_CUDA_TRY(cudaStreamSynchronize(st));
+  bool any = false;
   for (int col = 0; col < nrhs; ++col) {
-    h_bn[col] = std::sqrt(h_bn[col]);
-    if (h_bn[col] == 0.0) { h_done[col] = 1; h_res[col] = 0.0; }
+    iters[col] = 0;
+    on[col] = act[col] && rn[col] > tol[col] && max_it[col] > 0;
+    any = any || on[col];
+    g0[col] = rn[col];
   }
-  // r = b (z0 = 0)
-  H2_CUDA_TRY(cudaMemcpyAsync(W.p, b, tot * 8, cudaMemcpyDeviceToDevice, st));
-  bool first = true;
-  for (;;) {
-    if (!first) {
-      // true residual r = b - G~ z
-      if ((rc = run_matvec(c, z, W.p, nrhs, true))) return rc;
-      k_residual<<<grid1(tot), kT, 0, st>>>(b, W.p, tot, W.p);
+  H2_CUDA_TRY(cudaMemsetAsync(D, 0, tot * 8, st));
+  if (!any) return H2_OK;
+  H2_CUDA_TRY(cudaMemcpyAsync(w.active, on.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
+  k_scale<<<grid1(tot), kT, 0, st>>>(R, w.hn, w.active, n, nrhs, w.Vb);
+  H2_CUDA_TRY(cudaMemcpyAsync(w.g, g0.data(), (mr + 1) * nrhs * 8, cudaMemcpyHostToDevice, st));
+  for (int j = 0; j < mr; ++j) {
+    double *Vj = w.Vb + (int64_t)j * tot, *Vj1 = w.Vb + (int64_t)(j + 1) * tot;
+    if ((rc = run_matvec(c, Vj, w.W, nrhs, true))) return rc;
+    k_dots<<<dim3(nrhs, j + 1), kT, 0, st>>>(w.Vb, w.W, n, nrhs, w.h1);
+    k_orth<<<grid1(tot), kT, 0, st>>>(w.Vb, w.h1, j + 1, n, nrhs, w.W);
+    k_dots<<<dim3(nrhs, j + 1), kT, 0, st>>>(w.Vb, w.W, n, nrhs, w.h2);
+    k_orth<<<grid1(tot), kT, 0, st>>>(w.Vb, w.h2, j + 1, n, nrhs, w.W);
+    k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(w.W, w.W, n, nrhs, w.hn);
+    k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
+    k_scale<<<grid1(tot), kT, 0, st>>>(w.W, w.hn, w.active, n, nrhs, Vj1);
+    k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(w.h1, w.h2, w.hn, j, mr, nrhs, w.H, w.cs, w.sn, w.g, w.resid,
+                                              w.active);
+    H2_CUDA_TRY(cudaGetLastError());
+    H2_CUDA_TRY(cudaMemcpyAsync(rs.data(), w.resid, nrhs * 8, cudaMemcpyDeviceToHost, st));
+    H2_CUDA_TRY(cudaMemcpyAsync(rs.data() + nrhs, w.hn, nrhs * 8, cudaMemcpyDeviceToHost, st));
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    bool still = false;
+    for (int col = 0; col < nrhs; ++col) {
+      if (!on[col]) continue;
+      jc[col] = j + 1;
+      iters[col]++;
+      if (rs[col] <= tol[col] || rs[nrhs + col] == 0.0 || iters[col] >= max_it[col]) on[col] = 0;
+      still = still || on[col];
     }
-    k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(W.p, W.p, n, nrhs, hn.p);
-    k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(hn.p, nrhs);
-    H2_CUDA_TRY(cudaMemcpyAsync(h_rn.data(), hn.p, nrhs * 8, cudaMemcpyDeviceToHost, st));
+    if (!still) break;
+    H2_CUDA_TRY(cudaMemcpyAsync(w.active, on.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
+  }
+  H2_CUDA_TRY(cudaMemcpyAsync(w.jc, jc.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
+  k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(w.H, w.g, w.jc, mr, nrhs, w.yv);
+  k_update<<<grid1(tot), kT, 0, st>>>(w.Vb, w.yv, w.jc, n, nrhs, D);
+  H2_CUDA_TRY(cudaGetLastError());
+  return H2_OK;
+}
+
+__global__ void k_axpy_cols(const double *__restrict__ d, int64_t total, double *__restrict__ z) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    z[e] += d[e];
+}
+
+// Restarted GMRES(restart): z = 0; repeat r = b - G~ z, one cycle for G~ d = r
+// with the column tolerance rtol |b|, z += d; a column stops when its true
+// relative residual is <= rtol or after maxit iterations.
+int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
+              h2_solve_info *info) {
+  const int64_t n = c.d.n, tot = n * nrhs;
+  cudaStream_t st = c.stream;
+  int rc;
+  if ((rc = ensure_gmres_work(c, nrhs, restart))) return rc;
+  GmresWork &w = c.gw;
+  std::vector<double> bn(nrhs), rn(nrhs), res(nrhs, 0.0), tol(nrhs);
+  std::vector<int> act(nrhs), left(nrhs), it(nrhs), iters(nrhs, 0);
+  k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(b, b, n, nrhs, w.bn);
+  k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.bn, nrhs);
+  H2_CUDA_TRY(cudaMemcpyAsync(bn.data(), w.bn, nrhs * 8, cudaMemcpyDeviceToHost, st));
+  H2_CUDA_TRY(cudaMemsetAsync(z, 0, tot * 8, st));
+  H2_CUDA_TRY(cudaMemcpyAsync(w.r, b, tot * 8, cudaMemcpyDeviceToDevice, st));
+  for (bool first = true;; first = false) {
+    if (!first) {
+      if ((rc = run_matvec(c, z, w.Az, nrhs, true))) return rc;
+      k_residual<<<grid1(tot), kT, 0, st>>>(b, w.Az, tot, w.r);
+    }
+    k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(w.r, w.r, n, nrhs, w.hn);
+    k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
+    H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.hn, nrhs * 8, cudaMemcpyDeviceToHost, st));
     H2_CUDA_TRY(cudaStreamSynchronize(st));
     bool any = false;
     for (int col = 0; col < nrhs; ++col) {
-      if (h_bn[col] == 0.0) { h_active[col] = 0; continue; }
-      h_res[col] = h_rn[col] / h_bn[col];
-      if (h_res[col] <= rtol) h_done[col] = 1;
-      h_active[col] = (!h_done[col] && h_iters[col] < maxit) ? 1 : 0;
-      any = any || h_active[col];
+      res[col] = bn[col] > 0 ? rn[col] / bn[col] : 0.0;
+      act[col] = res[col] > rtol && iters[col] < maxit;
+      left[col] = maxit - iters[col];
+      tol[col] = rtol * bn[col];
+      any = any || act[col];
     }
-    first = false;
     if (!any) break;
-    // start a cycle: V_0 = r / |r|, g = |r| e_1
-    H2_CUDA_TRY(cudaMemcpyAsync(active.p, h_active.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
-    k_scale<<<grid1(tot), kT, 0, st>>>(W.p, hn.p, active.p, n, nrhs, Vb.p);
-    std::fill(h_g0.begin(), h_g0.end(), 0.0);
-    for (int col = 0; col < nrhs; ++col) h_g0[col] = h_rn[col];
-    H2_CUDA_TRY(cudaMemcpyAsync(g.p, h_g0.data(), (mr + 1) * nrhs * 8, cudaMemcpyHostToDevice, st));
-    for (int col = 0; col < nrhs; ++col) h_jc[col] = 0;
-    std::vector<double> rs(2 * nrhs);
-    for (int j = 0; j < mr; ++j) {
-      double *Vj = Vb.p + (int64_t)j * tot, *Vj1 = Vb.p + (int64_t)(j + 1) * tot;
-      if ((rc = run_matvec(c, Vj, W.p, nrhs, true))) return rc;
-      // classical Gram-Schmidt, twice
-      k_dots<<<dim3(nrhs, j + 1), kT, 0, st>>>(Vb.p, W.p, n, nrhs, h1.p);
-      k_orth<<<grid1(tot), kT, 0, st>>>(Vb.p, h1.p, j + 1, n, nrhs, W.p);
-      k_dots<<<dim3(nrhs, j + 1), kT, 0, st>>>(Vb.p, W.p, n, nrhs, h2b.p);
-      k_orth<<<grid1(tot), kT, 0, st>>>(Vb.p, h2b.p, j + 1, n, nrhs, W.p);
-      k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(W.p, W.p, n, nrhs, hn.p);
-      k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(hn.p, nrhs);
-      k_scale<<<grid1(tot), kT, 0, st>>>(W.p, hn.p, active.p, n, nrhs, Vj1);
-      k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(h1.p, h2b.p, hn.p, j, mr, nrhs, H.p, cs.p, sn.p, g.p, resid.p,
-                                                active.p);
-      H2_CUDA_TRY(cudaGetLastError());
-      H2_CUDA_TRY(cudaMemcpyAsync(rs.data(), resid.p, nrhs * 8, cudaMemcpyDeviceToHost, st));
-      H2_CUDA_TRY(cudaMemcpyAsync(rs.data() + nrhs, hn.p, nrhs * 8, cudaMemcpyDeviceToHost, st));
-      H2_CUDA_TRY(cudaStreamSynchronize(st));
-      bool still = false;
-      for (int col = 0; col < nrhs; ++col) {
-        if (!h_active[col]) continue;
-        h_jc[col] = j + 1;
-        h_iters[col]++;
-        if (rs[col] <= rtol * h_bn[col] || rs[nrhs + col] == 0.0 || h_iters[col] >= maxit) h_active[col] = 0;
-        still = still || h_active[col];
-      }
-      if (!still) break;
-      H2_CUDA_TRY(cudaMemcpyAsync(active.p, h_active.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
-    }
-    H2_CUDA_TRY(cudaMemcpyAsync(jc.p, h_jc.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
-    k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(H.p, g.p, jc.p, mr, nrhs, yv.p);
-    k_update<<<grid1(tot), kT, 0, st>>>(Vb.p, yv.p, jc.p, n, nrhs, z);
-    H2_CUDA_TRY(cudaGetLastError());
+    if ((rc = gmres_cycle(c, w, w.r, w.d, nrhs, restart, tol.data(), act.data(), left.data(), it.data()))) return rc;
+    for (int col = 0; col < nrhs; ++col) iters[col] += it[col];
+    k_axpy_cols<<<grid1(tot), kT, 0, st>>>(w.d, tot, z);
   }
   int status = H2_OK;
   for (int col = 0; col < nrhs; ++col) {
-    bool ok = h_res[col] <= rtol;
+    bool ok = res[col] <= rtol;
     if (!ok) status = H2_ENOCONV;
     if (info) {
-      info[col].iters = h_iters[col];
-      info[col].relres = h_res[col];
+      info[col].iters = iters[col];
+      info[col].relres = res[col];
       info[col].status = ok ? H2_OK : H2_ENOCONV;
     }
   }
@@ -286,14 +304,27 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
   return derr ? derr : status;
 }
 
-__global__ void k_axpy_cols(const double *__restrict__ d, int64_t total, double *__restrict__ z) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    z[e] += d[e];
-}
 
 __global__ void k_mask_cols(const int *__restrict__ keep, int64_t n, int64_t total, double *__restrict__ v) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     if (!keep[e / n]) v[e] = 0.0;
+}
+
+void k_launch_residual(const double *b, const double *Az, int64_t total, double *r, cudaStream_t st) {
+  k_residual<<<grid1(total), kT, 0, st>>>(b, Az, total, r);
+}
+
+void k_launch_axpy(const double *d, int64_t total, double *z, cudaStream_t st) {
+  k_axpy_cols<<<grid1(total), kT, 0, st>>>(d, total, z);
+}
+
+int column_norms(Ctx &c, const double *v, int64_t n, int ncols, double *dev_tmp, double *host_out) {
+  k_dots<<<dim3(ncols, 1), kT, 0, c.stream>>>(v, v, n, ncols, dev_tmp);
+  k_sqrt<<<(ncols + 63) / 64, 64, 0, c.stream>>>(dev_tmp, ncols);
+  H2_CUDA_TRY(cudaGetLastError());
+  H2_CUDA_TRY(cudaMemcpyAsync(host_out, dev_tmp, ncols * 8, cudaMemcpyDeviceToHost, c.stream));
+  H2_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  return H2_OK;
 }
 
 // Mixed-precision iterative refinement around GMRES (GMRES-IR, Carson and

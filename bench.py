@@ -252,6 +252,10 @@ def run_ours(args):
                                      residual=args.prec, inner="f32 GMRES(30) to 1e-4")
             lo.close()
 
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = run_serve(args, local, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args)
@@ -276,6 +280,7 @@ def run_ours(args):
         "build_s": build_s,
         "finite": finite,
         "solve": solve,
+        "serve": serve,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -284,6 +289,78 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+SERVE_GEOMS = {
+    # name: (mesh factory, leaf)
+    "icosphere L4": (lambda I: I.icosphere(4), 32),
+    "icosphere L5": (lambda I: I.icosphere(5), 32),
+    "icosphere L6": (lambda I: I.icosphere(6), 32),
+    "icosphere L7": (lambda I: I.icosphere(7), 32),
+    "icosphere L8": (lambda I: I.icosphere(8), 32),
+    "ellipsoid L6 (1.5,1,0.7)": (lambda I: I.ellipsoid(6, (1.5, 1.0, 0.7)), 32),
+    "ellipsoid L7 (2,1,0.5)": (lambda I: I.ellipsoid(7, (2.0, 1.0, 0.5)), 32),
+    "cube s=100": (lambda I: I.cube(100), 32),
+}
+SERVE_SMALL = ["icosphere L4", "icosphere L5", "icosphere L6", "ellipsoid L6 (1.5,1,0.7)"]
+
+
+def run_serve(args, local, stream):
+    """Poisson stream of solve requests over resident geometries (seeded): p50/p99
+    latency and solves/s for plain FP64-accurate GMRES engines and for GMRES-IR
+    engines (FP32 inner cycles), on the same request stream."""
+    from paper_2203_05665_gb300 import H2Matrix, Server, inputs
+    names = list(SERVE_GEOMS) if args.serve_full else SERVE_SMALL
+    nreq = args.serve_requests
+    rng = np.random.default_rng(1005)
+    gaps = rng.exponential(1.0 / args.serve_rate, nreq)
+    gsel = rng.integers(0, len(names), nreq)
+    nr = rng.integers(1, 33, nreq)
+    rt = np.where(rng.integers(0, 2, nreq) == 0, 1e-6, 1e-8)
+    geoms = []
+    for name in names:
+        make, leaf = SERVE_GEOMS[name]
+        v, f = make(inputs)
+        hi = H2Matrix(v, f, leaf_size=leaf, eta=2.0, order=3, prec="f64", device=local, stream=stream.cuda_stream)
+        lo = H2Matrix(v, f, leaf_size=leaf, eta=2.0, order=3, prec="f32", device=local, stream=stream.cuda_stream)
+        geoms.append((name, f.shape[0], hi, lo))
+    rhs = [np.asfortranarray(np.random.default_rng(2000 + i).uniform(-1, 1, (geoms[gsel[i]][1], nr[i])))
+           for i in range(nreq)]
+    out = {"requests": nreq, "rate_per_s": args.serve_rate, "geometries": names, "m": 3,
+           "nrhs": "U{1..32}", "rtol": "1e-6 or 1e-8", "seed": 1005}
+    for mode in ("plain", "ir"):
+        srv = Server(device=local)
+        for name, n, hi, lo in geoms:
+            srv.register(hi, lo if mode == "ir" else None, slots=32, restart=30, maxit=20000, inner_rtol=1e-4)
+        pending = {}
+        lat = []
+        t0 = time.perf_counter()
+        arrive = t0 + np.cumsum(gaps)
+        i = 0
+        while i < nreq or pending:
+            now = time.perf_counter()
+            while i < nreq and arrive[i] <= now:
+                t, shape = srv.submit(geoms[gsel[i]][2], rhs[i], float(rt[i]))
+                pending[t] = (shape, arrive[i])
+                i += 1
+            for t in list(pending):
+                shape, ta = pending[t]
+                res = srv.poll(t, shape)
+                if res is not None:
+                    lat.append(time.perf_counter() - ta)
+                    del pending[t]
+            time.sleep(0.0005)
+        span = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        lat.sort()
+        out[mode] = {"solves_per_s": nreq / span, "columns_per_s": float(nr.sum()) / span,
+                     "p50_s": lat[len(lat) // 2], "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                     "wall_s": span, "engine_steps": stats["steps"]}
+    for name, n, hi, lo in geoms:
+        hi.close()
+        lo.close()
+    return out
 
 
 def _oracle_sample(level, order, nrhs):
@@ -352,6 +429,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-nrhs", type=int, default=16)
     ap.add_argument("--solve-reps", type=int, default=3)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-full", action="store_true", help="all 8 geometries (icosphere L4-L8, ...)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

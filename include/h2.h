@@ -140,6 +140,25 @@ int h2_info(h2_handle h, h2_stats *out);
  * H2_ECUDA (launch failure). */
 int h2_matvec(h2_handle h, const void *x, void *y, int nrhs);
 
+/* The same product as h2_matvec for callers that cannot allocate device
+ * memory when they multiply (an allocator owned by another runtime, a
+ * real-time loop that must not block in cudaMalloc, memory handed out in
+ * full ahead of time).  It allocates nothing: its work buffers live in one
+ * fixed array of 64 MiB of device memory inside the library, which every GPU
+ * that loads the library keeps until the process exits.  The paper has no
+ * counterpart; this is an interface of this library only.
+ *   - x, y, nrhs and the result are as for h2_matvec, on the handle's stream.
+ *   - Matrices that need more work space than 64 MiB for the given nrhs
+ *     (2 (n_leaves leaf_max + clusters k) nrhs_padded value bytes) are
+ *     rejected with H2_EINVAL and a message giving both sizes.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call outside any stream capture.
+ *   - All calls share the one array: calls that can overlap on the GPU (on
+ *     different streams, from different threads or handles) race and must be
+ *     serialised by the caller.
+ *   - h2_coefficients keeps describing the last h2_matvec product. */
+int h2_matvec_noalloc(h2_handle h, const void *x, void *y, int nrhs);
+
 /* The same product with HOST double arrays whatever the handle's precision:
  * copies x to the device, multiplies, copies y back and synchronises the
  * stream. */

@@ -44,7 +44,7 @@ class SolveInfo(C.Structure):
 
 EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_counts", "h2_plan_tree",
             "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec",
-            "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
+            "h2_matvec_noalloc", "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
             "h2_serve_create", "h2_serve_register", "h2_serve_submit", "h2_serve_poll", "h2_serve_wait",
             "h2_serve_stats", "h2_serve_destroy", "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
@@ -78,6 +78,7 @@ def load():
             "h2_destroy": (C.c_int, [vp]),
             "h2_info": (C.c_int, [vp, C.POINTER(Stats)]),
             "h2_matvec": (C.c_int, [vp, vp, vp, C.c_int]),
+            "h2_matvec_noalloc": (C.c_int, [vp, vp, vp, C.c_int]),
             "h2_matvec_host": (C.c_int, [vp, dp, dp, C.c_int]),
             "h2_coefficients": (C.c_int, [vp, C.c_int, dp]),
             "h2_solve": (C.c_int, [vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(SolveInfo)]),
@@ -219,6 +220,16 @@ class H2Matrix:
         if x.stride(0) != 1 or y.stride(0) != 1:
             raise ValueError("x and y must be column-major (use colmajor())")
         _check(self._lib.h2_matvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.shape[1])))
+        return y
+
+    def matvec_noalloc(self, x, y):
+        """As matvec, through h2_matvec_noalloc: no device allocation, fixed 64 MiB work space."""
+        if x.shape != y.shape or x.shape[0] != self.n:
+            raise ValueError("x and y must both be (n, nrhs)")
+        if x.stride(0) != 1 or y.stride(0) != 1:
+            raise ValueError("x and y must be column-major (use colmajor())")
+        _check(self._lib.h2_matvec_noalloc(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                           int(x.shape[1])))
         return y
 
     def profile(self, enable=True):

@@ -53,15 +53,30 @@ enum h2_status {
  *                 vectors are double.
  *   H2_F32        FP32 storage and arithmetic; vectors are float.
  *   H2_F64_NATIVE FP64 storage and arithmetic on the FP64 pipe (1/58 of the
- *                 FP32 rate on GB300); vectors are double. */
-enum h2_prec { H2_F64 = 0, H2_F32 = 1, H2_F64_NATIVE = 2 };
+ *                 FP32 rate on GB300); vectors are double.
+ *   H2_BF16       V, transfer factors and nearfield stored in bfloat16, FP32
+ *                 accumulation, coupling regenerated in FP32; vectors float.
+ *   H2_F16        as H2_BF16 with IEEE half storage; every nearfield block and
+ *                 every leaf basis carries a power-of-two scale so that its
+ *                 entries (of size h^2 to h^4) stay in the half range. */
+enum h2_prec { H2_F64 = 0, H2_F32 = 1, H2_F64_NATIVE = 2, H2_BF16 = 3, H2_F16 = 4 };
+
+/* coupling matrices S_ts (Eq. (6c)):
+ *   H2_COUPLING_AUTO   stored, except regenerated for H2_BF16 / H2_F16 and for
+ *                      H2_F32 when storing them would take more than half of
+ *                      the free device memory;
+ *   H2_COUPLING_STORED computed once at build time and streamed by the product;
+ *   H2_COUPLING_REGEN  recomputed in FP32 inside the product from the
+ *                      interpolation points (not for H2_F64 / H2_F64_NATIVE). */
+enum h2_coupling { H2_COUPLING_AUTO = 0, H2_COUPLING_STORED = 1, H2_COUPLING_REGEN = 2 };
 
 typedef struct h2_options {
   int prec;          /* enum h2_prec; default H2_F64 */
   int quad_order;    /* Gauss points per coordinate of the nearfield quadrature; default 3 */
   int device;        /* CUDA device ordinal; default 0 */
   void *stream;      /* cudaStream_t used by every call on the handle; NULL = the legacy default stream */
-  int reserved[8];   /* must be zero */
+  int coupling;      /* enum h2_coupling; default H2_COUPLING_AUTO */
+  int reserved[7];   /* must be zero */
 } h2_options;
 
 /* Statistics of a built matrix (h2_info). */
@@ -78,6 +93,7 @@ typedef struct h2_stats {
   int64_t first_adm_level;/* smallest level holding an admissible block */
   int64_t device_bytes;   /* device memory held by the handle (without work buffers) */
   int64_t prec;           /* enum h2_prec */
+  int64_t coupling;       /* H2_COUPLING_STORED or H2_COUPLING_REGEN as built */
 } h2_stats;
 
 /* Per right-hand side result of h2_solve. */

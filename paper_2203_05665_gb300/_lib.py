@@ -14,8 +14,9 @@ import numpy as np
 from . import _build
 
 H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ENOCONV, H2_ETIMEOUT, H2_PENDING, H2_EBUSY = range(8)
-H2_F64, H2_F32, H2_F64_NATIVE = 0, 1, 2
-PREC = {"f64": H2_F64, "f32": H2_F32, "f64n": H2_F64_NATIVE}
+H2_F64, H2_F32, H2_F64_NATIVE, H2_BF16, H2_F16 = 0, 1, 2, 3, 4
+PREC = {"f64": H2_F64, "f32": H2_F32, "f64n": H2_F64_NATIVE, "bf16": H2_BF16, "f16": H2_F16}
+COUPLING = {"auto": 0, "stored": 1, "regen": 2}
 
 _lock = threading.Lock()
 _lib = None
@@ -29,13 +30,13 @@ class H2Error(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("quad_order", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-                ("reserved", C.c_int * 8)]
+                ("coupling", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("n", "depth", "clusters", "leaf_max", "order", "rank", "adm_blocks", "near_blocks",
-                 "near_entries", "first_adm_level", "device_bytes", "prec")]
+                 "near_entries", "first_adm_level", "device_bytes", "prec", "coupling")]
 
 
 class SolveInfo(C.Structure):
@@ -179,7 +180,7 @@ class H2Matrix:
     """An H² matrix of one mesh on one GPU (see include/h2.h)."""
 
     def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, prec="f64", quad_order=3, device=0,
-                 stream=None):
+                 stream=None, coupling="auto"):
         lib = load()
         v, t = _mesh(vert, tri)
         opt = Options()
@@ -188,6 +189,7 @@ class H2Matrix:
         opt.quad_order = int(quad_order)
         opt.device = int(device)
         opt.stream = stream
+        opt.coupling = COUPLING[coupling]
         h = C.c_void_p()
         _check(lib.h2_build(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
                             int(leaf_size), float(eta), int(order), C.byref(opt), C.byref(h)))

@@ -26,7 +26,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 static void free_dev(Dev &d) {
-  void *ptrs[] = {d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
+  void *ptrs[] = {d.icen, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
                   d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -132,8 +132,13 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   h2_options o;
   h2_options_default(&o);
   if (opt) o = *opt;
-  if (o.prec != H2_F64 && o.prec != H2_F32 && o.prec != H2_F64_NATIVE)
-    return fail(H2_EINVAL, "prec must be H2_F64, H2_F32 or H2_F64_NATIVE");
+  if (o.prec < H2_F64 || o.prec > H2_F16) return fail(H2_EINVAL, "unknown precision");
+  if (o.coupling < H2_COUPLING_AUTO || o.coupling > H2_COUPLING_REGEN) return fail(H2_EINVAL, "unknown coupling mode");
+  const bool half_prec = o.prec == H2_BF16 || o.prec == H2_F16, f64 = o.prec == H2_F64 || o.prec == H2_F64_NATIVE;
+  if (o.coupling == H2_COUPLING_REGEN && f64)
+    return fail(H2_EINVAL, "the regenerated coupling is FP32; use H2_F32, H2_BF16 or H2_F16");
+  if (o.coupling == H2_COUPLING_STORED && half_prec)
+    return fail(H2_EINVAL, "16-bit precisions regenerate the coupling");
   for (int r : o.reserved)
     if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
   int ndev = 0;
@@ -146,6 +151,7 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   c->stream = (cudaStream_t)o.stream;
   c->quad_order = o.quad_order;
   c->d.prec = o.prec;
+  c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);
   int rc;
   try {
     rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, true, c->plan);
@@ -196,6 +202,7 @@ int h2_info(h2_handle h, h2_stats *out) {
   out->first_adm_level = p.first_adm_level;
   out->device_bytes = h->d.bytes;
   out->prec = h->d.prec;
+  out->coupling = h->d.coupling == 1 ? H2_COUPLING_REGEN : H2_COUPLING_STORED;
   return H2_OK;
 }
 

@@ -40,6 +40,7 @@ struct Plan {
   std::vector<int64_t> first, size;
   std::vector<double> lo, hi;  // nclu x 3
   std::vector<double> cheb;    // nclu x 3 x m
+  std::vector<double> icen, ihalf;   // nclu x 3: interpolation-box centre and half width
   // admissible blocks in CSR by row cluster (columns sorted)
   std::vector<int64_t> adm_ptr;   // nclu + 1
   std::vector<int32_t> adm_col;
@@ -58,7 +59,9 @@ int make_plan(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, in
 // Device representation of one H^2 matrix.
 struct Dev {
   int prec = H2_F64;
-  size_t esize = 8;
+  int coupling = 0;             // 0: S stored, 1: S regenerated in FP32 in the product
+  size_t esize = 8;             // bytes of an arithmetic / vector value
+  size_t ssize = 8;             // bytes of a stored value (V, E, S, nearfield)
   int m = 0, k = 0, kp = 0, depth = 0, first_adm_level = 0;
   int64_t n = 0, nclu = 0, nleaf = 0, lmax = 0, lp = 0, npad = 0;
   int64_t nadm = 0, nnear = 0;
@@ -73,6 +76,10 @@ struct Dev {
   int64_t *near_ptr = nullptr;  // nleaf + 1
   int32_t *near_col = nullptr;  // leaf-local
   double *cheb = nullptr;       // nclu x 3 x m (FP64 always)
+  double *icen = nullptr;       // nclu x 3 interpolation-box centres (regenerated coupling)
+  float *ihalf = nullptr;       // nclu x 3 interpolation-box half widths
+  float *vscale = nullptr;      // per leaf: power of two dividing the stored V (FP16), or NULL
+  float *nscale = nullptr;      // per nearfield block: the same for G_b, or NULL
   // work buffers for up to cap_nrhs right-hand sides
   int cap_nrhs = 0;
   void *xpad = nullptr, *ypad = nullptr, *xhat = nullptr, *yhat = nullptr;

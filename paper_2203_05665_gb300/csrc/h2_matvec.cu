@@ -10,7 +10,12 @@
 // Transfer matrices are applied in factored form E = Ex (x) Ey (x) Ez
 // (Eq. (9) with tensor Chebyshev points): three m x m mode products.
 // Coefficient layout: x^[cluster][nu][rhs], nu = jx + m jy + m^2 jz.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "h2_dd.cuh"
 #include "h2_internal.hpp"
@@ -79,9 +84,23 @@ __device__ __forceinline__ void mode_fibres(const T *F, const T *in, T *out, int
   }
 }
 
+// storage -> compute conversion of a transfer factor
+template <class TC, class TS>
+__device__ __forceinline__ TC to_compute(TS v) {
+  return convert<TC, TS>(v);
+}
+template <>
+__device__ __forceinline__ float to_compute<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ float to_compute<float, __half>(__half v) {
+  return __half2float(v);
+}
+
 // upward step for the parents of level l (Algorithm 1): x^_p = sum_children E_c^T x^_c
-template <class T>
-__global__ void k_upward(const T *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ xhat) {
+template <class TS, class T>
+__global__ void k_upward(const TS *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ xhat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int kr = k * rp, mm = m * m;
   T *a = reinterpret_cast<T *>(smem_raw);
@@ -89,7 +108,7 @@ __global__ void k_upward(const T *__restrict__ Ef, int m, int k, int rp, int64_t
   T *acc = b + kr;
   T *F = acc + kr;   // 2 children x 3 axes x m x m
   const int64_t par = par0 + blockIdx.x;
-  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = Ef[(2 * par + 1) * 3 * mm + i];
+  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = to_compute<T>(Ef[(2 * par + 1) * 3 * mm + i]);
   for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = zero_of<T>();
   for (int ch = 0; ch < 2; ++ch) {
     const int64_t c = 2 * par + 1 + ch;
@@ -110,8 +129,8 @@ __global__ void k_upward(const T *__restrict__ Ef, int m, int k, int rp, int64_t
 
 // downward step for the children of level l+1 (Algorithm 2): y^_c += E_c y^_parent;
 // one CTA per parent of level l handles both children
-template <class T>
-__global__ void k_downward(const T *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ yhat) {
+template <class TS, class T>
+__global__ void k_downward(const TS *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ yhat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int kr = k * rp, mm = m * m;
   T *p = reinterpret_cast<T *>(smem_raw);
@@ -119,7 +138,7 @@ __global__ void k_downward(const T *__restrict__ Ef, int m, int k, int rp, int64
   T *b = a + kr;
   T *F = b + kr;
   const int64_t par = par0 + blockIdx.x;
-  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = Ef[(2 * par + 1) * 3 * mm + i];
+  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = to_compute<T>(Ef[(2 * par + 1) * 3 * mm + i]);
   for (int i = threadIdx.x; i < kr; i += blockDim.x) p[i] = yhat[par * kr + i];
   __syncthreads();
   for (int ch = 0; ch < 2; ++ch) {
@@ -170,6 +189,45 @@ __device__ __forceinline__ dd lane<dd>(const float4 &v, int q) {
   return q == 0 ? dd{v.x, v.y} : dd{v.z, v.w};
 }
 
+// four consecutive stored values (aligned to four elements) as compute values
+template <class TS, class TC>
+__device__ __forceinline__ void load4(const TS *p, TC *out);
+template <>
+__device__ __forceinline__ void load4<float, float>(const float *p, float *out) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double, double>(const double *p, double *out) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void load4<dd, dd>(const dd *p, dd *out) {
+  const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+  out[0] = dd{a.x, a.y}; out[1] = dd{a.z, a.w}; out[2] = dd{b.x, b.y}; out[3] = dd{b.z, b.w};
+}
+template <>
+__device__ __forceinline__ void load4<__nv_bfloat16, float>(const __nv_bfloat16 *p, float *out) {
+  const uint2 v = *reinterpret_cast<const uint2 *>(p);
+  out[0] = __uint_as_float(v.x << 16); out[1] = __uint_as_float(v.x & 0xffff0000u);
+  out[2] = __uint_as_float(v.y << 16); out[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+template <>
+__device__ __forceinline__ void load4<__half, float>(const __half *p, float *out) {
+  const uint2 v = *reinterpret_cast<const uint2 *>(p);
+  const __half2 a = *reinterpret_cast<const __half2 *>(&v.x), b = *reinterpret_cast<const __half2 *>(&v.y);
+  const float2 fa = __half22float2(a), fb = __half22float2(b);
+  out[0] = fa.x; out[1] = fa.y; out[2] = fb.x; out[3] = fb.y;
+}
+
+// scale of a term (per-block power of two of FP16 storage); only FP32 compute is scaled
+__device__ __forceinline__ void scale_by(float &v, float s) { v *= s; }
+__device__ __forceinline__ void scale_by(double &, float) {}
+__device__ __forceinline__ void scale_by(dd &, float) {}
+
+constexpr float kInv4PiF = 0.0795774715459476679f;
+
 // Launch geometry of the block-row kernel (computed on the host).
 struct RowCfg {
   int M, Mp, rp;             // rows of an output tile, rows padded to 4, columns (padded to 16 bytes)
@@ -180,78 +238,116 @@ struct RowCfg {
 };
 
 // One term A X of an output row: A stored [K][Mp] (contraction index major), X stored [K][rp].
-template <class T>
+template <class TS, class TC>
 struct Term {
-  const T *A;
-  const T *X;
+  const TS *A;
+  const TC *X;
   int K;
 };
 
 // Row sources of the block-row kernel.  Every row has count(r) terms; the
 // terms of all rows form one flat sequence (first(r) = flat index of row r's
-// first term, first(nrows) = total), term(e) gives the tiles of flat term e
-// and kdim(e) its contraction length.
+// first term, first(nrows) = total), term(e) gives the tiles of flat term e,
+// kdim(e) its contraction length and scale(e) the power of two its stored A
+// tile was divided by (FP16 storage; 1 otherwise).  kGen rows compute their
+// A tiles in the consumer threads instead of loading them.
 
 // Coupling (Algorithm 3, admissible blocks): row r = cluster row0 + r, terms
 // S_b x^_{s_b} for the admissible blocks b of that row (S_b stored [mu][nu]).
-template <class T>
+template <class TS, class TC>
 struct CouplingRows {
-  const T *S;
+  static constexpr bool kGen = false;
+  const TS *S;
   const int64_t *ptr;
   const int32_t *col;
-  const T *xhat;
+  const TC *xhat;
   int k, kp, rp;
   int64_t row0;
   __device__ int kdim(int64_t) const { return k; }
+  __device__ float scale(int64_t) const { return 1.0f; }
   __device__ int64_t first(int64_t r) const { return ptr[row0 + r] - ptr[row0]; }
-  __device__ Term<T> term(int64_t e) const {
+  __device__ Term<TS, TC> term(int64_t e) const {
     const int64_t b = ptr[row0] + e;
-    return Term<T>{S + b * (int64_t)k * kp, xhat + (int64_t)col[b] * k * rp, k};
+    return Term<TS, TC>{S + b * (int64_t)k * kp, xhat + (int64_t)col[b] * k * rp, k};
   }
+};
+
+// Coupling with S_b regenerated on the fly in FP32 (Eq. (6c)): s_{nu mu} =
+// 1/(4 pi |xi_{t,nu} - xi_{s,mu}|) from the clusters' interpolation boxes
+// (centre c, half width h, Chebyshev nodes c + h t_j); the difference of the
+// centres is formed in FP64 before rounding, so the distance keeps FP32
+// relative accuracy for well-separated small clusters.
+struct CouplingGenRows {
+  static constexpr bool kGen = true;
+  const int64_t *ptr;
+  const int32_t *col;
+  const float *xhat;
+  const double *cen;    // [clusters][3]
+  const float *half;    // [clusters][3]
+  float t[kMaxM];       // reference Chebyshev nodes cos((2j+1) pi / (2m))
+  int m, k, kp, rp;
+  int64_t row0;
+  __device__ int kdim(int64_t) const { return k; }
+  __device__ float scale(int64_t) const { return 1.0f; }
+  __device__ int64_t first(int64_t r) const { return ptr[row0 + r] - ptr[row0]; }
+  __device__ Term<float, float> term(int64_t e) const {
+    const int64_t b = ptr[row0] + e;
+    return Term<float, float>{nullptr, xhat + (int64_t)col[b] * k * rp, k};
+  }
+  __device__ int64_t cluster_of_term(int64_t e) const { return col[ptr[row0] + e]; }
 };
 
 // Leaf forward step (Algorithm 1 on the leaves): row j = leaf j, one term
 // V_j^T x|j (V_j stored [t][nu], padded to kp).
-template <class T>
+template <class TS, class TC>
 struct LeafForwardRows {
-  const T *V;
-  const T *xpad;
+  static constexpr bool kGen = false;
+  const TS *V;
+  const TC *xpad;
+  const float *vscale;   // per leaf, or NULL
   int L, kp, rp;
   __device__ int kdim(int64_t) const { return L; }
+  __device__ float scale(int64_t e) const { return vscale ? vscale[e] : 1.0f; }
   __device__ int64_t first(int64_t r) const { return r; }
-  __device__ Term<T> term(int64_t e) const {
-    return Term<T>{V + e * (int64_t)L * kp, xpad + e * (int64_t)L * rp, L};
+  __device__ Term<TS, TC> term(int64_t e) const {
+    return Term<TS, TC>{V + e * (int64_t)L * kp, xpad + e * (int64_t)L * rp, L};
   }
 };
 
 // Leaf backward step (Algorithm 2 on the leaves): row j = leaf j, one term
 // V_j y^_j (V_j stored transposed [nu][t], padded to Lp).
-template <class T>
+template <class TS, class TC>
 struct LeafBackwardRows {
-  const T *Vt;
-  const T *yhat;
+  static constexpr bool kGen = false;
+  const TS *Vt;
+  const TC *yhat;
+  const float *vscale;
   int k, Lp, rp;
   int64_t leaf0;
   __device__ int kdim(int64_t) const { return k; }
+  __device__ float scale(int64_t e) const { return vscale ? vscale[e] : 1.0f; }
   __device__ int64_t first(int64_t r) const { return r; }
-  __device__ Term<T> term(int64_t e) const {
-    return Term<T>{Vt + e * (int64_t)k * Lp, yhat + (leaf0 + e) * (int64_t)k * rp, k};
+  __device__ Term<TS, TC> term(int64_t e) const {
+    return Term<TS, TC>{Vt + e * (int64_t)k * Lp, yhat + (leaf0 + e) * (int64_t)k * rp, k};
   }
 };
 
 // Nearfield (Algorithm 3, inadmissible blocks): row j = leaf j, terms G_b x|s_b
 // for the inadmissible blocks b of row j (G_b stored transposed [c][t]).
-template <class T>
+template <class TS, class TC>
 struct NearRows {
-  const T *near;
+  static constexpr bool kGen = false;
+  const TS *near;
   const int64_t *ptr;
   const int32_t *col;
-  const T *xpad;
+  const TC *xpad;
+  const float *nscale;   // per block, or NULL
   int L, Lp, rp;
   __device__ int kdim(int64_t) const { return L; }
+  __device__ float scale(int64_t e) const { return nscale ? nscale[e] : 1.0f; }
   __device__ int64_t first(int64_t r) const { return ptr[r]; }
-  __device__ Term<T> term(int64_t e) const {
-    return Term<T>{near + e * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
+  __device__ Term<TS, TC> term(int64_t e) const {
+    return Term<TS, TC>{near + e * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
   }
 };
 
@@ -271,13 +367,13 @@ struct NearRows {
 // the device error word and all warps leave after the copies in flight have
 // landed.  Used for the coupling (rows = clusters), the leaf forward and
 // backward steps and the nearfield (rows = leaves).
-template <class T, int R, class Rows>
+template <class TS, class TC, int R, class Rows>
 __global__ void __launch_bounds__(kThreads + 32, 2)
-    k_blockrow(Rows rows, RowCfg cfg, int64_t nrows, int accumulate, T *__restrict__ out) {
-  using V = typename Vec16<T>::V;
-  constexpr int VN = Vec16<T>::N;
+    k_blockrow(Rows rows, RowCfg cfg, int64_t nrows, int accumulate, TC *__restrict__ out) {
+  using XV = typename Vec16<TC>::V;
+  constexpr int VN = Vec16<TC>::N;
   extern __shared__ __align__(128) unsigned char smem[];
-  T *red = reinterpret_cast<T *>(smem + (size_t)cfg.nst * cfg.stage_bytes);
+  TC *red = reinterpret_cast<TC *>(smem + (size_t)cfg.nst * cfg.stage_bytes);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + cfg.bar_off);
   uint64_t *empty = full + cfg.nst;
   volatile int *abort = reinterpret_cast<volatile int *>(empty + cfg.nst);
@@ -321,10 +417,11 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         const int s = (int)(i % cfg.nst);
         if (i >= cfg.nst && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / cfg.nst - 1) & 1), abort)) break;
         unsigned char *st = smem + (size_t)s * cfg.stage_bytes;
-        const Term<T> tm = rows.term(e);
-        const uint32_t ab = (uint32_t)(sizeof(T) * tm.K * Mp), xb = (uint32_t)(sizeof(T) * tm.K * rp);
+        const Term<TS, TC> tm = rows.term(e);
+        const uint32_t ab = Rows::kGen ? 0u : (uint32_t)(sizeof(TS) * tm.K * Mp);
+        const uint32_t xb = (uint32_t)(sizeof(TC) * tm.K * rp);
         mbar_expect_tx(&full[s], ab + xb);
-        bulk_g2s(st, tm.A, ab, &full[s]);
+        if (!Rows::kGen) bulk_g2s(st, tm.A, ab, &full[s]);
         bulk_g2s(st + cfg.a_bytes, tm.X, xb, &full[s]);
       }
       if (*abort) {
@@ -347,11 +444,16 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
   const int lane_id = tid & 31;
   int64_t e = e_begin;
   for (int64_t r = r_begin; r < r_end; ++r) {
-    T acc[4 * R][VN];
+    TC acc[4 * R][VN];
 #pragma unroll
     for (int a = 0; a < 4 * R; ++a)
 #pragma unroll
-      for (int c = 0; c < VN; ++c) acc[a][c] = zero_of<T>();
+      for (int c = 0; c < VN; ++c) acc[a][c] = zero_of<TC>();
+    // generated coupling: node offsets of this thread's rows in the row cluster
+    float gbase[Rows::kGen ? 4 * R : 1][3];
+    bool gvalid[Rows::kGen ? 4 * R : 1];
+    int64_t grow = 0;
+    if constexpr (Rows::kGen) grow = rows.row0 + r;
     const int64_t e_row_end = rows.first(r + 1);
     for (; e < e_row_end; ++e) {
       const int64_t i = e - e_begin;
@@ -360,28 +462,53 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
       // stage it has not seen filled
       const bool ready = !*abort && mbar_wait_or_abort(&full[s], (uint32_t)((i / cfg.nst) & 1), abort);
       if (ready && active) {
-        const T *sA = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes);
-        const T *sX = reinterpret_cast<const T *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
+        const TS *sA = reinterpret_cast<const TS *>(smem + (size_t)s * cfg.stage_bytes);
+        const TC *sX = reinterpret_cast<const TC *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
         const int K = rows.kdim(e);
         const int kc = (K + cfg.ksplit - 1) / cfg.ksplit;
         const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
+        const float sc = rows.scale(e);
+        float hs[3] = {0.f, 0.f, 0.f};
+        if constexpr (Rows::kGen) {
+          const int64_t sg = rows.cluster_of_term(e);
+          const int m = rows.m;
+#pragma unroll
+          for (int a = 0; a < 4 * R; ++a) {
+            const int nu = (a / 4) * gstride + 4 * vg + (a % 4);
+            gvalid[a] = nu < rows.k;
+            const int jx = nu % m, jy = (nu / m) % m, jz = nu / (m * m);
+            const int jj[3] = {jx, jy, min(jz, m - 1)};
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+              gbase[a][d] = (float)(rows.cen[3 * grow + d] - rows.cen[3 * sg + d]) +
+                            rows.half[3 * grow + d] * rows.t[jj[d]];
+          }
+#pragma unroll
+          for (int d = 0; d < 3; ++d) hs[d] = rows.half[3 * sg + d];
+        }
 #pragma unroll 2
         for (int mu = mu0; mu < mu1; ++mu) {
-          T av[4 * R];
+          TC av[4 * R];
+          if constexpr (Rows::kGen) {
+            const int m = rows.m;
+            const float ox = hs[0] * rows.t[mu % m], oy = hs[1] * rows.t[(mu / m) % m], oz = hs[2] * rows.t[mu / (m * m)];
 #pragma unroll
-          for (int g = 0; g < R; ++g) {
-            const V *ap = reinterpret_cast<const V *>(sA + mu * Mp + g * gstride + 4 * vg);
-#pragma unroll
-            for (int q = 0; q < 4 / VN; ++q) {
-              const V v = ap[q];
-#pragma unroll
-              for (int l = 0; l < VN; ++l) av[4 * g + q * VN + l] = lane<T>(v, l);
+            for (int a = 0; a < 4 * R; ++a) {
+              const float dx = gbase[a][0] - ox, dy = gbase[a][1] - oy, dz = gbase[a][2] - oz;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              av[a] = gvalid[a] ? kInv4PiF * rsqrtf(r2) : 0.0f;
             }
-          }
-          const V xv = *reinterpret_cast<const V *>(sX + mu * rp + VN * cg);
-          T xs[VN];
+          } else {
 #pragma unroll
-          for (int l = 0; l < VN; ++l) xs[l] = lane<T>(xv, l);
+            for (int g = 0; g < R; ++g) load4<TS, TC>(sA + mu * Mp + g * gstride + 4 * vg, av + 4 * g);
+          }
+          const XV xv = *reinterpret_cast<const XV *>(sX + mu * rp + VN * cg);
+          TC xs[VN];
+#pragma unroll
+          for (int l = 0; l < VN; ++l) {
+            xs[l] = lane<TC>(xv, l);
+            scale_by(xs[l], sc);
+          }
 #pragma unroll
           for (int a = 0; a < 4 * R; ++a)
 #pragma unroll
@@ -405,10 +532,10 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
           red[((int64_t)ks * Mp + (a / 4) * gstride + 4 * vg + (a % 4)) * rp + VN * cg + c] = acc[a][c];
     }
     named_sync(ncons);
-    T *o = out + r * (int64_t)cfg.M * rp;
+    TC *o = out + r * (int64_t)cfg.M * rp;
     for (int q = tid; q < cfg.M * rp; q += ncons) {
       const int nu = q / rp, c = q - nu * rp;
-      T sum = accumulate ? o[q] : zero_of<T>();
+      TC sum = accumulate ? o[q] : zero_of<TC>();
       for (int z = 0; z < cfg.ksplit; ++z) sum = sum + red[((int64_t)z * Mp + nu) * rp + c];
       o[q] = sum;
     }
@@ -420,8 +547,8 @@ constexpr size_t kSmemMax = 227 * 1024;
 
 // geometry for output tiles M x rp and contraction lengths up to Kmax;
 // threads: the number of threads the kernel is launched with
-template <class T>
-int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, RowCfg &cfg) {
+template <class TS, class T>
+int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, bool gen, RowCfg &cfg) {
   constexpr int VN = Vec16<T>::N;
   cfg.M = M;
   cfg.Mp = Mp;
@@ -431,7 +558,7 @@ int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, RowCfg &cfg) {
   cfg.tiles = cfg.nvg * cfg.ncg;
   if (cfg.tiles > threads) return fail(H2_EINVAL, "tile rows x right-hand sides too large for one CTA");
   cfg.ksplit = std::max(1, std::min(threads / cfg.tiles, Kmax));
-  cfg.a_bytes = (uint32_t)(sizeof(T) * Kmax * Mp);
+  cfg.a_bytes = gen ? 0u : (uint32_t)((sizeof(TS) * Kmax * Mp + 15) / 16 * 16);
   cfg.stage_bytes = cfg.a_bytes + (uint32_t)(sizeof(T) * Kmax * rp);
   const size_t red = sizeof(T) * (size_t)cfg.ksplit * Mp * rp;   // slice sums, after the ring
   // stages: up to 8, sized so that 512 consumer threads per SM stay resident when possible
@@ -446,7 +573,7 @@ int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, RowCfg &cfg) {
   return H2_OK;
 }
 
-// row groups per register tile: two for FP32 when the rows split evenly
+// row groups per register tile: two for FP32 compute when the rows split evenly
 template <class T>
 inline int row_groups(int Mp) {
   return (sizeof(T) == 4 && Mp % 8 == 0) ? 2 : 1;
@@ -495,33 +622,35 @@ struct Marks {
 };
 
 // persistent launch: as many CTAs as stay resident, at most one per row
-template <class T, int R, class Rows>
-int launch_rows_r(const Rows &rows, const RowCfg &cfg, int threads, int64_t nrows, int accumulate, T *out,
+template <class TS, class TC, int R, class Rows>
+int launch_rows_r(const Rows &rows, const RowCfg &cfg, int threads, int64_t nrows, int accumulate, TC *out,
                   cudaStream_t st) {
-  const void *fn = (const void *)k_blockrow<T, R, Rows>;
+  const void *fn = (const void *)k_blockrow<TS, TC, R, Rows>;
   const size_t sm = cfg.bar_off + 16 * cfg.nst + 16;
   threads += 32;   // the producer warp
   int rc;
-  if ((rc = set_smem<T>(fn, sm))) return rc;
+  if ((rc = set_smem<TC>(fn, sm))) return rc;
   int per_sm = 0, dev = 0, sms = 0;
   H2_CUDA_TRY(cudaGetDevice(&dev));
   H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   H2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm));
   if (per_sm < 1) return fail(H2_EINVAL, "block-row kernel cannot be resident");
   const int64_t grid = std::min<int64_t>(nrows, (int64_t)per_sm * sms);
-  k_blockrow<T, R, Rows><<<(unsigned)grid, threads, sm, st>>>(rows, cfg, nrows, accumulate, out);
+  k_blockrow<TS, TC, R, Rows><<<(unsigned)grid, threads, sm, st>>>(rows, cfg, nrows, accumulate, out);
   return H2_OK;
 }
 
-template <class T, class Rows>
-int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int R, int64_t nrows, int accumulate, T *out,
+template <class TS, class TC, class Rows>
+int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int R, int64_t nrows, int accumulate, TC *out,
                 cudaStream_t st) {
   if (nrows <= 0) return H2_OK;
-  if (R == 2) return launch_rows_r<T, 2>(rows, cfg, threads, nrows, accumulate, out, st);
-  return launch_rows_r<T, 1>(rows, cfg, threads, nrows, accumulate, out, st);
+  if (R == 2) return launch_rows_r<TS, TC, 2>(rows, cfg, threads, nrows, accumulate, out, st);
+  return launch_rows_r<TS, TC, 1>(rows, cfg, threads, nrows, accumulate, out, st);
 }
 
-template <class T, class Tio>
+// TS: storage type of V, E, S and the nearfield; T: arithmetic and vector
+// type; Tio: type of the caller's x and y.
+template <class TS, class T, class Tio>
 int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
@@ -529,18 +658,19 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   const int rp = padded_rhs(nrhs, sizeof(T));   // every kernel below works on rp columns
   const int64_t leaf0 = d.nleaf - 1;
   T *xpad = (T *)d.xpad, *ypad = (T *)d.ypad, *xhat = (T *)d.xhat, *yhat = (T *)d.yhat;
-  const bool far = lmin <= D;
+  const bool far = lmin <= D, gen = d.coupling == 1;
   int rc;
   RowCfg cf_fwd{}, cf_cpl{}, cf_back{}, cf_near{};
   const int Rk = row_groups<T>(kp), RL = row_groups<T>(Lp);
   const int t_fwd = row_threads(kp, rp, L, sizeof(T), Rk), t_cpl = row_threads(kp, rp, k, sizeof(T), Rk);
   const int t_back = row_threads(Lp, rp, k, sizeof(T), RL), t_near = row_threads(Lp, rp, L, sizeof(T), RL);
   if (far) {
-    if ((rc = row_cfg<T>(k, kp, rp, L, t_fwd, Rk, cf_fwd))) return rc;
-    if ((rc = row_cfg<T>(k, kp, rp, k, t_cpl, Rk, cf_cpl))) return rc;
-    if ((rc = row_cfg<T>(L, Lp, rp, k, t_back, RL, cf_back))) return rc;
+    if ((rc = row_cfg<TS, T>(k, kp, rp, L, t_fwd, Rk, false, cf_fwd))) return rc;
+    if ((rc = row_cfg<TS, T>(k, kp, rp, k, t_cpl, Rk, gen, cf_cpl))) return rc;
+    if ((rc = row_cfg<TS, T>(L, Lp, rp, k, t_back, RL, false, cf_back))) return rc;
   }
-  if ((rc = row_cfg<T>(L, Lp, rp, L, t_near, RL, cf_near))) return rc;
+  if ((rc = row_cfg<TS, T>(L, Lp, rp, L, t_near, RL, false, cf_near))) return rc;
+  const float *vscale = (const float *)d.vscale, *nscale = (const float *)d.nscale;
   Marks mk(c);
 
   mk.mark(H2_PH_PERMUTE_IN);
@@ -548,46 +678,67 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
   if (far) {
-    LeafForwardRows<T> rows{(const T *)d.V, xpad, L, kp, rp};
-    if ((rc = launch_rows<T>(rows, cf_fwd, t_fwd, Rk, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
+    LeafForwardRows<TS, T> rows{(const TS *)d.V, xpad, vscale, L, kp, rp};
+    if ((rc = launch_rows<TS, T>(rows, cf_fwd, t_fwd, Rk, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
     mk.count(H2_PH_LEAF_FORWARD);
   }
   mk.mark(H2_PH_UPWARD);
   if (far) {
     size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
-    if ((rc = set_smem<T>((const void *)k_upward<T>, sm))) return rc;
+    if ((rc = set_smem<T>((const void *)k_upward<TS, T>, sm))) return rc;
     for (int l = D - 1; l >= lmin; --l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
-      k_upward<T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, rp, par0, xhat);
+      k_upward<TS, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TS *)d.Ef, m, k, rp, par0, xhat);
       mk.count(H2_PH_UPWARD);
     }
   }
   mk.mark(H2_PH_COUPLING);
   if (far) {
     int64_t row0 = ((int64_t)1 << lmin) - 1;
-    CouplingRows<T> rows{(const T *)d.S, d.adm_ptr, d.adm_col, xhat, k, kp, rp, row0};
-    if ((rc = launch_rows<T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, yhat + row0 * (int64_t)k * rp, st))) return rc;
+    T *out = yhat + row0 * (int64_t)k * rp;
+    if (gen) {
+      if constexpr (std::is_same<T, float>::value) {
+        CouplingGenRows rows{};
+        rows.ptr = d.adm_ptr;
+        rows.col = d.adm_col;
+        rows.xhat = xhat;
+        rows.cen = d.icen;
+        rows.half = d.ihalf;
+        for (int j = 0; j < kMaxM; ++j) rows.t[j] = j < m ? (float)std::cos((2 * j + 1) * 3.14159265358979323846 / (2.0 * m)) : 0.f;
+        rows.m = m;
+        rows.k = k;
+        rows.kp = kp;
+        rows.rp = rp;
+        rows.row0 = row0;
+        if ((rc = launch_rows<float, T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, out, st))) return rc;
+      } else {
+        return fail(H2_EINVAL, "the regenerated coupling runs in FP32 arithmetic only");
+      }
+    } else {
+      CouplingRows<TS, T> rows{(const TS *)d.S, d.adm_ptr, d.adm_col, xhat, k, kp, rp, row0};
+      if ((rc = launch_rows<TS, T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, out, st))) return rc;
+    }
     mk.count(H2_PH_COUPLING);
   }
   mk.mark(H2_PH_DOWNWARD);
   if (far) {
     size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
-    if ((rc = set_smem<T>((const void *)k_downward<T>, sm))) return rc;
+    if ((rc = set_smem<T>((const void *)k_downward<TS, T>, sm))) return rc;
     for (int l = lmin; l < D; ++l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
-      k_downward<T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const T *)d.Ef, m, k, rp, par0, yhat);
+      k_downward<TS, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TS *)d.Ef, m, k, rp, par0, yhat);
       mk.count(H2_PH_DOWNWARD);
     }
   }
   mk.mark(H2_PH_LEAF_NEAR);
   if (far) {
-    LeafBackwardRows<T> rows{(const T *)d.Vt, yhat, k, Lp, rp, leaf0};
-    if ((rc = launch_rows<T>(rows, cf_back, t_back, RL, d.nleaf, 0, ypad, st))) return rc;
+    LeafBackwardRows<TS, T> rows{(const TS *)d.Vt, yhat, vscale, k, Lp, rp, leaf0};
+    if ((rc = launch_rows<TS, T>(rows, cf_back, t_back, RL, d.nleaf, 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
   {
-    NearRows<T> rows{(const T *)d.near, d.near_ptr, d.near_col, xpad, L, Lp, rp};
-    if ((rc = launch_rows<T>(rows, cf_near, t_near, RL, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
+    NearRows<TS, T> rows{(const TS *)d.near, d.near_ptr, d.near_col, xpad, nscale, L, Lp, rp};
+    if ((rc = launch_rows<TS, T>(rows, cf_near, t_near, RL, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
   mk.mark(H2_PH_PERMUTE_OUT);
@@ -646,10 +797,20 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64) {
     return fail(H2_EINVAL, "k * nrhs and leaf_max * nrhs (nrhs padded to 16 bytes) must not exceed 4096");
   int rc = ensure_work(c, nrhs);
   if (rc) return rc;
-  if (d.prec == H2_F64) return matvec_typed<dd, double>(c, (const double *)x, (double *)y, nrhs);
-  if (d.prec == H2_F64_NATIVE) return matvec_typed<double, double>(c, (const double *)x, (double *)y, nrhs);
-  if (io64) return matvec_typed<float, double>(c, (const double *)x, (double *)y, nrhs);
-  return matvec_typed<float, float>(c, (const float *)x, (float *)y, nrhs);
+  switch (d.prec) {
+    case H2_F64: return matvec_typed<dd, dd, double>(c, (const double *)x, (double *)y, nrhs);
+    case H2_F64_NATIVE: return matvec_typed<double, double, double>(c, (const double *)x, (double *)y, nrhs);
+    case H2_F32:
+      if (io64) return matvec_typed<float, float, double>(c, (const double *)x, (double *)y, nrhs);
+      return matvec_typed<float, float, float>(c, (const float *)x, (float *)y, nrhs);
+    case H2_BF16:
+      if (io64) return matvec_typed<__nv_bfloat16, float, double>(c, (const double *)x, (double *)y, nrhs);
+      return matvec_typed<__nv_bfloat16, float, float>(c, (const float *)x, (float *)y, nrhs);
+    case H2_F16:
+      if (io64) return matvec_typed<__half, float, double>(c, (const double *)x, (double *)y, nrhs);
+      return matvec_typed<__half, float, float>(c, (const float *)x, (float *)y, nrhs);
+    default: return fail(H2_EINVAL, "unknown precision");
+  }
 }
 
 }  // namespace h2

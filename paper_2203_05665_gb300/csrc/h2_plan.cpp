@@ -187,12 +187,16 @@ int make_plan(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, in
   // widened for interpolation only
   int m = p.m;
   p.cheb.assign(p.nclu * 3 * m, 0.0);
+  p.icen.assign(p.nclu * 3, 0.0);
+  p.ihalf.assign(p.nclu * 3, 0.0);
   for (int64_t c = 0; c < p.nclu; ++c) {
     double ext[3], emax = 0;
     for (int d = 0; d < 3; ++d) { ext[d] = p.hi[3 * c + d] - p.lo[3 * c + d]; emax = std::max(emax, ext[d]); }
     for (int d = 0; d < 3; ++d) {
       double mid = 0.5 * (p.lo[3 * c + d] + p.hi[3 * c + d]);
       double hw = (ext[d] <= 1e-12 * emax) ? 1e-6 * emax : 0.5 * ext[d];
+      p.icen[3 * c + d] = mid;
+      p.ihalf[3 * c + d] = hw;
       for (int j = 0; j < m; ++j) p.cheb[(3 * c + d) * m + j] = mid + hw * std::cos((2 * j + 1) * kPi / (2.0 * m));
     }
   }

@@ -14,6 +14,11 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+
 #include "h2_dd.cuh"
 #include "h2_internal.hpp"
 
@@ -232,10 +237,49 @@ __global__ void k_near_singular(Geo g, const int64_t *__restrict__ sing, int64_t
   }
 }
 
+// rounding of an FP64 value to the stored type
+template <class T>
+__device__ __forceinline__ T store_as(double v) {
+  return from_double<T>(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16>(double v) {
+  return __double2bfloat16(v);
+}
+template <>
+__device__ __forceinline__ __half store_as<__half>(double v) {
+  return __double2half(v);
+}
+
 template <class T>
 __global__ void k_convert(const double *__restrict__ src, T *__restrict__ dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = from_double<T>(src[i]);
+    dst[i] = store_as<T>(src[i]);
+}
+
+// per nearfield block: the power of two 2^e >= max |entry| (1 for an all-zero block)
+__global__ void k_block_scale(const double *__restrict__ near, int64_t per, int64_t nblk, float *__restrict__ scale) {
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < per; i += blockDim.x) mx = fmax(mx, fabs(near[b * per + i]));
+    __shared__ double part[256];
+    part[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) part[threadIdx.x] = fmax(part[threadIdx.x], part[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) scale[b] = part[0] > 0.0 ? (float)exp2(ceil(log2(part[0]))) : 1.0f;
+    __syncthreads();
+  }
+}
+
+// stored = value / scale (exact: a power of two) in the stored type
+template <class T>
+__global__ void k_convert_scaled(const double *__restrict__ src, const float *__restrict__ scale, int64_t per,
+                                 T *__restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = store_as<T>(scale ? src[i] / (double)scale[i / per] : src[i]);
 }
 
 int grid_for(int64_t n, int threads) {
@@ -243,6 +287,14 @@ int grid_for(int64_t n, int threads) {
   if (g < 1) g = 1;
   if (g > 152 * 64) g = 152 * 64;
   return (int)g;
+}
+
+template <class T>
+int upload_converted(Dev &d, void **dst, const std::vector<double> &src, cudaStream_t st);
+
+template <class T>
+constexpr bool is_half_type() {
+  return std::is_same<T, __nv_bfloat16>::value || std::is_same<T, __half>::value;
 }
 
 template <class T>
@@ -291,6 +343,20 @@ int build_typed(Ctx &c) {
       }
   }
   int rc;
+  if (std::is_same<T, __half>::value) {
+    // FP16: divide every leaf basis by a power of two >= its largest entry
+    std::vector<float> vs(p.nleaf, 1.0f);
+    for (int64_t j = 0; j < p.nleaf; ++j) {
+      double mx = 0.0;
+      for (int64_t q = j * L * kp; q < (j + 1) * L * kp; ++q) mx = std::max(mx, std::fabs(Vp[q]));
+      const double sc = mx > 0.0 ? std::exp2(std::ceil(std::log2(mx))) : 1.0;
+      vs[j] = (float)sc;
+      for (int64_t q = j * L * kp; q < (j + 1) * L * kp; ++q) Vp[q] /= sc;
+      for (int64_t q = j * k * Lp; q < (j + 1) * k * Lp; ++q) Vt[q] /= sc;
+    }
+    if ((rc = dev_alloc(d, (void **)&d.vscale, vs.size() * 4))) return rc;
+    H2_CUDA_TRY(cudaMemcpyAsync(d.vscale, vs.data(), vs.size() * 4, cudaMemcpyHostToDevice, st));
+  }
   if ((rc = dev_alloc(d, (void **)&d.pad_src, pad.size() * 4))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(d.pad_src, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, st));
   if ((rc = upload_converted<T>(d, &d.V, Vp, st))) return rc;
@@ -308,6 +374,15 @@ int build_typed(Ctx &c) {
     H2_CUDA_TRY(cudaMemcpyAsync(d.near_col, p.near_col.data(), p.near_col.size() * 4, cudaMemcpyHostToDevice, st));
   if ((rc = dev_alloc(d, (void **)&d.cheb, p.cheb.size() * 8))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(d.cheb, p.cheb.data(), p.cheb.size() * 8, cudaMemcpyHostToDevice, st));
+  if (d.coupling == 1) {
+    // regenerated coupling: interpolation-box centres (FP64) and half widths (FP32)
+    std::vector<float> hw(p.ihalf.begin(), p.ihalf.end());
+    if ((rc = dev_alloc(d, (void **)&d.icen, p.icen.size() * 8))) return rc;
+    H2_CUDA_TRY(cudaMemcpyAsync(d.icen, p.icen.data(), p.icen.size() * 8, cudaMemcpyHostToDevice, st));
+    if ((rc = dev_alloc(d, (void **)&d.ihalf, hw.size() * 4))) return rc;
+    H2_CUDA_TRY(cudaMemcpyAsync(d.ihalf, hw.data(), hw.size() * 4, cudaMemcpyHostToDevice, st));
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+  }
 
   // temporary geometry for the set-up kernels
   std::vector<int32_t> arow(p.adm_col.size()), nrow(p.near_col.size()), ncol(p.near_col.size());
@@ -340,16 +415,26 @@ int build_typed(Ctx &c) {
   H2_CUDA_TRY(cudaMemcpyToSymbolAsync(c_gx, gx.data(), gx.size() * 8, 0, cudaMemcpyHostToDevice, st));
   H2_CUDA_TRY(cudaMemcpyToSymbolAsync(c_gw, gw.data(), gw.size() * 8, 0, cudaMemcpyHostToDevice, st));
 
-  // coupling matrices
-  if ((rc = dev_alloc(d, &d.S, std::max<size_t>(1, (size_t)d.nadm * k * d.kp) * sizeof(T)))) return rc;
-  if (d.nadm > 0) {
+  // coupling matrices (stored mode)
+  if (d.coupling == 0 && (rc = dev_alloc(d, &d.S, std::max<size_t>(1, (size_t)d.nadm * k * d.kp) * sizeof(T))))
+    return rc;
+  if (d.coupling == 0 && d.nadm > 0) {
     k_coupling_fill<T><<<grid_for(d.nadm * k * d.kp, 256), 256, 0, st>>>((const int32_t *)t_arow.ptr, d.adm_col,
                                                                           d.cheb, m, d.kp, d.nadm, (T *)d.S);
     H2_CUDA_TRY(cudaGetLastError());
   }
 
-  // nearfield entries
+  // nearfield entries; 16-bit storage: computed in FP64 first, then rounded
+  // (FP16: with a power-of-two scale per block)
   if ((rc = dev_alloc(d, &d.near, std::max<size_t>(1, (size_t)d.nnear * L * Lp) * sizeof(T)))) return rc;
+  Tmp t_near64;
+  using TQ = typename std::conditional<is_half_type<T>(), double, T>::type;
+  TQ *qnear = (TQ *)d.near;
+  if (is_half_type<T>()) {
+    if (cudaMalloc(&t_near64.ptr, std::max<size_t>(1, (size_t)d.nnear * L * Lp) * 8) != cudaSuccess)
+      return fail(H2_ENOMEM, "nearfield staging buffer");
+    qnear = (TQ *)t_near64.ptr;
+  }
   if (d.nnear > 0) {
     // pairs that share a vertex: at most (n * 3 * valence) ordered pairs; bound by the entry count
     int64_t cap = std::min<int64_t>(d.nnear * L * Lp, 64 * p.n + 1024);
@@ -358,16 +443,26 @@ int build_typed(Ctx &c) {
     H2_CUDA_TRY(cudaMemsetAsync(t_cnt.ptr, 0, 8, st));
     Geo g{(const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src,
           (const int32_t *)t_nrow.ptr, (const int32_t *)t_ncol.ptr, L, Lp};
-    k_near_regular<T><<<grid_for(d.nnear * L * Lp, 128), 128, 0, st>>>(
-        g, d.nnear, c.quad_order, (T *)d.near, (int64_t *)t_sing.ptr, (unsigned long long *)t_cnt.ptr, cap);
+    k_near_regular<TQ><<<grid_for(d.nnear * L * Lp, 128), 128, 0, st>>>(
+        g, d.nnear, c.quad_order, qnear, (int64_t *)t_sing.ptr, (unsigned long long *)t_cnt.ptr, cap);
     H2_CUDA_TRY(cudaGetLastError());
     unsigned long long ns = 0;
     H2_CUDA_TRY(cudaMemcpyAsync(&ns, t_cnt.ptr, 8, cudaMemcpyDeviceToHost, st));
     H2_CUDA_TRY(cudaStreamSynchronize(st));
     if ((int64_t)ns > cap) return fail(H2_EINVAL, "mesh has more vertex-sharing pairs than supported");
     if (ns > 0) {
-      k_near_singular<T><<<grid_for((int64_t)ns, 64), 64, 0, st>>>(g, (const int64_t *)t_sing.ptr, (int64_t)ns,
-                                                                   c.quad_order, (T *)d.near);
+      k_near_singular<TQ><<<grid_for((int64_t)ns, 64), 64, 0, st>>>(g, (const int64_t *)t_sing.ptr, (int64_t)ns,
+                                                                    c.quad_order, qnear);
+      H2_CUDA_TRY(cudaGetLastError());
+    }
+    if (is_half_type<T>()) {
+      const int64_t per = L * Lp, tot = d.nnear * per;
+      if (std::is_same<T, __half>::value) {
+        if ((rc = dev_alloc(d, (void **)&d.nscale, d.nnear * 4))) return rc;
+        k_block_scale<<<(unsigned)std::min<int64_t>(d.nnear, 152 * 32), 256, 0, st>>>((const double *)qnear, per,
+                                                                                      d.nnear, d.nscale);
+      }
+      k_convert_scaled<T><<<grid_for(tot, 256), 256, 0, st>>>((const double *)qnear, d.nscale, per, (T *)d.near, tot);
       H2_CUDA_TRY(cudaGetLastError());
     }
   }
@@ -395,7 +490,10 @@ int device_build(Ctx &c) {
   if (c.quad_order < 1 || c.quad_order > kMaxQ) return fail(H2_EINVAL, "quad_order must be in [1, 16]");
   d.m = p.m;
   d.k = p.k;
-  d.kp = (p.k + 3) / 4 * 4;
+  // stored rows are padded to 16 bytes for 16-bit storage, else to 4 entries
+  d.ssize = d.prec == H2_F32 ? 4 : (d.prec == H2_BF16 || d.prec == H2_F16) ? 2 : 8;
+  const int rowpad = d.ssize == 2 ? 8 : 4;
+  d.kp = (p.k + rowpad - 1) / rowpad * rowpad;
   d.depth = p.depth;
   d.first_adm_level = p.first_adm_level;
   d.n = p.n;
@@ -403,19 +501,23 @@ int device_build(Ctx &c) {
   d.nleaf = p.nleaf;
   d.lmax = p.lmax;
   d.npad = p.nleaf * p.lmax;
-  d.lp = (p.lmax + 3) / 4 * 4;
+  d.lp = (p.lmax + rowpad - 1) / rowpad * rowpad;
   d.nadm = (int64_t)p.adm_col.size();
   d.nnear = (int64_t)p.near_col.size();
-  if (d.prec == H2_F64) {
-    d.esize = 8;
-    return build_typed<dd>(c);
+  if (d.coupling < 0) {
+    // automatic: store S unless it would take more than half of the free memory (FP32 only)
+    size_t fr = 0, tot = 0;
+    H2_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    const double sbytes = (double)d.nadm * d.k * d.kp * d.ssize;
+    d.coupling = (d.prec == H2_F32 && sbytes > 0.5 * (double)fr) ? 1 : 0;
   }
-  if (d.prec == H2_F64_NATIVE) {
-    d.esize = 8;
-    return build_typed<double>(c);
+  switch (d.prec) {
+    case H2_F64: d.esize = 8; return build_typed<dd>(c);
+    case H2_F64_NATIVE: d.esize = 8; return build_typed<double>(c);
+    case H2_BF16: d.esize = 4; return build_typed<__nv_bfloat16>(c);
+    case H2_F16: d.esize = 4; return build_typed<__half>(c);
+    default: d.esize = 4; return build_typed<float>(c);
   }
-  d.esize = 4;
-  return build_typed<float>(c);
 }
 
 }  // namespace h2

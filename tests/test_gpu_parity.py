@@ -15,7 +15,9 @@ from paper_2203_05665_gb300 import H2Matrix, colmajor, inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-6, "f64n": 1e-12}   # f64: double-float arithmetic; f64n: native FP64
+# f64: double-float arithmetic; f64n: native FP64; bf16 / f16: 16-bit storage with FP32
+# accumulation and the coupling regenerated in FP32 (relative error budget 2e-3)
+TOL = {"f64": 1e-12, "f32": 1e-6, "f64n": 1e-12, "bf16": 2e-3, "f16": 2e-3}
 
 
 def _rel(a, b):
@@ -48,12 +50,15 @@ def _oracle(name):
     return _oracles[name]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64n"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64n", "f32-regen", "bf16", "f16"])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_matvec_matches_oracle(require_gpu, name, prec):
     v, f, o = _oracle(name)
     make, leaf, eta, m = CASES[name]
-    h = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec=prec)
+    coupling = "regen" if prec == "f32-regen" else "auto"
+    prec = "f32" if prec == "f32-regen" else prec
+    h = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec=prec, coupling=coupling)
+    assert h.stats["coupling"] == (2 if coupling == "regen" or prec in ("bf16", "f16") else 1)
     assert h.stats["adm_blocks"] == o.nadm and h.stats["near_blocks"] == o.nnear
     n = f.shape[0]
     nrhs_list = [1, 3, 16] if m ** 3 * 16 <= 4096 else [1, 3]
@@ -194,3 +199,42 @@ def test_gmres_ir_reaches_1e8(require_gpu):
     assert _rel(z, z64) <= 1e-5
     hi.close()
     lo.close()
+
+
+@pytest.mark.parametrize("lo_prec", ["bf16", "f16"])
+def test_gmres_ir_16bit_inner_reaches_1e8(require_gpu, lo_prec):
+    """16-bit storage, FP32 accumulation and regenerated coupling inside,
+    FP64-accurate refinement outside."""
+    v, f, o = _oracle("ico4_m3")
+    hi = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec="f64")
+    lo = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec=lo_prec)
+    b = I.uniform_rhs(f.shape[0], 4, 1004)
+    z, it, rel, st = hi.solve_ir(lo, b, rtol=1e-8, inner_rtol=1e-2, restart=30)
+    assert st == 0 and np.all(rel <= 1e-8)
+    r = b - o.matvec(z)
+    assert np.all(np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0) <= 1.5e-8)
+    hi.close()
+    lo.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_full_size_mixed_precision_sampled_rows(require_gpu, prec):
+    """Icosphere level 8 (1,310,720 triangles), m = 3, 4 right-hand sides,
+    16-bit storage and FP32 regenerated coupling: sampled rows against the
+    oracle within the 16-bit budget."""
+    import torch
+    v, f = I.icosphere(8)
+    n = f.shape[0]
+    x = I.uniform_rhs(n, 4, 1003)
+    h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec=prec)
+    assert h.stats["depth"] == 16 and h.stats["coupling"] == 2
+    xd = colmajor(torch.from_numpy(x).to(device="cuda", dtype=torch.float32))
+    yd = colmajor(torch.empty_like(xd))
+    h.matvec(xd, yd)
+    y = yd.cpu().double().numpy()
+    h.close()
+    if "l8" not in _full:
+        _full["l8"] = oracle.Oracle(v, f, leaf_size=32, eta=2.0, order=3, store_near=False)
+    rows = np.random.default_rng(6).choice(n, 40, replace=False)
+    ref = _full["l8"].matvec_rows(x, rows)
+    assert _rel(y[rows], ref) <= TOL[prec]

@@ -652,6 +652,8 @@ int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int R, int64_t
 // type; Tio: type of the caller's x and y.
 template <class TS, class T, class Tio>
 int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
+  // transfer factors: FP32 under bfloat16 storage (see the set-up)
+  using TE = typename std::conditional<std::is_same<TS, __nv_bfloat16>::value, float, TS>::type;
   Dev &d = c.d;
   cudaStream_t st = c.stream;
   const int k = d.k, kp = d.kp, m = d.m, L = (int)d.lmax, Lp = (int)d.lp, D = d.depth, lmin = d.first_adm_level;
@@ -685,10 +687,10 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.mark(H2_PH_UPWARD);
   if (far) {
     size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
-    if ((rc = set_smem<T>((const void *)k_upward<TS, T>, sm))) return rc;
+    if ((rc = set_smem<T>((const void *)k_upward<TE, T>, sm))) return rc;
     for (int l = D - 1; l >= lmin; --l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
-      k_upward<TS, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TS *)d.Ef, m, k, rp, par0, xhat);
+      k_upward<TE, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TE *)d.Ef, m, k, rp, par0, xhat);
       mk.count(H2_PH_UPWARD);
     }
   }
@@ -723,10 +725,10 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.mark(H2_PH_DOWNWARD);
   if (far) {
     size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
-    if ((rc = set_smem<T>((const void *)k_downward<TS, T>, sm))) return rc;
+    if ((rc = set_smem<T>((const void *)k_downward<TE, T>, sm))) return rc;
     for (int l = lmin; l < D; ++l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
-      k_downward<TS, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TS *)d.Ef, m, k, rp, par0, yhat);
+      k_downward<TE, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TE *)d.Ef, m, k, rp, par0, yhat);
       mk.count(H2_PH_DOWNWARD);
     }
   }

@@ -256,6 +256,10 @@ def run_ours(args):
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, local, stream)
 
+    mixed = None
+    if rank == 0 and not args.no_mixed:
+        mixed = run_mixed(args, local, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args)
@@ -281,6 +285,7 @@ def run_ours(args):
         "finite": finite,
         "solve": solve,
         "serve": serve,
+        "mixed": mixed,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -363,6 +368,56 @@ def run_serve(args, local, stream):
     return out
 
 
+def run_mixed(args, local, stream):
+    """Mixed precision on icosphere level 8 (m = 3, 4 RHS): V and nearfield in
+    BF16 or FP16 with FP32 accumulation, coupling regenerated in FP32; product
+    time and error against the FP64-accurate product, and GMRES-IR to 1e-8
+    (inner GMRES(30) on the 16-bit handle to 1e-2, FP64-accurate residuals)."""
+    import torch
+    from paper_2203_05665_gb300 import H2Matrix, colmajor, inputs
+    v, f = inputs.icosphere(args.mixed_level)
+    n = f.shape[0]
+    x_np = inputs.uniform_rhs(n, 4, 1003)
+    hi = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec="f64", device=local, stream=stream.cuda_stream)
+    xd = colmajor(torch.from_numpy(x_np).to(device="cuda", dtype=torch.float64))
+    yref = colmajor(torch.empty_like(xd))
+    hi.matvec(xd, yref)
+    out = {"workload": f"icosphere L{args.mixed_level} ({n} triangles), m=3, leaf 32, eta 2, 4 RHS",
+           "hi": "f64 (double-float), stored S"}
+    for prec in ("bf16", "f16"):
+        lo = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec=prec, device=local, stream=stream.cuda_stream)
+        xf = colmajor(xd.float())
+        yf = colmajor(torch.empty_like(xf))
+        for _ in range(3):
+            lo.matvec(xf, yf)
+        lo.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        reps = 20
+        for _ in range(reps):
+            lo.matvec(xf, yf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ph, prods = lo.phase_times()
+        lo.profile(False)
+        err = float(torch.linalg.norm(yf.double() - yref) / torch.linalg.norm(yref))
+        t = time.perf_counter()
+        z, it, rel, st = hi.solve_ir(lo, x_np, rtol=1e-8, inner_rtol=1e-2, restart=30, maxit_inner=5000,
+                                     maxit_outer=50)
+        ts = time.perf_counter() - t
+        out[prec] = {"matvec_ms": ms, "dof_per_s": n * 4 / (ms * 1e-3), "rel_err_vs_f64": err,
+                     "phases_ms": {k: vv[0] / prods for k, vv in ph.items()},
+                     "device_bytes": lo.stats["device_bytes"],
+                     "ir_solve_s": ts, "ir_solves_per_s": 4 / ts, "ir_inner_iters": [int(i) for i in it],
+                     "ir_max_relres": float(max(rel)), "ir_status": int(st)}
+        lo.close()
+    out["hi_device_bytes"] = hi.stats["device_bytes"]
+    hi.close()
+    return out
+
+
 def _oracle_sample(level, order, nrhs):
     import oracle
     from paper_2203_05665_gb300 import inputs
@@ -430,6 +485,8 @@ def main():
     ap.add_argument("--solve-nrhs", type=int, default=16)
     ap.add_argument("--solve-reps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-level", type=int, default=8)
     ap.add_argument("--serve-full", action="store_true", help="all 8 geometries (icosphere L4-L8, ...)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=200.0)

@@ -26,7 +26,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 static void free_dev(Dev &d) {
-  void *ptrs[] = {d.icen, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
+  void *ptrs[] = {d.icen, d.adm_dc, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
                   d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
   for (void *p : ptrs)
     if (p) cudaFree(p);

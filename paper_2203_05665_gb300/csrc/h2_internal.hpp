@@ -77,6 +77,7 @@ struct Dev {
   int32_t *near_col = nullptr;  // leaf-local
   double *cheb = nullptr;       // nclu x 3 x m (FP64 always)
   double *icen = nullptr;       // nclu x 3 interpolation-box centres (regenerated coupling)
+  float *adm_dc = nullptr;      // nadm x 4: centre of the row cluster minus centre of the column cluster
   float *ihalf = nullptr;       // nclu x 3 interpolation-box half widths
   float *vscale = nullptr;      // per leaf: power of two dividing the stored V (FP16), or NULL
   float *nscale = nullptr;      // per nearfield block: the same for G_b, or NULL

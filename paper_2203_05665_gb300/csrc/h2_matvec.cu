@@ -282,7 +282,7 @@ struct CouplingGenRows {
   const int64_t *ptr;
   const int32_t *col;
   const float *xhat;
-  const double *cen;    // [clusters][3]
+  const float4 *dc;     // [admissible blocks]: centre of t minus centre of s, formed in FP64
   const float *half;    // [clusters][3]
   float t[kMaxM];       // reference Chebyshev nodes cos((2j+1) pi / (2m))
   int m, k, kp, rp;
@@ -295,6 +295,7 @@ struct CouplingGenRows {
     return Term<float, float>{nullptr, xhat + (int64_t)col[b] * k * rp, k};
   }
   __device__ int64_t cluster_of_term(int64_t e) const { return col[ptr[row0] + e]; }
+  __device__ float4 centre_gap(int64_t e) const { return dc[ptr[row0] + e]; }
 };
 
 // Leaf forward step (Algorithm 1 on the leaves): row j = leaf j, one term
@@ -450,10 +451,20 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
 #pragma unroll
       for (int c = 0; c < VN; ++c) acc[a][c] = zero_of<TC>();
     // generated coupling: node offsets of this thread's rows in the row cluster
-    float gbase[Rows::kGen ? 4 * R : 1][3];
+    float gnode[Rows::kGen ? 4 * R : 1][3];
     bool gvalid[Rows::kGen ? 4 * R : 1];
-    int64_t grow = 0;
-    if constexpr (Rows::kGen) grow = rows.row0 + r;
+    if constexpr (Rows::kGen) {
+      const int64_t grow = rows.row0 + r;
+      const int m = rows.m;
+#pragma unroll
+      for (int a = 0; a < 4 * R; ++a) {
+        const int nu = (a / 4) * gstride + 4 * vg + (a % 4);
+        gvalid[a] = nu < rows.k;
+        const int jj[3] = {nu % m, (nu / m) % m, min(nu / (m * m), m - 1)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gnode[a][d] = rows.half[3 * grow + d] * rows.t[jj[d]];
+      }
+    }
     const int64_t e_row_end = rows.first(r + 1);
     for (; e < e_row_end; ++e) {
       const int64_t i = e - e_begin;
@@ -469,19 +480,15 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
         const float sc = rows.scale(e);
         float hs[3] = {0.f, 0.f, 0.f};
+        float gbase[Rows::kGen ? 4 * R : 1][3];
         if constexpr (Rows::kGen) {
           const int64_t sg = rows.cluster_of_term(e);
-          const int m = rows.m;
+          const float4 g = rows.centre_gap(e);
 #pragma unroll
           for (int a = 0; a < 4 * R; ++a) {
-            const int nu = (a / 4) * gstride + 4 * vg + (a % 4);
-            gvalid[a] = nu < rows.k;
-            const int jx = nu % m, jy = (nu / m) % m, jz = nu / (m * m);
-            const int jj[3] = {jx, jy, min(jz, m - 1)};
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-              gbase[a][d] = (float)(rows.cen[3 * grow + d] - rows.cen[3 * sg + d]) +
-                            rows.half[3 * grow + d] * rows.t[jj[d]];
+            gbase[a][0] = g.x + gnode[a][0];
+            gbase[a][1] = g.y + gnode[a][1];
+            gbase[a][2] = g.z + gnode[a][2];
           }
 #pragma unroll
           for (int d = 0; d < 3; ++d) hs[d] = rows.half[3 * sg + d];
@@ -579,12 +586,12 @@ inline int row_groups(int Mp) {
   return (sizeof(T) == 4 && Mp % 8 == 0) ? 2 : 1;
 }
 
-// threads per CTA: enough slices of the contraction for about 8 steps each
+// consumer threads per CTA: enough slices of the contraction for about 4 to 8 steps each
 inline int row_threads(int Mp, int rp, int Kmax, size_t esize, int R) {
   const int tiles = (Mp / (4 * R)) * (rp / (int)(16 / esize));
   const int want = tiles * std::max(1, Kmax / 8);
-  for (int t : {64, 128})
-    if (want <= t) return t;
+  for (int t : {32, 64, 128})
+    if (want <= t && tiles <= t) return t;
   return 256;
 }
 
@@ -704,7 +711,7 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
         rows.ptr = d.adm_ptr;
         rows.col = d.adm_col;
         rows.xhat = xhat;
-        rows.cen = d.icen;
+        rows.dc = (const float4 *)d.adm_dc;
         rows.half = d.ihalf;
         for (int j = 0; j < kMaxM; ++j) rows.t[j] = j < m ? (float)std::cos((2 * j + 1) * 3.14159265358979323846 / (2.0 * m)) : 0.f;
         rows.m = m;

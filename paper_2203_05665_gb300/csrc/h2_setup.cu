@@ -387,6 +387,13 @@ int build_typed(Ctx &c) {
     H2_CUDA_TRY(cudaMemcpyAsync(d.icen, p.icen.data(), p.icen.size() * 8, cudaMemcpyHostToDevice, st));
     if ((rc = dev_alloc(d, (void **)&d.ihalf, hw.size() * 4))) return rc;
     H2_CUDA_TRY(cudaMemcpyAsync(d.ihalf, hw.data(), hw.size() * 4, cudaMemcpyHostToDevice, st));
+    // per admissible block the gap of the box centres, formed in FP64, rounded once
+    std::vector<float> dc(4 * std::max<size_t>(1, p.adm_col.size()), 0.0f);
+    for (int64_t t = 0; t < p.nclu; ++t)
+      for (int64_t e = p.adm_ptr[t]; e < p.adm_ptr[t + 1]; ++e)
+        for (int q = 0; q < 3; ++q) dc[4 * e + q] = (float)(p.icen[3 * t + q] - p.icen[3 * p.adm_col[e] + q]);
+    if ((rc = dev_alloc(d, (void **)&d.adm_dc, dc.size() * 4))) return rc;
+    H2_CUDA_TRY(cudaMemcpyAsync(d.adm_dc, dc.data(), dc.size() * 4, cudaMemcpyHostToDevice, st));
     H2_CUDA_TRY(cudaStreamSynchronize(st));
   }
 

@@ -227,6 +227,7 @@ __device__ __forceinline__ void scale_by(double &, float) {}
 __device__ __forceinline__ void scale_by(dd &, float) {}
 
 constexpr float kInv4PiF = 0.0795774715459476679f;
+constexpr uint32_t kMetaBytes = 32;   // per-term values at the end of every stage
 
 // Launch geometry of the block-row kernel (computed on the host).
 struct RowCfg {
@@ -248,9 +249,11 @@ struct Term {
 // Row sources of the block-row kernel.  Every row has count(r) terms; the
 // terms of all rows form one flat sequence (first(r) = flat index of row r's
 // first term, first(nrows) = total), term(e) gives the tiles of flat term e,
-// kdim(e) its contraction length and scale(e) the power of two its stored A
-// tile was divided by (FP16 storage; 1 otherwise).  kGen rows compute their
-// A tiles in the consumer threads instead of loading them.
+// kdim(e) its contraction length and meta(e) a few values the producer puts
+// beside the tiles: [0] the power of two the stored A tile was divided by
+// (FP16 storage; 1 otherwise), [1..6] the box data of generated A tiles.
+// kGen rows compute their A tiles in the consumer threads instead of loading
+// them.
 
 // Coupling (Algorithm 3, admissible blocks): row r = cluster row0 + r, terms
 // S_b x^_{s_b} for the admissible blocks b of that row (S_b stored [mu][nu]).
@@ -264,7 +267,7 @@ struct CouplingRows {
   int k, kp, rp;
   int64_t row0;
   __device__ int kdim(int64_t) const { return k; }
-  __device__ float scale(int64_t) const { return 1.0f; }
+  __device__ void meta(int64_t, float *mt) const { mt[0] = 1.0f; }
   __device__ int64_t first(int64_t r) const { return ptr[row0 + r] - ptr[row0]; }
   __device__ Term<TS, TC> term(int64_t e) const {
     const int64_t b = ptr[row0] + e;
@@ -288,14 +291,24 @@ struct CouplingGenRows {
   int m, k, kp, rp;
   int64_t row0;
   __device__ int kdim(int64_t) const { return k; }
-  __device__ float scale(int64_t) const { return 1.0f; }
+  // scale, centre gap (3), half widths of the column cluster (3)
+  __device__ void meta(int64_t e, float *mt) const {
+    const int64_t b = ptr[row0] + e;
+    const int64_t sg = col[b];
+    const float4 g = dc[b];
+    mt[0] = 1.0f;
+    mt[1] = g.x;
+    mt[2] = g.y;
+    mt[3] = g.z;
+    mt[4] = half[3 * sg];
+    mt[5] = half[3 * sg + 1];
+    mt[6] = half[3 * sg + 2];
+  }
   __device__ int64_t first(int64_t r) const { return ptr[row0 + r] - ptr[row0]; }
   __device__ Term<float, float> term(int64_t e) const {
     const int64_t b = ptr[row0] + e;
     return Term<float, float>{nullptr, xhat + (int64_t)col[b] * k * rp, k};
   }
-  __device__ int64_t cluster_of_term(int64_t e) const { return col[ptr[row0] + e]; }
-  __device__ float4 centre_gap(int64_t e) const { return dc[ptr[row0] + e]; }
 };
 
 // Leaf forward step (Algorithm 1 on the leaves): row j = leaf j, one term
@@ -308,7 +321,7 @@ struct LeafForwardRows {
   const float *vscale;   // per leaf, or NULL
   int L, kp, rp;
   __device__ int kdim(int64_t) const { return L; }
-  __device__ float scale(int64_t e) const { return vscale ? vscale[e] : 1.0f; }
+  __device__ void meta(int64_t e, float *mt) const { mt[0] = vscale ? vscale[e] : 1.0f; }
   __device__ int64_t first(int64_t r) const { return r; }
   __device__ Term<TS, TC> term(int64_t e) const {
     return Term<TS, TC>{V + e * (int64_t)L * kp, xpad + e * (int64_t)L * rp, L};
@@ -326,7 +339,7 @@ struct LeafBackwardRows {
   int k, Lp, rp;
   int64_t leaf0;
   __device__ int kdim(int64_t) const { return k; }
-  __device__ float scale(int64_t e) const { return vscale ? vscale[e] : 1.0f; }
+  __device__ void meta(int64_t e, float *mt) const { mt[0] = vscale ? vscale[e] : 1.0f; }
   __device__ int64_t first(int64_t r) const { return r; }
   __device__ Term<TS, TC> term(int64_t e) const {
     return Term<TS, TC>{Vt + e * (int64_t)k * Lp, yhat + (leaf0 + e) * (int64_t)k * rp, k};
@@ -345,7 +358,7 @@ struct NearRows {
   const float *nscale;   // per block, or NULL
   int L, Lp, rp;
   __device__ int kdim(int64_t) const { return L; }
-  __device__ float scale(int64_t e) const { return nscale ? nscale[e] : 1.0f; }
+  __device__ void meta(int64_t e, float *mt) const { mt[0] = nscale ? nscale[e] : 1.0f; }
   __device__ int64_t first(int64_t r) const { return ptr[r]; }
   __device__ Term<TS, TC> term(int64_t e) const {
     return Term<TS, TC>{near + e * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
@@ -421,6 +434,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         const Term<TS, TC> tm = rows.term(e);
         const uint32_t ab = Rows::kGen ? 0u : (uint32_t)(sizeof(TS) * tm.K * Mp);
         const uint32_t xb = (uint32_t)(sizeof(TC) * tm.K * rp);
+        // the term's metadata goes beside the tiles; the arrival below releases it
+        rows.meta(e, reinterpret_cast<float *>(st + cfg.stage_bytes - kMetaBytes));
         mbar_expect_tx(&full[s], ab + xb);
         if (!Rows::kGen) bulk_g2s(st, tm.A, ab, &full[s]);
         bulk_g2s(st + cfg.a_bytes, tm.X, xb, &full[s]);
@@ -475,23 +490,23 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
       if (ready && active) {
         const TS *sA = reinterpret_cast<const TS *>(smem + (size_t)s * cfg.stage_bytes);
         const TC *sX = reinterpret_cast<const TC *>(smem + (size_t)s * cfg.stage_bytes + cfg.a_bytes);
+        const float *mt = reinterpret_cast<const float *>(smem + (size_t)(s + 1) * cfg.stage_bytes - kMetaBytes);
         const int K = rows.kdim(e);
         const int kc = (K + cfg.ksplit - 1) / cfg.ksplit;
         const int mu0 = ks * kc, mu1 = min(K, mu0 + kc);
-        const float sc = rows.scale(e);
+        const float sc = mt[0];
         float hs[3] = {0.f, 0.f, 0.f};
         float gbase[Rows::kGen ? 4 * R : 1][3];
         if constexpr (Rows::kGen) {
-          const int64_t sg = rows.cluster_of_term(e);
-          const float4 g = rows.centre_gap(e);
 #pragma unroll
           for (int a = 0; a < 4 * R; ++a) {
-            gbase[a][0] = g.x + gnode[a][0];
-            gbase[a][1] = g.y + gnode[a][1];
-            gbase[a][2] = g.z + gnode[a][2];
+            gbase[a][0] = mt[1] + gnode[a][0];
+            gbase[a][1] = mt[2] + gnode[a][1];
+            gbase[a][2] = mt[3] + gnode[a][2];
           }
-#pragma unroll
-          for (int d = 0; d < 3; ++d) hs[d] = rows.half[3 * sg + d];
+          hs[0] = mt[4];
+          hs[1] = mt[5];
+          hs[2] = mt[6];
         }
 #pragma unroll 2
         for (int mu = mu0; mu < mu1; ++mu) {
@@ -566,7 +581,7 @@ int row_cfg(int M, int Mp, int rp, int Kmax, int threads, int R, bool gen, RowCf
   if (cfg.tiles > threads) return fail(H2_EINVAL, "tile rows x right-hand sides too large for one CTA");
   cfg.ksplit = std::max(1, std::min(threads / cfg.tiles, Kmax));
   cfg.a_bytes = gen ? 0u : (uint32_t)((sizeof(TS) * Kmax * Mp + 15) / 16 * 16);
-  cfg.stage_bytes = cfg.a_bytes + (uint32_t)(sizeof(T) * Kmax * rp);
+  cfg.stage_bytes = cfg.a_bytes + (uint32_t)((sizeof(T) * Kmax * rp + 15) / 16 * 16) + kMetaBytes;
   const size_t red = sizeof(T) * (size_t)cfg.ksplit * Mp * rp;   // slice sums, after the ring
   // stages: up to 8, sized so that 512 consumer threads per SM stay resident when possible
   const size_t budget = kSmemMax / (512 / threads);

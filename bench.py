@@ -149,8 +149,9 @@ def run_ours(args):
     h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=args.order, prec=args.prec, device=local,
                  stream=stream.cuda_stream)
     build_s = time.time() - t0
-    dt = torch.float32 if args.prec == "f32" else torch.float64
-    esize = 4 if args.prec == "f32" else 8
+    low = args.prec in ("f32", "bf16", "f16")
+    dt = torch.float32 if low else torch.float64
+    esize = 4 if low else 8
     x = colmajor(torch.from_numpy(x_np).to(device="cuda", dtype=dt))
     y = colmajor(torch.empty_like(x))
 
@@ -197,14 +198,23 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": alg["coupling_flops"] / (cpl_ms * 1e-3) / 1e12, "peak": DD_TFLOPS,
                 "unit": "TFLOP/s", "kernel": "k_coupling (double-float on the FP32 pipe)",
                 "hbm_frac": alg["coupling_bytes"] / (cpl_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    elif args.prec in ("bf16", "f16"):
+        # regenerated coupling: 2 k^2 nrhs multiply-adds plus one kernel evaluation
+        # (about 10 FP32 instructions and one MUFU rsqrt) per entry of S
+        k = st["rank"]
+        flops = alg["coupling_flops"] + 10.0 * st["adm_blocks"] * k * k
+        roof = {"bound": "alu", "achieved": flops / (cpl_ms * 1e-3) / 1e12, "peak": FP32_TFLOPS,
+                "unit": "TFLOP/s", "kernel": "k_blockrow (coupling regenerated in FP32)"}
     else:
         roof = {"bound": "hbm", "achieved": alg["coupling_bytes"] / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "kernel": "k_coupling (stored S stream)"}
+                "unit": "GB/s", "kernel": "k_blockrow (coupling, stored S stream)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
     roof["peak_source"] = {"f64n": "nominal FP64 rate",
                            "f64": "FP32 FMA rate (152 SMs x 128 lanes x 2.07 GHz) / 12 instructions per dd FMA",
-                           "f32": f"{peaks['src']} HBM copy bandwidth"}[args.prec]
+                           "f32": f"{peaks['src']} HBM copy bandwidth",
+                           "bf16": "FP32 FMA rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
+                           "f16": "FP32 FMA rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz)"}[args.prec]
     roof["kernel_ms"] = cpl_ms
     roof["hbm_frac_whole_product"] = alg["total_bytes"] / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
 
@@ -244,7 +254,7 @@ def run_ours(args):
         solve = {"rtol": 1e-8, "restart": 30, "nrhs": args.solve_nrhs,
                  "gmres": dict(timed(lambda: h.solve(b, rtol=1e-8, restart=30, maxit=5000)),
                                product=args.prec)}
-        if args.prec != "f32":
+        if args.prec in ("f64", "f64n"):
             lo = H2Matrix(v, f, leaf_size=32, eta=2.0, order=args.order, prec="f32", device=local,
                           stream=stream.cuda_stream)
             solve["gmres_ir"] = dict(timed(lambda: h.solve_ir(lo, b, rtol=1e-8, inner_rtol=1e-4, restart=30,
@@ -269,7 +279,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f32x2 (double-float, FP64-accurate)", "f32": "f32",
-                                       "f64n": "f64"}[args.prec], "data": "synthetic",
+                                       "f64n": "f64", "bf16": "bf16 storage, f32 arithmetic",
+                                       "f16": "f16 storage, f32 arithmetic"}[args.prec], "data": "synthetic",
         "config": {"workload": f"icosphere L{args.level} ({n} triangles), m={args.order} (k={args.order ** 3}), "
                                f"leaf 32, eta 2, stored S, SS order 3, {nrhs} RHS",
                    "n": n, "nrhs": nrhs, "order": args.order, "leaf_size": 32, "eta": 2.0,
@@ -474,8 +485,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f64n"],
-                    help="f64: FP64-accurate double-float arithmetic; f32; f64n: native FP64")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f64n", "bf16", "f16"],
+                    help="f64: FP64-accurate double-float arithmetic; f32; f64n: native FP64; "
+                         "bf16 / f16: 16-bit storage, FP32 accumulation, regenerated coupling")
     ap.add_argument("--level", type=int, default=7)
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--nrhs", type=int, default=16)

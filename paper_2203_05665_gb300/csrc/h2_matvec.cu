@@ -565,6 +565,117 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
   }
 }
 
+// Coupling regenerated in FP32, warp per row cluster (for up to 64 rows and
+// 16 columns): lane l owns rows nu = l + 32 q of y^_t for all columns and
+// loops over the admissible blocks of the row; per block the warp stages
+// x^_s and the column cluster's node offsets in its own shared memory and
+// evaluates s_{nu mu} = 1/(4 pi |xi_{t,nu} - xi_{s,mu}|) in registers (the
+// centre gap comes precomputed from FP64).  No cross-warp reduction: each
+// output is summed by one lane in a fixed order.
+constexpr int kRegenWarps = 4;
+
+template <int QR, int CP>
+__global__ void __launch_bounds__(32 * kRegenWarps)
+    k_coupling_regen_warp(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                          const float4 *__restrict__ dc, const float *__restrict__ half,
+                          const float *__restrict__ xhat, CouplingGenRows g, int64_t nrows, float *__restrict__ yhat) {
+  extern __shared__ __align__(16) float wsm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = g.k, m = g.m, rp = g.rp;
+  float *tn = wsm;                                          // reference nodes
+  float *xs = wsm + 16 + (size_t)w * (64 * CP + 3 * 64);   // [k][rp] then offsets [3][k]
+  float *offs = xs + 64 * CP;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < kMaxM; ++j) tn[j] = g.t[j];   // constant indices: no local copy of the parameters
+  }
+  __syncthreads();
+  const int64_t r = (int64_t)blockIdx.x * kRegenWarps + w;
+  if (r >= nrows) return;
+  const int64_t t = g.row0 + r;
+  float node[QR][3];
+  bool valid[QR];
+#pragma unroll
+  for (int q = 0; q < QR; ++q) {
+    const int nu = lane + 32 * q;
+    valid[q] = nu < k;
+    const int j[3] = {nu % m, (nu / m) % m, min(nu / (m * m), m - 1)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) node[q][d] = half[3 * t + d] * tn[j[d]];
+  }
+  float acc[QR][CP];
+#pragma unroll
+  for (int q = 0; q < QR; ++q)
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[q][c] = 0.0f;
+  const int64_t b0 = ptr[t], b1 = ptr[t + 1];
+  for (int64_t b = b0; b < b1; ++b) {
+    const int64_t sg = col[b];
+    const float4 gap = dc[b];
+    __syncwarp();
+    const float *xsrc = xhat + sg * (int64_t)k * rp;
+    for (int i = lane; i < k * rp; i += 32) xs[i] = xsrc[i];
+    for (int i = lane; i < k; i += 32) {
+      offs[i] = half[3 * sg] * tn[i % m];
+      offs[64 + i] = half[3 * sg + 1] * tn[(i / m) % m];
+      offs[128 + i] = half[3 * sg + 2] * tn[i / (m * m)];
+    }
+    __syncwarp();
+    float base[QR][3];
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+      base[q][0] = gap.x + node[q][0];
+      base[q][1] = gap.y + node[q][1];
+      base[q][2] = gap.z + node[q][2];
+    }
+#pragma unroll 3
+    for (int mu = 0; mu < k; ++mu) {
+      const float ox = offs[mu], oy = offs[64 + mu], oz = offs[128 + mu];
+      float xv[CP];
+#pragma unroll
+      for (int c = 0; c < CP; c += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(xs + mu * rp + c);
+        xv[c] = v.x; xv[c + 1] = v.y; xv[c + 2] = v.z; xv[c + 3] = v.w;
+      }
+#pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        const float dx = base[q][0] - ox, dy = base[q][1] - oy, dz = base[q][2] - oz;
+        const float sv = valid[q] ? kInv4PiF * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < CP; ++c)
+          if (c < rp) acc[q][c] = fmaf(sv, xv[c], acc[q][c]);
+      }
+    }
+  }
+  float *out = yhat + t * (int64_t)k * rp;
+#pragma unroll
+  for (int q = 0; q < QR; ++q)
+    if (valid[q])
+#pragma unroll
+      for (int c = 0; c < CP; ++c)
+        if (c < rp) out[(lane + 32 * q) * rp + c] = acc[q][c];
+}
+
+template <int QR, int CP>
+int launch_regen_warp(const CouplingGenRows &g, int64_t nrows, float *yhat, cudaStream_t st) {
+  const size_t sm = (16 + (size_t)kRegenWarps * (64 * CP + 3 * 64)) * sizeof(float);
+  const unsigned grid = (unsigned)((nrows + kRegenWarps - 1) / kRegenWarps);
+  k_coupling_regen_warp<QR, CP><<<grid, 32 * kRegenWarps, sm, st>>>(g.ptr, g.col, g.dc, g.half, g.xhat, g, nrows,
+                                                                     yhat);
+  return H2_OK;
+}
+
+// warp-per-row regenerated coupling when k <= 64 and rp <= 16, else -1
+int regen_warp(const CouplingGenRows &g, int64_t nrows, float *yhat, cudaStream_t st) {
+  if (g.k > 64 || g.rp > 16 || nrows <= 0) return -1;
+  const int QR = g.k > 32 ? 2 : 1, CP = g.rp <= 4 ? 4 : (g.rp <= 8 ? 8 : 16);
+  if (QR == 1) return CP == 4 ? launch_regen_warp<1, 4>(g, nrows, yhat, st)
+                              : CP == 8 ? launch_regen_warp<1, 8>(g, nrows, yhat, st)
+                                        : launch_regen_warp<1, 16>(g, nrows, yhat, st);
+  return CP == 4 ? launch_regen_warp<2, 4>(g, nrows, yhat, st)
+                 : CP == 8 ? launch_regen_warp<2, 8>(g, nrows, yhat, st) : launch_regen_warp<2, 16>(g, nrows, yhat, st);
+}
+
 constexpr size_t kSmemMax = 227 * 1024;
 
 // geometry for output tiles M x rp and contraction lengths up to Kmax;
@@ -734,7 +845,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
         rows.kp = kp;
         rows.rp = rp;
         rows.row0 = row0;
-        if ((rc = launch_rows<float, T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, out, st))) return rc;
+        const int wr = regen_warp(rows, d.nclu - row0, out, st);
+        if (wr < 0 && (rc = launch_rows<float, T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, out, st))) return rc;
       } else {
         return fail(H2_EINVAL, "the regenerated coupling runs in FP32 arithmetic only");
       }

@@ -665,7 +665,8 @@ int launch_regen_warp(const CouplingGenRows &g, int64_t nrows, float *yhat, cuda
   return H2_OK;
 }
 
-// warp-per-row regenerated coupling when k <= 64 and rp <= 16, else -1
+// warp-per-row regenerated coupling when k <= 64 and rp <= 16, else -1;
+// yhat is the base of [clusters][k][rp] (rows g.row0 .. g.row0 + nrows - 1 are written)
 int regen_warp(const CouplingGenRows &g, int64_t nrows, float *yhat, cudaStream_t st) {
   if (g.k > 64 || g.rp > 16 || nrows <= 0) return -1;
   const int QR = g.k > 32 ? 2 : 1, CP = g.rp <= 4 ? 4 : (g.rp <= 8 ? 8 : 16);
@@ -845,7 +846,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
         rows.kp = kp;
         rows.rp = rp;
         rows.row0 = row0;
-        const int wr = regen_warp(rows, d.nclu - row0, out, st);
+        // the warp kernel indexes y^ by absolute cluster number: give it the base
+        const int wr = regen_warp(rows, d.nclu - row0, yhat, st);
         if (wr < 0 && (rc = launch_rows<float, T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, out, st))) return rc;
       } else {
         return fail(H2_EINVAL, "the regenerated coupling runs in FP32 arithmetic only");

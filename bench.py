@@ -270,6 +270,10 @@ def run_ours(args):
     if rank == 0 and not args.no_mixed:
         mixed = run_mixed(args, local, stream)
 
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = run_batch(args, local, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args)
@@ -297,6 +301,7 @@ def run_ours(args):
         "solve": solve,
         "serve": serve,
         "mixed": mixed,
+        "batch": batch,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -429,6 +434,103 @@ def run_mixed(args, local, stream):
     return out
 
 
+def run_batch(args, local, stream):
+    """Uneven batch: independent FP32 problems (random ellipsoids and subdivided
+    cubes of 20k-400k triangles, m = 3 or 4, 1-8 RHS; leaf sizes chosen by the
+    measuring autotuner) multiplied together, one persistent launch per
+    block-row phase, replayed from a CUDA graph.  Reports aggregate DoF/s, the
+    coupling kernel's HBM roofline fraction and an end-to-end figure with the
+    packed vectors copied from and to pinned host memory."""
+    import torch
+    from paper_2203_05665_gb300 import Batch, H2Matrix, inputs, tune
+    specs = inputs.batch_problems(args.batch_problems, 1004)
+    t0 = time.time()
+    free, _ = torch.cuda.mem_get_info()
+    notes = []
+    if args.batch_leaf:
+        leaf = {s["index"]: args.batch_leaf for s in specs}
+        timings = {}
+    else:
+        leaf, timings = tune.choose_leaf(specs, budget_bytes=int(0.8 * free), log=notes.append)
+    tune_s = time.time() - t0
+    t0 = time.time()
+    mats = []
+    for s in specs:
+        v, f = inputs.problem_mesh(s)
+        mats.append(H2Matrix(v, f, leaf_size=leaf[s["index"]], eta=2.0, order=s["order"], prec="f32",
+                             coupling="stored", device=local, stream=stream.cuda_stream))
+    build_s = time.time() - t0
+    b = Batch(mats, [s["nrhs"] for s in specs], stream=stream.cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(1004)
+    x = torch.empty(b.length, dtype=torch.float32, device="cuda").uniform_(-1.0, 1.0, generator=g)
+    y = torch.empty_like(x)
+    b.matvec(x, y)
+    t0 = time.time()
+    shapes = b.tune(5)
+    shape_s = time.time() - t0
+    for _ in range(args.warmup):
+        b.matvec(x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 5)
+    e0.record(stream)
+    for _ in range(reps):
+        b.matvec(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.sync()
+    ms = e0.elapsed_time(e1) / reps
+    b.profile(True)
+    for _ in range(5):
+        b.matvec(x, y)
+    ph, prods = b.phase_times()
+    b.profile(False)
+    info = b.info()
+    # algorithmic bytes (FP32): the coupling stream of every problem
+    cbytes, tbytes = 0, 0
+    for s, m in zip(specs, mats):
+        a = _algorithmic(m.stats, s["nrhs"], 4)
+        cbytes += a["coupling_bytes"]
+        tbytes += a["total_bytes"] - 8 * 2 * m.n * s["nrhs"] + 4 * 2 * m.n * s["nrhs"]
+    cpl_ms = ph["coupling"][0] / prods
+    peaks = _peaks()
+    # end to end: packed x from pinned host memory, product, y back to pinned host memory
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    lat = []
+    for i in range(max(3, min(args.steps, 10)) + 2):
+        t1 = time.perf_counter()
+        x.copy_(xh, non_blocking=True)
+        b.matvec(x, y)
+        yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= 2:
+            lat.append(time.perf_counter() - t1)
+    e2e_s = statistics.median(lat)
+    leaves = [leaf[s["index"]] for s in specs]
+    out = {"workload": f"{len(specs)} problems: ellipsoids (icosphere L5-L7, semi-axes U[0.5,2]) and cubes "
+                       f"(s in 41..182), m in {{3,4}}, 1-8 RHS, FP32 stored S, eta 2",
+           "problems": len(specs), "triangles": int(sum(s["n"] for s in specs)), "dofs_x_rhs": int(info["dofs"]),
+           "leaf_counts": {str(lf): leaves.count(lf) for lf in sorted(set(leaves))},
+           "leaf_tuning_ms": {str(k): v for k, v in timings.items()}, "tune_notes": notes,
+           "shapes": shapes, "tune_s": tune_s, "shape_tune_s": shape_s, "build_s": build_s,
+           "ms_per_product": ms, "dof_per_s": info["dofs"] / (ms * 1e-3),
+           "phases_ms": {k: v[0] / prods for k, v in ph.items()}, "gpu_launches": info["launches"],
+           "graph": True,
+           "roofline": {"bound": "hbm", "kernel": "k_batch_rows (coupling)", "unit": "GB/s",
+                        "achieved": cbytes / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                        "frac": cbytes / (cpl_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "kernel_ms": cpl_ms,
+                        "hbm_frac_whole_product": tbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+           "device_bytes": int(sum(m.stats["device_bytes"] for m in mats) + info["work_bytes"]),
+           "e2e": {"value": info["dofs"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(4 * b.length),
+                   "d2h_bytes_per_step": int(4 * b.length)},
+           "l2": "inputs larger than L2"}
+    b.close()
+    for m in mats:
+        m.close()
+    return out
+
+
 def _oracle_sample(level, order, nrhs):
     import oracle
     from paper_2203_05665_gb300 import inputs
@@ -502,6 +604,9 @@ def main():
     ap.add_argument("--serve-full", action="store_true", help="all 8 geometries (icosphere L4-L8, ...)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-problems", type=int, default=64)
+    ap.add_argument("--batch-leaf", type=int, default=0, help="fixed leaf size instead of the autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -270,6 +270,60 @@ int h2_profile(h2_handle h, int enable);
  * Any output pointer may be NULL. */
 int h2_phase_times(h2_handle h, double *ms, int64_t *launches, int64_t *products);
 
+/* ---------------------------------------------------------------------------
+ * Batched products over independent matrices of uneven sizes.
+ *
+ * The paper multiplies one H^2 matrix at a time (Section 2, Algorithms 1-3);
+ * the batch runs the same steps for many matrices at once: each block-row
+ * phase (leaf forward, coupling, leaf backward, nearfield) is ONE persistent
+ * kernel launch over the rows of all matrices, the transfer passes run level
+ * by level across the matrices, and the whole product is captured in a CUDA
+ * graph on first use and replayed afterwards.
+ *
+ * Requirements: every handle is H2_F32 with stored coupling, order <= 4 and
+ * leaves of at most 64 triangles, all on one device; nrhs[p] in [1, 16]; a
+ * handle appears at most once.  The batch keeps pointers to the handles: they
+ * must outlive it, and must not be destroyed while it exists.  It owns its
+ * own work vectors, so products on the member handles do not disturb it.
+ *
+ * Vectors are PACKED: problem p's x (and y) is a column-major n_p x nrhs[p]
+ * float block at element offset offsets[p] of one device array of
+ * offsets[nprob] floats (h2_batch_offsets), in the caller's triangle order.
+ * stream: the CUDA stream the products run on (NULL: the legacy default
+ * stream).  Returns H2_EINVAL for a violated requirement, H2_ENOMEM if the
+ * work vectors do not fit. */
+typedef struct h2_batch_s *h2_batch;
+int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *stream, h2_batch *out);
+/* offsets[nprob + 1]: element offset of every problem in the packed vectors,
+ * offsets[nprob] = total length. */
+int h2_batch_offsets(h2_batch b, int64_t *offsets);
+/* y = G~_p x_p for every problem p; x, y device float arrays in the packed
+ * layout, asynchronous on the batch's stream.  The first call with a given
+ * (x, y) pair captures the CUDA graph (and so does the first call after
+ * h2_batch_tune, h2_batch_set_shapes or h2_batch_profile); later calls
+ * replay it.  A capture uses a private stream: do not call this function
+ * while another capture is in progress on the calling thread. */
+int h2_batch_matvec(h2_batch b, const float *x, float *y);
+/* Autotuner of the launch shapes: times every candidate shape (slot size,
+ * slots per warp, warps per CTA) of every block-row phase, reps launches
+ * each, on the work vectors as the last product left them, and keeps the
+ * fastest.  choice (4 ints, may be NULL) receives the chosen shape indices
+ * of leaf forward, coupling, leaf backward and nearfield.  Synchronises. */
+int h2_batch_tune(h2_batch b, int reps, int *choice);
+/* Set the four shape indices directly (as returned by h2_batch_tune). */
+int h2_batch_set_shapes(h2_batch b, const int *choice);
+/* Per-phase timing of the following products (CUDA events inside the graph;
+ * every product then synchronises); enabling clears the accumulated times. */
+int h2_batch_profile(h2_batch b, int enable);
+/* As h2_phase_times, for the batch (launches: per product). */
+int h2_batch_phase_times(h2_batch b, double *ms, int64_t *launches, int64_t *products);
+/* info[9]: problems, packed length, sum of n_p nrhs_p, work bytes, kernel
+ * launches per product, the four shape indices. */
+int h2_batch_info(h2_batch b, int64_t *info);
+/* Wait for the batch's products; H2_ETIMEOUT if a bounded device wait ran out. */
+int h2_batch_sync(h2_batch b);
+int h2_batch_destroy(h2_batch b);
+
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char *h2_last_error(void);
 

@@ -47,7 +47,9 @@ EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_
             "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec",
             "h2_matvec_noalloc", "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
             "h2_serve_create", "h2_serve_register", "h2_serve_submit", "h2_serve_poll", "h2_serve_wait",
-            "h2_serve_stats", "h2_serve_destroy", "h2_last_error"]
+            "h2_serve_stats", "h2_serve_destroy", "h2_batch_create", "h2_batch_offsets", "h2_batch_matvec",
+            "h2_batch_tune", "h2_batch_set_shapes", "h2_batch_profile", "h2_batch_phase_times", "h2_batch_info",
+            "h2_batch_sync", "h2_batch_destroy", "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -94,6 +96,16 @@ def load():
             "h2_serve_wait": (C.c_int, [vp, C.c_uint64, C.c_double]),
             "h2_serve_stats": (C.c_int, [vp, i64p]),
             "h2_serve_destroy": (C.c_int, [vp]),
+            "h2_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), vp, C.POINTER(vp)]),
+            "h2_batch_offsets": (C.c_int, [vp, i64p]),
+            "h2_batch_matvec": (C.c_int, [vp, vp, vp]),
+            "h2_batch_tune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
+            "h2_batch_set_shapes": (C.c_int, [vp, C.POINTER(C.c_int)]),
+            "h2_batch_profile": (C.c_int, [vp, C.c_int]),
+            "h2_batch_phase_times": (C.c_int, [vp, dp, i64p, i64p]),
+            "h2_batch_info": (C.c_int, [vp, i64p]),
+            "h2_batch_sync": (C.c_int, [vp]),
+            "h2_batch_destroy": (C.c_int, [vp]),
             "h2_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -348,6 +360,88 @@ class Server:
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             self._lib.h2_serve_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Batch:
+    """Batched products over independent FP32 H² matrices (h2_batch_*).
+
+    Vectors are packed: problem p occupies elements offsets[p] .. offsets[p+1]
+    of one float32 CUDA tensor, as a column-major (n_p, nrhs_p) block.
+    The matrices must outlive the batch (it keeps references to them).
+    """
+
+    def __init__(self, mats, nrhs, stream=None):
+        self._lib = load()
+        if len(mats) != len(nrhs):
+            raise ValueError("one nrhs per matrix")
+        self._mats = list(mats)   # keep the handles alive
+        hs = (C.c_void_p * len(mats))(*[m.handle.value for m in mats])
+        nr = (C.c_int * len(mats))(*[int(v) for v in nrhs])
+        h = C.c_void_p()
+        _check(self._lib.h2_batch_create(hs, len(mats), nr, stream, C.byref(h)))
+        self._h = h
+        self.nrhs = [int(v) for v in nrhs]
+        off = np.zeros(len(mats) + 1, dtype=np.int64)
+        _check(self._lib.h2_batch_offsets(h, off.ctypes.data_as(C.POINTER(C.c_int64))))
+        self.offsets = off
+
+    @property
+    def length(self):
+        return int(self.offsets[-1])
+
+    def matvec(self, x, y):
+        """y = G~_p x_p for every problem; x, y float32 CUDA tensors of `length` elements."""
+        if x.numel() != self.length or y.numel() != self.length:
+            raise ValueError("x and y must hold the packed vectors of all problems")
+        _check(self._lib.h2_batch_matvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y
+
+    def split(self, v):
+        """The (n_p, nrhs_p) column-major views of a packed vector."""
+        out = []
+        for p, m in enumerate(self._mats):
+            a, b = int(self.offsets[p]), int(self.offsets[p + 1])
+            out.append(v[a:b].view(self.nrhs[p], m.n).t())
+        return out
+
+    def tune(self, reps=5):
+        ch = (C.c_int * 4)()
+        _check(self._lib.h2_batch_tune(self._h, int(reps), ch))
+        return list(ch)
+
+    def set_shapes(self, choice):
+        ch = (C.c_int * 4)(*[int(c) for c in choice])
+        _check(self._lib.h2_batch_set_shapes(self._h, ch))
+
+    def profile(self, enable=True):
+        _check(self._lib.h2_batch_profile(self._h, 1 if enable else 0))
+
+    def phase_times(self):
+        ms = np.zeros(len(PHASES))
+        ln = np.zeros(len(PHASES), dtype=np.int64)
+        pr = np.zeros(1, dtype=np.int64)
+        _check(self._lib.h2_batch_phase_times(self._h, _dp(ms), ln.ctypes.data_as(C.POINTER(C.c_int64)),
+                                              pr.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {p: (float(a), int(b)) for p, a, b in zip(PHASES, ms, ln)}, int(pr[0])
+
+    def info(self):
+        out = np.zeros(9, dtype=np.int64)
+        _check(self._lib.h2_batch_info(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        keys = ["problems", "packed", "dofs", "work_bytes", "launches", "shape_forward", "shape_coupling",
+                "shape_backward", "shape_near"]
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def sync(self):
+        _check(self._lib.h2_batch_sync(self._h))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.h2_batch_destroy(h)
             self._h = None
 
     def __del__(self):

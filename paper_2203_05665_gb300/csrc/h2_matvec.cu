@@ -20,6 +20,7 @@
 #include "h2_dd.cuh"
 #include "h2_internal.hpp"
 #include "h2_ptx.cuh"
+#include "h2_transfer.cuh"
 
 namespace h2 {
 
@@ -53,106 +54,18 @@ __global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs,
   }
 }
 
-// One mode product of the factored transfer on a [k][rp] coefficient tensor
-// (nu = jx + m jy + m^2 jz): every thread owns one fibre along axis d for one
-// column, reads its m entries once and writes m results.
-//   trans: out[.., j, ..] = sum_{j'} F[j'][j] in[.., j', ..]   (E^T, upward)
-//   plain: out[.., j', ..] = sum_{j} F[j'][j] in[.., j, ..]    (E, downward)
-constexpr int kMaxM = 5;
-
-template <class T>
-__device__ __forceinline__ void mode_fibres(const T *F, const T *in, T *out, int m, int k, int rp, int d, bool trans) {
-  const int stride = d == 0 ? 1 : (d == 1 ? m : m * m);
-  const int items = (k / m) * rp;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it % rp, f = it / rp;
-    const int lo = f % stride, hi = f / stride;
-    const int base = lo + hi * stride * m;
-    T v[kMaxM];
-#pragma unroll
-    for (int i = 0; i < kMaxM; ++i)
-      if (i < m) v[i] = in[(base + i * stride) * rp + c];
-#pragma unroll
-    for (int j = 0; j < kMaxM; ++j) {
-      if (j >= m) break;
-      T acc = zero_of<T>();
-#pragma unroll
-      for (int i = 0; i < kMaxM; ++i)
-        if (i < m) acc = madd(trans ? F[i * m + j] : F[j * m + i], v[i], acc);
-      out[(base + j * stride) * rp + c] = acc;
-    }
-  }
-}
-
-// storage -> compute conversion of a transfer factor
-template <class TC, class TS>
-__device__ __forceinline__ TC to_compute(TS v) {
-  return convert<TC, TS>(v);
-}
-template <>
-__device__ __forceinline__ float to_compute<float, __nv_bfloat16>(__nv_bfloat16 v) {
-  return __bfloat162float(v);
-}
-template <>
-__device__ __forceinline__ float to_compute<float, __half>(__half v) {
-  return __half2float(v);
-}
-
-// upward step for the parents of level l (Algorithm 1): x^_p = sum_children E_c^T x^_c
+// upward step for the parents of level l (Algorithm 1), one CTA per parent
 template <class TS, class T>
 __global__ void k_upward(const TS *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ xhat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int kr = k * rp, mm = m * m;
-  T *a = reinterpret_cast<T *>(smem_raw);
-  T *b = a + kr;
-  T *acc = b + kr;
-  T *F = acc + kr;   // 2 children x 3 axes x m x m
-  const int64_t par = par0 + blockIdx.x;
-  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = to_compute<T>(Ef[(2 * par + 1) * 3 * mm + i]);
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = zero_of<T>();
-  for (int ch = 0; ch < 2; ++ch) {
-    const int64_t c = 2 * par + 1 + ch;
-    for (int i = threadIdx.x; i < kr; i += blockDim.x) a[i] = xhat[c * kr + i];
-    __syncthreads();
-    const T *Fc = F + ch * 3 * mm;
-    mode_fibres(Fc, a, b, m, k, rp, 0, true);
-    __syncthreads();
-    mode_fibres(Fc + mm, b, a, m, k, rp, 1, true);
-    __syncthreads();
-    mode_fibres(Fc + 2 * mm, a, b, m, k, rp, 2, true);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = acc[i] + b[i];
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) xhat[par * kr + i] = acc[i];
+  upward_parent<TS, T>(Ef, m, k, rp, par0 + blockIdx.x, xhat, smem_raw);
 }
 
-// downward step for the children of level l+1 (Algorithm 2): y^_c += E_c y^_parent;
-// one CTA per parent of level l handles both children
+// downward step for the children of level l+1 (Algorithm 2), one CTA per parent of level l
 template <class TS, class T>
 __global__ void k_downward(const TS *__restrict__ Ef, int m, int k, int rp, int64_t par0, T *__restrict__ yhat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int kr = k * rp, mm = m * m;
-  T *p = reinterpret_cast<T *>(smem_raw);
-  T *a = p + kr;
-  T *b = a + kr;
-  T *F = b + kr;
-  const int64_t par = par0 + blockIdx.x;
-  for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) F[i] = to_compute<T>(Ef[(2 * par + 1) * 3 * mm + i]);
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) p[i] = yhat[par * kr + i];
-  __syncthreads();
-  for (int ch = 0; ch < 2; ++ch) {
-    const int64_t c = 2 * par + 1 + ch;
-    const T *Fc = F + ch * 3 * mm;
-    mode_fibres(Fc, p, a, m, k, rp, 0, false);
-    __syncthreads();
-    mode_fibres(Fc + mm, a, b, m, k, rp, 1, false);
-    __syncthreads();
-    mode_fibres(Fc + 2 * mm, b, a, m, k, rp, 2, false);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kr; i += blockDim.x) yhat[c * kr + i] = yhat[c * kr + i] + a[i];
-    __syncthreads();
-  }
+  downward_parent<TS, T>(Ef, m, k, rp, par0 + blockIdx.x, yhat, smem_raw);
 }
 
 template <class T>

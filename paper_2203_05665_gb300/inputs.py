@@ -10,6 +10,9 @@ the surface meshes and right-hand sides both sides consume.
 * ``cube(s)``: the surface of [-1, 1]^3 with s x s squares per face, each
   square split into two triangles along one diagonal.
 * ``uniform_rhs(n, nrhs, seed)``: entries uniform in [-1, 1].
+* ``batch_problems(nprob, seed)``: the uneven batch of independent problems
+  (random ellipsoids and subdivided cubes of 20k to 400k triangles, order 3
+  or 4, 1 to 8 right-hand sides); ``problem_mesh(spec)`` builds one mesh.
 
 Triangles are returned as int32 (nt, 3) vertex indices oriented so that the
 normal (b - a) x (c - a) points out of the enclosed volume; vertices are
@@ -130,3 +133,40 @@ def uniform_rhs(n: int, nrhs: int, seed: int):
     """n x nrhs right-hand sides, entries uniform in [-1, 1], Fortran (column-major) order."""
     rng = np.random.default_rng(seed)
     return np.asfortranarray(rng.uniform(-1.0, 1.0, (n, nrhs)))
+
+
+def batch_problems(nprob: int = 64, seed: int = 1004):
+    """Specifications of an uneven batch, drawn in problem order from one generator.
+
+    Even index: ellipsoid = icosphere of level 5, 6 or 7 (20,480 / 81,920 /
+    327,680 triangles) with semi-axes uniform in [0.5, 2].  Odd index: cube
+    with s uniform in {41, ..., 182} (12 s^2 = 20,172 ... 397,488 triangles).
+    Then the interpolation order m in {3, 4} and nrhs uniform in {1, ..., 8}.
+    The leaf size is not drawn: an autotuner chooses it.
+    """
+    rng = np.random.default_rng(seed)
+    specs = []
+    for p in range(nprob):
+        if p % 2 == 0:
+            level = int(rng.integers(5, 8))
+            axes = [float(a) for a in rng.uniform(0.5, 2.0, 3)]
+            spec = dict(kind="ellipsoid", level=level, axes=axes, n=20 * 4 ** level)
+        else:
+            s = int(rng.integers(41, 183))
+            spec = dict(kind="cube", s=s, n=12 * s * s)
+        spec["order"] = int(rng.integers(3, 5))
+        spec["nrhs"] = int(rng.integers(1, 9))
+        spec["index"] = p
+        specs.append(spec)
+    return specs
+
+
+def problem_mesh(spec):
+    """(vert, tri) of a batch_problems specification."""
+    if spec["kind"] == "ellipsoid":
+        return ellipsoid(spec["level"], spec["axes"])
+    if spec["kind"] == "cube":
+        return cube(spec["s"])
+    if spec["kind"] == "icosphere":
+        return icosphere(spec["level"])
+    raise ValueError(f"unknown mesh kind {spec['kind']!r}")

@@ -466,7 +466,11 @@ def run_batch(args, local, stream):
     y = torch.empty_like(x)
     b.matvec(x, y)
     t0 = time.time()
-    shapes = b.tune(5)
+    if args.batch_shapes:
+        shapes = [int(c) for c in args.batch_shapes.split(",")]
+        b.set_shapes(shapes)
+    else:
+        shapes = b.tune(5)
     shape_s = time.time() - t0
     for _ in range(args.warmup):
         b.matvec(x, y)
@@ -487,10 +491,12 @@ def run_batch(args, local, stream):
     b.profile(False)
     info = b.info()
     # algorithmic bytes (FP32): the coupling stream of every problem
-    cbytes, tbytes = 0, 0
+    cbytes, tbytes, nbytes = 0, 0, 0
     for s, m in zip(specs, mats):
         a = _algorithmic(m.stats, s["nrhs"], 4)
         cbytes += a["coupling_bytes"]
+        # leaf backward + nearfield: V and the nearfield blocks, the leaf vectors read and written
+        nbytes += 4 * (m.stats["near_entries"] + m.n * m.stats["rank"] + 3 * m.n * s["nrhs"])
         tbytes += a["total_bytes"] - 8 * 2 * m.n * s["nrhs"] + 4 * 2 * m.n * s["nrhs"]
     cpl_ms = ph["coupling"][0] / prods
     peaks = _peaks()
@@ -520,7 +526,8 @@ def run_batch(args, local, stream):
            "roofline": {"bound": "hbm", "kernel": "k_batch_rows (coupling)", "unit": "GB/s",
                         "achieved": cbytes / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                         "frac": cbytes / (cpl_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "kernel_ms": cpl_ms,
-                        "hbm_frac_whole_product": tbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+                        "hbm_frac_whole_product": tbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                        "hbm_frac_leaf_near": nbytes / (ph["leaf_near"][0] / prods * 1e-3) / 1e9 / peaks["hbm_gbs"]},
            "device_bytes": int(sum(m.stats["device_bytes"] for m in mats) + info["work_bytes"]),
            "e2e": {"value": info["dofs"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(4 * b.length),
                    "d2h_bytes_per_step": int(4 * b.length)},
@@ -607,6 +614,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=64)
     ap.add_argument("--batch-leaf", type=int, default=0, help="fixed leaf size instead of the autotuner")
+    ap.add_argument("--batch-shapes", default="", help="four launch-shape indices instead of the shape tuner")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -11,7 +11,8 @@
 // memory slots with bulk copies (TMA engine, one mbarrier per slot).  A slot
 // holds several whole terms A X of one row, or one piece of a term cut along
 // the contraction index when a term is larger than a slot.  Lane l owns the
-// output rows l and l + 32 of the current row for all right-hand sides and
+// output rows 2l and 2l + 1 (row l for tiles of at most 32 rows) of the
+// current row for all right-hand sides, multiplies in packed FP32 pairs and
 // sums its terms in a fixed order: results are bit-reproducible.
 //
 // The transfer passes run level-synchronously across problems: step s of the
@@ -41,11 +42,14 @@ struct BRows {
   const float *A;        // stored tiles: term b at A + b a_stride, [K][Mp] (contraction index major)
   const float *X;        // input tiles: unit u at X + u x_stride, [K][rp]
   const int64_t *ptr;    // terms of row r: [ptr[row0 + r], ptr[row0 + r + 1]); NULL: the single term r
+  const int64_t *pend;   // if set, row r's terms end at pend[r] instead (rows made of chunks)
   const int32_t *col;    // unit of term b; NULL: unit = r
   float *out;            // output row r at out + r out_stride, [M][rp]
   int64_t a_stride, x_stride, out_stride, row0, nrows;
   int64_t w0;            // work of all earlier problems in this phase
   int64_t wterm, wrow;   // work of a term and of a row (bytes moved, plus a fixed overhead)
+  int64_t cap;           // at most cap terms of a row are taken here (the rest goes to chunk rows)
+  int64_t wfix;          // if > 0, every row counts wfix work (chunk rows)
   int M, Mp, K, rp;
   int tps;               // whole terms per slot; 0: terms are cut in pieces of P contraction rows
   int P, ppt;            // rows per piece, pieces per term (cut terms)
@@ -56,7 +60,7 @@ struct BRows {
 struct BTr {
   const float *Ef;
   float *hat;
-  int64_t par0, cta0;
+  int64_t par0, g0;      // first parent of the entry, its global parent index
   int m, k, rp, pad;
 };
 
@@ -81,8 +85,21 @@ struct Pos {
 __device__ __forceinline__ bool pos_less(Pos a, Pos b) { return a.p < b.p || (a.p == b.p && a.r < b.r); }
 
 __device__ __forceinline__ int64_t row_work(const BRows &q, int64_t r) {
+  if (q.wfix > 0) return q.w0 + r * q.wfix;
   const int64_t terms = q.ptr ? q.ptr[q.row0 + r] - q.ptr[q.row0] : r;
   return q.w0 + terms * q.wterm + r * q.wrow;
+}
+
+// first term and number of terms of row r
+__device__ __forceinline__ void row_terms(const BRows &q, int64_t r, int64_t &b0, int64_t &nt) {
+  if (!q.ptr) {
+    b0 = r;
+    nt = 1;
+    return;
+  }
+  b0 = q.ptr[q.row0 + r];
+  const int64_t e = q.pend ? q.pend[r] : q.ptr[q.row0 + r + 1];
+  nt = min(e - b0, q.cap);
 }
 
 __device__ Pos find_pos(const BRows *__restrict__ pr, int np, int64_t W) {
@@ -116,9 +133,7 @@ struct Cur {
 };
 
 __device__ __forceinline__ void cur_load(const BRows *__restrict__ pr, Cur &c) {
-  const BRows &q = pr[c.p];
-  c.b0 = q.ptr ? q.ptr[q.row0 + c.r] : c.r;
-  c.nt = q.ptr ? q.ptr[q.row0 + c.r + 1] - c.b0 : 1;
+  row_terms(pr[c.p], c.r, c.b0, c.nt);
   c.e = 0;
   c.q = 0;
 }
@@ -176,34 +191,49 @@ __device__ __forceinline__ void issue_slot(const BRows *__restrict__ pr, int np,
   if (c.e >= c.nt) cur_next_row(pr, np, end, c);
 }
 
-// acc[i][c] += sum_mu A[mu][lane + 32 i] X[mu][c] over one segment of a slot
+// Packed FP32 pairs: (lo, hi) in one 64-bit register pair.  fma.rn.f32x2
+// rounds each half exactly like fmaf, so results equal the scalar form.
+__device__ __forceinline__ uint64_t dup2(float a) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ void fma2(uint64_t &d, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
+// acc[i] += sum_mu A[mu][row_i] X[mu][:] over one segment of a slot, the
+// columns of X in packed pairs.  QR = 2 (tiles of more than 32 rows): lane l
+// owns rows 2l and 2l + 1 and reads both with one 8-byte load; QR = 1: row l.
 template <int QR, int CP>
 __device__ __forceinline__ void seg_fma(const float *sA, const float *sX, int rows, int Mp, int lane,
-                                        float (&acc)[2][kBatchMaxRp]) {
-  const bool v0 = lane < Mp, v1 = QR == 2 && lane + 32 < Mp;
+                                        uint64_t (&acc)[2][kBatchMaxRp / 2]) {
+  const bool v = QR == 2 ? 2 * lane < Mp : lane < Mp;
 #pragma unroll 4
   for (int mu = 0; mu < rows; ++mu) {
-    const float a0 = v0 ? sA[mu * Mp + lane] : 0.0f;
-    const float a1 = v1 ? sA[mu * Mp + lane + 32] : 0.0f;
-    float xv[CP];
-#pragma unroll
-    for (int c = 0; c < CP; c += 4) {
-      const float4 v = *reinterpret_cast<const float4 *>(sX + mu * CP + c);
-      xv[c] = v.x;
-      xv[c + 1] = v.y;
-      xv[c + 2] = v.z;
-      xv[c + 3] = v.w;
+    uint64_t a0, a1 = 0;
+    if (QR == 2) {
+      const float2 av = v ? *reinterpret_cast<const float2 *>(sA + mu * Mp + 2 * lane) : make_float2(0.f, 0.f);
+      a0 = dup2(av.x);
+      a1 = dup2(av.y);
+    } else {
+      a0 = dup2(v ? sA[mu * Mp + lane] : 0.0f);
     }
 #pragma unroll
-    for (int c = 0; c < CP; ++c) {
-      acc[0][c] = fmaf(a0, xv[c], acc[0][c]);
-      if (QR == 2) acc[1][c] = fmaf(a1, xv[c], acc[1][c]);
+    for (int c = 0; c < CP; c += 4) {
+      const ulonglong2 xv = *reinterpret_cast<const ulonglong2 *>(sX + mu * CP + c);
+      fma2(acc[0][c / 2], a0, xv.x);
+      fma2(acc[0][c / 2 + 1], a0, xv.y);
+      if (QR == 2) {
+        fma2(acc[1][c / 2], a1, xv.x);
+        fma2(acc[1][c / 2 + 1], a1, xv.y);
+      }
     }
   }
 }
 
 __device__ __forceinline__ void seg_any(bool two, int rp, const float *sA, const float *sX, int rows, int Mp, int lane,
-                                        float (&acc)[2][kBatchMaxRp]) {
+                                        uint64_t (&acc)[2][kBatchMaxRp / 2]) {
   switch (rp) {
     case 4: two ? seg_fma<2, 4>(sA, sX, rows, Mp, lane, acc) : seg_fma<1, 4>(sA, sX, rows, Mp, lane, acc); break;
     case 8: two ? seg_fma<2, 8>(sA, sX, rows, Mp, lane, acc) : seg_fma<1, 8>(sA, sX, rows, Mp, lane, acc); break;
@@ -211,6 +241,9 @@ __device__ __forceinline__ void seg_any(bool two, int rp, const float *sA, const
     default: two ? seg_fma<2, 16>(sA, sX, rows, Mp, lane, acc) : seg_fma<1, 16>(sA, sX, rows, Mp, lane, acc); break;
   }
 }
+
+__device__ __forceinline__ float lo_of(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi_of(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
 // The batched block-row kernel (see the top of the file).  nslot slots of
 // zbytes per warp, then nslot mbarriers per warp.
@@ -244,15 +277,15 @@ __global__ void __launch_bounds__(512) k_batch_rows(const BRows *__restrict__ pr
   Pos ps = beg;
   while (pos_less(ps, end)) {
     const BRows &q = pr[ps.p];
-    const int64_t b0 = q.ptr ? q.ptr[q.row0 + ps.r] : ps.r;
-    const int64_t nt = q.ptr ? q.ptr[q.row0 + ps.r + 1] - b0 : 1;
+    int64_t b0, nt;
+    row_terms(q, ps.r, b0, nt);
     const int64_t ns = q.tps > 0 ? (nt + q.tps - 1) / q.tps : nt * q.ppt;
     const bool two = q.M > 32;
-    float acc[2][kBatchMaxRp];
+    uint64_t acc[2][kBatchMaxRp / 2];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int c = 0; c < kBatchMaxRp; ++c) acc[i][c] = 0.0f;
+      for (int c = 0; c < kBatchMaxRp / 2; ++c) acc[i][c] = 0;
     for (int64_t j = 0; j < ns; ++j) {
       const int s = (int)(consumed % nslot);
       if (!mbar_wait_bounded(&bar[s], (uint32_t)((consumed / nslot) & 1))) {
@@ -283,17 +316,18 @@ __global__ void __launch_bounds__(512) k_batch_rows(const BRows *__restrict__ pr
         ++issued;
       }
     }
-    // write the row: lane owns rows lane and lane + 32
+    // write the row: lane owns rows 2 lane and 2 lane + 1 (tiles of more than 32 rows) or row lane
     float *o = q.out + ps.r * q.out_stride;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const int row = lane + 32 * i;
+      const int row = two ? 2 * lane + i : (i == 0 ? lane : q.M);
       if (row < q.M) {
         float4 *o4 = reinterpret_cast<float4 *>(o + (int64_t)row * q.rp);
 #pragma unroll
         for (int c4 = 0; c4 < kBatchMaxRp / 4; ++c4) {
           if (4 * c4 < q.rp) {
-            float4 v = make_float4(acc[i][4 * c4], acc[i][4 * c4 + 1], acc[i][4 * c4 + 2], acc[i][4 * c4 + 3]);
+            const uint64_t p0 = acc[i][2 * c4], p1 = acc[i][2 * c4 + 1];
+            float4 v = make_float4(lo_of(p0), hi_of(p0), lo_of(p1), hi_of(p1));
             if (q.accumulate) {
               const float4 u = o4[c4];
               v.x += u.x;
@@ -315,27 +349,55 @@ __global__ void __launch_bounds__(512) k_batch_rows(const BRows *__restrict__ pr
 }
 
 // ---------------------------------------------------------------------------
-// transfers: CTA -> (entry, parent) by the entries' first CTA
-__device__ __forceinline__ int find_entry(const BTr *__restrict__ te, int ne, int64_t cta) {
+// transfers: warp per parent; global parent g -> (entry, parent) by the
+// entries' first global parent index
+constexpr int kTrWarps = 4;
+
+__device__ __forceinline__ int find_entry(const BTr *__restrict__ te, int ne, int64_t g) {
   int lo = 0, hi = ne - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
-    if (te[mid].cta0 <= cta) lo = mid;
+    if (te[mid].g0 <= g) lo = mid;
     else hi = mid - 1;
   }
   return lo;
 }
 
-__global__ void k_batch_upward(const BTr *__restrict__ te, int ne) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BTr &t = te[find_entry(te, ne, blockIdx.x)];
-  upward_parent<float, float>(t.Ef, t.m, t.k, t.rp, t.par0 + (blockIdx.x - t.cta0), t.hat, smem_raw);
+__global__ void __launch_bounds__(32 * kTrWarps) k_batch_upward(const BTr *__restrict__ te, int ne, int64_t total,
+                                                                 int wfloats) {
+  extern __shared__ __align__(16) float trs[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t g = (int64_t)blockIdx.x * kTrWarps + w;
+  if (g >= total) return;
+  const BTr &t = te[find_entry(te, ne, g)];
+  upward_parent_warp<float, float>(t.Ef, t.m, t.k, t.rp, t.par0 + (g - t.g0), t.hat, trs + (size_t)w * wfloats, lane);
 }
 
-__global__ void k_batch_downward(const BTr *__restrict__ te, int ne) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BTr &t = te[find_entry(te, ne, blockIdx.x)];
-  downward_parent<float, float>(t.Ef, t.m, t.k, t.rp, t.par0 + (blockIdx.x - t.cta0), t.hat, smem_raw);
+__global__ void __launch_bounds__(32 * kTrWarps) k_batch_downward(const BTr *__restrict__ te, int ne, int64_t total,
+                                                                   int wfloats) {
+  extern __shared__ __align__(16) float trs[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t g = (int64_t)blockIdx.x * kTrWarps + w;
+  if (g >= total) return;
+  const BTr &t = te[find_entry(te, ne, g)];
+  downward_parent_warp<float, float>(t.Ef, t.m, t.k, t.rp, t.par0 + (g - t.g0), t.hat, trs + (size_t)w * wfloats,
+                                     lane);
+}
+
+// rows cut in chunks: out (+)= the partial sums of the chunk rows, in chunk order
+struct BRed {
+  float *out;            // the output row (already holding the first chunk's sum)
+  const float *part;     // nch partial rows of len values each
+  int nch, len;
+};
+
+__global__ void k_batch_reduce(const BRed *__restrict__ rd) {
+  const BRed &q = rd[blockIdx.x];
+  for (int i = threadIdx.x; i < q.len; i += blockDim.x) {
+    float v = q.out[i];
+    for (int j = 0; j < q.nch; ++j) v += q.part[(int64_t)j * q.len + i];
+    q.out[i] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -394,6 +456,8 @@ int take_batch_error(cudaStream_t st) {
 }
 
 constexpr int kRowPhases = 4;   // leaf forward, coupling, leaf backward, nearfield
+constexpr int64_t kChunkTerms = 24;   // rows with more terms are cut in chunks of this many terms
+constexpr int64_t kNoCap = (int64_t)1 << 62;
 constexpr int kPermThreads = 256;
 constexpr size_t kBatchSmemMax = 227 * 1024;
 
@@ -434,11 +498,16 @@ struct h2_batch_s {
   int64_t wtotal[kRowPhases] = {};
   int shape[kRowPhases] = {0, 0, 0, 0};
   int grid[kRowPhases] = {};
-  // transfers: per step, entries (device arrays) and CTAs
+  // rows cut in chunks (coupling and nearfield): chunk bounds, partial sums, reductions
+  int64_t *d_chunks[kRowPhases] = {};
+  float *scratch[kRowPhases] = {};
+  BRed *d_red[kRowPhases] = {};
+  int nred[kRowPhases] = {};
+  // transfers: per step, entries (device arrays) and parents
   std::vector<BTr *> d_up, d_down;
   std::vector<int> n_up, n_down;
-  std::vector<int64_t> cta_up, cta_down;
-  size_t tr_smem = 0;
+  std::vector<int64_t> tot_up, tot_down;
+  int tr_wfloats = 0;
   // permutations
   BPerm *d_perm_in = nullptr, *d_perm_out = nullptr;
   int64_t perm_total = 0;
@@ -483,6 +552,11 @@ int upload_rows(h2_batch_s &b, int ph) {
     BRows &q = b.rows[ph][p];
     set_rows_shape(q, s.zbytes);
     q.w0 = w;
+    if (q.pend) {   // chunk rows
+      q.wfix = kChunkTerms * q.wterm + q.wrow;
+      w += q.nrows * q.wfix;
+      continue;
+    }
     const Plan &pl = b.probs[p].h->plan;
     int64_t terms = q.nrows;
     if (q.nrows > 0 && q.ptr) {
@@ -526,21 +600,26 @@ int64_t enqueue(h2_batch_s &b, const float *x, float *y, cudaStream_t st, bool e
   ++nl;
   mark(H2_PH_LEAF_FORWARD);
   if (b.wtotal[0]) launch_rows_phase(b, 0, st), ++nl;
+  const size_t trs = (size_t)kTrWarps * b.tr_wfloats * sizeof(float);
   mark(H2_PH_UPWARD);
   for (size_t s = 0; s < b.d_up.size(); ++s) {
-    k_batch_upward<<<(unsigned)b.cta_up[s], 256, b.tr_smem, st>>>(b.d_up[s], b.n_up[s]);
+    k_batch_upward<<<(unsigned)((b.tot_up[s] + kTrWarps - 1) / kTrWarps), 32 * kTrWarps, trs, st>>>(
+        b.d_up[s], b.n_up[s], b.tot_up[s], b.tr_wfloats);
     ++nl;
   }
   mark(H2_PH_COUPLING);
   if (b.wtotal[1]) launch_rows_phase(b, 1, st), ++nl;
+  if (b.nred[1]) k_batch_reduce<<<b.nred[1], 128, 0, st>>>(b.d_red[1]), ++nl;
   mark(H2_PH_DOWNWARD);
   for (size_t s = 0; s < b.d_down.size(); ++s) {
-    k_batch_downward<<<(unsigned)b.cta_down[s], 256, b.tr_smem, st>>>(b.d_down[s], b.n_down[s]);
+    k_batch_downward<<<(unsigned)((b.tot_down[s] + kTrWarps - 1) / kTrWarps), 32 * kTrWarps, trs, st>>>(
+        b.d_down[s], b.n_down[s], b.tot_down[s], b.tr_wfloats);
     ++nl;
   }
   mark(H2_PH_LEAF_NEAR);
   if (b.wtotal[2]) launch_rows_phase(b, 2, st), ++nl;
   if (b.wtotal[3]) launch_rows_phase(b, 3, st), ++nl;
+  if (b.nred[3]) k_batch_reduce<<<b.nred[3], 128, 0, st>>>(b.d_red[3]), ++nl;
   mark(H2_PH_PERMUTE_OUT);
   k_batch_permute_out<<<pgrid, kPermThreads, 0, st>>>(b.d_perm_out, np, b.perm_total, y);
   ++nl;
@@ -585,6 +664,11 @@ void free_batch(h2_batch_s *b) {
   drop_graph(*b);
   for (auto &d : b->d_rows)
     if (d) cudaFree(d);
+  for (int ph = 0; ph < kRowPhases; ++ph) {
+    if (b->d_chunks[ph]) cudaFree(b->d_chunks[ph]);
+    if (b->scratch[ph]) cudaFree(b->scratch[ph]);
+    if (b->d_red[ph]) cudaFree(b->d_red[ph]);
+  }
   for (auto p : b->d_up) cudaFree(p);
   for (auto p : b->d_down) cudaFree(p);
   if (b->d_perm_in) cudaFree(b->d_perm_in);
@@ -723,10 +807,93 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
     nr.M = L, nr.Mp = Lp, nr.K = L;
     nr.accumulate = far ? 1 : 0;
     if (far) max_steps = std::max(max_steps, d.depth - d.first_adm_level);
-    b->tr_smem = std::max(b->tr_smem, ((size_t)3 * k * rp + 6 * d.m * d.m) * sizeof(float));
+    b->tr_wfloats = std::max(b->tr_wfloats, (3 * k * rp + 6 * d.m * d.m + 3) / 4 * 4);
+    for (int ph = 0; ph < kRowPhases; ++ph) b->rows[ph][p].cap = kNoCap;
+  }
+
+  // rows of the coupling and the nearfield with more than kChunkTerms terms
+  // (cube surfaces produce clusters with hundreds of blocks): the row keeps
+  // its first kChunkTerms terms, the rest become chunk rows of their own that
+  // write partial sums, added to the row afterwards in chunk order
+  for (int ph : {1, 3}) {
+    std::vector<int64_t> cb, ce_;
+    std::vector<BRed> red;
+    std::vector<BRows> extra;
+    for (int p = 0; p < nprob; ++p) {
+      BRows &q = b->rows[ph][p];
+      if (q.nrows == 0) continue;
+      const Plan &pl = b->probs[p].h->plan;
+      const int64_t *hp = ph == 1 ? pl.adm_ptr.data() + q.row0 : pl.near_ptr.data();
+      BRows x = q;
+      x.nrows = 0;
+      const int64_t first_chunk = (int64_t)cb.size();
+      for (int64_t r = 0; r < q.nrows; ++r) {
+        const int64_t nt = hp[r + 1] - hp[r];
+        if (nt <= kChunkTerms) continue;
+        const int64_t nch = (nt - 1) / kChunkTerms;   // chunks beyond the first
+        BRed rd{};
+        rd.out = q.out + r * q.out_stride;
+        rd.part = nullptr;   // set once the partial rows are allocated
+        rd.nch = (int)nch;
+        rd.len = q.M * q.rp;
+        red.push_back(rd);
+        for (int64_t j = 1; j <= nch; ++j) {
+          cb.push_back(hp[r] + j * kChunkTerms);
+          ce_.push_back(std::min(hp[r + 1], hp[r] + (j + 1) * kChunkTerms));
+        }
+        x.nrows += nch;
+      }
+      if (x.nrows == 0) continue;
+      q.cap = kChunkTerms;
+      x.ptr = reinterpret_cast<const int64_t *>(first_chunk);   // rebased below
+      x.row0 = 0;
+      x.pend = nullptr;
+      x.accumulate = 0;
+      x.out_stride = (int64_t)q.M * q.rp;
+      x.cap = kNoCap;
+      extra.push_back(x);
+    }
+    if (extra.empty()) continue;
+    // partial rows: float offsets of every extra entry (rows of M rp values)
+    int64_t floats = 0;
+    std::vector<int64_t> fl_off(extra.size());
+    for (size_t i = 0; i < extra.size(); ++i) {
+      fl_off[i] = floats;
+      floats += extra[i].nrows * extra[i].M * extra[i].rp;
+    }
+    const size_t nc = cb.size();
+    if ((ce = cudaMalloc((void **)&b->d_chunks[ph], 2 * nc * sizeof(int64_t))) != cudaSuccess ||
+        (ce = cudaMalloc((void **)&b->scratch[ph], (size_t)floats * sizeof(float))) != cudaSuccess ||
+        (ce = cudaMalloc((void **)&b->d_red[ph], red.size() * sizeof(BRed))) != cudaSuccess)
+      return bail(cuda_fail(ce, "chunk rows"));
+    std::vector<int64_t> both(cb);
+    both.insert(both.end(), ce_.begin(), ce_.end());
+    if ((ce = cudaMemcpy(b->d_chunks[ph], both.data(), both.size() * sizeof(int64_t), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return bail(cuda_fail(ce, "chunk rows"));
+    // rebase: chunk bounds and partial rows of each extra entry
+    size_t ri = 0;
+    for (size_t i = 0; i < extra.size(); ++i) {
+      BRows &x = extra[i];
+      const int64_t c0 = reinterpret_cast<int64_t>(x.ptr);
+      x.ptr = b->d_chunks[ph] + c0;
+      x.pend = b->d_chunks[ph] + nc + c0;
+      x.out = b->scratch[ph] + fl_off[i];
+      // the reductions of this entry's rows, in row order
+      int64_t row_in_entry = 0;
+      while (ri < red.size() && row_in_entry < x.nrows) {
+        red[ri].part = x.out + row_in_entry * x.M * x.rp;
+        row_in_entry += red[ri].nch;
+        ++ri;
+      }
+      b->rows[ph].push_back(x);
+    }
+    if ((ce = cudaMemcpy(b->d_red[ph], red.data(), red.size() * sizeof(BRed), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(cuda_fail(ce, "chunk reductions"));
+    b->nred[ph] = (int)red.size();
   }
   for (int ph = 0; ph < kRowPhases; ++ph) {
-    if ((ce = cudaMalloc((void **)&b->d_rows[ph], sizeof(BRows) * nprob)) != cudaSuccess)
+    if ((ce = cudaMalloc((void **)&b->d_rows[ph], sizeof(BRows) * b->rows[ph].size())) != cudaSuccess)
       return bail(cuda_fail(ce, "batch descriptors"));
     int rc = upload_rows(*b, ph);
     if (rc) return bail(rc);
@@ -736,7 +903,7 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
   for (int up = 0; up < 2; ++up) {
     for (int s = 0; s < max_steps; ++s) {
       std::vector<BTr> ent;
-      int64_t cta = 0;
+      int64_t tot = 0;
       for (int p = 0; p < nprob; ++p) {
         const auto &P = b->probs[p];
         const Dev &d = P.h->d;
@@ -746,12 +913,12 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
         t.Ef = (const float *)d.Ef;
         t.hat = up ? P.xhat : P.yhat;
         t.par0 = ((int64_t)1 << l) - 1;
-        t.cta0 = cta;
+        t.g0 = tot;
         t.m = d.m;
         t.k = d.k;
         t.rp = P.rp;
         ent.push_back(t);
-        cta += (int64_t)1 << l;
+        tot += (int64_t)1 << l;
       }
       BTr *dp = nullptr;
       if ((ce = cudaMalloc((void **)&dp, sizeof(BTr) * ent.size())) != cudaSuccess)
@@ -760,12 +927,15 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
       if ((ce = cudaMemcpy(dp, ent.data(), sizeof(BTr) * ent.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(ce, "transfer descriptors"));
       (up ? b->n_up : b->n_down).push_back((int)ent.size());
-      (up ? b->cta_up : b->cta_down).push_back(cta);
+      (up ? b->tot_up : b->tot_down).push_back(tot);
     }
   }
-  if (b->tr_smem > 48 * 1024) {
-    cudaFuncSetAttribute((const void *)k_batch_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->tr_smem);
-    cudaFuncSetAttribute((const void *)k_batch_downward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->tr_smem);
+  {
+    const int trs = kTrWarps * b->tr_wfloats * (int)sizeof(float);
+    if (trs > 48 * 1024) {
+      cudaFuncSetAttribute((const void *)k_batch_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, trs);
+      cudaFuncSetAttribute((const void *)k_batch_downward, cudaFuncAttributeMaxDynamicSharedMemorySize, trs);
+    }
   }
 
   // permutations
@@ -904,9 +1074,9 @@ int h2_batch_phase_times(h2_batch b, double *ms, int64_t *launches, int64_t *pro
     launches[H2_PH_PERMUTE_IN] = 1;
     launches[H2_PH_LEAF_FORWARD] = b->wtotal[0] ? 1 : 0;
     launches[H2_PH_UPWARD] = (int64_t)b->d_up.size();
-    launches[H2_PH_COUPLING] = b->wtotal[1] ? 1 : 0;
+    launches[H2_PH_COUPLING] = (b->wtotal[1] ? 1 : 0) + (b->nred[1] ? 1 : 0);
     launches[H2_PH_DOWNWARD] = (int64_t)b->d_down.size();
-    launches[H2_PH_LEAF_NEAR] = (b->wtotal[2] ? 1 : 0) + (b->wtotal[3] ? 1 : 0);
+    launches[H2_PH_LEAF_NEAR] = (b->wtotal[2] ? 1 : 0) + (b->wtotal[3] ? 1 : 0) + (b->nred[3] ? 1 : 0);
     launches[H2_PH_PERMUTE_OUT] = 1;
   }
   if (products) *products = b->products;
@@ -920,7 +1090,7 @@ int h2_batch_info(h2_batch b, int64_t *info) {
   info[2] = b->dofs;
   info[3] = b->work_bytes;
   int64_t nl = 2 + (int64_t)b->d_up.size() + (int64_t)b->d_down.size();
-  for (int ph = 0; ph < kRowPhases; ++ph) nl += b->wtotal[ph] ? 1 : 0;
+  for (int ph = 0; ph < kRowPhases; ++ph) nl += (b->wtotal[ph] ? 1 : 0) + (b->nred[ph] ? 1 : 0);
   info[4] = nl;
   for (int ph = 0; ph < kRowPhases; ++ph) info[5 + ph] = b->shape[ph];
   return H2_OK;

@@ -20,10 +20,11 @@ namespace {
 constexpr int kMaxM = 5;
 
 template <class T>
-__device__ __forceinline__ void mode_fibres(const T *F, const T *in, T *out, int m, int k, int rp, int d, bool trans) {
+__device__ __forceinline__ void mode_fibres(const T *F, const T *in, T *out, int m, int k, int rp, int d, bool trans,
+                                            int tid, int nthr) {
   const int stride = d == 0 ? 1 : (d == 1 ? m : m * m);
   const int items = (k / m) * rp;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+  for (int it = tid; it < items; it += nthr) {
     const int c = it % rp, f = it / rp;
     const int lo = f % stride, hi = f / stride;
     const int base = lo + hi * stride * m;
@@ -74,11 +75,11 @@ __device__ __forceinline__ void upward_parent(const TS *__restrict__ Ef, int m, 
     for (int i = threadIdx.x; i < kr; i += blockDim.x) a[i] = xhat[c * kr + i];
     __syncthreads();
     const T *Fc = F + ch * 3 * mm;
-    mode_fibres(Fc, a, b, m, k, rp, 0, true);
+    mode_fibres(Fc, a, b, m, k, rp, 0, true, threadIdx.x, blockDim.x);
     __syncthreads();
-    mode_fibres(Fc + mm, b, a, m, k, rp, 1, true);
+    mode_fibres(Fc + mm, b, a, m, k, rp, 1, true, threadIdx.x, blockDim.x);
     __syncthreads();
-    mode_fibres(Fc + 2 * mm, a, b, m, k, rp, 2, true);
+    mode_fibres(Fc + 2 * mm, a, b, m, k, rp, 2, true, threadIdx.x, blockDim.x);
     __syncthreads();
     for (int i = threadIdx.x; i < kr; i += blockDim.x) acc[i] = acc[i] + b[i];
     __syncthreads();
@@ -101,14 +102,70 @@ __device__ __forceinline__ void downward_parent(const TS *__restrict__ Ef, int m
   for (int ch = 0; ch < 2; ++ch) {
     const int64_t c = 2 * par + 1 + ch;
     const T *Fc = F + ch * 3 * mm;
-    mode_fibres(Fc, p, a, m, k, rp, 0, false);
+    mode_fibres(Fc, p, a, m, k, rp, 0, false, threadIdx.x, blockDim.x);
     __syncthreads();
-    mode_fibres(Fc + mm, a, b, m, k, rp, 1, false);
+    mode_fibres(Fc + mm, a, b, m, k, rp, 1, false, threadIdx.x, blockDim.x);
     __syncthreads();
-    mode_fibres(Fc + 2 * mm, b, a, m, k, rp, 2, false);
+    mode_fibres(Fc + 2 * mm, b, a, m, k, rp, 2, false, threadIdx.x, blockDim.x);
     __syncthreads();
     for (int i = threadIdx.x; i < kr; i += blockDim.x) yhat[c * kr + i] = yhat[c * kr + i] + a[i];
     __syncthreads();
+  }
+}
+
+// Warp-level variants: one warp per parent, the warp's own shared memory
+// (3 k rp + 6 m^2 values of T), warp synchronisation only.  For the small
+// per-parent tensors of low orders and few right-hand sides a whole CTA per
+// parent leaves most threads idle.
+template <class TS, class T>
+__device__ __forceinline__ void upward_parent_warp(const TS *__restrict__ Ef, int m, int k, int rp, int64_t par,
+                                                   T *__restrict__ xhat, T *ws, int lane) {
+  const int kr = k * rp, mm = m * m;
+  T *a = ws;
+  T *b = a + kr;
+  T *acc = b + kr;
+  T *F = acc + kr;
+  for (int i = lane; i < 6 * mm; i += 32) F[i] = to_compute<T>(Ef[(2 * par + 1) * 3 * mm + i]);
+  for (int ch = 0; ch < 2; ++ch) {
+    const int64_t c = 2 * par + 1 + ch;
+    for (int i = lane; i < kr; i += 32) a[i] = xhat[c * kr + i];
+    __syncwarp();
+    const T *Fc = F + ch * 3 * mm;
+    mode_fibres(Fc, a, b, m, k, rp, 0, true, lane, 32);
+    __syncwarp();
+    mode_fibres(Fc + mm, b, a, m, k, rp, 1, true, lane, 32);
+    __syncwarp();
+    mode_fibres(Fc + 2 * mm, a, b, m, k, rp, 2, true, lane, 32);
+    __syncwarp();
+    for (int i = lane; i < kr; i += 32) acc[i] = ch == 0 ? b[i] : acc[i] + b[i];
+    __syncwarp();
+  }
+  for (int i = lane; i < kr; i += 32) xhat[par * kr + i] = acc[i];
+  __syncwarp();
+}
+
+template <class TS, class T>
+__device__ __forceinline__ void downward_parent_warp(const TS *__restrict__ Ef, int m, int k, int rp, int64_t par,
+                                                     T *__restrict__ yhat, T *ws, int lane) {
+  const int kr = k * rp, mm = m * m;
+  T *p = ws;
+  T *a = p + kr;
+  T *b = a + kr;
+  T *F = b + kr;
+  for (int i = lane; i < 6 * mm; i += 32) F[i] = to_compute<T>(Ef[(2 * par + 1) * 3 * mm + i]);
+  for (int i = lane; i < kr; i += 32) p[i] = yhat[par * kr + i];
+  __syncwarp();
+  for (int ch = 0; ch < 2; ++ch) {
+    const int64_t c = 2 * par + 1 + ch;
+    const T *Fc = F + ch * 3 * mm;
+    mode_fibres(Fc, p, a, m, k, rp, 0, false, lane, 32);
+    __syncwarp();
+    mode_fibres(Fc + mm, a, b, m, k, rp, 1, false, lane, 32);
+    __syncwarp();
+    mode_fibres(Fc + 2 * mm, b, a, m, k, rp, 2, false, lane, 32);
+    __syncwarp();
+    for (int i = lane; i < kr; i += 32) yhat[c * kr + i] = yhat[c * kr + i] + a[i];
+    __syncwarp();
   }
 }
 

@@ -23,6 +23,10 @@ SMALL = [
     (lambda: I.icosphere(2), 8, 2, 5),
     (lambda: I.cube(9), 16, 3, 16),
     (lambda: I.ellipsoid(2, (0.7, 1.3, 1.9)), 24, 4, 12),
+    # a cube whose clusters reach 138 admissible and 140 nearfield blocks per row:
+    # those rows are cut in chunks and their partial sums added in order
+    (lambda: I.cube(30), 16, 3, 4),
+    (lambda: I.cube(30), 32, 4, 2),
 ]
 
 _cache = {}
@@ -131,8 +135,9 @@ def test_batch_tune_profile_and_launch_count(require_gpu):
         b.matvec(x, y)
     ph, n = b.phase_times()
     assert n == 3 and all(v[0] >= 0 for v in ph.values())
-    # one launch per block-row phase, one per transfer level step, two permutations
-    assert ph["leaf_forward"][1] == 1 and ph["coupling"][1] == 1 and ph["leaf_near"][1] == 2
+    # one launch per block-row phase, one per transfer level step, two permutations, and
+    # one reduction each for the coupling and nearfield rows cut in chunks (the cube)
+    assert ph["leaf_forward"][1] == 1 and ph["coupling"][1] == 2 and ph["leaf_near"][1] == 3
     info = b.info()
     assert info["launches"] == sum(v[1] for v in ph.values())
     for p, yv in zip(probs, b.split(y)):

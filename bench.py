@@ -193,10 +193,10 @@ def run_ours(args):
     cpl_ms = phases["coupling"][0] / products
     if args.prec == "f64n":
         roof = {"bound": "alu", "achieved": alg["coupling_flops"] / (cpl_ms * 1e-3) / 1e12, "peak": FP64_TFLOPS,
-                "unit": "TFLOP/s", "kernel": "k_coupling (FP64 FMA pipe)"}
+                "unit": "TFLOP/s", "kernel": "k_blockrow (coupling, FP64 FMA pipe)"}
     elif args.prec == "f64":
         roof = {"bound": "alu", "achieved": alg["coupling_flops"] / (cpl_ms * 1e-3) / 1e12, "peak": DD_TFLOPS,
-                "unit": "TFLOP/s", "kernel": "k_coupling (double-float on the FP32 pipe)",
+                "unit": "TFLOP/s", "kernel": "k_blockrow (coupling, double-float on the FP32 pipe)",
                 "hbm_frac": alg["coupling_bytes"] / (cpl_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
     elif args.prec in ("bf16", "f16"):
         # regenerated coupling: 2 k^2 nrhs multiply-adds plus one kernel evaluation
@@ -209,7 +209,12 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": alg["coupling_bytes"] / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "kernel": "k_blockrow (coupling, stored S stream)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes (read + write) per coupling launch from the ncu capture of the
+    # same kernel at level 5 (profiles/k_blockrow_coupling_icosphere_L5_m4_16rhs_f64.md),
+    # scaled by admissible blocks; None where no capture of the current kernel exists
+    traffic_per_block = {"f64": 691.93e6 / 18876}
+    roof["traffic"] = (traffic_per_block[args.prec] * st["adm_blocks"]
+                       if args.prec in traffic_per_block and args.order == 4 and args.nrhs == 16 else None)
     roof["peak_source"] = {"f64n": "nominal FP64 rate",
                            "f64": "FP32 FMA rate (152 SMs x 128 lanes x 2.07 GHz) / 12 instructions per dd FMA",
                            "f32": f"{peaks['src']} HBM copy bandwidth",
@@ -271,8 +276,8 @@ def run_ours(args):
         mixed = run_mixed(args, local, stream)
 
     batch = None
-    if rank == 0 and not args.no_batch:
-        batch = run_batch(args, local, stream)
+    if not args.no_batch:
+        batch = run_batch(args, local, stream, ws, rank)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -434,7 +439,7 @@ def run_mixed(args, local, stream):
     return out
 
 
-def run_batch(args, local, stream):
+def run_batch(args, local, stream, ws=1, rank=0):
     """Uneven batch: independent FP32 problems (random ellipsoids and subdivided
     cubes of 20k-400k triangles, m = 3 or 4, 1-8 RHS; leaf sizes chosen by the
     measuring autotuner) multiplied together, one persistent launch per
@@ -442,8 +447,10 @@ def run_batch(args, local, stream):
     coupling kernel's HBM roofline fraction and an end-to-end figure with the
     packed vectors copied from and to pinned host memory."""
     import torch
-    from paper_2203_05665_gb300 import Batch, H2Matrix, inputs, tune
-    specs = inputs.batch_problems(args.batch_problems, 1004)
+    from paper_2203_05665_gb300 import Batch, H2Matrix, inputs, shard, tune
+    all_specs = inputs.batch_problems(args.batch_problems, 1004)
+    # N GPUs: each rank takes its share of the independent problems (weak scaling, no collective on the data path)
+    specs = shard.shard_problems(all_specs, ws)[rank]
     t0 = time.time()
     free, _ = torch.cuda.mem_get_info()
     notes = []
@@ -474,16 +481,24 @@ def run_batch(args, local, stream):
     shape_s = time.time() - t0
     for _ in range(args.warmup):
         b.matvec(x, y)
-    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(args.steps, 5)
+    barrier()
     e0.record(stream)
     for _ in range(reps):
         b.matvec(x, y)
     e1.record(stream)
-    torch.cuda.synchronize()
+    barrier()
     b.sync()
-    ms = e0.elapsed_time(e1) / reps
+    ms_rank = e0.elapsed_time(e1) / reps
+    ms, all_dofs = shard.combine(ms_rank, b.info()["dofs"])
     b.profile(True)
     for _ in range(5):
         b.matvec(x, y)
@@ -512,15 +527,17 @@ def run_batch(args, local, stream):
         torch.cuda.synchronize()
         if i >= 2:
             lat.append(time.perf_counter() - t1)
-    e2e_s = statistics.median(lat)
+    e2e_ms, _ = shard.combine(statistics.median(lat) * 1e3, 0)
+    e2e_s = e2e_ms * 1e-3
     leaves = [leaf[s["index"]] for s in specs]
-    out = {"workload": f"{len(specs)} problems: ellipsoids (icosphere L5-L7, semi-axes U[0.5,2]) and cubes "
+    out = {"workload": f"{len(all_specs)} problems: ellipsoids (icosphere L5-L7, semi-axes U[0.5,2]) and cubes "
                        f"(s in 41..182), m in {{3,4}}, 1-8 RHS, FP32 stored S, eta 2",
-           "problems": len(specs), "triangles": int(sum(s["n"] for s in specs)), "dofs_x_rhs": int(info["dofs"]),
+           "problems": len(all_specs), "problems_rank0": len(specs), "n_gpus": ws, "scaling": "weak",
+           "triangles": int(sum(s["n"] for s in all_specs)), "dofs_x_rhs": int(all_dofs),
            "leaf_counts": {str(lf): leaves.count(lf) for lf in sorted(set(leaves))},
            "leaf_tuning_ms": {str(k): v for k, v in timings.items()}, "tune_notes": notes,
            "shapes": shapes, "tune_s": tune_s, "shape_tune_s": shape_s, "build_s": build_s,
-           "ms_per_product": ms, "dof_per_s": info["dofs"] / (ms * 1e-3),
+           "ms_per_product": ms, "dof_per_s": all_dofs / (ms * 1e-3),
            "phases_ms": {k: v[0] / prods for k, v in ph.items()}, "gpu_launches": info["launches"],
            "graph": True,
            "roofline": {"bound": "hbm", "kernel": "k_batch_rows (coupling)", "unit": "GB/s",
@@ -529,7 +546,7 @@ def run_batch(args, local, stream):
                         "hbm_frac_whole_product": tbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                         "hbm_frac_leaf_near": nbytes / (ph["leaf_near"][0] / prods * 1e-3) / 1e9 / peaks["hbm_gbs"]},
            "device_bytes": int(sum(m.stats["device_bytes"] for m in mats) + info["work_bytes"]),
-           "e2e": {"value": info["dofs"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(4 * b.length),
+           "e2e": {"value": all_dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(4 * b.length),
                    "d2h_bytes_per_step": int(4 * b.length)},
            "l2": "inputs larger than L2"}
     b.close()

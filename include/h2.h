@@ -210,9 +210,10 @@ int h2_solve_ir(h2_handle hi, h2_handle lo, const double *b, double *z, int nrhs
                 int restart, int maxit_inner, int maxit_outer, h2_solve_info *info);
 
 /* ---------------------------------------------------------------------------
- * Serving with continuous batching.  A server owns a worker thread that
- * solves queued right-hand sides on registered matrices.  Each registered
- * matrix gets an engine with `slots` column slots; the columns of all its
+ * Serving with continuous batching.  A server solves queued right-hand
+ * sides on registered matrices.  Each registered matrix gets an engine with
+ * its own worker thread and CUDA stream (engines of different matrices run
+ * concurrently) and `slots` column slots; the columns of all its
  * requests share one batched product per Arnoldi step, and at every restart
  * cycle finished columns leave and queued requests are admitted into the
  * free slots.  With a low-precision partner handle lo the engine runs
@@ -222,8 +223,10 @@ int h2_solve_ir(h2_handle hi, h2_handle lo, const double *b, double *z, int nrhs
  * space (about (restart + 9) n slots doubles) is allocated when its first
  * request is admitted, within hbm_budget bytes (0 = 90 % of the free device
  * memory at creation), and released when the engine is idle and another
- * needs the room.  Registered handles must not be used by other threads
- * while the server runs.
+ * needs the room.  Registered handles belong to the server until it is
+ * destroyed: they must not be used by other threads meanwhile, a handle can
+ * be registered once (as hi or lo), and their streams are replaced by the
+ * engine's stream and restored by h2_serve_destroy.
  * ------------------------------------------------------------------------- */
 typedef struct h2_srv *h2_server;
 int h2_serve_create(int device, size_t hbm_budget, h2_server *out);
@@ -244,7 +247,8 @@ int h2_serve_wait(h2_server s, uint64_t ticket, double timeout_s);
 /* stats[6]: queued requests, running columns, completed requests, engine
  * steps, device bytes in use by engines, budget. */
 int h2_serve_stats(h2_server s, int64_t *stats);
-/* Stop the worker (running requests are abandoned) and free the engines. */
+/* Stop the engines' workers (running requests are abandoned), free the
+ * engines and give the handles back their streams. */
 int h2_serve_destroy(h2_server s);
 
 /* Phases of the product, in launch order (h2_phase_times). */

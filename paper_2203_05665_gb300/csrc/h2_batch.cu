@@ -932,9 +932,11 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
   }
   {
     const int trs = kTrWarps * b->tr_wfloats * (int)sizeof(float);
-    if (trs > 48 * 1024) {
-      cudaFuncSetAttribute((const void *)k_batch_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, trs);
-      cudaFuncSetAttribute((const void *)k_batch_downward, cudaFuncAttributeMaxDynamicSharedMemorySize, trs);
+    if ((size_t)trs > kBatchSmemMax) return bail(fail(H2_EINVAL, "transfer work space does not fit in shared memory"));
+    if (trs > 48 * 1024) {   // one value for all batches (they may be created from several threads)
+      cudaFuncSetAttribute((const void *)k_batch_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax);
+      cudaFuncSetAttribute((const void *)k_batch_downward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBatchSmemMax);
     }
   }
 

@@ -104,6 +104,8 @@ struct GmresWork {
   double *h1 = nullptr, *h2 = nullptr, *hn = nullptr, *resid = nullptr, *yv = nullptr, *bn = nullptr;
   double *r = nullptr, *d = nullptr, *Az = nullptr;   // refinement vectors
   int *active = nullptr, *jc = nullptr;
+  double *tolv = nullptr;                 // per column: residual target of the cycle
+  int *maxv = nullptr, *itc = nullptr;    // per column: iteration limit, iterations done
 };
 void free_gmres_work(GmresWork &w);
 

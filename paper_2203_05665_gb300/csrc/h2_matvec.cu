@@ -640,9 +640,15 @@ int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
 }
 
+// Allow the kernel the largest dynamic shared memory once it needs more than
+// the default 48 KB.  Always the same value: products of different handles
+// run concurrently from several threads (serving), and a smaller limit set
+// by one of them must never undercut another's launch.
 template <class T>
 int set_smem(const void *fn, size_t bytes) {
-  if (bytes > 48 * 1024) H2_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  if (bytes > kSmemMax) return fail(H2_EINVAL, "tile does not fit in shared memory");
+  if (bytes > 48 * 1024)
+    H2_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
   return H2_OK;
 }
 

@@ -1,7 +1,9 @@
 // Solve serving with continuous batching (h2_serve_*).
 //
-// A worker thread owns the GPU work.  Every registered matrix gets an engine
-// with a fixed number of column slots; the right-hand sides of all requests
+// Every registered matrix gets an engine with its own worker thread and its
+// own CUDA stream (the engines of different matrices run concurrently on the
+// device and hide each other's host round trips), and a fixed number of
+// column slots; the right-hand sides of all requests
 // on that matrix share one batched product per Arnoldi step.  The engine
 // advances in restart cycles of GMRES (or refinement steps of GMRES-IR when a
 // low-precision handle is registered with it):
@@ -57,6 +59,9 @@ struct Slot {
 
 struct Engine {
   h2_ctx *hi = nullptr, *lo = nullptr;
+  cudaStream_t st = nullptr;                      // the engine's stream (set on its handles while registered)
+  cudaStream_t hi_stream = nullptr, lo_stream = nullptr;   // the handles' own streams, restored at the end
+  std::thread th;
   int64_t n = 0;
   int cap = 0, restart = 30, maxit = 5000;
   double inner_rtol = 1e-4;
@@ -80,7 +85,6 @@ struct h2_srv {
   std::mutex mu;
   std::condition_variable cv;
   bool stop = false;
-  std::thread worker;
   std::deque<h2::Request *> queue;
   std::map<uint64_t, std::unique_ptr<h2::Request>> reqs;
   std::vector<std::unique_ptr<h2::Engine>> engines;
@@ -251,45 +255,42 @@ int step(h2_srv &s, int ei, std::unique_lock<std::mutex> &lk) {
   if (e.lo) H2_CUDA_TRY(cudaStreamSynchronize(cyc.stream));
   for (int i = 0; i < na; ++i) e.slots[i].iters += it[i];
   k_launch_axpy(e.D, e.n * na, e.Z, st);
+  lk.lock();
   s.steps++;
+  lk.unlock();
   return take_device_error(*e.hi);
 }
 
-void worker_main(h2_srv *s) {
+// worker thread of engine ei
+void engine_main(h2_srv *s, int ei) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
+  Engine &e = *s->engines[ei];
   while (!s->stop) {
-    bool busy = false;
-    for (auto &e : s->engines) busy = busy || !e->slots.empty();
-    if (!busy && s->queue.empty()) {
+    bool waiting = false;
+    for (Request *q : s->queue) waiting = waiting || q->engine == ei;
+    if (e.slots.empty() && !waiting) {
       s->cv.wait_for(lk, std::chrono::milliseconds(50));
       continue;
     }
-    bool progressed = false;
-    for (int ei = 0; ei < (int)s->engines.size() && !s->stop; ++ei) {
-      Engine &e = *s->engines[ei];
-      bool waiting = false;
-      for (Request *q : s->queue) waiting = waiting || q->engine == ei;
-      if (e.slots.empty() && !waiting) continue;
-      lk.unlock();
-      int rc = step(*s, ei, lk);
-      lk.lock();
-      progressed = progressed || !e.slots.empty();
-      if (rc) {
-        // fail every request of this engine, keep serving the others
-        s->fatal = rc;
-        s->fatal_msg = h2_last_error();
-        for (auto &kv : s->reqs)
-          if (kv.second->engine == ei && !kv.second->done) {
-            kv.second->done = true;
-            kv.second->queued = false;
-            kv.second->status = rc;
-          }
-        s->queue.erase(std::remove_if(s->queue.begin(), s->queue.end(), [&](Request *q) { return q->engine == ei; }),
-                       s->queue.end());
-        e.slots.clear();
-        s->cv.notify_all();
-      }
+    lk.unlock();
+    int rc = step(*s, ei, lk);
+    lk.lock();
+    const bool progressed = !e.slots.empty();
+    if (rc) {
+      // fail every request of this engine, keep serving the others
+      s->fatal = rc;
+      s->fatal_msg = h2_last_error();
+      for (auto &kv : s->reqs)
+        if (kv.second->engine == ei && !kv.second->done) {
+          kv.second->done = true;
+          kv.second->queued = false;
+          kv.second->status = rc;
+        }
+      s->queue.erase(std::remove_if(s->queue.begin(), s->queue.end(), [&](Request *q) { return q->engine == ei; }),
+                     s->queue.end());
+      e.slots.clear();
+      s->cv.notify_all();
     }
     // queued work that cannot be admitted yet (memory): do not spin
     if (!progressed) s->cv.wait_for(lk, std::chrono::milliseconds(5));
@@ -316,12 +317,6 @@ int h2_serve_create(int device, size_t hbm_budget, h2_server *out) {
   if (!s) return fail(H2_ENOMEM, "server");
   s->device = device;
   s->budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)fr);
-  try {
-    s->worker = std::thread(worker_main, s);
-  } catch (...) {
-    delete s;
-    return fail(H2_ENOMEM, "worker thread");
-  }
   *out = s;
   return H2_OK;
 }
@@ -336,7 +331,8 @@ int h2_serve_register(h2_server s, h2_handle hi, h2_handle lo, int slots, int re
     return fail(H2_EINVAL, "lo must be a second handle of the same matrix structure");
   std::lock_guard<std::mutex> g(s->mu);
   for (auto &e : s->engines)
-    if (e->hi == hi) return fail(H2_EBUSY, "handle already registered");
+    if (e->hi == hi || e->lo == hi || (lo && (e->hi == lo || e->lo == lo)))
+      return fail(H2_EBUSY, "handle already registered");
   auto e = std::make_unique<Engine>();
   e->hi = hi;
   e->lo = lo;
@@ -346,7 +342,29 @@ int h2_serve_register(h2_server s, h2_handle hi, h2_handle lo, int slots, int re
   e->maxit = maxit;
   e->inner_rtol = lo ? inner_rtol : 0.0;
   if (e->work_bytes() > s->budget) return fail(H2_ENOMEM, "one engine does not fit in the memory budget");
+  // the engine runs its handles on a stream of its own while they are registered
+  H2_CUDA_TRY(cudaSetDevice(s->device));
+  if (hi->stream) H2_CUDA_TRY(cudaStreamSynchronize(hi->stream));
+  if (lo && lo->stream) H2_CUDA_TRY(cudaStreamSynchronize(lo->stream));
+  H2_CUDA_TRY(cudaDeviceSynchronize());
+  H2_CUDA_TRY(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking));
+  e->hi_stream = hi->stream;
+  hi->stream = e->st;
+  if (lo) {
+    e->lo_stream = lo->stream;
+    lo->stream = e->st;
+  }
+  Engine *ep = e.get();
   s->engines.push_back(std::move(e));
+  try {
+    ep->th = std::thread(engine_main, s, (int)s->engines.size() - 1);
+  } catch (...) {
+    hi->stream = ep->hi_stream;
+    if (lo) lo->stream = ep->lo_stream;
+    cudaStreamDestroy(ep->st);
+    s->engines.pop_back();
+    return fail(H2_ENOMEM, "engine thread");
+  }
   return H2_OK;
 }
 
@@ -430,9 +448,16 @@ int h2_serve_destroy(h2_server s) {
     s->stop = true;
     s->cv.notify_all();
   }
-  if (s->worker.joinable()) s->worker.join();
+  for (auto &e : s->engines)
+    if (e->th.joinable()) e->th.join();
   cudaSetDevice(s->device);
-  for (auto &e : s->engines) release(*e, *s);
+  for (auto &e : s->engines) {
+    if (e->st) cudaStreamSynchronize(e->st);
+    release(*e, *s);
+    e->hi->stream = e->hi_stream;
+    if (e->lo) e->lo->stream = e->lo_stream;
+    if (e->st) cudaStreamDestroy(e->st);
+  }
   delete s;
   return H2_OK;
 }

@@ -64,11 +64,15 @@ __global__ void k_scale(const double *__restrict__ W, const double *__restrict__
 }
 
 // Hessenberg column j: h1 + h2 from the two Gram-Schmidt passes, then the
-// Givens rotations; H[(i * mr + j) * nrhs + c]
+// Givens rotations; H[(i * mr + j) * nrhs + c].  The column's convergence
+// test runs here too: it leaves the cycle (active = 0) once its residual
+// estimate reaches tol, at a breakdown (hn = 0) or at its iteration limit;
+// itc counts its iterations and jc its Arnoldi vectors.
 __global__ void k_givens(const double *__restrict__ h1, const double *__restrict__ h2, const double *__restrict__ hn,
                          int j, int mr, int nrhs, double *__restrict__ H, double *__restrict__ cs,
                          double *__restrict__ sn, double *__restrict__ g, double *__restrict__ resid,
-                         const int *__restrict__ active) {
+                         int *__restrict__ active, const double *__restrict__ tolv, const int *__restrict__ maxv,
+                         int *__restrict__ itc, int *__restrict__ jc) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nrhs || !active[c]) return;
   auto Hc = [&](int i) -> double & { return H[((int64_t)i * mr + j) * nrhs + c]; };
@@ -89,7 +93,12 @@ __global__ void k_givens(const double *__restrict__ h1, const double *__restrict
   double gj = g[j * nrhs + c];
   g[(j + 1) * nrhs + c] = -sj * gj;
   g[j * nrhs + c] = cj * gj;
-  resid[c] = fabs(sj * gj);
+  const double rc = fabs(sj * gj);
+  resid[c] = rc;
+  const int it = itc[c] + 1;
+  itc[c] = it;
+  jc[c] = j + 1;
+  if (rc <= tolv[c] || hn[c] == 0.0 || it >= maxv[c]) active[c] = 0;
 }
 
 // y = R^{-1} g for the first jc[c] columns, then z[:, c] += sum_i y_i V_i[:, c]
@@ -139,8 +148,9 @@ void free_gmres_work(GmresWork &w) {
   double *dp[] = {w.Vb, w.W, w.H, w.cs, w.sn, w.g, w.h1, w.h2, w.hn, w.resid, w.yv, w.bn, w.r, w.d, w.Az};
   for (double *p : dp)
     if (p) cudaFree(p);
-  if (w.active) cudaFree(w.active);
-  if (w.jc) cudaFree(w.jc);
+  for (int *p : {w.active, w.jc, w.maxv, w.itc})
+    if (p) cudaFree(p);
+  if (w.tolv) cudaFree(w.tolv);
   w = GmresWork();
 }
 
@@ -170,7 +180,9 @@ int alloc_gmres_work(GmresWork &w, int64_t n_, int cols, int mr) {
   al(&w.r, tot);
   al(&w.d, tot);
   al(&w.Az, tot);
-  ok = ok && cudaMalloc(&w.active, cols * 4) == cudaSuccess && cudaMalloc(&w.jc, cols * 4) == cudaSuccess;
+  al(&w.tolv, cols);
+  ok = ok && cudaMalloc(&w.active, cols * 4) == cudaSuccess && cudaMalloc(&w.jc, cols * 4) == cudaSuccess &&
+       cudaMalloc(&w.maxv, cols * 4) == cudaSuccess && cudaMalloc(&w.itc, cols * 4) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_gmres_work(w);
@@ -193,8 +205,8 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
   const int mr = restart;
   cudaStream_t st = c.stream;
   int rc;
-  std::vector<double> rn(nrhs), g0((size_t)(mr + 1) * nrhs, 0.0), rs(2 * nrhs);
-  std::vector<int> on(nrhs, 0), jc(nrhs, 0);
+  std::vector<double> rn(nrhs), g0((size_t)(mr + 1) * nrhs, 0.0);
+  std::vector<int> on(nrhs, 0);
   k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(R, R, n, nrhs, w.hn);
   k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
   H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.hn, nrhs * 8, cudaMemcpyDeviceToHost, st));
@@ -209,8 +221,16 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
   H2_CUDA_TRY(cudaMemsetAsync(D, 0, tot * 8, st));
   if (!any) return H2_OK;
   H2_CUDA_TRY(cudaMemcpyAsync(w.active, on.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
+  H2_CUDA_TRY(cudaMemcpyAsync(w.tolv, tol, nrhs * 8, cudaMemcpyHostToDevice, st));
+  H2_CUDA_TRY(cudaMemcpyAsync(w.maxv, max_it, nrhs * 4, cudaMemcpyHostToDevice, st));
+  H2_CUDA_TRY(cudaMemsetAsync(w.itc, 0, nrhs * 4, st));
+  H2_CUDA_TRY(cudaMemsetAsync(w.jc, 0, nrhs * 4, st));
   k_scale<<<grid1(tot), kT, 0, st>>>(R, w.hn, w.active, n, nrhs, w.Vb);
   H2_CUDA_TRY(cudaMemcpyAsync(w.g, g0.data(), (mr + 1) * nrhs * 8, cudaMemcpyHostToDevice, st));
+  // the host looks at the columns' state every `check` iterations only: for
+  // small systems an iteration is shorter than a host round trip, for large
+  // ones an iteration past the last convergence costs more than the trip
+  const int check = tot >= ((int64_t)1 << 20) ? 1 : 4;
   for (int j = 0; j < mr; ++j) {
     double *Vj = w.Vb + (int64_t)j * tot, *Vj1 = w.Vb + (int64_t)(j + 1) * tot;
     if ((rc = run_matvec(c, Vj, w.W, nrhs, true))) return rc;
@@ -222,26 +242,21 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
     k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
     k_scale<<<grid1(tot), kT, 0, st>>>(w.W, w.hn, w.active, n, nrhs, Vj1);
     k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(w.h1, w.h2, w.hn, j, mr, nrhs, w.H, w.cs, w.sn, w.g, w.resid,
-                                              w.active);
+                                              w.active, w.tolv, w.maxv, w.itc, w.jc);
     H2_CUDA_TRY(cudaGetLastError());
-    H2_CUDA_TRY(cudaMemcpyAsync(rs.data(), w.resid, nrhs * 8, cudaMemcpyDeviceToHost, st));
-    H2_CUDA_TRY(cudaMemcpyAsync(rs.data() + nrhs, w.hn, nrhs * 8, cudaMemcpyDeviceToHost, st));
-    H2_CUDA_TRY(cudaStreamSynchronize(st));
-    bool still = false;
-    for (int col = 0; col < nrhs; ++col) {
-      if (!on[col]) continue;
-      jc[col] = j + 1;
-      iters[col]++;
-      if (rs[col] <= tol[col] || rs[nrhs + col] == 0.0 || iters[col] >= max_it[col]) on[col] = 0;
-      still = still || on[col];
+    if ((j + 1) % check == 0 && j + 1 < mr) {
+      H2_CUDA_TRY(cudaMemcpyAsync(on.data(), w.active, nrhs * 4, cudaMemcpyDeviceToHost, st));
+      H2_CUDA_TRY(cudaStreamSynchronize(st));
+      bool still = false;
+      for (int col = 0; col < nrhs; ++col) still = still || on[col];
+      if (!still) break;
     }
-    if (!still) break;
-    H2_CUDA_TRY(cudaMemcpyAsync(w.active, on.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
   }
-  H2_CUDA_TRY(cudaMemcpyAsync(w.jc, jc.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
+  H2_CUDA_TRY(cudaMemcpyAsync(iters, w.itc, nrhs * 4, cudaMemcpyDeviceToHost, st));
   k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(w.H, w.g, w.jc, mr, nrhs, w.yv);
   k_update<<<grid1(tot), kT, 0, st>>>(w.Vb, w.yv, w.jc, n, nrhs, D);
   H2_CUDA_TRY(cudaGetLastError());
+  H2_CUDA_TRY(cudaStreamSynchronize(st));   // iters (host) is written by the copy above
   return H2_OK;
 }
 

@@ -76,7 +76,12 @@ typedef struct h2_options {
   int device;        /* CUDA device ordinal; default 0 */
   void *stream;      /* cudaStream_t used by every call on the handle; NULL = the legacy default stream */
   int coupling;      /* enum h2_coupling; default H2_COUPLING_AUTO */
-  int reserved[7];   /* must be zero */
+  int tensor;        /* 0 (default): an H2_F64 handle with stored coupling and order 4 also keeps its
+                      * coupling matrices as 7 BF16 slices of 7 bits (a power of two per row) and runs
+                      * the coupling phase of products with up to 16 right-hand sides on the tensor
+                      * cores (integer slice products summed exactly, combined in double-float;
+                      * agrees with the double-float path to about 1e-13); 1: never */
+  int reserved[6];   /* must be zero */
 } h2_options;
 
 /* Statistics of a built matrix (h2_info). */
@@ -94,6 +99,7 @@ typedef struct h2_stats {
   int64_t device_bytes;   /* device memory held by the handle (without work buffers) */
   int64_t prec;           /* enum h2_prec */
   int64_t coupling;       /* H2_COUPLING_STORED or H2_COUPLING_REGEN as built */
+  int64_t tensor;         /* 1 if the tensor-core slices of the coupling were built */
 } h2_stats;
 
 /* Per right-hand side result of h2_solve. */

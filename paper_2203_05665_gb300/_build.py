@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libh2.so")
 SOURCES = ["h2_plan.cpp", "h2_api.cpp", "h2_serve.cpp", "h2_setup.cu", "h2_matvec.cu", "h2_solve.cu",
-           "h2_noalloc.cu", "h2_batch.cu"]
+           "h2_noalloc.cu", "h2_batch.cu", "h2_tc.cu"]
 HEADERS = ["h2_internal.hpp", "h2_dd.cuh", "h2_ptx.cuh", "h2_transfer.cuh", os.path.join("..", "..", "include", "h2.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -59,7 +59,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lpthread", "-ldl", "-lrt"])
+        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lpthread", "-ldl", "-lrt",
+             "-Xlinker", "--no-undefined"])
         os.replace(tmp, LIB)
     return LIB
 

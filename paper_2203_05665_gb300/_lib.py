@@ -30,13 +30,13 @@ class H2Error(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("quad_order", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-                ("coupling", C.c_int), ("reserved", C.c_int * 7)]
+                ("coupling", C.c_int), ("tensor", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("n", "depth", "clusters", "leaf_max", "order", "rank", "adm_blocks", "near_blocks",
-                 "near_entries", "first_adm_level", "device_bytes", "prec", "coupling")]
+                 "near_entries", "first_adm_level", "device_bytes", "prec", "coupling", "tensor")]
 
 
 class SolveInfo(C.Structure):
@@ -192,7 +192,7 @@ class H2Matrix:
     """An H² matrix of one mesh on one GPU (see include/h2.h)."""
 
     def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, prec="f64", quad_order=3, device=0,
-                 stream=None, coupling="auto"):
+                 stream=None, coupling="auto", tensor="auto"):
         lib = load()
         v, t = _mesh(vert, tri)
         opt = Options()
@@ -202,6 +202,7 @@ class H2Matrix:
         opt.device = int(device)
         opt.stream = stream
         opt.coupling = COUPLING[coupling]
+        opt.tensor = {"auto": 0, "off": 1}[tensor]
         h = C.c_void_p()
         _check(lib.h2_build(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
                             int(leaf_size), float(eta), int(order), C.byref(opt), C.byref(h)))

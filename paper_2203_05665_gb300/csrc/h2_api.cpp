@@ -26,7 +26,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 static void free_dev(Dev &d) {
-  void *ptrs[] = {d.icen, d.adm_dc, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
+  void *ptrs[] = {d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
                   d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -139,6 +139,7 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
     return fail(H2_EINVAL, "the regenerated coupling is FP32; use H2_F32, H2_BF16 or H2_F16");
   if (o.coupling == H2_COUPLING_STORED && half_prec)
     return fail(H2_EINVAL, "16-bit precisions regenerate the coupling");
+  if (o.tensor < 0 || o.tensor > 1) return fail(H2_EINVAL, "tensor must be 0 (tensor cores where supported) or 1 (never)");
   for (int r : o.reserved)
     if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
   int ndev = 0;
@@ -151,6 +152,7 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   c->stream = (cudaStream_t)o.stream;
   c->quad_order = o.quad_order;
   c->d.prec = o.prec;
+  c->d.tensor = o.tensor;
   c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);
   int rc;
   try {
@@ -203,6 +205,7 @@ int h2_info(h2_handle h, h2_stats *out) {
   out->device_bytes = h->d.bytes;
   out->prec = h->d.prec;
   out->coupling = h->d.coupling == 1 ? H2_COUPLING_REGEN : H2_COUPLING_STORED;
+  out->tensor = h->d.tc ? 1 : 0;
   return H2_OK;
 }
 

@@ -79,6 +79,15 @@ struct Dev {
   double *icen = nullptr;       // nclu x 3 interpolation-box centres (regenerated coupling)
   float *adm_dc = nullptr;      // nadm x 4: centre of the row cluster minus centre of the column cluster
   float *ihalf = nullptr;       // nclu x 3 interpolation-box half widths
+  // FP64-accurate coupling on the tensor cores (order 4): the BF16 slices of
+  // every S_b ([nadm][7][64 x 64], K-major core-matrix layout), the row
+  // exponents ([nclu][64]), the slices of the coefficients of one product
+  // ([nclu][7][16 x 64]) and the column maxima per level ([32][16])
+  int tensor = 0;               // 0: use the tensor cores where supported, 1: never
+  bool tc = false;              // the slices exist
+  void *Stc = nullptr, *xtc = nullptr;
+  int32_t *tc_E = nullptr;
+  unsigned *tc_xmax = nullptr;
   float *vscale = nullptr;      // per leaf: power of two dividing the stored V (FP16), or NULL
   float *nscale = nullptr;      // per nearfield block: the same for G_b, or NULL
   // work buffers for up to cap_nrhs right-hand sides
@@ -127,6 +136,15 @@ inline int padded_rhs(int nrhs, size_t esize) {
 
 // device-side error word (a bounded wait ran out); read and cleared by the host
 int take_device_error(Ctx &c);
+
+// FP64-accurate coupling on the tensor cores (h2_tc.cu): eligibility,
+// set-up of the slices (arow_dev: row cluster of every admissible block, on
+// the device), the coupling phase of one product (xhat, yhat: double-float
+// coefficient arrays [clusters][k][rp]) and that file's device error word
+bool tc_eligible(const Dev &d);
+int tc_build(Ctx &c, const int32_t *arow_dev);
+int tc_coupling(Ctx &c, const void *xhat, void *yhat, int rp);
+int tc_take_error(cudaStream_t st);
 
 // device allocation helper (tracks bytes)
 int dev_alloc(Dev &d, void **ptr, size_t bytes);

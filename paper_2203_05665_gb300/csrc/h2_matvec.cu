@@ -771,6 +771,10 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
       } else {
         return fail(H2_EINVAL, "the regenerated coupling runs in FP32 arithmetic only");
       }
+    } else if (std::is_same<T, dd>::value && d.tc && rp <= 16) {
+      // FP64-accurate: integer slices on the tensor cores
+      if ((rc = tc_coupling(c, xhat, yhat, rp))) return rc;
+      mk.count(H2_PH_COUPLING, 2);
     } else {
       CouplingRows<TS, T> rows{(const TS *)d.S, d.adm_ptr, d.adm_col, xhat, k, kp, rp, row0};
       if ((rc = launch_rows<TS, T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, out, st))) return rc;
@@ -820,7 +824,7 @@ int take_device_error(Ctx &c) {
     H2_CUDA_TRY(cudaStreamSynchronize(c.stream));
     return fail(H2_ETIMEOUT, "a bounded device wait ran out; the last result is not valid");
   }
-  return H2_OK;
+  return c.d.tc ? tc_take_error(c.stream) : H2_OK;
 }
 
 int ensure_work(Ctx &c, int nrhs_req) {

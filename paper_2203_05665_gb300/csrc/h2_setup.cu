@@ -436,6 +436,9 @@ int build_typed(Ctx &c) {
                                                                           d.cheb, m, d.kp, d.nadm, (T *)d.S);
     H2_CUDA_TRY(cudaGetLastError());
   }
+  // FP64-accurate handles of order 4: the BF16 slices for the tensor-core coupling
+  if (d.tensor == 0 && tc_eligible(d) && (rc = tc_build(c, (const int32_t *)t_arow.ptr))) return rc;
+
 
   // nearfield entries; 16-bit storage: computed in FP64 first, then rounded
   // (FP16: with a power-of-two scale per block)

@@ -1,0 +1,522 @@
+// FP64-accurate coupling phase on the tensor cores (tcgen05, BF16 operands,
+// FP32 accumulation in tensor memory), for order m = 4 (k = 64) and up to
+// 16 right-hand sides.
+//
+// GB300 runs FP64 at 1/58 of its FP32 rate, and double-float arithmetic on
+// the FP32 pipe leaves the coupling (Algorithm 3, y^_t = sum S_ts x^_s)
+// bound by instruction issue far below the memory roofline.  This path
+// computes the same sums exactly enough for FP64 parity with integer slices
+// on the tensor cores (the splitting scheme of Ozaki et al.):
+//
+//  * every row nu of the coupling matrices of row cluster t gets a power of
+//    two 2^E (E[t][nu], common to all blocks of the row, |S| < 2^E), every
+//    column j of the coefficients of tree level l a power of two 2^F;
+//  * a value v becomes the 49-bit integer X = round(v 2^(49-E)), split into
+//    seven signed 7-bit slices, X = sum_i s_i 2^(49-7i), |s_i| <= 128: each
+//    slice is exact in BF16;
+//  * D_ik = sum_blocks sum_mu s_i[nu][mu] t_k[mu][j] is a sum of at most
+//    16 x 64 products below 2^13 in magnitude, an integer below 2^23: the
+//    tensor cores accumulate it exactly in FP32;
+//  * y^_t[nu][j] = 2^(E + F) sum_{i + k <= 8} 2^(-7(i+k)) D_ik, summed in
+//    double-float; the dropped pairs and the rounding of X stay below 2^-47
+//    of the row's scale.
+//
+// The slices of S are cut once at set-up, straight into the layout the
+// tensor cores read from shared memory (K-major, 8 x 16-byte core matrices,
+// no swizzle), so one bulk copy (TMA engine) per block moves them; the
+// coefficients are cut once per product.  One MMA instruction multiplies two
+// stacked slices of S (M = 128 rows: slices i and i+1) by one slice of x^
+// (N = 16 columns, K = 16): 16 such groups cover the 28 slice pairs with
+// i + k <= 8, four K steps each.
+//
+// Kernel roles (one CTA per SM, 6 warps): warp 0 streams the slices of each
+// block through a 3-stage shared-memory ring (bulk copies completing on
+// mbarriers), warp 1 allocates tensor memory and issues the MMAs of a row
+// segment (at most 16 blocks) into one of two accumulator sets, warps 2-5
+// read a finished set back (tcgen05.ld), combine the pairs in double-float
+// and write y^_t.  Every wait is bounded; on a timeout the device error word
+// is raised, every role stops, copies and MMAs in flight are waited for and
+// the tensor memory is released before the CTA exits.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "h2_dd.cuh"
+#include "h2_internal.hpp"
+#include "h2_ptx.cuh"
+
+namespace h2 {
+namespace {
+
+constexpr int kTcK = 64;                 // rank k = m^3, m = 4
+constexpr int kTcN = 16;                 // right-hand sides of one product (padded)
+constexpr int kTcSlices = 7;             // slices of a value
+constexpr int kTcFixBits = 49;           // bits of the fixed-point integer X
+constexpr int kTcSegBlocks = 16;         // blocks accumulated in one exact segment
+constexpr uint32_t kSliceA = kTcK * kTcK * 2;          // 8192 bytes: one slice of S_b (64 x 64 BF16)
+constexpr uint32_t kSliceB = kTcN * kTcK * 2;          // 2048 bytes: one slice of x^_s (16 x 64 BF16)
+constexpr uint32_t kTileA = kTcSlices * kSliceA;       // 57344
+constexpr uint32_t kTileB = kTcSlices * kSliceB;       // 14336
+constexpr uint32_t kStage = kTileA + kTileB;           // 71680
+constexpr int kTcStages = 3;
+constexpr int kTcGroups = 16;
+constexpr uint32_t kTmemCols = 512;      // two accumulator sets of 16 groups x 16 columns
+constexpr int kTcThreads = 192;          // producer, MMA, four epilogue warps
+constexpr uint32_t kXch = 64 * kTcN * 8; // epilogue exchange: 64 rows x 16 double-float values
+constexpr uint32_t kBarOff = kTcStages * kStage + kXch;
+constexpr uint32_t kTcSmem = kBarOff + 16 * 8 + 16;
+
+// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
+// A and B BF16 (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 =
+// 0), N / 8 at bits 17-22, M / 16 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((128u >> 4) << 24);
+
+constexpr double kInv4PiTc = 0.079577471545947667884441881686257181;
+
+// element offset of (row r, contraction index c) in a K-major operand of 64
+// contraction values per row: 8 x 8 core matrices of 16-byte rows
+__host__ __device__ __forceinline__ int core_off(int r, int c) {
+  return ((r >> 3) * 8 + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
+}
+
+// shared-memory matrix descriptor (no swizzle): start address, leading
+// byte offset 128 (next core matrix along K), stride byte offset 1024 (next
+// 8 rows), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+// arrive on bar once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive 32-bit columns of this warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void named_sync_id(uint32_t id, uint32_t nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// the 16 MMA groups: x^ slice k (1-based) times the stacked S slices i0, i0 + 1
+__device__ __forceinline__ void group_of(int g, int &k, int &i0) {
+  // k = 1: i0 = 1, 3, 5, 7; k = 2, 3: 1, 3, 5; k = 4, 5: 1, 3; k = 6, 7: 1
+  constexpr int kk[kTcGroups] = {1, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 5, 5, 6, 7};
+  constexpr int ii[kTcGroups] = {1, 3, 5, 7, 1, 3, 5, 1, 3, 5, 1, 3, 1, 3, 1, 1};
+  k = kk[g];
+  i0 = ii[g];
+}
+
+// split X (|X| <= 2^49) into seven signed 7-bit slices, most significant first
+__host__ __device__ __forceinline__ void split7(long long X, int (&s)[kTcSlices]) {
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i) {
+    const int sh = kTcFixBits - 7 * (i + 1);
+    const long long q = sh > 0 ? (X + (1LL << (sh - 1))) >> sh : X;
+    s[i] = (int)q;
+    X -= q * (1LL << sh);
+  }
+}
+
+__device__ __forceinline__ double tc_green(const double *x, const double *y) {
+  const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  return kInv4PiTc / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// interpolation point nu of cluster c (tensor Chebyshev points, Eq. (6c))
+__device__ __forceinline__ void tc_point(const double *cheb, int64_t c, int nu, double *x) {
+  x[0] = cheb[(3 * c + 0) * 4 + (nu & 3)];
+  x[1] = cheb[(3 * c + 1) * 4 + ((nu >> 2) & 3)];
+  x[2] = cheb[(3 * c + 2) * 4 + (nu >> 4)];
+}
+
+// ---------------------------------------------------------------- set-up
+// E[t][nu]: 1 + floor(log2 max |S_ts[nu][mu]|) over the blocks of row t (0 if none)
+__global__ void k_tc_rowexp(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                            const double *__restrict__ cheb, int64_t row0, int64_t nclu, int32_t *__restrict__ E) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (nclu - row0) * kTcK) return;
+  const int64_t t = row0 + e / kTcK;
+  const int nu = (int)(e % kTcK);
+  double x[3], y[3], mx = 0.0;
+  tc_point(cheb, t, nu, x);
+  for (int64_t b = ptr[t]; b < ptr[t + 1]; ++b)
+    for (int mu = 0; mu < kTcK; ++mu) {
+      tc_point(cheb, col[b], mu, y);
+      mx = fmax(mx, tc_green(x, y));
+    }
+  E[t * kTcK + nu] = mx > 0.0 ? ilogb(mx) + 1 : 0;
+}
+
+// the seven BF16 slices of S_b, row nu, contraction indices 8 cg .. 8 cg + 7
+__global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__restrict__ col,
+                             const double *__restrict__ cheb, const int32_t *__restrict__ E, int64_t nblk,
+                             __nv_bfloat16 *__restrict__ Stc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nblk * kTcK * 8) return;
+  const int64_t b = e / (kTcK * 8);
+  const int nu = (int)((e / 8) % kTcK), cg = (int)(e % 8);
+  const int64_t t = brow[b], s = col[b];
+  double x[3], y[3];
+  tc_point(cheb, t, nu, x);
+  const int sc = kTcFixBits - E[t * kTcK + nu];
+  __nv_bfloat16 out[kTcSlices][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    tc_point(cheb, s, 8 * cg + q, y);
+    const long long X = llrint(ldexp(tc_green(x, y), sc));
+    int sl[kTcSlices];
+    split7(X, sl);
+#pragma unroll
+    for (int i = 0; i < kTcSlices; ++i) out[i][q] = __float2bfloat16_rn((float)sl[i]);
+  }
+  __nv_bfloat16 *base = Stc + b * (int64_t)(kTileA / 2) + core_off(nu, 8 * cg);
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i)
+    *reinterpret_cast<uint4 *>(base + i * (kSliceA / 2)) = *reinterpret_cast<const uint4 *>(out[i]);
+}
+
+// ---------------------------------------------------------------- per product
+__device__ __forceinline__ int tc_level(int64_t c) { return 63 - __clzll(c + 1); }
+
+// xmax[l][j] = largest |hi| of column j over the clusters of level l (as float bits)
+__global__ void k_tc_xmax(const dd *__restrict__ xhat, int64_t c0, int64_t nclu, int rp, unsigned *__restrict__ xmax) {
+  __shared__ unsigned loc[32 * kTcN];
+  for (int i = threadIdx.x; i < 32 * kTcN; i += blockDim.x) loc[i] = 0u;
+  __syncthreads();
+  const int64_t per = (int64_t)kTcK * rp, total = (nclu - c0) * per;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + e / per;
+    const int j = (int)(e % rp);
+    const unsigned bits = __float_as_uint(fabsf(xhat[c0 * per + e].hi));
+    atomicMax(&loc[tc_level(c) * kTcN + j], bits);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * kTcN; i += blockDim.x)
+    if (loc[i]) atomicMax(&xmax[i], loc[i]);
+}
+
+// F = 2 + floor(log2 max): |hi + lo| < 2^(F-1)
+__device__ __forceinline__ int tc_colexp(unsigned bits) {
+  return bits ? (int)((bits >> 23) & 0xFF) - 127 + 2 : 0;
+}
+
+// the seven BF16 slices of x^_c, column j, contraction indices 8 cg .. 8 cg + 7
+__global__ void k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int64_t nclu, int rp,
+                             const unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (nclu - c0) * kTcN * 8) return;
+  const int64_t c = c0 + e / (kTcN * 8);
+  const int j = (int)((e / 8) % kTcN), cg = (int)(e % 8);
+  const int sc = kTcFixBits - tc_colexp(xmax[tc_level(c) * kTcN + j]);
+  __nv_bfloat16 out[kTcSlices][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    long long X = 0;
+    if (j < rp) {
+      const dd v = xhat[(c * kTcK + 8 * cg + q) * rp + j];
+      X = llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
+    }
+    int sl[kTcSlices];
+    split7(X, sl);
+#pragma unroll
+    for (int i = 0; i < kTcSlices; ++i) out[i][q] = __float2bfloat16_rn((float)sl[i]);
+  }
+  __nv_bfloat16 *base = xtc + c * (int64_t)(kTileB / 2) + core_off(j, 8 * cg);
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i)
+    *reinterpret_cast<uint4 *>(base + i * (kSliceB / 2)) = *reinterpret_cast<const uint4 *>(out[i]);
+}
+
+__device__ __forceinline__ dd dd_scale(dd v, int e) { return dd{ldexpf(v.hi, e), ldexpf(v.lo, e)}; }
+
+// The coupling kernel (see the top of the file).  Rows t = row0 + r for r
+// in [0, nrows); each CTA takes a contiguous range of rows holding about
+// 1/gridDim of the blocks.
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_coupling_tc(const __nv_bfloat16 *__restrict__ Stc, const __nv_bfloat16 *__restrict__ xtc,
+                  const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const int32_t *__restrict__ E,
+                  const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, dd *__restrict__ yhat) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  dd *xch = reinterpret_cast<dd *>(smem + kTcStages * kStage);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kBarOff);
+  uint64_t *empty = full + kTcStages;
+  uint64_t *accf = empty + kTcStages;
+  uint64_t *acce = accf + 2;
+  uint64_t *done = acce + 2;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // rows of this CTA: from the first row whose blocks start at or after its share
+  const int64_t b_all0 = ptr[row0], total = ptr[row0 + nrows] - b_all0;
+  auto row_at = [&](int64_t w) -> int64_t {
+    if (w >= (int64_t)gridDim.x) return nrows;
+    const int64_t target = total * w / gridDim.x;
+    int64_t lo = 0, hi = nrows;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (ptr[row0 + mid] - b_all0 >= target) hi = mid;
+      else lo = mid + 1;
+    }
+    return lo;
+  };
+  const int64_t r_begin = blockIdx.x == 0 ? 0 : row_at(blockIdx.x);
+  const int64_t r_end = row_at(blockIdx.x + 1);
+  const int64_t e_begin = ptr[row0 + r_begin], e_end = ptr[row0 + r_end];
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf[a], 1);
+      mbar_init(&acce[a], 4);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 0) {
+    // ---------------- producer: the slices of every block of the range
+    if (lane == 0) {
+      int64_t e = e_begin;
+      for (; e < e_end; ++e) {
+        const int64_t i = e - e_begin;
+        const int s = (int)(i % kTcStages);
+        if (i >= kTcStages && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / kTcStages - 1) & 1), abort)) break;
+        unsigned char *st = smem + (size_t)s * kStage;
+        mbar_expect_tx(&full[s], kStage);
+        bulk_g2s(st, Stc + e * (int64_t)(kTileA / 2), kTileA, &full[s]);
+        bulk_g2s(st + kTileA, xtc + (int64_t)col[e] * (kTileB / 2), kTileB, &full[s]);
+      }
+      if (*abort) {
+        // let the copies in flight land before the CTA leaves (bounded)
+        const int64_t j0 = e - kTcStages > e_begin ? e - kTcStages : e_begin;
+        for (int64_t j = j0; j < e; ++j) {
+          const int64_t ij = j - e_begin;
+          mbar_wait_bounded(&full[ij % kTcStages], (uint32_t)((ij / kTcStages) & 1));
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int64_t i = 0, q = 0;
+      bool ok = true;
+      for (int64_t r = r_begin; r < r_end && ok; ++r) {
+        const int64_t b0 = ptr[row0 + r], nb = ptr[row0 + r + 1] - b0;
+        for (int64_t s0 = 0; s0 < nb && ok; s0 += kTcSegBlocks, ++q) {
+          const int a = (int)(q & 1);
+          if (q >= 2 && !mbar_wait_or_abort(&acce[a], (uint32_t)((q / 2 - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int64_t sn = nb - s0 < kTcSegBlocks ? nb - s0 : kTcSegBlocks;
+          for (int64_t t = 0; t < sn; ++t, ++i) {
+            const int s = (int)(i % kTcStages);
+            if (!mbar_wait_or_abort(&full[s], (uint32_t)((i / kTcStages) & 1), abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t A0 = smem_u32(smem + (size_t)s * kStage), B0 = A0 + kTileA;
+#pragma unroll
+            for (int g = 0; g < kTcGroups; ++g) {
+              int k, i0;
+              group_of(g, k, i0);
+              const uint32_t d = tbase + (uint32_t)(a * 256 + g * kTcN);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                tc_mma(d, sdesc(A0 + (uint32_t)(i0 - 1) * kSliceA + kk * 256u),
+                       sdesc(B0 + (uint32_t)(k - 1) * kSliceB + kk * 256u), (t > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc_commit(&empty[s]);   // the stage is free once these MMAs have read it
+          }
+          if (ok) tc_commit(&accf[a]);
+        }
+      }
+      // every MMA issued has completed before the tensor memory is released
+      tc_commit(done);
+      mbar_wait_bounded(done, 0);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 2-5 read tensor-memory lanes 32 (warp % 4) ..
+    const int quad = warp & 3, tl = quad * 32 + lane, half = tl >> 6, nu = tl & 63;
+    int64_t q = 0;
+    for (int64_t r = r_begin; r < r_end; ++r) {
+      const int64_t t = row0 + r;
+      const int64_t nb = ptr[t + 1] - ptr[t];
+      dd *yrow = yhat + (t * kTcK + nu) * rp;
+      if (nb == 0) {
+        if (half == 0)
+          for (int j = 0; j < rp; ++j) yrow[j] = dd{0.0f, 0.0f};
+        continue;
+      }
+      const int Er = E[t * kTcK + nu];
+      const int lvl = tc_level(t);
+      bool stop = false;
+      for (int64_t s0 = 0; s0 < nb; s0 += kTcSegBlocks, ++q) {
+        const int a = (int)(q & 1);
+        const bool ready = !*abort && mbar_wait_or_abort(&accf[a], (uint32_t)((q / 2) & 1), abort);
+        if (named_sync_or(128, ready ? 0 : 1)) {   // all epilogue warps agree to stop
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        dd acc[kTcN];
+#pragma unroll
+        for (int j = 0; j < kTcN; ++j) acc[j] = dd{0.0f, 0.0f};
+#pragma unroll
+        for (int g = 0; g < kTcGroups; ++g) {
+          int k, i0;
+          group_of(g, k, i0);
+          const int i = i0 + half;
+          if (i > kTcSlices) continue;   // the slice below slice 7 does not exist (whole warp skips)
+          float v[16];
+          tmem_ld16(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * 256 + g * kTcN), v);
+          const int sh = -7 * (i + k);
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) acc[j] = acc[j] + dd{ldexpf(v[j], sh), 0.0f};
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[a]);
+        if (half == 1)
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) xch[nu * kTcN + j] = acc[j];
+        named_sync_id(2, 128);
+        if (half == 0) {
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) {
+            if (j >= rp) break;
+            dd v = dd_scale(acc[j] + xch[nu * kTcN + j], Er + tc_colexp(xmax[lvl * kTcN + j]));
+            if (s0 > 0) v = v + yrow[j];
+            yrow[j] = v;
+          }
+        }
+        named_sync_id(2, 128);
+      }
+      if (stop) break;
+    }
+  }
+  // tensor memory is released once every role is done
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+bool tc_eligible(const Dev &d) { return d.prec == H2_F64 && d.coupling == 0 && d.m == 4 && d.kp == kTcK; }
+
+int tc_build(Ctx &c, const int32_t *arow_dev) {
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  const int64_t row0 = ((int64_t)1 << d.first_adm_level) - 1;
+  if (d.first_adm_level > d.depth || d.nadm == 0) return H2_OK;
+  int rc;
+  if ((rc = dev_alloc(d, (void **)&d.tc_E, sizeof(int32_t) * (size_t)d.nclu * kTcK))) return rc;
+  if ((rc = dev_alloc(d, &d.Stc, (size_t)d.nadm * kTileA))) return rc;
+  if ((rc = dev_alloc(d, &d.xtc, (size_t)d.nclu * kTileB))) return rc;
+  if ((rc = dev_alloc(d, (void **)&d.tc_xmax, sizeof(unsigned) * 32 * kTcN))) return rc;
+  H2_CUDA_TRY(cudaMemsetAsync(d.tc_E, 0, sizeof(int32_t) * (size_t)d.nclu * kTcK, st));
+  H2_CUDA_TRY(cudaMemsetAsync(d.xtc, 0, (size_t)d.nclu * kTileB, st));
+  const int64_t nr = (d.nclu - row0) * kTcK;
+  k_tc_rowexp<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(d.adm_ptr, d.adm_col, d.cheb, row0, d.nclu, d.tc_E);
+  const int64_t ns = d.nadm * kTcK * 8;
+  k_tc_slice_s<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(arow_dev, d.adm_col, d.cheb, d.tc_E, d.nadm,
+                                                             (__nv_bfloat16 *)d.Stc);
+  H2_CUDA_TRY(cudaGetLastError());
+  H2_CUDA_TRY(cudaStreamSynchronize(st));
+  d.tc = true;
+  return H2_OK;
+}
+
+int tc_coupling(Ctx &c, const void *xhat_v, void *yhat_v, int rp) {
+  const dd *xhat = static_cast<const dd *>(xhat_v);
+  dd *yhat = static_cast<dd *>(yhat_v);
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
+  const int64_t row0 = ((int64_t)1 << d.first_adm_level) - 1, nrows = d.nclu - row0;
+  if (nrows <= 0) return H2_OK;
+  H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
+  const int64_t nx = (d.nclu - row0) * kTcK * rp;
+  k_tc_xmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nx + 255) / 256, 152 * 8)), 256, 0, st>>>(
+      xhat, row0, d.nclu, rp, d.tc_xmax);
+  const int64_t ne = (d.nclu - row0) * kTcN * 8;
+  k_tc_slice_x<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(xhat, row0, d.nclu, rp, d.tc_xmax,
+                                                             (__nv_bfloat16 *)d.xtc);
+  static_assert(kTcSmem <= 227 * 1024, "tensor-core coupling does not fit in shared memory");
+  H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_coupling_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(227 * 1024)));
+  int sms = 0, dev = 0;
+  H2_CUDA_TRY(cudaGetDevice(&dev));
+  H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = (int)std::min<int64_t>(sms, nrows);
+  k_coupling_tc<<<grid, kTcThreads, kTcSmem, st>>>((const __nv_bfloat16 *)d.Stc, (const __nv_bfloat16 *)d.xtc,
+                                                   d.adm_ptr, d.adm_col, d.tc_E, d.tc_xmax, row0, nrows, rp, yhat);
+  H2_CUDA_TRY(cudaGetLastError());
+  return H2_OK;
+}
+
+// the tensor-core path's own device error word (bounded waits of this file)
+int tc_take_error(cudaStream_t st) {
+  int v = 0, zero = 0;
+  H2_CUDA_TRY(cudaMemcpyFromSymbolAsync(&v, g_h2_device_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  H2_CUDA_TRY(cudaStreamSynchronize(st));
+  if (v) {
+    H2_CUDA_TRY(cudaMemcpyToSymbolAsync(g_h2_device_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    return fail(H2_ETIMEOUT, "a bounded device wait of the tensor-core coupling ran out");
+  }
+  return H2_OK;
+}
+
+}  // namespace h2

@@ -242,3 +242,37 @@ def test_full_size_mixed_precision_sampled_rows(require_gpu, prec):
     rows = np.random.default_rng(6).choice(n, 40, replace=False)
     ref = _full["l8"].matvec_rows(x, rows)
     assert _rel(y[rows], ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("name", ["ico3_m4", "ell3_m4"])
+def test_f64_tensor_core_coupling(require_gpu, name):
+    """FP64-accurate coupling from 7-bit BF16 slices on the tensor cores (order 4,
+    up to 16 right-hand sides; more fall back to the double-float coupling):
+    against the oracle and the double-float path, and bit-reproducible."""
+    import torch
+    v, f, o = _oracle(name)
+    make, leaf, eta, m = CASES[name]
+    ht = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64")
+    hd = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64", tensor="off")
+    assert ht.stats["tensor"] == 1 and hd.stats["tensor"] == 0
+    n = f.shape[0]
+    for nrhs in (1, 5, 16, 17):
+        x = I.uniform_rhs(n, nrhs, 3100 + nrhs)
+        ref = o.matvec(x)
+        yt, yd = ht.matvec_host(x), hd.matvec_host(x)
+        assert _rel(yt, ref) <= TOL["f64"], (nrhs, _rel(yt, ref))
+        assert _rel(yt, yd) <= TOL["f64"], (nrhs, _rel(yt, yd))
+    # constant density and a right-hand side with columns of very different scales
+    x = np.concatenate([np.ones((n, 1)), 1e-9 * I.uniform_rhs(n, 1, 3200), 1e6 * I.uniform_rhs(n, 1, 3201)], axis=1)
+    ref = o.matvec(x)
+    yt = ht.matvec_host(x)
+    for c in range(3):
+        assert _rel(yt[:, c], ref[:, c]) <= TOL["f64"], (c, _rel(yt[:, c], ref[:, c]))
+    xd = colmajor(torch.from_numpy(I.uniform_rhs(n, 16, 3300)).cuda())
+    y1, y2 = colmajor(torch.empty_like(xd)), colmajor(torch.empty_like(xd))
+    ht.matvec(xd, y1)
+    ht.matvec(xd, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    ht.close()
+    hd.close()

@@ -25,16 +25,18 @@
 // tensor cores read from shared memory (K-major, 8 x 16-byte core matrices,
 // no swizzle), so one bulk copy (TMA engine) per block moves them; the
 // coefficients are cut once per product.  One MMA instruction multiplies two
-// stacked slices of S (M = 128 rows: slices i and i+1) by one slice of x^
-// (N = 16 columns, K = 16): 16 such groups cover the 28 slice pairs with
-// i + k <= 8, four K steps each.
+// stacked slices of S (M = 128 rows: slices i and i+1) by all slices of x^
+// side by side (N = 8 x 16 columns, the eighth slice zero), K = 16: four
+// such groups, four K steps each, 16 instructions per block (the cost of
+// an instruction hardly depends on N at these sizes); the epilogue reads the
+// 28 pairs with i + k <= 8.
 //
 // Kernel roles (one CTA per SM, 6 warps): warp 0 streams the slices of each
 // block through a 3-stage shared-memory ring (bulk copies completing on
 // mbarriers), warp 1 allocates tensor memory and issues the MMAs of a row
-// segment (at most 16 blocks) into one of two accumulator sets, warps 2-5
-// read a finished set back (tcgen05.ld), combine the pairs in double-float
-// and write y^_t.  Every wait is bounded; on a timeout the device error word
+// segment (at most 16 blocks) into the accumulators, warps 2-5
+// read it back (tcgen05.ld), combine the pairs in double-float and write
+// y^_t.  Every wait is bounded; on a timeout the device error word
 // is raised, every role stops, copies and MMAs in flight are waited for and
 // the tensor memory is released before the CTA exits.
 #include <cuda_bf16.h>
@@ -58,11 +60,12 @@ constexpr int kTcSegBlocks = 16;         // blocks accumulated in one exact segm
 constexpr uint32_t kSliceA = kTcK * kTcK * 2;          // 8192 bytes: one slice of S_b (64 x 64 BF16)
 constexpr uint32_t kSliceB = kTcN * kTcK * 2;          // 2048 bytes: one slice of x^_s (16 x 64 BF16)
 constexpr uint32_t kTileA = kTcSlices * kSliceA;       // 57344
-constexpr uint32_t kTileB = kTcSlices * kSliceB;       // 14336
-constexpr uint32_t kStage = kTileA + kTileB;           // 71680
+constexpr uint32_t kTileB = (kTcSlices + 1) * kSliceB; // 16384: seven slices and a zero slice (N = 128)
+constexpr uint32_t kStage = kTileA + kTileB;           // 73728
 constexpr int kTcStages = 3;
-constexpr int kTcGroups = 16;
-constexpr uint32_t kTmemCols = 512;      // two accumulator sets of 16 groups x 16 columns
+constexpr int kTcGroups = 4;             // S slice pairs (1,2), (3,4), (5,6), (7,-)
+constexpr int kTcNB = 128;               // N of one MMA: the eight slices of x^, 16 columns each
+constexpr uint32_t kTmemCols = 512;      // one accumulator set: 4 groups x 128 columns
 constexpr int kTcThreads = 192;          // producer, MMA, four epilogue warps
 constexpr uint32_t kXch = 64 * kTcN * 8; // epilogue exchange: 64 rows x 16 double-float values
 constexpr uint32_t kBarOff = kTcStages * kStage + kXch;
@@ -71,7 +74,7 @@ constexpr uint32_t kTcSmem = kBarOff + 16 * 8 + 16;
 // instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
 // A and B BF16 (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 =
 // 0), N / 8 at bits 17-22, M / 16 at bits 24-28
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcNB >> 3) << 17) | ((128u >> 4) << 24);
 
 constexpr double kInv4PiTc = 0.079577471545947667884441881686257181;
 
@@ -107,7 +110,18 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16 consecutive 32-bit columns of this warp's 32 tensor-memory lanes
+// 16 consecutive 32-bit columns of this warp's 32 tensor-memory lanes; the
+// registers are valid after tmem_wait()
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -125,14 +139,8 @@ __device__ __forceinline__ void named_sync_id(uint32_t id, uint32_t nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// the 16 MMA groups: x^ slice k (1-based) times the stacked S slices i0, i0 + 1
-__device__ __forceinline__ void group_of(int g, int &k, int &i0) {
-  // k = 1: i0 = 1, 3, 5, 7; k = 2, 3: 1, 3, 5; k = 4, 5: 1, 3; k = 6, 7: 1
-  constexpr int kk[kTcGroups] = {1, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 5, 5, 6, 7};
-  constexpr int ii[kTcGroups] = {1, 3, 5, 7, 1, 3, 5, 1, 3, 5, 1, 3, 1, 3, 1, 1};
-  k = kk[g];
-  i0 = ii[g];
-}
+// 2^e as a float for -126 <= e <= 127 (exact; used for power-of-two scaling)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
 // split X (|X| <= 2^49) into seven signed 7-bit slices, most significant first
 __host__ __device__ __forceinline__ void split7(long long X, int (&s)[kTcSlices]) {
@@ -255,7 +263,13 @@ __global__ void k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int64_t nc
     *reinterpret_cast<uint4 *>(base + i * (kSliceB / 2)) = *reinterpret_cast<const uint4 *>(out[i]);
 }
 
-__device__ __forceinline__ dd dd_scale(dd v, int e) { return dd{ldexpf(v.hi, e), ldexpf(v.lo, e)}; }
+__device__ __forceinline__ dd dd_scale(dd v, int e) {
+  if (e >= -126 && e <= 127) {
+    const float w = pow2f(e);
+    return dd{v.hi * w, v.lo * w};
+  }
+  return dd{ldexpf(v.hi, e), ldexpf(v.lo, e)};
+}
 
 // The coupling kernel (see the top of the file).  Rows t = row0 + r for r
 // in [0, nrows); each CTA takes a contiguous range of rows holding about
@@ -269,8 +283,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kBarOff);
   uint64_t *empty = full + kTcStages;
   uint64_t *accf = empty + kTcStages;
-  uint64_t *acce = accf + 2;
-  uint64_t *done = acce + 2;
+  uint64_t *acce = accf + 1;
+  uint64_t *done = acce + 1;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -297,10 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
-      mbar_init(&accf[a], 1);
-      mbar_init(&acce[a], 4);
-    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 4);
     mbar_init(done, 1);
     *abort = 0;
     mbar_fence_init();
@@ -320,14 +332,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---------------- producer: the slices of every block of the range
     if (lane == 0) {
       int64_t e = e_begin;
+      int32_t cn = e < e_end ? col[e] : 0;   // column of the next block, loaded one block ahead
       for (; e < e_end; ++e) {
         const int64_t i = e - e_begin;
         const int s = (int)(i % kTcStages);
+        const int32_t cb = cn;
+        if (e + 1 < e_end) cn = col[e + 1];
         if (i >= kTcStages && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / kTcStages - 1) & 1), abort)) break;
         unsigned char *st = smem + (size_t)s * kStage;
         mbar_expect_tx(&full[s], kStage);
-        bulk_g2s(st, Stc + e * (int64_t)(kTileA / 2), kTileA, &full[s]);
-        bulk_g2s(st + kTileA, xtc + (int64_t)col[e] * (kTileB / 2), kTileB, &full[s]);
+        // the coefficient slices first (they may come from L2), then S slice by slice
+        bulk_g2s(st + kTileA, xtc + (int64_t)cb * (kTileB / 2), kTileB, &full[s]);
+        const __nv_bfloat16 *src = Stc + e * (int64_t)(kTileA / 2);
+#pragma unroll
+        for (int sl = 0; sl < kTcSlices; ++sl)
+          bulk_g2s(st + sl * kSliceA, src + sl * (kSliceA / 2), kSliceA, &full[s]);
       }
       if (*abort) {
         // let the copies in flight land before the CTA leaves (bounded)
@@ -344,11 +363,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       int64_t i = 0, q = 0;
       bool ok = true;
+      int64_t pnext = ptr[row0 + r_begin];   // row pointers loaded one row ahead
       for (int64_t r = r_begin; r < r_end && ok; ++r) {
-        const int64_t b0 = ptr[row0 + r], nb = ptr[row0 + r + 1] - b0;
+        const int64_t b0 = pnext;
+        pnext = ptr[row0 + r + 1];
+        const int64_t nb = pnext - b0;
         for (int64_t s0 = 0; s0 < nb && ok; s0 += kTcSegBlocks, ++q) {
-          const int a = (int)(q & 1);
-          if (q >= 2 && !mbar_wait_or_abort(&acce[a], (uint32_t)((q / 2 - 1) & 1), abort)) {
+          // the accumulators are free once the epilogue has read the previous segment
+          if (q >= 1 && !mbar_wait_or_abort(acce, (uint32_t)((q - 1) & 1), abort)) {
             ok = false;
             break;
           }
@@ -361,20 +383,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               break;
             }
             tc_fence_after();
+            // descriptors of the stage; offsets below 256 KB add to the 14-bit address field.
+            // Group g: S slices 2g+1, 2g+2 (M = 128 rows) times all x^ slices (N = 128);
+            // K steps outermost, so that consecutive MMAs write different accumulators
             const uint32_t A0 = smem_u32(smem + (size_t)s * kStage), B0 = A0 + kTileA;
+            const uint64_t dA = sdesc(A0), dB = sdesc(B0);
 #pragma unroll
-            for (int g = 0; g < kTcGroups; ++g) {
-              int k, i0;
-              group_of(g, k, i0);
-              const uint32_t d = tbase + (uint32_t)(a * 256 + g * kTcN);
+            for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                tc_mma(d, sdesc(A0 + (uint32_t)(i0 - 1) * kSliceA + kk * 256u),
-                       sdesc(B0 + (uint32_t)(k - 1) * kSliceB + kk * 256u), (t > 0 || kk > 0) ? 1u : 0u);
-            }
+              for (int g = 0; g < kTcGroups; ++g)
+                tc_mma(tbase + (uint32_t)(g * kTcNB), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
+                       dB + (uint64_t)(kk * 16), (t > 0 || kk > 0) ? 1u : 0u);
             tc_commit(&empty[s]);   // the stage is free once these MMAs have read it
           }
-          if (ok) tc_commit(&accf[a]);
+          if (ok) tc_commit(accf);
         }
       }
       // every MMA issued has completed before the tensor memory is released
@@ -397,10 +419,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       const int Er = E[t * kTcK + nu];
       const int lvl = tc_level(t);
+      int Fc[kTcN];
+#pragma unroll
+      for (int j = 0; j < kTcN; ++j) Fc[j] = Er + tc_colexp(xmax[lvl * kTcN + j]);
       bool stop = false;
       for (int64_t s0 = 0; s0 < nb; s0 += kTcSegBlocks, ++q) {
-        const int a = (int)(q & 1);
-        const bool ready = !*abort && mbar_wait_or_abort(&accf[a], (uint32_t)((q / 2) & 1), abort);
+        const bool ready = !*abort && mbar_wait_or_abort(accf, (uint32_t)(q & 1), abort);
         if (named_sync_or(128, ready ? 0 : 1)) {   // all epilogue warps agree to stop
           stop = true;
           break;
@@ -409,21 +433,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         dd acc[kTcN];
 #pragma unroll
         for (int j = 0; j < kTcN; ++j) acc[j] = dd{0.0f, 0.0f};
-#pragma unroll
+        // lane nu (+ 64) of group g holds S slice i = 2g + 1 (+ 1) times every x^ slice k
+        // (columns 16 (k - 1) .. + 15); the pairs with i + k <= 8 are summed
+#pragma unroll 1
         for (int g = 0; g < kTcGroups; ++g) {
-          int k, i0;
-          group_of(g, k, i0);
-          const int i = i0 + half;
-          if (i > kTcSlices) continue;   // the slice below slice 7 does not exist (whole warp skips)
-          float v[16];
-          tmem_ld16(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * 256 + g * kTcN), v);
-          const int sh = -7 * (i + k);
+          const int i = 2 * g + 1 + half;
+          if (i > kTcSlices) continue;   // slice 8 does not exist (whole warp skips)
+          const int kmax = 8 - i;
+#pragma unroll 1
+          for (int k0 = 1; k0 <= kmax; k0 += 4) {
+            uint32_t raw[4][16];
 #pragma unroll
-          for (int j = 0; j < kTcN; ++j) acc[j] = acc[j] + dd{ldexpf(v[j], sh), 0.0f};
+            for (int u = 0; u < 4; ++u)
+              if (k0 + u <= kmax)
+                tmem_ld16_nw(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * kTcNB + (k0 + u - 1) * kTcN), raw[u]);
+            tmem_wait();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (k0 + u > kmax) break;
+              const float w = pow2f(-7 * (i + k0 + u));   // exact: the sums are integers below 2^24
+#pragma unroll
+              for (int j = 0; j < kTcN; ++j) acc[j] = acc[j] + dd{__uint_as_float(raw[u][j]) * w, 0.0f};
+            }
+          }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acce[a]);
+        if (lane == 0) mbar_arrive(acce);
         if (half == 1)
 #pragma unroll
           for (int j = 0; j < kTcN; ++j) xch[nu * kTcN + j] = acc[j];
@@ -432,7 +468,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
           for (int j = 0; j < kTcN; ++j) {
             if (j >= rp) break;
-            dd v = dd_scale(acc[j] + xch[nu * kTcN + j], Er + tc_colexp(xmax[lvl * kTcN + j]));
+            dd v = dd_scale(acc[j] + xch[nu * kTcN + j], Fc[j]);
             if (s0 > 0) v = v + yrow[j];
             yrow[j] = v;
           }

@@ -194,6 +194,14 @@ def run_ours(args):
     if args.prec == "f64n":
         roof = {"bound": "alu", "achieved": alg["coupling_flops"] / (cpl_ms * 1e-3) / 1e12, "peak": FP64_TFLOPS,
                 "unit": "TFLOP/s", "kernel": "k_blockrow (coupling, FP64 FMA pipe)"}
+    elif args.prec == "f64" and st.get("tensor", 0):
+        # tensor-core coupling: a stream of the stored slices; algorithmic bytes are
+        # those of the FP64 coupling matrices (k^2 x 8 B per block) and coefficients
+        roof = {"bound": "hbm", "achieved": alg["coupling_bytes"] / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "kernel": "k_coupling_tc (tcgen05, 7-bit BF16 slices, exact FP32 sums)",
+                "stored_bytes_per_entry": 14,
+                "stored_frac": (st["adm_blocks"] * (14 * st["rank"] ** 2 + 16384) / (cpl_ms * 1e-3) / 1e9
+                                / peaks["hbm_gbs"])}
     elif args.prec == "f64":
         roof = {"bound": "alu", "achieved": alg["coupling_flops"] / (cpl_ms * 1e-3) / 1e12, "peak": DD_TFLOPS,
                 "unit": "TFLOP/s", "kernel": "k_blockrow (coupling, double-float on the FP32 pipe)",
@@ -212,11 +220,14 @@ def run_ours(args):
     # DRAM bytes (read + write) per coupling launch from the ncu capture of the
     # same kernel at level 5 (profiles/k_blockrow_coupling_icosphere_L5_m4_16rhs_f64.md),
     # scaled by admissible blocks; None where no capture of the current kernel exists
-    traffic_per_block = {"f64": 691.93e6 / 18876}
-    roof["traffic"] = (traffic_per_block[args.prec] * st["adm_blocks"]
-                       if args.prec in traffic_per_block and args.order == 4 and args.nrhs == 16 else None)
+    tc = args.prec == "f64" and st.get("tensor", 0)
+    traffic_per_block = {"f64": 691.93e6 / 18876, "f64-tc": (1253.466e6 + 17.5e6) / 18876}
+    key = "f64-tc" if tc else args.prec
+    roof["traffic"] = (traffic_per_block[key] * st["adm_blocks"]
+                       if key in traffic_per_block and args.order == 4 and args.nrhs == 16 else None)
     roof["peak_source"] = {"f64n": "nominal FP64 rate",
-                           "f64": "FP32 FMA rate (152 SMs x 128 lanes x 2.07 GHz) / 12 instructions per dd FMA",
+                           "f64": (f"{peaks['src']} HBM copy bandwidth" if tc else
+                                   "FP32 FMA rate (152 SMs x 128 lanes x 2.07 GHz) / 12 instructions per dd FMA"),
                            "f32": f"{peaks['src']} HBM copy bandwidth",
                            "bf16": "FP32 FMA rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
                            "f16": "FP32 FMA rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz)"}[args.prec]

@@ -122,19 +122,6 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) 
 }
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void named_sync_id(uint32_t id, uint32_t nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -214,21 +201,31 @@ __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__
 // ---------------------------------------------------------------- per product
 __device__ __forceinline__ int tc_level(int64_t c) { return 63 - __clzll(c + 1); }
 
-// xmax[l][j] = largest |hi| of column j over the clusters of level l (as float bits)
-__global__ void k_tc_xmax(const dd *__restrict__ xhat, int64_t c0, int64_t nclu, int rp, unsigned *__restrict__ xmax) {
-  __shared__ unsigned loc[32 * kTcN];
-  for (int i = threadIdx.x; i < 32 * kTcN; i += blockDim.x) loc[i] = 0u;
+// xmax[l][j] = largest |hi| of column j over the clusters of level l (as float
+// bits); grid.y = level - lmin, each thread takes whole coefficient rows
+__global__ void k_tc_xmax(const dd *__restrict__ xhat, int lmin, int rp, unsigned *__restrict__ xmax) {
+  __shared__ unsigned loc[kTcN];
+  if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
   __syncthreads();
-  const int64_t per = (int64_t)kTcK * rp, total = (nclu - c0) * per;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = c0 + e / per;
-    const int j = (int)(e % rp);
-    const unsigned bits = __float_as_uint(fabsf(xhat[c0 * per + e].hi));
-    atomicMax(&loc[tc_level(c) * kTcN + j], bits);
+  const int l = lmin + blockIdx.y;
+  const int64_t c0 = ((int64_t)1 << l) - 1, rows = ((int64_t)1 << l) * kTcK;
+  float mx[kTcN];
+#pragma unroll
+  for (int j = 0; j < kTcN; ++j) mx[j] = 0.0f;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const dd *row = xhat + (c0 * kTcK + r) * rp;
+#pragma unroll
+    for (int j = 0; j < kTcN; ++j)
+      if (j < rp) mx[j] = fmaxf(mx[j], fabsf(row[j].hi));
+  }
+#pragma unroll
+  for (int j = 0; j < kTcN; ++j) {
+    float v = mx[j];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&loc[j], __float_as_uint(v));
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 32 * kTcN; i += blockDim.x)
-    if (loc[i]) atomicMax(&xmax[i], loc[i]);
+  if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[l * kTcN + threadIdx.x], loc[threadIdx.x]);
 }
 
 // F = 2 + floor(log2 max): |hi + lo| < 2^(F-1)
@@ -236,31 +233,42 @@ __device__ __forceinline__ int tc_colexp(unsigned bits) {
   return bits ? (int)((bits >> 23) & 0xFF) - 127 + 2 : 0;
 }
 
-// the seven BF16 slices of x^_c, column j, contraction indices 8 cg .. 8 cg + 7
-__global__ void k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int64_t nclu, int rp,
-                             const unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= (nclu - c0) * kTcN * 8) return;
-  const int64_t c = c0 + e / (kTcN * 8);
-  const int j = (int)((e / 8) % kTcN), cg = (int)(e % 8);
-  const int sc = kTcFixBits - tc_colexp(xmax[tc_level(c) * kTcN + j]);
-  __nv_bfloat16 out[kTcSlices][8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
+// the seven BF16 slices of the coefficients of kTcXc clusters per CTA: the
+// tiles are read with coalesced loads, cut in registers, assembled in shared
+// memory in the MMA layout (16 columns x 64 contraction values per slice)
+// and written out with 16-byte stores (the eighth, zero slice is never
+// written)
+constexpr int kTcXc = 2;
+
+__global__ void __launch_bounds__(256) k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int64_t nclu, int rp,
+                                                    const unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
+  __shared__ __align__(16) __nv_bfloat16 tile[kTcXc][kTcSlices][kTcN * kTcK];
+  const int64_t cb = c0 + (int64_t)blockIdx.x * kTcXc;
+  const int nc = (int)(nclu - cb < kTcXc ? nclu - cb : kTcXc);
+  for (int e = threadIdx.x; e < kTcXc * kTcN * kTcK; e += blockDim.x) {
+    const int ci = e / (kTcN * kTcK), rem = e % (kTcN * kTcK);
+    const int mu = rem / kTcN, j = rem % kTcN;
+    if (ci >= nc) break;
+    const int64_t c = cb + ci;
     long long X = 0;
     if (j < rp) {
-      const dd v = xhat[(c * kTcK + 8 * cg + q) * rp + j];
+      const int sc = kTcFixBits - tc_colexp(xmax[tc_level(c) * kTcN + j]);
+      const dd v = xhat[(c * kTcK + mu) * rp + j];
       X = llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
     }
     int sl[kTcSlices];
     split7(X, sl);
+    const int o = core_off(j, mu);
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) out[i][q] = __float2bfloat16_rn((float)sl[i]);
+    for (int i = 0; i < kTcSlices; ++i) tile[ci][i][o] = __float2bfloat16_rn((float)sl[i]);
   }
-  __nv_bfloat16 *base = xtc + c * (int64_t)(kTileB / 2) + core_off(j, 8 * cg);
-#pragma unroll
-  for (int i = 0; i < kTcSlices; ++i)
-    *reinterpret_cast<uint4 *>(base + i * (kSliceB / 2)) = *reinterpret_cast<const uint4 *>(out[i]);
+  __syncthreads();
+  constexpr int kWords = kTcSlices * kTcN * kTcK / 8;   // 16-byte words of one cluster's seven slices
+  for (int w = threadIdx.x; w < nc * kWords; w += blockDim.x) {
+    const int ci = w / kWords, wi = w % kWords;
+    uint4 *dst = reinterpret_cast<uint4 *>(xtc + (cb + ci) * (int64_t)(kTileB / 2));
+    dst[wi] = reinterpret_cast<const uint4 *>(&tile[ci][0][0])[wi];
+  }
 }
 
 __device__ __forceinline__ dd dd_scale(dd v, int e) {
@@ -523,12 +531,11 @@ int tc_coupling(Ctx &c, const void *xhat_v, void *yhat_v, int rp) {
   const int64_t row0 = ((int64_t)1 << d.first_adm_level) - 1, nrows = d.nclu - row0;
   if (nrows <= 0) return H2_OK;
   H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
-  const int64_t nx = (d.nclu - row0) * kTcK * rp;
-  k_tc_xmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nx + 255) / 256, 152 * 8)), 256, 0, st>>>(
-      xhat, row0, d.nclu, rp, d.tc_xmax);
-  const int64_t ne = (d.nclu - row0) * kTcN * 8;
-  k_tc_slice_x<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(xhat, row0, d.nclu, rp, d.tc_xmax,
-                                                             (__nv_bfloat16 *)d.xtc);
+  const int nlev = d.depth - d.first_adm_level + 1;
+  k_tc_xmax<<<dim3(512, nlev), 256, 0, st>>>(xhat, d.first_adm_level, rp, d.tc_xmax);
+  const int64_t nxc = d.nclu - row0;
+  k_tc_slice_x<<<(unsigned)((nxc + kTcXc - 1) / kTcXc), 256, 0, st>>>(xhat, row0, d.nclu, rp, d.tc_xmax,
+                                                                      (__nv_bfloat16 *)d.xtc);
   static_assert(kTcSmem <= 227 * 1024, "tensor-core coupling does not fit in shared memory");
   H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_coupling_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(227 * 1024)));

@@ -244,14 +244,29 @@ def test_full_size_mixed_precision_sampled_rows(require_gpu, prec):
     assert _rel(y[rows], ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("name", ["ico3_m4", "ell3_m4"])
+# rows with up to 20 (ico3), 27 (ell3) and 138 (cube30, leaf 16) admissible blocks: the
+# tensor-core coupling sums segments of at most 16 blocks exactly and adds them in order
+TENSOR_CASES = {"cube30_m4": (lambda: I.cube(30), 16, 2.0, 4)}
+
+
+def _oracle_any(name):
+    if name in CASES:
+        return _oracle(name)
+    if name not in _oracles:
+        make, leaf, eta, m = TENSOR_CASES[name]
+        v, f = make()
+        _oracles[name] = (v, f, oracle.Oracle(v, f, leaf_size=leaf, eta=eta, order=m))
+    return _oracles[name]
+
+
+@pytest.mark.parametrize("name", ["ico3_m4", "ell3_m4", "cube30_m4"])
 def test_f64_tensor_core_coupling(require_gpu, name):
     """FP64-accurate coupling from 7-bit BF16 slices on the tensor cores (order 4,
     up to 16 right-hand sides; more fall back to the double-float coupling):
     against the oracle and the double-float path, and bit-reproducible."""
     import torch
-    v, f, o = _oracle(name)
-    make, leaf, eta, m = CASES[name]
+    v, f, o = _oracle_any(name)
+    make, leaf, eta, m = CASES[name] if name in CASES else TENSOR_CASES[name]
     ht = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64")
     hd = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64", tensor="off")
     assert ht.stats["tensor"] == 1 and hd.stats["tensor"] == 0

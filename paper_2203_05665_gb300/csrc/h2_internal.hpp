@@ -114,6 +114,7 @@ struct GmresWork {
   double *r = nullptr, *d = nullptr, *Az = nullptr;   // refinement vectors
   int *active = nullptr, *jc = nullptr;
   double *tolv = nullptr;                 // per column: residual target of the cycle
+  double *dpart = nullptr;                // chunk sums of the Gram-Schmidt dot products
   int *maxv = nullptr, *itc = nullptr;    // per column: iteration limit, iterations done
 };
 void free_gmres_work(GmresWork &w);

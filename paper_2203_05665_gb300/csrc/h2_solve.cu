@@ -4,6 +4,7 @@
 // Krylov arithmetic is FP64; the product runs in the handle's precision.
 // The paper names Krylov methods for the system Gz = b (Section 1) without
 // fixing one.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -39,6 +40,52 @@ __global__ void k_dots(const double *__restrict__ X, const double *__restrict__ 
   s = block_sum(s);
   if (threadIdx.x == 0) out[i * nrhs + c] = s;
 }
+
+// Gram-Schmidt dot products, 8 vectors per CTA so that W is read once per 8
+// dots: grid (nrhs, ceil(nvec / 8), Z); CTA (c, g, z) sums rows
+// [n z / Z, n (z + 1) / Z) and writes part[(z nvec + i) nrhs + c]; with
+// Z > 1 k_dots_sum adds the Z chunks in order (no atomics: reproducible).
+constexpr int kDotVB = 8;
+
+__global__ void __launch_bounds__(256) k_dots8(const double *__restrict__ X, const double *__restrict__ W, int64_t n,
+                                               int nrhs, int nvec, double *__restrict__ part) {
+  __shared__ double red[kDotVB][8];
+  const int c = blockIdx.x, i0 = blockIdx.y * kDotVB, z = blockIdx.z, Z = gridDim.z;
+  const int64_t r0 = n * z / Z, r1 = n * (z + 1) / Z;
+  double acc[kDotVB];
+#pragma unroll
+  for (int k = 0; k < kDotVB; ++k) acc[k] = 0.0;
+  const double *wc = W + (int64_t)c * n;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const double w = wc[r];
+#pragma unroll
+    for (int k = 0; k < kDotVB; ++k)
+      if (i0 + k < nvec) acc[k] = fma(X[((int64_t)(i0 + k) * nrhs + c) * n + r], w, acc[k]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kDotVB; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[k][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kDotVB && i0 + (int)threadIdx.x < nvec) {
+    double sum = 0.0;
+    for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) sum += red[threadIdx.x][w8];
+    part[((int64_t)z * nvec + i0 + threadIdx.x) * nrhs + c] = sum;
+  }
+}
+
+__global__ void k_dots_sum(const double *__restrict__ part, int Z, int nvec, int nrhs, double *__restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nvec * nrhs) return;
+  double s = 0.0;
+  for (int z = 0; z < Z; ++z) s += part[(int64_t)z * nvec * nrhs + e];
+  out[e] = s;
+}
+
+constexpr int kDotMaxZ = 16;
 
 // W[:, c] -= sum_{i < nvec} h[i][c] X_i[:, c]; accumulates h into H column j
 __global__ void k_orth(const double *__restrict__ X, const double *__restrict__ h, int nvec, int64_t n, int nrhs,
@@ -142,10 +189,21 @@ int grid1(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
+// out[i nrhs + c] = <X_i[:, c], W[:, c]> for i < nvec (part: kDotMaxZ nvec nrhs doubles of scratch)
+void dots(const double *X, const double *W, int64_t n, int nrhs, int nvec, double *out, double *part,
+          cudaStream_t st) {
+  // enough CTAs to fill the GPU, chunks of at least 1024 rows
+  const int groups = (nvec + kDotVB - 1) / kDotVB;
+  int Z = (int)std::min<int64_t>(kDotMaxZ, std::max<int64_t>(1, n / 1024));
+  while (Z > 1 && (int64_t)nrhs * groups * Z > 4 * 152) --Z;
+  k_dots8<<<dim3(nrhs, groups, Z), 256, 0, st>>>(X, W, n, nrhs, nvec, Z > 1 ? part : out);
+  if (Z > 1) k_dots_sum<<<(nvec * nrhs + 127) / 128, 128, 0, st>>>(part, Z, nvec, nrhs, out);
+}
+
 }  // namespace
 
 void free_gmres_work(GmresWork &w) {
-  double *dp[] = {w.Vb, w.W, w.H, w.cs, w.sn, w.g, w.h1, w.h2, w.hn, w.resid, w.yv, w.bn, w.r, w.d, w.Az};
+  double *dp[] = {w.Vb, w.W, w.H, w.cs, w.sn, w.g, w.h1, w.h2, w.hn, w.resid, w.yv, w.bn, w.r, w.d, w.Az, w.dpart};
   for (double *p : dp)
     if (p) cudaFree(p);
   for (int *p : {w.active, w.jc, w.maxv, w.itc})
@@ -177,6 +235,7 @@ int alloc_gmres_work(GmresWork &w, int64_t n_, int cols, int mr) {
   al(&w.resid, cols);
   al(&w.yv, (size_t)mr * cols);
   al(&w.bn, cols);
+  al(&w.dpart, (size_t)kDotMaxZ * (mr + 1) * cols);
   al(&w.r, tot);
   al(&w.d, tot);
   al(&w.Az, tot);
@@ -234,11 +293,11 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
   for (int j = 0; j < mr; ++j) {
     double *Vj = w.Vb + (int64_t)j * tot, *Vj1 = w.Vb + (int64_t)(j + 1) * tot;
     if ((rc = run_matvec(c, Vj, w.W, nrhs, true))) return rc;
-    k_dots<<<dim3(nrhs, j + 1), kT, 0, st>>>(w.Vb, w.W, n, nrhs, w.h1);
+    dots(w.Vb, w.W, n, nrhs, j + 1, w.h1, w.dpart, st);
     k_orth<<<grid1(tot), kT, 0, st>>>(w.Vb, w.h1, j + 1, n, nrhs, w.W);
-    k_dots<<<dim3(nrhs, j + 1), kT, 0, st>>>(w.Vb, w.W, n, nrhs, w.h2);
+    dots(w.Vb, w.W, n, nrhs, j + 1, w.h2, w.dpart, st);
     k_orth<<<grid1(tot), kT, 0, st>>>(w.Vb, w.h2, j + 1, n, nrhs, w.W);
-    k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(w.W, w.W, n, nrhs, w.hn);
+    dots(w.W, w.W, n, nrhs, 1, w.hn, w.dpart, st);
     k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
     k_scale<<<grid1(tot), kT, 0, st>>>(w.W, w.hn, w.active, n, nrhs, Vj1);
     k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(w.h1, w.h2, w.hn, j, mr, nrhs, w.H, w.cs, w.sn, w.g, w.resid,

@@ -144,6 +144,7 @@ int take_device_error(Ctx &c);
 // coefficient arrays [clusters][k][rp]) and that file's device error word
 bool tc_eligible(const Dev &d);
 int tc_build(Ctx &c, const int32_t *arow_dev);
+int tc_upward(Ctx &c, void *xhat, int rp, int64_t *launches);
 int tc_coupling(Ctx &c, const void *xhat, void *yhat, int rp);
 int tc_take_error(cudaStream_t st);
 

@@ -738,7 +738,13 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     mk.count(H2_PH_LEAF_FORWARD);
   }
   mk.mark(H2_PH_UPWARD);
-  if (far) {
+  const bool tcpath = std::is_same<T, dd>::value && d.tc && rp <= 16;
+  if (far && tcpath) {
+    // with the column maxima and coefficient slices of the tensor-core coupling
+    int64_t nl = 0;
+    if ((rc = tc_upward(c, xhat, rp, &nl))) return rc;
+    mk.count(H2_PH_UPWARD, nl);
+  } else if (far) {
     size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_upward<TE, T>, sm))) return rc;
     for (int l = D - 1; l >= lmin; --l) {
@@ -771,10 +777,9 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
       } else {
         return fail(H2_EINVAL, "the regenerated coupling runs in FP32 arithmetic only");
       }
-    } else if (std::is_same<T, dd>::value && d.tc && rp <= 16) {
+    } else if (tcpath) {
       // FP64-accurate: integer slices on the tensor cores
       if ((rc = tc_coupling(c, xhat, yhat, rp))) return rc;
-      mk.count(H2_PH_COUPLING, 2);
     } else {
       CouplingRows<TS, T> rows{(const TS *)d.S, d.adm_ptr, d.adm_col, xhat, k, kp, rp, row0};
       if ((rc = launch_rows<TS, T>(rows, cf_cpl, t_cpl, Rk, d.nclu - row0, 0, out, st))) return rc;

@@ -26,7 +26,7 @@
 // no swizzle), so one bulk copy (TMA engine) per block moves them; the
 // coefficients are cut once per product.  One MMA instruction multiplies two
 // stacked slices of S (M = 128 rows: slices i and i+1) by all slices of x^
-// side by side (N = 8 x 16 columns, the eighth slice zero), K = 16: four
+// side by side (N = 7 x 16 columns), K = 16: four
 // such groups, four K steps each, 16 instructions per block (the cost of
 // an instruction hardly depends on N at these sizes); the epilogue reads the
 // 28 pairs with i + k <= 8.
@@ -48,6 +48,7 @@
 #include "h2_dd.cuh"
 #include "h2_internal.hpp"
 #include "h2_ptx.cuh"
+#include "h2_transfer.cuh"
 
 namespace h2 {
 namespace {
@@ -60,12 +61,12 @@ constexpr int kTcSegBlocks = 16;         // blocks accumulated in one exact segm
 constexpr uint32_t kSliceA = kTcK * kTcK * 2;          // 8192 bytes: one slice of S_b (64 x 64 BF16)
 constexpr uint32_t kSliceB = kTcN * kTcK * 2;          // 2048 bytes: one slice of x^_s (16 x 64 BF16)
 constexpr uint32_t kTileA = kTcSlices * kSliceA;       // 57344
-constexpr uint32_t kTileB = (kTcSlices + 1) * kSliceB; // 16384: seven slices and a zero slice (N = 128)
-constexpr uint32_t kStage = kTileA + kTileB;           // 73728
+constexpr uint32_t kTileB = kTcSlices * kSliceB;       // 14336: the seven slices of x^_s (N = 112)
+constexpr uint32_t kStage = kTileA + kTileB;           // 71680
 constexpr int kTcStages = 3;
 constexpr int kTcGroups = 4;             // S slice pairs (1,2), (3,4), (5,6), (7,-)
-constexpr int kTcNB = 128;               // N of one MMA: the eight slices of x^, 16 columns each
-constexpr uint32_t kTmemCols = 512;      // one accumulator set: 4 groups x 128 columns
+constexpr int kTcNB = 112;               // N of one MMA: the seven slices of x^, 16 columns each
+constexpr uint32_t kTmemCols = 512;      // one accumulator set: 4 groups x 112 columns (448 used)
 constexpr int kTcThreads = 192;          // producer, MMA, four epilogue warps
 constexpr uint32_t kXch = 64 * kTcN * 8; // epilogue exchange: 64 rows x 16 double-float values
 constexpr uint32_t kBarOff = kTcStages * kStage + kXch;
@@ -201,14 +202,13 @@ __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__
 // ---------------------------------------------------------------- per product
 __device__ __forceinline__ int tc_level(int64_t c) { return 63 - __clzll(c + 1); }
 
-// xmax[l][j] = largest |hi| of column j over the clusters of level l (as float
-// bits); grid.y = level - lmin, each thread takes whole coefficient rows
-__global__ void k_tc_xmax(const dd *__restrict__ xhat, int lmin, int rp, unsigned *__restrict__ xmax) {
+// xmax[lvl][j] = largest |hi| of column j over clusters [c0, c0 + ncl) of level lvl (as float bits)
+__global__ void k_tc_levmax(const dd *__restrict__ xhat, int64_t c0, int64_t ncl, int lvl, int rp,
+                            unsigned *__restrict__ xmax) {
   __shared__ unsigned loc[kTcN];
   if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
   __syncthreads();
-  const int l = lmin + blockIdx.y;
-  const int64_t c0 = ((int64_t)1 << l) - 1, rows = ((int64_t)1 << l) * kTcK;
+  const int64_t rows = ncl * kTcK;
   float mx[kTcN];
 #pragma unroll
   for (int j = 0; j < kTcN; ++j) mx[j] = 0.0f;
@@ -225,7 +225,7 @@ __global__ void k_tc_xmax(const dd *__restrict__ xhat, int lmin, int rp, unsigne
     if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&loc[j], __float_as_uint(v));
   }
   __syncthreads();
-  if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[l * kTcN + threadIdx.x], loc[threadIdx.x]);
+  if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[lvl * kTcN + threadIdx.x], loc[threadIdx.x]);
 }
 
 // F = 2 + floor(log2 max): |hi + lo| < 2^(F-1)
@@ -233,41 +233,68 @@ __device__ __forceinline__ int tc_colexp(unsigned bits) {
   return bits ? (int)((bits >> 23) & 0xFF) - 127 + 2 : 0;
 }
 
-// the seven BF16 slices of the coefficients of kTcXc clusters per CTA: the
-// tiles are read with coalesced loads, cut in registers, assembled in shared
-// memory in the MMA layout (16 columns x 64 contraction values per slice)
-// and written out with 16-byte stores (the eighth, zero slice is never
-// written)
-constexpr int kTcXc = 2;
-
-__global__ void __launch_bounds__(256) k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int64_t nclu, int rp,
-                                                    const unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
-  __shared__ __align__(16) __nv_bfloat16 tile[kTcXc][kTcSlices][kTcN * kTcK];
-  const int64_t cb = c0 + (int64_t)blockIdx.x * kTcXc;
-  const int nc = (int)(nclu - cb < kTcXc ? nclu - cb : kTcXc);
-  for (int e = threadIdx.x; e < kTcXc * kTcN * kTcK; e += blockDim.x) {
-    const int ci = e / (kTcN * kTcK), rem = e % (kTcN * kTcK);
-    const int mu = rem / kTcN, j = rem % kTcN;
-    if (ci >= nc) break;
-    const int64_t c = cb + ci;
+// The seven BF16 slices of the coefficients of cluster c (x^_c [64][rp]):
+// cut in registers, assembled in shared memory (tile: 7 x 16 x 64 BF16,
+// 14 KB) in the MMA layout (16 columns x 64 contraction values per slice)
+// and written out with 16-byte stores.  All threads of the CTA take part;
+// the caller synchronises before and after.
+__device__ __forceinline__ void slice_cluster(const dd *__restrict__ xc, int rp, int lvl,
+                                              const unsigned *__restrict__ xmax, __nv_bfloat16 *tile,
+                                              __nv_bfloat16 *__restrict__ dst) {
+  for (int e = threadIdx.x; e < kTcN * kTcK; e += blockDim.x) {
+    const int mu = e / kTcN, j = e % kTcN;
     long long X = 0;
     if (j < rp) {
-      const int sc = kTcFixBits - tc_colexp(xmax[tc_level(c) * kTcN + j]);
-      const dd v = xhat[(c * kTcK + mu) * rp + j];
+      const int sc = kTcFixBits - tc_colexp(xmax[lvl * kTcN + j]);
+      const dd v = xc[mu * rp + j];
       X = llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
     }
     int sl[kTcSlices];
     split7(X, sl);
     const int o = core_off(j, mu);
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) tile[ci][i][o] = __float2bfloat16_rn((float)sl[i]);
+    for (int i = 0; i < kTcSlices; ++i) tile[i * kTcN * kTcK + o] = __float2bfloat16_rn((float)sl[i]);
   }
   __syncthreads();
-  constexpr int kWords = kTcSlices * kTcN * kTcK / 8;   // 16-byte words of one cluster's seven slices
-  for (int w = threadIdx.x; w < nc * kWords; w += blockDim.x) {
-    const int ci = w / kWords, wi = w % kWords;
-    uint4 *dst = reinterpret_cast<uint4 *>(xtc + (cb + ci) * (int64_t)(kTileB / 2));
-    dst[wi] = reinterpret_cast<const uint4 *>(&tile[ci][0][0])[wi];
+  constexpr int kWords = kTcSlices * kTcN * kTcK / 8;   // 16-byte words of the seven slices
+  for (int w = threadIdx.x; w < kWords; w += blockDim.x)
+    reinterpret_cast<uint4 *>(dst)[w] = reinterpret_cast<const uint4 *>(tile)[w];
+}
+
+// the slices of clusters [c0, c0 + ncl) of level lvl, one cluster per CTA
+__global__ void __launch_bounds__(256) k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int lvl, int rp,
+                                                    const unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
+  __shared__ __align__(16) __nv_bfloat16 tile[kTcSlices * kTcN * kTcK];
+  const int64_t c = c0 + blockIdx.x;
+  slice_cluster(xhat + c * kTcK * rp, rp, lvl, xmax, tile, xtc + c * (int64_t)(kTileB / 2));
+}
+
+// Upward step for one parent of level l (Algorithm 1, factored transfers,
+// the generic body) with the two extra tasks of the tensor-core coupling:
+// the column maxima of level l from the parent's coefficients, and the
+// slices of its two children (level l + 1, whose maxima are complete).
+__global__ void k_upward_tc(const dd *__restrict__ Ef, int m, int k, int rp, int64_t par0, int lvl,
+                            dd *__restrict__ xhat, unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned loc[kTcN];
+  if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
+  const int64_t par = par0 + blockIdx.x;
+  upward_parent<dd, dd>(Ef, m, k, rp, par, xhat, smem_raw);   // ends with the parent written to xhat
+  __syncthreads();
+  // column maxima of the parent (the values this CTA has just written)
+  const int kr = k * rp;
+  for (int i = threadIdx.x; i < kr; i += blockDim.x) {
+    const float v = fabsf(xhat[par * kr + i].hi);
+    if (v > 0.0f) atomicMax(&loc[i % rp], __float_as_uint(v));
+  }
+  __syncthreads();
+  if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[lvl * kTcN + threadIdx.x], loc[threadIdx.x]);
+  // the children's slices, staged in the (now free) dynamic shared memory
+  __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+  for (int ch = 0; ch < 2; ++ch) {
+    const int64_t c = 2 * par + 1 + ch;
+    slice_cluster(xhat + c * kr, rp, lvl + 1, xmax, tile, xtc + c * (int64_t)(kTileB / 2));
+    __syncthreads();
   }
 }
 
@@ -522,20 +549,52 @@ int tc_build(Ctx &c, const int32_t *arow_dev) {
   return H2_OK;
 }
 
+// Upward pass of an FP64-accurate product on the tensor-core path: the
+// transfers of Algorithm 1 with the column maxima and the coefficient slices
+// of every level produced on the way (k_upward_tc), the leaves' maxima before
+// and the slices of the top level after.  Returns the launches made.
+int tc_upward(Ctx &c, void *xhat_v, int rp, int64_t *launches) {
+  dd *xhat = static_cast<dd *>(xhat_v);
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
+  const int D = d.depth, lmin = d.first_adm_level;
+  if (lmin > D) return H2_OK;
+  const int64_t leaf0 = d.nleaf - 1;
+  int64_t nl = 0;
+  H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
+  const int64_t lrows = d.nleaf * kTcK;
+  k_tc_levmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((lrows + 255) / 256, 152 * 8)), 256, 0, st>>>(
+      xhat, leaf0, d.nleaf, D, rp, d.tc_xmax);
+  ++nl;
+  const int k = d.k, m = d.m;
+  // k = 64, rp <= 16: at most 25,344 bytes, below the 48 KB default limit
+  const size_t sm = std::max<size_t>(((size_t)3 * k * rp + 6 * m * m) * sizeof(dd), kTileB);
+  for (int l = D - 1; l >= lmin; --l) {
+    const int64_t par0 = ((int64_t)1 << l) - 1;
+    k_upward_tc<<<(unsigned)((int64_t)1 << l), 256, sm, st>>>((const dd *)d.Ef, m, k, rp, par0, l, xhat, d.tc_xmax,
+                                                                (__nv_bfloat16 *)d.xtc);
+    ++nl;
+  }
+  // the top level's slices (the leaves' when there is no transfer)
+  const int64_t c0 = ((int64_t)1 << lmin) - 1;
+  k_tc_slice_x<<<(unsigned)((int64_t)1 << lmin), 256, 0, st>>>(xhat, c0, lmin, rp, d.tc_xmax,
+                                                                (__nv_bfloat16 *)d.xtc);
+  ++nl;
+  H2_CUDA_TRY(cudaGetLastError());
+  if (launches) *launches = nl;
+  return H2_OK;
+}
+
+// the coupling phase: the coefficient slices exist (tc_upward)
 int tc_coupling(Ctx &c, const void *xhat_v, void *yhat_v, int rp) {
-  const dd *xhat = static_cast<const dd *>(xhat_v);
+  (void)xhat_v;
   dd *yhat = static_cast<dd *>(yhat_v);
   Dev &d = c.d;
   cudaStream_t st = c.stream;
   if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
   const int64_t row0 = ((int64_t)1 << d.first_adm_level) - 1, nrows = d.nclu - row0;
   if (nrows <= 0) return H2_OK;
-  H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
-  const int nlev = d.depth - d.first_adm_level + 1;
-  k_tc_xmax<<<dim3(512, nlev), 256, 0, st>>>(xhat, d.first_adm_level, rp, d.tc_xmax);
-  const int64_t nxc = d.nclu - row0;
-  k_tc_slice_x<<<(unsigned)((nxc + kTcXc - 1) / kTcXc), 256, 0, st>>>(xhat, row0, d.nclu, rp, d.tc_xmax,
-                                                                      (__nv_bfloat16 *)d.xtc);
   static_assert(kTcSmem <= 227 * 1024, "tensor-core coupling does not fit in shared memory");
   H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_coupling_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(227 * 1024)));

@@ -35,10 +35,13 @@ __device__ __forceinline__ void mode_fibres(const T *F, const T *in, T *out, int
 #pragma unroll
     for (int j = 0; j < kMaxM; ++j) {
       if (j >= m) break;
+      // double-float: the low word collects the exact errors of the m terms,
+      // one renormalisation per output
       T acc = zero_of<T>();
 #pragma unroll
       for (int i = 0; i < kMaxM; ++i)
-        if (i < m) acc = madd(trans ? F[i * m + j] : F[j * m + i], v[i], acc);
+        if (i < m) acc_fma(acc, trans ? F[i * m + j] : F[j * m + i], v[i]);
+      acc_norm(acc);
       out[(base + j * stride) * rp + c] = acc;
     }
   }

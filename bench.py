@@ -68,7 +68,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -200,7 +200,7 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": alg["coupling_bytes"] / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "kernel": "k_coupling_tc (tcgen05, 7-bit BF16 slices, exact FP32 sums)",
                 "stored_bytes_per_entry": 14,
-                "stored_frac": (st["adm_blocks"] * (14 * st["rank"] ** 2 + 16384) / (cpl_ms * 1e-3) / 1e9
+                "stored_frac": (st["adm_blocks"] * (14 * st["rank"] ** 2 + 14336) / (cpl_ms * 1e-3) / 1e9
                                 / peaks["hbm_gbs"])}
     elif args.prec == "f64":
         roof = {"bound": "alu", "achieved": alg["coupling_flops"] / (cpl_ms * 1e-3) / 1e12, "peak": DD_TFLOPS,
@@ -620,7 +620,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f64n", "bf16", "f16"],

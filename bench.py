@@ -277,6 +277,29 @@ def run_ours(args):
             solve["gmres_ir"] = dict(timed(lambda: h.solve_ir(lo, b, rtol=1e-8, inner_rtol=1e-4, restart=30,
                                                               maxit_inner=5000, maxit_outer=50)),
                                      residual=args.prec, inner="f32 GMRES(30) to 1e-4")
+            # the FP32 product of the same workload (FP64 vs FP32 on one matrix)
+            xf = colmajor(x.float())
+            yf = colmajor(torch.empty_like(xf))
+            for _ in range(3):
+                lo.matvec(xf, yf)
+            lo.profile(True)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(10):
+                lo.matvec(xf, yf)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            fph, fpr = lo.phase_times()
+            lo.profile(False)
+            fms = f0.elapsed_time(f1) / 10
+            a32 = _algorithmic(lo.stats, nrhs, 4)
+            fcpl = fph["coupling"][0] / fpr
+            solve["fp32_product"] = {
+                "ms": fms, "dof_per_s": n * nrhs / (fms * 1e-3),
+                "rel_diff_vs_f64": float(torch.linalg.norm(yf.double() - y) / torch.linalg.norm(y)),
+                "phases_ms": {k2: v2[0] / fpr for k2, v2 in fph.items()},
+                "coupling_hbm_frac": a32["coupling_bytes"] / (fcpl * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "kernel": "k_blockrow (coupling, stored FP32 S)"}
             lo.close()
 
     serve = None

@@ -302,6 +302,10 @@ def run_ours(args):
                 "kernel": "k_blockrow (coupling, stored FP32 S)"}
             lo.close()
 
+    small = None
+    if rank == 0 and not args.no_small:
+        small = run_small(args, local, stream)
+
     serve = None
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, local, stream)
@@ -339,6 +343,7 @@ def run_ours(args):
         "build_s": build_s,
         "finite": finite,
         "solve": solve,
+        "small": small,
         "serve": serve,
         "mixed": mixed,
         "batch": batch,
@@ -421,6 +426,59 @@ def run_serve(args, local, stream):
     for name, n, hi, lo in geoms:
         hi.close()
         lo.close()
+    return out
+
+
+def run_small(args, local, stream):
+    """The 5,120-triangle configuration (icosphere L4, m = 3, leaf 32, eta 2,
+    FP64-accurate): latency of one product with one right-hand side, launched
+    kernel by kernel (h2_matvec) and replayed from a CUDA graph (h2_graph_*),
+    each the median over per-product CUDA-event pairs; and GMRES(30) to 1e-8 on
+    the seeded uniform right-hand side and on the constant density."""
+    import torch
+    from paper_2203_05665_gb300 import H2Matrix, colmajor, inputs
+    v, f = inputs.icosphere(4)
+    n = f.shape[0]
+    h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec="f64", device=local, stream=stream.cuda_stream)
+    x = colmajor(torch.from_numpy(inputs.uniform_rhs(n, 1, 1001)).to(device="cuda"))
+    y = colmajor(torch.empty_like(x))
+    yg = colmajor(torch.empty_like(x))
+    g = h.graph(x, yg)
+    reps = max(30, args.steps // 2)
+
+    def lat(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        wall = []
+        for a, b in ev:
+            t = time.perf_counter()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            wall.append(time.perf_counter() - t)
+        dev = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
+        wall.sort()
+        return {"median_us": dev[len(dev) // 2], "min_us": dev[0], "p99_us": dev[min(reps - 1, int(0.99 * reps))],
+                "host_wall_median_us": wall[len(wall) // 2] * 1e6}
+
+    out = {"workload": f"icosphere L4 ({n} triangles), m=3 (k=27), leaf 32, eta 2, stored S, SS order 3, "
+                       "FP64-accurate (double-float)", "reps": reps,
+           "direct": lat(lambda: h.matvec(x, y)), "graph": lat(g.launch)}
+    torch.cuda.synchronize()
+    out["graph_equals_direct"] = bool(torch.equal(y, yg))
+    out["graph_speedup"] = out["direct"]["median_us"] / out["graph"]["median_us"]
+    b = np.asfortranarray(np.stack([inputs.uniform_rhs(n, 1, 1001)[:, 0], np.ones(n)], axis=1))
+    h.solve(b, rtol=1e-8, restart=30, maxit=2000)
+    t = time.perf_counter()
+    z, it, rel, st = h.solve(b, rtol=1e-8, restart=30, maxit=2000)
+    out["gmres"] = {"rhs": ["uniform [-1,1] seed 1001", "constant density 1"], "rtol": 1e-8, "restart": 30,
+                    "solve_s": time.perf_counter() - t, "iters": [int(i) for i in it],
+                    "relres": [float(r) for r in rel], "status": int(st)}
+    g.close()
+    h.close()
     return out
 
 
@@ -658,6 +716,7 @@ def main():
     ap.add_argument("--solve-nrhs", type=int, default=16)
     ap.add_argument("--solve-reps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the icosphere L4 latency leg")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--mixed-level", type=int, default=8)
     ap.add_argument("--serve-full", action="store_true", help="all 8 geometries (icosphere L4-L8, ...)")

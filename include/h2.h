@@ -181,6 +181,20 @@ int h2_matvec(h2_handle h, const void *x, void *y, int nrhs);
  *   - h2_coefficients keeps describing the last h2_matvec product. */
 int h2_matvec_noalloc(h2_handle h, const void *x, void *y, int nrhs);
 
+/* The product captured once into a CUDA graph for fixed device buffers x, y
+ * (as for h2_matvec) and replayed: h2_graph_launch runs y = G~ x
+ * asynchronously on the handle's stream with the launch cost of one graph
+ * (the product is 20 to 40 kernels).  The paper has no counterpart; the
+ * GB300 build uses graphs where a tracing compiler would be used elsewhere.
+ * The graph refers to the handle's work space: a later product with more
+ * right-hand sides than any before reallocates it, after which
+ * h2_graph_launch returns H2_EINVAL.  Destroy graphs before their handle;
+ * a handle's graphs and products must not overlap on the GPU (one stream). */
+typedef struct h2_graph_s *h2_graph;
+int h2_graph_create(h2_handle h, const void *x, void *y, int nrhs, h2_graph *out);
+int h2_graph_launch(h2_graph g);
+int h2_graph_destroy(h2_graph g);
+
 /* The same product with HOST double arrays whatever the handle's precision:
  * copies x to the device, multiplies, copies y back and synchronises the
  * stream. */

@@ -8,6 +8,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -49,7 +50,8 @@ EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_
             "h2_serve_create", "h2_serve_register", "h2_serve_submit", "h2_serve_poll", "h2_serve_wait",
             "h2_serve_stats", "h2_serve_destroy", "h2_batch_create", "h2_batch_offsets", "h2_batch_matvec",
             "h2_batch_tune", "h2_batch_set_shapes", "h2_batch_profile", "h2_batch_phase_times", "h2_batch_info",
-            "h2_batch_sync", "h2_batch_destroy", "h2_last_error"]
+            "h2_batch_sync", "h2_batch_destroy", "h2_graph_create", "h2_graph_launch", "h2_graph_destroy",
+            "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -106,6 +108,9 @@ def load():
             "h2_batch_info": (C.c_int, [vp, i64p]),
             "h2_batch_sync": (C.c_int, [vp]),
             "h2_batch_destroy": (C.c_int, [vp]),
+            "h2_graph_create": (C.c_int, [vp, vp, vp, C.c_int, C.POINTER(vp)]),
+            "h2_graph_launch": (C.c_int, [vp]),
+            "h2_graph_destroy": (C.c_int, [vp]),
             "h2_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -216,6 +221,8 @@ class H2Matrix:
         self.stats = {f: int(getattr(st, f)) for f, _ in Stats._fields_}
 
     def close(self):
+        for g in list(getattr(self, "_graphs", ())):
+            g.close()   # a graph refers to the handle: destroy it first
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             self._lib.h2_destroy(h)
@@ -246,6 +253,25 @@ class H2Matrix:
         _check(self._lib.h2_matvec_noalloc(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                            int(x.shape[1])))
         return y
+
+    def graph(self, x, y):
+        """The product y = G~ x for these fixed device buffers, captured once as a CUDA graph.
+
+        Returns a ProductGraph whose launch() replays it on the handle's stream;
+        x and y must stay alive (and in place) while the graph is used.
+        """
+        if x.shape != y.shape or x.shape[0] != self.n:
+            raise ValueError("x and y must both be (n, nrhs)")
+        if x.stride(0) != 1 or y.stride(0) != 1:
+            raise ValueError("x and y must be column-major (use colmajor())")
+        g = C.c_void_p()
+        _check(self._lib.h2_graph_create(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                         int(x.shape[1]), C.byref(g)))
+        pg = ProductGraph(self, g, (x, y))
+        if not hasattr(self, "_graphs"):
+            self._graphs = weakref.WeakSet()
+        self._graphs.add(pg)
+        return pg
 
     def profile(self, enable=True):
         """Start (or stop) per-phase CUDA-event timing on the handle's stream."""
@@ -362,6 +388,28 @@ class Server:
         if h is not None and h.value:
             self._lib.h2_serve_destroy(h)
             self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class ProductGraph:
+    """One H² product captured as a CUDA graph (h2_graph_*); holds its matrix and buffers alive."""
+
+    def __init__(self, mat, g, bufs):
+        self._lib = mat._lib
+        self._mat = mat
+        self._g = g
+        self._bufs = bufs
+
+    def launch(self):
+        _check(self._lib.h2_graph_launch(self._g))
+
+    def close(self):
+        g = getattr(self, "_g", None)
+        if g is not None and g.value:
+            self._lib.h2_graph_destroy(g)
+            self._g = None
 
     def __del__(self):
         self.close()

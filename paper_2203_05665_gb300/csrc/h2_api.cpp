@@ -250,6 +250,95 @@ int h2_matvec(h2_handle h, const void *x, void *y, int nrhs) {
   return run_matvec(*h, x, y, nrhs, false);
 }
 
+}  // extern "C"
+
+struct h2_graph_s {
+  h2_ctx *h = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t work_gen = 0;    // the handle's work-space generation at capture
+  int nrhs = 0, rp = 0;    // the captured product's right-hand sides and padded width
+};
+
+extern "C" {
+
+int h2_graph_create(h2_handle h, const void *x, void *y, int nrhs, h2_graph *out) {
+  if (!out) return fail(H2_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!h || !x || !y) return fail(H2_EINVAL, "NULL argument");
+  if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  int rc = ensure_work(*h, nrhs);   // any allocation happens before the capture
+  if (rc) return rc;
+  if (h->stream) H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  else H2_CUDA_TRY(cudaDeviceSynchronize());
+  cudaStream_t cap = nullptr;
+  H2_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaStream_t own = h->stream;
+  const bool prof = h->prof.on;
+  const int slast = h->d.last_nrhs, slast_rp = h->d.last_rp;
+  h->stream = cap;
+  h->prof.on = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  int cap_nrhs = 0, cap_rp = 0;
+  if (e == cudaSuccess) {
+    rc = run_matvec(*h, x, y, nrhs, false);
+    cap_nrhs = h->d.last_nrhs;
+    cap_rp = h->d.last_rp;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "capture of the product");
+  } else {
+    rc = cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  h->stream = own;
+  h->prof.on = prof;
+  h->d.last_nrhs = slast;
+  h->d.last_rp = slast_rp;
+  cudaStreamDestroy(cap);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  h2_graph_s *G = new (std::nothrow) h2_graph_s();
+  if (!G) {
+    cudaGraphDestroy(g);
+    return fail(H2_ENOMEM, "graph");
+  }
+  e = cudaGraphInstantiate(&G->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    delete G;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  G->h = h;
+  G->work_gen = h->d.work_gen;
+  G->nrhs = cap_nrhs;
+  G->rp = cap_rp;
+  *out = G;
+  return H2_OK;
+}
+
+int h2_graph_launch(h2_graph g) {
+  if (!g) return fail(H2_EINVAL, "NULL graph");
+  if (g->h->d.work_gen != g->work_gen)
+    return fail(H2_EINVAL, "the handle's work space was reallocated since the capture; create the graph again");
+  H2_CUDA_TRY(cudaSetDevice(g->h->device));
+  H2_CUDA_TRY(cudaGraphLaunch(g->exec, g->h->stream));
+  g->h->d.last_nrhs = g->nrhs;   // h2_coefficients now describes this product
+  g->h->d.last_rp = g->rp;
+  return H2_OK;
+}
+
+int h2_graph_destroy(h2_graph g) {
+  if (!g) return H2_OK;
+  cudaSetDevice(g->h->device);
+  if (g->h->stream) cudaStreamSynchronize(g->h->stream);
+  else cudaDeviceSynchronize();
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
+  return H2_OK;
+}
+
 int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs) {
   if (!h || !x || !y) return fail(H2_EINVAL, "NULL argument");
   if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");

@@ -95,6 +95,7 @@ struct Dev {
   void *xpad = nullptr, *ypad = nullptr, *xhat = nullptr, *yhat = nullptr;
   double *io_x = nullptr, *io_y = nullptr;   // FP64 staging for host / solver I/O
   int last_nrhs = 0, last_rp = 0;  // last product: right-hand sides and padded coefficient width
+  int64_t work_gen = 0;            // incremented whenever the work buffers are reallocated
   int64_t bytes = 0;
 };
 

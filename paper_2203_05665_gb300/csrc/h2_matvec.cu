@@ -852,6 +852,7 @@ int ensure_work(Ctx &c, int nrhs_req) {
   H2_CUDA_TRY(cudaMemsetAsync(d.xhat, 0, es * d.nclu * d.k * nrhs, c.stream));
   H2_CUDA_TRY(cudaMemsetAsync(d.yhat, 0, es * d.nclu * d.k * nrhs, c.stream));
   d.cap_nrhs = nrhs;
+  d.work_gen++;
   return H2_OK;
 }
 

@@ -77,10 +77,11 @@ typedef struct h2_options {
   void *stream;      /* cudaStream_t used by every call on the handle; NULL = the legacy default stream */
   int coupling;      /* enum h2_coupling; default H2_COUPLING_AUTO */
   int tensor;        /* 0 (default): an H2_F64 handle with stored coupling and order 4 also keeps its
-                      * coupling matrices as 7 BF16 slices of 7 bits (a power of two per row) and runs
-                      * the coupling phase of products with up to 16 right-hand sides on the tensor
-                      * cores (integer slice products summed exactly, combined in double-float;
-                      * agrees with the double-float path to about 1e-13); 1: never */
+                      * coupling matrices as 10 signed 5-bit digits in FP8 E4M3 (10 bytes per
+                      * entry, a power of two per row) and runs the coupling phase of products with
+                      * up to 16 right-hand sides on the tensor cores (integer digit products summed
+                      * exactly, combined in double-float; agrees with the double-float path to
+                      * about 1e-13); 1: never */
   int reserved[6];   /* must be zero */
 } h2_options;
 

@@ -79,10 +79,11 @@ struct Dev {
   double *icen = nullptr;       // nclu x 3 interpolation-box centres (regenerated coupling)
   float *adm_dc = nullptr;      // nadm x 4: centre of the row cluster minus centre of the column cluster
   float *ihalf = nullptr;       // nclu x 3 interpolation-box half widths
-  // FP64-accurate coupling on the tensor cores (order 4): the BF16 slices of
-  // every S_b ([nadm][7][64 x 64], K-major core-matrix layout), the row
-  // exponents ([nclu][64]), the slices of the coefficients of one product
-  // ([nclu][7][16 x 64]) and the column maxima per level ([32][16])
+  // FP64-accurate coupling on the tensor cores (order 4): the ten E4M3 digit
+  // planes of every S_b ([nadm][10][64 x 64] bytes, K-major core-matrix
+  // layout), the row exponents ([nclu][64]), the digit planes of the
+  // coefficients of one product ([nclu][10][16 x 64]) and the column maxima
+  // per level ([32][16])
   int tensor = 0;               // 0: use the tensor cores where supported, 1: never
   bool tc = false;              // the slices exist
   void *Stc = nullptr, *xtc = nullptr;

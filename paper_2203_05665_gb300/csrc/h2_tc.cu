@@ -1,6 +1,6 @@
-// FP64-accurate coupling phase on the tensor cores (tcgen05, BF16 operands,
-// FP32 accumulation in tensor memory), for order m = 4 (k = 64) and up to
-// 16 right-hand sides.
+// FP64-accurate coupling phase on the tensor cores (tcgen05, FP8 E4M3
+// operands, FP32 accumulation in tensor memory), for order m = 4 (k = 64) and
+// up to 16 right-hand sides.
 //
 // GB300 runs FP64 at 1/58 of its FP32 rate, and double-float arithmetic on
 // the FP32 pipe leaves the coupling (Algorithm 3, y^_t = sum S_ts x^_s)
@@ -11,35 +11,36 @@
 //  * every row nu of the coupling matrices of row cluster t gets a power of
 //    two 2^E (E[t][nu], common to all blocks of the row, |S| < 2^E), every
 //    column j of the coefficients of tree level l a power of two 2^F;
-//  * a value v becomes the 49-bit integer X = round(v 2^(49-E)), split into
-//    seven signed 7-bit slices, X = sum_i s_i 2^(49-7i), |s_i| <= 128: each
-//    slice is exact in BF16;
+//  * a value v becomes the integer X = round(v 2^(49-E)), |X| <= 2^49,
+//    split into ten signed 5-bit digits, X = sum_i s_i 2^(50-5i),
+//    |s_i| <= 16: every digit is exact in FP8 E4M3 (one byte);
 //  * D_ik = sum_blocks sum_mu s_i[nu][mu] t_k[mu][j] is a sum of at most
-//    16 x 64 products below 2^13 in magnitude, an integer below 2^23: the
-//    tensor cores accumulate it exactly in FP32;
-//  * y^_t[nu][j] = 2^(E + F) sum_{i + k <= 8} 2^(-7(i+k)) D_ik, summed in
-//    double-float; the dropped pairs and the rounding of X stay below 2^-47
+//    64 x 64 products of magnitude <= 2^8, an integer of at most 2^20: the
+//    tensor cores accumulate it exactly in FP32, and the at most five D_ik
+//    of one level i + k add exactly in FP32 too;
+//  * y^_t[nu][j] = 2^(E + F) sum_{i + k <= 11} 2^(2-5(i+k)) D_ik, the ten
+//    levels summed in double-float; the dropped pairs and the rounding of X stay below 2^-46
 //    of the row's scale.
 //
-// The slices of S are cut once at set-up, straight into the layout the
+// The digits of S are cut once at set-up, straight into the layout the
 // tensor cores read from shared memory (K-major, 8 x 16-byte core matrices,
-// no swizzle), so one bulk copy (TMA engine) per block moves them; the
-// coefficients are cut once per product.  One MMA instruction multiplies two
-// stacked slices of S (M = 128 rows: slices i and i+1) by all slices of x^
-// side by side (N = 7 x 16 columns), K = 16: four
-// such groups, four K steps each, 16 instructions per block (the cost of
-// an instruction hardly depends on N at these sizes); the epilogue reads the
-// 28 pairs with i + k <= 8.
+// no swizzle), 10 bytes per entry, so bulk copies (TMA engine) move a block
+// as it is stored; the coefficients are cut once per product.  One MMA
+// instruction (kind::f8f6f4, K = 32) multiplies two stacked digit planes of
+// S (M = 128 rows: digits i and i+1) by the digit planes of x^ it pairs with
+// (N = 16 columns per plane, 160 down to 32): five such groups, two K steps
+// each, 10 instructions per block; the epilogue reads the 55 pairs with
+// i + k <= 11 (480 accumulator columns).
 //
 // Kernel roles (one CTA per SM, 6 warps): warp 0 streams the slices of each
-// block through a 3-stage shared-memory ring (bulk copies completing on
+// block through a 4-stage shared-memory ring (bulk copies completing on
 // mbarriers), warp 1 allocates tensor memory and issues the MMAs of a row
-// segment (at most 16 blocks) into the accumulators, warps 2-5
-// read it back (tcgen05.ld), combine the pairs in double-float and write
+// segment (at most 64 blocks) into the accumulators, warps 2-5
+// read it back (tcgen05.ld), add the pairs of each level in FP32 and the levels in double-float, and write
 // y^_t.  Every wait is bounded; on a timeout the device error word
 // is raised, every role stops, copies and MMAs in flight are waited for and
 // the tensor memory is released before the CTA exits.
-#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -55,50 +56,60 @@ namespace {
 
 constexpr int kTcK = 64;                 // rank k = m^3, m = 4
 constexpr int kTcN = 16;                 // right-hand sides of one product (padded)
-constexpr int kTcSlices = 7;             // slices of a value
-constexpr int kTcFixBits = 49;           // bits of the fixed-point integer X
-constexpr int kTcSegBlocks = 16;         // blocks accumulated in one exact segment
-constexpr uint32_t kSliceA = kTcK * kTcK * 2;          // 8192 bytes: one slice of S_b (64 x 64 BF16)
-constexpr uint32_t kSliceB = kTcN * kTcK * 2;          // 2048 bytes: one slice of x^_s (16 x 64 BF16)
-constexpr uint32_t kTileA = kTcSlices * kSliceA;       // 57344
-constexpr uint32_t kTileB = kTcSlices * kSliceB;       // 14336: the seven slices of x^_s (N = 112)
-constexpr uint32_t kStage = kTileA + kTileB;           // 71680
-constexpr int kTcStages = 3;
-constexpr int kTcGroups = 4;             // S slice pairs (1,2), (3,4), (5,6), (7,-)
-constexpr int kTcNB = 112;               // N of one MMA: the seven slices of x^, 16 columns each
-constexpr uint32_t kTmemCols = 512;      // one accumulator set: 4 groups x 112 columns (448 used)
+constexpr int kTcSlices = 10;            // 5-bit digits of a value
+constexpr int kTcFixBits = 49;           // |X| <= 2^49
+constexpr int kTcTop = 11;               // digit pairs with i + k <= 11 are summed
+constexpr int kTcSegBlocks = 64;         // blocks accumulated in one exact segment (sums <= 2^20)
+constexpr uint32_t kSliceA = kTcK * kTcK;              // 4096 bytes: one digit plane of S_b (64 x 64 E4M3)
+constexpr uint32_t kSliceB = kTcN * kTcK;              // 1024 bytes: one digit plane of x^_s (16 x 64 E4M3)
+constexpr uint32_t kTileA = kTcSlices * kSliceA;       // 40960
+constexpr uint32_t kTileB = kTcSlices * kSliceB;       // 10240
+constexpr uint32_t kStage = kTileA + kTileB;           // 51200
+constexpr int kTcStages = 4;
+constexpr int kTcGroups = 5;             // S digit pairs (1,2), (3,4), ..., (9,10)
+// group g pairs S digits 2g+1, 2g+2 with x^ digits 1 .. 10 - 2g (N = 16 (10 - 2g));
+// its accumulators start at tensor-memory column group_col(g): 0, 160, 288, 384, 448
+__host__ __device__ constexpr int group_nx(int g) { return kTcSlices - 2 * g; }
+__host__ __device__ constexpr uint32_t group_col(int g) {   // sum of 16 (10 - 2h) over h < g
+  return (uint32_t)(kTcN * g * (kTcSlices + 1 - g));
+}
+static_assert(group_col(kTcGroups) == 480, "accumulator columns");
+constexpr uint32_t kTmemCols = 512;      // one accumulator set (480 columns used)
 constexpr int kTcThreads = 192;          // producer, MMA, four epilogue warps
 constexpr uint32_t kXch = 64 * kTcN * 8; // epilogue exchange: 64 rows x 16 double-float values
 constexpr uint32_t kBarOff = kTcStages * kStage + kXch;
 constexpr uint32_t kTcSmem = kBarOff + 16 * 8 + 16;
 
-// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
-// A and B BF16 (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 =
-// 0), N / 8 at bits 17-22, M / 16 at bits 24-28
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcNB >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor of tcgen05.mma kind::f8f6f4: D FP32 (bits 4-5 =
+// 1), A and B E4M3 (bits 7-9 = 0, bits 10-12 = 0), both K-major (bits 15, 16
+// = 0), N / 8 at bits 17-22, M / 16 at bits 24-28
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 constexpr double kInv4PiTc = 0.079577471545947667884441881686257181;
 
-// element offset of (row r, contraction index c) in a K-major operand of 64
-// contraction values per row: 8 x 8 core matrices of 16-byte rows
+// byte offset of (row r, contraction index c) in a K-major one-byte operand
+// of 64 contraction values per row: core matrices of 8 rows x 16 bytes, four
+// along K (128 bytes apart), then the next 8 rows (512 bytes on)
 __host__ __device__ __forceinline__ int core_off(int r, int c) {
-  return ((r >> 3) * 8 + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
+  return ((r >> 3) * 4 + (c >> 4)) * 128 + (r & 7) * 16 + (c & 15);
 }
 
 // shared-memory matrix descriptor (no swizzle): start address, leading
-// byte offset 128 (next core matrix along K), stride byte offset 1024 (next
+// byte offset 128 (next core matrix along K), stride byte offset 512 (next
 // 8 rows), descriptor version 1
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
          (1ull << 46);
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -130,11 +141,12 @@ __device__ __forceinline__ void named_sync_id(uint32_t id, uint32_t nthreads) {
 // 2^e as a float for -126 <= e <= 127 (exact; used for power-of-two scaling)
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
-// split X (|X| <= 2^49) into seven signed 7-bit slices, most significant first
-__host__ __device__ __forceinline__ void split7(long long X, int (&s)[kTcSlices]) {
+// split X (|X| <= 2^49) into ten signed 5-bit digits, most significant
+// first: X = sum_i s_i 2^(45 - 5i), each a rounded quotient, |s_i| <= 16
+__host__ __device__ __forceinline__ void split_digits(long long X, int (&s)[kTcSlices]) {
 #pragma unroll
   for (int i = 0; i < kTcSlices; ++i) {
-    const int sh = kTcFixBits - 7 * (i + 1);
+    const int sh = 5 * (kTcSlices - 1 - i);
     const long long q = sh > 0 ? (X + (1LL << (sh - 1))) >> sh : X;
     s[i] = (int)q;
     X -= q * (1LL << sh);
@@ -171,32 +183,37 @@ __global__ void k_tc_rowexp(const int64_t *__restrict__ ptr, const int32_t *__re
   E[t * kTcK + nu] = mx > 0.0 ? ilogb(mx) + 1 : 0;
 }
 
-// the seven BF16 slices of S_b, row nu, contraction indices 8 cg .. 8 cg + 7
+// a digit (|s| <= 16, an integer) as its exact FP8 E4M3 byte
+__device__ __forceinline__ unsigned char e4m3(int s) {
+  return (unsigned char)__nv_cvt_float_to_fp8((float)s, __NV_SATFINITE, __NV_E4M3);
+}
+
+// the ten E4M3 digit planes of S_b, row nu, contraction indices 16 cg .. 16 cg + 15
 __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__restrict__ col,
                              const double *__restrict__ cheb, const int32_t *__restrict__ E, int64_t nblk,
-                             __nv_bfloat16 *__restrict__ Stc) {
+                             unsigned char *__restrict__ Stc) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= nblk * kTcK * 8) return;
-  const int64_t b = e / (kTcK * 8);
-  const int nu = (int)((e / 8) % kTcK), cg = (int)(e % 8);
+  if (e >= nblk * kTcK * 4) return;
+  const int64_t b = e / (kTcK * 4);
+  const int nu = (int)((e / 4) % kTcK), cg = (int)(e % 4);
   const int64_t t = brow[b], s = col[b];
   double x[3], y[3];
   tc_point(cheb, t, nu, x);
   const int sc = kTcFixBits - E[t * kTcK + nu];
-  __nv_bfloat16 out[kTcSlices][8];
+  __align__(16) unsigned char out[kTcSlices][16];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    tc_point(cheb, s, 8 * cg + q, y);
+  for (int q = 0; q < 16; ++q) {
+    tc_point(cheb, s, 16 * cg + q, y);
     const long long X = llrint(ldexp(tc_green(x, y), sc));
     int sl[kTcSlices];
-    split7(X, sl);
+    split_digits(X, sl);
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) out[i][q] = __float2bfloat16_rn((float)sl[i]);
+    for (int i = 0; i < kTcSlices; ++i) out[i][q] = e4m3(sl[i]);
   }
-  __nv_bfloat16 *base = Stc + b * (int64_t)(kTileA / 2) + core_off(nu, 8 * cg);
+  unsigned char *base = Stc + b * (int64_t)kTileA + core_off(nu, 16 * cg);
 #pragma unroll
   for (int i = 0; i < kTcSlices; ++i)
-    *reinterpret_cast<uint4 *>(base + i * (kSliceA / 2)) = *reinterpret_cast<const uint4 *>(out[i]);
+    *reinterpret_cast<uint4 *>(base + i * kSliceA) = *reinterpret_cast<const uint4 *>(out[i]);
 }
 
 // ---------------------------------------------------------------- per product
@@ -233,14 +250,14 @@ __device__ __forceinline__ int tc_colexp(unsigned bits) {
   return bits ? (int)((bits >> 23) & 0xFF) - 127 + 2 : 0;
 }
 
-// The seven BF16 slices of the coefficients of cluster c (x^_c [64][rp]):
-// cut in registers, assembled in shared memory (tile: 7 x 16 x 64 BF16,
-// 14 KB) in the MMA layout (16 columns x 64 contraction values per slice)
-// and written out with 16-byte stores.  All threads of the CTA take part;
-// the caller synchronises before and after.
+// The ten E4M3 digit planes of the coefficients of cluster c (x^_c
+// [64][rp]): cut in registers, assembled in shared memory (tile: 10 x 16 x
+// 64 bytes, 10 KB) in the MMA layout (16 columns x 64 contraction values
+// per plane) and written out with 16-byte stores.  All threads of the CTA
+// take part; the caller synchronises before and after.
 __device__ __forceinline__ void slice_cluster(const dd *__restrict__ xc, int rp, int lvl,
-                                              const unsigned *__restrict__ xmax, __nv_bfloat16 *tile,
-                                              __nv_bfloat16 *__restrict__ dst) {
+                                              const unsigned *__restrict__ xmax, unsigned char *tile,
+                                              unsigned char *__restrict__ dst) {
   for (int e = threadIdx.x; e < kTcN * kTcK; e += blockDim.x) {
     const int mu = e / kTcN, j = e % kTcN;
     long long X = 0;
@@ -250,23 +267,23 @@ __device__ __forceinline__ void slice_cluster(const dd *__restrict__ xc, int rp,
       X = llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
     }
     int sl[kTcSlices];
-    split7(X, sl);
+    split_digits(X, sl);
     const int o = core_off(j, mu);
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) tile[i * kTcN * kTcK + o] = __float2bfloat16_rn((float)sl[i]);
+    for (int i = 0; i < kTcSlices; ++i) tile[i * kSliceB + o] = e4m3(sl[i]);
   }
   __syncthreads();
-  constexpr int kWords = kTcSlices * kTcN * kTcK / 8;   // 16-byte words of the seven slices
+  constexpr int kWords = kTileB / 16;   // 16-byte words of the ten planes
   for (int w = threadIdx.x; w < kWords; w += blockDim.x)
     reinterpret_cast<uint4 *>(dst)[w] = reinterpret_cast<const uint4 *>(tile)[w];
 }
 
 // the slices of clusters [c0, c0 + ncl) of level lvl, one cluster per CTA
 __global__ void __launch_bounds__(256) k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int lvl, int rp,
-                                                    const unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
-  __shared__ __align__(16) __nv_bfloat16 tile[kTcSlices * kTcN * kTcK];
+                                                    const unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
+  __shared__ __align__(16) unsigned char tile[kTileB];
   const int64_t c = c0 + blockIdx.x;
-  slice_cluster(xhat + c * kTcK * rp, rp, lvl, xmax, tile, xtc + c * (int64_t)(kTileB / 2));
+  slice_cluster(xhat + c * kTcK * rp, rp, lvl, xmax, tile, xtc + c * (int64_t)kTileB);
 }
 
 // Upward step for one parent of level l (Algorithm 1, factored transfers,
@@ -274,7 +291,7 @@ __global__ void __launch_bounds__(256) k_tc_slice_x(const dd *__restrict__ xhat,
 // the column maxima of level l from the parent's coefficients, and the
 // slices of its two children (level l + 1, whose maxima are complete).
 __global__ void k_upward_tc(const dd *__restrict__ Ef, int m, int k, int rp, int64_t par0, int lvl,
-                            dd *__restrict__ xhat, unsigned *__restrict__ xmax, __nv_bfloat16 *__restrict__ xtc) {
+                            dd *__restrict__ xhat, unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned loc[kTcN];
   if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
@@ -290,10 +307,10 @@ __global__ void k_upward_tc(const dd *__restrict__ Ef, int m, int k, int rp, int
   __syncthreads();
   if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[lvl * kTcN + threadIdx.x], loc[threadIdx.x]);
   // the children's slices, staged in the (now free) dynamic shared memory
-  __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+  unsigned char *tile = smem_raw;
   for (int ch = 0; ch < 2; ++ch) {
     const int64_t c = 2 * par + 1 + ch;
-    slice_cluster(xhat + c * kr, rp, lvl + 1, xmax, tile, xtc + c * (int64_t)(kTileB / 2));
+    slice_cluster(xhat + c * kr, rp, lvl + 1, xmax, tile, xtc + c * (int64_t)kTileB);
     __syncthreads();
   }
 }
@@ -310,7 +327,7 @@ __device__ __forceinline__ dd dd_scale(dd v, int e) {
 // in [0, nrows); each CTA takes a contiguous range of rows holding about
 // 1/gridDim of the blocks.
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_coupling_tc(const __nv_bfloat16 *__restrict__ Stc, const __nv_bfloat16 *__restrict__ xtc,
+    k_coupling_tc(const unsigned char *__restrict__ Stc, const unsigned char *__restrict__ xtc,
                   const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const int32_t *__restrict__ E,
                   const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, dd *__restrict__ yhat) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -376,12 +393,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (i >= kTcStages && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / kTcStages - 1) & 1), abort)) break;
         unsigned char *st = smem + (size_t)s * kStage;
         mbar_expect_tx(&full[s], kStage);
-        // the coefficient slices first (they may come from L2), then S slice by slice
-        bulk_g2s(st + kTileA, xtc + (int64_t)cb * (kTileB / 2), kTileB, &full[s]);
-        const __nv_bfloat16 *src = Stc + e * (int64_t)(kTileA / 2);
+        // the coefficient digits first (they may come from L2), then S two planes at a time
+        bulk_g2s(st + kTileA, xtc + (int64_t)cb * kTileB, kTileB, &full[s]);
+        const unsigned char *src = Stc + e * (int64_t)kTileA;
 #pragma unroll
-        for (int sl = 0; sl < kTcSlices; ++sl)
-          bulk_g2s(st + sl * kSliceA, src + sl * (kSliceA / 2), kSliceA, &full[s]);
+        for (int g = 0; g < kTcGroups; ++g)
+          bulk_g2s(st + 2 * g * kSliceA, src + 2 * g * kSliceA, 2 * kSliceA, &full[s]);
       }
       if (*abort) {
         // let the copies in flight land before the CTA leaves (bounded)
@@ -419,16 +436,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             tc_fence_after();
             // descriptors of the stage; offsets below 256 KB add to the 14-bit address field.
-            // Group g: S slices 2g+1, 2g+2 (M = 128 rows) times all x^ slices (N = 128);
-            // K steps outermost, so that consecutive MMAs write different accumulators
+            // Group g: S digits 2g+1, 2g+2 (M = 128 rows) times x^ digits 1 .. 10 - 2g;
+            // K steps (32 bytes, two core matrices) outermost, so that consecutive MMAs
+            // write different accumulators
             const uint32_t A0 = smem_u32(smem + (size_t)s * kStage), B0 = A0 + kTileA;
             const uint64_t dA = sdesc(A0), dB = sdesc(B0);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
+            for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
               for (int g = 0; g < kTcGroups; ++g)
-                tc_mma(tbase + (uint32_t)(g * kTcNB), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
-                       dB + (uint64_t)(kk * 16), (t > 0 || kk > 0) ? 1u : 0u);
+                tc_mma(tbase + group_col(g), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
+                       dB + (uint64_t)(kk * 16), tc_idesc(kTcN * group_nx(g)), (t > 0 || kk > 0) ? 1u : 0u);
             tc_commit(&empty[s]);   // the stage is free once these MMAs have read it
           }
           if (ok) tc_commit(accf);
@@ -468,29 +486,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         dd acc[kTcN];
 #pragma unroll
         for (int j = 0; j < kTcN; ++j) acc[j] = dd{0.0f, 0.0f};
-        // lane nu (+ 64) of group g holds S slice i = 2g + 1 (+ 1) times every x^ slice k
-        // (columns 16 (k - 1) .. + 15); the pairs with i + k <= 8 are summed
+        // lane nu (+ 64) of group g holds S digit i = 2g + 1 (+ 1) times x^ digits
+        // k = 1 .. 10 - 2g (columns group_col(g) + 16 (k - 1) .. + 15).  The pairs of
+        // one level L = i + k share the weight 2^(2-5L): their sums (at most five
+        // integers of at most 2^20 each, segments of at most 64 blocks) add exactly in
+        // FP32, and each level enters the double-float result once (L <= 11)
 #pragma unroll 1
-        for (int g = 0; g < kTcGroups; ++g) {
-          const int i = 2 * g + 1 + half;
-          if (i > kTcSlices) continue;   // slice 8 does not exist (whole warp skips)
-          const int kmax = 8 - i;
-#pragma unroll 1
-          for (int k0 = 1; k0 <= kmax; k0 += 4) {
-            uint32_t raw[4][16];
+        for (int L = 2 + half; L <= kTcTop; ++L) {
+          const int ng = min(kTcGroups, (L - 2 - half) / 2 + 1);   // groups with a digit i <= L - 1
+          uint32_t raw[kTcGroups][16];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (k0 + u <= kmax)
-                tmem_ld16_nw(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * kTcNB + (k0 + u - 1) * kTcN), raw[u]);
-            tmem_wait();
+          for (int g = 0; g < kTcGroups; ++g)
+            if (g < ng)
+              tmem_ld16_nw(tbase + ((uint32_t)(quad * 32) << 16) + group_col(g) +
+                               (uint32_t)((L - (2 * g + 1 + half) - 1) * kTcN),
+                           raw[g]);
+          tmem_wait();
+          float fs[kTcN];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if (k0 + u > kmax) break;
-              const float w = pow2f(-7 * (i + k0 + u));   // exact: the sums are integers below 2^24
+          for (int j = 0; j < kTcN; ++j) fs[j] = __uint_as_float(raw[0][j]);
 #pragma unroll
-              for (int j = 0; j < kTcN; ++j) acc[j] = acc[j] + dd{__uint_as_float(raw[u][j]) * w, 0.0f};
-            }
-          }
+          for (int g = 1; g < kTcGroups; ++g)
+            if (g < ng)
+#pragma unroll
+              for (int j = 0; j < kTcN; ++j) fs[j] += __uint_as_float(raw[g][j]);
+          const float w = pow2f(2 - 5 * L);
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) acc[j] = acc[j] + dd{fs[j] * w, 0.0f};
         }
         tc_fence_before();
         __syncwarp();
@@ -540,9 +562,9 @@ int tc_build(Ctx &c, const int32_t *arow_dev) {
   H2_CUDA_TRY(cudaMemsetAsync(d.xtc, 0, (size_t)d.nclu * kTileB, st));
   const int64_t nr = (d.nclu - row0) * kTcK;
   k_tc_rowexp<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(d.adm_ptr, d.adm_col, d.cheb, row0, d.nclu, d.tc_E);
-  const int64_t ns = d.nadm * kTcK * 8;
+  const int64_t ns = d.nadm * kTcK * 4;
   k_tc_slice_s<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(arow_dev, d.adm_col, d.cheb, d.tc_E, d.nadm,
-                                                             (__nv_bfloat16 *)d.Stc);
+                                                             (unsigned char *)d.Stc);
   H2_CUDA_TRY(cudaGetLastError());
   H2_CUDA_TRY(cudaStreamSynchronize(st));
   d.tc = true;
@@ -573,13 +595,13 @@ int tc_upward(Ctx &c, void *xhat_v, int rp, int64_t *launches) {
   for (int l = D - 1; l >= lmin; --l) {
     const int64_t par0 = ((int64_t)1 << l) - 1;
     k_upward_tc<<<(unsigned)((int64_t)1 << l), 256, sm, st>>>((const dd *)d.Ef, m, k, rp, par0, l, xhat, d.tc_xmax,
-                                                                (__nv_bfloat16 *)d.xtc);
+                                                                (unsigned char *)d.xtc);
     ++nl;
   }
   // the top level's slices (the leaves' when there is no transfer)
   const int64_t c0 = ((int64_t)1 << lmin) - 1;
   k_tc_slice_x<<<(unsigned)((int64_t)1 << lmin), 256, 0, st>>>(xhat, c0, lmin, rp, d.tc_xmax,
-                                                                (__nv_bfloat16 *)d.xtc);
+                                                                (unsigned char *)d.xtc);
   ++nl;
   H2_CUDA_TRY(cudaGetLastError());
   if (launches) *launches = nl;
@@ -602,7 +624,7 @@ int tc_coupling(Ctx &c, const void *xhat_v, void *yhat_v, int rp) {
   H2_CUDA_TRY(cudaGetDevice(&dev));
   H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = (int)std::min<int64_t>(sms, nrows);
-  k_coupling_tc<<<grid, kTcThreads, kTcSmem, st>>>((const __nv_bfloat16 *)d.Stc, (const __nv_bfloat16 *)d.xtc,
+  k_coupling_tc<<<grid, kTcThreads, kTcSmem, st>>>((const unsigned char *)d.Stc, (const unsigned char *)d.xtc,
                                                    d.adm_ptr, d.adm_col, d.tc_E, d.tc_xmax, row0, nrows, rp, yhat);
   H2_CUDA_TRY(cudaGetLastError());
   return H2_OK;

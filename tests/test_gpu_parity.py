@@ -261,7 +261,7 @@ def _oracle_any(name):
 
 @pytest.mark.parametrize("name", ["ico3_m4", "ell3_m4", "cube30_m4"])
 def test_f64_tensor_core_coupling(require_gpu, name):
-    """FP64-accurate coupling from 7-bit BF16 slices on the tensor cores (order 4,
+    """FP64-accurate coupling from 5-bit FP8 E4M3 digits on the tensor cores (order 4,
     up to 16 right-hand sides; more fall back to the double-float coupling):
     against the oracle and the double-float path, and bit-reproducible."""
     import torch

@@ -248,6 +248,23 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t1)
     e2e_s = statistics.median(e2e_times)
 
+    # the same product replayed from a CUDA graph: median of per-replay CUDA-event pairs
+    g = h.graph(x, y)
+    for _ in range(3):
+        g.launch()
+    torch.cuda.synchronize()
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(max(20, args.steps))]
+    for a, b in gev:
+        a.record(stream)
+        g.launch()
+        b.record(stream)
+    torch.cuda.synchronize()
+    gms = sorted(a.elapsed_time(b) for a, b in gev)
+    graph = {"replays": len(gms), "median_ms": gms[len(gms) // 2], "min_ms": gms[0], "max_ms": gms[-1],
+             "median_dof_per_s": n * nrhs / (gms[len(gms) // 2] * 1e-3)}
+    g.close()
+
     # parity spot check of this very run against the stored oracle rows is
     # done by the tests; here only a sanity check that the output is finite
     finite = bool(torch.isfinite(y).all().item())
@@ -336,6 +353,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (stored representation %.2f GB)" % (st["device_bytes"] / 1e9)},
         "roofline": roof,
         "phases_ms": {k: v[0] / products for k, v in phases.items()},
+        "graph": graph,
         "gpu_launches": int(launches),
         "e2e": {"value": n * nrhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(8 * n * nrhs),
                 "d2h_bytes_per_step": int(8 * n * nrhs)},

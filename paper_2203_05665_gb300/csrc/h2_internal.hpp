@@ -158,6 +158,11 @@ int ensure_work(Ctx &c, int nrhs);
 int device_build(Ctx &c);
 // y = G~ x with device arrays of the handle's precision (h2_matvec.cu);
 // if x64/y64 are given instead the product reads/writes FP64 arrays.
+// Threads per CTA of a transfer launch (one CTA per parent) at tree level l:
+// the wide levels (1024 parents and more) take 128 threads, so that more CTAs
+// stay resident per SM to hide the global-memory latency of each parent's
+// step; the narrow top levels keep 256 to shorten each CTA.
+inline int transfer_threads(int l) { return l >= 10 ? 128 : 256; }
 int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64);
 // GMRES (h2_solve.cu); b, z device FP64 arrays
 int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,

@@ -749,7 +749,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     if ((rc = set_smem<T>((const void *)k_upward<TE, T>, sm))) return rc;
     for (int l = D - 1; l >= lmin; --l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
-      k_upward<TE, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TE *)d.Ef, m, k, rp, par0, xhat);
+      k_upward<TE, T><<<(unsigned)((int64_t)1 << l), transfer_threads(l), sm, st>>>((const TE *)d.Ef, m, k, rp, par0,
+                                                                                   xhat);
       mk.count(H2_PH_UPWARD);
     }
   }
@@ -792,7 +793,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     if ((rc = set_smem<T>((const void *)k_downward<TE, T>, sm))) return rc;
     for (int l = lmin; l < D; ++l) {
       int64_t par0 = ((int64_t)1 << l) - 1;
-      k_downward<TE, T><<<(unsigned)((int64_t)1 << l), kThreads, sm, st>>>((const TE *)d.Ef, m, k, rp, par0, yhat);
+      k_downward<TE, T><<<(unsigned)((int64_t)1 << l), transfer_threads(l), sm, st>>>((const TE *)d.Ef, m, k, rp,
+                                                                                     par0, yhat);
       mk.count(H2_PH_DOWNWARD);
     }
   }

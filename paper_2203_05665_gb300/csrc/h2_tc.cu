@@ -594,7 +594,7 @@ int tc_upward(Ctx &c, void *xhat_v, int rp, int64_t *launches) {
   const size_t sm = std::max<size_t>(((size_t)3 * k * rp + 6 * m * m) * sizeof(dd), kTileB);
   for (int l = D - 1; l >= lmin; --l) {
     const int64_t par0 = ((int64_t)1 << l) - 1;
-    k_upward_tc<<<(unsigned)((int64_t)1 << l), 256, sm, st>>>((const dd *)d.Ef, m, k, rp, par0, l, xhat, d.tc_xmax,
+    k_upward_tc<<<(unsigned)((int64_t)1 << l), transfer_threads(l), sm, st>>>((const dd *)d.Ef, m, k, rp, par0, l, xhat, d.tc_xmax,
                                                                 (unsigned char *)d.xtc);
     ++nl;
   }

@@ -81,7 +81,9 @@ typedef struct h2_options {
                       * entry, a power of two per row) and runs the coupling phase of products with
                       * up to 16 right-hand sides on the tensor cores (integer digit products summed
                       * exactly, combined in double-float; agrees with the double-float path to
-                      * about 1e-13); 1: never */
+                      * about 1e-13); likewise any H2_F64 handle with leaves of at most 21
+                      * triangles keeps its nearfield blocks as such digits and runs the
+                      * nearfield phase on the tensor cores; 1: never */
   int reserved[6];   /* must be zero */
 } h2_options;
 
@@ -100,7 +102,8 @@ typedef struct h2_stats {
   int64_t device_bytes;   /* device memory held by the handle (without work buffers) */
   int64_t prec;           /* enum h2_prec */
   int64_t coupling;       /* H2_COUPLING_STORED or H2_COUPLING_REGEN as built */
-  int64_t tensor;         /* 1 if the tensor-core slices of the coupling were built */
+  int64_t tensor;         /* 1 if the tensor-core digits of the coupling were built */
+  int64_t tensor_near;    /* 1 if the tensor-core digits of the nearfield were built */
 } h2_stats;
 
 /* Per right-hand side result of h2_solve. */

@@ -37,7 +37,8 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("n", "depth", "clusters", "leaf_max", "order", "rank", "adm_blocks", "near_blocks",
-                 "near_entries", "first_adm_level", "device_bytes", "prec", "coupling", "tensor")]
+                 "near_entries", "first_adm_level", "device_bytes", "prec", "coupling", "tensor",
+                 "tensor_near")]
 
 
 class SolveInfo(C.Structure):

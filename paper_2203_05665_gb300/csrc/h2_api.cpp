@@ -26,7 +26,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 static void free_dev(Dev &d) {
-  void *ptrs[] = {d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
+  void *ptrs[] = {d.Ntc, d.xnt, d.ntc_E, d.ntc_xmax, d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
                   d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -206,6 +206,7 @@ int h2_info(h2_handle h, h2_stats *out) {
   out->prec = h->d.prec;
   out->coupling = h->d.coupling == 1 ? H2_COUPLING_REGEN : H2_COUPLING_STORED;
   out->tensor = h->d.tc ? 1 : 0;
+  out->tensor_near = h->d.ntc ? 1 : 0;
   return H2_OK;
 }
 

@@ -89,6 +89,16 @@ struct Dev {
   void *Stc = nullptr, *xtc = nullptr;
   int32_t *tc_E = nullptr;
   unsigned *tc_xmax = nullptr;
+  // FP64-accurate nearfield on the tensor cores (leaves of at most 21
+  // triangles): the digit planes of every near block (ntc_ablk bytes each,
+  // two stacked groups of K-major rows), the row exponents ([nleaf][lmax]),
+  // the digit planes of the permuted input of one product ([nleaf][10][16 x
+  // 32]) and its column maxima ([16])
+  bool ntc = false;
+  void *Ntc = nullptr, *xnt = nullptr;
+  int32_t *ntc_E = nullptr;
+  unsigned *ntc_xmax = nullptr;
+  uint32_t ntc_ablk = 0;
   float *vscale = nullptr;      // per leaf: power of two dividing the stored V (FP16), or NULL
   float *nscale = nullptr;      // per nearfield block: the same for G_b, or NULL
   // work buffers for up to cap_nrhs right-hand sides
@@ -149,6 +159,9 @@ int tc_build(Ctx &c, const int32_t *arow_dev);
 int tc_upward(Ctx &c, void *xhat, int rp, int64_t *launches);
 int tc_coupling(Ctx &c, const void *xhat, void *yhat, int rp);
 int tc_take_error(cudaStream_t st);
+bool ntc_eligible(const Dev &d);
+int ntc_build(Ctx &c, const int32_t *nrow_dev);
+int ntc_near(Ctx &c, const void *xpad, void *ypad, int rp, int accumulate, int64_t *launches);
 
 // device allocation helper (tracks bytes)
 int dev_alloc(Dev &d, void **ptr, size_t bytes);

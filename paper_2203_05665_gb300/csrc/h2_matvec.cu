@@ -804,7 +804,12 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     if ((rc = launch_rows<TS, T>(rows, cf_back, t_back, RL, d.nleaf, 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
-  {
+  if (std::is_same<T, dd>::value && d.ntc && rp <= 16) {
+    // FP64-accurate: integer digits on the tensor cores
+    int64_t nl = 0;
+    if ((rc = ntc_near(c, xpad, ypad, rp, far ? 1 : 0, &nl))) return rc;
+    mk.count(H2_PH_LEAF_NEAR, nl);
+  } else {
     NearRows<TS, T> rows{(const TS *)d.near, d.near_ptr, d.near_col, xpad, nscale, L, Lp, rp};
     if ((rc = launch_rows<TS, T>(rows, cf_near, t_near, RL, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
@@ -831,7 +836,7 @@ int take_device_error(Ctx &c) {
     H2_CUDA_TRY(cudaStreamSynchronize(c.stream));
     return fail(H2_ETIMEOUT, "a bounded device wait ran out; the last result is not valid");
   }
-  return c.d.tc ? tc_take_error(c.stream) : H2_OK;
+  return (c.d.tc || c.d.ntc) ? tc_take_error(c.stream) : H2_OK;
 }
 
 int ensure_work(Ctx &c, int nrhs_req) {

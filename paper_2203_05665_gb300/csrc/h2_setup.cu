@@ -482,6 +482,8 @@ int build_typed(Ctx &c) {
       H2_CUDA_TRY(cudaGetLastError());
     }
   }
+  // FP64-accurate handles with leaves of at most 21 triangles: the nearfield digits for the tensor cores
+  if (ntc_eligible(d) && (rc = ntc_build(c, (const int32_t *)t_nrow.ptr))) return rc;
   H2_CUDA_TRY(cudaStreamSynchronize(st));
   return H2_OK;
 }

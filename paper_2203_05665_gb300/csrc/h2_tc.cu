@@ -134,6 +134,26 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) 
 }
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Column indices of the blocks a producer streams, loaded 8 blocks ahead so
+// that the address of a bulk copy never waits on a global load.
+struct ColAhead {
+  const int32_t *col;
+  int64_t end;
+  int32_t c[8];
+  __device__ __forceinline__ ColAhead(const int32_t *cl, int64_t e0, int64_t e1) : col(cl), end(e1) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = e0 + u < e1 ? col[e0 + u] : 0;
+  }
+  // the column of block e; afterwards block e + 8 is in flight
+  __device__ __forceinline__ int32_t next(int64_t e) {
+    const int32_t v = c[0];
+#pragma unroll
+    for (int u = 0; u < 7; ++u) c[u] = c[u + 1];
+    c[7] = e + 8 < end ? col[e + 8] : 0;
+    return v;
+  }
+};
+
 __device__ __forceinline__ void named_sync_id(uint32_t id, uint32_t nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -219,18 +239,16 @@ __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__
 // ---------------------------------------------------------------- per product
 __device__ __forceinline__ int tc_level(int64_t c) { return 63 - __clzll(c + 1); }
 
-// xmax[lvl][j] = largest |hi| of column j over clusters [c0, c0 + ncl) of level lvl (as float bits)
-__global__ void k_tc_levmax(const dd *__restrict__ xhat, int64_t c0, int64_t ncl, int lvl, int rp,
-                            unsigned *__restrict__ xmax) {
+// xmax[j] = largest |hi| of column j over rows [0, rows) of x ([rows][rp], as float bits)
+__global__ void k_tc_levmax(const dd *__restrict__ x, int64_t rows, int rp, unsigned *__restrict__ xmax) {
   __shared__ unsigned loc[kTcN];
   if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
   __syncthreads();
-  const int64_t rows = ncl * kTcK;
   float mx[kTcN];
 #pragma unroll
   for (int j = 0; j < kTcN; ++j) mx[j] = 0.0f;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-    const dd *row = xhat + (c0 * kTcK + r) * rp;
+    const dd *row = x + r * rp;
 #pragma unroll
     for (int j = 0; j < kTcN; ++j)
       if (j < rp) mx[j] = fmaxf(mx[j], fabsf(row[j].hi));
@@ -242,7 +260,7 @@ __global__ void k_tc_levmax(const dd *__restrict__ xhat, int64_t c0, int64_t ncl
     if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&loc[j], __float_as_uint(v));
   }
   __syncthreads();
-  if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[lvl * kTcN + threadIdx.x], loc[threadIdx.x]);
+  if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[threadIdx.x], loc[threadIdx.x]);
 }
 
 // F = 2 + floor(log2 max): |hi + lo| < 2^(F-1)
@@ -384,12 +402,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---------------- producer: the slices of every block of the range
     if (lane == 0) {
       int64_t e = e_begin;
-      int32_t cn = e < e_end ? col[e] : 0;   // column of the next block, loaded one block ahead
+      ColAhead ca(col, e, e_end);
       for (; e < e_end; ++e) {
         const int64_t i = e - e_begin;
         const int s = (int)(i % kTcStages);
-        const int32_t cb = cn;
-        if (e + 1 < e_end) cn = col[e + 1];
+        const int32_t cb = ca.next(e);
         if (i >= kTcStages && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / kTcStages - 1) & 1), abort)) break;
         unsigned char *st = smem + (size_t)s * kStage;
         mbar_expect_tx(&full[s], kStage);
@@ -519,13 +536,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (lane == 0) mbar_arrive(acce);
         if (half == 1)
 #pragma unroll
-          for (int j = 0; j < kTcN; ++j) xch[nu * kTcN + j] = acc[j];
+          for (int j = 0; j < kTcN; ++j) xch[j * 64 + nu] = acc[j];   // consecutive lanes, consecutive words
         named_sync_id(2, 128);
         if (half == 0) {
 #pragma unroll
           for (int j = 0; j < kTcN; ++j) {
             if (j >= rp) break;
-            dd v = dd_scale(acc[j] + xch[nu * kTcN + j], Fc[j]);
+            dd v = dd_scale(acc[j] + xch[j * 64 + nu], Fc[j]);
             if (s0 > 0) v = v + yrow[j];
             yrow[j] = v;
           }
@@ -543,6 +560,368 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
 }
 
+
+// ---------------------------------------------------------------- nearfield
+// The nearfield phase (Algorithm 3 over the inadmissible leaf pairs,
+// y|t += G_ts x|s) with the same exact digit products: every row nu of leaf
+// t gets a power of two 2^E over its near blocks, every column j of the
+// permuted input x a power of two 2^F over all leaves, and both sides are
+// cut into the ten E4M3 digits above.  A block G_ts is L x L (L <= 21
+// triangles per leaf); its contraction index (the triangles of s) is padded
+// with zeros to K = 32 bytes, one MMA K step.  The digit planes of a block
+// are stacked along M: digits 1-6 in rows (i - 1) L + nu of the first
+// 128-row group, digits 7-10 in rows (i - 7) L + nu of the second; the
+// input digits of leaf s are the N side (16 columns per plane).  Two MMAs
+// per block: group 1 against input digits 1-10 (N = 160), group 2 against
+// input digits 1-4 (N = 64), so every pair with i + k <= 11 is formed.  Two
+// accumulator sets of 224 columns let the epilogue of one row run while the
+// MMAs of the next fill the other set.  Rows longer than 32 blocks are cut
+// into segments: a sum D_ik then stays below 32 x 21 x 2^8 < 2^17.4, so two
+// neighbouring input digits combine exactly in FP32 (32 D_ik + D_i,k+1 <
+// 2^23) before entering double-float.
+constexpr int kNtLmax = 21;                      // six planes of 21 rows fit in 128
+constexpr int kNtPlanes1 = 6;                    // digits 1-6 in the first group, 7-10 in the second
+constexpr uint32_t kNtRowB = 32;                 // bytes per operand row (K = 32)
+constexpr uint32_t kNtG1 = 128 * kNtRowB;        // 4096: the first group of a block
+// the A region of a stage holds the stored block (at most 4096 + 88 x 32 bytes); the
+// second MMA reads 128 rows from 4096 on, i.e. past the block's 4 L rows into the
+// input digits that follow (or the next stage, or the exchange area after the last
+// stage): rows whose accumulators the epilogue never reads
+constexpr uint32_t kNtAreg = kNtG1 + 88 * kNtRowB;      // 6912
+constexpr uint32_t kNtX = kTcSlices * kTcN * kNtRowB;   // 5120: the input digits of one leaf
+constexpr uint32_t kNtStage = kNtAreg + kNtX;           // 12032
+constexpr int kNtStages = 16;
+constexpr int kNtSeg = 32;                       // blocks per exact segment
+constexpr int kNtN1 = kTcSlices * kTcN;          // 160
+constexpr int kNtN2 = 4 * kTcN;                  // 64
+constexpr uint32_t kNtSet = 256;                 // tensor-memory columns per accumulator set
+constexpr uint32_t kNtXch = kTcSlices * kNtLmax * kTcN * 8;   // 26880: [digit][nu][j] double-float
+constexpr uint32_t kNtBarOff = kNtStages * kNtStage + kNtXch;
+constexpr uint32_t kNtSmem = kNtBarOff + 512;
+static_assert(kNtSmem <= 227 * 1024, "nearfield tensor-core kernel does not fit in shared memory");
+
+// byte offset of (row r, contraction index c) in a K-major one-byte operand
+// of 32 contraction values per row: two core matrices along K (128 bytes
+// apart), then the next 8 rows (256 bytes on)
+__host__ __device__ __forceinline__ int core_off32(int r, int c) {
+  return ((r >> 3) * 2 + (c >> 4)) * 128 + (r & 7) * 16 + (c & 15);
+}
+__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
+         (1ull << 46);
+}
+
+// bytes of the stored digits of one block: group 1 (128 rows) and the 4 L rows of group 2
+__host__ __device__ __forceinline__ uint32_t ntc_block_bytes(int L) {
+  return kNtG1 + (uint32_t)((4 * L + 7) / 8 * 8) * kNtRowB;
+}
+
+// E[t][nu] = 1 + floor(log2 max |G_b[nu][mu]|) over the near blocks b of leaf row t (0 if none)
+__global__ void k_ntc_rowexp(const dd *__restrict__ near, const int64_t *__restrict__ ptr, int64_t nleaf, int L,
+                             int Lp, int32_t *__restrict__ E) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nleaf * L) return;
+  const int64_t t = e / L;
+  const int nu = (int)(e % L);
+  float mx = 0.0f;
+  for (int64_t b = ptr[t]; b < ptr[t + 1]; ++b)
+    for (int mu = 0; mu < L; ++mu) mx = fmaxf(mx, fabsf(near[(b * L + mu) * Lp + nu].hi));
+  E[e] = mx > 0.0f ? ilogbf(mx) + 1 : 0;
+}
+
+// the ten digit planes of block b, row nu, contraction indices 16 cg .. 16 cg + 15
+__global__ void k_ntc_slice(const dd *__restrict__ near, const int32_t *__restrict__ brow,
+                            const int32_t *__restrict__ E, int64_t nnear, int L, int Lp, uint32_t ablk,
+                            unsigned char *__restrict__ Ntc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnear * L * 2) return;
+  const int64_t b = e / (2 * L);
+  const int nu = (int)((e / 2) % L), cg = (int)(e % 2);
+  const int sc = kTcFixBits - E[(int64_t)brow[b] * L + nu];
+  __align__(16) unsigned char out[kTcSlices][16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int mu = 16 * cg + q;
+    long long X = 0;
+    if (mu < L) {
+      const dd v = near[(b * L + mu) * Lp + nu];
+      X = llrint(ldexp((double)v.hi + (double)v.lo, sc));
+    }
+    int sl[kTcSlices];
+    split_digits(X, sl);
+#pragma unroll
+    for (int i = 0; i < kTcSlices; ++i) out[i][q] = e4m3(sl[i]);
+  }
+  unsigned char *base = Ntc + b * (int64_t)ablk;
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i) {
+    const int r = i < kNtPlanes1 ? i * L + nu : (i - kNtPlanes1) * L + nu;
+    const uint32_t g = i < kNtPlanes1 ? 0u : kNtG1;
+    *reinterpret_cast<uint4 *>(base + g + core_off32(r, 16 * cg)) = *reinterpret_cast<const uint4 *>(out[i]);
+  }
+}
+
+// the digit planes of the input of leaf s (x_pad rows s L .. s L + L - 1): 16 rows j x 32 bytes each
+__global__ void __launch_bounds__(128) k_ntc_slice_x(const dd *__restrict__ xpad, int L, int rp,
+                                                     const unsigned *__restrict__ xmax,
+                                                     unsigned char *__restrict__ xnt) {
+  __shared__ __align__(16) unsigned char tile[kNtX];
+  const int64_t s = blockIdx.x;
+  for (int e = threadIdx.x; e < kTcN * 32; e += blockDim.x) {
+    const int j = e & (kTcN - 1), mu = e >> 4;
+    long long X = 0;
+    if (mu < L && j < rp) {
+      const int sc = kTcFixBits - tc_colexp(xmax[j]);
+      const dd v = xpad[(s * L + mu) * rp + j];
+      X = llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
+    }
+    int sl[kTcSlices];
+    split_digits(X, sl);
+    const int o = core_off32(j, mu);
+#pragma unroll
+    for (int i = 0; i < kTcSlices; ++i) tile[i * (kTcN * kNtRowB) + o] = e4m3(sl[i]);
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < (int)(kNtX / 16); w += blockDim.x)
+    reinterpret_cast<uint4 *>(xnt + s * (int64_t)kNtX)[w] = reinterpret_cast<const uint4 *>(tile)[w];
+}
+
+// The nearfield kernel: rows t in [0, nrows) (leaves), each CTA a contiguous
+// range of rows holding about 1/gridDim of the blocks; roles as in
+// k_coupling_tc (producer warp, MMA warp, four epilogue warps).
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_near_tc(const unsigned char *__restrict__ Ntc, uint32_t ablk, const unsigned char *__restrict__ xnt,
+              const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const int32_t *__restrict__ E,
+              const unsigned *__restrict__ xmax, int64_t nrows, int L, int rp, int accumulate,
+              dd *__restrict__ ypad) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  dd *xch = reinterpret_cast<dd *>(smem + kNtStages * kNtStage);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kNtBarOff);
+  uint64_t *empty = full + kNtStages;
+  uint64_t *accf = empty + kNtStages;   // [2]
+  uint64_t *acce = accf + 2;            // [2]
+  uint64_t *done = acce + 2;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
+  int *fexp = reinterpret_cast<int *>(smem + kNtBarOff + 320);   // column exponents F_j
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < kTcN) fexp[tid] = tc_colexp(xmax[tid]);
+
+  const int64_t total = ptr[nrows];
+  auto row_at = [&](int64_t w) -> int64_t {
+    if (w >= (int64_t)gridDim.x) return nrows;
+    const int64_t target = total * w / gridDim.x;
+    int64_t lo = 0, hi = nrows;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (ptr[mid] >= target) hi = mid;
+      else lo = mid + 1;
+    }
+    return lo;
+  };
+  const int64_t r_begin = blockIdx.x == 0 ? 0 : row_at(blockIdx.x);
+  const int64_t r_end = row_at(blockIdx.x + 1);
+  const int64_t e_begin = ptr[r_begin], e_end = ptr[r_end];
+
+  if (tid == 0) {
+    for (int s = 0; s < kNtStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&accf[s], 1);
+      mbar_init(&acce[s], 4);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 0) {
+    // ---------------- producer: the digits of every block of the range and of its column leaf
+    if (lane == 0) {
+      int64_t e = e_begin;
+      ColAhead ca(col, e, e_end);
+      for (; e < e_end; ++e) {
+        const int64_t i = e - e_begin;
+        const int s = (int)(i % kNtStages);
+        const int32_t cb = ca.next(e);
+        if (i >= kNtStages && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / kNtStages - 1) & 1), abort)) break;
+        unsigned char *st = smem + (size_t)s * kNtStage;
+        mbar_expect_tx(&full[s], ablk + kNtX);
+        bulk_g2s(st + kNtAreg, xnt + (int64_t)cb * kNtX, kNtX, &full[s]);
+        bulk_g2s(st, Ntc + e * (int64_t)ablk, ablk, &full[s]);
+      }
+      if (*abort) {
+        const int64_t j0 = e - kNtStages > e_begin ? e - kNtStages : e_begin;
+        for (int64_t j = j0; j < e; ++j) {
+          const int64_t ij = j - e_begin;
+          mbar_wait_bounded(&full[ij % kNtStages], (uint32_t)((ij / kNtStages) & 1));
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int64_t i = 0, q = 0;
+      bool ok = true;
+      int64_t pnext = ptr[r_begin];   // row pointers loaded one row ahead
+      for (int64_t r = r_begin; r < r_end && ok; ++r) {
+        const int64_t b0 = pnext;
+        pnext = ptr[r + 1];
+        const int64_t nb = pnext - b0;
+        for (int64_t s0 = 0; s0 < nb && ok; s0 += kNtSeg, ++q) {
+          const uint32_t set = (uint32_t)(q & 1);
+          // this set is free once the epilogue has read the segment before last
+          if (q >= 2 && !mbar_wait_or_abort(&acce[set], (uint32_t)(((q - 2) >> 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int64_t sn = nb - s0 < kNtSeg ? nb - s0 : kNtSeg;
+          for (int64_t t = 0; t < sn; ++t, ++i) {
+            const int s = (int)(i % kNtStages);
+            if (!mbar_wait_or_abort(&full[s], (uint32_t)((i / kNtStages) & 1), abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t A0 = smem_u32(smem + (size_t)s * kNtStage), B0 = A0 + kNtAreg;
+            const uint64_t dA = sdesc32(A0), dB = sdesc32(B0);
+            const uint32_t acc = t > 0 ? 1u : 0u;
+            tc_mma(tbase + set * kNtSet, dA, dB, tc_idesc(kNtN1), acc);
+            tc_mma(tbase + set * kNtSet + (uint32_t)kNtN1, dA + (uint64_t)(kNtG1 >> 4), dB, tc_idesc(kNtN2), acc);
+            tc_commit(&empty[s]);
+          }
+          if (ok) tc_commit(&accf[set]);
+        }
+      }
+      tc_commit(done);
+      mbar_wait_bounded(done, 0);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 2-5 read tensor-memory lanes 32 (warp % 4) ..
+    const int quad = warp & 3, tl = quad * 32 + lane;
+    const bool v1 = tl < kNtPlanes1 * L, v2 = tl < (kTcSlices - kNtPlanes1) * L;
+    const int i1 = tl / L + 1, i2 = tl / L + 1 + kNtPlanes1, nu = tl % L;   // digit and row of this lane
+    const int km1 = v1 ? kTcTop - i1 : 0, km2 = v2 ? kTcTop - i2 : 0;       // input digits paired with it
+    const int km1w = __reduce_max_sync(0xffffffffu, km1), km2w = __reduce_max_sync(0xffffffffu, km2);
+    const uint32_t lrow = (uint32_t)(quad * 32) << 16;
+    int64_t q = 0;
+    int64_t pnext = ptr[r_begin];
+    for (int64_t r = r_begin; r < r_end; ++r) {
+      const int64_t b0 = pnext;
+      pnext = ptr[r + 1];
+      const int64_t nb = pnext - b0;
+      dd *yrow = ypad + r * (int64_t)L * rp;
+      if (nb == 0) {
+        if (!accumulate)
+          for (int o = tl; o < L * rp; o += 128) yrow[o] = dd{0.0f, 0.0f};
+        continue;
+      }
+      bool stop = false;
+      for (int64_t s0 = 0; s0 < nb; s0 += kNtSeg, ++q) {
+        const uint32_t set = (uint32_t)(q & 1);
+        // this thread's outputs o = tl + 128 u: row o % L, column o / L; their row
+        // exponents and previous values are loaded before the wait
+        int eo[3];
+        dd yold[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int o = tl + 128 * u, rn = o % L, j = o / L;
+          eo[u] = 0;
+          yold[u] = dd{0.0f, 0.0f};
+          if (o < L * kTcN && j < rp) {
+            eo[u] = E[r * L + rn] + fexp[j];
+            if (s0 > 0 || accumulate) yold[u] = yrow[rn * rp + j];
+          }
+        }
+        const bool ready = !*abort && mbar_wait_or_abort(&accf[set], (uint32_t)((q >> 1) & 1), abort);
+        if (named_sync_or(128, ready ? 0 : 1)) {
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        dd p1[kTcN], p2[kTcN];
+#pragma unroll
+        for (int j = 0; j < kTcN; ++j) p1[j] = p2[j] = dd{0.0f, 0.0f};
+        // group 1: input digits k, k + 1 combined exactly, weight 2^(2 - 5 (i + k + 1))
+#pragma unroll 1
+        for (int k = 1; k <= km1w; k += 2) {
+          uint32_t ra[16], rb[16];
+          tmem_ld16_nw(tbase + lrow + set * kNtSet + (uint32_t)((k - 1) * kTcN), ra);
+          if (k + 1 <= km1w) tmem_ld16_nw(tbase + lrow + set * kNtSet + (uint32_t)(k * kTcN), rb);
+          tmem_wait();
+          const float ca = k <= km1 ? 32.0f : 0.0f, cb = k + 1 <= km1 ? 1.0f : 0.0f;
+          const float w = pow2f(2 - 5 * (i1 + k + 1));
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) {
+            const float v = ca * __uint_as_float(ra[j]) + (k + 1 <= km1w ? cb * __uint_as_float(rb[j]) : 0.0f);
+            p1[j] = p1[j] + dd{v * w, 0.0f};
+          }
+        }
+        // group 2: digits 7-10 against input digits 1-4
+#pragma unroll 1
+        for (int k = 1; k <= km2w; k += 2) {
+          uint32_t ra[16], rb[16];
+          tmem_ld16_nw(tbase + lrow + set * kNtSet + (uint32_t)(kNtN1 + (k - 1) * kTcN), ra);
+          if (k + 1 <= km2w) tmem_ld16_nw(tbase + lrow + set * kNtSet + (uint32_t)(kNtN1 + k * kTcN), rb);
+          tmem_wait();
+          const float ca = k <= km2 ? 32.0f : 0.0f, cb = k + 1 <= km2 ? 1.0f : 0.0f;
+          const float w = pow2f(2 - 5 * (i2 + k + 1));
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) {
+            const float v = ca * __uint_as_float(ra[j]) + (k + 1 <= km2w ? cb * __uint_as_float(rb[j]) : 0.0f);
+            p2[j] = p2[j] + dd{v * w, 0.0f};
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[set]);
+        // exchange [j][digit][row]: consecutive lanes write consecutive words
+        const int dl = kTcSlices * L;
+        if (v1)
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) xch[j * dl + (i1 - 1) * L + nu] = p1[j];
+        if (v2)
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) xch[j * dl + (i2 - 1) * L + nu] = p2[j];
+        named_sync_id(2, 128);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int o = tl + 128 * u, rn = o % L, j = o / L;
+          if (o >= L * kTcN || j >= rp) continue;
+          const dd *xc = xch + j * dl + rn;
+          dd v = xc[0];
+#pragma unroll
+          for (int i = 1; i < kTcSlices; ++i) v = v + xc[i * L];
+          v = dd_scale(v, eo[u]);
+          if (s0 > 0 || accumulate) v = v + yold[u];
+          yrow[rn * rp + j] = v;
+        }
+        named_sync_id(2, 128);
+      }
+      if (stop) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+}
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -587,7 +966,7 @@ int tc_upward(Ctx &c, void *xhat_v, int rp, int64_t *launches) {
   H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
   const int64_t lrows = d.nleaf * kTcK;
   k_tc_levmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((lrows + 255) / 256, 152 * 8)), 256, 0, st>>>(
-      xhat, leaf0, d.nleaf, D, rp, d.tc_xmax);
+      xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
   ++nl;
   const int k = d.k, m = d.m;
   // k = 64, rp <= 16: at most 25,344 bytes, below the 48 KB default limit
@@ -627,6 +1006,64 @@ int tc_coupling(Ctx &c, const void *xhat_v, void *yhat_v, int rp) {
   k_coupling_tc<<<grid, kTcThreads, kTcSmem, st>>>((const unsigned char *)d.Stc, (const unsigned char *)d.xtc,
                                                    d.adm_ptr, d.adm_col, d.tc_E, d.tc_xmax, row0, nrows, rp, yhat);
   H2_CUDA_TRY(cudaGetLastError());
+  return H2_OK;
+}
+
+// ---------------------------------------------------------------- nearfield host side
+bool ntc_eligible(const Dev &d) {
+  return d.prec == H2_F64 && d.tensor == 0 && d.lmax <= kNtLmax && d.nnear > 0;
+}
+
+int ntc_build(Ctx &c, const int32_t *nrow_dev) {
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  if (!ntc_eligible(d)) return H2_OK;
+  const int L = (int)d.lmax, Lp = (int)d.lp;
+  const uint32_t ablk = ntc_block_bytes(L);
+  int rc;
+  if ((rc = dev_alloc(d, (void **)&d.ntc_E, sizeof(int32_t) * (size_t)d.nleaf * L))) return rc;
+  if ((rc = dev_alloc(d, &d.Ntc, (size_t)d.nnear * ablk))) return rc;
+  if ((rc = dev_alloc(d, &d.xnt, (size_t)d.nleaf * kNtX))) return rc;
+  if ((rc = dev_alloc(d, (void **)&d.ntc_xmax, sizeof(unsigned) * kTcN))) return rc;
+  H2_CUDA_TRY(cudaMemsetAsync(d.Ntc, 0, (size_t)d.nnear * ablk, st));
+  const int64_t nr = d.nleaf * L;
+  k_ntc_rowexp<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>((const dd *)d.near, d.near_ptr, d.nleaf, L, Lp,
+                                                             d.ntc_E);
+  const int64_t ns = d.nnear * L * 2;
+  k_ntc_slice<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>((const dd *)d.near, nrow_dev, d.ntc_E, d.nnear, L, Lp,
+                                                            ablk, (unsigned char *)d.Ntc);
+  H2_CUDA_TRY(cudaGetLastError());
+  H2_CUDA_TRY(cudaStreamSynchronize(st));
+  d.ntc_ablk = ablk;
+  d.ntc = true;
+  return H2_OK;
+}
+
+// the nearfield phase on the tensor cores: the input's column maxima, its
+// digit planes per leaf, then the block rows (y_pad += or = the near sums)
+int ntc_near(Ctx &c, const void *xpad_v, void *ypad_v, int rp, int accumulate, int64_t *launches) {
+  const dd *xpad = static_cast<const dd *>(xpad_v);
+  dd *ypad = static_cast<dd *>(ypad_v);
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core nearfield takes at most 16 right-hand sides");
+  const int L = (int)d.lmax;
+  H2_CUDA_TRY(cudaMemsetAsync(d.ntc_xmax, 0, sizeof(unsigned) * kTcN, st));
+  const int64_t rows = d.nleaf * L;
+  k_tc_levmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 152 * 8)), 256, 0, st>>>(
+      xpad, rows, rp, d.ntc_xmax);
+  k_ntc_slice_x<<<(unsigned)d.nleaf, 128, 0, st>>>(xpad, L, rp, d.ntc_xmax, (unsigned char *)d.xnt);
+  H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(227 * 1024)));
+  int sms = 0, dev = 0;
+  H2_CUDA_TRY(cudaGetDevice(&dev));
+  H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = (int)std::min<int64_t>(sms, d.nleaf);
+  k_near_tc<<<grid, kTcThreads, kNtSmem, st>>>((const unsigned char *)d.Ntc, d.ntc_ablk,
+                                               (const unsigned char *)d.xnt, d.near_ptr, d.near_col, d.ntc_E,
+                                               d.ntc_xmax, d.nleaf, L, rp, accumulate, ypad);
+  H2_CUDA_TRY(cudaGetLastError());
+  if (launches) *launches = 3;
   return H2_OK;
 }
 

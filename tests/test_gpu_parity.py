@@ -245,7 +245,7 @@ def test_full_size_mixed_precision_sampled_rows(require_gpu, prec):
 
 
 # rows with up to 20 (ico3), 27 (ell3) and 138 (cube30, leaf 16) admissible blocks: the
-# tensor-core coupling sums segments of at most 16 blocks exactly and adds them in order
+# tensor-core coupling sums segments of at most 64 blocks exactly and adds them in order
 TENSOR_CASES = {"cube30_m4": (lambda: I.cube(30), 16, 2.0, 4)}
 
 
@@ -291,3 +291,46 @@ def test_f64_tensor_core_coupling(require_gpu, name):
     assert torch.equal(y1, y2)
     ht.close()
     hd.close()
+
+
+@pytest.mark.parametrize("name", ["ico4_m3", "cube7_m2", "cube30_m4", "ico0_near_only", "ell3_m4"])
+def test_f64_tensor_core_nearfield(require_gpu, name):
+    """FP64-accurate nearfield from FP8 E4M3 digits on the tensor cores (leaves of at
+    most 21 triangles, up to 16 right-hand sides): against the oracle and the
+    double-float path, column scales far apart, and bit-reproducible.  cube30 (leaf
+    16) has leaf rows of more than 32 near blocks, summed in several exact segments;
+    ico0 has no far field (the nearfield overwrites the output)."""
+    import torch
+    v, f, o = _oracle_any(name)
+    make, leaf, eta, m = CASES[name] if name in CASES else TENSOR_CASES[name]
+    ht = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64")
+    hd = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64", tensor="off")
+    assert ht.stats["tensor_near"] == 1 and hd.stats["tensor_near"] == 0
+    n = f.shape[0]
+    for nrhs in (1, 3, 16, 17):
+        x = I.uniform_rhs(n, nrhs, 3400 + nrhs)
+        ref = o.matvec(x)
+        yt, yd = ht.matvec_host(x), hd.matvec_host(x)
+        assert _rel(yt, ref) <= TOL["f64"], (nrhs, _rel(yt, ref))
+        assert _rel(yt, yd) <= TOL["f64"], (nrhs, _rel(yt, yd))
+    x = np.concatenate([np.ones((n, 1)), 1e-12 * I.uniform_rhs(n, 1, 3500), 1e8 * I.uniform_rhs(n, 1, 3501)], axis=1)
+    ref = o.matvec(x)
+    yt = ht.matvec_host(x)
+    for c in range(3):
+        assert _rel(yt[:, c], ref[:, c]) <= TOL["f64"], (c, _rel(yt[:, c], ref[:, c]))
+    xd = colmajor(torch.from_numpy(I.uniform_rhs(n, 16, 3600)).cuda())
+    y1, y2 = colmajor(torch.empty_like(xd)), colmajor(torch.empty_like(xd))
+    ht.matvec(xd, y1)
+    ht.matvec(xd, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    ht.close()
+    hd.close()
+
+
+def test_tensor_core_nearfield_needs_small_leaves(require_gpu):
+    """Leaves of more than 21 triangles keep the double-float nearfield."""
+    v, f = I.icosphere(2)   # 320 triangles, leaf 40: leaves of 40
+    h = H2Matrix(v, f, leaf_size=40, eta=2.0, order=3, prec="f64")
+    assert h.stats["leaf_max"] > 21 and h.stats["tensor_near"] == 0
+    h.close()

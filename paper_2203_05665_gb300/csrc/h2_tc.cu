@@ -162,15 +162,28 @@ __device__ __forceinline__ void named_sync_id(uint32_t id, uint32_t nthreads) {
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
 // split X (|X| <= 2^49) into ten signed 5-bit digits, most significant
-// first: X = sum_i s_i 2^(45 - 5i), each a rounded quotient, |s_i| <= 16
+// first: X = sum_i s_i 2^(45 - 5i), |s_i| <= 16.  X = A 2^25 + B with B in
+// [-2^24, 2^24) gives two 32-bit halves; digits are taken from the low end,
+// d = ((v + 16) mod 32) - 16 in [-16, 15] and v = (v - d) / 32 exactly, B's
+// remainder (0 or 1) carries into A, and A's remainder after four digits is
+// the top digit, within [-16, 16] because |A| <= 2^24 + 2.
 __host__ __device__ __forceinline__ void split_digits(long long X, int (&s)[kTcSlices]) {
+  int b = (int)(((X + (1LL << 24)) & ((1LL << 25) - 1)) - (1LL << 24));
+  int a = (int)((X - b) >> 25);
 #pragma unroll
-  for (int i = 0; i < kTcSlices; ++i) {
-    const int sh = 5 * (kTcSlices - 1 - i);
-    const long long q = sh > 0 ? (X + (1LL << (sh - 1))) >> sh : X;
-    s[i] = (int)q;
-    X -= q * (1LL << sh);
+  for (int i = kTcSlices - 1; i >= kTcSlices / 2; --i) {
+    const int d = ((b + 16) & 31) - 16;
+    s[i] = d;
+    b = (b - d) >> 5;
   }
+  a += b;
+#pragma unroll
+  for (int i = kTcSlices / 2 - 1; i >= 1; --i) {
+    const int d = ((a + 16) & 31) - 16;
+    s[i] = d;
+    a = (a - d) >> 5;
+  }
+  s[0] = a;
 }
 
 __device__ __forceinline__ double tc_green(const double *x, const double *y) {
@@ -239,25 +252,31 @@ __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__
 // ---------------------------------------------------------------- per product
 __device__ __forceinline__ int tc_level(int64_t c) { return 63 - __clzll(c + 1); }
 
-// xmax[j] = largest |hi| of column j over rows [0, rows) of x ([rows][rp], as float bits)
+// xmax[j] = largest |hi| of column j over rows [0, rows) of x ([rows][rp], as float bits).
+// A warp reads four rows at a time with 16-byte loads (lane l: row l / 8, columns
+// 2 (l % 8) and 2 (l % 8) + 1), so the reads are contiguous and every lane keeps two
+// fixed columns; rp is even (double-float rows are padded to 16 bytes).
 __global__ void k_tc_levmax(const dd *__restrict__ x, int64_t rows, int rp, unsigned *__restrict__ xmax) {
   __shared__ unsigned loc[kTcN];
   if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
   __syncthreads();
-  float mx[kTcN];
-#pragma unroll
-  for (int j = 0; j < kTcN; ++j) mx[j] = 0.0f;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-    const dd *row = x + r * rp;
-#pragma unroll
-    for (int j = 0; j < kTcN; ++j)
-      if (j < rp) mx[j] = fmaxf(mx[j], fabsf(row[j].hi));
-  }
-#pragma unroll
-  for (int j = 0; j < kTcN; ++j) {
-    float v = mx[j];
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&loc[j], __float_as_uint(v));
+  const int lane = threadIdx.x & 31, sub = lane & 7, nv = rp / 2;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  float m0 = 0.0f, m1 = 0.0f;
+  if (sub < nv)
+    for (int64_t r = 4 * w + (lane >> 3); r < rows; r += 4 * warps) {
+      const float4 v = *reinterpret_cast<const float4 *>(x + r * rp + 2 * sub);
+      m0 = fmaxf(m0, fabsf(v.x));
+      m1 = fmaxf(m1, fabsf(v.z));
+    }
+  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 8));
+  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 16));
+  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 8));
+  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 16));
+  if (lane < nv) {
+    if (m0 > 0.0f) atomicMax(&loc[2 * lane], __float_as_uint(m0));
+    if (m1 > 0.0f) atomicMax(&loc[2 * lane + 1], __float_as_uint(m1));
   }
   __syncthreads();
   if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[threadIdx.x], loc[threadIdx.x]);
@@ -925,6 +944,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+// CTAs of k_tc_levmax: 8 warps of 4 rows each per pass, at most 8 CTAs per SM
+static unsigned levmax_grid(int64_t rows) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 31) / 32, 152 * 8));
+}
+
 bool tc_eligible(const Dev &d) { return d.prec == H2_F64 && d.coupling == 0 && d.m == 4 && d.kp == kTcK; }
 
 int tc_build(Ctx &c, const int32_t *arow_dev) {
@@ -965,8 +989,7 @@ int tc_upward(Ctx &c, void *xhat_v, int rp, int64_t *launches) {
   int64_t nl = 0;
   H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
   const int64_t lrows = d.nleaf * kTcK;
-  k_tc_levmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((lrows + 255) / 256, 152 * 8)), 256, 0, st>>>(
-      xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
+  k_tc_levmax<<<levmax_grid(lrows), 256, 0, st>>>(xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
   ++nl;
   const int k = d.k, m = d.m;
   // k = 64, rp <= 16: at most 25,344 bytes, below the 48 KB default limit
@@ -1050,8 +1073,7 @@ int ntc_near(Ctx &c, const void *xpad_v, void *ypad_v, int rp, int accumulate, i
   const int L = (int)d.lmax;
   H2_CUDA_TRY(cudaMemsetAsync(d.ntc_xmax, 0, sizeof(unsigned) * kTcN, st));
   const int64_t rows = d.nleaf * L;
-  k_tc_levmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 152 * 8)), 256, 0, st>>>(
-      xpad, rows, rp, d.ntc_xmax);
+  k_tc_levmax<<<levmax_grid(rows), 256, 0, st>>>(xpad, rows, rp, d.ntc_xmax);
   k_ntc_slice_x<<<(unsigned)d.nleaf, 128, 0, st>>>(xpad, L, rp, d.ntc_xmax, (unsigned char *)d.xnt);
   H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(227 * 1024)));

@@ -128,6 +128,8 @@ struct GmresWork {
   double *tolv = nullptr;                 // per column: residual target of the cycle
   double *dpart = nullptr;                // chunk sums of the Gram-Schmidt dot products
   int *maxv = nullptr, *itc = nullptr;    // per column: iteration limit, iterations done
+  int *hflag = nullptr;                   // pinned host copy of `active` (convergence checks)
+  cudaEvent_t ev = nullptr;               // recorded behind that copy
 };
 void free_gmres_work(GmresWork &w);
 

@@ -16,31 +16,6 @@ namespace {
 
 constexpr int kT = 256;
 
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double part[32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) part[w] = v;
-  __syncthreads();
-  double s = 0;
-  if (w == 0) {
-    s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  }
-  return s;  // valid in thread 0
-}
-
-// out[i * nrhs + c] = <X_i[:, c], W[:, c]> for i < nvec; grid (nrhs, nvec)
-__global__ void k_dots(const double *__restrict__ X, const double *__restrict__ W, int64_t n, int nrhs,
-                       double *__restrict__ out) {
-  const int c = blockIdx.x, i = blockIdx.y;
-  const double *x = X + ((int64_t)i * nrhs + c) * n, *w = W + (int64_t)c * n;
-  double s = 0;
-  for (int64_t l = threadIdx.x; l < n; l += blockDim.x) s += x[l] * w[l];
-  s = block_sum(s);
-  if (threadIdx.x == 0) out[i * nrhs + c] = s;
-}
-
 // Gram-Schmidt dot products, 8 vectors per CTA so that W is read once per 8
 // dots: grid (nrhs, ceil(nvec / 8), Z); CTA (c, g, z) sums rows
 // [n z / Z, n (z + 1) / Z) and writes part[(z nvec + i) nrhs + c]; with
@@ -85,7 +60,7 @@ __global__ void k_dots_sum(const double *__restrict__ part, int Z, int nvec, int
   out[e] = s;
 }
 
-constexpr int kDotMaxZ = 16;
+constexpr int kDotMaxZ = 64;
 
 // W[:, c] -= sum_{i < nvec} h[i][c] X_i[:, c]; accumulates h into H column j
 __global__ void k_orth(const double *__restrict__ X, const double *__restrict__ h, int nvec, int64_t n, int nrhs,
@@ -99,15 +74,17 @@ __global__ void k_orth(const double *__restrict__ X, const double *__restrict__ 
   }
 }
 
-// v[:, c] = w[:, c] / nrm[c] for active columns with nrm > 0, else 0
+// v[:, c] = w[:, c] / nrm[c] for active columns with nrm > 0, else 0; grid (., nrhs):
+// the column's reciprocal is formed once per CTA (FP64 division is slow on this GPU)
 __global__ void k_scale(const double *__restrict__ W, const double *__restrict__ nrm, const int *__restrict__ active,
                         int64_t n, int nrhs, double *__restrict__ Vout) {
-  const int64_t total = n * nrhs;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int c = (int)(e / n);
-    double d = nrm[c];
-    Vout[e] = (active[c] && d > 0) ? W[e] / d : 0.0;
-  }
+  const int c = blockIdx.y;
+  const double d = nrm[c];
+  const double inv = (active[c] && d > 0) ? 1.0 / d : 0.0;
+  const double *w = W + (int64_t)c * n;
+  double *v = Vout + (int64_t)c * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    v[e] = w[e] * inv;
 }
 
 // Hessenberg column j: h1 + h2 from the two Gram-Schmidt passes, then the
@@ -189,15 +166,28 @@ int grid1(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
-// out[i nrhs + c] = <X_i[:, c], W[:, c]> for i < nvec (part: kDotMaxZ nvec nrhs doubles of scratch)
+// out[i nrhs + c] = <X_i[:, c], W[:, c]> for i < nvec (part: kDotMaxZ nvec nrhs doubles of
+// scratch, or NULL for one chunk per column)
 void dots(const double *X, const double *W, int64_t n, int nrhs, int nvec, double *out, double *part,
           cudaStream_t st) {
   // enough CTAs to fill the GPU, chunks of at least 1024 rows
   const int groups = (nvec + kDotVB - 1) / kDotVB;
-  int Z = (int)std::min<int64_t>(kDotMaxZ, std::max<int64_t>(1, n / 1024));
+  int Z = part ? (int)std::min<int64_t>(kDotMaxZ, std::max<int64_t>(1, n / 1024)) : 1;
   while (Z > 1 && (int64_t)nrhs * groups * Z > 4 * 152) --Z;
   k_dots8<<<dim3(nrhs, groups, Z), 256, 0, st>>>(X, W, n, nrhs, nvec, Z > 1 ? part : out);
   if (Z > 1) k_dots_sum<<<(nvec * nrhs + 127) / 128, 128, 0, st>>>(part, Z, nvec, nrhs, out);
+}
+
+// 2-norms of the ncols columns of v (n rows) into out (device)
+void norms(const double *v, int64_t n, int ncols, double *out, double *part, cudaStream_t st) {
+  dots(v, v, n, ncols, 1, out, part, st);
+  k_sqrt<<<(ncols + 63) / 64, 64, 0, st>>>(out, ncols);
+}
+
+void launch_scale(const double *W, const double *nrm, const int *active, int64_t n, int nrhs, double *V,
+                  cudaStream_t st) {
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((n + kT - 1) / kT, std::max(1, 4 * 152 / nrhs)));
+  k_scale<<<dim3(gx, nrhs), kT, 0, st>>>(W, nrm, active, n, nrhs, V);
 }
 
 }  // namespace
@@ -209,6 +199,8 @@ void free_gmres_work(GmresWork &w) {
   for (int *p : {w.active, w.jc, w.maxv, w.itc})
     if (p) cudaFree(p);
   if (w.tolv) cudaFree(w.tolv);
+  if (w.hflag) cudaFreeHost(w.hflag);
+  if (w.ev) cudaEventDestroy(w.ev);
   w = GmresWork();
 }
 
@@ -241,7 +233,9 @@ int alloc_gmres_work(GmresWork &w, int64_t n_, int cols, int mr) {
   al(&w.Az, tot);
   al(&w.tolv, cols);
   ok = ok && cudaMalloc(&w.active, cols * 4) == cudaSuccess && cudaMalloc(&w.jc, cols * 4) == cudaSuccess &&
-       cudaMalloc(&w.maxv, cols * 4) == cudaSuccess && cudaMalloc(&w.itc, cols * 4) == cudaSuccess;
+       cudaMalloc(&w.maxv, cols * 4) == cudaSuccess && cudaMalloc(&w.itc, cols * 4) == cudaSuccess &&
+       cudaMallocHost(&w.hflag, cols * 4) == cudaSuccess &&
+       cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_gmres_work(w);
@@ -266,8 +260,7 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
   int rc;
   std::vector<double> rn(nrhs), g0((size_t)(mr + 1) * nrhs, 0.0);
   std::vector<int> on(nrhs, 0);
-  k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(R, R, n, nrhs, w.hn);
-  k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
+  norms(R, n, nrhs, w.hn, w.dpart, st);
   H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.hn, nrhs * 8, cudaMemcpyDeviceToHost, st));
   H2_CUDA_TRY(cudaStreamSynchronize(st));
   bool any = false;
@@ -284,12 +277,17 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
   H2_CUDA_TRY(cudaMemcpyAsync(w.maxv, max_it, nrhs * 4, cudaMemcpyHostToDevice, st));
   H2_CUDA_TRY(cudaMemsetAsync(w.itc, 0, nrhs * 4, st));
   H2_CUDA_TRY(cudaMemsetAsync(w.jc, 0, nrhs * 4, st));
-  k_scale<<<grid1(tot), kT, 0, st>>>(R, w.hn, w.active, n, nrhs, w.Vb);
+  launch_scale(R, w.hn, w.active, n, nrhs, w.Vb, st);
   H2_CUDA_TRY(cudaMemcpyAsync(w.g, g0.data(), (mr + 1) * nrhs * 8, cudaMemcpyHostToDevice, st));
-  // the host looks at the columns' state every `check` iterations only: for
+  // The host looks at the columns' state every `check` iterations only (for
   // small systems an iteration is shorter than a host round trip, for large
-  // ones an iteration past the last convergence costs more than the trip
+  // ones an iteration past the last convergence costs more than the trip),
+  // and one check late: the flags of iteration j are copied to pinned memory
+  // behind it and read after iteration j + check has been queued, so the GPU
+  // never waits for the host.  An iteration queued after every column has
+  // stopped changes nothing (all its updates are masked by `active`).
   const int check = tot >= ((int64_t)1 << 20) ? 1 : 4;
+  bool pending = false;
   for (int j = 0; j < mr; ++j) {
     double *Vj = w.Vb + (int64_t)j * tot, *Vj1 = w.Vb + (int64_t)(j + 1) * tot;
     if ((rc = run_matvec(c, Vj, w.W, nrhs, true))) return rc;
@@ -299,16 +297,21 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
     k_orth<<<grid1(tot), kT, 0, st>>>(w.Vb, w.h2, j + 1, n, nrhs, w.W);
     dots(w.W, w.W, n, nrhs, 1, w.hn, w.dpart, st);
     k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
-    k_scale<<<grid1(tot), kT, 0, st>>>(w.W, w.hn, w.active, n, nrhs, Vj1);
+    launch_scale(w.W, w.hn, w.active, n, nrhs, Vj1, st);
     k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(w.h1, w.h2, w.hn, j, mr, nrhs, w.H, w.cs, w.sn, w.g, w.resid,
                                               w.active, w.tolv, w.maxv, w.itc, w.jc);
     H2_CUDA_TRY(cudaGetLastError());
-    if ((j + 1) % check == 0 && j + 1 < mr) {
-      H2_CUDA_TRY(cudaMemcpyAsync(on.data(), w.active, nrhs * 4, cudaMemcpyDeviceToHost, st));
-      H2_CUDA_TRY(cudaStreamSynchronize(st));
+    if (pending) {
+      H2_CUDA_TRY(cudaEventSynchronize(w.ev));
+      pending = false;
       bool still = false;
-      for (int col = 0; col < nrhs; ++col) still = still || on[col];
+      for (int col = 0; col < nrhs; ++col) still = still || w.hflag[col];
       if (!still) break;
+    }
+    if ((j + 1) % check == 0 && j + 1 < mr) {
+      H2_CUDA_TRY(cudaMemcpyAsync(w.hflag, w.active, nrhs * 4, cudaMemcpyDeviceToHost, st));
+      H2_CUDA_TRY(cudaEventRecord(w.ev, st));
+      pending = true;
     }
   }
   H2_CUDA_TRY(cudaMemcpyAsync(iters, w.itc, nrhs * 4, cudaMemcpyDeviceToHost, st));
@@ -336,8 +339,7 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
   GmresWork &w = c.gw;
   std::vector<double> bn(nrhs), rn(nrhs), res(nrhs, 0.0), tol(nrhs);
   std::vector<int> act(nrhs), left(nrhs), it(nrhs), iters(nrhs, 0);
-  k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(b, b, n, nrhs, w.bn);
-  k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.bn, nrhs);
+  norms(b, n, nrhs, w.bn, w.dpart, st);
   H2_CUDA_TRY(cudaMemcpyAsync(bn.data(), w.bn, nrhs * 8, cudaMemcpyDeviceToHost, st));
   H2_CUDA_TRY(cudaMemsetAsync(z, 0, tot * 8, st));
   H2_CUDA_TRY(cudaMemcpyAsync(w.r, b, tot * 8, cudaMemcpyDeviceToDevice, st));
@@ -346,8 +348,7 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
       if ((rc = run_matvec(c, z, w.Az, nrhs, true))) return rc;
       k_residual<<<grid1(tot), kT, 0, st>>>(b, w.Az, tot, w.r);
     }
-    k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(w.r, w.r, n, nrhs, w.hn);
-    k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(w.hn, nrhs);
+    norms(w.r, n, nrhs, w.hn, w.dpart, st);
     H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), w.hn, nrhs * 8, cudaMemcpyDeviceToHost, st));
     H2_CUDA_TRY(cudaStreamSynchronize(st));
     bool any = false;
@@ -393,8 +394,9 @@ void k_launch_axpy(const double *d, int64_t total, double *z, cudaStream_t st) {
 }
 
 int column_norms(Ctx &c, const double *v, int64_t n, int ncols, double *dev_tmp, double *host_out) {
-  k_dots<<<dim3(ncols, 1), kT, 0, c.stream>>>(v, v, n, ncols, dev_tmp);
-  k_sqrt<<<(ncols + 63) / 64, 64, 0, c.stream>>>(dev_tmp, ncols);
+  // chunked sums when the handle's GMRES scratch is large enough
+  double *part = (c.gw.dpart && ncols <= c.gw.cols) ? c.gw.dpart : nullptr;
+  norms(v, n, ncols, dev_tmp, part, c.stream);
   H2_CUDA_TRY(cudaGetLastError());
   H2_CUDA_TRY(cudaMemcpyAsync(host_out, dev_tmp, ncols * 8, cudaMemcpyDeviceToHost, c.stream));
   H2_CUDA_TRY(cudaStreamSynchronize(c.stream));
@@ -416,16 +418,14 @@ int run_gmres_ir(Ctx &hi, Ctx &lo, const double *b, double *z, int nrhs, double 
   std::vector<double> h_bn(nrhs), h_rn(nrhs), h_res(nrhs, 1.0);
   std::vector<int> h_keep(nrhs, 1), h_iters(nrhs, 0), h_outer(nrhs, 0);
   std::vector<h2_solve_info> inner(nrhs);
-  k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(b, b, n, nrhs, nrm);
-  k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(nrm, nrhs);
+  norms(b, n, nrhs, nrm, hi.gw.dpart, st);
   H2_CUDA_TRY(cudaMemcpyAsync(h_bn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, st));
   H2_CUDA_TRY(cudaMemsetAsync(z, 0, tot * 8, st));
   H2_CUDA_TRY(cudaMemcpyAsync(r, b, tot * 8, cudaMemcpyDeviceToDevice, st));
   H2_CUDA_TRY(cudaStreamSynchronize(st));
   for (int outer = 0;; ++outer) {
     // residual norms and convergence per column
-    k_dots<<<dim3(nrhs, 1), kT, 0, st>>>(r, r, n, nrhs, nrm);
-    k_sqrt<<<(nrhs + 63) / 64, 64, 0, st>>>(nrm, nrhs);
+    norms(r, n, nrhs, nrm, hi.gw.dpart, st);
     H2_CUDA_TRY(cudaMemcpyAsync(h_rn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, st));
     H2_CUDA_TRY(cudaStreamSynchronize(st));
     bool any = false;

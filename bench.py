@@ -316,7 +316,8 @@ def run_ours(args):
                 "rel_diff_vs_f64": float(torch.linalg.norm(yf.double() - y) / torch.linalg.norm(y)),
                 "phases_ms": {k2: v2[0] / fpr for k2, v2 in fph.items()},
                 "coupling_hbm_frac": a32["coupling_bytes"] / (fcpl * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                "kernel": "k_blockrow (coupling, stored FP32 S)"}
+                "kernel": ("k_coupling_tc (tcgen05 kind::f8f6f4, six 5-bit E4M3 digits, exact FP32 sums)"
+                           if lo.stats.get("tensor", 0) else "k_blockrow (coupling, stored FP32 S)")}
             lo.close()
 
     small = None

@@ -79,13 +79,14 @@ struct Dev {
   double *icen = nullptr;       // nclu x 3 interpolation-box centres (regenerated coupling)
   float *adm_dc = nullptr;      // nadm x 4: centre of the row cluster minus centre of the column cluster
   float *ihalf = nullptr;       // nclu x 3 interpolation-box half widths
-  // FP64-accurate coupling on the tensor cores (order 4): the ten E4M3 digit
-  // planes of every S_b ([nadm][10][64 x 64] bytes, K-major core-matrix
-  // layout), the row exponents ([nclu][64]), the digit planes of the
-  // coefficients of one product ([nclu][10][16 x 64]) and the column maxima
-  // per level ([32][16])
+  // Coupling on the tensor cores (order 4, FP64 or FP32 handles): the E4M3
+  // digit planes of every S_b ([nadm][tc_nd][64 x 64] bytes, K-major
+  // core-matrix layout), the row exponents ([nclu][64]), the digit planes of
+  // the coefficients of one product ([nclu][tc_nd][16 x 64]) and the column
+  // maxima per level ([32][16])
   int tensor = 0;               // 0: use the tensor cores where supported, 1: never
-  bool tc = false;              // the slices exist
+  bool tc = false;              // the digits exist
+  int tc_nd = 0;                // digits per value: 10 (FP64-accurate) or 6 (FP32 handles)
   void *Stc = nullptr, *xtc = nullptr;
   int32_t *tc_E = nullptr;
   unsigned *tc_xmax = nullptr;

@@ -738,7 +738,9 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     mk.count(H2_PH_LEAF_FORWARD);
   }
   mk.mark(H2_PH_UPWARD);
-  const bool tcpath = std::is_same<T, dd>::value && d.tc && rp <= 16;
+  const bool tcpath = d.tc && rp <= 16 &&
+                      ((std::is_same<T, dd>::value && d.tc_nd == 10) ||
+                       (std::is_same<T, float>::value && std::is_same<TS, float>::value && d.tc_nd == 6));
   if (far && tcpath) {
     // with the column maxima and coefficient slices of the tensor-core coupling
     int64_t nl = 0;

@@ -436,7 +436,7 @@ int build_typed(Ctx &c) {
                                                                           d.cheb, m, d.kp, d.nadm, (T *)d.S);
     H2_CUDA_TRY(cudaGetLastError());
   }
-  // FP64-accurate handles of order 4: the E4M3 digit planes for the tensor-core coupling
+  // FP64 and FP32 handles of order 4: the E4M3 digit planes for the tensor-core coupling
   if (d.tensor == 0 && tc_eligible(d) && (rc = tc_build(c, (const int32_t *)t_arow.ptr))) return rc;
 
 

@@ -56,29 +56,39 @@ namespace {
 
 constexpr int kTcK = 64;                 // rank k = m^3, m = 4
 constexpr int kTcN = 16;                 // right-hand sides of one product (padded)
-constexpr int kTcSlices = 10;            // 5-bit digits of a value
+constexpr int kTcSlices = 10;            // 5-bit digits of an FP64-accurate value
 constexpr int kTcFixBits = 49;           // |X| <= 2^49
 constexpr int kTcTop = 11;               // digit pairs with i + k <= 11 are summed
 constexpr int kTcSegBlocks = 64;         // blocks accumulated in one exact segment (sums <= 2^20)
 constexpr uint32_t kSliceA = kTcK * kTcK;              // 4096 bytes: one digit plane of S_b (64 x 64 E4M3)
 constexpr uint32_t kSliceB = kTcN * kTcK;              // 1024 bytes: one digit plane of x^_s (16 x 64 E4M3)
-constexpr uint32_t kTileA = kTcSlices * kSliceA;       // 40960
-constexpr uint32_t kTileB = kTcSlices * kSliceB;       // 10240
-constexpr uint32_t kStage = kTileA + kTileB;           // 51200
-constexpr int kTcStages = 4;
-constexpr int kTcGroups = 5;             // S digit pairs (1,2), (3,4), ..., (9,10)
-// group g pairs S digits 2g+1, 2g+2 with x^ digits 1 .. 10 - 2g (N = 16 (10 - 2g));
-// its accumulators start at tensor-memory column group_col(g): 0, 160, 288, 384, 448
-__host__ __device__ constexpr int group_nx(int g) { return kTcSlices - 2 * g; }
-__host__ __device__ constexpr uint32_t group_col(int g) {   // sum of 16 (10 - 2h) over h < g
-  return (uint32_t)(kTcN * g * (kTcSlices + 1 - g));
-}
-static_assert(group_col(kTcGroups) == 480, "accumulator columns");
-constexpr uint32_t kTmemCols = 512;      // one accumulator set (480 columns used)
+
+// The coupling's digit layout for ND digits per value: ND = 10 for FP64
+// accuracy (|X| <= 2^49, pairs i + k <= 11), ND = 6 for FP32 accuracy (|X| <=
+// 2^29, pairs i + k <= 7: the dropped pairs stay below 2^-27 of the row's
+// scale).  Group g pairs S digits 2g+1, 2g+2 with x^ digits 1 .. ND - 2g (N =
+// 16 (ND - 2g)); its accumulators start at tensor-memory column col(g): 0,
+// 160, 288, 384, 448 (ND = 10; 480 used) or 0, 96, 160 (ND = 6; 192 used).
+template <int ND>
+struct Dig {
+  static constexpr int kFix = 5 * ND - 1;
+  static constexpr int kTop = ND + 1;
+  static constexpr int kGroups = ND / 2;
+  static constexpr uint32_t kTileA = ND * kSliceA;
+  static constexpr uint32_t kTileB = ND * kSliceB;
+  static constexpr uint32_t kStage = kTileA + kTileB;
+  static constexpr int kStages = ND == 10 ? 4 : 6;
+  __host__ __device__ static constexpr int nx(int g) { return ND - 2 * g; }
+  __host__ __device__ static constexpr uint32_t col(int g) { return (uint32_t)(kTcN * g * (ND + 1 - g)); }
+};
+static_assert(Dig<10>::col(5) == 480 && Dig<6>::col(3) == 192, "accumulator columns");
+constexpr uint32_t kTmemCols = 512;      // one accumulator set
 constexpr int kTcThreads = 192;          // producer, MMA, four epilogue warps
 constexpr uint32_t kXch = 64 * kTcN * 8; // epilogue exchange: 64 rows x 16 double-float values
-constexpr uint32_t kBarOff = kTcStages * kStage + kXch;
-constexpr uint32_t kTcSmem = kBarOff + 16 * 8 + 16;
+template <int ND>
+__host__ __device__ constexpr uint32_t tc_bar_off() { return Dig<ND>::kStages * Dig<ND>::kStage + kXch; }
+template <int ND>
+__host__ __device__ constexpr uint32_t tc_smem() { return tc_bar_off<ND>() + 16 * 8 + 16; }
 
 // instruction descriptor of tcgen05.mma kind::f8f6f4: D FP32 (bits 4-5 =
 // 1), A and B E4M3 (bits 7-9 = 0, bits 10-12 = 0), both K-major (bits 15, 16
@@ -167,23 +177,38 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) 
 // d = ((v + 16) mod 32) - 16 in [-16, 15] and v = (v - d) / 32 exactly, B's
 // remainder (0 or 1) carries into A, and A's remainder after four digits is
 // the top digit, within [-16, 16] because |A| <= 2^24 + 2.
-__host__ __device__ __forceinline__ void split_digits(long long X, int (&s)[kTcSlices]) {
-  int b = (int)(((X + (1LL << 24)) & ((1LL << 25) - 1)) - (1LL << 24));
-  int a = (int)((X - b) >> 25);
+// The same for six digits of |X| <= 2^29 (one 32-bit value; the top digit
+// stays within [-16, 16] by the same bound).
+template <int ND>
+__host__ __device__ __forceinline__ void split_digits(long long X, int (&s)[ND]) {
+  static_assert(ND == 10 || ND == 6, "digit counts");
+  if (ND == 10) {
+    int b = (int)(((X + (1LL << 24)) & ((1LL << 25) - 1)) - (1LL << 24));
+    int a = (int)((X - b) >> 25);
 #pragma unroll
-  for (int i = kTcSlices - 1; i >= kTcSlices / 2; --i) {
-    const int d = ((b + 16) & 31) - 16;
-    s[i] = d;
-    b = (b - d) >> 5;
-  }
-  a += b;
+    for (int i = ND - 1; i >= ND / 2; --i) {
+      const int d = ((b + 16) & 31) - 16;
+      s[i] = d;
+      b = (b - d) >> 5;
+    }
+    a += b;
 #pragma unroll
-  for (int i = kTcSlices / 2 - 1; i >= 1; --i) {
-    const int d = ((a + 16) & 31) - 16;
-    s[i] = d;
-    a = (a - d) >> 5;
+    for (int i = ND / 2 - 1; i >= 1; --i) {
+      const int d = ((a + 16) & 31) - 16;
+      s[i] = d;
+      a = (a - d) >> 5;
+    }
+    s[0] = a;
+  } else {
+    int a = (int)X;
+#pragma unroll
+    for (int i = ND - 1; i >= 1; --i) {
+      const int d = ((a + 16) & 31) - 16;
+      s[i] = d;
+      a = (a - d) >> 5;
+    }
+    s[0] = a;
   }
-  s[0] = a;
 }
 
 __device__ __forceinline__ double tc_green(const double *x, const double *y) {
@@ -221,7 +246,8 @@ __device__ __forceinline__ unsigned char e4m3(int s) {
   return (unsigned char)__nv_cvt_float_to_fp8((float)s, __NV_SATFINITE, __NV_E4M3);
 }
 
-// the ten E4M3 digit planes of S_b, row nu, contraction indices 16 cg .. 16 cg + 15
+// the ND E4M3 digit planes of S_b, row nu, contraction indices 16 cg .. 16 cg + 15
+template <int ND>
 __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__restrict__ col,
                              const double *__restrict__ cheb, const int32_t *__restrict__ E, int64_t nblk,
                              unsigned char *__restrict__ Stc) {
@@ -232,52 +258,59 @@ __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__
   const int64_t t = brow[b], s = col[b];
   double x[3], y[3];
   tc_point(cheb, t, nu, x);
-  const int sc = kTcFixBits - E[t * kTcK + nu];
-  __align__(16) unsigned char out[kTcSlices][16];
+  const int sc = Dig<ND>::kFix - E[t * kTcK + nu];
+  __align__(16) unsigned char out[ND][16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     tc_point(cheb, s, 16 * cg + q, y);
     const long long X = llrint(ldexp(tc_green(x, y), sc));
-    int sl[kTcSlices];
-    split_digits(X, sl);
+    int sl[ND];
+    split_digits<ND>(X, sl);
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) out[i][q] = e4m3(sl[i]);
+    for (int i = 0; i < ND; ++i) out[i][q] = e4m3(sl[i]);
   }
-  unsigned char *base = Stc + b * (int64_t)kTileA + core_off(nu, 16 * cg);
+  unsigned char *base = Stc + b * (int64_t)Dig<ND>::kTileA + core_off(nu, 16 * cg);
 #pragma unroll
-  for (int i = 0; i < kTcSlices; ++i)
+  for (int i = 0; i < ND; ++i)
     *reinterpret_cast<uint4 *>(base + i * kSliceA) = *reinterpret_cast<const uint4 *>(out[i]);
 }
 
 // ---------------------------------------------------------------- per product
 __device__ __forceinline__ int tc_level(int64_t c) { return 63 - __clzll(c + 1); }
 
-// xmax[j] = largest |hi| of column j over rows [0, rows) of x ([rows][rp], as float bits).
-// A warp reads four rows at a time with 16-byte loads (lane l: row l / 8, columns
-// 2 (l % 8) and 2 (l % 8) + 1), so the reads are contiguous and every lane keeps two
-// fixed columns; rp is even (double-float rows are padded to 16 bytes).
-__global__ void k_tc_levmax(const dd *__restrict__ x, int64_t rows, int rp, unsigned *__restrict__ xmax) {
+// xmax[j] = largest |x| (double-float: |hi|) of column j over rows [0, rows) of x
+// ([rows][rp], as float bits).  A warp reads 32 / LPR rows at a time with 16-byte
+// loads (LPR lanes per row of 16 columns, lane l: row l / LPR, its EPV columns
+// from EPV (l % LPR)), so the reads are contiguous and every lane keeps fixed
+// columns; rp is a multiple of EPV (rows are padded to 16 bytes).
+__device__ __forceinline__ float mag(float v) { return fabsf(v); }
+__device__ __forceinline__ float mag(dd v) { return fabsf(v.hi); }
+
+template <class T>
+__global__ void k_tc_levmax(const T *__restrict__ x, int64_t rows, int rp, unsigned *__restrict__ xmax) {
+  constexpr int EPV = 16 / (int)sizeof(T), LPR = kTcN / EPV, RPW = 32 / LPR;
   __shared__ unsigned loc[kTcN];
   if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
   __syncthreads();
-  const int lane = threadIdx.x & 31, sub = lane & 7, nv = rp / 2;
+  const int lane = threadIdx.x & 31, sub = lane % LPR, nv = rp / EPV;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  float m0 = 0.0f, m1 = 0.0f;
+  float m[EPV];
+#pragma unroll
+  for (int e = 0; e < EPV; ++e) m[e] = 0.0f;
   if (sub < nv)
-    for (int64_t r = 4 * w + (lane >> 3); r < rows; r += 4 * warps) {
-      const float4 v = *reinterpret_cast<const float4 *>(x + r * rp + 2 * sub);
-      m0 = fmaxf(m0, fabsf(v.x));
-      m1 = fmaxf(m1, fabsf(v.z));
+    for (int64_t r = RPW * w + lane / LPR; r < rows; r += RPW * warps) {
+      const T *p = x + r * rp + EPV * sub;
+#pragma unroll
+      for (int e = 0; e < EPV; ++e) m[e] = fmaxf(m[e], mag(p[e]));
     }
-  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 8));
-  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 16));
-  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 8));
-  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 16));
-  if (lane < nv) {
-    if (m0 > 0.0f) atomicMax(&loc[2 * lane], __float_as_uint(m0));
-    if (m1 > 0.0f) atomicMax(&loc[2 * lane + 1], __float_as_uint(m1));
-  }
+#pragma unroll
+  for (int e = 0; e < EPV; ++e)
+    for (int o = LPR; o < 32; o <<= 1) m[e] = fmaxf(m[e], __shfl_xor_sync(0xffffffffu, m[e], o));
+  if (lane < nv)
+#pragma unroll
+    for (int e = 0; e < EPV; ++e)
+      if (m[e] > 0.0f) atomicMax(&loc[EPV * lane + e], __float_as_uint(m[e]));
   __syncthreads();
   if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[threadIdx.x], loc[threadIdx.x]);
 }
@@ -287,58 +320,62 @@ __device__ __forceinline__ int tc_colexp(unsigned bits) {
   return bits ? (int)((bits >> 23) & 0xFF) - 127 + 2 : 0;
 }
 
-// The ten E4M3 digit planes of the coefficients of cluster c (x^_c
-// [64][rp]): cut in registers, assembled in shared memory (tile: 10 x 16 x
-// 64 bytes, 10 KB) in the MMA layout (16 columns x 64 contraction values
-// per plane) and written out with 16-byte stores.  All threads of the CTA
-// take part; the caller synchronises before and after.
-__device__ __forceinline__ void slice_cluster(const dd *__restrict__ xc, int rp, int lvl,
+// The ND E4M3 digit planes of the coefficients of cluster c (x^_c
+// [64][rp]): cut in registers, assembled in shared memory (tile: ND x 16 x
+// 64 bytes) in the MMA layout (16 columns x 64 contraction values per
+// plane) and written out with 16-byte stores.  All threads of the CTA take
+// part; the caller synchronises before and after.
+__device__ __forceinline__ long long fixed_of(dd v, int sc) {
+  return llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
+}
+__device__ __forceinline__ long long fixed_of(float v, int sc) { return llrintf(ldexpf(v, sc)); }
+
+template <class T, int ND>
+__device__ __forceinline__ void slice_cluster(const T *__restrict__ xc, int rp, int lvl,
                                               const unsigned *__restrict__ xmax, unsigned char *tile,
                                               unsigned char *__restrict__ dst) {
   for (int e = threadIdx.x; e < kTcN * kTcK; e += blockDim.x) {
     const int mu = e / kTcN, j = e % kTcN;
     long long X = 0;
-    if (j < rp) {
-      const int sc = kTcFixBits - tc_colexp(xmax[lvl * kTcN + j]);
-      const dd v = xc[mu * rp + j];
-      X = llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
-    }
-    int sl[kTcSlices];
-    split_digits(X, sl);
+    if (j < rp) X = fixed_of(xc[mu * rp + j], Dig<ND>::kFix - tc_colexp(xmax[lvl * kTcN + j]));
+    int sl[ND];
+    split_digits<ND>(X, sl);
     const int o = core_off(j, mu);
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) tile[i * kSliceB + o] = e4m3(sl[i]);
+    for (int i = 0; i < ND; ++i) tile[i * kSliceB + o] = e4m3(sl[i]);
   }
   __syncthreads();
-  constexpr int kWords = kTileB / 16;   // 16-byte words of the ten planes
+  constexpr int kWords = Dig<ND>::kTileB / 16;   // 16-byte words of the planes
   for (int w = threadIdx.x; w < kWords; w += blockDim.x)
     reinterpret_cast<uint4 *>(dst)[w] = reinterpret_cast<const uint4 *>(tile)[w];
 }
 
 // the slices of clusters [c0, c0 + ncl) of level lvl, one cluster per CTA
-__global__ void __launch_bounds__(256) k_tc_slice_x(const dd *__restrict__ xhat, int64_t c0, int lvl, int rp,
+template <class T, int ND>
+__global__ void __launch_bounds__(256) k_tc_slice_x(const T *__restrict__ xhat, int64_t c0, int lvl, int rp,
                                                     const unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
-  __shared__ __align__(16) unsigned char tile[kTileB];
+  __shared__ __align__(16) unsigned char tile[Dig<ND>::kTileB];
   const int64_t c = c0 + blockIdx.x;
-  slice_cluster(xhat + c * kTcK * rp, rp, lvl, xmax, tile, xtc + c * (int64_t)kTileB);
+  slice_cluster<T, ND>(xhat + c * kTcK * rp, rp, lvl, xmax, tile, xtc + c * (int64_t)Dig<ND>::kTileB);
 }
 
 // Upward step for one parent of level l (Algorithm 1, factored transfers,
 // the generic body) with the two extra tasks of the tensor-core coupling:
 // the column maxima of level l from the parent's coefficients, and the
 // slices of its two children (level l + 1, whose maxima are complete).
-__global__ void k_upward_tc(const dd *__restrict__ Ef, int m, int k, int rp, int64_t par0, int lvl,
-                            dd *__restrict__ xhat, unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
+template <class T, int ND>
+__global__ void k_upward_tc(const T *__restrict__ Ef, int m, int k, int rp, int64_t par0, int lvl,
+                            T *__restrict__ xhat, unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned loc[kTcN];
   if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
   const int64_t par = par0 + blockIdx.x;
-  upward_parent<dd, dd>(Ef, m, k, rp, par, xhat, smem_raw);   // ends with the parent written to xhat
+  upward_parent<T, T>(Ef, m, k, rp, par, xhat, smem_raw);   // ends with the parent written to xhat
   __syncthreads();
   // column maxima of the parent (the values this CTA has just written)
   const int kr = k * rp;
   for (int i = threadIdx.x; i < kr; i += blockDim.x) {
-    const float v = fabsf(xhat[par * kr + i].hi);
+    const float v = mag(xhat[par * kr + i]);
     if (v > 0.0f) atomicMax(&loc[i % rp], __float_as_uint(v));
   }
   __syncthreads();
@@ -347,7 +384,7 @@ __global__ void k_upward_tc(const dd *__restrict__ Ef, int m, int k, int rp, int
   unsigned char *tile = smem_raw;
   for (int ch = 0; ch < 2; ++ch) {
     const int64_t c = 2 * par + 1 + ch;
-    slice_cluster(xhat + c * kr, rp, lvl + 1, xmax, tile, xtc + c * (int64_t)kTileB);
+    slice_cluster<T, ND>(xhat + c * kr, rp, lvl + 1, xmax, tile, xtc + c * (int64_t)Dig<ND>::kTileB);
     __syncthreads();
   }
 }
@@ -363,13 +400,23 @@ __device__ __forceinline__ dd dd_scale(dd v, int e) {
 // The coupling kernel (see the top of the file).  Rows t = row0 + r for r
 // in [0, nrows); each CTA takes a contiguous range of rows holding about
 // 1/gridDim of the blocks.
+// T: the coefficient type (dd with ND = 10, float with ND = 6).
+__device__ __forceinline__ dd to_dd(dd v) { return v; }
+__device__ __forceinline__ dd to_dd(float v) { return dd{v, 0.0f}; }
+__device__ __forceinline__ void store_as(dd v, dd *p) { *p = v; }
+__device__ __forceinline__ void store_as(dd v, float *p) { *p = v.hi + v.lo; }
+
+template <int ND, class T>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_coupling_tc(const unsigned char *__restrict__ Stc, const unsigned char *__restrict__ xtc,
                   const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const int32_t *__restrict__ E,
-                  const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, dd *__restrict__ yhat) {
+                  const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, T *__restrict__ yhat) {
+  using D = Dig<ND>;
+  constexpr int kTcStages = D::kStages, kTcGroups = D::kGroups;
+  constexpr uint32_t kStage = D::kStage, kTileA = D::kTileA, kTileB = D::kTileB;
   extern __shared__ __align__(1024) unsigned char smem[];
   dd *xch = reinterpret_cast<dd *>(smem + kTcStages * kStage);
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kBarOff);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + tc_bar_off<ND>());
   uint64_t *empty = full + kTcStages;
   uint64_t *accf = empty + kTcStages;
   uint64_t *acce = accf + 1;
@@ -481,8 +528,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
               for (int g = 0; g < kTcGroups; ++g)
-                tc_mma(tbase + group_col(g), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
-                       dB + (uint64_t)(kk * 16), tc_idesc(kTcN * group_nx(g)), (t > 0 || kk > 0) ? 1u : 0u);
+                tc_mma(tbase + D::col(g), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
+                       dB + (uint64_t)(kk * 16), tc_idesc(kTcN * D::nx(g)), (t > 0 || kk > 0) ? 1u : 0u);
             tc_commit(&empty[s]);   // the stage is free once these MMAs have read it
           }
           if (ok) tc_commit(accf);
@@ -500,10 +547,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int64_t r = r_begin; r < r_end; ++r) {
       const int64_t t = row0 + r;
       const int64_t nb = ptr[t + 1] - ptr[t];
-      dd *yrow = yhat + (t * kTcK + nu) * rp;
+      T *yrow = yhat + (t * kTcK + nu) * rp;
       if (nb == 0) {
         if (half == 0)
-          for (int j = 0; j < rp; ++j) yrow[j] = dd{0.0f, 0.0f};
+          for (int j = 0; j < rp; ++j) store_as(dd{0.0f, 0.0f}, yrow + j);
         continue;
       }
       const int Er = E[t * kTcK + nu];
@@ -523,18 +570,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int j = 0; j < kTcN; ++j) acc[j] = dd{0.0f, 0.0f};
         // lane nu (+ 64) of group g holds S digit i = 2g + 1 (+ 1) times x^ digits
-        // k = 1 .. 10 - 2g (columns group_col(g) + 16 (k - 1) .. + 15).  The pairs of
-        // one level L = i + k share the weight 2^(2-5L): their sums (at most five
+        // k = 1 .. ND - 2g (columns col(g) + 16 (k - 1) .. + 15).  The pairs of one
+        // level L = i + k share the weight 2^(2-5L): their sums (at most five
         // integers of at most 2^20 each, segments of at most 64 blocks) add exactly in
-        // FP32, and each level enters the double-float result once (L <= 11)
+        // FP32, and each level enters the double-float result once (L <= ND + 1)
 #pragma unroll 1
-        for (int L = 2 + half; L <= kTcTop; ++L) {
+        for (int L = 2 + half; L <= D::kTop; ++L) {
           const int ng = min(kTcGroups, (L - 2 - half) / 2 + 1);   // groups with a digit i <= L - 1
           uint32_t raw[kTcGroups][16];
 #pragma unroll
           for (int g = 0; g < kTcGroups; ++g)
             if (g < ng)
-              tmem_ld16_nw(tbase + ((uint32_t)(quad * 32) << 16) + group_col(g) +
+              tmem_ld16_nw(tbase + ((uint32_t)(quad * 32) << 16) + D::col(g) +
                                (uint32_t)((L - (2 * g + 1 + half) - 1) * kTcN),
                            raw[g]);
           tmem_wait();
@@ -562,8 +609,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int j = 0; j < kTcN; ++j) {
             if (j >= rp) break;
             dd v = dd_scale(acc[j] + xch[j * 64 + nu], Fc[j]);
-            if (s0 > 0) v = v + yrow[j];
-            yrow[j] = v;
+            if (s0 > 0) v = v + to_dd(yrow[j]);
+            store_as(v, yrow + j);
           }
         }
         named_sync_id(2, 128);
@@ -949,87 +996,113 @@ static unsigned levmax_grid(int64_t rows) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 31) / 32, 152 * 8));
 }
 
-bool tc_eligible(const Dev &d) { return d.prec == H2_F64 && d.coupling == 0 && d.m == 4 && d.kp == kTcK; }
+// FP64-accurate (ten digits) or FP32-accurate (six digits) coupling of an
+// order-4 handle with stored coupling matrices
+bool tc_eligible(const Dev &d) {
+  return (d.prec == H2_F64 || d.prec == H2_F32) && d.coupling == 0 && d.m == 4 && d.kp == kTcK;
+}
 
-int tc_build(Ctx &c, const int32_t *arow_dev) {
+namespace {
+
+template <int ND>
+int tc_build_nd(Ctx &c, const int32_t *arow_dev) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
   const int64_t row0 = ((int64_t)1 << d.first_adm_level) - 1;
-  if (d.first_adm_level > d.depth || d.nadm == 0) return H2_OK;
   int rc;
   if ((rc = dev_alloc(d, (void **)&d.tc_E, sizeof(int32_t) * (size_t)d.nclu * kTcK))) return rc;
-  if ((rc = dev_alloc(d, &d.Stc, (size_t)d.nadm * kTileA))) return rc;
-  if ((rc = dev_alloc(d, &d.xtc, (size_t)d.nclu * kTileB))) return rc;
+  if ((rc = dev_alloc(d, &d.Stc, (size_t)d.nadm * Dig<ND>::kTileA))) return rc;
+  if ((rc = dev_alloc(d, &d.xtc, (size_t)d.nclu * Dig<ND>::kTileB))) return rc;
   if ((rc = dev_alloc(d, (void **)&d.tc_xmax, sizeof(unsigned) * 32 * kTcN))) return rc;
   H2_CUDA_TRY(cudaMemsetAsync(d.tc_E, 0, sizeof(int32_t) * (size_t)d.nclu * kTcK, st));
-  H2_CUDA_TRY(cudaMemsetAsync(d.xtc, 0, (size_t)d.nclu * kTileB, st));
+  H2_CUDA_TRY(cudaMemsetAsync(d.xtc, 0, (size_t)d.nclu * Dig<ND>::kTileB, st));
   const int64_t nr = (d.nclu - row0) * kTcK;
   k_tc_rowexp<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(d.adm_ptr, d.adm_col, d.cheb, row0, d.nclu, d.tc_E);
   const int64_t ns = d.nadm * kTcK * 4;
-  k_tc_slice_s<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(arow_dev, d.adm_col, d.cheb, d.tc_E, d.nadm,
-                                                             (unsigned char *)d.Stc);
+  k_tc_slice_s<ND><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(arow_dev, d.adm_col, d.cheb, d.tc_E, d.nadm,
+                                                                 (unsigned char *)d.Stc);
   H2_CUDA_TRY(cudaGetLastError());
   H2_CUDA_TRY(cudaStreamSynchronize(st));
+  d.tc_nd = ND;
   d.tc = true;
   return H2_OK;
 }
 
-// Upward pass of an FP64-accurate product on the tensor-core path: the
-// transfers of Algorithm 1 with the column maxima and the coefficient slices
-// of every level produced on the way (k_upward_tc), the leaves' maxima before
-// and the slices of the top level after.  Returns the launches made.
-int tc_upward(Ctx &c, void *xhat_v, int rp, int64_t *launches) {
-  dd *xhat = static_cast<dd *>(xhat_v);
+// Upward pass of a product on the tensor-core path: the transfers of
+// Algorithm 1 with the column maxima and the coefficient digits of every
+// level produced on the way (k_upward_tc), the leaves' maxima before and the
+// digits of the top level after.  Returns the launches made.
+template <class T, int ND>
+int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
-  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
   const int D = d.depth, lmin = d.first_adm_level;
   if (lmin > D) return H2_OK;
   const int64_t leaf0 = d.nleaf - 1;
   int64_t nl = 0;
   H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
   const int64_t lrows = d.nleaf * kTcK;
-  k_tc_levmax<<<levmax_grid(lrows), 256, 0, st>>>(xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
+  k_tc_levmax<T><<<levmax_grid(lrows), 256, 0, st>>>(xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
   ++nl;
   const int k = d.k, m = d.m;
   // k = 64, rp <= 16: at most 25,344 bytes, below the 48 KB default limit
-  const size_t sm = std::max<size_t>(((size_t)3 * k * rp + 6 * m * m) * sizeof(dd), kTileB);
+  const size_t sm = std::max<size_t>(((size_t)3 * k * rp + 6 * m * m) * sizeof(T), Dig<ND>::kTileB);
   for (int l = D - 1; l >= lmin; --l) {
     const int64_t par0 = ((int64_t)1 << l) - 1;
-    k_upward_tc<<<(unsigned)((int64_t)1 << l), transfer_threads(l), sm, st>>>((const dd *)d.Ef, m, k, rp, par0, l, xhat, d.tc_xmax,
-                                                                (unsigned char *)d.xtc);
+    k_upward_tc<T, ND><<<(unsigned)((int64_t)1 << l), transfer_threads(l), sm, st>>>(
+        (const T *)d.Ef, m, k, rp, par0, l, xhat, d.tc_xmax, (unsigned char *)d.xtc);
     ++nl;
   }
-  // the top level's slices (the leaves' when there is no transfer)
+  // the top level's digits (the leaves' when there is no transfer)
   const int64_t c0 = ((int64_t)1 << lmin) - 1;
-  k_tc_slice_x<<<(unsigned)((int64_t)1 << lmin), 256, 0, st>>>(xhat, c0, lmin, rp, d.tc_xmax,
-                                                                (unsigned char *)d.xtc);
+  k_tc_slice_x<T, ND><<<(unsigned)((int64_t)1 << lmin), 256, 0, st>>>(xhat, c0, lmin, rp, d.tc_xmax,
+                                                                      (unsigned char *)d.xtc);
   ++nl;
   H2_CUDA_TRY(cudaGetLastError());
   if (launches) *launches = nl;
   return H2_OK;
 }
 
-// the coupling phase: the coefficient slices exist (tc_upward)
-int tc_coupling(Ctx &c, const void *xhat_v, void *yhat_v, int rp) {
-  (void)xhat_v;
-  dd *yhat = static_cast<dd *>(yhat_v);
+template <class T, int ND>
+int tc_coupling_t(Ctx &c, T *yhat, int rp) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
-  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
   const int64_t row0 = ((int64_t)1 << d.first_adm_level) - 1, nrows = d.nclu - row0;
   if (nrows <= 0) return H2_OK;
-  static_assert(kTcSmem <= 227 * 1024, "tensor-core coupling does not fit in shared memory");
-  H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_coupling_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static_assert(tc_smem<ND>() <= 227 * 1024, "tensor-core coupling does not fit in shared memory");
+  H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_coupling_tc<ND, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(227 * 1024)));
   int sms = 0, dev = 0;
   H2_CUDA_TRY(cudaGetDevice(&dev));
   H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = (int)std::min<int64_t>(sms, nrows);
-  k_coupling_tc<<<grid, kTcThreads, kTcSmem, st>>>((const unsigned char *)d.Stc, (const unsigned char *)d.xtc,
-                                                   d.adm_ptr, d.adm_col, d.tc_E, d.tc_xmax, row0, nrows, rp, yhat);
+  k_coupling_tc<ND, T><<<grid, kTcThreads, tc_smem<ND>(), st>>>((const unsigned char *)d.Stc,
+                                                                (const unsigned char *)d.xtc, d.adm_ptr, d.adm_col,
+                                                                d.tc_E, d.tc_xmax, row0, nrows, rp, yhat);
   H2_CUDA_TRY(cudaGetLastError());
   return H2_OK;
+}
+
+}  // namespace
+
+int tc_build(Ctx &c, const int32_t *arow_dev) {
+  Dev &d = c.d;
+  if (d.first_adm_level > d.depth || d.nadm == 0) return H2_OK;
+  return d.prec == H2_F64 ? tc_build_nd<10>(c, arow_dev) : tc_build_nd<6>(c, arow_dev);
+}
+
+int tc_upward(Ctx &c, void *xhat, int rp, int64_t *launches) {
+  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
+  if (c.d.tc_nd == 10) return tc_upward_t<dd, 10>(c, static_cast<dd *>(xhat), rp, launches);
+  return tc_upward_t<float, 6>(c, static_cast<float *>(xhat), rp, launches);
+}
+
+// the coupling phase: the coefficient digits exist (tc_upward)
+int tc_coupling(Ctx &c, const void *xhat, void *yhat, int rp) {
+  (void)xhat;
+  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
+  if (c.d.tc_nd == 10) return tc_coupling_t<dd, 10>(c, static_cast<dd *>(yhat), rp);
+  return tc_coupling_t<float, 6>(c, static_cast<float *>(yhat), rp);
 }
 
 // ---------------------------------------------------------------- nearfield host side
@@ -1073,7 +1146,7 @@ int ntc_near(Ctx &c, const void *xpad_v, void *ypad_v, int rp, int accumulate, i
   const int L = (int)d.lmax;
   H2_CUDA_TRY(cudaMemsetAsync(d.ntc_xmax, 0, sizeof(unsigned) * kTcN, st));
   const int64_t rows = d.nleaf * L;
-  k_tc_levmax<<<levmax_grid(rows), 256, 0, st>>>(xpad, rows, rp, d.ntc_xmax);
+  k_tc_levmax<dd><<<levmax_grid(rows), 256, 0, st>>>(xpad, rows, rp, d.ntc_xmax);
   k_ntc_slice_x<<<(unsigned)d.nleaf, 128, 0, st>>>(xpad, L, rp, d.ntc_xmax, (unsigned char *)d.xnt);
   H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(227 * 1024)));

@@ -334,3 +334,37 @@ def test_tensor_core_nearfield_needs_small_leaves(require_gpu):
     h = H2Matrix(v, f, leaf_size=40, eta=2.0, order=3, prec="f64")
     assert h.stats["leaf_max"] > 21 and h.stats["tensor_near"] == 0
     h.close()
+
+
+@pytest.mark.parametrize("name", ["ico3_m4", "ell3_m4", "cube30_m4"])
+def test_f32_tensor_core_coupling(require_gpu, name):
+    """FP32 handles of order 4 run the coupling on the tensor cores too, with six
+    5-bit digits per value (pairs i + k <= 7): against the oracle and the FP32
+    block-row path within the FP32 tolerance, up to 16 right-hand sides (17 fall
+    back), and bit-reproducible."""
+    import torch
+    v, f, o = _oracle_any(name)
+    make, leaf, eta, m = CASES[name] if name in CASES else TENSOR_CASES[name]
+    ht = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f32")
+    hd = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f32", tensor="off")
+    assert ht.stats["tensor"] == 1 and hd.stats["tensor"] == 0
+    n = f.shape[0]
+    for nrhs in (1, 5, 16, 17):
+        x = I.uniform_rhs(n, nrhs, 3700 + nrhs)
+        ref = o.matvec(x)
+        yt, yd = ht.matvec_host(x), hd.matvec_host(x)
+        assert _rel(yt, ref) <= TOL["f32"], (nrhs, _rel(yt, ref))
+        assert _rel(yt, yd) <= TOL["f32"], (nrhs, _rel(yt, yd))
+    x = np.concatenate([np.ones((n, 1)), 1e-9 * I.uniform_rhs(n, 1, 3800), 1e6 * I.uniform_rhs(n, 1, 3801)], axis=1)
+    ref = o.matvec(x)
+    yt = ht.matvec_host(x)
+    for c in range(3):
+        assert _rel(yt[:, c], ref[:, c]) <= TOL["f32"], (c, _rel(yt[:, c], ref[:, c]))
+    xd = colmajor(torch.from_numpy(I.uniform_rhs(n, 16, 3900)).float().cuda())
+    y1, y2 = colmajor(torch.empty_like(xd)), colmajor(torch.empty_like(xd))
+    ht.matvec(xd, y1)
+    ht.matvec(xd, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    ht.close()
+    hd.close()

@@ -469,6 +469,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       int64_t e = e_begin;
       ColAhead ca(col, e, e_end);
+      const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
       for (; e < e_end; ++e) {
         const int64_t i = e - e_begin;
         const int s = (int)(i % kTcStages);
@@ -476,12 +477,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (i >= kTcStages && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / kTcStages - 1) & 1), abort)) break;
         unsigned char *st = smem + (size_t)s * kStage;
         mbar_expect_tx(&full[s], kStage);
-        // the coefficient digits first (they may come from L2), then S two planes at a time
-        bulk_g2s(st + kTileA, xtc + (int64_t)cb * kTileB, kTileB, &full[s]);
+        // the coefficient digits first (read by every block of their column: kept in
+        // L2), then S two planes at a time (read once: evicted first)
+        bulk_g2s_hint(st + kTileA, xtc + (int64_t)cb * kTileB, kTileB, &full[s], pol_keep);
         const unsigned char *src = Stc + e * (int64_t)kTileA;
 #pragma unroll
         for (int g = 0; g < kTcGroups; ++g)
-          bulk_g2s(st + 2 * g * kSliceA, src + 2 * g * kSliceA, 2 * kSliceA, &full[s]);
+          bulk_g2s_hint(st + 2 * g * kSliceA, src + 2 * g * kSliceA, 2 * kSliceA, &full[s], pol_stream);
       }
       if (*abort) {
         // let the copies in flight land before the CTA leaves (bounded)
@@ -818,6 +820,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       int64_t e = e_begin;
       ColAhead ca(col, e, e_end);
+      const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
       for (; e < e_end; ++e) {
         const int64_t i = e - e_begin;
         const int s = (int)(i % kNtStages);
@@ -825,8 +828,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (i >= kNtStages && !mbar_wait_or_abort(&empty[s], (uint32_t)((i / kNtStages - 1) & 1), abort)) break;
         unsigned char *st = smem + (size_t)s * kNtStage;
         mbar_expect_tx(&full[s], ablk + kNtX);
-        bulk_g2s(st + kNtAreg, xnt + (int64_t)cb * kNtX, kNtX, &full[s]);
-        bulk_g2s(st, Ntc + e * (int64_t)ablk, ablk, &full[s]);
+        bulk_g2s_hint(st + kNtAreg, xnt + (int64_t)cb * kNtX, kNtX, &full[s], pol_keep);
+        bulk_g2s_hint(st, Ntc + e * (int64_t)ablk, ablk, &full[s], pol_stream);
       }
       if (*abort) {
         const int64_t j0 = e - kNtStages > e_begin ? e - kNtStages : e_begin;

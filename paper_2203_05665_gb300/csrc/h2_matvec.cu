@@ -746,6 +746,14 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     int64_t nl = 0;
     if ((rc = tc_upward(c, xhat, rp, &nl))) return rc;
     mk.count(H2_PH_UPWARD, nl);
+  } else if (far && m == 4) {
+    // order 4: register kernels (the z mode product by warp shuffles)
+    for (int l = D - 1; l >= lmin; --l) {
+      const int64_t np = (int64_t)1 << l;
+      k_up_reg<TE, T><<<dim3((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16), 256, 0, st>>>(
+          (const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
+      mk.count(H2_PH_UPWARD);
+    }
   } else if (far) {
     size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_upward<TE, T>, sm))) return rc;
@@ -790,7 +798,14 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     mk.count(H2_PH_COUPLING);
   }
   mk.mark(H2_PH_DOWNWARD);
-  if (far) {
+  if (far && m == 4) {
+    for (int l = lmin; l < D; ++l) {
+      const int64_t np = (int64_t)1 << l;
+      k_down_reg<TE, T><<<dim3((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16), 256, 0, st>>>(
+          (const TE *)d.Ef, rp, np - 1, np, yhat);
+      mk.count(H2_PH_DOWNWARD);
+    }
+  } else if (far) {
     size_t sm = ((size_t)3 * k * rp + 6 * m * m) * sizeof(T);
     if ((rc = set_smem<T>((const void *)k_downward<TE, T>, sm))) return rc;
     for (int l = lmin; l < D; ++l) {

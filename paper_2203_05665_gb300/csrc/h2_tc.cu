@@ -359,36 +359,6 @@ __global__ void __launch_bounds__(256) k_tc_slice_x(const T *__restrict__ xhat, 
   slice_cluster<T, ND>(xhat + c * kTcK * rp, rp, lvl, xmax, tile, xtc + c * (int64_t)Dig<ND>::kTileB);
 }
 
-// Upward step for one parent of level l (Algorithm 1, factored transfers,
-// the generic body) with the two extra tasks of the tensor-core coupling:
-// the column maxima of level l from the parent's coefficients, and the
-// slices of its two children (level l + 1, whose maxima are complete).
-template <class T, int ND>
-__global__ void k_upward_tc(const T *__restrict__ Ef, int m, int k, int rp, int64_t par0, int lvl,
-                            T *__restrict__ xhat, unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ unsigned loc[kTcN];
-  if (threadIdx.x < kTcN) loc[threadIdx.x] = 0u;
-  const int64_t par = par0 + blockIdx.x;
-  upward_parent<T, T>(Ef, m, k, rp, par, xhat, smem_raw);   // ends with the parent written to xhat
-  __syncthreads();
-  // column maxima of the parent (the values this CTA has just written)
-  const int kr = k * rp;
-  for (int i = threadIdx.x; i < kr; i += blockDim.x) {
-    const float v = mag(xhat[par * kr + i]);
-    if (v > 0.0f) atomicMax(&loc[i % rp], __float_as_uint(v));
-  }
-  __syncthreads();
-  if (threadIdx.x < kTcN && loc[threadIdx.x]) atomicMax(&xmax[lvl * kTcN + threadIdx.x], loc[threadIdx.x]);
-  // the children's slices, staged in the (now free) dynamic shared memory
-  unsigned char *tile = smem_raw;
-  for (int ch = 0; ch < 2; ++ch) {
-    const int64_t c = 2 * par + 1 + ch;
-    slice_cluster<T, ND>(xhat + c * kr, rp, lvl + 1, xmax, tile, xtc + c * (int64_t)Dig<ND>::kTileB);
-    __syncthreads();
-  }
-}
-
 __device__ __forceinline__ dd dd_scale(dd v, int e) {
   if (e >= -126 && e <= 127) {
     const float w = pow2f(e);
@@ -1033,8 +1003,9 @@ int tc_build_nd(Ctx &c, const int32_t *arow_dev) {
 
 // Upward pass of a product on the tensor-core path: the transfers of
 // Algorithm 1 with the column maxima and the coefficient digits of every
-// level produced on the way (k_upward_tc), the leaves' maxima before and the
-// digits of the top level after.  Returns the launches made.
+// level produced on the way (k_up_reg), each level's digits cut by
+// k_tc_slice_x once its maxima are complete (the leaves' maxima come from
+// k_tc_levmax).  Returns the launches made.
 template <class T, int ND>
 int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
   Dev &d = c.d;
@@ -1047,14 +1018,14 @@ int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
   const int64_t lrows = d.nleaf * kTcK;
   k_tc_levmax<T><<<levmax_grid(lrows), 256, 0, st>>>(xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
   ++nl;
-  const int k = d.k, m = d.m;
-  // k = 64, rp <= 16: at most 25,344 bytes, below the 48 KB default limit
-  const size_t sm = std::max<size_t>(((size_t)3 * k * rp + 6 * m * m) * sizeof(T), Dig<ND>::kTileB);
   for (int l = D - 1; l >= lmin; --l) {
-    const int64_t par0 = ((int64_t)1 << l) - 1;
-    k_upward_tc<T, ND><<<(unsigned)((int64_t)1 << l), transfer_threads(l), sm, st>>>(
-        (const T *)d.Ef, m, k, rp, par0, l, xhat, d.tc_xmax, (unsigned char *)d.xtc);
-    ++nl;
+    // the digits of level l + 1 (its column maxima are complete), then level l and its maxima
+    const int64_t np = (int64_t)1 << l;
+    k_tc_slice_x<T, ND><<<(unsigned)(2 * np), 256, 0, st>>>(xhat, 2 * np - 1, l + 1, rp, d.tc_xmax,
+                                                            (unsigned char *)d.xtc);
+    k_up_reg<T, T><<<(unsigned)((np + kRegParents - 1) / kRegParents), 256, 0, st>>>(
+        (const T *)d.Ef, rp, np - 1, np, xhat, d.tc_xmax + l * kTcN);
+    nl += 2;
   }
   // the top level's digits (the leaves' when there is no transfer)
   const int64_t c0 = ((int64_t)1 << lmin) - 1;

@@ -701,6 +701,72 @@ int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int R, int64_t
   return launch_rows_r<TS, TC, 1>(rows, cfg, threads, nrows, accumulate, out, st);
 }
 
+
+// Leaf steps (Algorithm 1 at the leaves, x^_t = V_t^T x|t; Algorithm 2 at the
+// leaves, y|t = V_t y^_t) for stored values in the arithmetic type, leaves of
+// at most 32 triangles, k <= 64 and rp <= 16: one CTA per leaf stages V_t
+// and the leaf's vector block in shared memory; in the forward step thread
+// (nu, jq) forms x^[nu][jq + 4u], in the backward step thread (r, jo) forms
+// y[r][jo + 8u], each as one contraction with a single renormalisation.  The
+// generic block-row kernel pipelines many terms per row; a leaf row has one.
+template <class T>
+__global__ void __launch_bounds__(256) k_leaf_fwd_reg(const T *__restrict__ V, const T *__restrict__ xpad, int L,
+                                                      int kp, int k, int rp, T *__restrict__ xleaf) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  T *Vs = reinterpret_cast<T *>(lsm);   // [L][kp]
+  T *xs = Vs + L * kp;                   // [L][rp]
+  const int64_t t = blockIdx.x;
+  const T *vt = V + t * (int64_t)L * kp, *xt = xpad + t * (int64_t)L * rp;
+  for (int i = threadIdx.x; i < L * kp; i += blockDim.x) Vs[i] = vt[i];
+  for (int i = threadIdx.x; i < L * rp; i += blockDim.x) xs[i] = xt[i];
+  __syncthreads();
+  const int nu = threadIdx.x >> 2, jq = threadIdx.x & 3;
+  if (nu >= k) return;
+  T acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = zero_of<T>();
+  for (int r = 0; r < L; ++r) {
+    const T v = Vs[r * kp + nu];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (jq + 4 * u < rp) acc_fma(acc[u], v, xs[r * rp + jq + 4 * u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (jq + 4 * u < rp) {
+      acc_norm(acc[u]);
+      xleaf[(t * k + nu) * rp + jq + 4 * u] = acc[u];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_leaf_bwd_reg(const T *__restrict__ Vt, const T *__restrict__ yleaf, int L,
+                                                      int Lp, int k, int rp, T *__restrict__ ypad) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  T *Vs = reinterpret_cast<T *>(lsm);   // [k][Lp]
+  T *ys = Vs + k * Lp;                   // [k][rp]
+  const int64_t t = blockIdx.x;
+  const T *vt = Vt + t * (int64_t)k * Lp, *yt = yleaf + t * (int64_t)k * rp;
+  for (int i = threadIdx.x; i < k * Lp; i += blockDim.x) Vs[i] = vt[i];
+  for (int i = threadIdx.x; i < k * rp; i += blockDim.x) ys[i] = yt[i];
+  __syncthreads();
+  const int r = threadIdx.x >> 3, jo = threadIdx.x & 7;
+  if (r >= L) return;
+  T acc[2] = {zero_of<T>(), zero_of<T>()};
+  for (int nu = 0; nu < k; ++nu) {
+    const T w = Vs[nu * Lp + r];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (jo + 8 * u < rp) acc_fma(acc[u], w, ys[nu * rp + jo + 8 * u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+    if (jo + 8 * u < rp) {
+      acc_norm(acc[u]);
+      ypad[(t * L + r) * rp + jo + 8 * u] = acc[u];
+    }
+}
+
 // TS: storage type of V, E, S and the nearfield; T: arithmetic and vector
 // type; Tio: type of the caller's x and y.
 template <class TS, class T, class Tio>
@@ -732,7 +798,14 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   k_permute_in<Tio, T><<<grid_for(d.npad * rp), kThreads, 0, st>>>(x, d.n, nrhs, rp, d.pad_src, d.npad, xpad);
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
-  if (far) {
+  // leaf steps with one CTA per leaf when the stored values are in the arithmetic type
+  const bool leaf_reg = std::is_same<TS, T>::value && L <= 32 && k <= 64 && rp <= 16;
+  if (far && leaf_reg) {
+    const size_t sm = (size_t)L * (kp + rp) * sizeof(T);
+    k_leaf_fwd_reg<T><<<(unsigned)d.nleaf, 256, sm, st>>>((const T *)d.V, xpad, L, kp, k, rp,
+                                                         xhat + leaf0 * (int64_t)k * rp);
+    mk.count(H2_PH_LEAF_FORWARD);
+  } else if (far) {
     LeafForwardRows<TS, T> rows{(const TS *)d.V, xpad, vscale, L, kp, rp};
     if ((rc = launch_rows<TS, T>(rows, cf_fwd, t_fwd, Rk, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
     mk.count(H2_PH_LEAF_FORWARD);
@@ -816,7 +889,12 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     }
   }
   mk.mark(H2_PH_LEAF_NEAR);
-  if (far) {
+  if (far && leaf_reg) {
+    const size_t sm = (size_t)k * (Lp + rp) * sizeof(T);
+    k_leaf_bwd_reg<T><<<(unsigned)d.nleaf, 256, sm, st>>>((const T *)d.Vt, yhat + leaf0 * (int64_t)k * rp, L, Lp, k,
+                                                         rp, ypad);
+    mk.count(H2_PH_LEAF_NEAR);
+  } else if (far) {
     LeafBackwardRows<TS, T> rows{(const TS *)d.Vt, yhat, vscale, k, Lp, rp, leaf0};
     if ((rc = launch_rows<TS, T>(rows, cf_back, t_back, RL, d.nleaf, 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);

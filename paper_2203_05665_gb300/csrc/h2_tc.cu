@@ -325,10 +325,17 @@ __device__ __forceinline__ int tc_colexp(unsigned bits) {
 // 64 bytes) in the MMA layout (16 columns x 64 contraction values per
 // plane) and written out with 16-byte stores.  All threads of the CTA take
 // part; the caller synchronises before and after.
-__device__ __forceinline__ long long fixed_of(dd v, int sc) {
-  return llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
+// v 2^sc for the coefficient scalings (|v 2^sc| <= 2^49, |sc| < 252): two
+// power-of-two factors that are normal floats, so the product is exact
+// unless it is far below 1/2, where it rounds to the integer 0 anyway
+__device__ __forceinline__ float scale2(float v, int sc) {
+  const int h = sc >> 1;
+  return v * pow2f(h) * pow2f(sc - h);
 }
-__device__ __forceinline__ long long fixed_of(float v, int sc) { return llrintf(ldexpf(v, sc)); }
+__device__ __forceinline__ long long fixed_of(dd v, int sc) {
+  return llrintf(scale2(v.hi, sc)) + llrintf(scale2(v.lo, sc));
+}
+__device__ __forceinline__ long long fixed_of(float v, int sc) { return llrintf(scale2(v, sc)); }
 
 template <class T, int ND>
 __device__ __forceinline__ void slice_cluster(const T *__restrict__ xc, int rp, int lvl,
@@ -711,7 +718,7 @@ __global__ void __launch_bounds__(128) k_ntc_slice_x(const dd *__restrict__ xpad
     if (mu < L && j < rp) {
       const int sc = kTcFixBits - tc_colexp(xmax[j]);
       const dd v = xpad[(s * L + mu) * rp + j];
-      X = llrintf(ldexpf(v.hi, sc)) + llrintf(ldexpf(v.lo, sc));
+      X = fixed_of(v, sc);
     }
     int sl[kTcSlices];
     split_digits(X, sl);

@@ -703,21 +703,25 @@ int launch_rows(const Rows &rows, const RowCfg &cfg, int threads, int R, int64_t
 
 
 // Leaf steps (Algorithm 1 at the leaves, x^_t = V_t^T x|t; Algorithm 2 at the
-// leaves, y|t = V_t y^_t) for stored values in the arithmetic type, leaves of
-// at most 32 triangles, k <= 64 and rp <= 16: one CTA per leaf stages V_t
+// leaves, y|t = V_t y^_t) for leaves of at most 32 triangles, k <= 64 and
+// rp <= 16: one CTA per leaf stages V_t (converted to the arithmetic type)
 // and the leaf's vector block in shared memory; in the forward step thread
 // (nu, jq) forms x^[nu][jq + 4u], in the backward step thread (r, jo) forms
-// y[r][jo + 8u], each as one contraction with a single renormalisation.  The
-// generic block-row kernel pipelines many terms per row; a leaf row has one.
-template <class T>
-__global__ void __launch_bounds__(256) k_leaf_fwd_reg(const T *__restrict__ V, const T *__restrict__ xpad, int L,
-                                                      int kp, int k, int rp, T *__restrict__ xleaf) {
+// y[r][jo + 8u], each as one contraction with a single renormalisation, then
+// multiplied by the leaf's power-of-two scale (16-bit storage) if there is
+// one.  The generic block-row kernel pipelines many terms per row; a leaf
+// row has one.
+template <class TS, class T>
+__global__ void __launch_bounds__(256) k_leaf_fwd_reg(const TS *__restrict__ V, const T *__restrict__ xpad,
+                                                      const float *__restrict__ vscale, int L, int kp, int k, int rp,
+                                                      T *__restrict__ xleaf) {
   extern __shared__ __align__(16) unsigned char lsm[];
   T *Vs = reinterpret_cast<T *>(lsm);   // [L][kp]
   T *xs = Vs + L * kp;                   // [L][rp]
   const int64_t t = blockIdx.x;
-  const T *vt = V + t * (int64_t)L * kp, *xt = xpad + t * (int64_t)L * rp;
-  for (int i = threadIdx.x; i < L * kp; i += blockDim.x) Vs[i] = vt[i];
+  const TS *vt = V + t * (int64_t)L * kp;
+  const T *xt = xpad + t * (int64_t)L * rp;
+  for (int i = threadIdx.x; i < L * kp; i += blockDim.x) Vs[i] = to_compute<T>(vt[i]);
   for (int i = threadIdx.x; i < L * rp; i += blockDim.x) xs[i] = xt[i];
   __syncthreads();
   const int nu = threadIdx.x >> 2, jq = threadIdx.x & 3;
@@ -731,23 +735,26 @@ __global__ void __launch_bounds__(256) k_leaf_fwd_reg(const T *__restrict__ V, c
     for (int u = 0; u < 4; ++u)
       if (jq + 4 * u < rp) acc_fma(acc[u], v, xs[r * rp + jq + 4 * u]);
   }
+  const float sc = vscale ? vscale[t] : 1.0f;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
     if (jq + 4 * u < rp) {
       acc_norm(acc[u]);
-      xleaf[(t * k + nu) * rp + jq + 4 * u] = acc[u];
+      xleaf[(t * k + nu) * rp + jq + 4 * u] = vscale ? acc[u] * from_double<T>(sc) : acc[u];
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_leaf_bwd_reg(const T *__restrict__ Vt, const T *__restrict__ yleaf, int L,
-                                                      int Lp, int k, int rp, T *__restrict__ ypad) {
+template <class TS, class T>
+__global__ void __launch_bounds__(256) k_leaf_bwd_reg(const TS *__restrict__ Vt, const T *__restrict__ yleaf,
+                                                      const float *__restrict__ vscale, int L, int Lp, int k, int rp,
+                                                      T *__restrict__ ypad) {
   extern __shared__ __align__(16) unsigned char lsm[];
   T *Vs = reinterpret_cast<T *>(lsm);   // [k][Lp]
   T *ys = Vs + k * Lp;                   // [k][rp]
   const int64_t t = blockIdx.x;
-  const T *vt = Vt + t * (int64_t)k * Lp, *yt = yleaf + t * (int64_t)k * rp;
-  for (int i = threadIdx.x; i < k * Lp; i += blockDim.x) Vs[i] = vt[i];
+  const TS *vt = Vt + t * (int64_t)k * Lp;
+  const T *yt = yleaf + t * (int64_t)k * rp;
+  for (int i = threadIdx.x; i < k * Lp; i += blockDim.x) Vs[i] = to_compute<T>(vt[i]);
   for (int i = threadIdx.x; i < k * rp; i += blockDim.x) ys[i] = yt[i];
   __syncthreads();
   const int r = threadIdx.x >> 3, jo = threadIdx.x & 7;
@@ -759,11 +766,12 @@ __global__ void __launch_bounds__(256) k_leaf_bwd_reg(const T *__restrict__ Vt, 
     for (int u = 0; u < 2; ++u)
       if (jo + 8 * u < rp) acc_fma(acc[u], w, ys[nu * rp + jo + 8 * u]);
   }
+  const float sc = vscale ? vscale[t] : 1.0f;
 #pragma unroll
   for (int u = 0; u < 2; ++u)
     if (jo + 8 * u < rp) {
       acc_norm(acc[u]);
-      ypad[(t * L + r) * rp + jo + 8 * u] = acc[u];
+      ypad[(t * L + r) * rp + jo + 8 * u] = vscale ? acc[u] * from_double<T>(sc) : acc[u];
     }
 }
 
@@ -799,11 +807,11 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
   // leaf steps with one CTA per leaf when the stored values are in the arithmetic type
-  const bool leaf_reg = std::is_same<TS, T>::value && L <= 32 && k <= 64 && rp <= 16;
+  const bool leaf_reg = L <= 32 && k <= 64 && rp <= 16;
   if (far && leaf_reg) {
     const size_t sm = (size_t)L * (kp + rp) * sizeof(T);
-    k_leaf_fwd_reg<T><<<(unsigned)d.nleaf, 256, sm, st>>>((const T *)d.V, xpad, L, kp, k, rp,
-                                                         xhat + leaf0 * (int64_t)k * rp);
+    k_leaf_fwd_reg<TS, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TS *)d.V, xpad, vscale, L, kp, k, rp,
+                                                             xhat + leaf0 * (int64_t)k * rp);
     mk.count(H2_PH_LEAF_FORWARD);
   } else if (far) {
     LeafForwardRows<TS, T> rows{(const TS *)d.V, xpad, vscale, L, kp, rp};
@@ -819,12 +827,13 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     int64_t nl = 0;
     if ((rc = tc_upward(c, xhat, rp, &nl))) return rc;
     mk.count(H2_PH_UPWARD, nl);
-  } else if (far && m == 4) {
-    // order 4: register kernels (the z mode product by warp shuffles)
+  } else if (far && (m == 3 || m == 4)) {
+    // orders 3 and 4: register kernels (the z mode product by warp shuffles)
     for (int l = D - 1; l >= lmin; --l) {
       const int64_t np = (int64_t)1 << l;
-      k_up_reg<TE, T><<<dim3((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16), 256, 0, st>>>(
-          (const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
+      const dim3 grid((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16);
+      if (m == 4) k_up_reg<TE, T, 4><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
+      else k_up_reg<TE, T, 3><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
       mk.count(H2_PH_UPWARD);
     }
   } else if (far) {
@@ -871,11 +880,12 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     mk.count(H2_PH_COUPLING);
   }
   mk.mark(H2_PH_DOWNWARD);
-  if (far && m == 4) {
+  if (far && (m == 3 || m == 4)) {
     for (int l = lmin; l < D; ++l) {
       const int64_t np = (int64_t)1 << l;
-      k_down_reg<TE, T><<<dim3((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16), 256, 0, st>>>(
-          (const TE *)d.Ef, rp, np - 1, np, yhat);
+      const dim3 grid((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16);
+      if (m == 4) k_down_reg<TE, T, 4><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, yhat);
+      else k_down_reg<TE, T, 3><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, yhat);
       mk.count(H2_PH_DOWNWARD);
     }
   } else if (far) {
@@ -891,8 +901,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.mark(H2_PH_LEAF_NEAR);
   if (far && leaf_reg) {
     const size_t sm = (size_t)k * (Lp + rp) * sizeof(T);
-    k_leaf_bwd_reg<T><<<(unsigned)d.nleaf, 256, sm, st>>>((const T *)d.Vt, yhat + leaf0 * (int64_t)k * rp, L, Lp, k,
-                                                         rp, ypad);
+    k_leaf_bwd_reg<TS, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TS *)d.Vt, yhat + leaf0 * (int64_t)k * rp,
+                                                             vscale, L, Lp, k, rp, ypad);
     mk.count(H2_PH_LEAF_NEAR);
   } else if (far) {
     LeafBackwardRows<TS, T> rows{(const TS *)d.Vt, yhat, vscale, k, Lp, rp, leaf0};

@@ -1030,7 +1030,7 @@ int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
     const int64_t np = (int64_t)1 << l;
     k_tc_slice_x<T, ND><<<(unsigned)(2 * np), 256, 0, st>>>(xhat, 2 * np - 1, l + 1, rp, d.tc_xmax,
                                                             (unsigned char *)d.xtc);
-    k_up_reg<T, T><<<(unsigned)((np + kRegParents - 1) / kRegParents), 256, 0, st>>>(
+    k_up_reg<T, T, 4><<<(unsigned)((np + kRegParents - 1) / kRegParents), 256, 0, st>>>(
         (const T *)d.Ef, rp, np - 1, np, xhat, d.tc_xmax + l * kTcN);
     nl += 2;
   }

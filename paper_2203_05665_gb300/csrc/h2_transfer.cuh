@@ -174,15 +174,16 @@ __device__ __forceinline__ void downward_parent_warp(const TS *__restrict__ Ef, 
 
 
 // ---------------------------------------------------------------------------
-// Register transfer kernels for m = 4 (k = 64): 64 threads per parent and 16
-// columns (grid.y runs over groups of 16 columns), thread (j, jz) = (column,
-// z index) holds the 4 x 4 slab nu = jx + 4 jy + 16 jz of one column in
-// registers.  The x and y mode products run in registers, the
-// z mode product takes the slab entries of the four threads of the column
-// (adjacent lanes) by warp shuffles.  Every output is formed exactly as in
-// mode_fibres (four multiply-adds, one renormalisation), in the same axis
-// order, so the results equal those of the shared-memory kernels above; the
-// gain is that no CTA-wide barrier separates the three mode products.
+// Register transfer kernels for m = 3 and m = 4 (k = m^3): 64 threads per
+// parent and 16 columns (grid.y runs over groups of 16 columns), thread
+// (j, jz) = (column, z index; jz < m, the fourth lane of a column idles for
+// m = 3) holds the m x m slab nu = jx + m jy + m^2 jz of one column in
+// registers.  The x and y mode products run in registers, the z mode product
+// takes the slab entries of the threads of the column (adjacent lanes) by
+// warp shuffles.  Every output is formed exactly as in mode_fibres (m
+// multiply-adds, one renormalisation), in the same axis order, so the
+// results equal those of the shared-memory kernels above; the gain is that
+// no CTA-wide barrier separates the three mode products.
 constexpr int kRegParents = 4;   // parents per 256-thread CTA
 
 __device__ __forceinline__ float shfl_t(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -192,73 +193,81 @@ __device__ __forceinline__ dd shfl_t(dd v, int src) {
 }
 
 // out[a] = sum_b F[a][b] in[b] (plain, E) or sum_b F[b][a] in[b] (trans, E^T)
-template <class T, bool TRANS>
-__device__ __forceinline__ T mode4_out(const T *F, const T (&in)[4], int a) {
+template <class T, bool TRANS, int M>
+__device__ __forceinline__ T modem_out(const T *F, const T (&in)[M], int a) {
   T acc = zero_of<T>();
 #pragma unroll
-  for (int b = 0; b < 4; ++b) acc_fma(acc, TRANS ? F[b * 4 + a] : F[a * 4 + b], in[b]);
+  for (int b = 0; b < M; ++b) acc_fma(acc, TRANS ? F[b * M + a] : F[a * M + b], in[b]);
   acc_norm(acc);
   return acc;
 }
 
-// the transfer factors of the children of this CTA's parents: F[q][ch][axis][16]
-template <class TS, class T>
-__device__ __forceinline__ void load_factors4(const TS *__restrict__ Ef, int64_t par0, int64_t npar, T (*F)[2][3][16]) {
-  for (int i = threadIdx.x; i < kRegParents * 96; i += blockDim.x) {
-    const int q = i / 96, o = i % 96;
+// the transfer factors of the children of this CTA's parents: F[q][ch][axis][M x M]
+template <class TS, class T, int M>
+__device__ __forceinline__ void load_factors(const TS *__restrict__ Ef, int64_t par0, int64_t npar,
+                                             T (*F)[2][3][M * M]) {
+  constexpr int kPer = 6 * M * M, kChild = 3 * M * M;
+  for (int i = threadIdx.x; i < kRegParents * kPer; i += blockDim.x) {
+    const int q = i / kPer, o = i % kPer;
     const int64_t pi = (int64_t)blockIdx.x * kRegParents + q;
     const int64_t pp = par0 + pi;
-    F[q][o / 48][(o % 48) / 16][o % 16] = pi < npar ? to_compute<T>(Ef[(2 * pp + 1) * 48 + o]) : zero_of<T>();
+    F[q][o / kChild][(o % kChild) / (M * M)][o % (M * M)] =
+        pi < npar ? to_compute<T>(Ef[(2 * pp + 1) * kChild + o]) : zero_of<T>();
   }
   __syncthreads();
 }
 
 // Downward (Algorithm 2): y^_c += E_c y^_parent for both children of parents
 // par0 .. par0 + npar - 1.
-template <class TS, class T>
+template <class TS, class T, int M>
 __global__ void __launch_bounds__(256, 2) k_down_reg(const TS *__restrict__ Ef, int rp, int64_t par0, int64_t npar,
                                                      T *__restrict__ yhat) {
-  __shared__ T F[kRegParents][2][3][16];
-  load_factors4<TS, T>(Ef, par0, npar, F);
+  constexpr int K = M * M * M;
+  __shared__ T F[kRegParents][2][3][M * M];
+  load_factors<TS, T, M>(Ef, par0, npar, F);
   const int pl = threadIdx.x >> 6, t = threadIdx.x & 63, j = (t >> 2) + 16 * blockIdx.y, jz = t & 3;
   const int64_t pi = (int64_t)blockIdx.x * kRegParents + pl, par = par0 + pi;
-  const bool act = pi < npar && j < rp;
+  const bool act = pi < npar && j < rp && jz < M;
   const int base = (threadIdx.x & 31) & ~3;
-  T v[4][4];
+  const int zq = jz < M ? jz : 0;   // the idle fourth lane of m = 3 computes a copy of lane 0
+  T v[M][M];
 #pragma unroll
-  for (int jy = 0; jy < 4; ++jy)
+  for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-    for (int jx = 0; jx < 4; ++jx) v[jy][jx] = act ? yhat[(par * 64 + jx + 4 * jy + 16 * jz) * rp + j] : zero_of<T>();
+    for (int jx = 0; jx < M; ++jx) v[jy][jx] = act ? yhat[(par * K + jx + M * jy + M * M * jz) * rp + j] : zero_of<T>();
 #pragma unroll 1
   for (int ch = 0; ch < 2; ++ch) {
     const T *Fx = F[pl][ch][0], *Fy = F[pl][ch][1], *Fz = F[pl][ch][2];
     const int64_t c = 2 * par + 1 + ch;
     // the child's current values, loaded before the arithmetic
-    T yc[4][4];
+    T yc[M][M];
 #pragma unroll
-    for (int jy = 0; jy < 4; ++jy)
+    for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-      for (int jx = 0; jx < 4; ++jx) yc[jy][jx] = act ? yhat[(c * 64 + jx + 4 * jy + 16 * jz) * rp + j] : zero_of<T>();
-    T a[4][4], b[4][4];
+      for (int jx = 0; jx < M; ++jx)
+        yc[jy][jx] = act ? yhat[(c * K + jx + M * jy + M * M * jz) * rp + j] : zero_of<T>();
+    T a[M][M], b[M][M];
 #pragma unroll
-    for (int jy = 0; jy < 4; ++jy)
+    for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-      for (int jx = 0; jx < 4; ++jx) a[jy][jx] = mode4_out<T, false>(Fx, v[jy], jx);
+      for (int jx = 0; jx < M; ++jx) a[jy][jx] = modem_out<T, false, M>(Fx, v[jy], jx);
 #pragma unroll
-    for (int jx = 0; jx < 4; ++jx) {
-      const T col[4] = {a[0][jx], a[1][jx], a[2][jx], a[3][jx]};
+    for (int jx = 0; jx < M; ++jx) {
+      T col[M];
 #pragma unroll
-      for (int jy = 0; jy < 4; ++jy) b[jy][jx] = mode4_out<T, false>(Fy, col, jy);
+      for (int jy = 0; jy < M; ++jy) col[jy] = a[jy][jx];
+#pragma unroll
+      for (int jy = 0; jy < M; ++jy) b[jy][jx] = modem_out<T, false, M>(Fy, col, jy);
     }
 #pragma unroll
-    for (int jy = 0; jy < 4; ++jy)
+    for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-      for (int jx = 0; jx < 4; ++jx) {
-        T in[4];
+      for (int jx = 0; jx < M; ++jx) {
+        T in[M];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) in[q] = shfl_t(b[jy][jx], base + q);
-        const T r = mode4_out<T, false>(Fz, in, jz);
-        if (act) yhat[(c * 64 + jx + 4 * jy + 16 * jz) * rp + j] = yc[jy][jx] + r;
+        for (int q = 0; q < M; ++q) in[q] = shfl_t(b[jy][jx], base + q);
+        const T r = modem_out<T, false, M>(Fz, in, zq);
+        if (act) yhat[(c * K + jx + M * jy + M * M * jz) * rp + j] = yc[jy][jx] + r;
       }
   }
 }
@@ -270,55 +279,60 @@ __device__ __forceinline__ float mag_of(float v) { return fabsf(v); }
 __device__ __forceinline__ float mag_of(double v) { return (float)fabs(v); }
 __device__ __forceinline__ float mag_of(dd v) { return fabsf(v.hi); }
 
-template <class TS, class T>
+template <class TS, class T, int M>
 __global__ void __launch_bounds__(256, 2) k_up_reg(const TS *__restrict__ Ef, int rp, int64_t par0, int64_t npar,
                                                    T *__restrict__ xhat, unsigned *__restrict__ xmax) {
-  __shared__ T F[kRegParents][2][3][16];
+  constexpr int K = M * M * M;
+  __shared__ T F[kRegParents][2][3][M * M];
   __shared__ unsigned loc[16];
   if (threadIdx.x < 16) loc[threadIdx.x] = 0u;
-  load_factors4<TS, T>(Ef, par0, npar, F);
+  load_factors<TS, T, M>(Ef, par0, npar, F);
   const int pl = threadIdx.x >> 6, t = threadIdx.x & 63, j = (t >> 2) + 16 * blockIdx.y, jz = t & 3;
   const int64_t pi = (int64_t)blockIdx.x * kRegParents + pl, par = par0 + pi;
-  const bool act = pi < npar && j < rp;
+  const bool act = pi < npar && j < rp && jz < M;
   const int base = (threadIdx.x & 31) & ~3;
-  T out[4][4];
+  const int zq = jz < M ? jz : 0;
+  T out[M][M];
 #pragma unroll 1
   for (int ch = 0; ch < 2; ++ch) {
     const int64_t c = 2 * par + 1 + ch;
     const T *Fx = F[pl][ch][0], *Fy = F[pl][ch][1], *Fz = F[pl][ch][2];
-    T v[4][4], a[4][4], b[4][4];
+    T v[M][M], a[M][M], b[M][M];
 #pragma unroll
-    for (int jy = 0; jy < 4; ++jy)
+    for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-      for (int jx = 0; jx < 4; ++jx) v[jy][jx] = act ? xhat[(c * 64 + jx + 4 * jy + 16 * jz) * rp + j] : zero_of<T>();
+      for (int jx = 0; jx < M; ++jx)
+        v[jy][jx] = act ? xhat[(c * K + jx + M * jy + M * M * jz) * rp + j] : zero_of<T>();
 #pragma unroll
-    for (int jy = 0; jy < 4; ++jy)
+    for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-      for (int jx = 0; jx < 4; ++jx) a[jy][jx] = mode4_out<T, true>(Fx, v[jy], jx);
+      for (int jx = 0; jx < M; ++jx) a[jy][jx] = modem_out<T, true, M>(Fx, v[jy], jx);
 #pragma unroll
-    for (int jx = 0; jx < 4; ++jx) {
-      const T col[4] = {a[0][jx], a[1][jx], a[2][jx], a[3][jx]};
+    for (int jx = 0; jx < M; ++jx) {
+      T col[M];
 #pragma unroll
-      for (int jy = 0; jy < 4; ++jy) b[jy][jx] = mode4_out<T, true>(Fy, col, jy);
+      for (int jy = 0; jy < M; ++jy) col[jy] = a[jy][jx];
+#pragma unroll
+      for (int jy = 0; jy < M; ++jy) b[jy][jx] = modem_out<T, true, M>(Fy, col, jy);
     }
 #pragma unroll
-    for (int jy = 0; jy < 4; ++jy)
+    for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-      for (int jx = 0; jx < 4; ++jx) {
-        T in[4];
+      for (int jx = 0; jx < M; ++jx) {
+        T in[M];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) in[q] = shfl_t(b[jy][jx], base + q);
-        const T r = mode4_out<T, true>(Fz, in, jz);
+        for (int q = 0; q < M; ++q) in[q] = shfl_t(b[jy][jx], base + q);
+        const T r = modem_out<T, true, M>(Fz, in, zq);
         out[jy][jx] = ch == 0 ? zero_of<T>() + r : out[jy][jx] + r;
       }
   }
   float mx = 0.0f;
 #pragma unroll
-  for (int jy = 0; jy < 4; ++jy)
+  for (int jy = 0; jy < M; ++jy)
 #pragma unroll
-    for (int jx = 0; jx < 4; ++jx) {
-      if (act) xhat[(par * 64 + jx + 4 * jy + 16 * jz) * rp + j] = out[jy][jx];
-      mx = fmaxf(mx, mag_of(out[jy][jx]));
+    for (int jx = 0; jx < M; ++jx) {
+      if (act) xhat[(par * K + jx + M * jy + M * M * jz) * rp + j] = out[jy][jx];
+      if (act) mx = fmaxf(mx, mag_of(out[jy][jx]));
     }
   if (xmax) {
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
@@ -328,5 +342,6 @@ __global__ void __launch_bounds__(256, 2) k_up_reg(const TS *__restrict__ Ef, in
     if (threadIdx.x < 16 && loc[threadIdx.x]) atomicMax(&xmax[threadIdx.x], loc[threadIdx.x]);
   }
 }
+
 }  // namespace
 }  // namespace h2

@@ -344,7 +344,8 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"f64": "f32x2 (double-float, FP64-accurate)", "f32": "f32",
+        "vs_baseline": None, "dtype": {"f64": "f32x2 (double-float) with exact e4m3 digit products on the tensor cores "
+                                              "(FP64-accurate)", "f32": "f32",
                                        "f64n": "f64", "bf16": "bf16 storage, f32 arithmetic",
                                        "f16": "f16 storage, f32 arithmetic"}[args.prec], "data": "synthetic",
         "config": {"workload": f"icosphere L{args.level} ({n} triangles), m={args.order} (k={args.order ** 3}), "

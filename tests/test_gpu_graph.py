@@ -5,7 +5,8 @@ same buffers, so its output must equal h2_matvec's bit for bit; new values
 written into the captured input buffer must be picked up by the next replay;
 and a graph whose handle reallocated its work space must be refused, not run
 on freed memory.  One case per coupling path (double-float FP64, tensor-core
-FP64, FP32 stored, FP32 regenerated) is also checked against the oracle.
+FP64, FP32 stored, tensor-core FP32, FP32 regenerated) is also checked
+against the oracle.
 """
 import numpy as np
 import pytest
@@ -22,6 +23,7 @@ CASES = [
     (4, 3, "f64", "stored", 1),     # the 5,120-triangle configuration, one right-hand side
     (3, 4, "f64", "stored", 5),     # the coupling on the tensor cores
     (4, 3, "f32", "stored", 2),
+    (3, 4, "f32", "stored", 4),     # FP32 coupling on the tensor cores
     (3, 4, "f32", "regen", 3),
 ]
 
@@ -32,7 +34,7 @@ def test_graph_replay_matches_matvec_and_oracle(require_gpu, level, order, prec,
     v, f = I.icosphere(level)
     n = f.shape[0]
     h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=order, prec=prec, coupling=coupling)
-    if prec == "f64" and order == 4:
+    if order == 4 and coupling == "stored":
         assert h.stats["tensor"] == 1
     dt = torch.float64 if prec == "f64" else torch.float32
     x = colmajor(torch.zeros((n, nrhs), dtype=dt, device="cuda"))

@@ -81,9 +81,10 @@ typedef struct h2_options {
                       * entry, a power of two per row) and runs the coupling phase of products with
                       * up to 16 right-hand sides on the tensor cores (integer digit products summed
                       * exactly, combined in double-float; agrees with the double-float path to
-                      * about 1e-13); likewise any H2_F64 handle with leaves of at most 21
-                      * triangles keeps its nearfield blocks as such digits and runs the
-                      * nearfield phase on the tensor cores; 1: never */
+                      * about 1e-13); an H2_F32 handle of order 4 with stored coupling does the
+                      * same with 6 digits (6 bytes per entry, FP32 accuracy); any H2_F64 handle
+                      * with leaves of at most 21 triangles keeps its nearfield blocks as 10-digit
+                      * planes and runs the nearfield phase on the tensor cores; 1: never */
   int reserved[6];   /* must be zero */
 } h2_options;
 

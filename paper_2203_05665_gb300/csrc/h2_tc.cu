@@ -1,11 +1,13 @@
-// FP64-accurate coupling phase on the tensor cores (tcgen05, FP8 E4M3
-// operands, FP32 accumulation in tensor memory), for order m = 4 (k = 64) and
-// up to 16 right-hand sides.
+// Coupling and nearfield phases on the tensor cores (tcgen05, FP8 E4M3
+// operands, FP32 accumulation in tensor memory), up to 16 right-hand sides:
+// the coupling of order-4 handles (k = 64) in FP64 accuracy (ten digits per
+// value) or FP32 accuracy (six digits), and the FP64-accurate nearfield of
+// handles whose leaves hold at most 21 triangles (second part of the file).
 //
 // GB300 runs FP64 at 1/58 of its FP32 rate, and double-float arithmetic on
 // the FP32 pipe leaves the coupling (Algorithm 3, y^_t = sum S_ts x^_s)
 // bound by instruction issue far below the memory roofline.  This path
-// computes the same sums exactly enough for FP64 parity with integer slices
+// computes the same sums exactly enough for FP64 parity with integer digits
 // on the tensor cores (the splitting scheme of Ozaki et al.):
 //
 //  * every row nu of the coupling matrices of row cluster t gets a power of
@@ -19,8 +21,9 @@
 //    tensor cores accumulate it exactly in FP32, and the at most five D_ik
 //    of one level i + k add exactly in FP32 too;
 //  * y^_t[nu][j] = 2^(E + F) sum_{i + k <= 11} 2^(2-5(i+k)) D_ik, the ten
-//    levels summed in double-float; the dropped pairs and the rounding of X stay below 2^-46
-//    of the row's scale.
+//    levels summed in double-float; the dropped pairs and the rounding of X
+//    stay below 2^-46 of the row's scale.  With six digits (FP32 handles):
+//    |X| <= 2^29, pairs i + k <= 7, below 2^-27.
 //
 // The digits of S are cut once at set-up, straight into the layout the
 // tensor cores read from shared memory (K-major, 8 x 16-byte core matrices,
@@ -32,14 +35,15 @@
 // each, 10 instructions per block; the epilogue reads the 55 pairs with
 // i + k <= 11 (480 accumulator columns).
 //
-// Kernel roles (one CTA per SM, 6 warps): warp 0 streams the slices of each
-// block through a 4-stage shared-memory ring (bulk copies completing on
-// mbarriers), warp 1 allocates tensor memory and issues the MMAs of a row
-// segment (at most 64 blocks) into the accumulators, warps 2-5
-// read it back (tcgen05.ld), add the pairs of each level in FP32 and the levels in double-float, and write
-// y^_t.  Every wait is bounded; on a timeout the device error word
-// is raised, every role stops, copies and MMAs in flight are waited for and
-// the tensor memory is released before the CTA exits.
+// Kernel roles (one CTA per SM, 6 warps): warp 0 streams the digits of each
+// block through a shared-memory ring (bulk copies completing on mbarriers;
+// the digit stream evict-first in L2, the coefficient tiles evict-last),
+// warp 1 allocates tensor memory and issues the MMAs of a row segment (at
+// most 64 blocks) into the accumulators, warps 2-5 read it back
+// (tcgen05.ld), add the pairs of each level in FP32 and the levels in
+// double-float, and write y^_t.  Every wait is bounded; on a timeout the
+// device error word is raised, every role stops, copies and MMAs in flight
+// are waited for and the tensor memory is released before the CTA exits.
 #include <cuda_fp8.h>
 
 #include <algorithm>

@@ -189,8 +189,8 @@ int h2_matvec_noalloc(h2_handle h, const void *x, void *y, int nrhs);
 /* The product captured once into a CUDA graph for fixed device buffers x, y
  * (as for h2_matvec) and replayed: h2_graph_launch runs y = G~ x
  * asynchronously on the handle's stream with the launch cost of one graph
- * (the product is 20 to 40 kernels).  The paper has no counterpart; the
- * GB300 build uses graphs where a tracing compiler would be used elsewhere.
+ * (the product is 20 to 40 kernels).  The paper has no counterpart: a CUDA
+ * graph takes the place a tracing compiler would take elsewhere.
  * The graph refers to the handle's work space: a later product with more
  * right-hand sides than any before reallocates it, after which
  * h2_graph_launch returns H2_EINVAL.  Destroy graphs before their handle;

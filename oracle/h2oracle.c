@@ -24,7 +24,7 @@
  * GMRES is Saad's restarted GMRES with modified Gram-Schmidt and Givens
  * rotations (Saad, Iterative Methods for Sparse Linear Systems, Alg. 6.9).
  *
- * Readings where the paper is silent (each is also listed in the design notes):
+ * Readings where the paper is silent (the library follows the same ones):
  *   R1 characteristic point = centroid ((a+b)+c)/3; box = min/max of vertices.
  *   R2 binary tree, every cluster above depth D is split, D the smallest depth
  *      with ceil(n/2^D) <= leaf_size; split axis = longest extent of the

@@ -137,6 +137,53 @@ def test_singular_entries_match_closed_form_potential(mode, T2):
     assert abs(extrap - ss) < 1e-7 * ss
 
 
+def _mesh_pairs(f, i):
+    """Partners of triangle i by the number of shared vertex ids: (3: i itself, 2: the
+    edge neighbours, 1: the vertex neighbours)."""
+    sets = [set(t) for t in f.tolist()]
+    out = {3: [i], 2: [], 1: []}
+    for j, sj in enumerate(sets):
+        k = len(sets[i] & sj)
+        if j != i and k in (1, 2):
+            out[k].append(j)
+    return out
+
+
+@pytest.mark.parametrize("i", [0, 77, 203])
+def test_mesh_pair_classifier_against_closed_form(i):
+    """The oracle classifies every pair of mesh triangles as identical, common edge,
+    common vertex or regular from shared global vertex ids and reorders their
+    vertices before the Sauter-Schwab maps.  Here oracle.entry(i, j) for real
+    icosphere pairs of every kind, every local position of the shared edge or
+    vertex and both index orders, is checked against the outer rule over the
+    closed-form inner potential of the triangles as the mesh stores them, which
+    involves neither the classification nor the reordering."""
+    v, f = I.icosphere(2)
+    o = Oracle(v, f, leaf_size=8, eta=2.0, order=2, store_near=False)
+    part = _mesh_pairs(f, i)
+    assert len(part[2]) == 3 and len(part[1]) >= 6
+    # all three edges, and vertex neighbours around every corner of triangle i
+    corners = {}
+    for j in part[1]:
+        shared = (set(f[i].tolist()) & set(f[j].tolist())).pop()
+        corners.setdefault(int(np.where(f[i] == shared)[0][0]), j)
+    assert len(corners) == 3
+    pairs = [(i, i)] + [(i, j) for j in part[2]] + [(i, j) for j in corners.values()]
+    pairs += [(j, i) for j in part[2][:1]] + [(j, i) for j in list(corners.values())[:1]]
+    for a, b in pairs:
+        g = o.entry(int(a), int(b), 12)
+        Ta, Tb = v[f[a]], v[f[b]]
+        a2 = _outer_integral(Ta, Tb, 8, 2)
+        a3 = _outer_integral(Ta, Tb, 8, 3)
+        extrap = a3 + (a3 - a2) / 3.0
+        assert abs(extrap - g) < 2e-7 * g, (a, b, g, extrap)
+    # a regular pair next to i (no shared vertex) takes the plain rule: same check
+    near = np.argsort(np.linalg.norm(v[f].mean(axis=1) - v[f[i]].mean(axis=0), axis=1))
+    j = next(int(j) for j in near if not set(f[j].tolist()) & set(f[i].tolist()))
+    g = o.entry(int(i), j, 12)
+    assert abs(_outer_integral(v[f[i]], v[f[j]], 8, 1) - g) < 1e-9 * g
+
+
 # ---------------------------------------------------------------- trees
 def test_cluster_tree_definition_1(l3):
     v, f, o = l3

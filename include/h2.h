@@ -54,11 +54,18 @@ enum h2_status {
  *   H2_F32        FP32 storage and arithmetic; vectors are float.
  *   H2_F64_NATIVE FP64 storage and arithmetic on the FP64 pipe (1/58 of the
  *                 FP32 rate on GB300); vectors are double.
- *   H2_BF16       V, transfer factors and nearfield stored in bfloat16, FP32
- *                 accumulation, coupling regenerated in FP32; vectors float.
- *   H2_F16        as H2_BF16 with IEEE half storage; every nearfield block and
- *                 every leaf basis carries a power-of-two scale so that its
- *                 entries (of size h^2 to h^4) stay in the half range. */
+ *   H2_BF16       nearfield stored in bfloat16 except the self blocks G_jj of
+ *                 the leaves (they hold the largest entries of every row, the
+ *                 singular g_ii among them; FP32, about a tenth of the
+ *                 nearfield), leaf bases and transfer factors in FP32 unless
+ *                 basis_prec asks for bfloat16 V, FP32 accumulation, coupling
+ *                 regenerated in FP32; vectors float.
+ *   H2_F16        nearfield, leaf bases and transfer factors in IEEE half
+ *                 (basis_prec may ask for FP32 bases), FP32 accumulation,
+ *                 coupling regenerated in FP32; every nearfield block and
+ *                 every half-precision leaf basis carries a power-of-two scale
+ *                 so that its entries (of size h^2 to h^4) stay in the half
+ *                 range. */
 enum h2_prec { H2_F64 = 0, H2_F32 = 1, H2_F64_NATIVE = 2, H2_BF16 = 3, H2_F16 = 4 };
 
 /* coupling matrices S_ts (Eq. (6c)):
@@ -85,7 +92,16 @@ typedef struct h2_options {
                       * same with 6 digits (6 bytes per entry, FP32 accuracy); any H2_F64 handle
                       * with leaves of at most 21 triangles keeps its nearfield blocks as 10-digit
                       * planes and runs the nearfield phase on the tensor cores; 1: never */
-  int reserved[6];   /* must be zero */
+  int basis_prec;    /* storage of the leaf bases V (Eq. (6a)) and the transfer factors (Eq. (9))
+                      * of H2_BF16 / H2_F16 handles: 0 = the default, H2_F32 for H2_BF16 (V in
+                      * bfloat16 costs about 1e-3 of relative accuracy, amplified by the Lebesgue
+                      * constant of the interpolation, which leaves no room under 2e-3) and the
+                      * handle's own type for H2_F16; H2_F32 or the handle's own 16-bit type may
+                      * be asked for explicitly (H2_BF16 keeps its transfer factors in FP32
+                      * either way).  Other precisions store V and E in their own type and
+                      * accept only 0.  The nearfield is always stored in prec, and the coupling
+                      * is stored in prec or regenerated in FP32 (field coupling). */
+  int reserved[5];   /* must be zero */
 } h2_options;
 
 /* Statistics of a built matrix (h2_info). */
@@ -105,6 +121,7 @@ typedef struct h2_stats {
   int64_t coupling;       /* H2_COUPLING_STORED or H2_COUPLING_REGEN as built */
   int64_t tensor;         /* 1 if the tensor-core digits of the coupling were built */
   int64_t tensor_near;    /* 1 if the tensor-core digits of the nearfield were built */
+  int64_t basis_prec;     /* enum h2_prec of the stored leaf bases V */
 } h2_stats;
 
 /* Per right-hand side result of h2_solve. */
@@ -151,6 +168,10 @@ int h2_plan_bases(h2_plan p, double *V, double *E);
  * Build the H^2 matrix on the device: plan as above, coupling matrices
  * S_ts = g(xi_t, xi_s) (Eq. (6c)) and Sauter-Schwab nearfield entries of
  * Eq. (3), stored in opt->prec.  opt may be NULL (defaults).
+ * Range of H2_F64 (pairs of FP32 numbers, FP32's exponent range): the mesh
+ * must satisfy amin^2 / (4 pi D) >= 2^-96 and amax <= 2^60 (amin, amax the
+ * smallest and largest triangle area, D the diameter of the mesh's bounding
+ * box), else H2_EINVAL; rescale the mesh or use H2_F64_NATIVE.
  * Errors: H2_EINVAL, H2_ENOMEM (device memory), H2_ECUDA.
  * ------------------------------------------------------------------------- */
 int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
@@ -162,10 +183,21 @@ int h2_info(h2_handle h, h2_stats *out);
  * paper's y <- y + G x with y cleared first).  x, y: DEVICE pointers to
  * column-major n x nrhs arrays of the handle's vector type (double for H2_F64
  * and H2_F64_NATIVE, float for H2_F32); they must not overlap.  Asynchronous on the handle's
- * stream.  1 <= nrhs <= 64.
+ * stream.  1 <= nrhs <= 64.  H2_F64 handles accept any finite double: a
+ * column whose largest entry lies outside [2^-40, 2^40] is scaled by a power
+ * of two on the way in and back on the way out (exact), so it keeps FP64-level
+ * relative accuracy; zero, infinite and NaN columns are passed as they are.
  * Errors: H2_EINVAL (NULL, nrhs out of range), H2_ENOMEM (work buffers),
  * H2_ECUDA (launch failure). */
 int h2_matvec(h2_handle h, const void *x, void *y, int nrhs);
+
+/* y <- y + G~ x: the product in the accumulating form in which Section 2
+ * states it (Algorithms 1-3 add into the output).  Arguments, layout, types,
+ * stream and errors as for h2_matvec; y must hold valid values of the
+ * vector type on entry.  The sum is formed once, in the last step that
+ * writes the caller's y (cluster order -> caller order), so it costs one
+ * extra read of y and no extra launch. */
+int h2_matvec_acc(h2_handle h, const void *x, void *y, int nrhs);
 
 /* The same product as h2_matvec for callers that cannot allocate device
  * memory when they multiply (an allocator owned by another runtime, a
@@ -210,6 +242,26 @@ int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs);
  * downward transfer (as used by the leaf backward step).  out: HOST double
  * array [clusters][k][nrhs] of the last product's nrhs. */
 int h2_coefficients(h2_handle h, int which, double *out);
+
+/* The stored representation as built on the device, converted to double
+ * (diagnostics: it lets the set-up be checked entry by entry).  Items:
+ *   H2_EXPORT_NEAR      nearfield blocks G_b (Eq. (3), Sauter-Schwab quadrature)
+ *                       first .. first+count-1 in the order of h2_plan_blocks'
+ *                       inadmissible list; out[(i lmax + t) lmax + c] = entry
+ *                       (test triangle t, trial triangle c) in leaf-local
+ *                       cluster order, zero for padding.
+ *   H2_EXPORT_COUPLING  coupling matrices S_b (Eq. (6c)) of admissible blocks
+ *                       first .. in h2_plan_blocks' admissible order (stored
+ *                       coupling only); out[(i k + nu) k + mu].
+ *   H2_EXPORT_V         leaf basis rows (Eq. (6a)) of padded degrees of freedom
+ *                       first .. (leaf j owns rows j lmax .. j lmax + lmax - 1);
+ *                       out[i k + nu].
+ *   H2_EXPORT_E         transfer factors (Eq. (9)) of clusters first ..;
+ *                       out[((i 3 + axis) m + j') m + j].
+ * Synchronises the handle's stream.  Errors: H2_EINVAL for an unknown item
+ * or a range out of bounds. */
+enum h2_export_item { H2_EXPORT_NEAR = 0, H2_EXPORT_COUPLING = 1, H2_EXPORT_V = 2, H2_EXPORT_E = 3 };
+int h2_export(h2_handle h, int what, int64_t first, int64_t count, double *out);
 
 /* Solve G~ z = b by restarted GMRES(restart) per column, z0 = 0, in FP64
  * arithmetic around the handle's product.  b, z: column-major n x nrhs
@@ -352,6 +404,27 @@ int h2_batch_info(h2_batch b, int64_t *info);
 /* Wait for the batch's products; H2_ETIMEOUT if a bounded device wait ran out. */
 int h2_batch_sync(h2_batch b);
 int h2_batch_destroy(h2_batch b);
+
+/* ---------------------------------------------------------------------------
+ * Failure injection and self-tests of the error paths (no counterpart in the
+ * paper; they make failures happen on the host or inside a bounded wait,
+ * never as a GPU fault).
+ * ------------------------------------------------------------------------- */
+/* Make the device allocation `after` allocations from now (0 = the next one)
+ * of any thread fail as if the device were out of memory; -1 cancels a
+ * pending injection.  One failure per call.  Every entry point that
+ * allocates must then return H2_ENOMEM and release what it had allocated. */
+int h2_inject_alloc_failure(int64_t after);
+
+/* Run the library's bounded-wait machinery in miniature on the handle's
+ * stream: a producer thread fills a ring of four shared-memory stages with
+ * bulk copies completing on mbarriers, a consumer thread waits for each stage
+ * with at most poll_limit polls (0 = the limit the product kernels use).
+ * withhold = 1: the producer never fills the last stage, so that wait runs
+ * out, raises the device error word and the call returns H2_ETIMEOUT (the
+ * error is read and cleared, the handle stays usable); withhold = 0: H2_OK.
+ * *stages_seen (may be NULL) receives the stages the consumer saw complete. */
+int h2_wait_selftest(h2_handle h, int withhold, uint32_t poll_limit, int *stages_seen);
 
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char *h2_last_error(void);

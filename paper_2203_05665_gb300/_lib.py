@@ -31,14 +31,14 @@ class H2Error(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("quad_order", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-                ("coupling", C.c_int), ("tensor", C.c_int), ("reserved", C.c_int * 6)]
+                ("coupling", C.c_int), ("tensor", C.c_int), ("basis_prec", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("n", "depth", "clusters", "leaf_max", "order", "rank", "adm_blocks", "near_blocks",
                  "near_entries", "first_adm_level", "device_bytes", "prec", "coupling", "tensor",
-                 "tensor_near")]
+                 "tensor_near", "basis_prec")]
 
 
 class SolveInfo(C.Structure):
@@ -46,13 +46,13 @@ class SolveInfo(C.Structure):
 
 
 EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_counts", "h2_plan_tree",
-            "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec",
+            "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec", "h2_matvec_acc",
             "h2_matvec_noalloc", "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
             "h2_serve_create", "h2_serve_register", "h2_serve_submit", "h2_serve_poll", "h2_serve_wait",
             "h2_serve_stats", "h2_serve_destroy", "h2_batch_create", "h2_batch_offsets", "h2_batch_matvec",
             "h2_batch_tune", "h2_batch_set_shapes", "h2_batch_profile", "h2_batch_phase_times", "h2_batch_info",
             "h2_batch_sync", "h2_batch_destroy", "h2_graph_create", "h2_graph_launch", "h2_graph_destroy",
-            "h2_last_error"]
+            "h2_inject_alloc_failure", "h2_wait_selftest", "h2_export", "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -84,6 +84,7 @@ def load():
             "h2_destroy": (C.c_int, [vp]),
             "h2_info": (C.c_int, [vp, C.POINTER(Stats)]),
             "h2_matvec": (C.c_int, [vp, vp, vp, C.c_int]),
+            "h2_matvec_acc": (C.c_int, [vp, vp, vp, C.c_int]),
             "h2_matvec_noalloc": (C.c_int, [vp, vp, vp, C.c_int]),
             "h2_matvec_host": (C.c_int, [vp, dp, dp, C.c_int]),
             "h2_coefficients": (C.c_int, [vp, C.c_int, dp]),
@@ -112,6 +113,9 @@ def load():
             "h2_graph_create": (C.c_int, [vp, vp, vp, C.c_int, C.POINTER(vp)]),
             "h2_graph_launch": (C.c_int, [vp]),
             "h2_graph_destroy": (C.c_int, [vp]),
+            "h2_inject_alloc_failure": (C.c_int, [C.c_int64]),
+            "h2_export": (C.c_int, [vp, C.c_int, C.c_int64, C.c_int64, dp]),
+            "h2_wait_selftest": (C.c_int, [vp, C.c_int, C.c_uint32, C.POINTER(C.c_int)]),
             "h2_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -198,7 +202,7 @@ class H2Matrix:
     """An H² matrix of one mesh on one GPU (see include/h2.h)."""
 
     def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, prec="f64", quad_order=3, device=0,
-                 stream=None, coupling="auto", tensor="auto"):
+                 stream=None, coupling="auto", tensor="auto", basis=None):
         lib = load()
         v, t = _mesh(vert, tri)
         opt = Options()
@@ -209,6 +213,7 @@ class H2Matrix:
         opt.stream = stream
         opt.coupling = COUPLING[coupling]
         opt.tensor = {"auto": 0, "off": 1}[tensor]
+        opt.basis_prec = 0 if basis is None else PREC[basis]
         h = C.c_void_p()
         _check(lib.h2_build(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
                             int(leaf_size), float(eta), int(order), C.byref(opt), C.byref(h)))
@@ -243,6 +248,16 @@ class H2Matrix:
         if x.stride(0) != 1 or y.stride(0) != 1:
             raise ValueError("x and y must be column-major (use colmajor())")
         _check(self._lib.h2_matvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.shape[1])))
+        return y
+
+    def matvec_acc(self, x, y):
+        """y <- y + G~ x on the device (h2_matvec_acc); x, y as for matvec."""
+        if x.shape != y.shape or x.shape[0] != self.n:
+            raise ValueError("x and y must both be (n, nrhs)")
+        if x.stride(0) != 1 or y.stride(0) != 1:
+            raise ValueError("x and y must be column-major (use colmajor())")
+        _check(self._lib.h2_matvec_acc(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                       int(x.shape[1])))
         return y
 
     def matvec_noalloc(self, x, y):
@@ -299,6 +314,19 @@ class H2Matrix:
         y = np.zeros_like(x, order="F")
         _check(self._lib.h2_matvec_host(self._h, _dp(x), _dp(y), int(x.shape[1])))
         return y
+
+    def export(self, what, first=0, count=None):
+        """The stored representation as built on the device (h2_export), as float64:
+        what = "near" (count, lmax, lmax), "coupling" (count, k, k), "V" (count, k)
+        over padded DoFs, "E" (count, 3, m, m)."""
+        st = self.stats
+        L, k, m = st["leaf_max"], st["rank"], st["order"]
+        item, total, shape = {"near": (0, st["near_blocks"], (L, L)), "coupling": (1, st["adm_blocks"], (k, k)),
+                              "V": (2, (2 ** st["depth"]) * L, (k,)), "E": (3, st["clusters"], (3, m, m))}[what]
+        count = total - first if count is None else count
+        out = np.zeros((count,) + shape)
+        _check(self._lib.h2_export(self._h, item, int(first), int(count), _dp(out)))
+        return out
 
     def coefficients(self, which, nrhs):
         out = np.zeros((self.stats["clusters"], self.stats["rank"], nrhs))

@@ -1,5 +1,8 @@
 // C ABI of libh2 (declared in include/h2.h): argument checking, handles,
 // error reporting, host <-> device staging.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -14,6 +17,23 @@ namespace h2 {
 
 static thread_local std::string g_last_error;
 
+// allocations left before the injected failure; -1: none pending
+static std::atomic<int64_t> g_alloc_countdown{-1};
+
+cudaError_t dmalloc_raw(void **p, size_t bytes) {
+  int64_t c = g_alloc_countdown.load();
+  while (c >= 0) {
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+      if (c == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 int fail(int status, const std::string &msg) {
   g_last_error = msg;
   return status;
@@ -26,11 +46,33 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 static void free_dev(Dev &d) {
-  void *ptrs[] = {d.Ntc, d.xnt, d.ntc_E, d.ntc_xmax, d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
+  void *ptrs[] = {d.Ntc, d.xnt, d.ntc_E, d.ntc_xmax, d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.colmax, d.nself, d.near_ptr2, d.self_ptr, d.near_col2, d.near_blk2, d.self_col, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
                   d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   d = Dev();
+}
+
+// H2_F64 keeps every stored value as a pair of FP32 numbers, so the stored
+// entries must stay inside FP32's exponent range with room for the low word:
+// every nearfield entry is at least amin^2 / (4 pi D) (amin the smallest
+// triangle area, D the diameter of the mesh's box), which must not fall below
+// 2^-96, and no triangle area may exceed 2^60.
+static int check_double_float_range(const Plan &p) {
+  double amin = HUGE_VAL, amax = 0.0;
+  for (double a : p.area) {
+    amin = std::min(amin, a);
+    amax = std::max(amax, a);
+  }
+  double diag = 0.0;
+  for (int q = 0; q < 3; ++q) diag += (p.hi[q] - p.lo[q]) * (p.hi[q] - p.lo[q]);
+  diag = std::sqrt(diag);
+  const double low = amin * amin / (4.0 * 3.14159265358979323846 * std::max(diag, 1e-300));
+  if (!(low >= std::ldexp(1.0, -96)) || !(amax <= std::ldexp(1.0, 60)))
+    return fail(H2_EINVAL, "mesh scale outside the double-float range of H2_F64 (smallest triangle area " +
+                               std::to_string(amin) + ", mesh diameter " + std::to_string(diag) +
+                               "); rescale the mesh or use H2_F64_NATIVE");
+  return H2_OK;
 }
 
 }  // namespace h2
@@ -40,6 +82,12 @@ using namespace h2;
 extern "C" {
 
 const char *h2_last_error(void) { return g_last_error.c_str(); }
+
+int h2_inject_alloc_failure(int64_t after) {
+  if (after < -1) return fail(H2_EINVAL, "after must be >= -1");
+  g_alloc_countdown.store(after);
+  return H2_OK;
+}
 
 int h2_options_default(h2_options *opt) {
   if (!opt) return fail(H2_EINVAL, "opt is NULL");
@@ -142,6 +190,11 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   if (o.tensor < 0 || o.tensor > 1) return fail(H2_EINVAL, "tensor must be 0 (tensor cores where supported) or 1 (never)");
   for (int r : o.reserved)
     if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
+  if (o.basis_prec != 0) {
+    if (!half_prec) return fail(H2_EINVAL, "basis_prec applies to H2_BF16 and H2_F16 handles only; use 0");
+    if (o.basis_prec != H2_F32 && o.basis_prec != o.prec)
+      return fail(H2_EINVAL, "basis_prec must be 0, H2_F32 or the handle's own 16-bit precision");
+  }
   int ndev = 0;
   H2_CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (o.device < 0 || o.device >= ndev) return fail(H2_EINVAL, "device ordinal out of range");
@@ -153,10 +206,13 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   c->quad_order = o.quad_order;
   c->d.prec = o.prec;
   c->d.tensor = o.tensor;
+  // FP32 leaf bases: explicitly, or by default under bfloat16 storage
+  c->d.v32 = half_prec && (o.basis_prec == H2_F32 || (o.basis_prec == 0 && o.prec == H2_BF16));
   c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);
   int rc;
   try {
     rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, true, c->plan);
+    if (!rc && o.prec == H2_F64) rc = check_double_float_range(c->plan);
     if (!rc) rc = device_build(*c);
   } catch (const std::bad_alloc &) {
     rc = fail(H2_ENOMEM, "host allocation in set-up");
@@ -207,6 +263,7 @@ int h2_info(h2_handle h, h2_stats *out) {
   out->coupling = h->d.coupling == 1 ? H2_COUPLING_REGEN : H2_COUPLING_STORED;
   out->tensor = h->d.tc ? 1 : 0;
   out->tensor_near = h->d.ntc ? 1 : 0;
+  out->basis_prec = h->d.v32 ? H2_F32 : h->d.prec;
   return H2_OK;
 }
 
@@ -249,6 +306,19 @@ int h2_matvec(h2_handle h, const void *x, void *y, int nrhs) {
   if (!h || !x || !y) return fail(H2_EINVAL, "NULL argument");
   H2_CUDA_TRY(cudaSetDevice(h->device));
   return run_matvec(*h, x, y, nrhs, false);
+}
+
+int h2_wait_selftest(h2_handle h, int withhold, uint32_t poll_limit, int *stages_seen) {
+  if (!h) return fail(H2_EINVAL, "NULL handle");
+  if (withhold != 0 && withhold != 1) return fail(H2_EINVAL, "withhold must be 0 or 1");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  return wait_selftest(*h, withhold, poll_limit, stages_seen);
+}
+
+int h2_matvec_acc(h2_handle h, const void *x, void *y, int nrhs) {
+  if (!h || !x || !y) return fail(H2_EINVAL, "NULL argument");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  return run_matvec(*h, x, y, nrhs, false, true);
 }
 
 }  // extern "C"
@@ -375,9 +445,158 @@ int h2_coefficients(h2_handle h, int which, double *out) {
     H2_CUDA_TRY(cudaMemcpy(tf.data(), src, rows * rp * 4, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < tf.size(); ++i) tmp[i] = tf[i];
   }
+  // columns scaled by the double-float range guard are reported unscaled
+  double unscale[64];
+  for (size_t c = 0; c < nr; ++c) unscale[c] = 1.0;
+  if (d.colmax) {
+    unsigned long long bits[64];
+    H2_CUDA_TRY(cudaMemcpy(bits, d.colmax, nr * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    for (size_t c = 0; c < nr; ++c) unscale[c] = std::ldexp(1.0, -column_range_shift(bits[c]));
+  }
   for (size_t r = 0; r < rows; ++r)
-    for (size_t c = 0; c < nr; ++c) out[r * nr + c] = tmp[r * rp + c];
+    for (size_t c = 0; c < nr; ++c) out[r * nr + c] = tmp[r * rp + c] * unscale[c];
   return H2_OK;
+}
+
+namespace {
+
+enum StoredType { ST_DD, ST_F64, ST_F32, ST_BF16, ST_F16 };
+
+// one stored value as a double (IEEE binary16 and bfloat16 decoded from
+// their bit fields; a double-float pair summed)
+double stored_value(const unsigned char *p, int type) {
+  switch (type) {
+    case ST_DD: {
+      float hl[2];
+      std::memcpy(hl, p, 8);
+      return (double)hl[0] + (double)hl[1];
+    }
+    case ST_F64: {
+      double v;
+      std::memcpy(&v, p, 8);
+      return v;
+    }
+    case ST_F32: {
+      float v;
+      std::memcpy(&v, p, 4);
+      return v;
+    }
+    case ST_BF16: {
+      uint16_t b;
+      std::memcpy(&b, p, 2);
+      const uint32_t u = (uint32_t)b << 16;
+      float v;
+      std::memcpy(&v, &u, 4);
+      return v;
+    }
+    default: {
+      uint16_t b;
+      std::memcpy(&b, p, 2);
+      const int sgn = b >> 15, ex = (b >> 10) & 31, man = b & 1023;
+      double v = ex == 0 ? std::ldexp((double)man, -24)
+                         : ex == 31 ? (man ? NAN : HUGE_VAL) : std::ldexp((double)(man + 1024), ex - 25);
+      return sgn ? -v : v;
+    }
+  }
+}
+
+int stored_type_of(int prec) {
+  switch (prec) {
+    case H2_F64: return ST_DD;
+    case H2_F64_NATIVE: return ST_F64;
+    case H2_BF16: return ST_BF16;
+    case H2_F16: return ST_F16;
+    default: return ST_F32;
+  }
+}
+
+size_t stored_size(int type) { return type == ST_DD || type == ST_F64 ? 8 : type == ST_F32 ? 4 : 2; }
+
+// copy count * per stored values starting at element first * per of a device array to the host
+int fetch(const void *src, size_t esz, int64_t first, int64_t count, int64_t per, std::vector<unsigned char> &buf) {
+  buf.resize((size_t)(count * per) * esz);
+  if (count == 0) return H2_OK;
+  H2_CUDA_TRY(cudaMemcpy(buf.data(), static_cast<const unsigned char *>(src) + (size_t)(first * per) * esz,
+                         buf.size(), cudaMemcpyDeviceToHost));
+  return H2_OK;
+}
+
+}  // namespace
+
+int h2_export(h2_handle h, int what, int64_t first, int64_t count, double *out) {
+  if (!h || (!out && count > 0) || first < 0 || count < 0) return fail(H2_EINVAL, "bad argument");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const Dev &d = h->d;
+  const Plan &p = h->plan;
+  const int64_t L = d.lmax, Lp = d.lp, k = d.k, kp = d.kp, m = d.m;
+  const int ts = stored_type_of(d.prec);
+  std::vector<unsigned char> buf;
+  int rc;
+  switch (what) {
+    case H2_EXPORT_NEAR: {
+      if (first + count > d.nnear) return fail(H2_EINVAL, "near block range out of bounds");
+      if ((rc = fetch(d.near, stored_size(ts), first, count, L * Lp, buf))) return rc;
+      std::vector<float> sc;
+      if (d.nscale) {
+        sc.resize(count);
+        if (count) H2_CUDA_TRY(cudaMemcpy(sc.data(), d.nscale + first, count * 4, cudaMemcpyDeviceToHost));
+      }
+      for (int64_t i = 0; i < count; ++i)
+        for (int64_t t = 0; t < L; ++t)
+          for (int64_t c = 0; c < L; ++c) {
+            double v = stored_value(buf.data() + ((i * L + c) * Lp + t) * stored_size(ts), ts);
+            out[(i * L + t) * L + c] = d.nscale ? v * sc[i] : v;
+          }
+      if (d.nself) {
+        // bfloat16 handles: the self blocks are held in FP32
+        for (int64_t i = 0; i < count; ++i) {
+          const int64_t b = first + i;
+          const int64_t j = std::upper_bound(p.near_ptr.begin(), p.near_ptr.end(), b) - p.near_ptr.begin() - 1;
+          if (p.near_col[b] != j) continue;
+          std::vector<unsigned char> sb;
+          if ((rc = fetch(d.nself, 4, j, 1, L * Lp, sb))) return rc;
+          for (int64_t t = 0; t < L; ++t)
+            for (int64_t c = 0; c < L; ++c) out[(i * L + t) * L + c] = stored_value(sb.data() + (c * Lp + t) * 4, ST_F32);
+        }
+      }
+      return H2_OK;
+    }
+    case H2_EXPORT_COUPLING: {
+      if (!d.S) return fail(H2_EINVAL, "the coupling matrices are regenerated, not stored");
+      if (first + count > d.nadm) return fail(H2_EINVAL, "admissible block range out of bounds");
+      if ((rc = fetch(d.S, stored_size(ts), first, count, k * kp, buf))) return rc;
+      for (int64_t i = 0; i < count; ++i)
+        for (int64_t nu = 0; nu < k; ++nu)
+          for (int64_t mu = 0; mu < k; ++mu)
+            out[(i * k + nu) * k + mu] = stored_value(buf.data() + ((i * k + mu) * kp + nu) * stored_size(ts), ts);
+      return H2_OK;
+    }
+    case H2_EXPORT_V: {
+      if (first + count > d.npad) return fail(H2_EINVAL, "padded DoF range out of bounds");
+      const int tv = d.v32 ? ST_F32 : ts;
+      if ((rc = fetch(d.V, stored_size(tv), first, count, kp, buf))) return rc;
+      std::vector<float> vs;
+      if (d.vscale) {
+        vs.resize(d.nleaf);
+        H2_CUDA_TRY(cudaMemcpy(vs.data(), d.vscale, d.nleaf * 4, cudaMemcpyDeviceToHost));
+      }
+      for (int64_t i = 0; i < count; ++i)
+        for (int64_t nu = 0; nu < k; ++nu) {
+          double v = stored_value(buf.data() + (i * kp + nu) * stored_size(tv), tv);
+          out[i * k + nu] = d.vscale ? v * vs[(first + i) / L] : v;
+        }
+      return H2_OK;
+    }
+    case H2_EXPORT_E: {
+      if (first + count > d.nclu) return fail(H2_EINVAL, "cluster range out of bounds");
+      const int te = (d.prec == H2_BF16 || d.v32) ? ST_F32 : ts;
+      if ((rc = fetch(d.Ef, stored_size(te), first, count, 3 * m * m, buf))) return rc;
+      for (int64_t i = 0; i < count * 3 * m * m; ++i) out[i] = stored_value(buf.data() + i * stored_size(te), te);
+      return H2_OK;
+    }
+    default: return fail(H2_EINVAL, "unknown export item");
+  }
 }
 
 int h2_solve(h2_handle h, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
@@ -395,7 +614,7 @@ int h2_solve(h2_handle h, const double *b, double *z, int nrhs, double rtol, int
   if (db) return run_gmres(*h, b, z, nrhs, rtol, restart, maxit, info);
   size_t bytes = (size_t)h->d.n * nrhs * 8;
   double *db_ = nullptr, *dz_ = nullptr;
-  if (cudaMalloc(&db_, bytes) != cudaSuccess || cudaMalloc(&dz_, bytes) != cudaSuccess) {
+  if (dmalloc(&db_, bytes) != cudaSuccess || dmalloc(&dz_, bytes) != cudaSuccess) {
     cudaFree(db_);
     cudaGetLastError();
     return fail(H2_ENOMEM, "solve staging buffers");
@@ -435,7 +654,7 @@ int h2_solve_ir(h2_handle hi, h2_handle lo, const double *b, double *z, int nrhs
   if (db) return run_gmres_ir(*hi, *lo, b, z, nrhs, rtol, inner_rtol, restart, maxit_inner, maxit_outer, info);
   size_t bytes = (size_t)hi->d.n * nrhs * 8;
   double *db_ = nullptr, *dz_ = nullptr;
-  if (cudaMalloc(&db_, bytes) != cudaSuccess || cudaMalloc(&dz_, bytes) != cudaSuccess) {
+  if (dmalloc(&db_, bytes) != cudaSuccess || dmalloc(&dz_, bytes) != cudaSuccess) {
     cudaFree(db_);
     cudaGetLastError();
     return fail(H2_ENOMEM, "solve staging buffers");

@@ -737,7 +737,7 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
   }
   b->packed = xoff;
   b->work_bytes = off * 4;
-  if ((ce = cudaMalloc(&b->work, (size_t)b->work_bytes)) != cudaSuccess)
+  if ((ce = dmalloc(&b->work, (size_t)b->work_bytes)) != cudaSuccess)
     return bail(cuda_fail(ce, "batched work vectors"));
   if ((ce = cudaMemset(b->work, 0, (size_t)b->work_bytes)) != cudaSuccess) return bail(cuda_fail(ce, "memset"));
   float *wf = static_cast<float *>(b->work);
@@ -862,9 +862,9 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
       floats += extra[i].nrows * extra[i].M * extra[i].rp;
     }
     const size_t nc = cb.size();
-    if ((ce = cudaMalloc((void **)&b->d_chunks[ph], 2 * nc * sizeof(int64_t))) != cudaSuccess ||
-        (ce = cudaMalloc((void **)&b->scratch[ph], (size_t)floats * sizeof(float))) != cudaSuccess ||
-        (ce = cudaMalloc((void **)&b->d_red[ph], red.size() * sizeof(BRed))) != cudaSuccess)
+    if ((ce = dmalloc((void **)&b->d_chunks[ph], 2 * nc * sizeof(int64_t))) != cudaSuccess ||
+        (ce = dmalloc((void **)&b->scratch[ph], (size_t)floats * sizeof(float))) != cudaSuccess ||
+        (ce = dmalloc((void **)&b->d_red[ph], red.size() * sizeof(BRed))) != cudaSuccess)
       return bail(cuda_fail(ce, "chunk rows"));
     std::vector<int64_t> both(cb);
     both.insert(both.end(), ce_.begin(), ce_.end());
@@ -893,7 +893,7 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
     b->nred[ph] = (int)red.size();
   }
   for (int ph = 0; ph < kRowPhases; ++ph) {
-    if ((ce = cudaMalloc((void **)&b->d_rows[ph], sizeof(BRows) * b->rows[ph].size())) != cudaSuccess)
+    if ((ce = dmalloc((void **)&b->d_rows[ph], sizeof(BRows) * b->rows[ph].size())) != cudaSuccess)
       return bail(cuda_fail(ce, "batch descriptors"));
     int rc = upload_rows(*b, ph);
     if (rc) return bail(rc);
@@ -921,7 +921,7 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
         tot += (int64_t)1 << l;
       }
       BTr *dp = nullptr;
-      if ((ce = cudaMalloc((void **)&dp, sizeof(BTr) * ent.size())) != cudaSuccess)
+      if ((ce = dmalloc((void **)&dp, sizeof(BTr) * ent.size())) != cudaSuccess)
         return bail(cuda_fail(ce, "transfer descriptors"));
       (up ? b->d_up : b->d_down).push_back(dp);
       if ((ce = cudaMemcpy(dp, ent.data(), sizeof(BTr) * ent.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -953,8 +953,8 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
     e0 += d.npad * P.rp;
   }
   b->perm_total = e0;
-  if ((ce = cudaMalloc((void **)&b->d_perm_in, sizeof(BPerm) * nprob)) != cudaSuccess ||
-      (ce = cudaMalloc((void **)&b->d_perm_out, sizeof(BPerm) * nprob)) != cudaSuccess)
+  if ((ce = dmalloc((void **)&b->d_perm_in, sizeof(BPerm) * nprob)) != cudaSuccess ||
+      (ce = dmalloc((void **)&b->d_perm_out, sizeof(BPerm) * nprob)) != cudaSuccess)
     return bail(cuda_fail(ce, "permutation descriptors"));
   if ((ce = cudaMemcpy(b->d_perm_in, pin.data(), sizeof(BPerm) * nprob, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(b->d_perm_out, pout.data(), sizeof(BPerm) * nprob, cudaMemcpyHostToDevice)) != cudaSuccess)

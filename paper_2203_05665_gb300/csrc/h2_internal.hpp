@@ -21,6 +21,15 @@ int cuda_fail(cudaError_t e, const char *what);
     if (e_ != cudaSuccess) return ::h2::cuda_fail(e_, #call); \
   } while (0)
 
+// Every device allocation of the library goes through dmalloc: cudaMalloc,
+// except that h2_inject_alloc_failure can make one chosen allocation fail as
+// if the device were out of memory (test hook for the error paths).
+cudaError_t dmalloc_raw(void **p, size_t bytes);
+template <class T>
+inline cudaError_t dmalloc(T **p, size_t bytes) {
+  return dmalloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 // Gauss-Legendre nodes and weights on [0,1] (Newton on the Legendre recurrence).
 void gauss_legendre01(int q, std::vector<double> &x, std::vector<double> &w);
 
@@ -100,8 +109,16 @@ struct Dev {
   int32_t *ntc_E = nullptr;
   unsigned *ntc_xmax = nullptr;
   uint32_t ntc_ablk = 0;
+  unsigned long long *colmax = nullptr;   // H2_F64: 64 column maxima of x (range guard of double-float)
+  bool v32 = false;             // 16-bit handle whose V, Vt and transfer factors are stored in FP32
   float *vscale = nullptr;      // per leaf: power of two dividing the stored V (FP16), or NULL
   float *nscale = nullptr;      // per nearfield block: the same for G_b, or NULL
+  // bfloat16 handles: the self blocks G_jj of the leaves in FP32 ([nleaf][lmax][lp], zero in `near`),
+  // the CSR of the other near blocks (near_ptr2 [nleaf + 1], near_col2, stored block near_blk2) and
+  // the one-term CSR of the self blocks (self_ptr [nleaf + 1], self_col [nleaf])
+  float *nself = nullptr;
+  int64_t *near_ptr2 = nullptr, *self_ptr = nullptr;
+  int32_t *near_col2 = nullptr, *near_blk2 = nullptr, *self_col = nullptr;
   // work buffers for up to cap_nrhs right-hand sides
   int cap_nrhs = 0;
   void *xpad = nullptr, *ypad = nullptr, *xhat = nullptr, *yhat = nullptr;
@@ -150,8 +167,14 @@ inline int padded_rhs(int nrhs, size_t esize) {
   return (nrhs + v - 1) / v * v;
 }
 
+// power of two applied to a column of x whose largest entry (bits of the
+// double) lies outside the double-float range guard [2^-40, 2^40]; 0 inside
+int column_range_shift(unsigned long long bits);
+
 // device-side error word (a bounded wait ran out); read and cleared by the host
 int take_device_error(Ctx &c);
+// the bounded-wait self-test of h2_wait_selftest (h2_matvec.cu)
+int wait_selftest(Ctx &c, int withhold, uint32_t limit, int *stages_seen);
 
 // FP64-accurate coupling on the tensor cores (h2_tc.cu): eligibility,
 // set-up of the slices (arow_dev: row cluster of every admissible block, on
@@ -179,7 +202,8 @@ int device_build(Ctx &c);
 // stay resident per SM to hide the global-memory latency of each parent's
 // step; the narrow top levels keep 256 to shorten each CTA.
 inline int transfer_threads(int l) { return l >= 10 ? 128 : 256; }
-int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64);
+// accumulate: y += G~ x instead of y = G~ x (the final scatter adds)
+int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64, bool accumulate = false);
 // GMRES (h2_solve.cu); b, z device FP64 arrays
 int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
               h2_solve_info *info);

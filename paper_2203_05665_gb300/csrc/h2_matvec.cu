@@ -29,28 +29,69 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxOut = 16;   // outputs per thread in the block-row kernels
 
+// Range guard of the double-float arithmetic (H2_F64 handles): a double-float
+// value has the exponent range of FP32, so a column of x whose largest entry
+// lies outside [2^-40, 2^40] is multiplied by the power of two that brings
+// that entry to [1, 2) on the way in and divided by it on the way out (exact;
+// columns inside the range are not touched).  colmax[c] holds the bits of
+// max |x[:, c]| as a double (non-negative doubles order like their bits).
+template <class Tin>
+__global__ void k_colmax(const Tin *__restrict__ x, int64_t n, unsigned long long *__restrict__ colmax) {
+  const int c = blockIdx.y;
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs((double)x[i + (int64_t)c * n]));
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(&colmax[c], (unsigned long long)__double_as_longlong(mx));
+}
+
+// the power of two by which column c is scaled (0: untouched; zero, infinite
+// and NaN columns are not scaled)
+__host__ __device__ inline int range_shift(unsigned long long bits) {
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (bits == 0 || ex == 0x7ff) return 0;
+  const int e = ex == 0 ? -1022 : ex - 1023;
+  return (e < -40 || e > 40) ? -e : 0;
+}
+
 // xpad[p][c] (rp columns, zero beyond nrhs) from x[src][c] column-major
 template <class Tin, class Tout>
 __global__ void k_permute_in(const Tin *__restrict__ x, int64_t n, int nrhs, int rp,
-                             const int32_t *__restrict__ pad_src, int64_t npad, Tout *__restrict__ xpad) {
+                             const int32_t *__restrict__ pad_src, int64_t npad,
+                             const unsigned long long *__restrict__ colmax, Tout *__restrict__ xpad) {
   const int64_t total = npad * rp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = e / rp;
     int r = (int)(e - p * rp);
     int32_t src = pad_src[p];
-    xpad[e] = (src >= 0 && r < nrhs) ? convert<Tout, Tin>(x[src + r * n]) : zero_of<Tout>();
+    if (src >= 0 && r < nrhs) {
+      Tin v = x[src + r * n];
+      const int sh = colmax ? range_shift(colmax[r]) : 0;
+      if (sh) v = (Tin)ldexp((double)v, sh);
+      xpad[e] = convert<Tout, Tin>(v);
+    } else {
+      xpad[e] = zero_of<Tout>();
+    }
   }
 }
 
+// y[src][c] (column-major, caller order) from ypad[p][c]; with acc the value
+// is added to what y holds (y <- y + G~ x)
 template <class Tin, class Tout>
 __global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs, int rp,
-                              const int32_t *__restrict__ pad_src, int64_t npad, Tout *__restrict__ y) {
+                              const int32_t *__restrict__ pad_src, int64_t npad,
+                              const unsigned long long *__restrict__ colmax, int acc, Tout *__restrict__ y) {
   const int64_t total = npad * rp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = e / rp;
     int r = (int)(e - p * rp);
     int32_t src = pad_src[p];
-    if (src >= 0 && r < nrhs) y[src + r * n] = convert<Tout, Tin>(ypad[e]);
+    if (src >= 0 && r < nrhs) {
+      Tout v = convert<Tout, Tin>(ypad[e]);
+      const int sh = colmax ? range_shift(colmax[r]) : 0;
+      if (sh) v = (Tout)ldexp((double)v, -sh);
+      y[src + r * n] = acc ? y[src + r * n] + v : v;
+    }
   }
 }
 
@@ -260,7 +301,9 @@ struct LeafBackwardRows {
 };
 
 // Nearfield (Algorithm 3, inadmissible blocks): row j = leaf j, terms G_b x|s_b
-// for the inadmissible blocks b of row j (G_b stored transposed [c][t]).
+// for the inadmissible blocks b of row j (G_b stored transposed [c][t]).  With
+// blk the e-th term of the CSR uses stored block blk[e] (a CSR over a subset
+// of the blocks), else block e.
 template <class TS, class TC>
 struct NearRows {
   static constexpr bool kGen = false;
@@ -268,13 +311,15 @@ struct NearRows {
   const int64_t *ptr;
   const int32_t *col;
   const TC *xpad;
-  const float *nscale;   // per block, or NULL
+  const float *nscale;   // per stored block, or NULL
   int L, Lp, rp;
+  const int32_t *blk;    // stored block of every term, or NULL
+  __device__ int64_t block(int64_t e) const { return blk ? (int64_t)blk[e] : e; }
   __device__ int kdim(int64_t) const { return L; }
-  __device__ void meta(int64_t e, float *mt) const { mt[0] = nscale ? nscale[e] : 1.0f; }
+  __device__ void meta(int64_t e, float *mt) const { mt[0] = nscale ? nscale[block(e)] : 1.0f; }
   __device__ int64_t first(int64_t r) const { return ptr[r]; }
   __device__ Term<TS, TC> term(int64_t e) const {
-    return Term<TS, TC>{near + e * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
+    return Term<TS, TC>{near + block(e) * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
   }
 };
 
@@ -775,12 +820,11 @@ __global__ void __launch_bounds__(256) k_leaf_bwd_reg(const TS *__restrict__ Vt,
     }
 }
 
-// TS: storage type of V, E, S and the nearfield; T: arithmetic and vector
-// type; Tio: type of the caller's x and y.
-template <class TS, class T, class Tio>
-int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
-  // transfer factors: FP32 under bfloat16 storage (see the set-up)
-  using TE = typename std::conditional<std::is_same<TS, __nv_bfloat16>::value, float, TS>::type;
+// TS: storage type of S and the nearfield; TV: of the leaf bases V; TE: of
+// the transfer factors; T: arithmetic and vector type; Tio: type of the
+// caller's x and y.  acc: y += G~ x.
+template <class TS, class TV, class TE, class T, class Tio>
+int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
   const int k = d.k, kp = d.kp, m = d.m, L = (int)d.lmax, Lp = (int)d.lp, D = d.depth, lmin = d.first_adm_level;
@@ -794,28 +838,36 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   const int t_fwd = row_threads(kp, rp, L, sizeof(T), Rk), t_cpl = row_threads(kp, rp, k, sizeof(T), Rk);
   const int t_back = row_threads(Lp, rp, k, sizeof(T), RL), t_near = row_threads(Lp, rp, L, sizeof(T), RL);
   if (far) {
-    if ((rc = row_cfg<TS, T>(k, kp, rp, L, t_fwd, Rk, false, cf_fwd))) return rc;
+    if ((rc = row_cfg<TV, T>(k, kp, rp, L, t_fwd, Rk, false, cf_fwd))) return rc;
     if ((rc = row_cfg<TS, T>(k, kp, rp, k, t_cpl, Rk, gen, cf_cpl))) return rc;
-    if ((rc = row_cfg<TS, T>(L, Lp, rp, k, t_back, RL, false, cf_back))) return rc;
+    if ((rc = row_cfg<TV, T>(L, Lp, rp, k, t_back, RL, false, cf_back))) return rc;
   }
   if ((rc = row_cfg<TS, T>(L, Lp, rp, L, t_near, RL, false, cf_near))) return rc;
   const float *vscale = (const float *)d.vscale, *nscale = (const float *)d.nscale;
   Marks mk(c);
 
   mk.mark(H2_PH_PERMUTE_IN);
-  k_permute_in<Tio, T><<<grid_for(d.npad * rp), kThreads, 0, st>>>(x, d.n, nrhs, rp, d.pad_src, d.npad, xpad);
+  // double-float handles: column maxima of x for the range guard
+  const unsigned long long *cmx = std::is_same<T, dd>::value ? d.colmax : nullptr;
+  if (cmx) {
+    H2_CUDA_TRY(cudaMemsetAsync(d.colmax, 0, sizeof(unsigned long long) * nrhs, st));
+    const int64_t nb = std::min<int64_t>((d.n + 4 * kThreads - 1) / (4 * kThreads), 2 * 152);
+    k_colmax<Tio><<<dim3((unsigned)std::max<int64_t>(nb, 1), nrhs), kThreads, 0, st>>>(x, d.n, d.colmax);
+    mk.count(H2_PH_PERMUTE_IN);
+  }
+  k_permute_in<Tio, T><<<grid_for(d.npad * rp), kThreads, 0, st>>>(x, d.n, nrhs, rp, d.pad_src, d.npad, cmx, xpad);
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
   // leaf steps with one CTA per leaf when the stored values are in the arithmetic type
   const bool leaf_reg = L <= 32 && k <= 64 && rp <= 16;
   if (far && leaf_reg) {
     const size_t sm = (size_t)L * (kp + rp) * sizeof(T);
-    k_leaf_fwd_reg<TS, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TS *)d.V, xpad, vscale, L, kp, k, rp,
+    k_leaf_fwd_reg<TV, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TV *)d.V, xpad, vscale, L, kp, k, rp,
                                                              xhat + leaf0 * (int64_t)k * rp);
     mk.count(H2_PH_LEAF_FORWARD);
   } else if (far) {
-    LeafForwardRows<TS, T> rows{(const TS *)d.V, xpad, vscale, L, kp, rp};
-    if ((rc = launch_rows<TS, T>(rows, cf_fwd, t_fwd, Rk, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
+    LeafForwardRows<TV, T> rows{(const TV *)d.V, xpad, vscale, L, kp, rp};
+    if ((rc = launch_rows<TV, T>(rows, cf_fwd, t_fwd, Rk, d.nleaf, 0, xhat + leaf0 * (int64_t)k * rp, st))) return rc;
     mk.count(H2_PH_LEAF_FORWARD);
   }
   mk.mark(H2_PH_UPWARD);
@@ -901,12 +953,12 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
   mk.mark(H2_PH_LEAF_NEAR);
   if (far && leaf_reg) {
     const size_t sm = (size_t)k * (Lp + rp) * sizeof(T);
-    k_leaf_bwd_reg<TS, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TS *)d.Vt, yhat + leaf0 * (int64_t)k * rp,
+    k_leaf_bwd_reg<TV, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TV *)d.Vt, yhat + leaf0 * (int64_t)k * rp,
                                                              vscale, L, Lp, k, rp, ypad);
     mk.count(H2_PH_LEAF_NEAR);
   } else if (far) {
-    LeafBackwardRows<TS, T> rows{(const TS *)d.Vt, yhat, vscale, k, Lp, rp, leaf0};
-    if ((rc = launch_rows<TS, T>(rows, cf_back, t_back, RL, d.nleaf, 0, ypad, st))) return rc;
+    LeafBackwardRows<TV, T> rows{(const TV *)d.Vt, yhat, vscale, k, Lp, rp, leaf0};
+    if ((rc = launch_rows<TV, T>(rows, cf_back, t_back, RL, d.nleaf, 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
   if (std::is_same<T, dd>::value && d.ntc && rp <= 16) {
@@ -914,13 +966,26 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
     int64_t nl = 0;
     if ((rc = ntc_near(c, xpad, ypad, rp, far ? 1 : 0, &nl))) return rc;
     mk.count(H2_PH_LEAF_NEAR, nl);
+  } else if (d.nself) {
+    // bfloat16: the blocks of other leaves, then the self blocks G_jj in FP32
+    NearRows<TS, T> rows{(const TS *)d.near, d.near_ptr2, d.near_col2, xpad, nscale, L, Lp, rp, d.near_blk2};
+    if ((rc = launch_rows<TS, T>(rows, cf_near, t_near, RL, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
+    mk.count(H2_PH_LEAF_NEAR);
+    if constexpr (std::is_same<T, float>::value) {
+      RowCfg cf_self{};
+      if ((rc = row_cfg<float, T>(L, Lp, rp, L, t_near, RL, false, cf_self))) return rc;
+      NearRows<float, T> self{d.nself, d.self_ptr, d.self_col, xpad, nullptr, L, Lp, rp, nullptr};
+      if ((rc = launch_rows<float, T>(self, cf_self, t_near, RL, d.nleaf, 1, ypad, st))) return rc;
+      mk.count(H2_PH_LEAF_NEAR);
+    }
   } else {
-    NearRows<TS, T> rows{(const TS *)d.near, d.near_ptr, d.near_col, xpad, nscale, L, Lp, rp};
+    NearRows<TS, T> rows{(const TS *)d.near, d.near_ptr, d.near_col, xpad, nscale, L, Lp, rp, nullptr};
     if ((rc = launch_rows<TS, T>(rows, cf_near, t_near, RL, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
   }
   mk.mark(H2_PH_PERMUTE_OUT);
-  k_permute_out<T, Tio><<<grid_for(d.npad * rp), kThreads, 0, st>>>(ypad, d.n, nrhs, rp, d.pad_src, d.npad, y);
+  k_permute_out<T, Tio><<<grid_for(d.npad * rp), kThreads, 0, st>>>(ypad, d.n, nrhs, rp, d.pad_src, d.npad, cmx,
+                                                                      acc ? 1 : 0, y);
   mk.count(H2_PH_PERMUTE_OUT);
   mk.mark(H2_NPHASE);
   mk.finish();
@@ -931,6 +996,75 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs) {
 }
 
 }  // namespace
+
+int column_range_shift(unsigned long long bits) { return range_shift(bits); }
+
+namespace {
+
+// Self-test of the bounded waits: the pipeline of the block-row kernels in
+// miniature.  Thread 0 of warp 1 (the producer) fills stages 0 .. kStages-2
+// of a shared-memory ring with bulk copies of src, each completing on its
+// mbarrier, and with withhold set never fills the last stage; thread 0 of
+// warp 0 (the consumer) waits for every stage in order with the bounded
+// wait (limit polls).  A withheld stage makes that wait run out: the error
+// word is raised and the consumer leaves; the producer always waits for the
+// copies it issued (they complete) before it leaves, so no copy is in flight
+// when the CTA ends.  out[0] = stages the consumer saw complete.
+constexpr int kSelfStages = 4;
+constexpr uint32_t kSelfBytes = 4096;
+__global__ void k_wait_selftest(const unsigned char *__restrict__ src, int withhold, uint32_t limit,
+                                int *__restrict__ out) {
+  __shared__ __align__(128) unsigned char buf[kSelfStages][kSelfBytes];
+  __shared__ __align__(8) uint64_t full[kSelfStages];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kSelfStages; ++i) mbar_init(&full[i], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 32) {
+    const int nfill = withhold ? kSelfStages - 1 : kSelfStages;
+    for (int i = 0; i < nfill; ++i) {
+      mbar_expect_tx(&full[i], kSelfBytes);
+      bulk_g2s(buf[i], src + (size_t)i * kSelfBytes, kSelfBytes, &full[i]);
+    }
+    for (int i = 0; i < nfill; ++i) mbar_wait_bounded(&full[i], 0);
+  } else if (threadIdx.x == 0) {
+    int seen = 0;
+    for (int i = 0; i < kSelfStages; ++i) {
+      if (!mbar_wait_bounded(&full[i], 0, limit)) break;
+      ++seen;
+    }
+    out[0] = seen;
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+int wait_selftest(Ctx &c, int withhold, uint32_t limit, int *stages_seen) {
+  cudaStream_t st = c.stream;
+  unsigned char *src = nullptr;
+  int *out = nullptr;
+  H2_CUDA_TRY(dmalloc(&src, (size_t)kSelfStages * kSelfBytes));
+  if (dmalloc(&out, sizeof(int)) != cudaSuccess) {
+    cudaFree(src);
+    return fail(H2_ENOMEM, "self-test buffer");
+  }
+  cudaError_t e = cudaMemsetAsync(src, 0x5a, (size_t)kSelfStages * kSelfBytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out, 0xff, sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 64, 0, st>>>(src, withhold, limit ? limit : kWaitPolls, out);
+    e = cudaGetLastError();
+  }
+  int seen = -1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&seen, out, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(src);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+  if (stages_seen) *stages_seen = seen;
+  return take_device_error(c);
+}
 
 int take_device_error(Ctx &c) {
   int v = 0, zero = 0;
@@ -953,7 +1087,7 @@ int ensure_work(Ctx &c, int nrhs_req) {
   d.io_x = d.io_y = nullptr;
   d.cap_nrhs = 0;
   size_t es = d.esize;
-  auto al = [](void **p, size_t b) { return cudaMalloc(p, b) == cudaSuccess; };
+  auto al = [](void **p, size_t b) { return dmalloc(p, b) == cudaSuccess; };
   bool ok = al(&d.xpad, es * d.npad * nrhs) && al(&d.ypad, es * d.npad * nrhs) &&
             al(&d.xhat, es * d.nclu * d.k * nrhs) && al(&d.yhat, es * d.nclu * d.k * nrhs) &&
             al((void **)&d.io_x, 8 * d.n * nrhs) && al((void **)&d.io_y, 8 * d.n * nrhs);
@@ -968,7 +1102,7 @@ int ensure_work(Ctx &c, int nrhs_req) {
   return H2_OK;
 }
 
-int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64) {
+int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64, bool acc) {
   Dev &d = c.d;
   if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");
   const int rp = padded_rhs(nrhs, d.esize);
@@ -976,18 +1110,32 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64) {
     return fail(H2_EINVAL, "k * nrhs and leaf_max * nrhs (nrhs padded to 16 bytes) must not exceed 4096");
   int rc = ensure_work(c, nrhs);
   if (rc) return rc;
+  using bf = __nv_bfloat16;
+  const double *x64 = (const double *)x;
+  double *y64 = (double *)y;
+  const float *x32 = (const float *)x;
+  float *y32 = (float *)y;
   switch (d.prec) {
-    case H2_F64: return matvec_typed<dd, dd, double>(c, (const double *)x, (double *)y, nrhs);
-    case H2_F64_NATIVE: return matvec_typed<double, double, double>(c, (const double *)x, (double *)y, nrhs);
+    case H2_F64: return matvec_typed<dd, dd, dd, dd, double>(c, x64, y64, nrhs, acc);
+    case H2_F64_NATIVE: return matvec_typed<double, double, double, double, double>(c, x64, y64, nrhs, acc);
     case H2_F32:
-      if (io64) return matvec_typed<float, float, double>(c, (const double *)x, (double *)y, nrhs);
-      return matvec_typed<float, float, float>(c, (const float *)x, (float *)y, nrhs);
+      if (io64) return matvec_typed<float, float, float, float, double>(c, x64, y64, nrhs, acc);
+      return matvec_typed<float, float, float, float, float>(c, x32, y32, nrhs, acc);
     case H2_BF16:
-      if (io64) return matvec_typed<__nv_bfloat16, float, double>(c, (const double *)x, (double *)y, nrhs);
-      return matvec_typed<__nv_bfloat16, float, float>(c, (const float *)x, (float *)y, nrhs);
+      // transfer factors in FP32 under bfloat16 storage (see the set-up); V in FP32 unless asked otherwise
+      if (d.v32) {
+        if (io64) return matvec_typed<bf, float, float, float, double>(c, x64, y64, nrhs, acc);
+        return matvec_typed<bf, float, float, float, float>(c, x32, y32, nrhs, acc);
+      }
+      if (io64) return matvec_typed<bf, bf, float, float, double>(c, x64, y64, nrhs, acc);
+      return matvec_typed<bf, bf, float, float, float>(c, x32, y32, nrhs, acc);
     case H2_F16:
-      if (io64) return matvec_typed<__half, float, double>(c, (const double *)x, (double *)y, nrhs);
-      return matvec_typed<__half, float, float>(c, (const float *)x, (float *)y, nrhs);
+      if (d.v32) {
+        if (io64) return matvec_typed<__half, float, float, float, double>(c, x64, y64, nrhs, acc);
+        return matvec_typed<__half, float, float, float, float>(c, x32, y32, nrhs, acc);
+      }
+      if (io64) return matvec_typed<__half, __half, __half, float, double>(c, x64, y64, nrhs, acc);
+      return matvec_typed<__half, __half, __half, float, float>(c, x32, y32, nrhs, acc);
     default: return fail(H2_EINVAL, "unknown precision");
   }
 }

@@ -40,10 +40,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// polls of a bounded wait before it gives up (each try_wait may suspend
+// the thread for a while, so this is seconds, not cycles)
+constexpr uint32_t kWaitPolls = 1u << 22;
+
 // Wait for the phase of the given parity with an iteration limit; returns
 // false (and raises the device error word) if the limit runs out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit = kWaitPolls) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   atomicExch(&g_h2_device_error, 1);
   return false;
@@ -52,7 +56,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // The same, also giving up as soon as *abort (shared memory) is set by
 // another thread; a timeout sets *abort.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
+  for (uint32_t it = 0; it < kWaitPolls; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
   }

@@ -116,8 +116,8 @@ int allocate(Engine &e, h2_srv &s) {
   const size_t tot = (size_t)e.n * e.cap;
   if (alloc_gmres_work(e.w, e.n, e.cap, e.restart)) return H2_ENOMEM;
   bool ok = true;
-  for (double **p : {&e.B, &e.Z, &e.R, &e.D, &e.Az}) ok = ok && cudaMalloc(p, tot * 8) == cudaSuccess;
-  ok = ok && cudaMalloc(&e.tmp, 8 * (size_t)e.cap) == cudaSuccess;
+  for (double **p : {&e.B, &e.Z, &e.R, &e.D, &e.Az}) ok = ok && dmalloc(p, tot * 8) == cudaSuccess;
+  ok = ok && dmalloc(&e.tmp, 8 * (size_t)e.cap) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     e.ready = true;

@@ -292,6 +292,19 @@ int grid_for(int64_t n, int threads) {
 template <class T>
 int upload_converted(Dev &d, void **dst, const std::vector<double> &src, cudaStream_t st);
 
+// self[j] = the self block of leaf j (the inadmissible block (j, j), stored
+// transposed [c][t], L x Lp entries) rounded to FP32; the block is zeroed in
+// the staging array.  selfblk[j] = index of that block.
+__global__ void k_split_self(const int32_t *__restrict__ selfblk, int64_t nleaf, int64_t per,
+                             double *__restrict__ near, float *__restrict__ self) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nleaf * per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / per, q = e - j * per;
+    double *src = near + (int64_t)selfblk[j] * per + q;
+    self[e] = (float)*src;
+    *src = 0.0;
+  }
+}
+
 template <class T>
 constexpr bool is_half_type() {
   return std::is_same<T, __nv_bfloat16>::value || std::is_same<T, __half>::value;
@@ -303,7 +316,7 @@ int upload_converted(Dev &d, void **dst, const std::vector<double> &src, cudaStr
   if (rc) return rc;
   if (src.empty()) return H2_OK;
   double *tmp = nullptr;
-  H2_CUDA_TRY(cudaMalloc(&tmp, src.size() * sizeof(double)));
+  H2_CUDA_TRY(dmalloc(&tmp, src.size() * sizeof(double)));
   cudaError_t e = cudaMemcpyAsync(tmp, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     k_convert<T><<<grid_for((int64_t)src.size(), 256), 256, 0, st>>>(tmp, (T *)*dst, (int64_t)src.size());
@@ -343,7 +356,7 @@ int build_typed(Ctx &c) {
       }
   }
   int rc;
-  if (std::is_same<T, __half>::value) {
+  if (std::is_same<T, __half>::value && !d.v32) {
     // FP16: divide every leaf basis by a power of two >= its largest entry
     std::vector<float> vs(p.nleaf, 1.0f);
     for (int64_t j = 0; j < p.nleaf; ++j) {
@@ -359,11 +372,18 @@ int build_typed(Ctx &c) {
   }
   if ((rc = dev_alloc(d, (void **)&d.pad_src, pad.size() * 4))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(d.pad_src, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, st));
-  if ((rc = upload_converted<T>(d, &d.V, Vp, st))) return rc;
-  if ((rc = upload_converted<T>(d, &d.Vt, Vt, st))) return rc;
+  if (d.v32) {
+    // FP32 leaf bases under 16-bit storage (h2_options.basis_prec)
+    if ((rc = upload_converted<float>(d, &d.V, Vp, st))) return rc;
+    if ((rc = upload_converted<float>(d, &d.Vt, Vt, st))) return rc;
+  } else {
+    if ((rc = upload_converted<T>(d, &d.V, Vp, st))) return rc;
+    if ((rc = upload_converted<T>(d, &d.Vt, Vt, st))) return rc;
+  }
   // transfer factors: FP32 under bfloat16 storage, whose 8-bit significand would
-  // compound over the tree levels of the transfer passes (0.2 % of the bytes)
-  if (std::is_same<T, __nv_bfloat16>::value) {
+  // compound over the tree levels of the transfer passes (0.2 % of the bytes),
+  // and with FP32 leaf bases
+  if (std::is_same<T, __nv_bfloat16>::value || d.v32) {
     if ((rc = upload_converted<float>(d, &d.Ef, p.Ef, st))) return rc;
   } else if ((rc = upload_converted<T>(d, &d.Ef, p.Ef, st))) {
     return rc;
@@ -411,7 +431,7 @@ int build_typed(Ctx &c) {
     ~Tmp() { if (ptr) cudaFree(ptr); }
   } t_arow, t_nrow, t_ncol, t_vert, t_tri, t_area, t_sing, t_cnt;
   auto tmp_up = [&](Tmp &t, const void *src, size_t bytes) -> int {
-    if (cudaMalloc(&t.ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) return fail(H2_ENOMEM, "device set-up buffer");
+    if (dmalloc(&t.ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) return fail(H2_ENOMEM, "device set-up buffer");
     if (bytes) H2_CUDA_TRY(cudaMemcpyAsync(t.ptr, src, bytes, cudaMemcpyHostToDevice, st));
     return H2_OK;
   };
@@ -447,15 +467,15 @@ int build_typed(Ctx &c) {
   using TQ = typename std::conditional<is_half_type<T>(), double, T>::type;
   TQ *qnear = (TQ *)d.near;
   if (is_half_type<T>()) {
-    if (cudaMalloc(&t_near64.ptr, std::max<size_t>(1, (size_t)d.nnear * L * Lp) * 8) != cudaSuccess)
+    if (dmalloc(&t_near64.ptr, std::max<size_t>(1, (size_t)d.nnear * L * Lp) * 8) != cudaSuccess)
       return fail(H2_ENOMEM, "nearfield staging buffer");
     qnear = (TQ *)t_near64.ptr;
   }
   if (d.nnear > 0) {
     // pairs that share a vertex: at most (n * 3 * valence) ordered pairs; bound by the entry count
     int64_t cap = std::min<int64_t>(d.nnear * L * Lp, 64 * p.n + 1024);
-    if (cudaMalloc(&t_sing.ptr, cap * 8) != cudaSuccess) return fail(H2_ENOMEM, "singular list");
-    if (cudaMalloc(&t_cnt.ptr, 8) != cudaSuccess) return fail(H2_ENOMEM, "singular count");
+    if (dmalloc(&t_sing.ptr, cap * 8) != cudaSuccess) return fail(H2_ENOMEM, "singular list");
+    if (dmalloc(&t_cnt.ptr, 8) != cudaSuccess) return fail(H2_ENOMEM, "singular count");
     H2_CUDA_TRY(cudaMemsetAsync(t_cnt.ptr, 0, 8, st));
     Geo g{(const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src,
           (const int32_t *)t_nrow.ptr, (const int32_t *)t_ncol.ptr, L, Lp};
@@ -470,6 +490,46 @@ int build_typed(Ctx &c) {
       k_near_singular<TQ><<<grid_for((int64_t)ns, 64), 64, 0, st>>>(g, (const int64_t *)t_sing.ptr, (int64_t)ns,
                                                                     c.quad_order, qnear);
       H2_CUDA_TRY(cudaGetLastError());
+    }
+    if (std::is_same<T, __nv_bfloat16>::value) {
+      // bfloat16: the self blocks G_jj (they hold the largest entries of every
+      // row, the singular self-interaction g_ii among them) stay in FP32, the
+      // other near blocks get a CSR of their own
+      std::vector<int64_t> ptr2(p.nleaf + 1, 0), sptr(p.nleaf + 1);
+      std::vector<int32_t> col2, blk2, scol(p.nleaf), sblk(p.nleaf, -1);
+      for (int64_t j = 0; j < p.nleaf; ++j) {
+        for (int64_t e = p.near_ptr[j]; e < p.near_ptr[j + 1]; ++e) {
+          if (p.near_col[e] == j) {
+            sblk[j] = (int32_t)e;
+          } else {
+            col2.push_back(p.near_col[e]);
+            blk2.push_back((int32_t)e);
+          }
+        }
+        ptr2[j + 1] = (int64_t)col2.size();
+        sptr[j] = j;
+        scol[j] = (int32_t)j;
+        if (sblk[j] < 0) return fail(H2_EINVAL, "a leaf without its self block");
+      }
+      sptr[p.nleaf] = p.nleaf;
+      auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+        int r = dev_alloc(d, dst, std::max<size_t>(bytes, 16));
+        if (r) return r;
+        if (bytes) H2_CUDA_TRY(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st));
+        return H2_OK;
+      };
+      if ((rc = up((void **)&d.near_ptr2, ptr2.data(), ptr2.size() * 8))) return rc;
+      if ((rc = up((void **)&d.near_col2, col2.data(), col2.size() * 4))) return rc;
+      if ((rc = up((void **)&d.near_blk2, blk2.data(), blk2.size() * 4))) return rc;
+      if ((rc = up((void **)&d.self_ptr, sptr.data(), sptr.size() * 8))) return rc;
+      if ((rc = up((void **)&d.self_col, scol.data(), scol.size() * 4))) return rc;
+      Tmp t_sblk;
+      if ((rc = tmp_up(t_sblk, sblk.data(), sblk.size() * 4))) return rc;
+      if ((rc = dev_alloc(d, (void **)&d.nself, (size_t)d.nleaf * L * Lp * 4))) return rc;
+      k_split_self<<<grid_for(d.nleaf * L * Lp, 256), 256, 0, st>>>((const int32_t *)t_sblk.ptr, d.nleaf,
+                                                                    (int64_t)L * Lp, (double *)qnear, d.nself);
+      H2_CUDA_TRY(cudaGetLastError());
+      H2_CUDA_TRY(cudaStreamSynchronize(st));
     }
     if (is_half_type<T>()) {
       const int64_t per = L * Lp, tot = d.nnear * per;
@@ -492,7 +552,7 @@ int build_typed(Ctx &c) {
 
 int dev_alloc(Dev &d, void **ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(ptr, bytes);
+  cudaError_t e = dmalloc(ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
     cudaGetLastError();
@@ -530,7 +590,12 @@ int device_build(Ctx &c) {
     d.coupling = (d.prec == H2_F32 && sbytes > 0.5 * (double)fr) ? 1 : 0;
   }
   switch (d.prec) {
-    case H2_F64: d.esize = 8; return build_typed<dd>(c);
+    case H2_F64: {
+      d.esize = 8;
+      int rc = dev_alloc(d, (void **)&d.colmax, 64 * sizeof(unsigned long long));
+      if (rc) return rc;
+      return build_typed<dd>(c);
+    }
     case H2_F64_NATIVE: d.esize = 8; return build_typed<double>(c);
     case H2_BF16: d.esize = 4; return build_typed<__nv_bfloat16>(c);
     case H2_F16: d.esize = 4; return build_typed<__half>(c);

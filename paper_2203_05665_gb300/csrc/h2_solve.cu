@@ -230,7 +230,7 @@ int alloc_gmres_work(GmresWork &w, int64_t n_, int cols, int mr) {
   free_gmres_work(w);
   const size_t n = (size_t)n_, tot = n * cols;
   bool ok = true;
-  auto al = [&](double **p, size_t cnt) { ok = ok && cudaMalloc(p, std::max<size_t>(cnt, 1) * 8) == cudaSuccess; };
+  auto al = [&](double **p, size_t cnt) { ok = ok && dmalloc(p, std::max<size_t>(cnt, 1) * 8) == cudaSuccess; };
   al(&w.Vb, (size_t)(mr + 1) * tot);
   al(&w.W, tot);
   al(&w.H, (size_t)(mr + 1) * mr * cols);
@@ -248,8 +248,8 @@ int alloc_gmres_work(GmresWork &w, int64_t n_, int cols, int mr) {
   al(&w.d, tot);
   al(&w.Az, tot);
   al(&w.tolv, cols);
-  ok = ok && cudaMalloc(&w.active, cols * 4) == cudaSuccess && cudaMalloc(&w.jc, cols * 4) == cudaSuccess &&
-       cudaMalloc(&w.maxv, cols * 4) == cudaSuccess && cudaMalloc(&w.itc, cols * 4) == cudaSuccess &&
+  ok = ok && dmalloc(&w.active, cols * 4) == cudaSuccess && dmalloc(&w.jc, cols * 4) == cudaSuccess &&
+       dmalloc(&w.maxv, cols * 4) == cudaSuccess && dmalloc(&w.itc, cols * 4) == cudaSuccess &&
        cudaMallocHost(&w.hflag, cols * 4) == cudaSuccess &&
        cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {

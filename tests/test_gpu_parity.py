@@ -17,11 +17,14 @@ pytestmark = pytest.mark.gpu
 
 # f64: double-float arithmetic; f64n: native FP64; bf16 / f16: 16-bit storage with FP32
 # accumulation and the coupling regenerated in FP32.  FP16 keeps 11 significant bits
-# (rounding error <= 2^-12 per stored entry), which meets the 2e-3 budget with room.
-# BF16 keeps 8 (<= 2^-9 = 1.95e-3 per entry), and the interpolation bases amplify the
-# error of V and E by their Lebesgue constant (about (2/pi log m + 1)^3, 5 to 8 for
-# m = 4, 5), so BF16 is held to 4e-3; its measured errors are reported in the design notes.
-TOL = {"f64": 1e-12, "f32": 1e-6, "f64n": 1e-12, "bf16": 4e-3, "f16": 2e-3}
+# (relative rounding error <= 2^-11 per stored entry), which meets the 2e-3 budget with
+# room.  BF16 keeps 8 (<= 2^-8 = 3.9e-3 per entry): a nearfield fully in bfloat16 gives
+# 1e-3 to 2.1e-3 on these meshes (the largest entries, the singular self-interactions,
+# dominate and do not average out), so a BF16 handle keeps the self blocks G_jj of the
+# leaves in FP32 (about a tenth of the nearfield) and its leaf bases and transfer factors
+# in FP32 (bfloat16 leaf bases add about 1e-3, amplified by the Lebesgue constant of the
+# interpolation).
+TOL = {"f64": 1e-12, "f32": 1e-6, "f64n": 1e-12, "bf16": 2e-3, "f16": 2e-3}
 
 
 def _rel(a, b):
@@ -75,6 +78,61 @@ def test_matvec_matches_oracle(require_gpu, name, prec):
     y1 = h.matvec_host(np.ones((n, 1)))
     assert _rel(y1, o.matvec(np.ones((n, 1)))) <= TOL[prec]
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64n", "bf16", "f16"])
+@pytest.mark.parametrize("name", ["ico4_m3", "ico3_m4", "ico0_near_only"])
+def test_matvec_acc_matches_oracle(require_gpu, name, prec):
+    """h2_matvec_acc: y <- y0 + G~ x, the accumulating form of Section 2, against
+    y0 + the oracle's product; y0 of the size of G~ x so that a dropped or doubled
+    y0 shows.  ico0 has no far field (the nearfield writes the padded output)."""
+    import torch
+    v, f, o = _oracle(name)
+    make, leaf, eta, m = CASES[name]
+    h = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec=prec)
+    n = f.shape[0]
+    dt = torch.float64 if prec in ("f64", "f64n") else torch.float32
+    for nrhs in (1, 3, 16):
+        x = I.uniform_rhs(n, nrhs, 4100 + nrhs)
+        ref = o.matvec(x)
+        y0 = I.uniform_rhs(n, nrhs, 4200 + nrhs) * np.abs(ref).max()
+        y0 = y0.astype(np.float32).astype(np.float64) if dt == torch.float32 else y0
+        xd = colmajor(torch.from_numpy(x).to(device="cuda", dtype=dt))
+        yd = colmajor(torch.from_numpy(y0).to(device="cuda", dtype=dt))
+        h.matvec_acc(xd, yd)
+        y = yd.cpu().double().numpy()
+        err = np.linalg.norm(y - (y0 + ref)) / np.linalg.norm(ref)
+        assert err <= TOL[prec], (name, prec, nrhs, err)
+        # twice: y0 + 2 G~ x
+        h.matvec_acc(xd, yd)
+        y2 = yd.cpu().double().numpy()
+        assert np.linalg.norm(y2 - (y0 + 2 * ref)) / np.linalg.norm(2 * ref) <= TOL[prec]
+    h.close()
+
+
+def test_basis_precision_option(require_gpu):
+    """basis_prec: BF16 handles keep V and E in FP32 by default, FP16 handles in
+    FP16; either may be asked for explicitly.  Every variant that the library
+    offers by default, and FP16 with FP32 bases, meets the 2e-3 budget."""
+    v, f, o = _oracle("ico3_m4")
+    n = f.shape[0]
+    x = I.uniform_rhs(n, 4, 4300)
+    ref = o.matvec(x)
+    sizes = {}
+    for prec, basis, expect, gated in (("bf16", None, "f32", True), ("bf16", "f32", "f32", True),
+                                       ("bf16", "bf16", "bf16", False), ("f16", None, "f16", True),
+                                       ("f16", "f32", "f32", True), ("f16", "f16", "f16", True)):
+        h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=4, prec=prec, basis=basis)
+        assert h.stats["basis_prec"] == {"f32": 1, "bf16": 3, "f16": 4}[expect]
+        sizes[(prec, basis)] = h.stats["device_bytes"]
+        err = _rel(h.matvec_host(x), ref)
+        assert np.isfinite(err) and err < 1e-2
+        if gated:
+            assert err <= TOL[prec], (prec, basis, err)
+        h.close()
+    # FP32 bases hold twice the bytes of 16-bit ones
+    assert sizes[("bf16", None)] > sizes[("bf16", "bf16")]
+    assert sizes[("f16", "f32")] > sizes[("f16", None)]
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f64n"])
@@ -368,3 +426,36 @@ def test_f32_tensor_core_coupling(require_gpu, name):
     assert torch.equal(y1, y2)
     ht.close()
     hd.close()
+
+
+def test_double_float_range_guard(require_gpu):
+    """H2_F64 stores pairs of FP32 numbers: columns of x far outside FP32's
+    exponent range are scaled by a power of two on the way in and back on the way
+    out, so each column keeps the 1e-12 accuracy; meshes whose entries would leave
+    the range are refused at build time."""
+    from paper_2203_05665_gb300 import H2Error
+    v, f, o = _oracle("ico3_m4")
+    n = f.shape[0]
+    h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=4, prec="f64")
+    scales = [1.0, 1e-280, 1e-40, 1e-13, 1e13, 1e40, 1e280]
+    x = np.concatenate([s * I.uniform_rhs(n, 1, 4400 + i) for i, s in enumerate(scales)], axis=1)
+    ref = o.matvec(x)
+    for nrhs in (len(scales), 3):
+        y = h.matvec_host(x[:, :nrhs])
+        for c in range(nrhs):
+            # compare at unit scale: the 2-norm of 1e-280-sized vectors underflows in numpy
+            e = _rel(y[:, c] / scales[c], ref[:, c] / scales[c])
+            assert e <= TOL["f64"], (scales[c], e)
+    # the diagnostics report the coefficients of the caller's (unscaled) x
+    _, xh, _ = o.matvec(x[:, :3], coeffs=True)
+    h.matvec_host(x[:, :3])
+    xg = h.coefficients(0, 3)
+    first = 2 ** h.stats["first_adm_level"] - 1
+    for c in range(3):
+        assert _rel(xg[first:, :, c] / scales[c], xh[first:, :, c] / scales[c]) <= 1e-13
+    h.close()
+    for sc in (1e-12, 1e20):
+        with pytest.raises(H2Error, match="double-float range"):
+            H2Matrix(v * sc, f, leaf_size=32, eta=2.0, order=3, prec="f64")
+    # FP64 storage takes the same meshes
+    H2Matrix(v * 1e-12, f, leaf_size=32, eta=2.0, order=3, prec="f64n").close()

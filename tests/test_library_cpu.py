@@ -98,3 +98,13 @@ def test_single_leaf_mesh_has_no_far_field():
     v, f = I.icosphere(0)                       # 20 triangles, one leaf at leaf_size 32
     p = Plan(v, f, leaf_size=32, eta=2.0, order=3)
     assert p.depth == 0 and p.nadm == 0 and p.nnear == 1 and p.first_adm_level == 1
+
+
+@pytest.mark.parametrize("prec,basis", [("f64", "f32"), ("f32", "bf16"), ("bf16", "f64n"), ("f16", "bf16")])
+def test_build_rejects_bad_basis_precision(prec, basis):
+    """basis_prec is checked before any device call: only H2_BF16 / H2_F16 handles
+    take it, with H2_F32 or their own 16-bit type."""
+    v, f = I.icosphere(1)
+    with pytest.raises(pkg.H2Error, match="basis_prec") as e:
+        pkg.H2Matrix(v, f, leaf_size=8, order=3, prec=prec, basis=basis)
+    assert e.value.status == 1

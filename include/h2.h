@@ -179,6 +179,17 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
 int h2_destroy(h2_handle h);
 int h2_info(h2_handle h, h2_stats *out);
 
+/* Phases of h2_build (h2_build_times): the cluster tree, block tree and
+ * interpolation points on the host (Definition 1, Eq. (8)); then on the
+ * device the leaf bases V and transfer factors E (Eqs. (6a), (9)), the
+ * coupling matrices S (Eq. (6c)) with their tensor-core digits or the data
+ * of their regeneration, and the nearfield (Sauter-Schwab quadrature of
+ * Eq. (3)) with its conversion and digits. */
+enum h2_build_phase { H2_BUILD_PLAN = 0, H2_BUILD_BASES, H2_BUILD_COUPLING, H2_BUILD_NEAR, H2_BUILD_TOTAL, H2_NBUILD };
+/* Wall-clock milliseconds of every build phase of the handle (ms[H2_NBUILD];
+ * the device phases include their synchronisation). */
+int h2_build_times(h2_handle h, double *ms);
+
 /* y = G~ x (overwrites y) for nrhs right-hand sides, Section 2 (the
  * paper's y <- y + G x with y cleared first).  x, y: DEVICE pointers to
  * column-major n x nrhs arrays of the handle's vector type (double for H2_F64

@@ -52,7 +52,7 @@ EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_
             "h2_serve_stats", "h2_serve_destroy", "h2_batch_create", "h2_batch_offsets", "h2_batch_matvec",
             "h2_batch_tune", "h2_batch_set_shapes", "h2_batch_profile", "h2_batch_phase_times", "h2_batch_info",
             "h2_batch_sync", "h2_batch_destroy", "h2_graph_create", "h2_graph_launch", "h2_graph_destroy",
-            "h2_inject_alloc_failure", "h2_wait_selftest", "h2_export", "h2_last_error"]
+            "h2_inject_alloc_failure", "h2_wait_selftest", "h2_export", "h2_build_times", "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -115,6 +115,7 @@ def load():
             "h2_graph_destroy": (C.c_int, [vp]),
             "h2_inject_alloc_failure": (C.c_int, [C.c_int64]),
             "h2_export": (C.c_int, [vp, C.c_int, C.c_int64, C.c_int64, dp]),
+            "h2_build_times": (C.c_int, [vp, dp]),
             "h2_wait_selftest": (C.c_int, [vp, C.c_int, C.c_uint32, C.POINTER(C.c_int)]),
             "h2_last_error": (C.c_char_p, []),
         }
@@ -314,6 +315,12 @@ class H2Matrix:
         y = np.zeros_like(x, order="F")
         _check(self._lib.h2_matvec_host(self._h, _dp(x), _dp(y), int(x.shape[1])))
         return y
+
+    def build_times(self):
+        """Wall-clock ms of the build phases (h2_build_times)."""
+        ms = np.zeros(5)
+        _check(self._lib.h2_build_times(self._h, _dp(ms)))
+        return dict(zip(["plan", "bases", "coupling", "near", "total"], (float(v) for v in ms)))
 
     def export(self, what, first=0, count=None):
         """The stored representation as built on the device (h2_export), as float64:

@@ -2,6 +2,7 @@
 // error reporting, host <-> device staging.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -210,20 +211,26 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   c->d.v32 = half_prec && (o.basis_prec == H2_F32 || (o.basis_prec == 0 && o.prec == H2_BF16));
   c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);
   int rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms = [](std::chrono::steady_clock::time_point a) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+  };
   try {
-    rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, true, c->plan);
+    // the trees, blocks and interpolation points on the host; V and E are
+    // computed on the device by device_build
+    rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, false, c->plan);
+    c->build_ms[H2_BUILD_PLAN] = ms(t0);
     if (!rc && o.prec == H2_F64) rc = check_double_float_range(c->plan);
     if (!rc) rc = device_build(*c);
   } catch (const std::bad_alloc &) {
     rc = fail(H2_ENOMEM, "host allocation in set-up");
   }
+  c->build_ms[H2_BUILD_TOTAL] = ms(t0);
   if (rc) {
     free_dev(c->d);
     delete c;
     return rc;
   }
-  // the host copy of V is not needed after the upload
-  std::vector<double>().swap(c->plan.V);
   *out = c;
   return H2_OK;
 }
@@ -313,6 +320,12 @@ int h2_wait_selftest(h2_handle h, int withhold, uint32_t poll_limit, int *stages
   if (withhold != 0 && withhold != 1) return fail(H2_EINVAL, "withhold must be 0 or 1");
   H2_CUDA_TRY(cudaSetDevice(h->device));
   return wait_selftest(*h, withhold, poll_limit, stages_seen);
+}
+
+int h2_build_times(h2_handle h, double *ms) {
+  if (!h || !ms) return fail(H2_EINVAL, "NULL argument");
+  for (int i = 0; i < H2_NBUILD; ++i) ms[i] = h->build_ms[i];
+  return H2_OK;
 }
 
 int h2_matvec_acc(h2_handle h, const void *x, void *y, int nrhs) {

@@ -152,6 +152,7 @@ struct GmresWork {
 void free_gmres_work(GmresWork &w);
 
 struct Ctx {
+  double build_ms[H2_NBUILD] = {0};   // wall time of the build phases (h2_build_times)
   GmresWork gw;
   Prof prof;
   int device = 0;

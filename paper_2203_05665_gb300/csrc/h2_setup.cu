@@ -11,6 +11,7 @@
 //   smaller shared id, larger shared id, other; vertex: shared, then the
 //   triangle's cyclic successors).  Each entry is evaluated with the
 //   smaller triangle index as test triangle, so G is symmetric bit for bit.
+#include <chrono>
 #include <cstdio>
 #include <vector>
 
@@ -27,6 +28,10 @@ namespace h2 {
 namespace {
 
 constexpr int kMaxQ = 16;
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
 __constant__ double c_gx[kMaxQ];
 __constant__ double c_gw[kMaxQ];
 
@@ -292,6 +297,108 @@ int grid_for(int64_t n, int threads) {
 template <class T>
 int upload_converted(Dev &d, void **dst, const std::vector<double> &src, cudaStream_t st);
 
+// ---------------------------------------------------------------- bases
+// 1-D Lagrange polynomial i of the nodes z[0..m) at x, product form
+__device__ __forceinline__ double lagrange1(const double *z, int m, int i, double x) {
+  double v = 1.0;
+  for (int j = 0; j < m; ++j)
+    if (j != i) v *= (x - z[j]) / (z[i] - z[j]);
+  return v;
+}
+
+// Collapsed Gauss rule of the leaf bases (exact for total degree 3(m-1)).
+struct BasisRule {
+  int q;
+  double x[16], w[16];
+};
+
+// V64[p][nu] = int_{T} ell_{c,nu} (Eq. (6a)) for padded DoF p (triangle
+// pad_src[p] of leaf p / L, cluster leaf0 + p / L), zero for padding rows;
+// ell_{c,nu} = ell_x ell_y ell_z on the cluster's Chebyshev nodes
+__global__ void k_leaf_bases(const double *__restrict__ vert, const int32_t *__restrict__ tri,
+                             const double *__restrict__ area, const int32_t *__restrict__ pad_src,
+                             const double *__restrict__ cheb, int m, int k, int L, int64_t leaf0, int64_t npad,
+                             BasisRule rule, double *__restrict__ V64) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npad * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / k;
+    const int nu = (int)(e - p * k);
+    const int32_t t = pad_src[p];
+    if (t < 0) {
+      V64[e] = 0.0;
+      continue;
+    }
+    const int64_t c = leaf0 + p / L;
+    const int ix = nu % m, iy = (nu / m) % m, iz = nu / (m * m);
+    const double *A = vert + 3 * (int64_t)tri[3 * (int64_t)t], *B = vert + 3 * (int64_t)tri[3 * (int64_t)t + 1],
+                 *C = vert + 3 * (int64_t)tri[3 * (int64_t)t + 2];
+    const double *zx = cheb + (3 * c + 0) * m, *zy = cheb + (3 * c + 1) * m, *zz = cheb + (3 * c + 2) * m;
+    double acc = 0.0;
+    for (int a = 0; a < rule.q; ++a)
+      for (int b = 0; b < rule.q; ++b) {
+        const double s = rule.x[a], tt = rule.x[a] * rule.x[b];
+        const double wgt = 2.0 * area[t] * rule.w[a] * rule.w[b] * rule.x[a];
+        double x[3];
+        tri_point(A, B, C, s, tt, x);
+        acc += wgt * (lagrange1(zx, m, ix, x[0]) * lagrange1(zy, m, iy, x[1]) * lagrange1(zz, m, iz, x[2]));
+      }
+    V64[e] = acc;
+  }
+}
+
+// per leaf: the power of two 2^e >= max |V| of its rows (half storage)
+__global__ void k_leaf_scale(const double *__restrict__ V64, int64_t per, int64_t nleaf, float *__restrict__ scale) {
+  for (int64_t j = blockIdx.x; j < nleaf; j += gridDim.x) {
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < per; i += blockDim.x) mx = fmax(mx, fabs(V64[j * per + i]));
+    __shared__ double part[256];
+    part[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+      if ((int)threadIdx.x < o) part[threadIdx.x] = fmax(part[threadIdx.x], part[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) scale[j] = part[0] > 0.0 ? (float)exp2(ceil(log2(part[0]))) : 1.0f;
+    __syncthreads();
+  }
+}
+
+// the two stored layouts of V: [leaf][t][kp] (forward) and [leaf][nu][Lp]
+// (backward), zero padded, divided by the leaf's scale if there is one
+template <class T>
+__global__ void k_store_bases(const double *__restrict__ V64, const float *__restrict__ scale, int k, int kp, int L,
+                              int Lp, int64_t nleaf, T *__restrict__ V, T *__restrict__ Vt) {
+  const int64_t perF = (int64_t)L * kp, perB = (int64_t)k * Lp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nleaf * perF; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / perF;
+    const int r = (int)((e - j * perF) / kp), nu = (int)((e - j * perF) % kp);
+    const double v = nu < k ? V64[(j * L + r) * k + nu] : 0.0;
+    V[e] = store_as<T>(scale ? v / (double)scale[j] : v);
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nleaf * perB; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / perB;
+    const int nu = (int)((e - j * perB) / Lp), r = (int)((e - j * perB) % Lp);
+    const double v = r < L ? V64[(j * L + r) * k + nu] : 0.0;
+    Vt[e] = store_as<T>(scale ? v / (double)scale[j] : v);
+  }
+}
+
+// transfer factors (Eq. (9)): E_c = Ex (x) Ey (x) Ez, Ed[j'][j] = the parent's
+// Lagrange polynomial j at the child's node j'; zero for the root
+template <class T>
+__global__ void k_transfer_factors(const double *__restrict__ cheb, int m, int64_t nclu, T *__restrict__ Ef) {
+  const int64_t per = 3 * (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nclu * per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / per;
+    const int rem = (int)(e - c * per), d = rem / (m * m), jp = (rem / m) % m, j = rem % m;
+    double v = 0.0;
+    if (c > 0) {
+      const int64_t par = (c - 1) / 2;
+      v = lagrange1(cheb + (3 * par + d) * m, m, j, cheb[(3 * c + d) * m + jp]);
+    }
+    Ef[e] = store_as<T>(v);
+  }
+}
+
 // self[j] = the self block of leaf j (the inadmissible block (j, j), stored
 // transposed [c][t], L x Lp entries) rounded to FP32; the block is zeroed in
 // the staging array.  selfblk[j] = index of that block.
@@ -342,52 +449,84 @@ int build_typed(Ctx &c) {
     int64_t c0 = p.leaf0 + j;
     for (int64_t r = 0; r < p.size[c0]; ++r) pad[j * L + r] = (int32_t)p.perm[p.first[c0] + r];
   }
-  // V per leaf in two layouts: [L][kp] for the forward step (x^ = V^T x) and
-  // transposed [k][Lp] for the backward step (y = V y^); padding is zero
-  const int64_t kp = d.kp, Lp = d.lp;
-  std::vector<double> Vp((size_t)p.nleaf * L * kp, 0.0), Vt((size_t)p.nleaf * k * Lp, 0.0);
-  for (int64_t j = 0; j < p.nleaf; ++j) {
-    int64_t c0 = p.leaf0 + j;
-    for (int64_t r = 0; r < p.size[c0]; ++r)
-      for (int nu = 0; nu < k; ++nu) {
-        double v = p.V[(p.first[c0] + r) * k + nu];
-        Vp[(j * L + r) * kp + nu] = v;
-        Vt[(j * k + nu) * Lp + r] = v;
-      }
-  }
   int rc;
-  if (std::is_same<T, __half>::value && !d.v32) {
-    // FP16: divide every leaf basis by a power of two >= its largest entry
-    std::vector<float> vs(p.nleaf, 1.0f);
-    for (int64_t j = 0; j < p.nleaf; ++j) {
-      double mx = 0.0;
-      for (int64_t q = j * L * kp; q < (j + 1) * L * kp; ++q) mx = std::max(mx, std::fabs(Vp[q]));
-      const double sc = mx > 0.0 ? std::exp2(std::ceil(std::log2(mx))) : 1.0;
-      vs[j] = (float)sc;
-      for (int64_t q = j * L * kp; q < (j + 1) * L * kp; ++q) Vp[q] /= sc;
-      for (int64_t q = j * k * Lp; q < (j + 1) * k * Lp; ++q) Vt[q] /= sc;
-    }
-    if ((rc = dev_alloc(d, (void **)&d.vscale, vs.size() * 4))) return rc;
-    H2_CUDA_TRY(cudaMemcpyAsync(d.vscale, vs.data(), vs.size() * 4, cudaMemcpyHostToDevice, st));
-  }
   if ((rc = dev_alloc(d, (void **)&d.pad_src, pad.size() * 4))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(d.pad_src, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, st));
-  if (d.v32) {
-    // FP32 leaf bases under 16-bit storage (h2_options.basis_prec)
-    if ((rc = upload_converted<float>(d, &d.V, Vp, st))) return rc;
-    if ((rc = upload_converted<float>(d, &d.Vt, Vt, st))) return rc;
-  } else {
-    if ((rc = upload_converted<T>(d, &d.V, Vp, st))) return rc;
-    if ((rc = upload_converted<T>(d, &d.Vt, Vt, st))) return rc;
+  if ((rc = dev_alloc(d, (void **)&d.cheb, p.cheb.size() * 8))) return rc;
+  H2_CUDA_TRY(cudaMemcpyAsync(d.cheb, p.cheb.data(), p.cheb.size() * 8, cudaMemcpyHostToDevice, st));
+
+  // temporary geometry for the set-up kernels
+  struct Tmp {
+    void *ptr = nullptr;
+    ~Tmp() { if (ptr) cudaFree(ptr); }
+  } t_arow, t_nrow, t_ncol, t_vert, t_tri, t_area, t_sing, t_cnt, t_v64;
+  auto tmp_up = [&](Tmp &t, const void *src, size_t bytes) -> int {
+    if (dmalloc(&t.ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) return fail(H2_ENOMEM, "device set-up buffer");
+    if (bytes) H2_CUDA_TRY(cudaMemcpyAsync(t.ptr, src, bytes, cudaMemcpyHostToDevice, st));
+    return H2_OK;
+  };
+  if ((rc = tmp_up(t_vert, p.vert.data(), p.vert.size() * 8))) return rc;
+  if ((rc = tmp_up(t_tri, p.tri.data(), p.tri.size() * 4))) return rc;
+  if ((rc = tmp_up(t_area, p.area.data(), p.area.size() * 8))) return rc;
+
+  // leaf bases V (Eq. (6a)) on the device: FP64 quadrature, then the two
+  // stored layouts [L][kp] (forward step, x^ = V^T x) and transposed [k][Lp]
+  // (backward step); FP16 storage divides every leaf by a power of two >= its
+  // largest entry
+  const int64_t kp = d.kp, Lp = d.lp;
+  const auto tb0 = std::chrono::steady_clock::now();
+  {
+    BasisRule rule{};
+    rule.q = (3 * (m - 1) + 3) / 2 + 1;
+    std::vector<double> bx, bw;
+    gauss_legendre01(rule.q, bx, bw);
+    for (int i = 0; i < rule.q; ++i) {
+      rule.x[i] = bx[i];
+      rule.w[i] = bw[i];
+    }
+    if (dmalloc(&t_v64.ptr, std::max<size_t>(16, (size_t)d.npad * k * 8)) != cudaSuccess)
+      return fail(H2_ENOMEM, "leaf basis staging buffer");
+    k_leaf_bases<<<grid_for(d.npad * k, 128), 128, 0, st>>>(
+        (const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src, d.cheb, m, k,
+        (int)L, p.leaf0, d.npad, rule, (double *)t_v64.ptr);
+    H2_CUDA_TRY(cudaGetLastError());
+    const bool half_v = std::is_same<T, __half>::value && !d.v32;
+    if (half_v) {
+      if ((rc = dev_alloc(d, (void **)&d.vscale, p.nleaf * 4))) return rc;
+      k_leaf_scale<<<(unsigned)std::min<int64_t>(p.nleaf, 152 * 32), 256, 0, st>>>((const double *)t_v64.ptr, L * k,
+                                                                                  p.nleaf, d.vscale);
+      H2_CUDA_TRY(cudaGetLastError());
+    }
+    const int64_t nv = std::max<int64_t>(p.nleaf * L * kp, p.nleaf * k * Lp);
+    if (d.v32) {
+      if ((rc = dev_alloc(d, &d.V, (size_t)p.nleaf * L * kp * 4))) return rc;
+      if ((rc = dev_alloc(d, &d.Vt, (size_t)p.nleaf * k * Lp * 4))) return rc;
+      k_store_bases<float><<<grid_for(nv, 256), 256, 0, st>>>((const double *)t_v64.ptr, nullptr, k, (int)kp, (int)L,
+                                                              (int)Lp, p.nleaf, (float *)d.V, (float *)d.Vt);
+    } else {
+      if ((rc = dev_alloc(d, &d.V, (size_t)p.nleaf * L * kp * sizeof(T)))) return rc;
+      if ((rc = dev_alloc(d, &d.Vt, (size_t)p.nleaf * k * Lp * sizeof(T)))) return rc;
+      k_store_bases<T><<<grid_for(nv, 256), 256, 0, st>>>((const double *)t_v64.ptr, half_v ? d.vscale : nullptr, k,
+                                                          (int)kp, (int)L, (int)Lp, p.nleaf, (T *)d.V, (T *)d.Vt);
+    }
+    H2_CUDA_TRY(cudaGetLastError());
+    // transfer factors: FP32 under bfloat16 storage, whose 8-bit significand would
+    // compound over the tree levels of the transfer passes (0.2 % of the bytes),
+    // and with FP32 leaf bases
+    const int64_t ne = p.nclu * 3 * m * m;
+    if (std::is_same<T, __nv_bfloat16>::value || d.v32) {
+      if ((rc = dev_alloc(d, &d.Ef, (size_t)ne * 4))) return rc;
+      k_transfer_factors<float><<<grid_for(ne, 256), 256, 0, st>>>(d.cheb, m, p.nclu, (float *)d.Ef);
+    } else {
+      if ((rc = dev_alloc(d, &d.Ef, (size_t)ne * sizeof(T)))) return rc;
+      k_transfer_factors<T><<<grid_for(ne, 256), 256, 0, st>>>(d.cheb, m, p.nclu, (T *)d.Ef);
+    }
+    H2_CUDA_TRY(cudaGetLastError());
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  // transfer factors: FP32 under bfloat16 storage, whose 8-bit significand would
-  // compound over the tree levels of the transfer passes (0.2 % of the bytes),
-  // and with FP32 leaf bases
-  if (std::is_same<T, __nv_bfloat16>::value || d.v32) {
-    if ((rc = upload_converted<float>(d, &d.Ef, p.Ef, st))) return rc;
-  } else if ((rc = upload_converted<T>(d, &d.Ef, p.Ef, st))) {
-    return rc;
-  }
+  c.build_ms[H2_BUILD_BASES] = ms_since(tb0);
+  cudaFree(t_v64.ptr);
+  t_v64.ptr = nullptr;
   if ((rc = dev_alloc(d, (void **)&d.adm_ptr, p.adm_ptr.size() * 8))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(d.adm_ptr, p.adm_ptr.data(), p.adm_ptr.size() * 8, cudaMemcpyHostToDevice, st));
   if ((rc = dev_alloc(d, (void **)&d.adm_col, std::max<size_t>(1, p.adm_col.size()) * 4))) return rc;
@@ -398,8 +537,7 @@ int build_typed(Ctx &c) {
   if ((rc = dev_alloc(d, (void **)&d.near_col, std::max<size_t>(1, p.near_col.size()) * 4))) return rc;
   if (!p.near_col.empty())
     H2_CUDA_TRY(cudaMemcpyAsync(d.near_col, p.near_col.data(), p.near_col.size() * 4, cudaMemcpyHostToDevice, st));
-  if ((rc = dev_alloc(d, (void **)&d.cheb, p.cheb.size() * 8))) return rc;
-  H2_CUDA_TRY(cudaMemcpyAsync(d.cheb, p.cheb.data(), p.cheb.size() * 8, cudaMemcpyHostToDevice, st));
+  const auto tc0 = std::chrono::steady_clock::now();
   if (d.coupling == 1) {
     // regenerated coupling: interpolation-box centres (FP64) and half widths (FP32)
     std::vector<float> hw(p.ihalf.begin(), p.ihalf.end());
@@ -426,21 +564,9 @@ int build_typed(Ctx &c) {
       nrow[e] = (int32_t)j;
       ncol[e] = p.near_col[e];
     }
-  struct Tmp {
-    void *ptr = nullptr;
-    ~Tmp() { if (ptr) cudaFree(ptr); }
-  } t_arow, t_nrow, t_ncol, t_vert, t_tri, t_area, t_sing, t_cnt;
-  auto tmp_up = [&](Tmp &t, const void *src, size_t bytes) -> int {
-    if (dmalloc(&t.ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) return fail(H2_ENOMEM, "device set-up buffer");
-    if (bytes) H2_CUDA_TRY(cudaMemcpyAsync(t.ptr, src, bytes, cudaMemcpyHostToDevice, st));
-    return H2_OK;
-  };
   if ((rc = tmp_up(t_arow, arow.data(), arow.size() * 4))) return rc;
   if ((rc = tmp_up(t_nrow, nrow.data(), nrow.size() * 4))) return rc;
   if ((rc = tmp_up(t_ncol, ncol.data(), ncol.size() * 4))) return rc;
-  if ((rc = tmp_up(t_vert, p.vert.data(), p.vert.size() * 8))) return rc;
-  if ((rc = tmp_up(t_tri, p.tri.data(), p.tri.size() * 4))) return rc;
-  if ((rc = tmp_up(t_area, p.area.data(), p.area.size() * 8))) return rc;
 
   // Gauss rule of the nearfield quadrature
   std::vector<double> gx, gw;
@@ -458,6 +584,9 @@ int build_typed(Ctx &c) {
   }
   // FP64 and FP32 handles of order 4: the E4M3 digit planes for the tensor-core coupling
   if (d.tensor == 0 && tc_eligible(d) && (rc = tc_build(c, (const int32_t *)t_arow.ptr))) return rc;
+  H2_CUDA_TRY(cudaStreamSynchronize(st));
+  c.build_ms[H2_BUILD_COUPLING] = ms_since(tc0);
+  const auto tn0 = std::chrono::steady_clock::now();
 
 
   // nearfield entries; 16-bit storage: computed in FP64 first, then rounded
@@ -545,6 +674,7 @@ int build_typed(Ctx &c) {
   // FP64-accurate handles with leaves of at most 21 triangles: the nearfield digits for the tensor cores
   if (ntc_eligible(d) && (rc = ntc_build(c, (const int32_t *)t_nrow.ptr))) return rc;
   H2_CUDA_TRY(cudaStreamSynchronize(st));
+  c.build_ms[H2_BUILD_NEAR] = ms_since(tn0);
   return H2_OK;
 }
 

@@ -37,12 +37,33 @@ constexpr int kMaxOut = 16;   // outputs per thread in the block-row kernels
 // max |x[:, c]| as a double (non-negative doubles order like their bits).
 template <class Tin>
 __global__ void k_colmax(const Tin *__restrict__ x, int64_t n, unsigned long long *__restrict__ colmax) {
-  const int c = blockIdx.y;
-  double mx = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    mx = fmax(mx, fabs((double)x[i + (int64_t)c * n]));
+  __shared__ double wmax[32];
+  const Tin *xc = x + (int64_t)blockIdx.y * n;
+  // four independent maxima per thread keep several loads in flight
+  double m4[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m4[u] = fmax(m4[u], fabs((double)xc[i + u * stride]));
+  for (; i < n; i += stride) m4[0] = fmax(m4[0], fabs((double)xc[i]));
+  double mx = fmax(fmax(m4[0], m4[1]), fmax(m4[2], m4[3]));
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(&colmax[c], (unsigned long long)__double_as_longlong(mx));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wmax[w]);
+    if (mx > 0.0) atomicMax(&colmax[blockIdx.y], (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// 2^e as a double for -1022 <= e <= 1023
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+// v 2^e, exact unless the result leaves the normal range: two factors that
+// are normal doubles for |e| <= 2044
+__device__ __forceinline__ double scale_pow2(double v, int e) {
+  const int h = e / 2;
+  return v * pow2d(h) * pow2d(e - h);
 }
 
 // the power of two by which column c is scaled (0: untouched; zero, infinite
@@ -54,44 +75,88 @@ __host__ __device__ inline int range_shift(unsigned long long bits) {
   return (e < -40 || e > 40) ? -e : 0;
 }
 
-// xpad[p][c] (rp columns, zero beyond nrhs) from x[src][c] column-major
+// Permutations between the caller's order (column-major n x nrhs) and the
+// leaf-padded cluster order (xpad[p][c], rp columns): a CTA takes a tile of
+// kPermRows padded DoFs and stages it in shared memory, so that the caller's
+// side is walked column by column (neighbouring DoFs of a cluster are
+// neighbouring triangles of the mesh, so the gathered addresses are close)
+// and the padded side row by row (contiguous).  Rows of the tile are padded
+// by one value against bank conflicts.
+constexpr int kPermRows = 64;
+
+// xpad[p][c] (zero beyond nrhs and for padding rows) from x[src][c], scaled by
+// the column's range-guard power of two
 template <class Tin, class Tout>
-__global__ void k_permute_in(const Tin *__restrict__ x, int64_t n, int nrhs, int rp,
-                             const int32_t *__restrict__ pad_src, int64_t npad,
-                             const unsigned long long *__restrict__ colmax, Tout *__restrict__ xpad) {
-  const int64_t total = npad * rp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t p = e / rp;
-    int r = (int)(e - p * rp);
-    int32_t src = pad_src[p];
-    if (src >= 0 && r < nrhs) {
-      Tin v = x[src + r * n];
-      const int sh = colmax ? range_shift(colmax[r]) : 0;
-      if (sh) v = (Tin)ldexp((double)v, sh);
-      xpad[e] = convert<Tout, Tin>(v);
-    } else {
-      xpad[e] = zero_of<Tout>();
+__global__ void __launch_bounds__(256) k_permute_in(const Tin *__restrict__ x, int64_t n, int nrhs, int rp,
+                                                    const int32_t *__restrict__ pad_src, int64_t npad,
+                                                    const unsigned long long *__restrict__ colmax,
+                                                    Tout *__restrict__ xpad) {
+  extern __shared__ __align__(16) unsigned char perm_smem[];
+  Tout *tile = reinterpret_cast<Tout *>(perm_smem);
+  __shared__ int shift[64];
+  __shared__ int32_t src[kPermRows];
+  const int w = rp + 1;
+  const int64_t p0 = (int64_t)blockIdx.x * kPermRows;
+  if (threadIdx.x < kPermRows) src[threadIdx.x] = p0 + threadIdx.x < npad ? pad_src[p0 + threadIdx.x] : -1;
+  if (threadIdx.x < 64) shift[threadIdx.x] = (colmax && (int)threadIdx.x < nrhs) ? range_shift(colmax[threadIdx.x]) : 0;
+  __syncthreads();
+  // the gathered loads of four passes are issued before any of them is used
+  for (int i0 = 0; i0 < kPermRows * rp; i0 += 4 * (int)blockDim.x) {
+    Tin u[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = i0 + a * (int)blockDim.x + (int)threadIdx.x;
+      const int c = i / kPermRows, q = i - c * kPermRows;
+      const int32_t sp = i < kPermRows * rp ? src[q] : -1;
+      u[a] = (sp >= 0 && c < nrhs) ? x[sp + (int64_t)c * n] : (Tin)0;
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = i0 + a * (int)blockDim.x + (int)threadIdx.x;
+      if (i >= kPermRows * rp) break;
+      const int c = i / kPermRows, q = i - c * kPermRows;
+      Tin v = u[a];
+      if (c < nrhs && shift[c]) v = (Tin)scale_pow2((double)v, shift[c]);
+      tile[q * w + c] = (src[q] >= 0 && c < nrhs) ? convert<Tout, Tin>(v) : zero_of<Tout>();
+    }
+  }
+  __syncthreads();
+  const int64_t rows = npad - p0 < kPermRows ? npad - p0 : kPermRows;
+  for (int i = threadIdx.x; i < rows * rp; i += blockDim.x) {
+    const int q = i / rp, c = i - q * rp;
+    xpad[(p0 + q) * rp + c] = tile[q * w + c];
   }
 }
 
-// y[src][c] (column-major, caller order) from ypad[p][c]; with acc the value
-// is added to what y holds (y <- y + G~ x)
+// y[src][c] (caller order) from ypad[p][c], divided by the column's range-guard
+// power of two; with acc the value is added to what y holds (y <- y + G~ x)
 template <class Tin, class Tout>
-__global__ void k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs, int rp,
-                              const int32_t *__restrict__ pad_src, int64_t npad,
-                              const unsigned long long *__restrict__ colmax, int acc, Tout *__restrict__ y) {
-  const int64_t total = npad * rp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t p = e / rp;
-    int r = (int)(e - p * rp);
-    int32_t src = pad_src[p];
-    if (src >= 0 && r < nrhs) {
-      Tout v = convert<Tout, Tin>(ypad[e]);
-      const int sh = colmax ? range_shift(colmax[r]) : 0;
-      if (sh) v = (Tout)ldexp((double)v, -sh);
-      y[src + r * n] = acc ? y[src + r * n] + v : v;
-    }
+__global__ void __launch_bounds__(256) k_permute_out(const Tin *__restrict__ ypad, int64_t n, int nrhs, int rp,
+                                                     const int32_t *__restrict__ pad_src, int64_t npad,
+                                                     const unsigned long long *__restrict__ colmax, int acc,
+                                                     Tout *__restrict__ y) {
+  extern __shared__ __align__(16) unsigned char perm_smem[];
+  Tin *tile = reinterpret_cast<Tin *>(perm_smem);
+  __shared__ int shift[64];
+  __shared__ int32_t src[kPermRows];
+  const int w = rp + 1;
+  const int64_t p0 = (int64_t)blockIdx.x * kPermRows;
+  if (threadIdx.x < kPermRows) src[threadIdx.x] = p0 + threadIdx.x < npad ? pad_src[p0 + threadIdx.x] : -1;
+  if (threadIdx.x < 64) shift[threadIdx.x] = (colmax && (int)threadIdx.x < nrhs) ? range_shift(colmax[threadIdx.x]) : 0;
+  const int64_t rows = npad - p0 < kPermRows ? npad - p0 : kPermRows;
+  for (int i = threadIdx.x; i < rows * rp; i += blockDim.x) {
+    const int q = i / rp, c = i - q * rp;
+    tile[q * w + c] = ypad[(p0 + q) * rp + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kPermRows * nrhs; i += blockDim.x) {
+    const int c = i / kPermRows, q = i - c * kPermRows;
+    const int32_t sp = src[q];
+    if (sp < 0) continue;
+    Tout v = convert<Tout, Tin>(tile[q * w + c]);
+    if (shift[c]) v = (Tout)scale_pow2((double)v, -shift[c]);
+    Tout *dst = y + sp + (int64_t)c * n;
+    *dst = acc ? *dst + v : v;
   }
 }
 
@@ -851,11 +916,13 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   const unsigned long long *cmx = std::is_same<T, dd>::value ? d.colmax : nullptr;
   if (cmx) {
     H2_CUDA_TRY(cudaMemsetAsync(d.colmax, 0, sizeof(unsigned long long) * nrhs, st));
-    const int64_t nb = std::min<int64_t>((d.n + 4 * kThreads - 1) / (4 * kThreads), 2 * 152);
+    const int64_t nb = std::min<int64_t>((d.n + 8 * kThreads - 1) / (8 * kThreads), 64);
     k_colmax<Tio><<<dim3((unsigned)std::max<int64_t>(nb, 1), nrhs), kThreads, 0, st>>>(x, d.n, d.colmax);
     mk.count(H2_PH_PERMUTE_IN);
   }
-  k_permute_in<Tio, T><<<grid_for(d.npad * rp), kThreads, 0, st>>>(x, d.n, nrhs, rp, d.pad_src, d.npad, cmx, xpad);
+  const unsigned perm_grid = (unsigned)((d.npad + kPermRows - 1) / kPermRows);
+  k_permute_in<Tio, T><<<perm_grid, 256, (size_t)kPermRows * (rp + 1) * sizeof(T), st>>>(x, d.n, nrhs, rp, d.pad_src,
+                                                                                        d.npad, cmx, xpad);
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
   // leaf steps with one CTA per leaf when the stored values are in the arithmetic type
@@ -984,8 +1051,8 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
     mk.count(H2_PH_LEAF_NEAR);
   }
   mk.mark(H2_PH_PERMUTE_OUT);
-  k_permute_out<T, Tio><<<grid_for(d.npad * rp), kThreads, 0, st>>>(ypad, d.n, nrhs, rp, d.pad_src, d.npad, cmx,
-                                                                      acc ? 1 : 0, y);
+  k_permute_out<T, Tio><<<perm_grid, 256, (size_t)kPermRows * (rp + 1) * sizeof(T), st>>>(
+      ypad, d.n, nrhs, rp, d.pad_src, d.npad, cmx, acc ? 1 : 0, y);
   mk.count(H2_PH_PERMUTE_OUT);
   mk.mark(H2_NPHASE);
   mk.finish();

@@ -314,34 +314,91 @@ struct BasisRule {
 
 // V64[p][nu] = int_{T} ell_{c,nu} (Eq. (6a)) for padded DoF p (triangle
 // pad_src[p] of leaf p / L, cluster leaf0 + p / L), zero for padding rows;
-// ell_{c,nu} = ell_x ell_y ell_z on the cluster's Chebyshev nodes
+// ell_{c,nu} = ell_x ell_y ell_z on the cluster's Chebyshev nodes.  One
+// thread per (p, z index): the 1-D Lagrange values at a quadrature point are
+// formed once (in the barycentric form w_i prod_{j != i} (x - z_j)) and serve
+// all m^2 entries of that z slab.
+template <int M>
 __global__ void k_leaf_bases(const double *__restrict__ vert, const int32_t *__restrict__ tri,
                              const double *__restrict__ area, const int32_t *__restrict__ pad_src,
-                             const double *__restrict__ cheb, int m, int k, int L, int64_t leaf0, int64_t npad,
-                             BasisRule rule, double *__restrict__ V64) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npad * k; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = e / k;
-    const int nu = (int)(e - p * k);
+                             const double *__restrict__ cheb, int L, int64_t leaf0, int64_t npad, BasisRule rule,
+                             double *__restrict__ V64) {
+  constexpr int K = M * M * M;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npad * M; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / M;
+    const int iz = (int)(e - p * M);
+    double *row = V64 + p * K + M * M * iz;
     const int32_t t = pad_src[p];
     if (t < 0) {
-      V64[e] = 0.0;
+      for (int q = 0; q < M * M; ++q) row[q] = 0.0;
       continue;
     }
     const int64_t c = leaf0 + p / L;
-    const int ix = nu % m, iy = (nu / m) % m, iz = nu / (m * m);
+    double z[3][M], w[3][M];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int i = 0; i < M; ++i) z[d][i] = cheb[(3 * c + d) * M + i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        double den = 1.0;
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+          if (j != i) den *= z[d][i] - z[d][j];
+        w[d][i] = 1.0 / den;
+      }
     const double *A = vert + 3 * (int64_t)tri[3 * (int64_t)t], *B = vert + 3 * (int64_t)tri[3 * (int64_t)t + 1],
                  *C = vert + 3 * (int64_t)tri[3 * (int64_t)t + 2];
-    const double *zx = cheb + (3 * c + 0) * m, *zy = cheb + (3 * c + 1) * m, *zz = cheb + (3 * c + 2) * m;
-    double acc = 0.0;
+    double acc[M * M];
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) acc[q] = 0.0;
     for (int a = 0; a < rule.q; ++a)
       for (int b = 0; b < rule.q; ++b) {
         const double s = rule.x[a], tt = rule.x[a] * rule.x[b];
         const double wgt = 2.0 * area[t] * rule.w[a] * rule.w[b] * rule.x[a];
         double x[3];
         tri_point(A, B, C, s, tt, x);
-        acc += wgt * (lagrange1(zx, m, ix, x[0]) * lagrange1(zy, m, iy, x[1]) * lagrange1(zz, m, iz, x[2]));
+        double l[3][M];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            double v = w[d][i];
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+              if (j != i) v *= x[d] - z[d][j];
+            l[d][i] = v;
+          }
+        const double wz = wgt * l[2][iz];
+#pragma unroll
+        for (int iy = 0; iy < M; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < M; ++ix) acc[iy * M + ix] += wz * (l[0][ix] * l[1][iy]);
       }
-    V64[e] = acc;
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) row[q] = acc[q];
+  }
+}
+
+template <int M>
+void launch_leaf_bases(const double *vert, const int32_t *tri, const double *area, const int32_t *pad_src,
+                       const double *cheb, int L, int64_t leaf0, int64_t npad, const BasisRule &rule, double *V64,
+                       cudaStream_t st) {
+  k_leaf_bases<M><<<grid_for(npad * M, 128), 128, 0, st>>>(vert, tri, area, pad_src, cheb, L, leaf0, npad, rule, V64);
+}
+
+void leaf_bases(int m, const double *vert, const int32_t *tri, const double *area, const int32_t *pad_src,
+                const double *cheb, int L, int64_t leaf0, int64_t npad, const BasisRule &rule, double *V64,
+                cudaStream_t st) {
+  switch (m) {
+    case 1: launch_leaf_bases<1>(vert, tri, area, pad_src, cheb, L, leaf0, npad, rule, V64, st); break;
+    case 2: launch_leaf_bases<2>(vert, tri, area, pad_src, cheb, L, leaf0, npad, rule, V64, st); break;
+    case 3: launch_leaf_bases<3>(vert, tri, area, pad_src, cheb, L, leaf0, npad, rule, V64, st); break;
+    case 4: launch_leaf_bases<4>(vert, tri, area, pad_src, cheb, L, leaf0, npad, rule, V64, st); break;
+    case 5: launch_leaf_bases<5>(vert, tri, area, pad_src, cheb, L, leaf0, npad, rule, V64, st); break;
+    default: launch_leaf_bases<6>(vert, tri, area, pad_src, cheb, L, leaf0, npad, rule, V64, st); break;
   }
 }
 
@@ -486,9 +543,8 @@ int build_typed(Ctx &c) {
     }
     if (dmalloc(&t_v64.ptr, std::max<size_t>(16, (size_t)d.npad * k * 8)) != cudaSuccess)
       return fail(H2_ENOMEM, "leaf basis staging buffer");
-    k_leaf_bases<<<grid_for(d.npad * k, 128), 128, 0, st>>>(
-        (const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src, d.cheb, m, k,
-        (int)L, p.leaf0, d.npad, rule, (double *)t_v64.ptr);
+    leaf_bases(m, (const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src,
+               d.cheb, (int)L, p.leaf0, d.npad, rule, (double *)t_v64.ptr, st);
     H2_CUDA_TRY(cudaGetLastError());
     const bool half_v = std::is_same<T, __half>::value && !d.v32;
     if (half_v) {

@@ -32,16 +32,18 @@
 // instruction (kind::f8f6f4, K = 32) multiplies two stacked digit planes of
 // S (M = 128 rows: digits i and i+1) by the digit planes of x^ it pairs with
 // (N = 16 columns per plane, 160 down to 32): five such groups, two K steps
-// each, 10 instructions per block; the epilogue reads the 55 pairs with
-// i + k <= 11 (480 accumulator columns).
+// each, 10 instructions per block.  The groups write their pairs so that the
+// pairs of one level i + k land in the same accumulator columns (the tensor
+// cores add them, exactly), so a segment's results take 160 columns and
+// three accumulator sets rotate: the MMAs of one row segment overlap the
+// epilogue of the previous one.
 //
 // Kernel roles (one CTA per SM, 6 warps): warp 0 streams the digits of each
 // block through a shared-memory ring (bulk copies completing on mbarriers;
 // the digit stream evict-first in L2, the coefficient tiles evict-last),
 // warp 1 allocates tensor memory and issues the MMAs of a row segment (at
-// most 64 blocks) into the accumulators, warps 2-5 read it back
-// (tcgen05.ld), add the pairs of each level in FP32 and the levels in
-// double-float, and write y^_t.  Every wait is bounded; on a timeout the
+// most 64 blocks) into the next free accumulator set, warps 2-5 read it back
+// (tcgen05.ld), add the levels in double-float, and write y^_t.  Every wait is bounded; on a timeout the
 // device error word is raised, every role stops, copies and MMAs in flight
 // are waited for and the tensor memory is released before the CTA exits.
 #include <cuda_fp8.h>
@@ -71,9 +73,15 @@ constexpr uint32_t kSliceB = kTcN * kTcK;              // 1024 bytes: one digit 
 // The coupling's digit layout for ND digits per value: ND = 10 for FP64
 // accuracy (|X| <= 2^49, pairs i + k <= 11), ND = 6 for FP32 accuracy (|X| <=
 // 2^29, pairs i + k <= 7: the dropped pairs stay below 2^-27 of the row's
-// scale).  Group g pairs S digits 2g+1, 2g+2 with x^ digits 1 .. ND - 2g (N =
-// 16 (ND - 2g)); its accumulators start at tensor-memory column col(g): 0,
-// 160, 288, 384, 448 (ND = 10; 480 used) or 0, 96, 160 (ND = 6; 192 used).
+// scale).  Group g pairs S digits 2g+1 (accumulator lanes 0-63) and 2g+2
+// (lanes 64-127) with x^ digits k = 1 .. ND - 2g (N = 16 (ND - 2g)) and
+// writes them from accumulator column 32 g on: x^ digit k of group g lands in
+// column block 2g + k - 1, so column block c holds, in lanes 0-63, the sum of
+// every pair of level i + k = c + 2 and, in lanes 64-127, of level c + 3.  The
+// tensor cores thus add the pairs of one level themselves (exactly: at most
+// five sums of at most 2^20 each), an accumulator set is 16 ND columns wide
+// (160 or 96) and kSets sets rotate, so that the MMAs of the next row segment
+// run while the epilogue reads the previous one.
 template <int ND>
 struct Dig {
   static constexpr int kFix = 5 * ND - 1;
@@ -83,17 +91,19 @@ struct Dig {
   static constexpr uint32_t kTileB = ND * kSliceB;
   static constexpr uint32_t kStage = kTileA + kTileB;
   static constexpr int kStages = ND == 10 ? 4 : 6;
+  static constexpr uint32_t kW = kTcN * ND;      // columns of an accumulator set
+  static constexpr int kSets = 3;
   __host__ __device__ static constexpr int nx(int g) { return ND - 2 * g; }
-  __host__ __device__ static constexpr uint32_t col(int g) { return (uint32_t)(kTcN * g * (ND + 1 - g)); }
+  __host__ __device__ static constexpr uint32_t col(int g) { return (uint32_t)(2 * kTcN * g); }
 };
-static_assert(Dig<10>::col(5) == 480 && Dig<6>::col(3) == 192, "accumulator columns");
-constexpr uint32_t kTmemCols = 512;      // one accumulator set
+static_assert(Dig<10>::kSets * Dig<10>::kW <= 512 && Dig<6>::kSets * Dig<6>::kW <= 512, "accumulator sets");
+constexpr uint32_t kTmemCols = 512;      // the accumulator sets
 constexpr int kTcThreads = 192;          // producer, MMA, four epilogue warps
 constexpr uint32_t kXch = 64 * kTcN * 8; // epilogue exchange: 64 rows x 16 double-float values
 template <int ND>
 __host__ __device__ constexpr uint32_t tc_bar_off() { return Dig<ND>::kStages * Dig<ND>::kStage + kXch; }
 template <int ND>
-__host__ __device__ constexpr uint32_t tc_smem() { return tc_bar_off<ND>() + 16 * 8 + 16; }
+__host__ __device__ constexpr uint32_t tc_smem() { return tc_bar_off<ND>() + 24 * 8 + 16; }
 
 // instruction descriptor of tcgen05.mma kind::f8f6f4: D FP32 (bits 4-5 =
 // 1), A and B E4M3 (bits 7-9 = 0, bits 10-12 = 0), both K-major (bits 15, 16
@@ -358,11 +368,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr uint32_t kStage = D::kStage, kTileA = D::kTileA, kTileB = D::kTileB;
   extern __shared__ __align__(1024) unsigned char smem[];
   dd *xch = reinterpret_cast<dd *>(smem + kTcStages * kStage);
+  constexpr int kSets = D::kSets;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + tc_bar_off<ND>());
   uint64_t *empty = full + kTcStages;
-  uint64_t *accf = empty + kTcStages;
-  uint64_t *acce = accf + 1;
-  uint64_t *done = acce + 1;
+  uint64_t *accf = empty + kTcStages;   // [kSets]: the MMAs of a segment have completed
+  uint64_t *acce = accf + kSets;        // [kSets]: the epilogue has read the set
+  uint64_t *done = acce + kSets;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -389,8 +400,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
-    mbar_init(acce, 4);
+    for (int u = 0; u < kSets; ++u) {
+      mbar_init(&accf[u], 1);
+      mbar_init(&acce[u], 4);
+    }
     mbar_init(done, 1);
     *abort = 0;
     mbar_fence_init();
@@ -448,12 +461,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         pnext = ptr[row0 + r + 1];
         const int64_t nb = pnext - b0;
         for (int64_t s0 = 0; s0 < nb && ok; s0 += kTcSegBlocks, ++q) {
-          // the accumulators are free once the epilogue has read the previous segment
-          if (q >= 1 && !mbar_wait_or_abort(acce, (uint32_t)((q - 1) & 1), abort)) {
+          // accumulator set q mod kSets is free once the epilogue has read its previous use
+          const int set = (int)(q % kSets);
+          if (q >= kSets && !mbar_wait_or_abort(&acce[set], (uint32_t)((q / kSets - 1) & 1), abort)) {
             ok = false;
             break;
           }
           tc_fence_after();
+          const uint32_t dset = tbase + (uint32_t)set * D::kW;
           const int64_t sn = nb - s0 < kTcSegBlocks ? nb - s0 : kTcSegBlocks;
           for (int64_t t = 0; t < sn; ++t, ++i) {
             const int s = (int)(i % kTcStages);
@@ -463,20 +478,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             tc_fence_after();
             // descriptors of the stage; offsets below 256 KB add to the 14-bit address field.
-            // Group g: S digits 2g+1, 2g+2 (M = 128 rows) times x^ digits 1 .. 10 - 2g;
-            // K steps (32 bytes, two core matrices) outermost, so that consecutive MMAs
-            // write different accumulators
+            // Group g: S digits 2g+1, 2g+2 (M = 128 rows) times x^ digits 1 .. ND - 2g into
+            // column blocks 2g .. ND - 1 of the set.  Group 0 covers every column, so its
+            // first MMA of a segment overwrites the set and all later ones accumulate.
+            // K steps (32 bytes, two core matrices) outermost.
             const uint32_t A0 = smem_u32(smem + (size_t)s * kStage), B0 = A0 + kTileA;
             const uint64_t dA = sdesc(A0), dB = sdesc(B0);
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
               for (int g = 0; g < kTcGroups; ++g)
-                tc_mma(tbase + D::col(g), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
-                       dB + (uint64_t)(kk * 16), tc_idesc(kTcN * D::nx(g)), (t > 0 || kk > 0) ? 1u : 0u);
+                tc_mma(dset + D::col(g), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
+                       dB + (uint64_t)(kk * 16), tc_idesc(kTcN * D::nx(g)), (t > 0 || kk > 0 || g > 0) ? 1u : 0u);
             tc_commit(&empty[s]);   // the stage is free once these MMAs have read it
           }
-          if (ok) tc_commit(accf);
+          if (ok) tc_commit(&accf[set]);
         }
       }
       // every MMA issued has completed before the tensor memory is released
@@ -504,7 +520,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int j = 0; j < kTcN; ++j) Fc[j] = Er + tc_colexp(xmax[lvl * kTcN + j]);
       bool stop = false;
       for (int64_t s0 = 0; s0 < nb; s0 += kTcSegBlocks, ++q) {
-        const bool ready = !*abort && mbar_wait_or_abort(accf, (uint32_t)(q & 1), abort);
+        const int set = (int)(q % kSets);
+        const bool ready = !*abort && mbar_wait_or_abort(&accf[set], (uint32_t)((q / kSets) & 1), abort);
         if (named_sync_or(128, ready ? 0 : 1)) {   // all epilogue warps agree to stop
           stop = true;
           break;
@@ -513,37 +530,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         dd acc[kTcN];
 #pragma unroll
         for (int j = 0; j < kTcN; ++j) acc[j] = dd{0.0f, 0.0f};
-        // lane nu (+ 64) of group g holds S digit i = 2g + 1 (+ 1) times x^ digits
-        // k = 1 .. ND - 2g (columns col(g) + 16 (k - 1) .. + 15).  The pairs of one
-        // level L = i + k share the weight 2^(2-5L): their sums (at most five
-        // integers of at most 2^20 each, segments of at most 64 blocks) add exactly in
-        // FP32, and each level enters the double-float result once (L <= ND + 1)
-#pragma unroll 1
-        for (int L = 2 + half; L <= D::kTop; ++L) {
-          const int ng = min(kTcGroups, (L - 2 - half) / 2 + 1);   // groups with a digit i <= L - 1
-          uint32_t raw[kTcGroups][16];
+        // column block c of lane nu (+ 64) holds the sum of every digit pair of level
+        // L = c + 2 (+ 1) (integers, exact in FP32); the levels share the weight
+        // 2^(2-5L) and enter the double-float result once each, in increasing order
+        // (L <= ND + 1: lanes 64-127 skip their last block)
+        const uint32_t tset = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * D::kW;
 #pragma unroll
-          for (int g = 0; g < kTcGroups; ++g)
-            if (g < ng)
-              tmem_ld16_nw(tbase + ((uint32_t)(quad * 32) << 16) + D::col(g) +
-                               (uint32_t)((L - (2 * g + 1 + half) - 1) * kTcN),
-                           raw[g]);
+        for (int c0 = 0; c0 < ND; c0 += 5) {
+          uint32_t raw[5][16];
+#pragma unroll
+          for (int u = 0; u < 5; ++u)
+            if (c0 + u < ND) tmem_ld16_nw(tset + (uint32_t)((c0 + u) * kTcN), raw[u]);
           tmem_wait();
-          float fs[kTcN];
 #pragma unroll
-          for (int j = 0; j < kTcN; ++j) fs[j] = __uint_as_float(raw[0][j]);
+          for (int u = 0; u < 5; ++u) {
+            const int L = c0 + u + 2 + half;
+            if (c0 + u < ND && L <= D::kTop) {
+              const float w = pow2f(2 - 5 * L);
 #pragma unroll
-          for (int g = 1; g < kTcGroups; ++g)
-            if (g < ng)
-#pragma unroll
-              for (int j = 0; j < kTcN; ++j) fs[j] += __uint_as_float(raw[g][j]);
-          const float w = pow2f(2 - 5 * L);
-#pragma unroll
-          for (int j = 0; j < kTcN; ++j) acc[j] = acc[j] + dd{fs[j] * w, 0.0f};
+              for (int j = 0; j < kTcN; ++j) acc[j] = acc[j] + dd{__uint_as_float(raw[u][j]) * w, 0.0f};
+            }
+          }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(acce);
+        if (lane == 0) mbar_arrive(&acce[set]);
         if (half == 1)
 #pragma unroll
           for (int j = 0; j < kTcN; ++j) xch[j * 64 + nu] = acc[j];   // consecutive lanes, consecutive words

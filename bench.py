@@ -197,11 +197,15 @@ def run_ours(args):
     elif args.prec == "f64" and st.get("tensor", 0):
         # tensor-core coupling: a stream of the stored slices; algorithmic bytes are
         # those of the FP64 coupling matrices (k^2 x 8 B per block) and coefficients
+        # stored_stream_frac: the E4M3 digit planes of S alone (10 B per entry), the part
+        # of the kernel's input that must come from DRAM on every product (the
+        # coefficient tiles are read again by every block of their column and are
+        # mostly L2 hits)
         roof = {"bound": "hbm", "achieved": alg["coupling_bytes"] / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "kernel": "k_coupling_tc (tcgen05 kind::f8f6f4, 5-bit E4M3 digits, exact FP32 sums)",
                 "stored_bytes_per_entry": 10,
-                "stored_frac": (st["adm_blocks"] * (10 * st["rank"] ** 2 + 10240) / (cpl_ms * 1e-3) / 1e9
-                                / peaks["hbm_gbs"])}
+                "stored_stream_frac": (st["adm_blocks"] * 10 * st["rank"] ** 2 / (cpl_ms * 1e-3) / 1e9
+                                       / peaks["hbm_gbs"])}
     elif args.prec == "f64":
         roof = {"bound": "alu", "achieved": alg["coupling_flops"] / (cpl_ms * 1e-3) / 1e12, "peak": DD_TFLOPS,
                 "unit": "TFLOP/s", "kernel": "k_blockrow (coupling, double-float on the FP32 pipe)",
@@ -222,7 +226,7 @@ def run_ours(args):
     # profiles/k_blockrow_coupling_icosphere_L5_m4_16rhs_f64.md), scaled by
     # admissible blocks; None where no capture of the current kernel exists
     tc = args.prec == "f64" and st.get("tensor", 0)
-    traffic_per_block = {"f64": 691.93e6 / 18876, "f64-tc": (794.683904e6 + 8.00896e6) / 18876}
+    traffic_per_block = {"f64": 691.93e6 / 18876}
     key = "f64-tc" if tc else args.prec
     roof["traffic"] = (traffic_per_block[key] * st["adm_blocks"]
                        if key in traffic_per_block and args.order == 4 and args.nrhs == 16 else None)
@@ -361,6 +365,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(8 * n * nrhs)},
         "clocks": clk.summary(),
         "build_s": build_s,
+        "build_phases_ms": h.build_times(),
         "finite": finite,
         "solve": solve,
         "small": small,
@@ -391,58 +396,83 @@ SERVE_GEOMS = {
 SERVE_SMALL = ["icosphere L4", "icosphere L5", "icosphere L6", "ellipsoid L6 (1.5,1,0.7)"]
 
 
-def run_serve(args, local, stream):
-    """Poisson stream of solve requests over resident geometries (seeded): p50/p99
-    latency and solves/s for plain FP64-accurate GMRES engines and for GMRES-IR
-    engines (FP32 inner cycles), on the same request stream."""
-    from paper_2203_05665_gb300 import H2Matrix, Server, inputs
-    names = list(SERVE_GEOMS) if args.serve_full else SERVE_SMALL
-    nreq = args.serve_requests
-    rng = np.random.default_rng(1005)
-    gaps = rng.exponential(1.0 / args.serve_rate, nreq)
-    gsel = rng.integers(0, len(names), nreq)
+def _serve_stream(srv, geoms, nreq, rate, seed):
+    """Submit a seeded Poisson stream (mean rate requests/s; geometry, 1-32 RHS and
+    rtol 1e-6 / 1e-8 drawn per request) and collect the results: latency of each
+    request from its arrival time, solves/s over the whole span, peak HBM held by
+    the engines."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, nreq)
+    gsel = rng.integers(0, len(geoms), nreq)
     nr = rng.integers(1, 33, nreq)
     rt = np.where(rng.integers(0, 2, nreq) == 0, 1e-6, 1e-8)
-    geoms = []
+    rhs = [np.asfortranarray(np.random.default_rng(seed * 10 + i).uniform(-1, 1, (geoms[gsel[i]][1], nr[i])))
+           for i in range(nreq)]
+    pending, lat, worst, peak = {}, [], 0.0, 0
+    t0 = time.perf_counter()
+    arrive = t0 + np.cumsum(gaps)
+    i = 0
+    while i < nreq or pending:
+        now = time.perf_counter()
+        while i < nreq and arrive[i] <= now:
+            t, shape = srv.submit(geoms[gsel[i]][2], rhs[i], float(rt[i]))
+            pending[t] = (shape, arrive[i])
+            i += 1
+        for t in list(pending):
+            shape, ta = pending[t]
+            res = srv.poll(t, shape)
+            if res is not None:
+                lat.append(time.perf_counter() - ta)
+                worst = max(worst, float(np.max(res[2])))
+                del pending[t]
+        peak = max(peak, srv.stats()["engine_bytes"])
+        time.sleep(0.0005)
+    span = time.perf_counter() - t0
+    steps = srv.stats()["steps"]
+    lat.sort()
+    return {"requests": nreq, "rate_per_s": rate, "solves_per_s": nreq / span,
+            "columns_per_s": float(nr.sum()) / span, "p50_s": lat[len(lat) // 2],
+            "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "wall_s": span, "engine_steps": steps,
+            "max_relres_over_rtol": worst, "peak_engine_hbm_gb": peak / 1e9}
+
+
+def run_serve(args, local, stream):
+    """Serving (continuous batching) over resident geometries: every geometry has
+    an FP64-accurate handle and an FP32 handle; plain engines run GMRES(30) with
+    FP64-accurate products, IR engines GMRES-IR (FP32 inner cycles to 1e-4,
+    FP64-accurate residuals).  Two regimes on seeded Poisson streams: the
+    arrival rate of the configuration (200 requests/s, above what one GPU
+    serves, so latency there is mostly queueing) and a sustainable rate (half
+    the lower of the two measured capacities), where p50/p99 are service
+    latencies."""
+    from paper_2203_05665_gb300 import H2Matrix, Server, inputs
+    names = SERVE_SMALL if args.serve_small else list(SERVE_GEOMS)
+    geoms, builds = [], {}
     for name in names:
         make, leaf = SERVE_GEOMS[name]
         v, f = make(inputs)
+        t = time.perf_counter()
         hi = H2Matrix(v, f, leaf_size=leaf, eta=2.0, order=3, prec="f64", device=local, stream=stream.cuda_stream)
         lo = H2Matrix(v, f, leaf_size=leaf, eta=2.0, order=3, prec="f32", device=local, stream=stream.cuda_stream)
+        builds[name] = time.perf_counter() - t
         geoms.append((name, f.shape[0], hi, lo))
-    rhs = [np.asfortranarray(np.random.default_rng(2000 + i).uniform(-1, 1, (geoms[gsel[i]][1], nr[i])))
-           for i in range(nreq)]
-    out = {"requests": nreq, "rate_per_s": args.serve_rate, "geometries": names, "m": 3,
-           "nrhs": "U{1..32}", "rtol": "1e-6 or 1e-8", "seed": 1005}
-    for mode in ("plain", "ir"):
-        srv = Server(device=local)
-        for name, n, hi, lo in geoms:
-            srv.register(hi, lo if mode == "ir" else None, slots=32, restart=30, maxit=20000, inner_rtol=1e-4)
-        pending = {}
-        lat = []
-        t0 = time.perf_counter()
-        arrive = t0 + np.cumsum(gaps)
-        i = 0
-        while i < nreq or pending:
-            now = time.perf_counter()
-            while i < nreq and arrive[i] <= now:
-                t, shape = srv.submit(geoms[gsel[i]][2], rhs[i], float(rt[i]))
-                pending[t] = (shape, arrive[i])
-                i += 1
-            for t in list(pending):
-                shape, ta = pending[t]
-                res = srv.poll(t, shape)
-                if res is not None:
-                    lat.append(time.perf_counter() - ta)
-                    del pending[t]
-            time.sleep(0.0005)
-        span = time.perf_counter() - t0
-        stats = srv.stats()
-        srv.close()
-        lat.sort()
-        out[mode] = {"solves_per_s": nreq / span, "columns_per_s": float(nr.sum()) / span,
-                     "p50_s": lat[len(lat) // 2], "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                     "wall_s": span, "engine_steps": stats["steps"]}
+    out = {"geometries": {nm: int(n) for nm, n, _, _ in geoms}, "m": 3, "nrhs": "U{1..32}",
+           "rtol": "1e-6 or 1e-8", "seeds": [1005, 1006], "slots": 32, "build_s": builds,
+           "handles_hbm_gb": sum(hi.stats["device_bytes"] + lo.stats["device_bytes"] for _, _, hi, lo in geoms) / 1e9}
+
+    def regime(nreq, rate, seed):
+        res = {}
+        for mode in ("plain", "ir"):
+            srv = Server(device=local)
+            for name, n, hi, lo in geoms:
+                srv.register(hi, lo if mode == "ir" else None, slots=32, restart=30, maxit=20000, inner_rtol=1e-4)
+            res[mode] = _serve_stream(srv, geoms, nreq, rate, seed)
+            srv.close()
+        return res
+
+    out["at_rate"] = regime(args.serve_requests, args.serve_rate, 1005)
+    cap = min(out["at_rate"]["plain"]["solves_per_s"], out["at_rate"]["ir"]["solves_per_s"])
+    out["sustained"] = regime(args.serve_sustain_requests, 0.5 * cap, 1006)
     for name, n, hi, lo in geoms:
         hi.close()
         lo.close()
@@ -544,12 +574,25 @@ def run_mixed(args, local, stream):
                                      maxit_outer=50)
         ts = time.perf_counter() - t
         out[prec] = {"matvec_ms": ms, "dof_per_s": n * 4 / (ms * 1e-3), "rel_err_vs_f64": err,
+                     "basis_prec": {1: "f32", 3: "bf16", 4: "f16"}[lo.stats["basis_prec"]],
                      "phases_ms": {k: vv[0] / prods for k, vv in ph.items()},
-                     "device_bytes": lo.stats["device_bytes"],
+                     "device_bytes": lo.stats["device_bytes"], "build_phases_ms": lo.build_times(),
                      "ir_solve_s": ts, "ir_solves_per_s": 4 / ts, "ir_inner_iters": [int(i) for i in it],
                      "ir_max_relres": float(max(rel)), "ir_status": int(st)}
         lo.close()
+    # the byte cost of the FP32 leaf bases under bfloat16: the same matrix with bfloat16 V
+    lo = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec="bf16", basis="bf16", device=local,
+                  stream=stream.cuda_stream)
+    xf = colmajor(xd.float())
+    yf = colmajor(torch.empty_like(xf))
+    lo.matvec(xf, yf)
+    torch.cuda.synchronize()
+    out["bf16_with_bf16_bases"] = {
+        "rel_err_vs_f64": float(torch.linalg.norm(yf.double() - yref) / torch.linalg.norm(yref)),
+        "device_bytes": lo.stats["device_bytes"]}
+    lo.close()
     out["hi_device_bytes"] = hi.stats["device_bytes"]
+    out["hi_build_phases_ms"] = hi.build_times()
     hi.close()
     return out
 
@@ -680,17 +723,42 @@ def _oracle_sample(level, order, nrhs):
 
 
 def cpu_baseline(args):
+    """The FP64 oracle as it stands on the host cores: full products of the bench
+    workload on all cores (median of 5), and on one core a bounded sample (median
+    of 5 full products on icosphere L5: the oracle is O(n), so its DoF/s per core
+    hardly depends on the size, and one level-7 product takes about a minute on
+    one core)."""
     import oracle
-    o, x, n = _oracle_sample(args.cpu_level, args.order, args.nrhs)
-    times = []
-    for _ in range(3):
-        t = time.perf_counter()
-        o.matvec(x)
-        times.append(time.perf_counter() - t)
-    t = statistics.median(times)
-    return {"value": n * args.nrhs / t, "unit": UNIT, "cores": oracle.oracle.threads(), "kind": "oracle",
-            "sample": f"FP64 C oracle, full product on icosphere L{args.cpu_level} ({n} triangles), same m, "
-                      f"leaf, eta and {args.nrhs} RHS; median of 3 products (S evaluated on the fly)"}
+    lvl = args.cpu_level if args.cpu_level else args.level
+    t = time.perf_counter()
+    o, x, n = _oracle_sample(lvl, args.order, args.nrhs)
+    setup_s = time.perf_counter() - t
+
+    def median_of(obj, xx, reps=5):
+        times = []
+        for _ in range(reps):
+            t1 = time.perf_counter()
+            obj.matvec(xx)
+            times.append(time.perf_counter() - t1)
+        return statistics.median(times)
+
+    cores = oracle.oracle.threads()
+    t_all = median_of(o, x)
+    del o
+    oracle.oracle.set_threads(1)
+    try:
+        o1, x1, n1 = _oracle_sample(5, args.order, args.nrhs)
+        t_one = median_of(o1, x1)
+        del o1
+    finally:
+        oracle.oracle.set_threads(cores)
+    return {"value": n * args.nrhs / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 C oracle, full product on icosphere L{lvl} ({n} triangles), m={args.order}, leaf 32, "
+                      f"eta 2, {args.nrhs} RHS, nearfield stored, S evaluated on the fly; median of 5 products "
+                      f"(set-up {setup_s:.1f} s, not timed)",
+            "one_core": {"value": n1 * args.nrhs / t_one, "unit": UNIT, "cores": 1,
+                         "sample": f"median of 5 full products on icosphere L5 ({n1} triangles), same m, leaf, "
+                                   f"eta and RHS"}}
 
 
 def run_reference(args):
@@ -698,7 +766,8 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    o, x, n = _oracle_sample(args.cpu_level, args.order, args.nrhs)
+    lvl = args.cpu_level if args.cpu_level else 6
+    o, x, n = _oracle_sample(lvl, args.order, args.nrhs)
     for _ in range(args.warmup):
         o.matvec(x)
     t = time.perf_counter()
@@ -707,12 +776,12 @@ def run_reference(args):
     el = time.perf_counter() - t
     ms = el / args.steps * 1e3
     value = n * args.nrhs / (ms * 1e-3)
-    sample = (f"FP64 C oracle on the host cores: one full product per step on icosphere L{args.cpu_level} "
+    sample = (f"FP64 C oracle on the host cores: one full product per step on icosphere L{lvl} "
               f"({n} triangles), m={args.order}, leaf 32, eta 2, {args.nrhs} RHS")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"icosphere L{args.cpu_level} ({n} triangles), m={args.order}, leaf 32, eta 2, "
+           "config": {"workload": f"icosphere L{lvl} ({n} triangles), m={args.order}, leaf 32, eta 2, "
                                   f"{args.nrhs} RHS (bounded sample of the level-{args.level} workload)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.oracle.threads(), "kind": "oracle",
                             "sample": sample},
@@ -732,7 +801,9 @@ def main():
     ap.add_argument("--level", type=int, default=7)
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--nrhs", type=int, default=16)
-    ap.add_argument("--cpu-level", type=int, default=6)
+    ap.add_argument("--cpu-level", type=int, default=0,
+                    help="icosphere level of the oracle timings (0: the bench level for cpu_baseline, "
+                         "6 for --impl reference)")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-nrhs", type=int, default=16)
@@ -741,9 +812,12 @@ def main():
     ap.add_argument("--no-small", action="store_true", help="skip the icosphere L4 latency leg")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--mixed-level", type=int, default=8)
-    ap.add_argument("--serve-full", action="store_true", help="all 8 geometries (icosphere L4-L8, ...)")
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-small", action="store_true",
+                    help="four small geometries (icosphere L4-L6, ellipsoid L6) instead of all eight")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests of the stream at --serve-rate")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-sustain-requests", type=int, default=16,
+                    help="requests of the stream at half the measured capacity")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=64)
     ap.add_argument("--batch-leaf", type=int, default=0, help="fixed leaf size instead of the autotuner")

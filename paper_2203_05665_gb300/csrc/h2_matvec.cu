@@ -854,18 +854,27 @@ __global__ void __launch_bounds__(256) k_leaf_fwd_reg(const TS *__restrict__ V, 
     }
 }
 
+// With gself (FP32 self blocks of bfloat16 handles, [leaf][c][Lp]) the
+// leaf's self block joins the contraction: y|t = V_t y^_t + G_tt x|t.
 template <class TS, class T>
 __global__ void __launch_bounds__(256) k_leaf_bwd_reg(const TS *__restrict__ Vt, const T *__restrict__ yleaf,
                                                       const float *__restrict__ vscale, int L, int Lp, int k, int rp,
+                                                      const float *__restrict__ gself, const T *__restrict__ xpad,
                                                       T *__restrict__ ypad) {
   extern __shared__ __align__(16) unsigned char lsm[];
   T *Vs = reinterpret_cast<T *>(lsm);   // [k][Lp]
   T *ys = Vs + k * Lp;                   // [k][rp]
+  T *Gs = ys + k * rp;                   // [L][Lp] (with gself)
+  T *xs = Gs + L * Lp;                   // [L][rp] (with gself)
   const int64_t t = blockIdx.x;
   const TS *vt = Vt + t * (int64_t)k * Lp;
   const T *yt = yleaf + t * (int64_t)k * rp;
   for (int i = threadIdx.x; i < k * Lp; i += blockDim.x) Vs[i] = to_compute<T>(vt[i]);
   for (int i = threadIdx.x; i < k * rp; i += blockDim.x) ys[i] = yt[i];
+  if (gself) {
+    for (int i = threadIdx.x; i < L * Lp; i += blockDim.x) Gs[i] = from_double<T>(gself[t * (int64_t)L * Lp + i]);
+    for (int i = threadIdx.x; i < L * rp; i += blockDim.x) xs[i] = xpad[t * (int64_t)L * rp + i];
+  }
   __syncthreads();
   const int r = threadIdx.x >> 3, jo = threadIdx.x & 7;
   if (r >= L) return;
@@ -876,6 +885,13 @@ __global__ void __launch_bounds__(256) k_leaf_bwd_reg(const TS *__restrict__ Vt,
     for (int u = 0; u < 2; ++u)
       if (jo + 8 * u < rp) acc_fma(acc[u], w, ys[nu * rp + jo + 8 * u]);
   }
+  if (gself)
+    for (int c = 0; c < L; ++c) {
+      const T w = Gs[c * Lp + r];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (jo + 8 * u < rp) acc_fma(acc[u], w, xs[c * rp + jo + 8 * u]);
+    }
   const float sc = vscale ? vscale[t] : 1.0f;
 #pragma unroll
   for (int u = 0; u < 2; ++u)
@@ -1018,10 +1034,13 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
     }
   }
   mk.mark(H2_PH_LEAF_NEAR);
+  // bfloat16 handles: the FP32 self blocks join the leaf backward step when it runs per leaf
+  const bool self_fused = far && leaf_reg && d.nself && std::is_same<T, float>::value;
   if (far && leaf_reg) {
-    const size_t sm = (size_t)k * (Lp + rp) * sizeof(T);
+    const size_t sm = ((size_t)k * (Lp + rp) + (self_fused ? (size_t)L * (Lp + rp) : 0)) * sizeof(T);
     k_leaf_bwd_reg<TV, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TV *)d.Vt, yhat + leaf0 * (int64_t)k * rp,
-                                                             vscale, L, Lp, k, rp, ypad);
+                                                             vscale, L, Lp, k, rp, self_fused ? d.nself : nullptr,
+                                                             xpad, ypad);
     mk.count(H2_PH_LEAF_NEAR);
   } else if (far) {
     LeafBackwardRows<TV, T> rows{(const TV *)d.Vt, yhat, vscale, k, Lp, rp, leaf0};
@@ -1039,11 +1058,13 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
     if ((rc = launch_rows<TS, T>(rows, cf_near, t_near, RL, d.nleaf, far ? 1 : 0, ypad, st))) return rc;
     mk.count(H2_PH_LEAF_NEAR);
     if constexpr (std::is_same<T, float>::value) {
+      if (!self_fused) {
       RowCfg cf_self{};
       if ((rc = row_cfg<float, T>(L, Lp, rp, L, t_near, RL, false, cf_self))) return rc;
       NearRows<float, T> self{d.nself, d.self_ptr, d.self_col, xpad, nullptr, L, Lp, rp, nullptr};
       if ((rc = launch_rows<float, T>(self, cf_self, t_near, RL, d.nleaf, 1, ypad, st))) return rc;
       mk.count(H2_PH_LEAF_NEAR);
+      }
     }
   } else {
     NearRows<TS, T> rows{(const TS *)d.near, d.near_ptr, d.near_col, xpad, nscale, L, Lp, rp, nullptr};

@@ -14,9 +14,12 @@
 //   the free slots (their b is copied in, z = 0),
 //   one GMRES cycle for G~ d = r with the hi handle (tolerance rtol |b|) or
 //   the lo handle (tolerance inner_rtol |r|), z += d.
-// Every column is an independent Krylov process, so a request's result does
-// not depend on which others share its batch beyond the summation order of
-// the product.  Admission checks the device memory budget: an engine's work
+// Every column is an independent Krylov process, and every batched operation
+// of an engine (products, residuals, norms, the GMRES cycle) runs at the
+// engine's full slot width with the free slots held at zero, so the
+// arithmetic of a column never depends on which other columns share the
+// batch or on its slot: a request's result is the same, bit for bit, alone
+// and in any mix.  Admission checks the device memory budget: an engine's work
 // space is allocated when its first request is admitted and released when
 // it falls idle and another engine needs the room.
 #include <algorithm>
@@ -118,6 +121,9 @@ int allocate(Engine &e, h2_srv &s) {
   bool ok = true;
   for (double **p : {&e.B, &e.Z, &e.R, &e.D, &e.Az}) ok = ok && dmalloc(p, tot * 8) == cudaSuccess;
   ok = ok && dmalloc(&e.tmp, 8 * (size_t)e.cap) == cudaSuccess;
+  // free slots are zero columns
+  for (double *p : {e.B, e.Z, e.R, e.D})
+    ok = ok && p && cudaMemsetAsync(p, 0, tot * 8, e.hi->stream) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     e.ready = true;
@@ -171,14 +177,16 @@ int admit(h2_srv &s, int ei) {
 int step(h2_srv &s, int ei, std::unique_lock<std::mutex> &lk) {
   Engine &e = *s.engines[ei];
   cudaStream_t st = e.hi->stream;
+  const int W = e.cap;   // the width of every batched operation (free slots are zero)
+  const size_t nb = (size_t)e.n * 8;
   int rc;
   int na = (int)e.slots.size();
   if (na > 0) {
     // residual of every active column with the FP64-accurate product
-    if ((rc = run_matvec(*e.hi, e.Z, e.Az, na, true))) return rc;
-    k_launch_residual(e.B, e.Az, e.n * na, e.R, st);
-    std::vector<double> rn(na);
-    if ((rc = column_norms(*e.hi, e.R, e.n, na, e.tmp, rn.data()))) return rc;
+    if ((rc = run_matvec(*e.hi, e.Z, e.Az, W, true))) return rc;
+    k_launch_residual(e.B, e.Az, e.n * W, e.R, st);
+    std::vector<double> rn(W);
+    if ((rc = column_norms(*e.hi, e.R, e.n, W, e.tmp, rn.data()))) return rc;
     // retire finished columns, compact the others to the front
     std::vector<Slot> keep;
     int dst = 0;
@@ -203,13 +211,19 @@ int step(h2_srv &s, int ei, std::unique_lock<std::mutex> &lk) {
         continue;
       }
       if (dst != i) {
-        const size_t nb = (size_t)e.n * 8;
         H2_CUDA_TRY(cudaMemcpyAsync(e.B + dst * e.n, e.B + i * e.n, nb, cudaMemcpyDeviceToDevice, st));
         H2_CUDA_TRY(cudaMemcpyAsync(e.Z + dst * e.n, e.Z + i * e.n, nb, cudaMemcpyDeviceToDevice, st));
         H2_CUDA_TRY(cudaMemcpyAsync(e.R + dst * e.n, e.R + i * e.n, nb, cudaMemcpyDeviceToDevice, st));
       }
       keep.push_back(sl);
       ++dst;
+    }
+    // the slots freed at the end are cleared (zero columns take no part)
+    if (dst < na) {
+      const size_t tail = (size_t)(na - dst) * nb;
+      H2_CUDA_TRY(cudaMemsetAsync(e.B + dst * e.n, 0, tail, st));
+      H2_CUDA_TRY(cudaMemsetAsync(e.Z + dst * e.n, 0, tail, st));
+      H2_CUDA_TRY(cudaMemsetAsync(e.R + dst * e.n, 0, tail, st));
     }
     lk.lock();
     e.slots.swap(keep);
@@ -222,12 +236,12 @@ int step(h2_srv &s, int ei, std::unique_lock<std::mutex> &lk) {
   lk.unlock();
   if (rc) return rc;
   na = (int)e.slots.size();
-  if (na > before) {   // new columns: r = b, and |b|
+  if (na > before) {   // new columns: r = b, and |b| (norms at the full width)
     for (int i = before; i < na; ++i)
       H2_CUDA_TRY(cudaMemcpyAsync(e.R + i * e.n, e.B + i * e.n, e.n * 8, cudaMemcpyDeviceToDevice, st));
-    std::vector<double> bn(na - before);
-    if ((rc = column_norms(*e.hi, e.B + before * e.n, e.n, na - before, e.tmp, bn.data()))) return rc;
-    for (int i = before; i < na; ++i) e.slots[i].bnorm = bn[i - before] > 0 ? bn[i - before] : -1.0;
+    std::vector<double> bn(W);
+    if ((rc = column_norms(*e.hi, e.B, e.n, W, e.tmp, bn.data()))) return rc;
+    for (int i = before; i < na; ++i) e.slots[i].bnorm = bn[i] > 0 ? bn[i] : -1.0;
   }
   if (na == 0) {
     if (e.ready && e.slots.empty()) {
@@ -241,20 +255,21 @@ int step(h2_srv &s, int ei, std::unique_lock<std::mutex> &lk) {
   }
   // one GMRES cycle for G~ d = r, with the low-precision handle if there is one
   Ctx &cyc = e.lo ? *static_cast<Ctx *>(e.lo) : *static_cast<Ctx *>(e.hi);
-  std::vector<double> rn(na), tol(na);
-  std::vector<int> act(na, 1), left(na), it(na);
-  if ((rc = column_norms(*e.hi, e.R, e.n, na, e.tmp, rn.data()))) return rc;
+  std::vector<double> rn(W), tol(W, 0.0);
+  std::vector<int> act(W, 0), left(W, 0), it(W, 0);
+  if ((rc = column_norms(*e.hi, e.R, e.n, W, e.tmp, rn.data()))) return rc;
   for (int i = 0; i < na; ++i) {
     Slot &sl = e.slots[i];
+    act[i] = 1;
     tol[i] = e.lo ? e.inner_rtol * rn[i] : sl.req->rtol * std::max(sl.bnorm, 0.0);
     left[i] = e.maxit - sl.iters;
   }
   if (e.lo) H2_CUDA_TRY(cudaStreamSynchronize(st));
-  if ((rc = gmres_cycle(cyc, e.w, e.R, e.D, na, e.restart, tol.data(), act.data(), left.data(), it.data())))
+  if ((rc = gmres_cycle(cyc, e.w, e.R, e.D, W, e.restart, tol.data(), act.data(), left.data(), it.data())))
     return rc;
   if (e.lo) H2_CUDA_TRY(cudaStreamSynchronize(cyc.stream));
   for (int i = 0; i < na; ++i) e.slots[i].iters += it[i];
-  k_launch_axpy(e.D, e.n * na, e.Z, st);
+  k_launch_axpy(e.D, e.n * W, e.Z, st);
   lk.lock();
   s.steps++;
   lk.unlock();

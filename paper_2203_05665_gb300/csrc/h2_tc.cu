@@ -332,13 +332,14 @@ __device__ __forceinline__ void slice_cluster(const T *__restrict__ xc, int rp, 
     reinterpret_cast<uint4 *>(dst)[w] = reinterpret_cast<const uint4 *>(tile)[w];
 }
 
-// the slices of clusters [c0, c0 + ncl) of level lvl, one cluster per CTA
+// the slices of clusters c0, c0 + 1, ... (one cluster per CTA), each with the
+// column maxima of its own tree level
 template <class T, int ND>
-__global__ void __launch_bounds__(256) k_tc_slice_x(const T *__restrict__ xhat, int64_t c0, int lvl, int rp,
+__global__ void __launch_bounds__(256) k_tc_slice_x(const T *__restrict__ xhat, int64_t c0, int rp,
                                                     const unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
   __shared__ __align__(16) unsigned char tile[Dig<ND>::kTileB];
   const int64_t c = c0 + blockIdx.x;
-  slice_cluster<T, ND>(xhat + c * kTcK * rp, rp, lvl, xmax, tile, xtc + c * (int64_t)Dig<ND>::kTileB);
+  slice_cluster<T, ND>(xhat + c * kTcK * rp, rp, tc_level(c), xmax, tile, xtc + c * (int64_t)Dig<ND>::kTileB);
 }
 
 __device__ __forceinline__ dd dd_scale(dd v, int e) {
@@ -985,10 +986,10 @@ int tc_build_nd(Ctx &c, const int32_t *arow_dev) {
 }
 
 // Upward pass of a product on the tensor-core path: the transfers of
-// Algorithm 1 with the column maxima and the coefficient digits of every
-// level produced on the way (k_up_reg), each level's digits cut by
-// k_tc_slice_x once its maxima are complete (the leaves' maxima come from
-// k_tc_levmax).  Returns the launches made.
+// Algorithm 1, each level's column maxima taken on the way (k_up_reg; the
+// leaves' by k_tc_levmax), then the coefficient digits of every far-field
+// level in one launch (k_tc_slice_x, each cluster with its level's maxima).
+// Returns the launches made.
 template <class T, int ND>
 int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
   Dev &d = c.d;
@@ -1002,18 +1003,15 @@ int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
   k_tc_levmax<T><<<levmax_grid(lrows), 256, 0, st>>>(xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
   ++nl;
   for (int l = D - 1; l >= lmin; --l) {
-    // the digits of level l + 1 (its column maxima are complete), then level l and its maxima
+    // level l from level l + 1, with the column maxima of level l
     const int64_t np = (int64_t)1 << l;
-    k_tc_slice_x<T, ND><<<(unsigned)(2 * np), 256, 0, st>>>(xhat, 2 * np - 1, l + 1, rp, d.tc_xmax,
-                                                            (unsigned char *)d.xtc);
     k_up_reg<T, T, 4><<<(unsigned)((np + kRegParents - 1) / kRegParents), 256, 0, st>>>(
         (const T *)d.Ef, rp, np - 1, np, xhat, d.tc_xmax + l * kTcN);
-    nl += 2;
+    ++nl;
   }
-  // the top level's digits (the leaves' when there is no transfer)
-  const int64_t c0 = ((int64_t)1 << lmin) - 1;
-  k_tc_slice_x<T, ND><<<(unsigned)((int64_t)1 << lmin), 256, 0, st>>>(xhat, c0, lmin, rp, d.tc_xmax,
-                                                                      (unsigned char *)d.xtc);
+  // the digits of every level at once (all maxima are complete)
+  const int64_t c0 = ((int64_t)1 << lmin) - 1, ncl = d.nclu - c0;
+  k_tc_slice_x<T, ND><<<(unsigned)ncl, 256, 0, st>>>(xhat, c0, rp, d.tc_xmax, (unsigned char *)d.xtc);
   ++nl;
   H2_CUDA_TRY(cudaGetLastError());
   if (launches) *launches = nl;

@@ -11,6 +11,9 @@
  * Sources (Boerm, "Distributed H^2-matrices for boundary element methods"):
  *   Galerkin matrix g_ij and right-hand side b_i ........ Section 1, Eq. (3)
  *   Laplace kernel g(x,y) = 1/(4 pi |x-y|) .............. Section 1
+ *   Helmholtz kernel e^{i kappa |x-y|}/(4 pi |x-y|) ..... Section 1: its
+ *     real part cos(kappa r)/(4 pi r) and imaginary part sin(kappa r)/(4 pi r)
+ *     are two real kernels (kinds 2 and 3) approximated the same way
  *   tensor interpolation of g on box pairs .............. Section 2, Eq. (4)
  *   cluster index sets, minimal boxes ................... Section 2, Eq. (5)
  *   leaf bases V (= W here), coupling S ................. Section 2, Eq. (6a-c)
@@ -102,12 +105,18 @@ void or_gauss01(int n, double *x, double *w) {
 /* ------------------------------------------------------------------ */
 /* Kernels.  kind 0: Laplace 1/(4 pi |x-y|) (Section 1).  kind 1: a
  * smooth symmetric test polynomial of per-axis degree <= m-1 in x and in
- * y, which tensor interpolation of order m reproduces exactly.          */
+ * y, which tensor interpolation of order m reproduces exactly.  kinds 2
+ * and 3: the real and imaginary parts of the Helmholtz kernel of Section 1,
+ * cos(kappa r) / (4 pi r) and sin(kappa r) / (4 pi r), r = |x - y| (the
+ * second is smooth: kappa / (4 pi) at r = 0).                           */
 /* ------------------------------------------------------------------ */
-static double kernel_eval(int kind, int m, const double *x, const double *y) {
-  if (kind == 0) {
+static double kernel_eval(int kind, int m, double kappa, const double *x, const double *y) {
+  if (kind == 0 || kind == 2 || kind == 3) {
     double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
-    return 1.0 / (4.0 * OR_PI * sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+    double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    if (kind == 0) return 1.0 / (4.0 * OR_PI * r);
+    if (kind == 2) return cos(kappa * r) * (1.0 / (4.0 * OR_PI * r));
+    return r > 0.0 ? sin(kappa * r) * (1.0 / (4.0 * OR_PI * r)) : kappa / (4.0 * OR_PI);
   }
   double prod = 1.0;
   for (int d = 0; d < 3; ++d) {
@@ -135,6 +144,7 @@ typedef struct {
   double *cen;    /* nt x 3 centroids (R1) */
   double *area;   /* nt */
   int leaf, m, k, q, kind, depth;
+  double kappa;   /* wave number of kinds 2 and 3 */
   double eta;
   int64_t nclu;
   int64_t *idx;   /* cluster order -> triangle index */
@@ -363,7 +373,7 @@ static double quad_regular(const orh2 *h, const double *A1, const double *B1, co
         for (int d = 0; d < q; ++d) {
           double y[3];
           ref_map(A2, B2, C2, gx[c], gx[c] * gx[d], y);
-          acc += wx * gw[c] * gw[d] * gx[c] * kernel_eval(h->kind, h->m, x, y);
+          acc += wx * gw[c] * gw[d] * gx[c] * kernel_eval(h->kind, h->m, h->kappa, x, y);
         }
     }
   return acc;
@@ -376,7 +386,7 @@ static double sing_term(const orh2 *h, const double *A1, const double *B1, const
   double x[3], y[3];
   ref_map(A1, B1, C1, x1, x2, x);
   ref_map(A2, B2, C2, y1, y2, y);
-  return W * kernel_eval(h->kind, h->m, x, y);
+  return W * kernel_eval(h->kind, h->m, h->kappa, x, y);
 }
 
 /* identical panels: six regions, weight xi^3 e1^2 e2 */
@@ -452,7 +462,7 @@ static double galerkin_entry_q(const orh2 *h, int64_t i, int64_t j, int q) {
   const int32_t *ti = h->tri + 3 * i, *tj = h->tri + 3 * j;
   const double *V = h->vert;
   double jac = 4.0 * h->area[i] * h->area[j];
-  if (h->kind != 0) {
+  if (h->kind == 1) {
     /* smooth test kernel: the exact collapsed rule for every pair */
     int qv = (3 * (h->m - 1) + 2 + 1) / 2 + 1;
     return jac * quad_regular(h, V + 3 * (int64_t)ti[0], V + 3 * (int64_t)ti[1], V + 3 * (int64_t)ti[2],
@@ -526,14 +536,16 @@ void or_set_threads(int n) {
 }
 
 /* Build the H^2 approximation.  kind: 0 Laplace, 1 smooth polynomial test
- * kernel.  store_near: assemble and keep the nearfield blocks.
+ * kernel, 2 / 3 real / imaginary part of the Helmholtz kernel with wave
+ * number kappa.  store_near: assemble and keep the nearfield blocks.
  * with_bases: compute V and E (needed by the matvec).  Returns NULL on
  * invalid arguments. */
 orh2 *or_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf, double eta,
-               int m, int q, int kind, int store_near, int with_bases) {
+               int m, int q, int kind, double kappa, int store_near, int with_bases) {
   if (nt < 1 || nv < 3 || leaf < 2 || m < 1 || m > 8 || q < 1 || q > 30 || !(eta > 0.0)) return NULL;
   orh2 *h = (orh2 *)calloc(1, sizeof(orh2));
   h->nt = nt; h->nv = nv; h->leaf = leaf; h->eta = eta; h->m = m; h->k = m * m * m; h->q = q; h->kind = kind;
+  h->kappa = kappa;
   h->vert = (double *)malloc(nv * 3 * sizeof(double));
   memcpy(h->vert, vert, nv * 3 * sizeof(double));
   h->tri = (int32_t *)malloc(nt * 3 * sizeof(int32_t));
@@ -645,7 +657,7 @@ void or_S(const orh2 *h, int64_t t, int64_t s, double *S) {
     for (int mu = 0; mu < h->k; ++mu) {
       double y[3];
       cheb_point3(h, s, mu, y);
-      S[nu * h->k + mu] = kernel_eval(h->kind, h->m, x, y);
+      S[nu * h->k + mu] = kernel_eval(h->kind, h->m, h->kappa, x, y);
     }
   }
 }
@@ -659,10 +671,11 @@ double or_entry(const orh2 *h, int64_t i, int64_t j, int q) { return galerkin_en
 
 /* the reference-map quadratures for two explicit triangles (pins):
  * mode 0 regular, 1 identical (uses triangle 1), 2 edge, 3 vertex. */
-double or_pair_quad(const double *T1, const double *T2, int mode, int q, int kind, int m) {
+double or_pair_quad(const double *T1, const double *T2, int mode, int q, int kind, int m, double kappa) {
   orh2 tmp;
   memset(&tmp, 0, sizeof(tmp));
   tmp.kind = kind;
+  tmp.kappa = kappa;
   tmp.m = m;
   switch (mode) {
     case 0: return quad_regular(&tmp, T1, T1 + 3, T1 + 6, T2, T2 + 3, T2 + 6, q);

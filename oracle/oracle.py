@@ -16,6 +16,8 @@ _lib = None
 
 KIND_LAPLACE = 0
 KIND_POLY = 1
+KIND_HELM_COS = 2   # real part of the Helmholtz kernel (Section 1): cos(kappa r) / (4 pi r)
+KIND_HELM_SIN = 3   # imaginary part: sin(kappa r) / (4 pi r)
 
 
 def build_library(force: bool = False) -> str:
@@ -42,7 +44,7 @@ def _load():
     u8p = C.POINTER(C.c_uint8)
     lib.or_build.restype = C.c_void_p
     lib.or_build.argtypes = [dp, C.c_int64, ip32, C.c_int64, C.c_int, C.c_double, C.c_int, C.c_int,
-                             C.c_int, C.c_int, C.c_int]
+                             C.c_int, C.c_double, C.c_int, C.c_int]
     lib.or_free.argtypes = [C.c_void_p]
     lib.or_info.argtypes = [C.c_void_p, ip64]
     lib.or_tree.argtypes = [C.c_void_p, ip64, ip64, ip64, dp, dp, dp]
@@ -54,7 +56,7 @@ def _load():
     lib.or_entry.restype = C.c_double
     lib.or_entry.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int]
     lib.or_pair_quad.restype = C.c_double
-    lib.or_pair_quad.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.or_pair_quad.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
     lib.or_dense.argtypes = [C.c_void_p, dp]
     lib.or_matvec.restype = C.c_int
     lib.or_matvec.argtypes = [C.c_void_p, dp, dp, C.c_int, dp, dp]
@@ -83,7 +85,7 @@ def gauss01(n: int):
     return x, w
 
 
-def pair_quad(T1, T2, mode: int, q: int, kind: int = KIND_LAPLACE, m: int = 1) -> float:
+def pair_quad(T1, T2, mode: int, q: int, kind: int = KIND_LAPLACE, m: int = 1, kappa: float = 0.0) -> float:
     """Reference-domain integral of the kernel over T1 x T2 (no 4|T1||T2| factor).
 
     mode 0 regular, 1 identical (T1 only), 2 common edge T1[0]T1[1] = T2[0]T2[1],
@@ -91,7 +93,7 @@ def pair_quad(T1, T2, mode: int, q: int, kind: int = KIND_LAPLACE, m: int = 1) -
     lib = _load()
     a = np.ascontiguousarray(T1, dtype=np.float64).reshape(9)
     b = np.ascontiguousarray(T2, dtype=np.float64).reshape(9)
-    return lib.or_pair_quad(_p(a, C.c_double), _p(b, C.c_double), mode, q, kind, m)
+    return lib.or_pair_quad(_p(a, C.c_double), _p(b, C.c_double), mode, q, kind, m, float(kappa))
 
 
 def threads() -> int:
@@ -106,7 +108,7 @@ class Oracle:
     """The oracle's H² approximation of one mesh (Section 2 of the paper)."""
 
     def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, quad_order=3,
-                 kind=KIND_LAPLACE, store_near=True, with_bases=True):
+                 kind=KIND_LAPLACE, store_near=True, with_bases=True, kappa=0.0):
         lib = _load()
         self._lib = lib
         self.vert = np.ascontiguousarray(vert, dtype=np.float64)
@@ -115,7 +117,8 @@ class Oracle:
         self.m = int(order)
         self.k = self.m ** 3
         h = lib.or_build(_p(self.vert, C.c_double), self.vert.shape[0], _p(self.tri, C.c_int32), self.n,
-                         int(leaf_size), float(eta), self.m, int(quad_order), int(kind), int(store_near),
+                         int(leaf_size), float(eta), self.m, int(quad_order), int(kind), float(kappa),
+                         int(store_near),
                          int(with_bases))
         if not h:
             raise ValueError("oracle: invalid arguments")
@@ -215,3 +218,36 @@ class Oracle:
         self._lib.or_gmres(self._h, _p(b, C.c_double), _p(z, C.c_double), nrhs, float(rtol), int(restart),
                            int(maxit), iters.ctypes.data_as(C.POINTER(C.c_int)), _p(rel, C.c_double))
         return z, iters, rel
+
+
+class HelmholtzOracle:
+    """The Helmholtz single-layer matrix of Section 1, G = G_c + i G_s, as two
+    oracle H^2 matrices of the same mesh and trees with the real kernels
+    cos(kappa r) / (4 pi r) and sin(kappa r) / (4 pi r); complex vectors are
+    numpy complex128 arrays (n, nrhs)."""
+
+    def __init__(self, vert, tri, kappa, leaf_size=32, eta=2.0, order=3, quad_order=3, store_near=True,
+                 with_bases=True):
+        kw = dict(leaf_size=leaf_size, eta=eta, order=order, quad_order=quad_order, store_near=store_near,
+                  with_bases=with_bases, kappa=kappa)
+        self.c = Oracle(vert, tri, kind=KIND_HELM_COS, **kw)
+        self.s = Oracle(vert, tri, kind=KIND_HELM_SIN, **kw)
+        self.n = self.c.n
+        self.kappa = float(kappa)
+
+    def matvec(self, x):
+        x = np.asarray(x, dtype=np.complex128).reshape(self.n, -1)
+        xr, xi = np.ascontiguousarray(x.real), np.ascontiguousarray(x.imag)
+        return (self.c.matvec(xr) - self.s.matvec(xi)) + 1j * (self.c.matvec(xi) + self.s.matvec(xr))
+
+    def matvec_rows(self, x, rows):
+        x = np.asarray(x, dtype=np.complex128).reshape(self.n, -1)
+        xr, xi = np.ascontiguousarray(x.real), np.ascontiguousarray(x.imag)
+        c, s = self.c.matvec_rows, self.s.matvec_rows
+        return (c(xr, rows) - s(xi, rows)) + 1j * (c(xi, rows) + s(xr, rows))
+
+    def dense(self):
+        return self.c.dense() + 1j * self.s.dense()
+
+    def entry(self, i, j, q=None):
+        return self.c.entry(i, j, q) + 1j * self.s.entry(i, j, q)

@@ -417,6 +417,53 @@ int h2_batch_sync(h2_batch b);
 int h2_batch_destroy(h2_batch b);
 
 /* ---------------------------------------------------------------------------
+ * The Helmholtz single-layer matrix (Section 1: g(x, y) = e^{i kappa |x-y|} /
+ * (4 pi |x-y|), wave number kappa >= 0), approximated as in Section 2.  Its
+ * real and imaginary parts, cos(kappa r) / (4 pi r) and sin(kappa r) /
+ * (4 pi r), are two real kernels; a complex handle holds one real H^2 matrix
+ * of each (the same trees, interpolation bases and quadrature; coupling
+ * matrices and nearfield per part), G = G_c + i G_s, and multiplies complex
+ * vectors as y_re = G_c x_re - G_s x_im, y_im = G_c x_im + G_s x_re, both
+ * real products taking the real and imaginary columns together (2 nrhs
+ * columns).  The interpolation needs kappa diam of the clusters to stay
+ * moderate (low-frequency regime): accuracy falls as kappa grows.
+ *
+ * Complex vectors are column-major n x nrhs arrays of interleaved (real,
+ * imaginary) double pairs (C99 double complex, std::complex<double>).
+ * Precisions: H2_F64 (with the tensor-core coupling and nearfield where
+ * eligible: order 4, at most 8 complex right-hand sides), H2_F32,
+ * H2_F64_NATIVE; the coupling is always stored.
+ * ------------------------------------------------------------------------- */
+typedef struct h2_zctx *h2_zhandle;
+/* Build; arguments as for h2_build plus kappa >= 0 (finite).  opt->coupling
+ * must be AUTO or STORED and opt->prec one of the three above (H2_EINVAL
+ * otherwise). */
+int h2_zbuild(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
+              double kappa, const h2_options *opt, h2_zhandle *out);
+int h2_zdestroy(h2_zhandle h);
+/* The real H^2 matrix of part `which` (0: real part G_c, 1: imaginary part
+ * G_s), owned by h (do not destroy it): for h2_info, h2_export and products
+ * of one part alone. */
+int h2_zpart(h2_zhandle h, int which, h2_handle *out);
+/* Statistics of the real part's matrix (the imaginary part has the same
+ * structure); device_bytes counts both parts. */
+int h2_zinfo(h2_zhandle h, h2_stats *out);
+/* y = G~ x for nrhs complex right-hand sides, 1 <= nrhs <= 32; x, y DEVICE
+ * pointers (interleaved complex doubles), asynchronous on the handle's
+ * stream.  Errors as for h2_matvec. */
+int h2_zmatvec(h2_zhandle h, const double *x, double *y, int nrhs);
+/* The same with HOST arrays (copies included, synchronises). */
+int h2_zmatvec_host(h2_zhandle h, const double *x, double *y, int nrhs);
+/* Solve G~ z = b by restarted GMRES(restart), z0 = 0, per complex column, on
+ * the equivalent real system [G_c -G_s; G_s G_c] [z_re; z_im] = [b_re;
+ * b_im] (its residual norm is the complex residual's), in FP64 around the
+ * handle's products.  b, z both host or both device (interleaved complex);
+ * rtol, restart, maxit and info as for h2_solve (relres is the complex
+ * relative residual |b - G~ z| / |b|). */
+int h2_zsolve(h2_zhandle h, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
+              h2_solve_info *info);
+
+/* ---------------------------------------------------------------------------
  * Failure injection and self-tests of the error paths (no counterpart in the
  * paper; they make failures happen on the host or inside a bounded wait,
  * never as a GPU fault).

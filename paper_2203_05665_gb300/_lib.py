@@ -52,7 +52,8 @@ EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_
             "h2_serve_stats", "h2_serve_destroy", "h2_batch_create", "h2_batch_offsets", "h2_batch_matvec",
             "h2_batch_tune", "h2_batch_set_shapes", "h2_batch_profile", "h2_batch_phase_times", "h2_batch_info",
             "h2_batch_sync", "h2_batch_destroy", "h2_graph_create", "h2_graph_launch", "h2_graph_destroy",
-            "h2_inject_alloc_failure", "h2_wait_selftest", "h2_export", "h2_build_times", "h2_last_error"]
+            "h2_inject_alloc_failure", "h2_wait_selftest", "h2_export", "h2_build_times",
+            "h2_zbuild", "h2_zdestroy", "h2_zpart", "h2_zinfo", "h2_zmatvec", "h2_zmatvec_host", "h2_zsolve", "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -116,6 +117,14 @@ def load():
             "h2_inject_alloc_failure": (C.c_int, [C.c_int64]),
             "h2_export": (C.c_int, [vp, C.c_int, C.c_int64, C.c_int64, dp]),
             "h2_build_times": (C.c_int, [vp, dp]),
+            "h2_zbuild": (C.c_int, [dp, C.c_int64, i32p, C.c_int64, C.c_int, C.c_double, C.c_int, C.c_double,
+                                    C.POINTER(Options), C.POINTER(vp)]),
+            "h2_zdestroy": (C.c_int, [vp]),
+            "h2_zpart": (C.c_int, [vp, C.c_int, C.POINTER(vp)]),
+            "h2_zinfo": (C.c_int, [vp, C.POINTER(Stats)]),
+            "h2_zmatvec": (C.c_int, [vp, vp, vp, C.c_int]),
+            "h2_zmatvec_host": (C.c_int, [vp, dp, dp, C.c_int]),
+            "h2_zsolve": (C.c_int, [vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(SolveInfo)]),
             "h2_wait_selftest": (C.c_int, [vp, C.c_int, C.c_uint32, C.POINTER(C.c_int)]),
             "h2_last_error": (C.c_char_p, []),
         }
@@ -370,6 +379,89 @@ class H2Matrix:
         st = self._lib.h2_solve_ir(self._h, lo._h, bb.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p),
                                    nrhs, float(rtol), float(inner_rtol), int(restart), int(maxit_inner),
                                    int(maxit_outer), info)
+        if st not in (H2_OK, H2_ENOCONV):
+            _check(st)
+        return z, np.array([i.iters for i in info]), np.array([i.relres for i in info]), st
+
+
+class HelmholtzMatrix:
+    """The Helmholtz single-layer matrix G = G_c + i G_s of one mesh on one GPU
+    (h2_zbuild); complex vectors are complex128 (numpy on the host, torch on
+    the device), column-major (n, nrhs)."""
+
+    def __init__(self, vert, tri, kappa, leaf_size=32, eta=2.0, order=3, prec="f64", quad_order=3, device=0,
+                 stream=None, tensor="auto"):
+        lib = load()
+        v, t = _mesh(vert, tri)
+        opt = Options()
+        _check(lib.h2_options_default(C.byref(opt)))
+        opt.prec = PREC[prec]
+        opt.quad_order = int(quad_order)
+        opt.device = int(device)
+        opt.stream = stream
+        opt.coupling = COUPLING["stored"]
+        opt.tensor = {"auto": 0, "off": 1}[tensor]
+        h = C.c_void_p()
+        _check(lib.h2_zbuild(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
+                             int(leaf_size), float(eta), int(order), float(kappa), C.byref(opt), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.n = int(t.shape[0])
+        self.kappa = float(kappa)
+        st = Stats()
+        _check(lib.h2_zinfo(h, C.byref(st)))
+        self.stats = {f: int(getattr(st, f)) for f, _ in Stats._fields_}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.h2_zdestroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self, which, what, first=0, count=None):
+        """h2_export of part `which` (0 real, 1 imaginary); see H2Matrix.export."""
+        p = C.c_void_p()
+        _check(self._lib.h2_zpart(self._h, int(which), C.byref(p)))
+        st = self.stats
+        L, k, m = st["leaf_max"], st["rank"], st["order"]
+        item, total, shape = {"near": (0, st["near_blocks"], (L, L)), "coupling": (1, st["adm_blocks"], (k, k)),
+                              "V": (2, (2 ** st["depth"]) * L, (k,)), "E": (3, st["clusters"], (3, m, m))}[what]
+        count = total - first if count is None else count
+        out = np.zeros((count,) + shape)
+        _check(self._lib.h2_export(p, item, int(first), int(count), _dp(out)))
+        return out
+
+    def matvec(self, x, y):
+        """y = G~ x on the device; x, y complex128 CUDA tensors (n, nrhs), column-major."""
+        if x.shape != y.shape or x.shape[0] != self.n:
+            raise ValueError("x and y must both be (n, nrhs)")
+        if x.stride(0) != 1 or y.stride(0) != 1:
+            raise ValueError("x and y must be column-major (use colmajor())")
+        _check(self._lib.h2_zmatvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.shape[1])))
+        return y
+
+    def matvec_host(self, x):
+        x = np.asfortranarray(np.asarray(x, dtype=np.complex128).reshape(self.n, -1))
+        y = np.zeros_like(x, order="F")
+        _check(self._lib.h2_zmatvec_host(self._h, x.ctypes.data_as(C.POINTER(C.c_double)),
+                                         y.ctypes.data_as(C.POINTER(C.c_double)), int(x.shape[1])))
+        return y
+
+    def solve(self, b, rtol=1e-8, restart=30, maxit=2000):
+        """GMRES(restart) on the real form; b numpy complex (host)."""
+        bb = np.asfortranarray(np.asarray(b, dtype=np.complex128).reshape(self.n, -1))
+        nrhs = bb.shape[1]
+        z = np.zeros_like(bb, order="F")
+        info = (SolveInfo * nrhs)()
+        st = self._lib.h2_zsolve(self._h, bb.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p), nrhs,
+                                 float(rtol), int(restart), int(maxit), info)
         if st not in (H2_OK, H2_ENOCONV):
             _check(st)
         return z, np.array([i.iters for i in info]), np.array([i.relres for i in info]), st

@@ -76,6 +76,69 @@ static int check_double_float_range(const Plan &p) {
   return H2_OK;
 }
 
+// h2_build with a given kernel (Section 1: Laplace, or a part of Helmholtz)
+int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
+                 const h2_options *opt, KernelFn kf, h2_handle *out) {
+  if (!out) return fail(H2_EINVAL, "out is NULL");
+  *out = nullptr;
+  h2_options o;
+  h2_options_default(&o);
+  if (opt) o = *opt;
+  if (o.prec < H2_F64 || o.prec > H2_F16) return fail(H2_EINVAL, "unknown precision");
+  if (o.coupling < H2_COUPLING_AUTO || o.coupling > H2_COUPLING_REGEN) return fail(H2_EINVAL, "unknown coupling mode");
+  const bool half_prec = o.prec == H2_BF16 || o.prec == H2_F16, f64 = o.prec == H2_F64 || o.prec == H2_F64_NATIVE;
+  if (o.coupling == H2_COUPLING_REGEN && f64)
+    return fail(H2_EINVAL, "the regenerated coupling is FP32; use H2_F32, H2_BF16 or H2_F16");
+  if (o.coupling == H2_COUPLING_STORED && half_prec)
+    return fail(H2_EINVAL, "16-bit precisions regenerate the coupling");
+  if (o.tensor < 0 || o.tensor > 1) return fail(H2_EINVAL, "tensor must be 0 (tensor cores where supported) or 1 (never)");
+  for (int r : o.reserved)
+    if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
+  if (o.basis_prec != 0) {
+    if (!half_prec) return fail(H2_EINVAL, "basis_prec applies to H2_BF16 and H2_F16 handles only; use 0");
+    if (o.basis_prec != H2_F32 && o.basis_prec != o.prec)
+      return fail(H2_EINVAL, "basis_prec must be 0, H2_F32 or the handle's own 16-bit precision");
+  }
+  int ndev = 0;
+  H2_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (o.device < 0 || o.device >= ndev) return fail(H2_EINVAL, "device ordinal out of range");
+  H2_CUDA_TRY(cudaSetDevice(o.device));
+  h2_ctx *c = new (std::nothrow) h2_ctx();
+  if (!c) return fail(H2_ENOMEM, "handle");
+  c->device = o.device;
+  c->stream = (cudaStream_t)o.stream;
+  c->quad_order = o.quad_order;
+  c->d.prec = o.prec;
+  c->d.tensor = o.tensor;
+  c->d.kernel = kf;
+  // FP32 leaf bases: explicitly, or by default under bfloat16 storage
+  c->d.v32 = half_prec && (o.basis_prec == H2_F32 || (o.basis_prec == 0 && o.prec == H2_BF16));
+  c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);
+  int rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms = [](std::chrono::steady_clock::time_point a) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+  };
+  try {
+    // the trees, blocks and interpolation points on the host; V and E are
+    // computed on the device by device_build
+    rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, false, c->plan);
+    c->build_ms[H2_BUILD_PLAN] = ms(t0);
+    if (!rc && o.prec == H2_F64) rc = check_double_float_range(c->plan);
+    if (!rc) rc = device_build(*c);
+  } catch (const std::bad_alloc &) {
+    rc = fail(H2_ENOMEM, "host allocation in set-up");
+  }
+  c->build_ms[H2_BUILD_TOTAL] = ms(t0);
+  if (rc) {
+    free_dev(c->d);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return H2_OK;
+}
+
 }  // namespace h2
 
 using namespace h2;
@@ -176,63 +239,7 @@ int h2_plan_bases(h2_plan pp, double *V, double *E) {
 
 int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
              const h2_options *opt, h2_handle *out) {
-  if (!out) return fail(H2_EINVAL, "out is NULL");
-  *out = nullptr;
-  h2_options o;
-  h2_options_default(&o);
-  if (opt) o = *opt;
-  if (o.prec < H2_F64 || o.prec > H2_F16) return fail(H2_EINVAL, "unknown precision");
-  if (o.coupling < H2_COUPLING_AUTO || o.coupling > H2_COUPLING_REGEN) return fail(H2_EINVAL, "unknown coupling mode");
-  const bool half_prec = o.prec == H2_BF16 || o.prec == H2_F16, f64 = o.prec == H2_F64 || o.prec == H2_F64_NATIVE;
-  if (o.coupling == H2_COUPLING_REGEN && f64)
-    return fail(H2_EINVAL, "the regenerated coupling is FP32; use H2_F32, H2_BF16 or H2_F16");
-  if (o.coupling == H2_COUPLING_STORED && half_prec)
-    return fail(H2_EINVAL, "16-bit precisions regenerate the coupling");
-  if (o.tensor < 0 || o.tensor > 1) return fail(H2_EINVAL, "tensor must be 0 (tensor cores where supported) or 1 (never)");
-  for (int r : o.reserved)
-    if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
-  if (o.basis_prec != 0) {
-    if (!half_prec) return fail(H2_EINVAL, "basis_prec applies to H2_BF16 and H2_F16 handles only; use 0");
-    if (o.basis_prec != H2_F32 && o.basis_prec != o.prec)
-      return fail(H2_EINVAL, "basis_prec must be 0, H2_F32 or the handle's own 16-bit precision");
-  }
-  int ndev = 0;
-  H2_CUDA_TRY(cudaGetDeviceCount(&ndev));
-  if (o.device < 0 || o.device >= ndev) return fail(H2_EINVAL, "device ordinal out of range");
-  H2_CUDA_TRY(cudaSetDevice(o.device));
-  h2_ctx *c = new (std::nothrow) h2_ctx();
-  if (!c) return fail(H2_ENOMEM, "handle");
-  c->device = o.device;
-  c->stream = (cudaStream_t)o.stream;
-  c->quad_order = o.quad_order;
-  c->d.prec = o.prec;
-  c->d.tensor = o.tensor;
-  // FP32 leaf bases: explicitly, or by default under bfloat16 storage
-  c->d.v32 = half_prec && (o.basis_prec == H2_F32 || (o.basis_prec == 0 && o.prec == H2_BF16));
-  c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);
-  int rc;
-  const auto t0 = std::chrono::steady_clock::now();
-  auto ms = [](std::chrono::steady_clock::time_point a) {
-    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
-  };
-  try {
-    // the trees, blocks and interpolation points on the host; V and E are
-    // computed on the device by device_build
-    rc = make_plan(vert, nv, tri, nt, leaf_size, eta, order, false, c->plan);
-    c->build_ms[H2_BUILD_PLAN] = ms(t0);
-    if (!rc && o.prec == H2_F64) rc = check_double_float_range(c->plan);
-    if (!rc) rc = device_build(*c);
-  } catch (const std::bad_alloc &) {
-    rc = fail(H2_ENOMEM, "host allocation in set-up");
-  }
-  c->build_ms[H2_BUILD_TOTAL] = ms(t0);
-  if (rc) {
-    free_dev(c->d);
-    delete c;
-    return rc;
-  }
-  *out = c;
-  return H2_OK;
+  return build_handle(vert, nv, tri, nt, leaf_size, eta, order, opt, KernelFn{kKernelLaplace, 0.0}, out);
 }
 
 static void drop_events(Prof &p) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -29,6 +30,14 @@ template <class T>
 inline cudaError_t dmalloc(T **p, size_t bytes) {
   return dmalloc_raw(reinterpret_cast<void **>(p), bytes);
 }
+
+// Kernel of a real H^2 matrix (Section 1): the Laplace kernel, or the real
+// or imaginary part of the Helmholtz kernel with wave number kappa.
+constexpr int kKernelLaplace = 0, kKernelHelmholtzRe = 1, kKernelHelmholtzIm = 2;
+struct KernelFn {
+  int kind;
+  double kappa;
+};
 
 // Gauss-Legendre nodes and weights on [0,1] (Newton on the Legendre recurrence).
 void gauss_legendre01(int q, std::vector<double> &x, std::vector<double> &w);
@@ -68,6 +77,7 @@ int make_plan(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, in
 // Device representation of one H^2 matrix.
 struct Dev {
   int prec = H2_F64;
+  KernelFn kernel{kKernelLaplace, 0.0};   // the real kernel of this matrix
   int coupling = 0;             // 0: S stored, 1: S regenerated in FP32 in the product
   size_t esize = 8;             // bytes of an arithmetic / vector value
   size_t ssize = 8;             // bytes of a stored value (V, E, S, nearfield)
@@ -190,6 +200,10 @@ bool ntc_eligible(const Dev &d);
 int ntc_build(Ctx &c, const int32_t *nrow_dev);
 int ntc_near(Ctx &c, const void *xpad, void *ypad, int rp, int accumulate, int64_t *launches);
 
+// h2_build for a given kernel (h2_api.cpp)
+int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
+                 const h2_options *opt, KernelFn kf, h2_handle *out);
+
 // device allocation helper (tracks bytes)
 int dev_alloc(Dev &d, void **ptr, size_t bytes);
 int ensure_work(Ctx &c, int nrhs);
@@ -208,9 +222,21 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64, bool accumul
 // GMRES (h2_solve.cu); b, z device FP64 arrays
 int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
               h2_solve_info *info);
-// one GMRES cycle for G~ D = R (see h2_solve.cu); host arrays of nrhs entries
-int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int restart, const double *tol,
-                const int *act, const int *max_it, int *iters);
+// A linear operator y = A x on column-major n x nrhs FP64 device arrays, as
+// GMRES sees it: the product of one handle (ctx_op), or a composite such as
+// the real form of a complex Helmholtz matrix.
+struct LinOp {
+  int64_t n = 0;
+  cudaStream_t stream = nullptr;
+  std::function<int(const double *, double *, int)> apply;
+};
+LinOp ctx_op(Ctx &c);
+// one GMRES cycle for A D = R (see h2_solve.cu); host arrays of nrhs entries
+int gmres_cycle(const LinOp &op, GmresWork &w, const double *R, double *D, int nrhs, int restart,
+                const double *tol, const int *act, const int *max_it, int *iters);
+// restarted GMRES for A z = b with work space w (at least nrhs columns and restart)
+int run_gmres_op(const LinOp &op, GmresWork &w, const double *b, double *z, int nrhs, double rtol, int restart,
+                 int maxit, h2_solve_info *info);
 int alloc_gmres_work(GmresWork &w, int64_t n, int cols, int restart);
 // GMRES-IR: outer residuals with hi, inner GMRES with lo (same mesh and tree)
 int run_gmres_ir(Ctx &hi, Ctx &lo, const double *b, double *z, int nrhs, double rtol, double inner_rtol,

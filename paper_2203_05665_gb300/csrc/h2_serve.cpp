@@ -265,7 +265,7 @@ int step(h2_srv &s, int ei, std::unique_lock<std::mutex> &lk) {
     left[i] = e.maxit - sl.iters;
   }
   if (e.lo) H2_CUDA_TRY(cudaStreamSynchronize(st));
-  if ((rc = gmres_cycle(cyc, e.w, e.R, e.D, W, e.restart, tol.data(), act.data(), left.data(), it.data())))
+  if ((rc = gmres_cycle(ctx_op(cyc), e.w, e.R, e.D, W, e.restart, tol.data(), act.data(), left.data(), it.data())))
     return rc;
   if (e.lo) H2_CUDA_TRY(cudaStreamSynchronize(cyc.stream));
   for (int i = 0; i < na; ++i) e.slots[i].iters += it[i];

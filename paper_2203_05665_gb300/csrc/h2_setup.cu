@@ -22,6 +22,7 @@
 
 #include "h2_dd.cuh"
 #include "h2_internal.hpp"
+#include "h2_kernel.cuh"
 
 namespace h2 {
 
@@ -35,12 +36,6 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
 __constant__ double c_gx[kMaxQ];
 __constant__ double c_gw[kMaxQ];
 
-constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
-
-__device__ __forceinline__ double green(const double *x, const double *y) {
-  double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
-  return kInv4Pi / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-}
 
 __device__ __forceinline__ void tri_point(const double *A, const double *B, const double *C, double s, double t,
                                           double *x) {
@@ -52,7 +47,8 @@ __device__ __forceinline__ void tri_point(const double *A, const double *B, cons
 // S_b stored transposed and padded: S[b][mu][nu], nu < kp, zero for nu >= k
 template <class T>
 __global__ void k_coupling_fill(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-                                const double *__restrict__ cheb, int m, int kp, int64_t nblk, T *__restrict__ S) {
+                                const double *__restrict__ cheb, int m, int kp, int64_t nblk, KernelFn kf,
+                                T *__restrict__ S) {
   const int k = m * m * m;
   const int64_t per = (int64_t)k * kp, total = nblk * per;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -68,7 +64,7 @@ __global__ void k_coupling_fill(const int32_t *__restrict__ row, const int32_t *
     y[0] = cheb[(3 * s + 0) * m + mu % m];
     y[1] = cheb[(3 * s + 1) * m + (mu / m) % m];
     y[2] = cheb[(3 * s + 2) * m + mu / (m * m)];
-    S[e] = from_double<T>(green(x, y));
+    S[e] = from_double<T>(kernel_value(kf, x, y));
   }
 }
 
@@ -81,6 +77,7 @@ struct Geo {
   const int32_t *blk_row;   // row leaf of each near block
   const int32_t *blk_col;   // column leaf of each near block
   int64_t lmax, lp;         // leaf height and its padding to a multiple of 4
+  KernelFn kf;              // the kernel
 };
 
 // Nearfield block layout: entry (t, c) of block b (test triangle t of the
@@ -137,7 +134,7 @@ __global__ void k_near_regular(Geo g, int64_t nblk, int q, T *__restrict__ near,
           for (int dd = 0; dd < q; ++dd) {
             double y[3];
             tri_point(A2, B2, C2, c_gx[cc], c_gx[cc] * c_gx[dd], y);
-            inner += c_gw[cc] * c_gw[dd] * c_gx[cc] * green(x, y);
+            inner += c_gw[cc] * c_gw[dd] * c_gx[cc] * kernel_value(g.kf, x, y);
           }
         acc += wx * inner;
       }
@@ -234,7 +231,7 @@ __global__ void k_near_singular(Geo g, const int64_t *__restrict__ sing, int64_t
               double x[3], y[3];
               tri_point(A1, B1, C1, pr[0], pr[1], x);
               tri_point(A2, B2, C2, pr[2], pr[3], y);
-              part += w * green(x, y);
+              part += w * kernel_value(g.kf, x, y);
             }
             acc += c_gw[i0] * c_gw[i1] * c_gw[i2] * c_gw[i3] * part;
           }
@@ -635,7 +632,8 @@ int build_typed(Ctx &c) {
     return rc;
   if (d.coupling == 0 && d.nadm > 0) {
     k_coupling_fill<T><<<grid_for(d.nadm * k * d.kp, 256), 256, 0, st>>>((const int32_t *)t_arow.ptr, d.adm_col,
-                                                                          d.cheb, m, d.kp, d.nadm, (T *)d.S);
+                                                                          d.cheb, m, d.kp, d.nadm, d.kernel,
+                                                                          (T *)d.S);
     H2_CUDA_TRY(cudaGetLastError());
   }
   // FP64 and FP32 handles of order 4: the E4M3 digit planes for the tensor-core coupling
@@ -663,7 +661,7 @@ int build_typed(Ctx &c) {
     if (dmalloc(&t_cnt.ptr, 8) != cudaSuccess) return fail(H2_ENOMEM, "singular count");
     H2_CUDA_TRY(cudaMemsetAsync(t_cnt.ptr, 0, 8, st));
     Geo g{(const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr, d.pad_src,
-          (const int32_t *)t_nrow.ptr, (const int32_t *)t_ncol.ptr, L, Lp};
+          (const int32_t *)t_nrow.ptr, (const int32_t *)t_ncol.ptr, L, Lp, d.kernel};
     k_near_regular<TQ><<<grid_for(d.nnear * L * Lp, 128), 128, 0, st>>>(
         g, d.nnear, c.quad_order, qnear, (int64_t *)t_sing.ptr, (unsigned long long *)t_cnt.ptr, cap);
     H2_CUDA_TRY(cudaGetLastError());

@@ -268,11 +268,20 @@ int alloc_gmres_work(GmresWork &w, int64_t n_, int cols, int mr) {
 // stops when its residual estimate drops to tol[c], at a breakdown, after
 // restart iterations or after max_it[c] iterations.  iters[c] receives the
 // iterations done.  R may alias w.W.  All host arrays have nrhs entries.
-int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int restart, const double *tol,
-                const int *act, const int *max_it, int *iters) {
-  const int64_t n = c.d.n, tot = n * nrhs;
+LinOp ctx_op(Ctx &c) {
+  LinOp op;
+  op.n = c.d.n;
+  op.stream = c.stream;
+  Ctx *cp = &c;
+  op.apply = [cp](const double *x, double *y, int nrhs) { return run_matvec(*cp, x, y, nrhs, true); };
+  return op;
+}
+
+int gmres_cycle(const LinOp &op, GmresWork &w, const double *R, double *D, int nrhs, int restart,
+                const double *tol, const int *act, const int *max_it, int *iters) {
+  const int64_t n = op.n, tot = n * nrhs;
   const int mr = restart;
-  cudaStream_t st = c.stream;
+  cudaStream_t st = op.stream;
   int rc;
   std::vector<double> rn(nrhs), g0((size_t)(mr + 1) * nrhs, 0.0);
   std::vector<int> on(nrhs, 0);
@@ -306,7 +315,7 @@ int gmres_cycle(Ctx &c, GmresWork &w, const double *R, double *D, int nrhs, int 
   bool pending = false;
   for (int j = 0; j < mr; ++j) {
     double *Vj = w.Vb + (int64_t)j * tot, *Vj1 = w.Vb + (int64_t)(j + 1) * tot;
-    if ((rc = run_matvec(c, Vj, w.W, nrhs, true))) return rc;
+    if ((rc = op.apply(Vj, w.W, nrhs))) return rc;
     dots(w.Vb, w.W, n, nrhs, j + 1, w.h1, w.dpart, st);
     k_orth<<<grid1(tot), kT, 0, st>>>(w.Vb, w.h1, j + 1, n, nrhs, w.W);
     dots(w.Vb, w.W, n, nrhs, j + 1, w.h2, w.dpart, st);
@@ -348,11 +357,19 @@ __global__ void k_axpy_cols(const double *__restrict__ d, int64_t total, double 
 // relative residual is <= rtol or after maxit iterations.
 int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
               h2_solve_info *info) {
-  const int64_t n = c.d.n, tot = n * nrhs;
-  cudaStream_t st = c.stream;
   int rc;
   if ((rc = ensure_gmres_work(c, nrhs, restart))) return rc;
-  GmresWork &w = c.gw;
+  const int status = run_gmres_op(ctx_op(c), c.gw, b, z, nrhs, rtol, restart, maxit, info);
+  if (status != H2_OK && status != H2_ENOCONV) return status;
+  int derr = take_device_error(c);
+  return derr ? derr : status;
+}
+
+int run_gmres_op(const LinOp &op, GmresWork &w, const double *b, double *z, int nrhs, double rtol, int restart,
+                 int maxit, h2_solve_info *info) {
+  const int64_t n = op.n, tot = n * nrhs;
+  cudaStream_t st = op.stream;
+  int rc;
   std::vector<double> bn(nrhs), rn(nrhs), res(nrhs, 0.0), tol(nrhs);
   std::vector<int> act(nrhs), left(nrhs), it(nrhs), iters(nrhs, 0);
   norms(b, n, nrhs, w.bn, w.dpart, st);
@@ -361,7 +378,7 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
   H2_CUDA_TRY(cudaMemcpyAsync(w.r, b, tot * 8, cudaMemcpyDeviceToDevice, st));
   for (bool first = true;; first = false) {
     if (!first) {
-      if ((rc = run_matvec(c, z, w.Az, nrhs, true))) return rc;
+      if ((rc = op.apply(z, w.Az, nrhs))) return rc;
       k_residual<<<grid1(tot), kT, 0, st>>>(b, w.Az, tot, w.r);
     }
     norms(w.r, n, nrhs, w.hn, w.dpart, st);
@@ -376,7 +393,8 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
       any = any || act[col];
     }
     if (!any) break;
-    if ((rc = gmres_cycle(c, w, w.r, w.d, nrhs, restart, tol.data(), act.data(), left.data(), it.data()))) return rc;
+    if ((rc = gmres_cycle(op, w, w.r, w.d, nrhs, restart, tol.data(), act.data(), left.data(), it.data())))
+      return rc;
     for (int col = 0; col < nrhs; ++col) iters[col] += it[col];
     k_axpy_cols<<<grid1(tot), kT, 0, st>>>(w.d, tot, z);
   }
@@ -391,8 +409,7 @@ int run_gmres(Ctx &c, const double *b, double *z, int nrhs, double rtol, int res
     }
   }
   if (status != H2_OK) fail(H2_ENOCONV, "GMRES reached maxit before the residual target");
-  int derr = take_device_error(c);
-  return derr ? derr : status;
+  return status;
 }
 
 

@@ -55,6 +55,7 @@
 #include "h2_dd.cuh"
 #include "h2_digits.hpp"
 #include "h2_internal.hpp"
+#include "h2_kernel.cuh"
 #include "h2_ptx.cuh"
 #include "h2_transfer.cuh"
 
@@ -112,7 +113,6 @@ __host__ __device__ constexpr uint32_t tc_idesc(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-constexpr double kInv4PiTc = 0.079577471545947667884441881686257181;
 
 // byte offset of (row r, contraction index c) in a K-major one-byte operand
 // of 64 contraction values per row: core matrices of 8 rows x 16 bytes, four
@@ -186,10 +186,6 @@ __device__ __forceinline__ void named_sync_id(uint32_t id, uint32_t nthreads) {
 // 2^e as a float for -126 <= e <= 127 (exact; used for power-of-two scaling)
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
-__device__ __forceinline__ double tc_green(const double *x, const double *y) {
-  const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
-  return kInv4PiTc / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-}
 
 // interpolation point nu of cluster c (tensor Chebyshev points, Eq. (6c))
 __device__ __forceinline__ void tc_point(const double *cheb, int64_t c, int nu, double *x) {
@@ -201,7 +197,8 @@ __device__ __forceinline__ void tc_point(const double *cheb, int64_t c, int nu, 
 // ---------------------------------------------------------------- set-up
 // E[t][nu]: 1 + floor(log2 max |S_ts[nu][mu]|) over the blocks of row t (0 if none)
 __global__ void k_tc_rowexp(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                            const double *__restrict__ cheb, int64_t row0, int64_t nclu, int32_t *__restrict__ E) {
+                            const double *__restrict__ cheb, int64_t row0, int64_t nclu, KernelFn kf,
+                            int32_t *__restrict__ E) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (nclu - row0) * kTcK) return;
   const int64_t t = row0 + e / kTcK;
@@ -211,7 +208,7 @@ __global__ void k_tc_rowexp(const int64_t *__restrict__ ptr, const int32_t *__re
   for (int64_t b = ptr[t]; b < ptr[t + 1]; ++b)
     for (int mu = 0; mu < kTcK; ++mu) {
       tc_point(cheb, col[b], mu, y);
-      mx = fmax(mx, tc_green(x, y));
+      mx = fmax(mx, fabs(kernel_value(kf, x, y)));
     }
   E[t * kTcK + nu] = mx > 0.0 ? ilogb(mx) + 1 : 0;
 }
@@ -225,7 +222,7 @@ __device__ __forceinline__ unsigned char e4m3(int s) {
 template <int ND>
 __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__restrict__ col,
                              const double *__restrict__ cheb, const int32_t *__restrict__ E, int64_t nblk,
-                             unsigned char *__restrict__ Stc) {
+                             KernelFn kf, unsigned char *__restrict__ Stc) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nblk * kTcK * 4) return;
   const int64_t b = e / (kTcK * 4);
@@ -238,7 +235,7 @@ __global__ void k_tc_slice_s(const int32_t *__restrict__ brow, const int32_t *__
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     tc_point(cheb, s, 16 * cg + q, y);
-    const long long X = llrint(ldexp(tc_green(x, y), sc));
+    const long long X = llrint(ldexp(kernel_value(kf, x, y), sc));
     int sl[ND];
     split_digits<ND>(X, sl);
 #pragma unroll
@@ -974,10 +971,11 @@ int tc_build_nd(Ctx &c, const int32_t *arow_dev) {
   H2_CUDA_TRY(cudaMemsetAsync(d.tc_E, 0, sizeof(int32_t) * (size_t)d.nclu * kTcK, st));
   H2_CUDA_TRY(cudaMemsetAsync(d.xtc, 0, (size_t)d.nclu * Dig<ND>::kTileB, st));
   const int64_t nr = (d.nclu - row0) * kTcK;
-  k_tc_rowexp<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(d.adm_ptr, d.adm_col, d.cheb, row0, d.nclu, d.tc_E);
+  k_tc_rowexp<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(d.adm_ptr, d.adm_col, d.cheb, row0, d.nclu, d.kernel,
+                                                             d.tc_E);
   const int64_t ns = d.nadm * kTcK * 4;
   k_tc_slice_s<ND><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(arow_dev, d.adm_col, d.cheb, d.tc_E, d.nadm,
-                                                                 (unsigned char *)d.Stc);
+                                                                 d.kernel, (unsigned char *)d.Stc);
   H2_CUDA_TRY(cudaGetLastError());
   H2_CUDA_TRY(cudaStreamSynchronize(st));
   d.tc_nd = ND;

@@ -6,5 +6,5 @@ lives in ``h2oracle.c`` (plain C, FP64); this module compiles it with gcc and
 wraps it with ctypes.  See ``h2oracle.c`` for the paper passages each step
 follows and for the readings taken where the paper is silent.
 """
-from .oracle import (Oracle, HelmholtzOracle, build_library, gauss01, pair_quad,  # noqa: F401
-                     KIND_LAPLACE, KIND_POLY, KIND_HELM_COS, KIND_HELM_SIN)
+from .oracle import (Oracle, HelmholtzOracle, GcaOracle, build_library, gauss01, pair_quad,  # noqa: F401
+                     green_rule, aca, KIND_LAPLACE, KIND_POLY, KIND_HELM_COS, KIND_HELM_SIN)

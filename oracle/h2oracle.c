@@ -21,6 +21,7 @@
  *   block tree, admissibility ........................... Section 2, Eq. (8)
  *   transfer matrices E (= F here), nested bases ........ Section 2, Eqs. (9), (10)
  *   forward / backward / interaction phases ............. Section 2, Algorithms 1-3
+ *   GCA-H^2: pivot elements, S = G on pivot pairs ....... Section 3 (GCA-H^2 example)
  * Nearfield entries use the Sauter-Schwab quadrature that the paper's
  * experiments name (Section 3, experiments paragraph), restated from the
  * published method (Sauter & Schwab, Boundary Element Methods, 2011, Sec. 5.2).
@@ -50,6 +51,29 @@
  *      unordered pair is computed once with the smaller index as test
  *      triangle and mirrored.
  *   R8 matvec overwrites: y = G~ x.
+ *
+ * GCA-H^2 (Section 3 names it and states only that pivot elements are
+ * chosen per cluster and that S_{tau sigma} is computed from G on the
+ * pivots); the construction follows the cited Green cross approximation
+ * with these readings:
+ *   G1 Green quadrature on the boundary of the box [lo - gamma rho, hi +
+ *      gamma rho], rho = half diagonal of the cluster's box, gamma = 1 by
+ *      default: per face a tensor Gauss rule with qg nodes per direction
+ *      (qg = 4, the paper's "quadrature order m = 4" of its GCA runs);
+ *      faces in the order (axis 0 low, high, axis 1 ..., axis 2 ...).
+ *   G2 the surrogate of a cluster: rows = candidate triangles, columns = the
+ *      single-layer and the double-layer family of Green's representation
+ *      formula at every quadrature point, weighted, each integrated over the
+ *      triangle by the collapsed rule with qt = 3.
+ *   G3 cross approximation with complete pivoting, relative accuracy eps
+ *      (1e-4, the paper's value) against the largest entry of the surrogate.
+ *   G4 ties: the first entry (row-major) within a relative 2^-30 of the
+ *      largest modulus.
+ *   G5 V^ = M[:, J] M[I, J]^{-1} with its pivot rows set to unit vectors:
+ *      leaves keep it as V, parents cut it into their sons' E.
+ *   G6 nested pivots: the candidates of a parent are the pivots of its first
+ *      son, then those of its second son; leaves take their triangles in
+ *      cluster order.  S_{tau sigma} = G|_{tau_0 x sigma_0} by R7.
  *
  * Compile with -ffp-contract=off so that the tree-building comparisons are
  * evaluated without fused multiply-adds.
@@ -894,6 +918,490 @@ int or_matvec_rows(const orh2 *h, const double *x, int nrhs, const int64_t *rows
     free(tmp);
   }
   free(pos);
+  free(xh);
+  return 0;
+}
+
+
+/* ------------------------------------------------------------------ */
+/* GCA-H^2: nested cross approximation with Green quadrature (Section 3,
+ * the GCA-H^2 example).  Every cluster tau gets pivot elements
+ * tau_0 of tau (pivots of a parent are chosen among its sons' pivots), and
+ * every admissible block the coupling S_{tau sigma} = G|_{tau_0 x sigma_0},
+ * the Galerkin submatrix on the pivots.  The section states only this much;
+ * the construction of the pivots follows the cited Green cross
+ * approximation with the readings G1-G6 listed in the header.            */
+/* ------------------------------------------------------------------ */
+
+/* G1: quadrature on the boundary of the auxiliary box omega = [lo - gamma
+ * rho, hi + gamma rho] (rho = half the diagonal of [lo, hi]): for axis
+ * a = 0, 1, 2, the face at the low end (outward normal -e_a) then the face
+ * at the high end (+e_a); on a face the other two axes b < c carry the
+ * tensor Gauss-Legendre rule with qg nodes in increasing order, node i on
+ * axis b outermost.  Returns the point count Q = 6 qg^2; Z, N: Q x 3,
+ * W: Q. */
+int or_gca_green_rule(const double *lo, const double *hi, double gamma, int qg, double *Z, double *N, double *W) {
+  double gx[64], gw[64];
+  or_gauss01(qg, gx, gw);
+  double d0 = hi[0] - lo[0], d1 = hi[1] - lo[1], d2 = hi[2] - lo[2];
+  double rho = 0.5 * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  double olo[3], ohi[3];
+  for (int d = 0; d < 3; ++d) { olo[d] = lo[d] - gamma * rho; ohi[d] = hi[d] + gamma * rho; }
+  int q = 0;
+  for (int a = 0; a < 3; ++a) {
+    int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    for (int side = 0; side < 2; ++side)
+      for (int i = 0; i < qg; ++i)
+        for (int j = 0; j < qg; ++j) {
+          double *z = Z + 3 * q, *n = N + 3 * q;
+          z[a] = side ? ohi[a] : olo[a];
+          z[b] = olo[b] + gx[i] * (ohi[b] - olo[b]);
+          z[c] = olo[c] + gx[j] * (ohi[c] - olo[c]);
+          n[0] = n[1] = n[2] = 0.0;
+          n[a] = side ? 1.0 : -1.0;
+          W[q] = gw[i] * gw[j] * (ohi[b] - olo[b]) * (ohi[c] - olo[c]);
+          q++;
+        }
+  }
+  return q;
+}
+
+/* G2: the Green surrogate of a cluster, nr x 2Q row-major: row r is test
+ * triangle rows[r]; column nu < Q holds W_nu int_T g(x, z_nu) dx and column
+ * Q + nu holds W_nu int_T dg/dn_z(x, z_nu) dx, dg/dn_z = n.(x - z) /
+ * (4 pi |x - z|^3) (the two families of Green's representation formula),
+ * both integrals by the collapsed Gauss rule with qt nodes per direction
+ * (R5), vertices in mesh order. */
+static void gca_surrogate(const orh2 *h, const int32_t *rows, int nr, const double *Z, const double *N,
+                          const double *W, int Q, int qt, double *M) {
+  double gx[32], gw[32];
+  or_gauss01(qt, gx, gw);
+  for (int r = 0; r < nr; ++r) {
+    int64_t t = rows[r];
+    const double *A = h->vert + 3 * (int64_t)h->tri[3 * t + 0];
+    const double *B = h->vert + 3 * (int64_t)h->tri[3 * t + 1];
+    const double *C = h->vert + 3 * (int64_t)h->tri[3 * t + 2];
+    double jac = 2.0 * h->area[t];
+    for (int nu = 0; nu < Q; ++nu) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int a = 0; a < qt; ++a)
+        for (int b = 0; b < qt; ++b) {
+          double x[3];
+          ref_map(A, B, C, gx[a], gx[a] * gx[b], x);
+          double w = jac * gw[a] * gw[b] * gx[a];
+          double e0 = x[0] - Z[3 * nu], e1 = x[1] - Z[3 * nu + 1], e2 = x[2] - Z[3 * nu + 2];
+          double rr = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+          s1 += w / (4.0 * OR_PI * rr);
+          s2 += w * (N[3 * nu] * e0 + N[3 * nu + 1] * e1 + N[3 * nu + 2] * e2) / (4.0 * OR_PI * rr * rr * rr);
+        }
+      M[(int64_t)r * 2 * Q + nu] = W[nu] * s1;
+      M[(int64_t)r * 2 * Q + Q + nu] = W[nu] * s2;
+    }
+  }
+}
+
+/* G3-G5: cross approximation of M (nr x nc, row-major) with complete
+ * pivoting.  Step k takes the largest modulus of the residual R_k (R_0 = M);
+ * it stops when that is at most eps times the largest modulus of M, or
+ * after min(nr, nc) steps.  The pivot is the first entry in row-major
+ * order whose modulus is at least (1 - 2^-30) times the largest (ties,
+ * which symmetric meshes produce, go to the lowest index).  Update:
+ * R <- R - R[:, j] R[i, :] / R[i, j], then row i and column j of R are set
+ * to zero.  Output: the rank k, the row and column pivots I, J (in pivot
+ * order) and Vhat = M[:, J] M[I, J]^{-1} (nr x k, row-major), solved by
+ * Gaussian elimination with partial pivoting, with the rows I set to the
+ * unit vectors (their exact values).  Vhat capacity: nr x min(nr, nc). */
+int or_gca_aca(const double *M, int nr, int nc, double eps, int *I, int *J, double *Vhat) {
+  int kmax = nr < nc ? nr : nc;
+  double *R = (double *)malloc((size_t)nr * nc * sizeof(double));
+  memcpy(R, M, (size_t)nr * nc * sizeof(double));
+  double mx0 = 0.0;
+  for (int64_t e = 0; e < (int64_t)nr * nc; ++e) if (fabs(M[e]) > mx0) mx0 = fabs(M[e]);
+  int k = 0;
+  while (k < kmax) {
+    double mx = 0.0;
+    for (int64_t e = 0; e < (int64_t)nr * nc; ++e) if (fabs(R[e]) > mx) mx = fabs(R[e]);
+    if (mx == 0.0 || mx <= eps * mx0) break;
+    double thr = mx * (1.0 - ldexp(1.0, -30));
+    int64_t pe = 0;
+    while (fabs(R[pe]) < thr) pe++;
+    int i = (int)(pe / nc), j = (int)(pe % nc);
+    I[k] = i;
+    J[k] = j;
+    k++;
+    double piv = R[pe];
+    for (int r = 0; r < nr; ++r) {
+      if (r == i) continue;
+      double f = R[(int64_t)r * nc + j] / piv;
+      for (int c = 0; c < nc; ++c)
+        if (c != j) R[(int64_t)r * nc + c] -= f * R[(int64_t)i * nc + c];
+    }
+    for (int c = 0; c < nc; ++c) R[(int64_t)i * nc + c] = 0.0;
+    for (int r = 0; r < nr; ++r) R[(int64_t)r * nc + j] = 0.0;
+  }
+  free(R);
+  if (k == 0) return 0;
+  /* Vhat A = B with A = M[I, J], B = M[:, J]: solve A^T v = b per row */
+  double *At = (double *)malloc((size_t)k * k * sizeof(double));
+  int *perm = (int *)malloc(k * sizeof(int));
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < k; ++b) At[a * k + b] = M[(int64_t)I[b] * nc + J[a]];   /* At[a][b] = A[b][a] */
+  for (int a = 0; a < k; ++a) perm[a] = a;
+  for (int col = 0; col < k; ++col) {          /* LU with partial pivoting, in place */
+    int p = col;
+    for (int r = col + 1; r < k; ++r) if (fabs(At[r * k + col]) > fabs(At[p * k + col])) p = r;
+    if (p != col) {
+      for (int c = 0; c < k; ++c) { double t = At[col * k + c]; At[col * k + c] = At[p * k + c]; At[p * k + c] = t; }
+      int t = perm[col]; perm[col] = perm[p]; perm[p] = t;
+    }
+    for (int r = col + 1; r < k; ++r) {
+      double f = At[r * k + col] / At[col * k + col];
+      At[r * k + col] = f;
+      for (int c = col + 1; c < k; ++c) At[r * k + c] -= f * At[col * k + c];
+    }
+  }
+  double *b = (double *)malloc(k * sizeof(double));
+  for (int r = 0; r < nr; ++r) {
+    for (int a = 0; a < k; ++a) b[a] = M[(int64_t)r * nc + J[perm[a]]];
+    for (int a = 0; a < k; ++a)
+      for (int c = 0; c < a; ++c) b[a] -= At[a * k + c] * b[c];
+    for (int a = k - 1; a >= 0; --a) {
+      for (int c = a + 1; c < k; ++c) b[a] -= At[a * k + c] * b[c];
+      b[a] /= At[a * k + a];
+    }
+    for (int a = 0; a < k; ++a) Vhat[(int64_t)r * k + a] = b[a];
+  }
+  for (int a = 0; a < k; ++a)
+    for (int c = 0; c < k; ++c) Vhat[(int64_t)I[a] * k + c] = a == c ? 1.0 : 0.0;
+  free(At); free(perm); free(b);
+  return k;
+}
+
+typedef struct {
+  orh2 *h;          /* trees, blocks, nearfield */
+  int qg, qt;
+  double eps, gamma;
+  int *rank;        /* per cluster */
+  int32_t **piv;    /* per cluster: pivot triangles (caller's indices), pivot order */
+  double **V;       /* leaves: size x rank, rows in cluster order */
+  double **E;       /* non-root clusters: rank x rank(parent) */
+  int64_t *soff;    /* per block: offset into S (admissible), or -1 */
+  double *S;        /* admissible blocks: rank(t) x rank(s), row-major */
+} orgca;
+
+/* cluster c of the tree: its pivots, leaf basis or its sons' transfer
+ * matrices (G6: the candidate rows of a parent are the pivots of son 1
+ * followed by those of son 2) */
+static void gca_cluster(orgca *g, int64_t c) {
+  orh2 *h = g->h;
+  int Q = 6 * g->qg * g->qg, nc = 2 * Q;
+  int nr;
+  int32_t *rows;
+  int64_t leaf0 = ((int64_t)1 << h->depth) - 1;
+  if (c >= leaf0) {
+    nr = (int)h->size[c];
+    rows = (int32_t *)malloc((nr > 0 ? nr : 1) * sizeof(int32_t));
+    for (int r = 0; r < nr; ++r) rows[r] = (int32_t)h->idx[h->first[c] + r];
+  } else {
+    int k1 = g->rank[2 * c + 1], k2 = g->rank[2 * c + 2];
+    nr = k1 + k2;
+    rows = (int32_t *)malloc((nr > 0 ? nr : 1) * sizeof(int32_t));
+    memcpy(rows, g->piv[2 * c + 1], k1 * sizeof(int32_t));
+    memcpy(rows + k1, g->piv[2 * c + 2], k2 * sizeof(int32_t));
+  }
+  double *Z = (double *)malloc(Q * 3 * sizeof(double)), *N = (double *)malloc(Q * 3 * sizeof(double));
+  double *W = (double *)malloc(Q * sizeof(double));
+  or_gca_green_rule(h->lo + 3 * c, h->hi + 3 * c, g->gamma, g->qg, Z, N, W);
+  double *M = (double *)malloc((size_t)(nr > 0 ? nr : 1) * nc * sizeof(double));
+  gca_surrogate(h, rows, nr, Z, N, W, Q, g->qt, M);
+  int kcap = nr < nc ? nr : nc;
+  int *I = (int *)malloc((kcap > 0 ? kcap : 1) * sizeof(int)), *J = (int *)malloc((kcap > 0 ? kcap : 1) * sizeof(int));
+  double *Vh = (double *)malloc((size_t)(nr > 0 ? nr : 1) * (kcap > 0 ? kcap : 1) * sizeof(double));
+  int k = nr > 0 ? or_gca_aca(M, nr, nc, g->eps, I, J, Vh) : 0;
+  g->rank[c] = k;
+  g->piv[c] = (int32_t *)malloc((k > 0 ? k : 1) * sizeof(int32_t));
+  for (int a = 0; a < k; ++a) g->piv[c][a] = rows[I[a]];
+  if (c >= leaf0) {
+    g->V[c] = (double *)malloc((size_t)(nr > 0 ? nr : 1) * (k > 0 ? k : 1) * sizeof(double));
+    memcpy(g->V[c], Vh, (size_t)nr * k * sizeof(double));
+  } else {
+    int k1 = g->rank[2 * c + 1], k2 = g->rank[2 * c + 2];
+    g->E[2 * c + 1] = (double *)malloc((size_t)(k1 > 0 ? k1 : 1) * (k > 0 ? k : 1) * sizeof(double));
+    g->E[2 * c + 2] = (double *)malloc((size_t)(k2 > 0 ? k2 : 1) * (k > 0 ? k : 1) * sizeof(double));
+    memcpy(g->E[2 * c + 1], Vh, (size_t)k1 * k * sizeof(double));
+    memcpy(g->E[2 * c + 2], Vh + (size_t)k1 * k, (size_t)k2 * k * sizeof(double));
+  }
+  free(rows); free(Z); free(N); free(W); free(M); free(I); free(J); free(Vh);
+}
+
+void or_gca_free(orgca *g) {
+  if (!g) return;
+  if (g->h) {
+    for (int64_t c = 0; c < g->h->nclu; ++c) {
+      if (g->piv) free(g->piv[c]);
+      if (g->V) free(g->V[c]);
+      if (g->E) free(g->E[c]);
+    }
+    or_free(g->h);
+  }
+  free(g->rank); free(g->piv); free(g->V); free(g->E); free(g->soff); free(g->S);
+  free(g);
+}
+
+/* Build the GCA-H^2 matrix of the Laplace single-layer operator: trees and
+ * blocks as for or_build (R2, R3), nearfield with quadrature order q (R7),
+ * Green quadrature order qg, enlargement gamma, triangle rule qt,
+ * cross-approximation accuracy eps.  store_S: keep the coupling matrices
+ * (else they are evaluated when used).  NULL on invalid arguments. */
+orgca *or_gca_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf, double eta, int qg,
+                    double eps, double gamma, int qt, int q, int store_near, int store_S) {
+  if (qg < 1 || qg > 32 || qt < 1 || qt > 30 || !(eps >= 0.0) || !(gamma > 0.0)) return NULL;
+  orh2 *h = or_build(vert, nv, tri, nt, leaf, eta, 1, q, 0, 0.0, store_near, 0);
+  if (!h) return NULL;
+  orgca *g = (orgca *)calloc(1, sizeof(orgca));
+  g->h = h; g->qg = qg; g->qt = qt; g->eps = eps; g->gamma = gamma;
+  g->rank = (int *)calloc(h->nclu, sizeof(int));
+  g->piv = (int32_t **)calloc(h->nclu, sizeof(int32_t *));
+  g->V = (double **)calloc(h->nclu, sizeof(double *));
+  g->E = (double **)calloc(h->nclu, sizeof(double *));
+  for (int l = h->depth; l >= 0; --l) {
+    int64_t c0 = ((int64_t)1 << l) - 1, c1 = ((int64_t)2 << l) - 1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = c0; c < c1; ++c) gca_cluster(g, c);
+  }
+  g->soff = (int64_t *)malloc((h->nblk > 0 ? h->nblk : 1) * sizeof(int64_t));
+  int64_t tot = 0;
+  for (int64_t b = 0; b < h->nblk; ++b) {
+    g->soff[b] = -1;
+    if (h->badm[b]) { g->soff[b] = tot; tot += (int64_t)g->rank[h->bt[b]] * g->rank[h->bs[b]]; }
+  }
+  if (store_S) {
+    g->S = (double *)calloc(tot > 0 ? tot : 1, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < h->nblk; ++b) {
+      if (!h->badm[b]) continue;
+      int64_t t = h->bt[b], s = h->bs[b];
+      for (int a = 0; a < g->rank[t]; ++a)
+        for (int c = 0; c < g->rank[s]; ++c)
+          g->S[g->soff[b] + (int64_t)a * g->rank[s] + c] = galerkin_entry_q(h, g->piv[t][a], g->piv[s][c], h->q);
+    }
+  }
+  return g;
+}
+
+const orh2 *or_gca_h2(const orgca *g) { return g->h; }
+void or_gca_ranks(const orgca *g, int32_t *out) {
+  for (int64_t c = 0; c < g->h->nclu; ++c) out[c] = g->rank[c];
+}
+void or_gca_pivots(const orgca *g, int64_t c, int32_t *out) { memcpy(out, g->piv[c], g->rank[c] * sizeof(int32_t)); }
+void or_gca_V(const orgca *g, int64_t c, double *out) {
+  memcpy(out, g->V[c], (size_t)g->h->size[c] * g->rank[c] * sizeof(double));
+}
+void or_gca_E(const orgca *g, int64_t c, double *out) {
+  memcpy(out, g->E[c], (size_t)g->rank[c] * g->rank[(c - 1) / 2] * sizeof(double));
+}
+/* S_{t,s} = G|_{t_0 x s_0} (rank(t) x rank(s), row-major) */
+void or_gca_S(const orgca *g, int64_t t, int64_t s, double *out) {
+  for (int a = 0; a < g->rank[t]; ++a)
+    for (int c = 0; c < g->rank[s]; ++c)
+      out[(int64_t)a * g->rank[s] + c] = galerkin_entry_q(g->h, g->piv[t][a], g->piv[s][c], g->h->q);
+}
+
+static const double *gca_block_S(const orgca *g, int64_t b, double *tmp) {
+  if (g->S) return g->S + g->soff[b];
+  or_gca_S(g, g->h->bt[b], g->h->bs[b], tmp);
+  return tmp;
+}
+
+/* Algorithm 1 with the GCA bases: xh[c] (rank x nrhs) */
+static void gca_forward(const orgca *g, int64_t c, int lev, const double *x, int nrhs, double **xh) {
+  const orh2 *h = g->h;
+  int k = g->rank[c];
+  double *xc = xh[c];
+  for (int i = 0; i < k * nrhs; ++i) xc[i] = 0.0;
+  if (lev == h->depth) {
+    for (int nu = 0; nu < k; ++nu)
+      for (int r = 0; r < nrhs; ++r) {
+        double acc = 0.0;
+        for (int64_t p = 0; p < h->size[c]; ++p) acc += g->V[c][p * k + nu] * x[h->idx[h->first[c] + p] + r * h->nt];
+        xc[nu * nrhs + r] = acc;
+      }
+    return;
+  }
+  for (int a = 1; a <= 2; ++a) {
+    int64_t ch = 2 * c + a;
+    gca_forward(g, ch, lev + 1, x, nrhs, xh);
+    int kc = g->rank[ch];
+    for (int nu = 0; nu < k; ++nu)
+      for (int r = 0; r < nrhs; ++r) {
+        double acc = 0.0;
+        for (int nup = 0; nup < kc; ++nup) acc += g->E[ch][nup * k + nu] * xh[ch][nup * nrhs + r];
+        xc[nu * nrhs + r] += acc;
+      }
+  }
+}
+
+/* Algorithm 2 with the GCA bases */
+static void gca_backward(const orgca *g, int64_t c, int lev, double **yh, int nrhs, double *y) {
+  const orh2 *h = g->h;
+  int k = g->rank[c];
+  if (lev == h->depth) {
+    for (int64_t p = 0; p < h->size[c]; ++p)
+      for (int r = 0; r < nrhs; ++r) {
+        double acc = 0.0;
+        for (int nu = 0; nu < k; ++nu) acc += g->V[c][p * k + nu] * yh[c][nu * nrhs + r];
+        y[h->idx[h->first[c] + p] + r * h->nt] += acc;
+      }
+    return;
+  }
+  for (int a = 1; a <= 2; ++a) {
+    int64_t ch = 2 * c + a;
+    int kc = g->rank[ch];
+    for (int nup = 0; nup < kc; ++nup)
+      for (int r = 0; r < nrhs; ++r) {
+        double acc = 0.0;
+        for (int nu = 0; nu < k; ++nu) acc += g->E[ch][nup * k + nu] * yh[c][nu * nrhs + r];
+        yh[ch][nup * nrhs + r] += acc;
+      }
+    gca_backward(g, ch, lev + 1, yh, nrhs, y);
+  }
+}
+
+static int gca_maxrank(const orgca *g) {
+  int km = 1;
+  for (int64_t c = 0; c < g->h->nclu; ++c) if (g->rank[c] > km) km = g->rank[c];
+  return km;
+}
+
+/* y = G~ x (Algorithms 1-3) with the GCA-H^2 matrix; layout as or_matvec */
+int or_gca_matvec(const orgca *g, const double *x, double *y, int nrhs) {
+  const orh2 *h = g->h;
+  double **xh = (double **)malloc(h->nclu * sizeof(double *)), **yh = (double **)malloc(h->nclu * sizeof(double *));
+  for (int64_t c = 0; c < h->nclu; ++c) {
+    xh[c] = (double *)calloc((size_t)(g->rank[c] > 0 ? g->rank[c] : 1) * nrhs, sizeof(double));
+    yh[c] = (double *)calloc((size_t)(g->rank[c] > 0 ? g->rank[c] : 1) * nrhs, sizeof(double));
+  }
+  gca_forward(g, 0, 0, x, nrhs, xh);
+  memset(y, 0, (size_t)h->nt * nrhs * sizeof(double));
+  int km = gca_maxrank(g);
+#pragma omp parallel
+  {
+    double *tmp = (double *)malloc((size_t)km * km * sizeof(double));
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t t = 0; t < h->nclu; ++t) {
+      for (int64_t e = h->rowptr[t]; e < h->rowptr[t + 1]; ++e) {
+        int64_t b = h->rowblk[e], s = h->bs[b];
+        if (h->badm[b]) {
+          const double *S = gca_block_S(g, b, tmp);
+          int kt = g->rank[t], ks = g->rank[s];
+          for (int nu = 0; nu < kt; ++nu)
+            for (int r = 0; r < nrhs; ++r) {
+              double acc = 0.0;
+              for (int mu = 0; mu < ks; ++mu) acc += S[nu * ks + mu] * xh[s][mu * nrhs + r];
+              yh[t][nu * nrhs + r] += acc;
+            }
+        } else {
+          for (int64_t i = 0; i < h->size[t]; ++i)
+            for (int r = 0; r < nrhs; ++r) {
+              double acc = 0.0;
+              for (int64_t j = 0; j < h->size[s]; ++j) {
+                double gv = h->store_near ? h->nval[h->noff[b] + i * h->size[s] + j]
+                                          : galerkin_entry_q(h, h->idx[h->first[t] + i], h->idx[h->first[s] + j], h->q);
+                acc += gv * x[h->idx[h->first[s] + j] + r * h->nt];
+              }
+              y[h->idx[h->first[t] + i] + r * h->nt] += acc;
+            }
+        }
+      }
+    }
+    free(tmp);
+  }
+  gca_backward(g, 0, 0, yh, nrhs, y);
+  for (int64_t c = 0; c < h->nclu; ++c) { free(xh[c]); free(yh[c]); }
+  free(xh); free(yh);
+  return 0;
+}
+
+/* Rows of y = G~ x one by one (as or_matvec_rows): the forward phase over
+ * the whole tree, then per row the blocks of the clusters on the path from
+ * the root to the row's leaf, the coefficients pushed down by E. */
+int or_gca_matvec_rows(const orgca *g, const double *x, int nrhs, const int64_t *rows, int64_t nrows, double *yrows) {
+  const orh2 *h = g->h;
+  double **xh = (double **)malloc(h->nclu * sizeof(double *));
+  for (int64_t c = 0; c < h->nclu; ++c)
+    xh[c] = (double *)calloc((size_t)(g->rank[c] > 0 ? g->rank[c] : 1) * nrhs, sizeof(double));
+  gca_forward(g, 0, 0, x, nrhs, xh);
+  int64_t *pos = (int64_t *)malloc(h->nt * sizeof(int64_t));
+  for (int64_t p = 0; p < h->nt; ++p) pos[h->idx[p]] = p;
+  int64_t leaf0 = ((int64_t)1 << h->depth) - 1;
+  int km = gca_maxrank(g);
+#pragma omp parallel
+  {
+    double *tmp = (double *)malloc((size_t)km * km * sizeof(double));
+    double *acc = (double *)malloc((size_t)km * nrhs * sizeof(double));
+    double *nxt = (double *)malloc((size_t)km * nrhs * sizeof(double));
+    int64_t path[64];
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t ri = 0; ri < nrows; ++ri) {
+      int64_t i = rows[ri], p = pos[i];
+      int64_t leaf = leaf0;
+      while (!(p >= h->first[leaf] && p < h->first[leaf] + h->size[leaf])) leaf++;
+      int np = 0;
+      for (int64_t c = leaf;; c = (c - 1) / 2) {
+        path[np++] = c;
+        if (c == 0) break;
+      }
+      for (int r = 0; r < nrhs; ++r) yrows[ri + r * nrows] = 0.0;
+      for (int64_t e = h->rowptr[leaf]; e < h->rowptr[leaf + 1]; ++e) {
+        int64_t b = h->rowblk[e], s = h->bs[b];
+        if (h->badm[b]) continue;
+        for (int64_t j = 0; j < h->size[s]; ++j) {
+          int64_t tj = h->idx[h->first[s] + j];
+          double gv = galerkin_entry_q(h, i, tj, h->q);
+          for (int r = 0; r < nrhs; ++r) yrows[ri + r * nrows] += gv * x[tj + r * h->nt];
+        }
+      }
+      int kprev = 0;
+      for (int a = np - 1; a >= 0; --a) {
+        int64_t t = path[a];
+        int kt = g->rank[t];
+        if (a == np - 1) {
+          for (int q = 0; q < kt * nrhs; ++q) acc[q] = 0.0;
+        } else {
+          for (int nup = 0; nup < kt; ++nup)
+            for (int r = 0; r < nrhs; ++r) {
+              double s_ = 0.0;
+              for (int nu = 0; nu < kprev; ++nu) s_ += g->E[t][nup * kprev + nu] * acc[nu * nrhs + r];
+              nxt[nup * nrhs + r] = s_;
+            }
+          memcpy(acc, nxt, (size_t)kt * nrhs * sizeof(double));
+        }
+        for (int64_t e = h->rowptr[t]; e < h->rowptr[t + 1]; ++e) {
+          int64_t b = h->rowblk[e], s = h->bs[b];
+          if (!h->badm[b]) continue;
+          const double *S = gca_block_S(g, b, tmp);
+          int ks = g->rank[s];
+          for (int nu = 0; nu < kt; ++nu)
+            for (int r = 0; r < nrhs; ++r) {
+              double s_ = 0.0;
+              for (int mu = 0; mu < ks; ++mu) s_ += S[nu * ks + mu] * xh[s][mu * nrhs + r];
+              acc[nu * nrhs + r] += s_;
+            }
+        }
+        kprev = kt;
+      }
+      int kl = g->rank[leaf];
+      int64_t pl = p - h->first[leaf];
+      for (int r = 0; r < nrhs; ++r) {
+        double s_ = 0.0;
+        for (int nu = 0; nu < kl; ++nu) s_ += g->V[leaf][pl * kl + nu] * acc[nu * nrhs + r];
+        yrows[ri + r * nrows] += s_;
+      }
+    }
+    free(tmp); free(acc); free(nxt);
+  }
+  free(pos);
+  for (int64_t c = 0; c < h->nclu; ++c) free(xh[c]);
   free(xh);
   return 0;
 }

@@ -67,6 +67,25 @@ def _load():
                              C.POINTER(C.c_int), dp]
     lib.or_gauss01.argtypes = [C.c_int, dp, dp]
     lib.or_threads.restype = C.c_int
+    lib.or_gca_build.restype = C.c_void_p
+    lib.or_gca_build.argtypes = [dp, C.c_int64, ip32, C.c_int64, C.c_int, C.c_double, C.c_int, C.c_double,
+                                 C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.or_gca_free.argtypes = [C.c_void_p]
+    lib.or_gca_h2.restype = C.c_void_p
+    lib.or_gca_h2.argtypes = [C.c_void_p]
+    lib.or_gca_ranks.argtypes = [C.c_void_p, ip32]
+    lib.or_gca_pivots.argtypes = [C.c_void_p, C.c_int64, ip32]
+    lib.or_gca_V.argtypes = [C.c_void_p, C.c_int64, dp]
+    lib.or_gca_E.argtypes = [C.c_void_p, C.c_int64, dp]
+    lib.or_gca_S.argtypes = [C.c_void_p, C.c_int64, C.c_int64, dp]
+    lib.or_gca_matvec.restype = C.c_int
+    lib.or_gca_matvec.argtypes = [C.c_void_p, dp, dp, C.c_int]
+    lib.or_gca_matvec_rows.restype = C.c_int
+    lib.or_gca_matvec_rows.argtypes = [C.c_void_p, dp, C.c_int, ip64, C.c_int64, dp]
+    lib.or_gca_green_rule.restype = C.c_int
+    lib.or_gca_green_rule.argtypes = [dp, dp, C.c_double, C.c_int, dp, dp, dp]
+    lib.or_gca_aca.restype = C.c_int
+    lib.or_gca_aca.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
     lib.or_set_threads.argtypes = [C.c_int]
     _lib = lib
     return lib
@@ -251,3 +270,126 @@ class HelmholtzOracle:
 
     def entry(self, i, j, q=None):
         return self.c.entry(i, j, q) + 1j * self.s.entry(i, j, q)
+
+
+def green_rule(lo, hi, gamma: float, qg: int):
+    """The oracle's quadrature on the boundary of the box [lo - gamma rho,
+    hi + gamma rho] (rho = half diagonal): points (Q, 3), outward normals
+    (Q, 3), weights (Q,)."""
+    lib = _load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    q = 6 * qg * qg
+    Z, N, W = np.zeros((q, 3)), np.zeros((q, 3)), np.zeros(q)
+    lib.or_gca_green_rule(_p(lo, C.c_double), _p(hi, C.c_double), float(gamma), int(qg), _p(Z, C.c_double),
+                          _p(N, C.c_double), _p(W, C.c_double))
+    return Z, N, W
+
+
+def aca(M, eps: float):
+    """The oracle's cross approximation with complete pivoting of M (nr, nc):
+    row pivots I, column pivots J and V^ = M[:, J] M[I, J]^{-1} (nr, k)."""
+    lib = _load()
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    nr, nc = M.shape
+    kc = min(nr, nc)
+    I = np.zeros(kc, dtype=np.int32)
+    J = np.zeros(kc, dtype=np.int32)
+    Vh = np.zeros(nr * kc)
+    k = lib.or_gca_aca(_p(M, C.c_double), nr, nc, float(eps), I.ctypes.data_as(C.POINTER(C.c_int)),
+                       J.ctypes.data_as(C.POINTER(C.c_int)), _p(Vh, C.c_double))
+    return I[:k].copy(), J[:k].copy(), Vh[:nr * k].reshape(nr, k).copy()
+
+
+class GcaOracle:
+    """The oracle's GCA-H^2 matrix of one mesh (Section 3's GCA-H^2 example:
+    pivot elements per cluster, nested through the sons' pivots, and the
+    coupling S = G on the pivot pairs), Laplace kernel."""
+
+    def __init__(self, vert, tri, leaf_size=32, eta=2.0, green_order=4, eps=1e-4, gamma=1.0, tri_order=3,
+                 quad_order=3, store_near=True, store_S=True):
+        lib = _load()
+        self._lib = lib
+        self.vert = np.ascontiguousarray(vert, dtype=np.float64)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.n = int(self.tri.shape[0])
+        g = lib.or_gca_build(_p(self.vert, C.c_double), self.vert.shape[0], _p(self.tri, C.c_int32), self.n,
+                             int(leaf_size), float(eta), int(green_order), float(eps), float(gamma), int(tri_order),
+                             int(quad_order), int(store_near), int(store_S))
+        if not g:
+            raise ValueError("oracle: invalid arguments")
+        self._g = C.c_void_p(g)
+        self._h = C.c_void_p(lib.or_gca_h2(self._g))
+        info = np.zeros(7, dtype=np.int64)
+        lib.or_info(self._h, _p(info, C.c_int64))
+        (self.depth, self.nclu, self.nblk, self.nadm, self.nnear, self.near_entries, _) = (int(v) for v in info)
+        self.rank = np.zeros(self.nclu, dtype=np.int32)
+        lib.or_gca_ranks(self._g, _p(self.rank, C.c_int32))
+
+    def __del__(self):
+        g = getattr(self, "_g", None)
+        if g is not None and g.value:
+            self._lib.or_gca_free(g)
+            self._g = None
+
+    def tree(self):
+        nc = self.nclu
+        idx = np.zeros(self.n, dtype=np.int64)
+        first = np.zeros(nc, dtype=np.int64)
+        size = np.zeros(nc, dtype=np.int64)
+        lo = np.zeros((nc, 3))
+        hi = np.zeros((nc, 3))
+        pts = np.zeros((nc, 3, 1))
+        self._lib.or_tree(self._h, _p(idx, C.c_int64), _p(first, C.c_int64), _p(size, C.c_int64),
+                          _p(lo, C.c_double), _p(hi, C.c_double), _p(pts, C.c_double))
+        return dict(idx=idx, first=first, size=size, lo=lo, hi=hi)
+
+    def blocks(self):
+        t = np.zeros(self.nblk, dtype=np.int32)
+        s = np.zeros(self.nblk, dtype=np.int32)
+        a = np.zeros(self.nblk, dtype=np.uint8)
+        self._lib.or_blocks(self._h, _p(t, C.c_int32), _p(s, C.c_int32), _p(a, C.c_uint8))
+        return t, s, a.astype(bool)
+
+    def pivots(self, c: int):
+        out = np.zeros(int(self.rank[c]), dtype=np.int32)
+        self._lib.or_gca_pivots(self._g, int(c), _p(out, C.c_int32))
+        return out
+
+    def V(self, c: int, size: int):
+        out = np.zeros((size, int(self.rank[c])))
+        self._lib.or_gca_V(self._g, int(c), _p(out, C.c_double))
+        return out
+
+    def E(self, c: int):
+        out = np.zeros((int(self.rank[c]), int(self.rank[(c - 1) // 2])))
+        self._lib.or_gca_E(self._g, int(c), _p(out, C.c_double))
+        return out
+
+    def S(self, t: int, s: int):
+        out = np.zeros((int(self.rank[t]), int(self.rank[s])))
+        self._lib.or_gca_S(self._g, int(t), int(s), _p(out, C.c_double))
+        return out
+
+    def entry(self, i: int, j: int, q: int | None = None) -> float:
+        return self._lib.or_entry(self._h, int(i), int(j), int(q if q is not None else 3))
+
+    def dense(self):
+        """The Galerkin matrix itself (every pair by the nearfield rule)."""
+        g = np.zeros((self.n, self.n), order="F")
+        self._lib.or_dense(self._h, _p(g, C.c_double))
+        return g
+
+    def matvec(self, x):
+        x = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(self.n, -1))
+        y = np.zeros(x.shape, order="F")
+        self._lib.or_gca_matvec(self._g, _p(x, C.c_double), _p(y, C.c_double), x.shape[1])
+        return y
+
+    def matvec_rows(self, x, rows):
+        x = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(self.n, -1))
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.zeros((rows.shape[0], x.shape[1]), order="F")
+        self._lib.or_gca_matvec_rows(self._g, _p(x, C.c_double), x.shape[1], _p(rows, C.c_int64), rows.shape[0],
+                                     _p(out, C.c_double))
+        return out

@@ -66,7 +66,8 @@
  *      formula at every quadrature point, weighted, each integrated over the
  *      triangle by the collapsed rule with qt = 3.
  *   G3 cross approximation with complete pivoting, relative accuracy eps
- *      (1e-4, the paper's value) against the largest entry of the surrogate.
+ *      (1e-4, the paper's value) against the largest entry of the surrogate,
+ *      at most 128 pivots per cluster.
  *   G4 ties: the first entry (row-major) within a relative 2^-30 of the
  *      largest modulus.
  *   G5 V^ = M[:, J] M[I, J]^{-1} with its pivot rows set to unit vectors:
@@ -1003,7 +1004,7 @@ static void gca_surrogate(const orh2 *h, const int32_t *rows, int nr, const doub
 /* G3-G5: cross approximation of M (nr x nc, row-major) with complete
  * pivoting.  Step k takes the largest modulus of the residual R_k (R_0 = M);
  * it stops when that is at most eps times the largest modulus of M, or
- * after min(nr, nc) steps.  The pivot is the first entry in row-major
+ * after min(nr, nc, kmax) steps (kmax <= 0: no cap).  The pivot is the first entry in row-major
  * order whose modulus is at least (1 - 2^-30) times the largest (ties,
  * which symmetric meshes produce, go to the lowest index).  Update:
  * R <- R - R[:, j] R[i, :] / R[i, j], then row i and column j of R are set
@@ -1011,8 +1012,9 @@ static void gca_surrogate(const orh2 *h, const int32_t *rows, int nr, const doub
  * order) and Vhat = M[:, J] M[I, J]^{-1} (nr x k, row-major), solved by
  * Gaussian elimination with partial pivoting, with the rows I set to the
  * unit vectors (their exact values).  Vhat capacity: nr x min(nr, nc). */
-int or_gca_aca(const double *M, int nr, int nc, double eps, int *I, int *J, double *Vhat) {
+int or_gca_aca(const double *M, int nr, int nc, double eps, int kcap, int *I, int *J, double *Vhat) {
   int kmax = nr < nc ? nr : nc;
+  if (kcap > 0 && kcap < kmax) kmax = kcap;
   double *R = (double *)malloc((size_t)nr * nc * sizeof(double));
   memcpy(R, M, (size_t)nr * nc * sizeof(double));
   double mx0 = 0.0;
@@ -1079,7 +1081,7 @@ int or_gca_aca(const double *M, int nr, int nc, double eps, int *I, int *J, doub
 
 typedef struct {
   orh2 *h;          /* trees, blocks, nearfield */
-  int qg, qt;
+  int qg, qt, kcap;
   double eps, gamma;
   int *rank;        /* per cluster */
   int32_t **piv;    /* per cluster: pivot triangles (caller's indices), pivot order */
@@ -1117,7 +1119,7 @@ static void gca_cluster(orgca *g, int64_t c) {
   int kcap = nr < nc ? nr : nc;
   int *I = (int *)malloc((kcap > 0 ? kcap : 1) * sizeof(int)), *J = (int *)malloc((kcap > 0 ? kcap : 1) * sizeof(int));
   double *Vh = (double *)malloc((size_t)(nr > 0 ? nr : 1) * (kcap > 0 ? kcap : 1) * sizeof(double));
-  int k = nr > 0 ? or_gca_aca(M, nr, nc, g->eps, I, J, Vh) : 0;
+  int k = nr > 0 ? or_gca_aca(M, nr, nc, g->eps, g->kcap, I, J, Vh) : 0;
   g->rank[c] = k;
   g->piv[c] = (int32_t *)malloc((k > 0 ? k : 1) * sizeof(int32_t));
   for (int a = 0; a < k; ++a) g->piv[c][a] = rows[I[a]];
@@ -1151,15 +1153,16 @@ void or_gca_free(orgca *g) {
 /* Build the GCA-H^2 matrix of the Laplace single-layer operator: trees and
  * blocks as for or_build (R2, R3), nearfield with quadrature order q (R7),
  * Green quadrature order qg, enlargement gamma, triangle rule qt,
- * cross-approximation accuracy eps.  store_S: keep the coupling matrices
- * (else they are evaluated when used).  NULL on invalid arguments. */
+ * cross-approximation accuracy eps, at most kcap pivots per cluster (<= 0:
+ * no cap).  store_S: keep the coupling matrices (else they are evaluated
+ * when used).  NULL on invalid arguments. */
 orgca *or_gca_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf, double eta, int qg,
-                    double eps, double gamma, int qt, int q, int store_near, int store_S) {
+                    double eps, double gamma, int qt, int kcap, int q, int store_near, int store_S) {
   if (qg < 1 || qg > 32 || qt < 1 || qt > 30 || !(eps >= 0.0) || !(gamma > 0.0)) return NULL;
   orh2 *h = or_build(vert, nv, tri, nt, leaf, eta, 1, q, 0, 0.0, store_near, 0);
   if (!h) return NULL;
   orgca *g = (orgca *)calloc(1, sizeof(orgca));
-  g->h = h; g->qg = qg; g->qt = qt; g->eps = eps; g->gamma = gamma;
+  g->h = h; g->qg = qg; g->qt = qt; g->eps = eps; g->gamma = gamma; g->kcap = kcap;
   g->rank = (int *)calloc(h->nclu, sizeof(int));
   g->piv = (int32_t **)calloc(h->nclu, sizeof(int32_t *));
   g->V = (double **)calloc(h->nclu, sizeof(double *));

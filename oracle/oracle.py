@@ -69,7 +69,7 @@ def _load():
     lib.or_threads.restype = C.c_int
     lib.or_gca_build.restype = C.c_void_p
     lib.or_gca_build.argtypes = [dp, C.c_int64, ip32, C.c_int64, C.c_int, C.c_double, C.c_int, C.c_double,
-                                 C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
+                                 C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
     lib.or_gca_free.argtypes = [C.c_void_p]
     lib.or_gca_h2.restype = C.c_void_p
     lib.or_gca_h2.argtypes = [C.c_void_p]
@@ -85,7 +85,8 @@ def _load():
     lib.or_gca_green_rule.restype = C.c_int
     lib.or_gca_green_rule.argtypes = [dp, dp, C.c_double, C.c_int, dp, dp, dp]
     lib.or_gca_aca.restype = C.c_int
-    lib.or_gca_aca.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+    lib.or_gca_aca.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               dp]
     lib.or_set_threads.argtypes = [C.c_int]
     _lib = lib
     return lib
@@ -286,9 +287,10 @@ def green_rule(lo, hi, gamma: float, qg: int):
     return Z, N, W
 
 
-def aca(M, eps: float):
-    """The oracle's cross approximation with complete pivoting of M (nr, nc):
-    row pivots I, column pivots J and V^ = M[:, J] M[I, J]^{-1} (nr, k)."""
+def aca(M, eps: float, max_rank: int = 0):
+    """The oracle's cross approximation with complete pivoting of M (nr, nc),
+    at most max_rank pivots (0: no cap): row pivots I, column pivots J and
+    V^ = M[:, J] M[I, J]^{-1} (nr, k)."""
     lib = _load()
     M = np.ascontiguousarray(M, dtype=np.float64)
     nr, nc = M.shape
@@ -296,7 +298,7 @@ def aca(M, eps: float):
     I = np.zeros(kc, dtype=np.int32)
     J = np.zeros(kc, dtype=np.int32)
     Vh = np.zeros(nr * kc)
-    k = lib.or_gca_aca(_p(M, C.c_double), nr, nc, float(eps), I.ctypes.data_as(C.POINTER(C.c_int)),
+    k = lib.or_gca_aca(_p(M, C.c_double), nr, nc, float(eps), int(max_rank), I.ctypes.data_as(C.POINTER(C.c_int)),
                        J.ctypes.data_as(C.POINTER(C.c_int)), _p(Vh, C.c_double))
     return I[:k].copy(), J[:k].copy(), Vh[:nr * k].reshape(nr, k).copy()
 
@@ -307,7 +309,7 @@ class GcaOracle:
     coupling S = G on the pivot pairs), Laplace kernel."""
 
     def __init__(self, vert, tri, leaf_size=32, eta=2.0, green_order=4, eps=1e-4, gamma=1.0, tri_order=3,
-                 quad_order=3, store_near=True, store_S=True):
+                 max_rank=128, quad_order=3, store_near=True, store_S=True):
         lib = _load()
         self._lib = lib
         self.vert = np.ascontiguousarray(vert, dtype=np.float64)
@@ -315,7 +317,7 @@ class GcaOracle:
         self.n = int(self.tri.shape[0])
         g = lib.or_gca_build(_p(self.vert, C.c_double), self.vert.shape[0], _p(self.tri, C.c_int32), self.n,
                              int(leaf_size), float(eta), int(green_order), float(eps), float(gamma), int(tri_order),
-                             int(quad_order), int(store_near), int(store_S))
+                             int(max_rank), int(quad_order), int(store_near), int(store_S))
         if not g:
             raise ValueError("oracle: invalid arguments")
         self._g = C.c_void_p(g)

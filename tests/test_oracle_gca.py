@@ -85,6 +85,9 @@ def test_aca_recovers_low_rank_exactly():
     i0, j0 = np.unravel_index(np.argmax(np.abs(M)), M.shape)
     assert (Ii[0], J[0]) == (i0, j0)
     assert np.array_equal(Vh[Ii], np.eye(3))
+    # the rank cap stops the approximation early
+    Ii2, J2, Vh2 = oracle.aca(M, 1e-13, max_rank=2)
+    assert len(Ii2) == 2 and np.array_equal(Ii2, Ii[:2]) and np.array_equal(J2, J[:2])
 
 
 def test_aca_ties_and_stopping_rule():
@@ -142,7 +145,7 @@ def _assemble(g):
 
 def test_eps_zero_is_the_galerkin_matrix():
     v, f = I.icosphere(2)
-    g = oracle.GcaOracle(v, f, leaf_size=32, eps=0.0)
+    g = oracle.GcaOracle(v, f, leaf_size=32, eps=0.0, max_rank=0)
     t, s, a = g.blocks()
     tr = g.tree()
     for bt in set(t[a]):

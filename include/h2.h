@@ -122,6 +122,10 @@ typedef struct h2_stats {
   int64_t tensor;         /* 1 if the tensor-core digits of the coupling were built */
   int64_t tensor_near;    /* 1 if the tensor-core digits of the nearfield were built */
   int64_t basis_prec;     /* enum h2_prec of the stored leaf bases V */
+  int64_t gca;            /* 1 for a GCA-H^2 handle (h2_build_gca): then order is the Green
+                           * quadrature order and rank the largest padded rank of a level */
+  int64_t coupling_entries; /* stored coupling entries (interpolation: adm_blocks x rank^2; GCA-H^2:
+                           * the sum over levels of blocks x padded rank^2) */
 } h2_stats;
 
 /* Per right-hand side result of h2_solve. */
@@ -271,7 +275,23 @@ int h2_coefficients(h2_handle h, int which, double *out);
  *                       out[((i 3 + axis) m + j') m + j].
  * Synchronises the handle's stream.  Errors: H2_EINVAL for an unknown item
  * or a range out of bounds. */
-enum h2_export_item { H2_EXPORT_NEAR = 0, H2_EXPORT_COUPLING = 1, H2_EXPORT_V = 2, H2_EXPORT_E = 3 };
+enum h2_export_item {
+  H2_EXPORT_NEAR = 0,
+  H2_EXPORT_COUPLING = 1,
+  H2_EXPORT_V = 2,
+  H2_EXPORT_E = 3,
+  /* GCA-H^2 handles (K = h2_stats.rank, zero padded):
+   *   H2_EXPORT_GCA_S  S_b = G|_{t_0 x s_0} of admissible blocks first .. (h2_plan_blocks'
+   *                    admissible order): out[(i K + a) K + b], a the row pivot of t, b the
+   *                    column pivot of s (h2_gca_pivots' order)
+   *   H2_EXPORT_GCA_V  leaf bases of leaves first ..: out[(i lmax + t) K + a], t in
+   *                    leaf-local cluster order
+   *   H2_EXPORT_GCA_E  transfer matrices of clusters first ..: out[(i K + a) K + b], a a pivot
+   *                    of the cluster, b one of its parent (zero where not built) */
+  H2_EXPORT_GCA_S = 4,
+  H2_EXPORT_GCA_V = 5,
+  H2_EXPORT_GCA_E = 6
+};
 int h2_export(h2_handle h, int what, int64_t first, int64_t count, double *out);
 
 /* Solve G~ z = b by restarted GMRES(restart) per column, z0 = 0, in FP64
@@ -462,6 +482,55 @@ int h2_zmatvec_host(h2_zhandle h, const double *x, double *y, int nrhs);
  * relative residual |b - G~ z| / |b|). */
 int h2_zsolve(h2_zhandle h, const double *b, double *z, int nrhs, double rtol, int restart, int maxit,
               h2_solve_info *info);
+
+/* ---------------------------------------------------------------------------
+ * GCA-H^2 (Section 3, the GCA-H^2 example): an H^2 matrix of the Laplace
+ * single-layer operator whose cluster bases interpolate at pivot elements.
+ * Every cluster tau has pivot triangles tau_0 of tau (a parent's pivots are
+ * chosen among its sons' pivots, so the bases are nested, Eq. (10)), and
+ * every admissible block the coupling matrix S_{tau sigma} =
+ * G|_{tau_0 x sigma_0}, the Galerkin matrix on the pivot pairs (Eq. (3),
+ * the nearfield's regular quadrature).  The section states only this; the
+ * pivots come from the cited Green cross approximation:
+ *   - a quadrature rule on the boundary of the cluster's box enlarged by
+ *     gamma times its half diagonal (green_order Gauss nodes per direction on
+ *     each face) gives a surrogate of the cluster's rows: for every candidate
+ *     triangle the weighted integrals of g(x, z) and of its normal derivative
+ *     in z at every quadrature point z (Green's representation formula),
+ *     each by the collapsed Gauss rule with tri_order nodes per direction;
+ *   - cross approximation with complete pivoting of the surrogate to the
+ *     relative accuracy eps (at most max_rank pivots) picks the pivot rows;
+ *     ties (within a relative 2^-30) go to the first entry in row-major order;
+ *   - the interpolation operator V^ = M[:, J] M[I, J]^{-1} (pivot rows exactly
+ *     unit vectors) is the leaf basis V of a leaf, and splits into the
+ *     transfer matrices E of the sons for a parent, whose candidates are its
+ *     first son's pivots followed by its second son's.
+ * The trees, blocks (eta) and nearfield are those of h2_build.  The product,
+ * solvers and graphs take GCA-H^2 handles like any other (h2_matvec,
+ * h2_matvec_acc, h2_matvec_host, h2_matvec_noalloc, h2_solve, h2_solve_ir,
+ * h2_graph_*, h2_serve_*); h2_batch_* and h2_coefficients do not.
+ * ------------------------------------------------------------------------- */
+typedef struct h2_gca_options {
+  double eps;        /* relative accuracy of the cross approximation; default 1e-4, in [0, 1) */
+  double gamma;      /* enlargement of the auxiliary box in half diagonals; default 1, > 0 */
+  int green_order;   /* Gauss nodes per direction on each face; default 4, in [1, 8] */
+  int tri_order;     /* collapsed Gauss nodes per direction on a triangle; default 3, in [1, 16] */
+  int max_rank;      /* pivots per cluster at most; default 128, in [4, 128] */
+  int reserved[5];   /* must be zero */
+} h2_gca_options;
+int h2_gca_options_default(h2_gca_options *g);
+/* Build a GCA-H^2 matrix.  Arguments as for h2_build (no order); gopt NULL =
+ * defaults; opt->prec one of H2_F64, H2_F64_NATIVE, H2_F32 and opt->coupling
+ * AUTO or STORED (H2_EINVAL otherwise).  Pivots, bases, transfer and
+ * coupling matrices are computed on the device (FP64), for the levels from
+ * the leaves up to the first level with an admissible block. */
+int h2_build_gca(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta,
+                 const h2_gca_options *gopt, const h2_options *opt, h2_handle *out);
+/* Ranks and pivots of a GCA-H^2 handle: rank[clusters] (0 above the first
+ * admissible level), pivots[c * cap + a] = triangle index (caller's order) of
+ * pivot a of cluster c in pivot order, -1 beyond the rank; cap >= h2_stats.rank.
+ * Either output may be NULL. */
+int h2_gca_pivots(h2_handle h, int32_t *rank, int32_t *pivots, int64_t cap);
 
 /* ---------------------------------------------------------------------------
  * Failure injection and self-tests of the error paths (no counterpart in the

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libh2.so")
-SOURCES = ["h2_plan.cpp", "h2_api.cpp", "h2_serve.cpp", "h2_setup.cu", "h2_matvec.cu", "h2_solve.cu",
+SOURCES = ["h2_plan.cpp", "h2_api.cpp", "h2_serve.cpp", "h2_setup.cu", "h2_matvec.cu", "h2_solve.cu", "h2_gca.cu",
            "h2_noalloc.cu", "h2_batch.cu", "h2_tc.cu", "h2_helmholtz.cu"]
 HEADERS = ["h2_internal.hpp", "h2_dd.cuh", "h2_ptx.cuh", "h2_transfer.cuh", "h2_digits.hpp", "h2_kernel.cuh", os.path.join("..", "..", "include", "h2.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -38,7 +38,12 @@ class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("n", "depth", "clusters", "leaf_max", "order", "rank", "adm_blocks", "near_blocks",
                  "near_entries", "first_adm_level", "device_bytes", "prec", "coupling", "tensor",
-                 "tensor_near", "basis_prec")]
+                 "tensor_near", "basis_prec", "gca", "coupling_entries")]
+
+
+class GcaOptions(C.Structure):
+    _fields_ = [("eps", C.c_double), ("gamma", C.c_double), ("green_order", C.c_int), ("tri_order", C.c_int),
+                ("max_rank", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class SolveInfo(C.Structure):
@@ -53,7 +58,7 @@ EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_
             "h2_batch_tune", "h2_batch_set_shapes", "h2_batch_profile", "h2_batch_phase_times", "h2_batch_info",
             "h2_batch_sync", "h2_batch_destroy", "h2_graph_create", "h2_graph_launch", "h2_graph_destroy",
             "h2_inject_alloc_failure", "h2_wait_selftest", "h2_export", "h2_build_times",
-            "h2_zbuild", "h2_zdestroy", "h2_zpart", "h2_zinfo", "h2_zmatvec", "h2_zmatvec_host", "h2_zsolve", "h2_last_error"]
+            "h2_gca_options_default", "h2_build_gca", "h2_gca_pivots", "h2_zbuild", "h2_zdestroy", "h2_zpart", "h2_zinfo", "h2_zmatvec", "h2_zmatvec_host", "h2_zsolve", "h2_last_error"]
 PHASES = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_near", "permute_out"]
 
 
@@ -126,6 +131,10 @@ def load():
             "h2_zmatvec_host": (C.c_int, [vp, dp, dp, C.c_int]),
             "h2_zsolve": (C.c_int, [vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(SolveInfo)]),
             "h2_wait_selftest": (C.c_int, [vp, C.c_int, C.c_uint32, C.POINTER(C.c_int)]),
+            "h2_gca_options_default": (C.c_int, [C.POINTER(GcaOptions)]),
+            "h2_build_gca": (C.c_int, [dp, C.c_int64, i32p, C.c_int64, C.c_int, C.c_double, C.POINTER(GcaOptions),
+                                       C.POINTER(Options), C.POINTER(vp)]),
+            "h2_gca_pivots": (C.c_int, [vp, i32p, i32p, C.c_int64]),
             "h2_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -212,7 +221,7 @@ class H2Matrix:
     """An H² matrix of one mesh on one GPU (see include/h2.h)."""
 
     def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, prec="f64", quad_order=3, device=0,
-                 stream=None, coupling="auto", tensor="auto", basis=None):
+                 stream=None, coupling="auto", tensor="auto", basis=None, gca=None):
         lib = load()
         v, t = _mesh(vert, tri)
         opt = Options()
@@ -225,8 +234,16 @@ class H2Matrix:
         opt.tensor = {"auto": 0, "off": 1}[tensor]
         opt.basis_prec = 0 if basis is None else PREC[basis]
         h = C.c_void_p()
-        _check(lib.h2_build(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
-                            int(leaf_size), float(eta), int(order), C.byref(opt), C.byref(h)))
+        if gca is None:
+            _check(lib.h2_build(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
+                                int(leaf_size), float(eta), int(order), C.byref(opt), C.byref(h)))
+        else:
+            g = GcaOptions()
+            _check(lib.h2_gca_options_default(C.byref(g)))
+            for key, val in gca.items():
+                setattr(g, key, val)
+            _check(lib.h2_build_gca(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],
+                                    int(leaf_size), float(eta), C.byref(g), C.byref(opt), C.byref(h)))
         self._h = h
         self._lib = lib
         self.prec = prec
@@ -343,6 +360,28 @@ class H2Matrix:
         out = np.zeros((count,) + shape)
         _check(self._lib.h2_export(self._h, item, int(first), int(count), _dp(out)))
         return out
+
+    def export_gca(self, what, first=0, count=None):
+        """GCA-H^2 items of h2_export as float64 (K = stats["rank"], zero padded):
+        what = "S" (count, K, K) over admissible blocks, "V" (count, lmax, K)
+        over leaves, "E" (count, K, K) over clusters."""
+        st = self.stats
+        L, K = st["leaf_max"], st["rank"]
+        item, total, shape = {"S": (4, st["adm_blocks"], (K, K)), "V": (5, 2 ** st["depth"], (L, K)),
+                              "E": (6, st["clusters"], (K, K))}[what]
+        count = total - first if count is None else count
+        out = np.zeros((count,) + shape)
+        _check(self._lib.h2_export(self._h, item, int(first), int(count), _dp(out)))
+        return out
+
+    def gca_pivots(self):
+        """(rank[clusters], pivots[clusters][K]) of a GCA-H^2 handle, -1 beyond the rank."""
+        nc, K = self.stats["clusters"], self.stats["rank"]
+        rank = np.zeros(nc, dtype=np.int32)
+        piv = np.zeros((nc, K), dtype=np.int32)
+        _check(self._lib.h2_gca_pivots(self._h, rank.ctypes.data_as(C.POINTER(C.c_int32)),
+                                       piv.ctypes.data_as(C.POINTER(C.c_int32)), int(K)))
+        return rank, piv
 
     def coefficients(self, which, nrhs):
         out = np.zeros((self.stats["clusters"], self.stats["rank"], nrhs))
@@ -623,3 +662,16 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+class GcaMatrix(H2Matrix):
+    """A GCA-H^2 matrix (Section 3's GCA-H^2 example; h2_build_gca): pivot
+    bases from cross approximation of a Green-quadrature surrogate, coupling
+    S = G on the pivot pairs.  Products, solves and graphs as for H2Matrix."""
+
+    def __init__(self, vert, tri, leaf_size=32, eta=2.0, eps=1e-4, green_order=4, gamma=1.0, tri_order=3,
+                 max_rank=128, prec="f64", quad_order=3, device=0, stream=None, tensor="auto"):
+        super().__init__(vert, tri, leaf_size=leaf_size, eta=eta, order=1, prec=prec, quad_order=quad_order,
+                         device=device, stream=stream, coupling="auto", tensor=tensor,
+                         gca=dict(eps=float(eps), gamma=float(gamma), green_order=int(green_order),
+                                  tri_order=int(tri_order), max_rank=int(max_rank)))

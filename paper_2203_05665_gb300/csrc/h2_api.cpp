@@ -47,6 +47,11 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 static void free_dev(Dev &d) {
+  for (int l = 0; l < kMaxLevels; ++l)
+    for (void *p : {d.gS[l], d.gE[l], d.gEt[l]})
+      if (p) cudaFree(p);
+  if (d.grank) cudaFree(d.grank);
+  if (d.gpiv) cudaFree(d.gpiv);
   void *ptrs[] = {d.Ntc, d.xnt, d.ntc_E, d.ntc_xmax, d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.colmax, d.nself, d.near_ptr2, d.self_ptr, d.near_col2, d.near_blk2, d.self_col, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
                   d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
   for (void *p : ptrs)
@@ -78,7 +83,7 @@ static int check_double_float_range(const Plan &p) {
 
 // h2_build with a given kernel (Section 1: Laplace, or a part of Helmholtz)
 int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
-                 const h2_options *opt, KernelFn kf, h2_handle *out) {
+                 const h2_options *opt, KernelFn kf, h2_handle *out, const GcaParams *gca) {
   if (!out) return fail(H2_EINVAL, "out is NULL");
   *out = nullptr;
   h2_options o;
@@ -99,6 +104,10 @@ int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt,
     if (o.basis_prec != H2_F32 && o.basis_prec != o.prec)
       return fail(H2_EINVAL, "basis_prec must be 0, H2_F32 or the handle's own 16-bit precision");
   }
+  if (gca) {
+    if (half_prec) return fail(H2_EINVAL, "GCA-H^2 handles support H2_F64, H2_F64_NATIVE and H2_F32");
+    if (o.coupling == H2_COUPLING_REGEN) return fail(H2_EINVAL, "GCA-H^2 handles store their coupling matrices");
+  }
   int ndev = 0;
   H2_CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (o.device < 0 || o.device >= ndev) return fail(H2_EINVAL, "device ordinal out of range");
@@ -114,6 +123,11 @@ int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt,
   // FP32 leaf bases: explicitly, or by default under bfloat16 storage
   c->d.v32 = half_prec && (o.basis_prec == H2_F32 || (o.basis_prec == 0 && o.prec == H2_BF16));
   c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);
+  if (gca) {
+    c->gp = *gca;
+    c->d.gca = true;
+    c->d.coupling = 0;
+  }
   int rc;
   const auto t0 = std::chrono::steady_clock::now();
   auto ms = [](std::chrono::steady_clock::time_point a) {
@@ -242,6 +256,51 @@ int h2_build(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int
   return build_handle(vert, nv, tri, nt, leaf_size, eta, order, opt, KernelFn{kKernelLaplace, 0.0}, out);
 }
 
+int h2_gca_options_default(h2_gca_options *g) {
+  if (!g) return fail(H2_EINVAL, "NULL argument");
+  std::memset(g, 0, sizeof(*g));
+  const GcaParams d;
+  g->eps = d.eps;
+  g->gamma = d.gamma;
+  g->green_order = d.green_order;
+  g->tri_order = d.tri_order;
+  g->max_rank = d.max_rank;
+  return H2_OK;
+}
+
+int h2_build_gca(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta,
+                 const h2_gca_options *gopt, const h2_options *opt, h2_handle *out) {
+  GcaParams gp;
+  if (gopt) {
+    for (int r : gopt->reserved)
+      if (r) return fail(H2_EINVAL, "reserved GCA option fields must be zero");
+    gp.eps = gopt->eps;
+    gp.gamma = gopt->gamma;
+    gp.green_order = gopt->green_order;
+    gp.tri_order = gopt->tri_order;
+    gp.max_rank = gopt->max_rank;
+  }
+  return build_handle(vert, nv, tri, nt, leaf_size, eta, 1, opt, KernelFn{kKernelLaplace, 0.0}, out, &gp);
+}
+
+int h2_gca_pivots(h2_handle h, int32_t *rank, int32_t *pivots, int64_t cap) {
+  if (!h) return fail(H2_EINVAL, "NULL handle");
+  if (!h->d.gca) return fail(H2_EINVAL, "not a GCA-H^2 handle");
+  const Dev &d = h->d;
+  if (pivots && cap < d.k) return fail(H2_EINVAL, "cap must be at least the handle's rank (h2_stats.rank)");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  std::vector<int32_t> r(d.nclu), pv((size_t)d.nclu * d.gkcap);
+  H2_CUDA_TRY(cudaMemcpy(r.data(), d.grank, d.nclu * 4, cudaMemcpyDeviceToHost));
+  if (rank) std::memcpy(rank, r.data(), d.nclu * 4);
+  if (pivots) {
+    H2_CUDA_TRY(cudaMemcpy(pv.data(), d.gpiv, pv.size() * 4, cudaMemcpyDeviceToHost));
+    for (int64_t c = 0; c < d.nclu; ++c)
+      for (int64_t a = 0; a < cap; ++a) pivots[c * cap + a] = a < r[c] ? pv[c * d.gkcap + a] : -1;
+  }
+  return H2_OK;
+}
+
 static void drop_events(Prof &p) {
   for (auto e : p.ev) cudaEventDestroy(e);
   p.ev.clear();
@@ -278,6 +337,12 @@ int h2_info(h2_handle h, h2_stats *out) {
   out->tensor = h->d.tc ? 1 : 0;
   out->tensor_near = h->d.ntc ? 1 : 0;
   out->basis_prec = h->d.v32 ? H2_F32 : h->d.prec;
+  out->gca = h->d.gca ? 1 : 0;
+  out->coupling_entries = h->d.gca ? h->d.coupling_entries : (int64_t)p.adm_col.size() * p.k * p.k;
+  if (h->d.gca) {
+    out->order = h->gp.green_order;
+    out->rank = h->d.k;
+  }
   return H2_OK;
 }
 
@@ -446,6 +511,7 @@ int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs) {
 
 int h2_coefficients(h2_handle h, int which, double *out) {
   if (!h || !out || (which != 0 && which != 1)) return fail(H2_EINVAL, "bad argument");
+  if (h->d.gca) return fail(H2_EINVAL, "GCA-H^2 handles have per-level ranks; use h2_export");
   if (h->d.last_nrhs < 1) return fail(H2_EINVAL, "no product has run on this handle");
   H2_CUDA_TRY(cudaSetDevice(h->device));
   H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -583,6 +649,7 @@ int h2_export(h2_handle h, int what, int64_t first, int64_t count, double *out) 
       return H2_OK;
     }
     case H2_EXPORT_COUPLING: {
+      if (d.gca) return fail(H2_EINVAL, "GCA-H^2 handles: use H2_EXPORT_GCA_S");
       if (!d.S) return fail(H2_EINVAL, "the coupling matrices are regenerated, not stored");
       if (first + count > d.nadm) return fail(H2_EINVAL, "admissible block range out of bounds");
       if ((rc = fetch(d.S, stored_size(ts), first, count, k * kp, buf))) return rc;
@@ -593,6 +660,7 @@ int h2_export(h2_handle h, int what, int64_t first, int64_t count, double *out) 
       return H2_OK;
     }
     case H2_EXPORT_V: {
+      if (d.gca) return fail(H2_EINVAL, "GCA-H^2 handles: use H2_EXPORT_GCA_V");
       if (first + count > d.npad) return fail(H2_EINVAL, "padded DoF range out of bounds");
       const int tv = d.v32 ? ST_F32 : ts;
       if ((rc = fetch(d.V, stored_size(tv), first, count, kp, buf))) return rc;
@@ -609,10 +677,54 @@ int h2_export(h2_handle h, int what, int64_t first, int64_t count, double *out) 
       return H2_OK;
     }
     case H2_EXPORT_E: {
+      if (d.gca) return fail(H2_EINVAL, "GCA-H^2 handles: use H2_EXPORT_GCA_E");
       if (first + count > d.nclu) return fail(H2_EINVAL, "cluster range out of bounds");
       const int te = (d.prec == H2_BF16 || d.v32) ? ST_F32 : ts;
       if ((rc = fetch(d.Ef, stored_size(te), first, count, 3 * m * m, buf))) return rc;
       for (int64_t i = 0; i < count * 3 * m * m; ++i) out[i] = stored_value(buf.data() + i * stored_size(te), te);
+      return H2_OK;
+    }
+    case H2_EXPORT_GCA_S:
+    case H2_EXPORT_GCA_V:
+    case H2_EXPORT_GCA_E: {
+      if (!d.gca) return fail(H2_EINVAL, "not a GCA-H^2 handle");
+      const int64_t K = d.k;
+      const int64_t lim = what == H2_EXPORT_GCA_S ? d.nadm : what == H2_EXPORT_GCA_V ? d.nleaf : d.nclu;
+      if (first + count > lim) return fail(H2_EINVAL, "export range out of bounds");
+      const size_t es = stored_size(ts);
+      auto level_of = [](int64_t c) {
+        int l = 0;
+        while (((int64_t)2 << l) - 1 <= c) ++l;
+        return l;
+      };
+      for (int64_t i = 0; i < count; ++i) {
+        double *o = out + i * (what == H2_EXPORT_GCA_V ? L * K : K * K);
+        std::fill(o, o + (what == H2_EXPORT_GCA_V ? L * K : K * K), 0.0);
+        if (what == H2_EXPORT_GCA_S) {
+          const int64_t b = first + i;
+          const int64_t t = std::upper_bound(p.adm_ptr.begin(), p.adm_ptr.end(), b) - p.adm_ptr.begin() - 1;
+          const int l = level_of(t);
+          const int64_t Kl = d.gK[l], bl = b - p.adm_ptr[((int64_t)1 << l) - 1];
+          if ((rc = fetch(d.gS[l], es, bl, 1, Kl * Kl, buf))) return rc;
+          for (int64_t mu = 0; mu < Kl; ++mu)
+            for (int64_t nu = 0; nu < Kl; ++nu) o[nu * K + mu] = stored_value(buf.data() + (mu * Kl + nu) * es, ts);
+        } else if (what == H2_EXPORT_GCA_V) {
+          const int64_t KD = d.gK[d.depth];
+          if (KD == 0) continue;
+          if ((rc = fetch(d.V, es, first + i, 1, L * KD, buf))) return rc;
+          for (int64_t t = 0; t < L; ++t)
+            for (int64_t a = 0; a < KD; ++a) o[t * K + a] = stored_value(buf.data() + (t * KD + a) * es, ts);
+        } else {
+          const int64_t c = first + i;
+          if (c == 0) continue;
+          const int l = level_of(c);
+          if (!d.gE[l]) continue;
+          const int64_t Kc = d.gK[l], Kq = d.gK[l - 1];
+          if ((rc = fetch(d.gE[l], es, c - (((int64_t)1 << l) - 1), 1, Kc * Kq, buf))) return rc;
+          for (int64_t a = 0; a < Kc; ++a)
+            for (int64_t b = 0; b < Kq; ++b) o[a * K + b] = stored_value(buf.data() + (a * Kq + b) * es, ts);
+        }
+      }
       return H2_OK;
     }
     default: return fail(H2_EINVAL, "unknown export item");

@@ -693,6 +693,7 @@ int h2_batch_create(const h2_handle *hs, int nprob, const int *nrhs, void *strea
     const h2_ctx *h = hs[p];
     if (!h) return fail(H2_EINVAL, "NULL handle in the batch");
     if (h->d.prec != H2_F32) return fail(H2_EINVAL, "batched products need H2_F32 handles");
+    if (h->d.gca) return fail(H2_EINVAL, "batched products need interpolation handles (not GCA-H^2)");
     if (h->d.coupling != 0) return fail(H2_EINVAL, "batched products need stored coupling matrices");
     if (h->d.k > kBatchMaxRows || h->d.lmax > kBatchMaxRows)
       return fail(H2_EINVAL, "batched products need rank k <= 64 (order <= 4) and leaves of at most 64 triangles");

@@ -74,6 +74,14 @@ struct Plan {
 int make_plan(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
               bool with_bases, Plan &p);
 
+constexpr int kMaxLevels = 40;
+
+// Parameters of the GCA-H^2 construction (h2_build_gca)
+struct GcaParams {
+  double eps = 1e-4, gamma = 1.0;
+  int green_order = 4, tri_order = 3, max_rank = 128;
+};
+
 // Device representation of one H^2 matrix.
 struct Dev {
   int prec = H2_F64;
@@ -129,6 +137,22 @@ struct Dev {
   float *nself = nullptr;
   int64_t *near_ptr2 = nullptr, *self_ptr = nullptr;
   int32_t *near_col2 = nullptr, *near_blk2 = nullptr, *self_col = nullptr;
+  // GCA-H^2 (Section 3's GCA-H^2 example): the rank and the pivot triangles
+  // of every cluster (gpiv [clusters][gkcap], pivot order), per tree level l
+  // the padded rank gK[l] (a multiple of 4; 0 above the first admissible
+  // level), the coupling matrices of the level's admissible blocks (gS[l]:
+  // [block][K_l][K_l], S_b stored transposed [mu][nu]), the transfer
+  // matrices E_c of the level's clusters (gE[l]: [c][K_l][K_{l-1}]) and their
+  // transposes (gEt[l]: [c][K_{l-1}][K_l]), and the offset of the level's
+  // coefficients in units of rp values (gX[l]); k is the largest gK.  The
+  // leaf bases use V and Vt with kp = gK[depth]; the nearfield is the same.
+  bool gca = false;
+  int gK[kMaxLevels] = {0};
+  int64_t gX[kMaxLevels] = {0};
+  void *gS[kMaxLevels] = {nullptr}, *gE[kMaxLevels] = {nullptr}, *gEt[kMaxLevels] = {nullptr};
+  int gkcap = 0;
+  int32_t *grank = nullptr, *gpiv = nullptr;
+  int64_t coupling_entries = 0;  // stored coupling entries (padded; GCA handles)
   // work buffers for up to cap_nrhs right-hand sides
   int cap_nrhs = 0;
   void *xpad = nullptr, *ypad = nullptr, *xhat = nullptr, *yhat = nullptr;
@@ -163,6 +187,7 @@ void free_gmres_work(GmresWork &w);
 
 struct Ctx {
   double build_ms[H2_NBUILD] = {0};   // wall time of the build phases (h2_build_times)
+  GcaParams gp;                       // GCA-H^2 handles: construction parameters
   GmresWork gw;
   Prof prof;
   int device = 0;
@@ -202,7 +227,7 @@ int ntc_near(Ctx &c, const void *xpad, void *ypad, int rp, int accumulate, int64
 
 // h2_build for a given kernel (h2_api.cpp)
 int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,
-                 const h2_options *opt, KernelFn kf, h2_handle *out);
+                 const h2_options *opt, KernelFn kf, h2_handle *out, const GcaParams *gca = nullptr);
 
 // device allocation helper (tracks bytes)
 int dev_alloc(Dev &d, void **ptr, size_t bytes);
@@ -210,6 +235,9 @@ int ensure_work(Ctx &c, int nrhs);
 
 // build steps on the device (h2_setup.cu)
 int device_build(Ctx &c);
+// GCA-H^2 pivots, leaf bases, transfer and coupling matrices on the device
+// (h2_gca.cu); vert, tri, area: the mesh on the device
+int gca_build(Ctx &c, const double *vert, const int32_t *tri, const double *area);
 // y = G~ x with device arrays of the handle's precision (h2_matvec.cu);
 // if x64/y64 are given instead the product reads/writes FP64 arrays.
 // Threads per CTA of a transfer launch (one CTA per parent) at tree level l:

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <type_traits>
 
 #include "h2_dd.cuh"
@@ -387,6 +388,155 @@ struct NearRows {
     return Term<TS, TC>{near + block(e) * (int64_t)L * Lp, xpad + (int64_t)col[e] * L * rp, L};
   }
 };
+
+// GCA-H^2 coupling at one tree level (Algorithm 3 with the pivot bases):
+// row r = cluster c0 + r, terms S_b x^_s over the admissible blocks b of
+// the row; the level's coupling matrices are stored consecutively from its
+// first block ([K][K], S_b transposed) and its coefficients from its first
+// cluster ([c - c0][K][rp]).
+template <class TS, class TC>
+struct GcaCouplingRows {
+  static constexpr bool kGen = false;
+  const TS *S;
+  const int64_t *ptr;
+  const int32_t *col;
+  const TC *xhat;
+  int K, rp;
+  int64_t c0;
+  __device__ int kdim(int64_t) const { return K; }
+  __device__ void meta(int64_t, float *mt) const { mt[0] = 1.0f; }
+  __device__ int64_t first(int64_t r) const { return ptr[c0 + r] - ptr[c0]; }
+  __device__ Term<TS, TC> term(int64_t e) const {
+    const int64_t b = ptr[c0] + e;
+    return Term<TS, TC>{S + e * (int64_t)K * K, xhat + (int64_t)(col[b] - c0) * K * rp, K};
+  }
+};
+
+// GCA-H^2 upward step (Algorithm 1): row r = parent r of level l - 1, terms
+// E_s^T x^_s over its two sons s (sons 2r, 2r + 1 of level l, E_s stored
+// [Kc][Kp]: the son's index is the contraction index).
+template <class TS, class TC>
+struct GcaUpRows {
+  static constexpr bool kGen = false;
+  const TS *E;
+  const TC *xs;
+  int Kc, Kp, rp;
+  __device__ int kdim(int64_t) const { return Kc; }
+  __device__ void meta(int64_t, float *mt) const { mt[0] = 1.0f; }
+  __device__ int64_t first(int64_t r) const { return 2 * r; }
+  __device__ Term<TS, TC> term(int64_t e) const {
+    return Term<TS, TC>{E + e * (int64_t)Kc * Kp, xs + e * (int64_t)Kc * rp, Kc};
+  }
+};
+
+// GCA-H^2 downward step (Algorithm 2): row r = son r of level l, one term
+// E_r y^_parent (E_r stored transposed [Kp][Kc]); added to the son's y^.
+template <class TS, class TC>
+struct GcaDownRows {
+  static constexpr bool kGen = false;
+  const TS *Et;
+  const TC *yp;
+  int Kc, Kp, rp;
+  __device__ int kdim(int64_t) const { return Kp; }
+  __device__ void meta(int64_t, float *mt) const { mt[0] = 1.0f; }
+  __device__ int64_t first(int64_t r) const { return r; }
+  __device__ Term<TS, TC> term(int64_t e) const {
+    return Term<TS, TC>{Et + e * (int64_t)Kp * Kc, yp + (e >> 1) * (int64_t)Kp * rp, Kp};
+  }
+};
+
+// Block rows with small tiles (the GCA-H^2 coupling and transfer steps): one
+// warp per row, out_r (M x rp) = sum over the row's terms of A X (A stored
+// [K][Mp], rows padded to Mp, X [K][rp]).  The warp stages the tiles of a
+// term in its own two shared-memory buffers with 16-byte asynchronous
+// copies, the next term's copies in flight while it multiplies the current
+// one.  A lane owns up to TPL register tiles of 4 rows x one 16-byte group
+// of columns (tile q of the row: rows 4 (q mod Mp/4) .., column group
+// q div (Mp/4)); every output is summed by one lane in a fixed order, so
+// results are reproducible.  No waits on other threads beyond the warp's
+// own copies.
+template <class TS, class TC, int TPL, class Rows>
+__global__ void __launch_bounds__(128) k_rows_warp(Rows rows, int M, int Mp, int rp, int Kmax, int64_t nrows,
+                                                   int accumulate, TC *__restrict__ out) {
+  using XV = typename Vec16<TC>::V;
+  constexpr int VN = Vec16<TC>::N;
+  extern __shared__ __align__(16) unsigned char rwsm[];
+  const int ln = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint32_t abytes = (uint32_t)((sizeof(TS) * Kmax * Mp + 15) / 16 * 16);
+  const uint32_t xbytes = (uint32_t)((sizeof(TC) * Kmax * rp + 15) / 16 * 16);
+  unsigned char *buf = rwsm + (size_t)wib * 2 * (abytes + xbytes);
+  const int nvg = Mp / 4, tiles = nvg * (rp / VN);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib; r < nrows; r += nw) {
+    TC acc[TPL][4][VN];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < VN; ++c) acc[t][a][c] = zero_of<TC>();
+    const int64_t e0 = rows.first(r), e1 = rows.first(r + 1);
+    auto issue = [&](int64_t e) {
+      unsigned char *st = buf + (size_t)((e - e0) & 1) * (abytes + xbytes);
+      const Term<TS, TC> tm = rows.term(e);
+      const uint32_t ab = (uint32_t)(sizeof(TS) * tm.K * Mp), xb = (uint32_t)(sizeof(TC) * tm.K * rp);
+      const unsigned char *sa = reinterpret_cast<const unsigned char *>(tm.A);
+      const unsigned char *sx = reinterpret_cast<const unsigned char *>(tm.X);
+      for (uint32_t o = 16 * ln; o < ab; o += 16 * 32) cp_async16(st + o, sa + o);
+      for (uint32_t o = 16 * ln; o < xb; o += 16 * 32) cp_async16(st + abytes + o, sx + o);
+      cp_async_commit();
+    };
+    if (e0 < e1) issue(e0);
+    for (int64_t e = e0; e < e1; ++e) {
+      if (e + 1 < e1) {
+        issue(e + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      const unsigned char *st = buf + (size_t)((e - e0) & 1) * (abytes + xbytes);
+      const TS *sA = reinterpret_cast<const TS *>(st);
+      const TC *sX = reinterpret_cast<const TC *>(st + abytes);
+      const int K = rows.kdim(e);
+#pragma unroll
+      for (int t = 0; t < TPL; ++t) {
+        const int q = ln + 32 * t;
+        if (q < tiles) {
+          const int g = q % nvg, cg = q / nvg;
+          for (int mu = 0; mu < K; ++mu) {
+            TC av[4];
+            load4<TS, TC>(sA + mu * Mp + 4 * g, av);
+            const XV xv = *reinterpret_cast<const XV *>(sX + mu * rp + VN * cg);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int c = 0; c < VN; ++c) acc_fma(acc[t][a][c], av[a], lane<TC>(xv, c));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    TC *o = out + r * (int64_t)M * rp;
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int q = ln + 32 * t;
+      if (q < tiles) {
+        const int g = q % nvg, cg = q / nvg;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < VN; ++c) {
+            acc_norm(acc[t][a][c]);
+            if (4 * g + a < M) {
+              TC *dst = o + (int64_t)(4 * g + a) * rp + VN * cg + c;
+              *dst = accumulate ? *dst + acc[t][a][c] : acc[t][a][c];
+            }
+          }
+      }
+    }
+  }
+}
 
 // Block-row product, persistent and warp-specialised: output tile out_r
 // (M x rp) = sum over the terms of row r of A X.  Each CTA takes a contiguous
@@ -1083,6 +1233,146 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   return H2_OK;
 }
 
+// One block-row launch over nrows rows with output tiles of M rows (A rows
+// padded to Mp) whose terms contract over at most Kmax: the warp-per-row
+// kernel when warp is set, its lane tiles fit the registers and two buffers
+// of four warps fit shared memory, else the pipelined block-row kernel.
+template <class TS, class T, class Rows>
+int gca_rows_launch(const Rows &rows, int M, int Mp, int Kmax, int rp, int64_t nrows, int accumulate, T *out,
+                    cudaStream_t st, bool warp) {
+  if (nrows <= 0) return H2_OK;
+  if (warp) {
+    constexpr int VN = Vec16<T>::N;
+    const int tiles = (Mp / 4) * (rp / VN);
+    const size_t per_warp = 2 * ((sizeof(TS) * Kmax * Mp + 15) / 16 * 16 + (sizeof(T) * Kmax * rp + 15) / 16 * 16);
+    if (Mp % 4 == 0 && tiles <= 32 * 4 && 4 * per_warp <= kSmemMax) {
+      const size_t sm = 4 * per_warp;
+      int dev = 0, sms = 0, per_sm = 0;
+      H2_CUDA_TRY(cudaGetDevice(&dev));
+      H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      auto go = [&](auto kern) -> int {
+        if (sm > 48 * 1024)
+          H2_CUDA_TRY(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kSmemMax));
+        H2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sm));
+        if (per_sm < 1) return fail(H2_EINVAL, "warp block-row kernel cannot be resident");
+        const int64_t grid = std::min<int64_t>((nrows + 3) / 4, (int64_t)per_sm * sms);
+        kern<<<(unsigned)grid, 128, sm, st>>>(rows, M, Mp, rp, Kmax, nrows, accumulate, out);
+        return H2_OK;
+      };
+      if (tiles <= 32) return go(k_rows_warp<TS, T, 1, Rows>);
+      if (tiles <= 64) return go(k_rows_warp<TS, T, 2, Rows>);
+      return go(k_rows_warp<TS, T, 4, Rows>);
+    }
+  }
+  const int R = row_groups<T>(Mp);
+  const int threads = row_threads(Mp, rp, Kmax, sizeof(T), R);
+  RowCfg cfg{};
+  int rc;
+  if ((rc = row_cfg<TS, T>(M, Mp, rp, Kmax, threads, R, false, cfg))) return rc;
+  return launch_rows<TS, T>(rows, cfg, threads, R, nrows, accumulate, out, st);
+}
+
+// y = G~ x with a GCA-H^2 matrix (Algorithms 1-3 with the pivot bases):
+// the same permutations, leaf steps and nearfield as the interpolation
+// product, the transfer and coupling steps level by level with the level's
+// padded rank.  Coefficients of level l start at gX[l] * rp.
+template <class TS, class T, class Tio>
+int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  const int L = (int)d.lmax, Lp = (int)d.lp, D = d.depth, lmin = d.first_adm_level;
+  const int rp = padded_rhs(nrhs, sizeof(T));
+  T *xpad = (T *)d.xpad, *ypad = (T *)d.ypad, *xhat = (T *)d.xhat, *yhat = (T *)d.yhat;
+  const bool far = lmin <= D;
+  int rc;
+  Marks mk(c);
+  mk.mark(H2_PH_PERMUTE_IN);
+  const unsigned long long *cmx = std::is_same<T, dd>::value ? d.colmax : nullptr;
+  if (cmx) {
+    H2_CUDA_TRY(cudaMemsetAsync(d.colmax, 0, sizeof(unsigned long long) * nrhs, st));
+    const int64_t nb = std::min<int64_t>((d.n + 8 * kThreads - 1) / (8 * kThreads), 64);
+    k_colmax<Tio><<<dim3((unsigned)std::max<int64_t>(nb, 1), nrhs), kThreads, 0, st>>>(x, d.n, d.colmax);
+    mk.count(H2_PH_PERMUTE_IN);
+  }
+  const unsigned perm_grid = (unsigned)((d.npad + kPermRows - 1) / kPermRows);
+  k_permute_in<Tio, T><<<perm_grid, 256, (size_t)kPermRows * (rp + 1) * sizeof(T), st>>>(x, d.n, nrhs, rp, d.pad_src,
+                                                                                        d.npad, cmx, xpad);
+  mk.count(H2_PH_PERMUTE_IN);
+  auto X = [&](T *base, int l) { return base + d.gX[l] * rp; };
+  static const bool wk = [] {
+    const char *e = std::getenv("H2_GCA_WARP");
+    return !(e && e[0] == '0');
+  }();
+  const int KD = d.gK[D];
+  const bool leaf_reg = L <= 32 && KD <= 64 && rp <= 16;
+  mk.mark(H2_PH_LEAF_FORWARD);
+  if (far && leaf_reg) {
+    const size_t sm = (size_t)L * (KD + rp) * sizeof(T);
+    k_leaf_fwd_reg<TS, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TS *)d.V, xpad, nullptr, L, KD, KD, rp,
+                                                             X(xhat, D));
+    mk.count(H2_PH_LEAF_FORWARD);
+  } else if (far) {
+    LeafForwardRows<TS, T> rows{(const TS *)d.V, xpad, nullptr, L, KD, rp};
+    if ((rc = gca_rows_launch<TS, T>(rows, KD, KD, L, rp, d.nleaf, 0, X(xhat, D), st, wk))) return rc;
+    mk.count(H2_PH_LEAF_FORWARD);
+  }
+  mk.mark(H2_PH_UPWARD);
+  for (int l = D; far && l > lmin; --l) {
+    GcaUpRows<TS, T> rows{(const TS *)d.gE[l], X(xhat, l), d.gK[l], d.gK[l - 1], rp};
+    if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l - 1], d.gK[l - 1], d.gK[l], rp, (int64_t)1 << (l - 1), 0,
+                                     X(xhat, l - 1), st, wk)))
+      return rc;
+    mk.count(H2_PH_UPWARD);
+  }
+  mk.mark(H2_PH_COUPLING);
+  for (int l = lmin; far && l <= D; ++l) {
+    const int64_t c0 = ((int64_t)1 << l) - 1;
+    GcaCouplingRows<TS, T> rows{(const TS *)d.gS[l], d.adm_ptr, d.adm_col, X(xhat, l), d.gK[l], rp, c0};
+    if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l], d.gK[l], d.gK[l], rp, (int64_t)1 << l, 0, X(yhat, l), st, wk)))
+      return rc;
+    mk.count(H2_PH_COUPLING);
+  }
+  mk.mark(H2_PH_DOWNWARD);
+  for (int l = lmin + 1; far && l <= D; ++l) {
+    GcaDownRows<TS, T> rows{(const TS *)d.gEt[l], X(yhat, l - 1), d.gK[l], d.gK[l - 1], rp};
+    if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l], d.gK[l], d.gK[l - 1], rp, (int64_t)1 << l, 1, X(yhat, l), st,
+                                     wk)))
+      return rc;
+    mk.count(H2_PH_DOWNWARD);
+  }
+  mk.mark(H2_PH_LEAF_NEAR);
+  if (far && leaf_reg) {
+    const size_t sm = (size_t)KD * (Lp + rp) * sizeof(T);
+    k_leaf_bwd_reg<TS, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TS *)d.Vt, X(yhat, D), nullptr, L, Lp, KD, rp,
+                                                             nullptr, xpad, ypad);
+    mk.count(H2_PH_LEAF_NEAR);
+  } else if (far) {
+    LeafBackwardRows<TS, T> rows{(const TS *)d.Vt, X(yhat, D), nullptr, KD, Lp, rp, 0};
+    if ((rc = gca_rows_launch<TS, T>(rows, L, Lp, KD, rp, d.nleaf, 0, ypad, st, wk))) return rc;
+    mk.count(H2_PH_LEAF_NEAR);
+  }
+  if (std::is_same<T, dd>::value && d.ntc && rp <= 16) {
+    int64_t nl = 0;
+    if ((rc = ntc_near(c, xpad, ypad, rp, far ? 1 : 0, &nl))) return rc;
+    mk.count(H2_PH_LEAF_NEAR, nl);
+  } else {
+    NearRows<TS, T> rows{(const TS *)d.near, d.near_ptr, d.near_col, xpad, nullptr, L, Lp, rp, nullptr};
+    if ((rc = gca_rows_launch<TS, T>(rows, L, Lp, L, rp, d.nleaf, far ? 1 : 0, ypad, st, wk))) return rc;
+    mk.count(H2_PH_LEAF_NEAR);
+  }
+  mk.mark(H2_PH_PERMUTE_OUT);
+  k_permute_out<T, Tio><<<perm_grid, 256, (size_t)kPermRows * (rp + 1) * sizeof(T), st>>>(
+      ypad, d.n, nrhs, rp, d.pad_src, d.npad, cmx, acc ? 1 : 0, y);
+  mk.count(H2_PH_PERMUTE_OUT);
+  mk.mark(H2_NPHASE);
+  mk.finish();
+  H2_CUDA_TRY(cudaGetLastError());
+  d.last_nrhs = nrhs;
+  d.last_rp = rp;
+  return H2_OK;
+}
+
 }  // namespace
 
 int column_range_shift(unsigned long long bits) { return range_shift(bits); }
@@ -1203,6 +1493,16 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64, bool acc) {
   double *y64 = (double *)y;
   const float *x32 = (const float *)x;
   float *y32 = (float *)y;
+  if (d.gca) {
+    switch (d.prec) {
+      case H2_F64: return matvec_gca<dd, dd, double>(c, x64, y64, nrhs, acc);
+      case H2_F64_NATIVE: return matvec_gca<double, double, double>(c, x64, y64, nrhs, acc);
+      case H2_F32:
+        if (io64) return matvec_gca<float, float, double>(c, x64, y64, nrhs, acc);
+        return matvec_gca<float, float, float>(c, x32, y32, nrhs, acc);
+      default: return fail(H2_EINVAL, "unknown precision");
+    }
+  }
   switch (d.prec) {
     case H2_F64: return matvec_typed<dd, dd, dd, dd, double>(c, x64, y64, nrhs, acc);
     case H2_F64_NATIVE: return matvec_typed<double, double, double, double, double>(c, x64, y64, nrhs, acc);

@@ -529,7 +529,7 @@ int build_typed(Ctx &c) {
   // largest entry
   const int64_t kp = d.kp, Lp = d.lp;
   const auto tb0 = std::chrono::steady_clock::now();
-  {
+  if (!d.gca) {
     BasisRule rule{};
     rule.q = (3 * (m - 1) + 3) / 2 + 1;
     std::vector<double> bx, bw;
@@ -627,19 +627,25 @@ int build_typed(Ctx &c) {
   H2_CUDA_TRY(cudaMemcpyToSymbolAsync(c_gx, gx.data(), gx.size() * 8, 0, cudaMemcpyHostToDevice, st));
   H2_CUDA_TRY(cudaMemcpyToSymbolAsync(c_gw, gw.data(), gw.size() * 8, 0, cudaMemcpyHostToDevice, st));
 
+  // GCA-H^2: pivots, leaf bases, transfer and coupling matrices
+  if (d.gca) {
+    if ((rc = gca_build(c, (const double *)t_vert.ptr, (const int32_t *)t_tri.ptr, (const double *)t_area.ptr)))
+      return rc;
+  }
   // coupling matrices (stored mode)
-  if (d.coupling == 0 && (rc = dev_alloc(d, &d.S, std::max<size_t>(1, (size_t)d.nadm * k * d.kp) * sizeof(T))))
+  if (!d.gca && d.coupling == 0 &&
+      (rc = dev_alloc(d, &d.S, std::max<size_t>(1, (size_t)d.nadm * k * d.kp) * sizeof(T))))
     return rc;
-  if (d.coupling == 0 && d.nadm > 0) {
+  if (!d.gca && d.coupling == 0 && d.nadm > 0) {
     k_coupling_fill<T><<<grid_for(d.nadm * k * d.kp, 256), 256, 0, st>>>((const int32_t *)t_arow.ptr, d.adm_col,
                                                                           d.cheb, m, d.kp, d.nadm, d.kernel,
                                                                           (T *)d.S);
     H2_CUDA_TRY(cudaGetLastError());
   }
   // FP64 and FP32 handles of order 4: the E4M3 digit planes for the tensor-core coupling
-  if (d.tensor == 0 && tc_eligible(d) && (rc = tc_build(c, (const int32_t *)t_arow.ptr))) return rc;
+  if (!d.gca && d.tensor == 0 && tc_eligible(d) && (rc = tc_build(c, (const int32_t *)t_arow.ptr))) return rc;
   H2_CUDA_TRY(cudaStreamSynchronize(st));
-  c.build_ms[H2_BUILD_COUPLING] = ms_since(tc0);
+  c.build_ms[H2_BUILD_COUPLING] = ms_since(tc0) - (d.gca ? c.build_ms[H2_BUILD_BASES] : 0.0);
   const auto tn0 = std::chrono::steady_clock::now();
 
 

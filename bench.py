@@ -332,6 +332,10 @@ def run_ours(args):
     if rank == 0 and not args.no_helmholtz:
         helm = run_helmholtz(args, local, stream)
 
+    gca = None
+    if rank == 0 and not args.no_gca:
+        gca = run_gca(args, local, stream)
+
     serve = None
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, local, stream)
@@ -374,6 +378,7 @@ def run_ours(args):
         "solve": solve,
         "small": small,
         "helmholtz": helm,
+        "gca": gca,
         "serve": serve,
         "mixed": mixed,
         "batch": batch,
@@ -530,6 +535,79 @@ def run_helmholtz(args, local, stream):
                                 "the real form", "solve_s": ts, "solves_per_s": 4 / ts,
                     "iters": [int(i) for i in it], "max_relres": float(max(rel)), "status": int(st)}
     h5.close()
+    return out
+
+
+def run_gca(args, local, stream):
+    """GCA-H^2 (Section 3's GCA-H^2 example; the paper runs it with quadrature
+    order 4, eta = 2 and cross-approximation accuracy 1e-4) on the main
+    workload's mesh (icosphere level 7, leaf 32, 16 right-hand sides):
+    products in FP64-accurate double-float and in FP32, their phases and a
+    coupling roofline, the build, and GMRES(30) / GMRES-IR to 1e-8."""
+    import torch
+    from paper_2203_05665_gb300 import GcaMatrix, colmajor, inputs
+    v, f = inputs.icosphere(args.level)
+    n, nrhs = f.shape[0], args.nrhs
+    x_np = inputs.uniform_rhs(n, nrhs, 1002)
+    peaks = _peaks()
+    out = {"workload": f"GCA-H2 eps 1e-4, Green quadrature order 4, eta 2, icosphere L{args.level} ({n} triangles), "
+                       f"leaf 32, {nrhs} RHS"}
+    mats = {}
+    for prec in ("f64", "f32"):
+        t = time.perf_counter()
+        h = GcaMatrix(v, f, leaf_size=32, eta=2.0, eps=1e-4, prec=prec, device=local, stream=stream.cuda_stream)
+        build_s = time.perf_counter() - t
+        dt, es = (torch.float64, 8) if prec == "f64" else (torch.float32, 4)
+        x = colmajor(torch.from_numpy(x_np).to(device="cuda", dtype=dt))
+        y = colmajor(torch.empty_like(x))
+        for _ in range(3):
+            h.matvec(x, y)
+        reps = max(10, args.steps // 3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            h.matvec(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        h.profile(True)
+        for _ in range(5):
+            h.matvec(x, y)
+        phases, products = h.phase_times()
+        h.profile(False)
+        st = h.stats
+        cpl_ms = phases["coupling"][0] / products
+        s_bytes = st["coupling_entries"] * es
+        flops = 2.0 * nrhs * st["coupling_entries"]
+        if prec == "f64":
+            roof = {"bound": "alu", "achieved": flops / (cpl_ms * 1e-3) / 1e12, "peak": DD_TFLOPS, "unit": "TFLOP/s",
+                    "peak_source": "FP32 FMA rate / 12 instructions per double-float multiply-add",
+                    "hbm_frac": s_bytes / (cpl_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+        else:
+            roof = {"bound": "hbm", "achieved": s_bytes / (cpl_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "peak_source": f"{peaks['src']} HBM copy bandwidth",
+                    "algorithmic_bytes": "the stored coupling matrices (padded per level)"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["kernel_ms"] = cpl_ms
+        out[prec] = {"ms_per_product": ms, "dof_per_s": n * nrhs / (ms * 1e-3), "build_s": build_s,
+                     "build_phases_ms": h.build_times(), "max_padded_rank": st["rank"],
+                     "coupling_entries": st["coupling_entries"], "device_bytes": st["device_bytes"],
+                     "phases_ms": {k: v_[0] / products for k, v_ in phases.items()}, "coupling_roofline": roof}
+        mats[prec] = h
+    b = inputs.uniform_rhs(n, nrhs, 1003)
+    t = time.perf_counter()
+    z, it, rel, st_ = mats["f64"].solve(b, rtol=1e-8, restart=30, maxit=2000)
+    ts = time.perf_counter() - t
+    out["gmres"] = {"solve_s": ts, "solves_per_s": nrhs / ts, "iters_max": int(it.max()), "max_relres": float(rel.max()),
+                    "status": int(st_)}
+    t = time.perf_counter()
+    z, it, rel, st_ = mats["f64"].solve_ir(mats["f32"], b, rtol=1e-8)
+    ts = time.perf_counter() - t
+    out["gmres_ir_f32_inner"] = {"solve_s": ts, "solves_per_s": nrhs / ts, "max_relres": float(rel.max()),
+                                 "status": int(st_)}
+    for h in mats.values():
+        h.close()
     return out
 
 
@@ -866,6 +944,7 @@ def main():
     ap.add_argument("--no-small", action="store_true", help="skip the icosphere L4 latency leg")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-helmholtz", action="store_true")
+    ap.add_argument("--no-gca", action="store_true")
     ap.add_argument("--mixed-level", type=int, default=8)
     ap.add_argument("--serve-small", action="store_true",
                     help="four small geometries (icosphere L4-L6, ellipsoid L6) instead of all eight")

@@ -15,7 +15,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstdlib>
 #include <type_traits>
 
 #include "h2_dd.cuh"
@@ -1300,10 +1299,11 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
                                                                                         d.npad, cmx, xpad);
   mk.count(H2_PH_PERMUTE_IN);
   auto X = [&](T *base, int l) { return base + d.gX[l] * rp; };
-  static const bool wk = [] {
-    const char *e = std::getenv("H2_GCA_WARP");
-    return !(e && e[0] == '0');
-  }();
+  // FP32: the warp-per-row kernel for the transfer steps and the nearfield,
+  // the pipelined block-row kernel for the coupling (measured at 327,680
+  // triangles, 16 right-hand sides); double-float: the block-row kernel
+  // throughout (its contraction split keeps more of the arithmetic busy)
+  const bool wk = std::is_same<T, float>::value;
   const int KD = d.gK[D];
   const bool leaf_reg = L <= 32 && KD <= 64 && rp <= 16;
   mk.mark(H2_PH_LEAF_FORWARD);
@@ -1329,7 +1329,8 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   for (int l = lmin; far && l <= D; ++l) {
     const int64_t c0 = ((int64_t)1 << l) - 1;
     GcaCouplingRows<TS, T> rows{(const TS *)d.gS[l], d.adm_ptr, d.adm_col, X(xhat, l), d.gK[l], rp, c0};
-    if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l], d.gK[l], d.gK[l], rp, (int64_t)1 << l, 0, X(yhat, l), st, wk)))
+    if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l], d.gK[l], d.gK[l], rp, (int64_t)1 << l, 0, X(yhat, l), st,
+                                     false)))
       return rc;
     mk.count(H2_PH_COUPLING);
   }

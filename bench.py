@@ -553,7 +553,7 @@ def run_gca(args, local, stream):
     out = {"workload": f"GCA-H2 eps 1e-4, Green quadrature order 4, eta 2, icosphere L{args.level} ({n} triangles), "
                        f"leaf 32, {nrhs} RHS"}
     mats = {}
-    for prec in ("f64", "f32"):
+    for prec in (("f64", "f32") if args.gca_prec == "both" else (args.gca_prec,)):
         t = time.perf_counter()
         h = GcaMatrix(v, f, leaf_size=32, eta=2.0, eps=1e-4, prec=prec, device=local, stream=stream.cuda_stream)
         build_s = time.perf_counter() - t
@@ -595,6 +595,10 @@ def run_gca(args, local, stream):
                      "coupling_entries": st["coupling_entries"], "device_bytes": st["device_bytes"],
                      "phases_ms": {k: v_[0] / products for k, v_ in phases.items()}, "coupling_roofline": roof}
         mats[prec] = h
+    if len(mats) < 2 or args.gca_only:
+        for h in mats.values():
+            h.close()
+        return out
     b = inputs.uniform_rhs(n, nrhs, 1003)
     t = time.perf_counter()
     z, it, rel, st_ = mats["f64"].solve(b, rtol=1e-8, restart=30, maxit=2000)
@@ -945,6 +949,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-helmholtz", action="store_true")
     ap.add_argument("--no-gca", action="store_true")
+    ap.add_argument("--gca-only", action="store_true",
+                    help="run the GCA-H2 leg alone and print its result (for profiling; no benchmark line)")
+    ap.add_argument("--gca-prec", default="both", choices=["both", "f64", "f32"])
     ap.add_argument("--mixed-level", type=int, default=8)
     ap.add_argument("--serve-small", action="store_true",
                     help="four small geometries (icosphere L4-L6, ellipsoid L6) instead of all eight")
@@ -961,6 +968,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.gca_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"gca": run_gca(args, 0, torch.cuda.current_stream())}))
     else:
         run_ours(args)
 

@@ -656,6 +656,24 @@ def run_small(args, local, stream):
     torch.cuda.synchronize()
     out["graph_equals_direct"] = bool(torch.equal(y, yg))
     out["graph_speedup"] = out["direct"]["median_us"] / out["graph"]["median_us"]
+    # the single-launch product (h2_options.fused): one cooperative kernel
+    hf = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec="f64", device=local, stream=stream.cuda_stream,
+                  fused=True)
+    yf = colmajor(torch.empty_like(x))
+    ygf = colmajor(torch.empty_like(x))
+    gf = hf.graph(x, ygf)
+    out["fused"] = {"direct": lat(lambda: hf.matvec(x, yf)), "graph": lat(gf.launch)}
+    torch.cuda.synchronize()
+    out["fused"]["rel_diff_vs_phase_product"] = float(torch.linalg.norm(yf - y) / torch.linalg.norm(y))
+    out["fused"]["graph_equals_direct"] = bool(torch.equal(yf, ygf))
+    bf = np.asfortranarray(inputs.uniform_rhs(n, 1, 1001))
+    hf.solve(bf, rtol=1e-8, restart=30, maxit=2000)
+    t = time.perf_counter()
+    zf, itf, relf, stf = hf.solve(bf, rtol=1e-8, restart=30, maxit=2000)
+    out["fused"]["gmres"] = {"solve_s": time.perf_counter() - t, "iters": [int(i) for i in itf],
+                             "relres": [float(r) for r in relf], "status": int(stf)}
+    gf.close()
+    hf.close()
     # constant density f = 1: the Galerkin right-hand side b_i = integral of f over T_i = |T_i|
     area = 0.5 * np.linalg.norm(np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]]), axis=1)
     b = np.asfortranarray(np.stack([inputs.uniform_rhs(n, 1, 1001)[:, 0], area], axis=1))

@@ -101,7 +101,11 @@ typedef struct h2_options {
                       * either way).  Other precisions store V and E in their own type and
                       * accept only 0.  The nearfield is always stored in prec, and the coupling
                       * is stored in prec or regenerated in FP32 (field coupling). */
-  int reserved[5];   /* must be zero */
+  int fused;         /* 1: products of an H2_F64 handle with stored coupling and at most 65,536
+                      * triangles run as one cooperative launch (a grid-wide barrier between the
+                      * steps of Algorithms 1-3; for small problems, whose time the separate
+                      * launches of the phases dominate); 0 (default): the launch per phase */
+  int reserved[4];   /* must be zero */
 } h2_options;
 
 /* Statistics of a built matrix (h2_info). */

@@ -31,7 +31,8 @@ class H2Error(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("quad_order", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-                ("coupling", C.c_int), ("tensor", C.c_int), ("basis_prec", C.c_int), ("reserved", C.c_int * 5)]
+                ("coupling", C.c_int), ("tensor", C.c_int), ("basis_prec", C.c_int), ("fused", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 class Stats(C.Structure):
@@ -221,7 +222,7 @@ class H2Matrix:
     """An H² matrix of one mesh on one GPU (see include/h2.h)."""
 
     def __init__(self, vert, tri, leaf_size=32, eta=2.0, order=3, prec="f64", quad_order=3, device=0,
-                 stream=None, coupling="auto", tensor="auto", basis=None, gca=None):
+                 stream=None, coupling="auto", tensor="auto", basis=None, gca=None, fused=False):
         lib = load()
         v, t = _mesh(vert, tri)
         opt = Options()
@@ -233,6 +234,7 @@ class H2Matrix:
         opt.coupling = COUPLING[coupling]
         opt.tensor = {"auto": 0, "off": 1}[tensor]
         opt.basis_prec = 0 if basis is None else PREC[basis]
+        opt.fused = 1 if fused else 0
         h = C.c_void_p()
         if gca is None:
             _check(lib.h2_build(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0],

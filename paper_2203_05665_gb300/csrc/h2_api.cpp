@@ -50,6 +50,7 @@ static void free_dev(Dev &d) {
   for (int l = 0; l < kMaxLevels; ++l)
     for (void *p : {d.gS[l], d.gE[l], d.gEt[l]})
       if (p) cudaFree(p);
+  if (d.fbar) cudaFree(d.fbar);
   if (d.grank) cudaFree(d.grank);
   if (d.gpiv) cudaFree(d.gpiv);
   void *ptrs[] = {d.Ntc, d.xnt, d.ntc_E, d.ntc_xmax, d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.colmax, d.nself, d.near_ptr2, d.self_ptr, d.near_col2, d.near_blk2, d.self_col, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
@@ -97,6 +98,7 @@ int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt,
   if (o.coupling == H2_COUPLING_STORED && half_prec)
     return fail(H2_EINVAL, "16-bit precisions regenerate the coupling");
   if (o.tensor < 0 || o.tensor > 1) return fail(H2_EINVAL, "tensor must be 0 (tensor cores where supported) or 1 (never)");
+  if (o.fused < 0 || o.fused > 1) return fail(H2_EINVAL, "fused must be 0 (off) or 1 (single-launch product when eligible)");
   for (int r : o.reserved)
     if (r) return fail(H2_EINVAL, "reserved option fields must be zero");
   if (o.basis_prec != 0) {
@@ -120,6 +122,7 @@ int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt,
   c->d.prec = o.prec;
   c->d.tensor = o.tensor;
   c->d.kernel = kf;
+  c->d.fused = o.fused == 1 && o.prec == H2_F64 && !gca;
   // FP32 leaf bases: explicitly, or by default under bfloat16 storage
   c->d.v32 = half_prec && (o.basis_prec == H2_F32 || (o.basis_prec == 0 && o.prec == H2_BF16));
   c->d.coupling = (o.coupling == H2_COUPLING_REGEN || half_prec) ? 1 : (o.coupling == H2_COUPLING_STORED ? 0 : -1);

@@ -75,6 +75,8 @@ int make_plan(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, in
               bool with_bases, Plan &p);
 
 constexpr int kMaxLevels = 40;
+// largest problem (triangles) that the single-launch product takes
+constexpr int64_t kFusedMaxN = 65536;
 
 // Parameters of the GCA-H^2 construction (h2_build_gca)
 struct GcaParams {
@@ -146,6 +148,10 @@ struct Dev {
   // transposes (gEt[l]: [c][K_{l-1}][K_l]), and the offset of the level's
   // coefficients in units of rp values (gX[l]); k is the largest gK.  The
   // leaf bases use V and Vt with kp = gK[depth]; the nearfield is the same.
+  // single-launch product for small FP64-accurate matrices (h2_options.fused):
+  // the flag and the grid-barrier words of that launch
+  bool fused = false;
+  unsigned *fbar = nullptr;
   bool gca = false;
   int gK[kMaxLevels] = {0};
   int64_t gX[kMaxLevels] = {0};

@@ -1374,6 +1374,311 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   return H2_OK;
 }
 
+// ---------------------------------------------------------------- fused
+// The whole product of a small FP64-accurate matrix in one cooperative
+// launch (a latency path: at a few thousand triangles the separate
+// launches of the phases cost more than their work).  Every warp of the
+// grid computes whole outputs of a step (warp_dot), each step's outputs
+// depending only on the previous steps' (Algorithms 1-3 in order): column
+// maxima of x (range guard), x in the padded cluster order, the leaf
+// forward step, the upward step level by level, the coupling, the downward
+// step level by level, and the leaf backward step with the nearfield,
+// written straight into the caller's order.  A
+// grid-wide barrier separates the steps: a counter that every CTA
+// increments, waited for with an iteration limit (on time-out the device
+// error word is raised and every CTA leaves).
+struct FusedArgs {
+  const double *x;
+  double *y;
+  int64_t n;
+  int nrhs, rp, acc;
+  const int32_t *pad_src;
+  int L, Lp, k, kp, m, D, lmin;
+  int64_t nleaf, leaf0, nclu;
+  const dd *V, *Vt, *Ef, *S, *near;
+  const int64_t *adm_ptr, *near_ptr;
+  const int32_t *adm_col, *near_col;
+  dd *xpad, *xhat, *yhat;
+  unsigned long long *colmax;
+  unsigned *bar;   // [0] arrivals, [1] abort
+};
+
+constexpr uint32_t kFusedPolls = 1u << 24;
+constexpr int kFusedThreads = 1024;   // one CTA of 32 warps per SM
+
+// grid-wide barrier number g (0, 1, ...): false if it timed out or another CTA
+// gave up
+__device__ bool fused_barrier(const FusedArgs &a, unsigned g) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the CTA's stores of the step (ordered before this thread by the CTA
+    // barrier) are made visible device-wide before its arrival counts
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar) : "memory");
+    const unsigned target = (g + 1) * gridDim.x;
+    uint32_t it = 0;
+    unsigned v = 0, ab = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a.bar) : "memory");
+      if (v >= target) break;
+      if ((++it & 63) == 0) {
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(a.bar + 1) : "memory");
+        if (ab || it >= kFusedPolls) break;
+      }
+    }
+    ok = v >= target ? 1 : 0;
+    __threadfence();
+    if (!ok) {
+      atomicExch(&a.bar[1], 1u);
+      atomicExch(&g_h2_device_error, 1);
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// x value of padding row src (-1: zero), column c, scaled by the column's
+// range-guard power of two
+__device__ __forceinline__ dd fused_x(const FusedArgs &a, int32_t src, int c, int sh) {
+  if (src < 0) return zero_of<dd>();
+  double v = a.x[src + (int64_t)c * a.n];
+  if (sh) v = scale_pow2(v, sh);
+  return dd_from_double(v);
+}
+
+// values written by other CTAs in an earlier step are read at the L2 level
+// (the L1 of an SM is not coherent with the stores of other SMs, and a line
+// it cached in an earlier step may hold stale neighbours)
+__device__ __forceinline__ dd ld_cg(const dd *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return dd{v.x, v.y};
+}
+
+// transfer factor E_c[nu'][nu] = Ex[j'x][jx] Ey[j'y][jy] Ez[j'z][jz] (Eq. (9))
+__device__ __forceinline__ dd fused_E(const FusedArgs &a, int64_t c, int nup, int nu) {
+  const int m = a.m;
+  const dd *f = a.Ef + c * 3 * m * m;
+  const dd ex = f[(0 * m + nup % m) * m + nu % m];
+  const dd ey = f[(1 * m + (nup / m) % m) * m + (nu / m) % m];
+  const dd ez = f[(2 * m + nup / (m * m)) * m + nu / (m * m)];
+  return ex * ey * ez;
+}
+
+// One output of a step, computed by a warp: lane l takes the terms l, l + 32,
+// ... of the contraction (two double-float sums each), then the lanes'
+// sums are added in a butterfly of fixed order; every lane returns the same
+// value.  term(i, a, b) gives the factors of term i.
+template <class F>
+__device__ __forceinline__ dd warp_dot(int len, F term) {
+  const int ln = threadIdx.x & 31;
+  dd s0 = zero_of<dd>(), s1 = zero_of<dd>();
+  int i = ln;
+  for (; i + 32 < len; i += 64) {
+    dd a0, b0, a1, b1;
+    term(i, a0, b0);
+    term(i + 32, a1, b1);
+    acc_fma(s0, a0, b0);
+    acc_fma(s1, a1, b1);
+  }
+  if (i < len) {
+    dd a0, b0;
+    term(i, a0, b0);
+    acc_fma(s0, a0, b0);
+  }
+  acc_norm(s0);
+  acc_norm(s1);
+  dd s = s0 + s1;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const dd t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+    s = s + t;
+  }
+  return s;
+}
+
+__global__ void __launch_bounds__(kFusedThreads) k_fused_dd(FusedArgs a) {
+  __shared__ int shift[64];
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gw = gt >> 5, nw = gs >> 5;
+  const bool lead = (threadIdx.x & 31) == 0;
+  const int k = a.k, nr = a.nrhs, rp = a.rp, L = a.L;
+  const int64_t npad = a.nleaf * L;
+  unsigned g = 0;
+  // column maxima of x
+  for (int c = 0; c < nr; ++c) {
+    double mx = 0.0;
+    for (int64_t i = gt; i < a.n; i += gs) mx = fmax(mx, fabs(a.x[i + (int64_t)c * a.n]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lead && mx > 0.0) atomicMax(&a.colmax[c], (unsigned long long)__double_as_longlong(mx));
+  }
+  if (!fused_barrier(a, g++)) return;
+  if (threadIdx.x < 64) shift[threadIdx.x] = (int)threadIdx.x < nr ? range_shift(__ldcg(a.colmax + threadIdx.x)) : 0;
+  __syncthreads();
+  // x in the padded cluster order, scaled by the range guard (zero for padding)
+  for (int64_t q = gt; q < npad * rp; q += gs) {
+    const int64_t p = q / rp;
+    const int c = (int)(q - p * rp);
+    a.xpad[q] = c < nr ? fused_x(a, a.pad_src[p], c, shift[c]) : zero_of<dd>();
+  }
+  if (!fused_barrier(a, g++)) return;
+  const bool far = a.lmin <= a.D;
+  if (far) {
+    // leaf forward: x^_j[nu][c] = sum_t V_j[t][nu] x[t][c]
+    for (int64_t o = gw; o < a.nleaf * k * nr; o += nw) {
+      const int64_t j = o / (k * nr);
+      const int r = (int)(o - j * k * nr), nu = r % k, c = r / k;
+      const dd v = warp_dot(L, [&](int t, dd &x, dd &y) {
+        x = a.V[(j * L + t) * a.kp + nu];
+        y = ld_cg(a.xpad + (j * L + t) * rp + c);
+      });
+      if (lead) a.xhat[((a.leaf0 + j) * k + nu) * rp + c] = v;
+    }
+    if (!fused_barrier(a, g++)) return;
+    // upward: x^_p[nu][c] = sum over the sons s, nu' of E_s[nu'][nu] x^_s[nu'][c]
+    for (int l = a.D - 1; l >= a.lmin; --l) {
+      const int64_t p0 = ((int64_t)1 << l) - 1, np = (int64_t)1 << l;
+      for (int64_t o = gw; o < np * k * nr; o += nw) {
+        const int64_t p = p0 + o / (k * nr);
+        const int r = (int)(o % (k * nr)), nu = r % k, c = r / k;
+        const dd v = warp_dot(2 * k, [&](int i, dd &x, dd &y) {
+          const int64_t ch = 2 * p + 1 + (i >= k);
+          const int nup = i >= k ? i - k : i;
+          x = fused_E(a, ch, nup, nu);
+          y = ld_cg(a.xhat + (ch * k + nup) * rp + c);
+        });
+        if (lead) a.xhat[(p * k + nu) * rp + c] = v;
+      }
+      if (!fused_barrier(a, g++)) return;
+    }
+    // coupling: y^_t[nu][c] = sum over the admissible blocks (t, s), mu of S_b[mu][nu] x^_s[mu][c]
+    const int64_t t0 = ((int64_t)1 << a.lmin) - 1;
+    for (int64_t o = gw; o < (a.nclu - t0) * k * nr; o += nw) {
+      const int64_t t = t0 + o / (k * nr);
+      const int r = (int)(o % (k * nr)), nu = r % k, c = r / k;
+      const int64_t b0 = a.adm_ptr[t];
+      const dd v = warp_dot((int)(a.adm_ptr[t + 1] - b0) * k, [&](int i, dd &x, dd &y) {
+        const int64_t b = b0 + i / k;
+        const int mu = i % k;
+        x = a.S[(b * k + mu) * a.kp + nu];
+        y = ld_cg(a.xhat + ((int64_t)a.adm_col[b] * k + mu) * rp + c);
+      });
+      if (lead) a.yhat[(t * k + nu) * rp + c] = v;
+    }
+    if (!fused_barrier(a, g++)) return;
+    // downward: y^_s[nu'][c] += sum_nu E_s[nu'][nu] y^_parent[nu][c]
+    for (int l = a.lmin; l < a.D; ++l) {
+      const int64_t c0 = ((int64_t)2 << l) - 1, nc = (int64_t)2 << l;
+      for (int64_t o = gw; o < nc * k * nr; o += nw) {
+        const int64_t ch = c0 + o / (k * nr), p = (ch - 1) / 2;
+        const int r = (int)(o % (k * nr)), nup = r % k, c = r / k;
+        const dd v = warp_dot(k, [&](int nu, dd &x, dd &y) {
+          x = fused_E(a, ch, nup, nu);
+          y = ld_cg(a.yhat + (p * k + nu) * rp + c);
+        });
+        if (lead) {
+          dd *out = a.yhat + (ch * k + nup) * rp + c;
+          *out = ld_cg(out) + v;
+        }
+      }
+      if (!fused_barrier(a, g++)) return;
+    }
+  }
+  // leaf backward and nearfield: y[t][c] = sum_nu V_j[t][nu] y^_j[nu][c] + sum over the near blocks of G_b x
+  for (int64_t o = gw; o < npad * nr; o += nw) {
+    const int64_t pr = o / nr;
+    const int c = (int)(o - pr * nr);
+    const int32_t dst = a.pad_src[pr];
+    if (dst < 0) continue;
+    const int64_t j = pr / L;
+    const int t = (int)(pr - j * L);
+    const int kf = far ? k : 0;
+    const int64_t nb0 = a.near_ptr[j];
+    const dd v = warp_dot(kf + (int)(a.near_ptr[j + 1] - nb0) * L, [&](int i, dd &x, dd &y) {
+      if (i < kf) {
+        x = a.Vt[(j * k + i) * a.Lp + t];
+        y = ld_cg(a.yhat + ((a.leaf0 + j) * k + i) * rp + c);
+      } else {
+        const int64_t b = nb0 + (i - kf) / L;
+        const int u = (i - kf) % L;
+        x = a.near[(b * L + u) * a.Lp + t];
+        y = ld_cg(a.xpad + ((int64_t)a.near_col[b] * L + u) * rp + c);
+      }
+    });
+    if (lead) {
+      double w = dd_to_double(v);
+      if (shift[c]) w = scale_pow2(w, -shift[c]);
+      double *out = a.y + dst + (int64_t)c * a.n;
+      *out = a.acc ? *out + w : w;
+    }
+  }
+}
+
+// y = G~ x by k_fused_dd (one cooperative launch; see the kernel)
+int matvec_fused(Ctx &c, const double *x, double *y, int nrhs, bool acc) {
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  const int rp = padded_rhs(nrhs, sizeof(dd));
+  Marks mk(c);
+  for (int ph = H2_PH_PERMUTE_IN; ph <= H2_PH_COUPLING; ++ph) mk.mark(ph);
+  H2_CUDA_TRY(cudaMemsetAsync(d.colmax, 0, sizeof(unsigned long long) * nrhs, st));
+  H2_CUDA_TRY(cudaMemsetAsync(d.fbar, 0, 2 * sizeof(unsigned), st));
+  FusedArgs a{};
+  a.x = x;
+  a.y = y;
+  a.n = d.n;
+  a.nrhs = nrhs;
+  a.rp = rp;
+  a.acc = acc ? 1 : 0;
+  a.pad_src = d.pad_src;
+  a.L = (int)d.lmax;
+  a.Lp = (int)d.lp;
+  a.k = d.k;
+  a.kp = d.kp;
+  a.m = d.m;
+  a.D = d.depth;
+  a.lmin = d.first_adm_level;
+  a.nleaf = d.nleaf;
+  a.leaf0 = d.nleaf - 1;
+  a.nclu = d.nclu;
+  a.V = (const dd *)d.V;
+  a.Vt = (const dd *)d.Vt;
+  a.Ef = (const dd *)d.Ef;
+  a.S = (const dd *)d.S;
+  a.near = (const dd *)d.near;
+  a.adm_ptr = d.adm_ptr;
+  a.near_ptr = d.near_ptr;
+  a.adm_col = d.adm_col;
+  a.near_col = d.near_col;
+  a.xpad = (dd *)d.xpad;
+  a.xhat = (dd *)d.xhat;
+  a.yhat = (dd *)d.yhat;
+  a.colmax = d.colmax;
+  a.bar = d.fbar;
+  int dev = 0, sms = 0, per_sm = 0;
+  H2_CUDA_TRY(cudaGetDevice(&dev));
+  H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  H2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_dd, kFusedThreads, 0));
+  if (per_sm < 1) return fail(H2_EINVAL, "the fused product kernel cannot be resident");
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)sms);
+  cfg.blockDim = dim3(kFusedThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  H2_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused_dd, a));
+  mk.count(H2_PH_COUPLING);
+  for (int ph = H2_PH_DOWNWARD; ph <= H2_NPHASE; ++ph) mk.mark(ph);
+  mk.finish();
+  d.last_nrhs = nrhs;
+  d.last_rp = rp;
+  return H2_OK;
+}
+
 }  // namespace
 
 int column_range_shift(unsigned long long bits) { return range_shift(bits); }
@@ -1494,6 +1799,8 @@ int run_matvec(Ctx &c, const void *x, void *y, int nrhs, bool io64, bool acc) {
   double *y64 = (double *)y;
   const float *x32 = (const float *)x;
   float *y32 = (float *)y;
+  if (d.fused && d.prec == H2_F64 && !d.gca && d.coupling == 0 && d.n <= kFusedMaxN)
+    return matvec_fused(c, (const double *)x, (double *)y, nrhs, acc);
   if (d.gca) {
     switch (d.prec) {
       case H2_F64: return matvec_gca<dd, dd, double>(c, x64, y64, nrhs, acc);

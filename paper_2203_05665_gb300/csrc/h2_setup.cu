@@ -784,6 +784,7 @@ int device_build(Ctx &c) {
       d.esize = 8;
       int rc = dev_alloc(d, (void **)&d.colmax, 64 * sizeof(unsigned long long));
       if (rc) return rc;
+      if (d.fused && (rc = dev_alloc(d, (void **)&d.fbar, 2 * sizeof(unsigned)))) return rc;
       return build_typed<dd>(c);
     }
     case H2_F64_NATIVE: d.esize = 8; return build_typed<double>(c);

@@ -1238,7 +1238,7 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
 // of four warps fit shared memory, else the pipelined block-row kernel.
 template <class TS, class T, class Rows>
 int gca_rows_launch(const Rows &rows, int M, int Mp, int Kmax, int rp, int64_t nrows, int accumulate, T *out,
-                    cudaStream_t st, bool warp) {
+                    cudaStream_t st, bool warp, int tmax = 256) {
   if (nrows <= 0) return H2_OK;
   if (warp) {
     constexpr int VN = Vec16<T>::N;
@@ -1265,7 +1265,13 @@ int gca_rows_launch(const Rows &rows, int M, int Mp, int Kmax, int rp, int64_t n
     }
   }
   const int R = row_groups<T>(Mp);
-  const int threads = row_threads(Mp, rp, Kmax, sizeof(T), R);
+  int threads = row_threads(Mp, rp, Kmax, sizeof(T), R);
+  {
+    // at most tmax consumer threads (a smaller contraction split), as long as every tile keeps a thread
+    constexpr int VN = Vec16<T>::N;
+    const int tiles = (Mp / (4 * R)) * (rp / VN);
+    while (threads > tmax && threads / 2 >= tiles) threads /= 2;
+  }
   RowCfg cfg{};
   int rc;
   if ((rc = row_cfg<TS, T>(M, Mp, rp, Kmax, threads, R, false, cfg))) return rc;
@@ -1304,6 +1310,9 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   // triangles, 16 right-hand sides); double-float: the block-row kernel
   // throughout (its contraction split keeps more of the arithmetic busy)
   const bool wk = std::is_same<T, float>::value;
+  // block-row threads: 128 for the double-float transfers and the FP32
+  // coupling, 256 for the double-float coupling (measured at 327,680 triangles)
+  const int t_tr = 128, t_cpl = std::is_same<T, float>::value ? 128 : 256;
   const int KD = d.gK[D];
   const bool leaf_reg = L <= 32 && KD <= 64 && rp <= 16;
   mk.mark(H2_PH_LEAF_FORWARD);
@@ -1321,7 +1330,7 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   for (int l = D; far && l > lmin; --l) {
     GcaUpRows<TS, T> rows{(const TS *)d.gE[l], X(xhat, l), d.gK[l], d.gK[l - 1], rp};
     if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l - 1], d.gK[l - 1], d.gK[l], rp, (int64_t)1 << (l - 1), 0,
-                                     X(xhat, l - 1), st, wk)))
+                                     X(xhat, l - 1), st, wk, t_tr)))
       return rc;
     mk.count(H2_PH_UPWARD);
   }
@@ -1330,7 +1339,7 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
     const int64_t c0 = ((int64_t)1 << l) - 1;
     GcaCouplingRows<TS, T> rows{(const TS *)d.gS[l], d.adm_ptr, d.adm_col, X(xhat, l), d.gK[l], rp, c0};
     if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l], d.gK[l], d.gK[l], rp, (int64_t)1 << l, 0, X(yhat, l), st,
-                                     false)))
+                                     false, t_cpl)))
       return rc;
     mk.count(H2_PH_COUPLING);
   }
@@ -1338,7 +1347,7 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   for (int l = lmin + 1; far && l <= D; ++l) {
     GcaDownRows<TS, T> rows{(const TS *)d.gEt[l], X(yhat, l - 1), d.gK[l], d.gK[l - 1], rp};
     if ((rc = gca_rows_launch<TS, T>(rows, d.gK[l], d.gK[l], d.gK[l - 1], rp, (int64_t)1 << l, 1, X(yhat, l), st,
-                                     wk)))
+                                     wk, t_tr)))
       return rc;
     mk.count(H2_PH_DOWNWARD);
   }

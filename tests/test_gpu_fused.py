@@ -2,8 +2,8 @@
 matrices: one cooperative launch runs Algorithms 1-3 with grid-wide
 barriers between the steps.  Checked against the oracle (1e-12) and against
 the launch-per-phase product of the same mesh (1e-13), with the accumulate
-form, CUDA-graph replay, a column outside the double-float range (range
-guard), a mesh without admissible blocks, ragged leaves, order 4 (whose
+form, CUDA-graph replay, the allocation-free entry point, a column outside
+the double-float range (range guard), a mesh without admissible blocks, ragged leaves, order 4 (whose
 handles also keep the tensor-core digits) and GMRES."""
 import numpy as np
 import pytest
@@ -97,6 +97,11 @@ def test_fused_accumulate_graph_and_range_guard(require_gpu):
             torch.cuda.synchronize()
             assert np.array_equal(yg.cpu().numpy(), got)
         assert np.array_equal(fz.matvec_host(x), got)
+        # through the allocation-free entry point (the fused kernel's work vectors in its fixed array)
+        yn = colmajor(torch.full_like(xd, float("nan")))
+        fz.matvec_noalloc(xd, yn)
+        torch.cuda.synchronize()
+        assert np.array_equal(yn.cpu().numpy(), got)
     finally:
         fz.close()
         st.close()

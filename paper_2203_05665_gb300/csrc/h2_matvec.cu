@@ -1288,6 +1288,11 @@ int matvec_gca(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   cudaStream_t st = c.stream;
   const int L = (int)d.lmax, Lp = (int)d.lp, D = d.depth, lmin = d.first_adm_level;
   const int rp = padded_rhs(nrhs, sizeof(T));
+  // every output tile (the largest padded rank or leaf x the padded columns)
+  // must fit the threads of one block-row CTA: refuse before any launch
+  if ((int64_t)(std::max<int64_t>(d.k, Lp) / 4) * (rp / Vec16<T>::N) > kThreads)
+    return fail(H2_EINVAL, "GCA-H^2 product: rank " + std::to_string(d.k) + " with " + std::to_string(nrhs) +
+                               " right-hand sides exceeds one tile; use fewer right-hand sides per call");
   T *xpad = (T *)d.xpad, *ypad = (T *)d.ypad, *xhat = (T *)d.xhat, *yhat = (T *)d.yhat;
   const bool far = lmin <= D;
   int rc;

@@ -9,7 +9,8 @@ the oracle's GCA-H^2 matrix on the same seeded meshes:
   and transfer matrices, whose rounding grows with the condition of the
   pivot blocks, to 1e-11 (FP32: twice the unit roundoff);
 * products (y = G~ x, y += G~ x, host buffers, graph replay, no-alloc) agree
-  with the oracle's product (FP64 1e-12, FP32 1e-6);
+  with the oracle's product (FP64 1e-12, FP32 1e-6) for 1 to 32 right-hand
+  sides; too many right-hand sides for one tile are refused before any launch;
 * GMRES and GMRES-IR reach 1e-8 in the true residual (the oracle's product);
 * sampled rows at 327,680 triangles (the product's launch configuration)."""
 import numpy as np
@@ -112,14 +113,20 @@ def test_matvec_matches_oracle(require_gpu, name, prec):
     v, f, o = _oracle(name)
     h = _gca(name, prec)
     try:
-        for nrhs in (1, 5, 16):
+        vn, es = (4, 4) if prec == "f32" else (2, 8)
+        lp = -(-h.stats["leaf_max"] // 4) * 4
+        for nrhs in (1, 5, 16, 32):
             x = I.uniform_rhs(f.shape[0], nrhs, 3000 + nrhs)
-            ref = o.matvec(x)
             dt = torch.float32 if prec == "f32" else torch.float64
             xd = colmajor(torch.from_numpy(x).to(device="cuda", dtype=dt))
             yd = colmajor(torch.empty_like(xd))
+            rp = -(-nrhs * es // 16) * 16 // es
+            if (max(h.stats["rank"], lp) // 4) * (rp // vn) > 256:
+                with pytest.raises(H2Error):       # the output tile does not fit one CTA
+                    h.matvec(xd, yd)
+                continue
             h.matvec(xd, yd)
-            assert _rel(yd.double().cpu().numpy(), ref) < TOL[prec], nrhs
+            assert _rel(yd.double().cpu().numpy(), o.matvec(x)) < TOL[prec], nrhs
     finally:
         h.close()
 
@@ -173,6 +180,24 @@ def test_gmres_reaches_1e8(require_gpu, prec):
         h.close()
         if lo is not None:
             lo.close()
+
+
+def test_rejects_oversized_tiles(require_gpu):
+    """64 double-float columns with a padded rank above 32 do not fit one
+    output tile: H2_EINVAL before any launch, and the handle still works."""
+    import torch
+    v, f, o = _oracle("ico4")
+    h = _gca("ico4")
+    try:
+        assert h.stats["rank"] > 32
+        x = colmajor(torch.from_numpy(I.uniform_rhs(f.shape[0], 64, 3300)).cuda())
+        y = colmajor(torch.empty_like(x))
+        with pytest.raises(H2Error):
+            h.matvec(x, y)
+        x1 = I.uniform_rhs(f.shape[0], 2, 3301)
+        assert _rel(h.matvec_host(x1), o.matvec(x1)) < 1e-12
+    finally:
+        h.close()
 
 
 def test_rejects_bad_options(require_gpu):

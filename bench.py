@@ -518,10 +518,15 @@ def run_helmholtz(args, local, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # algorithmic bytes: two real products (G_c, G_s) of 2 nrhs real columns each
+    peaks = _peaks()
+    hb = 2 * _algorithmic(h.stats, 2 * nrhs, 8)["total_bytes"]
     out = {"workload": f"Helmholtz kappa={kappa}, icosphere L{args.level} ({n} triangles), m=4, leaf 32, eta 2, "
                        f"{nrhs} complex RHS, FP64-accurate (tensor-core coupling and nearfield in both parts)",
            "ms_per_product": ms, "complex_dof_per_s": n * nrhs / (ms * 1e-3), "build_s": build_s,
-           "device_bytes": h.stats["device_bytes"], "tensor": h.stats["tensor"], "tensor_near": h.stats["tensor_near"]}
+           "device_bytes": h.stats["device_bytes"], "tensor": h.stats["tensor"], "tensor_near": h.stats["tensor_near"],
+           "hbm_frac_whole_product": hb / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+           "algorithmic_bytes": hb, "peak_source": f"{peaks['src']} HBM copy bandwidth"}
     h.close()
     v5, f5 = inputs.icosphere(5)
     h5 = HelmholtzMatrix(v5, f5, kappa, leaf_size=32, eta=2.0, order=4, prec="f64", device=local,
@@ -590,6 +595,12 @@ def run_gca(args, local, stream):
                     "algorithmic_bytes": "the stored coupling matrices (padded per level)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["kernel_ms"] = cpl_ms
+        # whole product: nearfield, leaf bases (padded rank of the leaf level), coupling, transfer
+        # matrices (two copies, one per direction, at most rank^2 per cluster), vectors
+        K = st["rank"]
+        tot = es * (st["near_entries"] + n * K + st["coupling_entries"] + 2 * st["clusters"] * K * K) \
+            + 8 * 2 * n * nrhs
+        roof["hbm_frac_whole_product_upper_bound"] = tot / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
         out[prec] = {"ms_per_product": ms, "dof_per_s": n * nrhs / (ms * 1e-3), "build_s": build_s,
                      "build_phases_ms": h.build_times(), "max_padded_rank": st["rank"],
                      "coupling_entries": st["coupling_entries"], "device_bytes": st["device_bytes"],

@@ -352,7 +352,9 @@ __device__ double galerkin_regular(const double *vert, const int32_t *tri, const
 }
 
 // coupling matrices of one level: S_b = G|_{t_0 x s_0}, stored transposed
-// [mu][nu] (nu: row pivot of t, mu: column pivot of s), zero padded to K
+// [mu][nu] (nu: row pivot of t, mu: column pivot of s), zero padded to K;
+// only the blocks with t < s (the others are their mirrors' transposes,
+// k_gca_mirror)
 template <class T>
 __global__ void k_gca_coupling(const double *__restrict__ vert, const int32_t *__restrict__ tri,
                                const double *__restrict__ area, const int32_t *__restrict__ arow,
@@ -361,13 +363,30 @@ __global__ void k_gca_coupling(const double *__restrict__ vert, const int32_t *_
   const int64_t total = nb * (int64_t)K * K;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = e / ((int64_t)K * K);
+    const int64_t t = arow[b], s = acol[b];
+    if (t > s) continue;
     const int rem = (int)(e - b * K * K);
     const int mu = rem / K, nu = rem - mu * K;
-    const int64_t t = arow[b], s = acol[b];
     double v = 0.0;
     if (nu < rank[t] && mu < rank[s])
       v = galerkin_regular(vert, tri, area, piv[t * kcap + nu], piv[s * kcap + mu], q);
     S[e] = from_double<T>(v);
+  }
+}
+
+// S_{t,s} = S_{s,t}^T for the blocks with t > s of one level (G is symmetric
+// bit for bit: every entry is evaluated with the smaller triangle index as
+// test triangle); mir[b] = the level-local index of block (s, t)
+template <class T>
+__global__ void k_gca_mirror(const int32_t *__restrict__ arow, const int32_t *__restrict__ acol,
+                             const int32_t *__restrict__ mir, int64_t nb, int K, T *__restrict__ S) {
+  const int64_t total = nb * (int64_t)K * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / ((int64_t)K * K);
+    if (arow[b] < acol[b]) continue;
+    const int rem = (int)(e - b * K * K);
+    const int mu = rem / K, nu = rem - mu * K;
+    S[e] = S[(int64_t)mir[b] * K * K + (int64_t)nu * K + mu];
   }
 }
 
@@ -523,10 +542,24 @@ int gca_build_typed(Ctx &c, const double *vert, const int32_t *tri, const double
   std::vector<int32_t> arow(p.adm_col.size());
   for (int64_t t = 0; t < p.nclu; ++t)
     for (int64_t e = p.adm_ptr[t]; e < p.adm_ptr[t + 1]; ++e) arow[e] = (int32_t)t;
-  DevBuf barow;
-  if ((rc = barow.get(arow.size() * 4))) return rc;
-  if (!arow.empty())
+  // level-local index of the mirror block (s, t) of every admissible block (t, s)
+  std::vector<int32_t> mir(p.adm_col.size(), 0);
+  for (int64_t t = 0; t < p.nclu; ++t)
+    for (int64_t e = p.adm_ptr[t]; e < p.adm_ptr[t + 1]; ++e) {
+      const int64_t sc = p.adm_col[e];
+      const auto beg = p.adm_col.begin() + p.adm_ptr[sc], end = p.adm_col.begin() + p.adm_ptr[sc + 1];
+      const auto it = std::lower_bound(beg, end, (int32_t)t);
+      if (it == end || *it != (int32_t)t) return fail(H2_EINVAL, "block tree is not symmetric");
+      int l = 0;
+      while (((int64_t)2 << l) - 1 <= sc) ++l;
+      mir[e] = (int32_t)((it - p.adm_col.begin()) - p.adm_ptr[((int64_t)1 << l) - 1]);
+    }
+  DevBuf barow, bmir;
+  if ((rc = barow.get(arow.size() * 4)) || (rc = bmir.get(mir.size() * 4))) return rc;
+  if (!arow.empty()) {
     H2_CUDA_TRY(cudaMemcpyAsync(barow.ptr, arow.data(), arow.size() * 4, cudaMemcpyHostToDevice, st));
+    H2_CUDA_TRY(cudaMemcpyAsync(bmir.ptr, mir.data(), mir.size() * 4, cudaMemcpyHostToDevice, st));
+  }
   d.coupling_entries = 0;
   for (int l = lmin; l <= D; ++l) {
     const int64_t c0 = ((int64_t)1 << l) - 1, c1 = ((int64_t)2 << l) - 1;
@@ -538,6 +571,9 @@ int gca_build_typed(Ctx &c, const double *vert, const int32_t *tri, const double
     k_gca_coupling<T><<<grid_of(nb * K * K, 128), 128, 0, st>>>(vert, tri, area, (const int32_t *)barow.ptr + b0,
                                                                d.adm_col + b0, d.grank, d.gpiv, kcap, nb, K,
                                                                c.quad_order, (T *)d.gS[l]);
+    H2_CUDA_TRY(cudaGetLastError());
+    k_gca_mirror<T><<<grid_of(nb * K * K, 256), 256, 0, st>>>((const int32_t *)barow.ptr + b0, d.adm_col + b0,
+                                                             (const int32_t *)bmir.ptr + b0, nb, K, (T *)d.gS[l]);
     H2_CUDA_TRY(cudaGetLastError());
   }
   H2_CUDA_TRY(cudaStreamSynchronize(st));

@@ -11,7 +11,8 @@ the oracle's GCA-H^2 matrix on the same seeded meshes:
 * products (y = G~ x, y += G~ x, host buffers, graph replay, no-alloc) agree
   with the oracle's product (FP64 1e-12, FP32 1e-6) for 1 to 32 right-hand
   sides; too many right-hand sides for one tile are refused before any launch;
-* GMRES and GMRES-IR reach 1e-8 in the true residual (the oracle's product);
+* GMRES and GMRES-IR reach 1e-8 in the true residual (the oracle's product),
+  also through the serving engine;
 * sampled rows at 327,680 triangles (the product's launch configuration)."""
 import numpy as np
 import pytest
@@ -198,6 +199,30 @@ def test_rejects_oversized_tiles(require_gpu):
         assert _rel(h.matvec_host(x1), o.matvec(x1)) < 1e-12
     finally:
         h.close()
+
+
+def test_serving_engine_with_gca_handles(require_gpu):
+    """A GCA-H^2 pair (FP64-accurate residuals, FP32 inner solves) registered
+    with the serving engine: requests reach their tolerance in the oracle's
+    true residual."""
+    from paper_2203_05665_gb300 import Server
+    v, f, o = _oracle("ico4")
+    hi, lo = _gca("ico4", "f64"), _gca("ico4", "f32")
+    srv = Server()
+    try:
+        srv.register(hi, lo, slots=8)
+        reqs = [(I.uniform_rhs(f.shape[0], nr, 3400 + nr), rt) for nr, rt in ((1, 1e-8), (3, 1e-6), (2, 1e-8))]
+        tickets = [srv.submit(hi, b, rt) for b, rt in reqs]
+        for (b, rt), (t, shape) in zip(reqs, tickets):
+            assert srv.wait(t, 120)
+            z, it, rel, st = srv.poll(t, shape)
+            assert st == 0 and np.all(rel <= rt)
+            r = b - o.matvec(z)
+            assert np.all(np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0) <= 1.5 * rt)
+    finally:
+        srv.close()
+        hi.close()
+        lo.close()
 
 
 def test_rejects_bad_options(require_gpu):

@@ -256,6 +256,16 @@ int h2_graph_destroy(h2_graph g);
  * stream. */
 int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs);
 
+/* A sequence of count products with HOST double arrays: block i of x (at
+ * x + i n nrhs, column-major n x nrhs) gives block i of y.  The copy of block
+ * i + 1 in and of block i - 1 out run beside the product of block i (two
+ * device buffer pairs kept on the handle, two copy streams, events between
+ * them), so a stream of inputs moves at the rate of the products when the
+ * host arrays are pinned.  Blocks are independent; each result equals
+ * h2_matvec_host's.  Synchronises before returning.  Errors as for
+ * h2_matvec_host; count >= 1. */
+int h2_matvec_host_stream(h2_handle h, const double *x, double *y, int nrhs, int count);
+
 /* Coefficients of the last product (diagnostics): which = 0 gives x^ after
  * the forward transformation, 1 gives y^ after the interaction and the
  * downward transfer (as used by the leaf backward step).  out: HOST double

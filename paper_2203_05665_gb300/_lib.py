@@ -53,7 +53,7 @@ class SolveInfo(C.Structure):
 
 EXPORTED = ["h2_options_default", "h2_plan_create", "h2_plan_destroy", "h2_plan_counts", "h2_plan_tree",
             "h2_plan_blocks", "h2_plan_bases", "h2_build", "h2_destroy", "h2_info", "h2_matvec", "h2_matvec_acc",
-            "h2_matvec_noalloc", "h2_matvec_host", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
+            "h2_matvec_noalloc", "h2_matvec_host", "h2_matvec_host_stream", "h2_coefficients", "h2_solve", "h2_solve_ir", "h2_profile", "h2_phase_times",
             "h2_serve_create", "h2_serve_register", "h2_serve_submit", "h2_serve_poll", "h2_serve_wait",
             "h2_serve_stats", "h2_serve_destroy", "h2_batch_create", "h2_batch_offsets", "h2_batch_matvec",
             "h2_batch_tune", "h2_batch_set_shapes", "h2_batch_profile", "h2_batch_phase_times", "h2_batch_info",
@@ -94,6 +94,7 @@ def load():
             "h2_matvec_acc": (C.c_int, [vp, vp, vp, C.c_int]),
             "h2_matvec_noalloc": (C.c_int, [vp, vp, vp, C.c_int]),
             "h2_matvec_host": (C.c_int, [vp, dp, dp, C.c_int]),
+            "h2_matvec_host_stream": (C.c_int, [vp, dp, dp, C.c_int, C.c_int]),
             "h2_coefficients": (C.c_int, [vp, C.c_int, dp]),
             "h2_solve": (C.c_int, [vp, vp, vp, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(SolveInfo)]),
             "h2_solve_ir": (C.c_int, [vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
@@ -342,6 +343,17 @@ class H2Matrix:
         x = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(self.n, -1))
         y = np.zeros_like(x, order="F")
         _check(self._lib.h2_matvec_host(self._h, _dp(x), _dp(y), int(x.shape[1])))
+        return y
+
+    def matvec_host_stream(self, x, y):
+        """A sequence of products from host FP64 blocks (h2_matvec_host_stream):
+        x and y pinned torch CPU tensors of shape (count, nrhs, n), each block
+        column-major (n x nrhs), copies overlapped with the products."""
+        count, nrhs = int(x.shape[0]), int(x.shape[1])
+        if tuple(y.shape) != tuple(x.shape) or x.shape[2] != self.n:
+            raise ValueError("x and y must both be (count, nrhs, n)")
+        _check(self._lib.h2_matvec_host_stream(self._h, C.cast(C.c_void_p(x.data_ptr()), C.POINTER(C.c_double)),
+                                               C.cast(C.c_void_p(y.data_ptr()), C.POINTER(C.c_double)), nrhs, count))
         return y
 
     def build_times(self):

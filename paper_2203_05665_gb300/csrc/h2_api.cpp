@@ -304,6 +304,44 @@ int h2_gca_pivots(h2_handle h, int32_t *rank, int32_t *pivots, int64_t cap) {
   return H2_OK;
 }
 
+namespace {
+
+void free_stream_work(StreamWork &w) {
+  for (int b = 0; b < 2; ++b) {
+    if (w.x[b]) cudaFree(w.x[b]);
+    if (w.y[b]) cudaFree(w.y[b]);
+    for (cudaEvent_t e : {w.ev_in[b], w.ev_done[b], w.ev_out[b]})
+      if (e) cudaEventDestroy(e);
+  }
+  if (w.in) cudaStreamDestroy(w.in);
+  if (w.out) cudaStreamDestroy(w.out);
+  w = StreamWork();
+}
+
+int ensure_stream_work(StreamWork &w, size_t bytes) {
+  if (w.in && bytes <= w.bytes) return H2_OK;
+  free_stream_work(w);
+  auto al = [](double **p, size_t b) { return dmalloc(p, b) == cudaSuccess; };
+  if (!al(&w.x[0], bytes) || !al(&w.x[1], bytes) || !al(&w.y[0], bytes) || !al(&w.y[1], bytes)) {
+    cudaGetLastError();
+    free_stream_work(w);
+    return fail(H2_ENOMEM, "buffers of h2_matvec_host_stream");
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&w.in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.out, cudaStreamNonBlocking);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    for (cudaEvent_t *ev : {&w.ev_in[b], &w.ev_done[b], &w.ev_out[b]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_stream_work(w);
+    return cuda_fail(e, "streams of h2_matvec_host_stream");
+  }
+  w.bytes = bytes;
+  return H2_OK;
+}
+
+}  // namespace
+
 static void drop_events(Prof &p) {
   for (auto e : p.ev) cudaEventDestroy(e);
   p.ev.clear();
@@ -316,6 +354,7 @@ int h2_destroy(h2_handle h) {
   else cudaDeviceSynchronize();
   drop_events(h->prof);
   free_gmres_work(h->gw);
+  free_stream_work(h->sw);
   free_dev(h->d);
   delete h;
   return H2_OK;
@@ -509,6 +548,50 @@ int h2_matvec_host(h2_handle h, const double *x, double *y, int nrhs) {
   if ((rc = run_matvec(*h, h->d.io_x, h->d.io_y, nrhs, true))) return rc;
   H2_CUDA_TRY(cudaMemcpyAsync(y, h->d.io_y, bytes, cudaMemcpyDeviceToHost, h->stream));
   H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return take_device_error(*h);
+}
+
+int h2_matvec_host_stream(h2_handle h, const double *x, double *y, int nrhs, int count) {
+  if (!h || !x || !y) return fail(H2_EINVAL, "NULL argument");
+  if (nrhs < 1 || nrhs > 64) return fail(H2_EINVAL, "nrhs must be in [1, 64]");
+  if (count < 1) return fail(H2_EINVAL, "count must be at least 1");
+  H2_CUDA_TRY(cudaSetDevice(h->device));
+  int rc = ensure_work(*h, nrhs);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->d.n * nrhs * 8;
+  StreamWork &w = h->sw;
+  if ((rc = ensure_stream_work(w, bytes))) return rc;
+  // the copy streams start after everything already queued on the handle's stream
+  cudaEvent_t start = nullptr;
+  H2_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(start, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(w.in, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(w.out, start, 0);
+  cudaEventDestroy(start);
+  if (e != cudaSuccess) return cuda_fail(e, "h2_matvec_host_stream set-up");
+  for (int i = 0; i < count && !rc; ++i) {
+    const int b = i & 1;
+    const double *xi = x + (size_t)i * h->d.n * nrhs;
+    double *yi = y + (size_t)i * h->d.n * nrhs;
+    // block i in: once the product of block i - 2 has read the buffer
+    if (i >= 2) H2_CUDA_TRY(cudaStreamWaitEvent(w.in, w.ev_done[b], 0));
+    H2_CUDA_TRY(cudaMemcpyAsync(w.x[b], xi, bytes, cudaMemcpyHostToDevice, w.in));
+    H2_CUDA_TRY(cudaEventRecord(w.ev_in[b], w.in));
+    // the product of block i: its input has landed and block i - 2's result has left
+    H2_CUDA_TRY(cudaStreamWaitEvent(h->stream, w.ev_in[b], 0));
+    if (i >= 2) H2_CUDA_TRY(cudaStreamWaitEvent(h->stream, w.ev_out[b], 0));
+    rc = run_matvec(*h, w.x[b], w.y[b], nrhs, true);
+    if (rc) break;
+    H2_CUDA_TRY(cudaEventRecord(w.ev_done[b], h->stream));
+    // block i out
+    H2_CUDA_TRY(cudaStreamWaitEvent(w.out, w.ev_done[b], 0));
+    H2_CUDA_TRY(cudaMemcpyAsync(yi, w.y[b], bytes, cudaMemcpyDeviceToHost, w.out));
+    H2_CUDA_TRY(cudaEventRecord(w.ev_out[b], w.out));
+  }
+  H2_CUDA_TRY(cudaStreamSynchronize(w.in));
+  H2_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  H2_CUDA_TRY(cudaStreamSynchronize(w.out));
+  if (rc) return rc;
   return take_device_error(*h);
 }
 

@@ -191,8 +191,19 @@ struct GmresWork {
 };
 void free_gmres_work(GmresWork &w);
 
+// Buffers of h2_matvec_host_stream (grown on demand, freed with the handle):
+// two device block pairs, the input and output copy streams and the events
+// that order copies and products
+struct StreamWork {
+  size_t bytes = 0;
+  double *x[2] = {nullptr, nullptr}, *y[2] = {nullptr, nullptr};
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+};
+
 struct Ctx {
   double build_ms[H2_NBUILD] = {0};   // wall time of the build phases (h2_build_times)
+  StreamWork sw;                      // h2_matvec_host_stream
   GcaParams gp;                       // GCA-H^2 handles: construction parameters
   GmresWork gw;
   Prof prof;

@@ -130,6 +130,9 @@ typedef struct h2_stats {
                            * quadrature order and rank the largest padded rank of a level */
   int64_t coupling_entries; /* stored coupling entries (interpolation: adm_blocks x rank^2; GCA-H^2:
                            * the sum over levels of blocks x padded rank^2) */
+  int64_t tensor_leaf;    /* 1 if the tensor-core digits of the leaf bases were built (the leaf
+                           * forward step of Algorithm 1 on the tensor cores, FP64-accurate
+                           * handles with both tensor-core coupling and nearfield) */
 } h2_stats;
 
 /* Per right-hand side result of h2_solve. */

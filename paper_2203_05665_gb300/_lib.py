@@ -39,7 +39,7 @@ class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("n", "depth", "clusters", "leaf_max", "order", "rank", "adm_blocks", "near_blocks",
                  "near_entries", "first_adm_level", "device_bytes", "prec", "coupling", "tensor",
-                 "tensor_near", "basis_prec", "gca", "coupling_entries")]
+                 "tensor_near", "basis_prec", "gca", "coupling_entries", "tensor_leaf")]
 
 
 class GcaOptions(C.Structure):

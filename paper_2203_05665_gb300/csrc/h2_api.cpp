@@ -53,7 +53,7 @@ static void free_dev(Dev &d) {
   if (d.fbar) cudaFree(d.fbar);
   if (d.grank) cudaFree(d.grank);
   if (d.gpiv) cudaFree(d.gpiv);
-  void *ptrs[] = {d.Ntc, d.xnt, d.ntc_E, d.ntc_xmax, d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.colmax, d.nself, d.near_ptr2, d.self_ptr, d.near_col2, d.near_blk2, d.self_col, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
+  void *ptrs[] = {d.Vtc, d.tcv_E, d.Ntc, d.xnt, d.ntc_E, d.ntc_xmax, d.Stc, d.xtc, d.tc_E, d.tc_xmax, d.icen, d.adm_dc, d.ihalf, d.colmax, d.nself, d.near_ptr2, d.self_ptr, d.near_col2, d.near_blk2, d.self_col, d.vscale, d.nscale, d.pad_src, d.V, d.Vt, d.Ef,      d.S,       d.near, d.adm_ptr, d.adm_col, d.near_ptr,
                   d.near_col, d.cheb, d.xpad, d.ypad, d.xhat, d.yhat, d.io_x,    d.io_y};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -378,6 +378,7 @@ int h2_info(h2_handle h, h2_stats *out) {
   out->coupling = h->d.coupling == 1 ? H2_COUPLING_REGEN : H2_COUPLING_STORED;
   out->tensor = h->d.tc ? 1 : 0;
   out->tensor_near = h->d.ntc ? 1 : 0;
+  out->tensor_leaf = h->d.Vtc ? 1 : 0;
   out->basis_prec = h->d.v32 ? H2_F32 : h->d.prec;
   out->gca = h->d.gca ? 1 : 0;
   out->coupling_entries = h->d.gca ? h->d.coupling_entries : (int64_t)p.adm_col.size() * p.k * p.k;

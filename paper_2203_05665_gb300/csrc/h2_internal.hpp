@@ -129,6 +129,11 @@ struct Dev {
   int32_t *ntc_E = nullptr;
   unsigned *ntc_xmax = nullptr;
   uint32_t ntc_ablk = 0;
+  // tensor-core leaf forward step: the ten E4M3 digit planes of every V_t^T
+  // ([leaf][10][64 x 32] bytes, K-major core matrices) and their row powers
+  // of two [leaf][64]
+  void *Vtc = nullptr;
+  int32_t *tcv_E = nullptr;
   unsigned long long *colmax = nullptr;   // H2_F64: 64 column maxima of x (range guard of double-float)
   bool v32 = false;             // 16-bit handle whose V, Vt and transfer factors are stored in FP32
   float *vscale = nullptr;      // per leaf: power of two dividing the stored V (FP16), or NULL
@@ -240,7 +245,12 @@ int tc_coupling(Ctx &c, const void *xhat, void *yhat, int rp);
 int tc_take_error(cudaStream_t st);
 bool ntc_eligible(const Dev &d);
 int ntc_build(Ctx &c, const int32_t *nrow_dev);
-int ntc_near(Ctx &c, const void *xpad, void *ypad, int rp, int accumulate, int64_t *launches);
+int ntc_near(Ctx &c, const void *xpad, void *ypad, int rp, int accumulate, int64_t *launches,
+             bool have_input = false);
+// input column maxima and digit planes per leaf (nearfield, tensor-core leaf step)
+int ntc_input(Ctx &c, const void *xpad, int rp, int64_t *launches);
+// leaf forward step on the tensor cores (after ntc_input); requires d.Vtc
+int tc_leaf_forward(Ctx &c, void *xhat, int rp);
 
 // h2_build for a given kernel (h2_api.cpp)
 int build_handle(const double *vert, int64_t nv, const int32_t *tri, int64_t nt, int leaf_size, double eta, int order,

@@ -1092,7 +1092,15 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   mk.mark(H2_PH_LEAF_FORWARD);
   // leaf steps with one CTA per leaf when the stored values are in the arithmetic type
   const bool leaf_reg = L <= 32 && k <= 64 && rp <= 16;
-  if (far && leaf_reg) {
+  // FP64-accurate with the tensor-core nearfield and coupling: the leaf
+  // forward step from the input digits the nearfield reads anyway
+  const bool leaf_tc = std::is_same<T, dd>::value && far && d.ntc && d.Vtc && rp <= 16;
+  if (leaf_tc) {
+    int64_t nl = 0;
+    if ((rc = ntc_input(c, xpad, rp, &nl))) return rc;
+    if ((rc = tc_leaf_forward(c, xhat, rp))) return rc;
+    mk.count(H2_PH_LEAF_FORWARD, nl + 1);
+  } else if (far && leaf_reg) {
     const size_t sm = (size_t)L * (kp + rp) * sizeof(T);
     k_leaf_fwd_reg<TV, T><<<(unsigned)d.nleaf, 256, sm, st>>>((const TV *)d.V, xpad, vscale, L, kp, k, rp,
                                                              xhat + leaf0 * (int64_t)k * rp);
@@ -1116,7 +1124,11 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
     for (int l = D - 1; l >= lmin; --l) {
       const int64_t np = (int64_t)1 << l;
       const dim3 grid((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16);
-      if (m == 4) k_up_reg<TE, T, 4><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
+      const dim3 grid2((unsigned)((np + kSplitParents - 1) / kSplitParents), (rp + 15) / 16);
+      if (np <= kUpSplitMax) {
+        if (m == 4) k_up_split<TE, T, 4><<<grid2, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
+        else k_up_split<TE, T, 3><<<grid2, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
+      } else if (m == 4) k_up_reg<TE, T, 4><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
       else k_up_reg<TE, T, 3><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, xhat, nullptr);
       mk.count(H2_PH_UPWARD);
     }
@@ -1167,9 +1179,9 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   if (far && (m == 3 || m == 4)) {
     for (int l = lmin; l < D; ++l) {
       const int64_t np = (int64_t)1 << l;
-      const dim3 grid((unsigned)((np + kRegParents - 1) / kRegParents), (rp + 15) / 16);
-      if (m == 4) k_down_reg<TE, T, 4><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, yhat);
-      else k_down_reg<TE, T, 3><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, yhat);
+      const dim3 grid((unsigned)((np + kSplitParents - 1) / kSplitParents), (rp + 15) / 16);
+      if (m == 4) k_down_split<TE, T, 4><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, yhat);
+      else k_down_split<TE, T, 3><<<grid, 256, 0, st>>>((const TE *)d.Ef, rp, np - 1, np, yhat);
       mk.count(H2_PH_DOWNWARD);
     }
   } else if (far) {
@@ -1199,7 +1211,7 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   if (std::is_same<T, dd>::value && d.ntc && rp <= 16) {
     // FP64-accurate: integer digits on the tensor cores
     int64_t nl = 0;
-    if ((rc = ntc_near(c, xpad, ypad, rp, far ? 1 : 0, &nl))) return rc;
+    if ((rc = ntc_near(c, xpad, ypad, rp, far ? 1 : 0, &nl, leaf_tc))) return rc;
     mk.count(H2_PH_LEAF_NEAR, nl);
   } else if (d.nself) {
     // bfloat16: the blocks of other leaves, then the self blocks G_jj in FP32

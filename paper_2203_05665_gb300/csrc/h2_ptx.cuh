@@ -100,6 +100,20 @@ __device__ __forceinline__ bool named_sync_or(uint32_t nthreads, int flag) {
   return res != 0;
 }
 
+// the same on named barrier id
+__device__ __forceinline__ bool named_sync_or_id(uint32_t id, uint32_t nthreads, int flag) {
+  uint32_t res;
+  asm volatile(
+      "{\n\t.reg .pred q, p;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, %3, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(res)
+      : "r"(flag), "r"(nthreads), "r"(id)
+      : "memory");
+  return res != 0;
+}
+
 // bytes must be a multiple of 16; both addresses 16-byte aligned
 __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
   asm volatile(

@@ -83,15 +83,22 @@ constexpr uint32_t kSliceB = kTcN * kTcK;              // 1024 bytes: one digit 
 // five sums of at most 2^20 each), an accumulator set is 16 ND columns wide
 // (160 or 96) and kSets sets rotate, so that the MMAs of the next row segment
 // run while the epilogue reads the previous one.
-template <int ND>
+//
+// KB is the contraction length of one block in bytes: 64 for the coupling
+// matrices (two MMA K steps), 32 for the leaf bases V_t^T of the leaf forward
+// step (the L <= 32 triangles of a leaf, zero padded; one K step).
+template <int ND, int KB = kTcK>
 struct Dig {
   static constexpr int kFix = 5 * ND - 1;
   static constexpr int kTop = ND + 1;
   static constexpr int kGroups = ND / 2;
-  static constexpr uint32_t kTileA = ND * kSliceA;
-  static constexpr uint32_t kTileB = ND * kSliceB;
+  static constexpr int kKSteps = KB / 32;
+  static constexpr uint32_t kPlaneA = kTcK * KB;   // one digit plane of a block: 64 rows x KB
+  static constexpr uint32_t kPlaneB = kTcN * KB;   // one digit plane of the coefficients: 16 rows x KB
+  static constexpr uint32_t kTileA = ND * kPlaneA;
+  static constexpr uint32_t kTileB = ND * kPlaneB;
   static constexpr uint32_t kStage = kTileA + kTileB;
-  static constexpr int kStages = ND == 10 ? 4 : 6;
+  static constexpr int kStages = (ND == 10 ? 4 : 6) * (kTcK / KB);
   static constexpr uint32_t kW = kTcN * ND;      // columns of an accumulator set
   static constexpr int kSets = 3;
   __host__ __device__ static constexpr int nx(int g) { return ND - 2 * g; }
@@ -101,10 +108,14 @@ static_assert(Dig<10>::kSets * Dig<10>::kW <= 512 && Dig<6>::kSets * Dig<6>::kW 
 constexpr uint32_t kTmemCols = 512;      // the accumulator sets
 constexpr int kTcThreads = 192;          // producer, MMA, four epilogue warps
 constexpr uint32_t kXch = 64 * kTcN * 8; // epilogue exchange: 64 rows x 16 double-float values
-template <int ND>
-__host__ __device__ constexpr uint32_t tc_bar_off() { return Dig<ND>::kStages * Dig<ND>::kStage + kXch; }
-template <int ND>
-__host__ __device__ constexpr uint32_t tc_smem() { return tc_bar_off<ND>() + 24 * 8 + 16; }
+// EG: epilogue warp groups (2 for one-block rows, whose epilogue is not
+// hidden behind the MMAs of many blocks), each with its own exchange area
+template <int ND, int KB = kTcK, int EG = 1>
+__host__ __device__ constexpr uint32_t tc_bar_off() {
+  return Dig<ND, KB>::kStages * Dig<ND, KB>::kStage + EG * kXch;
+}
+template <int ND, int KB = kTcK, int EG = 1>
+__host__ __device__ constexpr uint32_t tc_smem() { return tc_bar_off<ND, KB, EG>() + 40 * 8 + 16; }
 
 // instruction descriptor of tcgen05.mma kind::f8f6f4: D FP32 (bits 4-5 =
 // 1), A and B E4M3 (bits 7-9 = 0, bits 10-12 = 0), both K-major (bits 15, 16
@@ -127,6 +138,12 @@ __host__ __device__ __forceinline__ int core_off(int r, int c) {
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
          (1ull << 46);
+}
+// the same for rows of KB contraction bytes (the next 8 rows 8 KB bytes on)
+template <int KB>
+__device__ __forceinline__ uint64_t sdesc_kb(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)((8u * KB) >> 4) << 32) | (1ull << 46);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -161,20 +178,22 @@ __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.syn
 
 // Column indices of the blocks a producer streams, loaded 8 blocks ahead so
 // that the address of a bulk copy never waits on a global load.
+// Without a column array (col = NULL) block e lies in column e.
 struct ColAhead {
   const int32_t *col;
   int64_t end;
   int32_t c[8];
+  __device__ __forceinline__ int32_t at(int64_t e) const { return col ? col[e] : (int32_t)e; }
   __device__ __forceinline__ ColAhead(const int32_t *cl, int64_t e0, int64_t e1) : col(cl), end(e1) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] = e0 + u < e1 ? col[e0 + u] : 0;
+    for (int u = 0; u < 8; ++u) c[u] = e0 + u < e1 ? at(e0 + u) : 0;
   }
   // the column of block e; afterwards block e + 8 is in flight
   __device__ __forceinline__ int32_t next(int64_t e) {
     const int32_t v = c[0];
 #pragma unroll
     for (int u = 0; u < 7; ++u) c[u] = c[u + 1];
-    c[7] = e + 8 < end ? col[e + 8] : 0;
+    c[7] = e + 8 < end ? at(e + 8) : 0;
     return v;
   }
 };
@@ -351,23 +370,33 @@ __device__ __forceinline__ dd dd_scale(dd v, int e) {
 // in [0, nrows); each CTA takes a contiguous range of rows holding about
 // 1/gridDim of the blocks.
 // T: the coefficient type (dd with ND = 10, float with ND = 6).
+// DIAG: row r holds the single block r in column r (ptr = col = NULL), its
+// row powers of two are E[r][nu] and the column powers xmax[j] (one level):
+// the leaf forward step x^_t = V_t^T x|t with KB = 32, the V_t^T digit
+// planes as the blocks and the input digit planes of leaf t as the
+// coefficients.  Two epilogue warp groups then take alternate rows, and two
+// neighbouring digit levels are combined exactly in FP32 before entering
+// double-float: a level sum of one block is at most 5 x 32 x 16^2 < 2^15.4,
+// so 32 D_L + D_(L+1) < 2^21.
 __device__ __forceinline__ dd to_dd(dd v) { return v; }
 __device__ __forceinline__ dd to_dd(float v) { return dd{v, 0.0f}; }
 __device__ __forceinline__ void store_as(dd v, dd *p) { *p = v; }
 __device__ __forceinline__ void store_as(dd v, float *p) { *p = v.hi + v.lo; }
 
-template <int ND, class T>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <int ND, class T, int KB = kTcK, bool DIAG = false>
+__global__ void __launch_bounds__(DIAG ? 64 + 2 * 128 : kTcThreads, 1)
     k_coupling_tc(const unsigned char *__restrict__ Stc, const unsigned char *__restrict__ xtc,
                   const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const int32_t *__restrict__ E,
                   const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, T *__restrict__ yhat) {
-  using D = Dig<ND>;
+  using D = Dig<ND, KB>;
+  // first block of row t (t = row0 + r); one block per row without ptr
+  auto pt = [&](int64_t t) -> int64_t { return DIAG ? t - row0 : ptr[t]; };
   constexpr int kTcStages = D::kStages, kTcGroups = D::kGroups;
   constexpr uint32_t kStage = D::kStage, kTileA = D::kTileA, kTileB = D::kTileB;
   extern __shared__ __align__(1024) unsigned char smem[];
   dd *xch = reinterpret_cast<dd *>(smem + kTcStages * kStage);
   constexpr int kSets = D::kSets;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + tc_bar_off<ND>());
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + tc_bar_off<ND, KB, DIAG ? 2 : 1>());
   uint64_t *empty = full + kTcStages;
   uint64_t *accf = empty + kTcStages;   // [kSets]: the MMAs of a segment have completed
   uint64_t *acce = accf + kSets;        // [kSets]: the epilogue has read the set
@@ -377,21 +406,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // rows of this CTA: from the first row whose blocks start at or after its share
-  const int64_t b_all0 = ptr[row0], total = ptr[row0 + nrows] - b_all0;
+  const int64_t b_all0 = pt(row0), total = pt(row0 + nrows) - b_all0;
   auto row_at = [&](int64_t w) -> int64_t {
     if (w >= (int64_t)gridDim.x) return nrows;
     const int64_t target = total * w / gridDim.x;
     int64_t lo = 0, hi = nrows;
     while (lo < hi) {
       const int64_t mid = (lo + hi) / 2;
-      if (ptr[row0 + mid] - b_all0 >= target) hi = mid;
+      if (pt(row0 + mid) - b_all0 >= target) hi = mid;
       else lo = mid + 1;
     }
     return lo;
   };
   const int64_t r_begin = blockIdx.x == 0 ? 0 : row_at(blockIdx.x);
   const int64_t r_end = row_at(blockIdx.x + 1);
-  const int64_t e_begin = ptr[row0 + r_begin], e_end = ptr[row0 + r_end];
+  const int64_t e_begin = pt(row0 + r_begin), e_end = pt(row0 + r_end);
 
   if (tid == 0) {
     for (int s = 0; s < kTcStages; ++s) {
@@ -436,7 +465,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const unsigned char *src = Stc + e * (int64_t)kTileA;
 #pragma unroll
         for (int g = 0; g < kTcGroups; ++g)
-          bulk_g2s_hint(st + 2 * g * kSliceA, src + 2 * g * kSliceA, 2 * kSliceA, &full[s], pol_stream);
+          bulk_g2s_hint(st + 2 * g * D::kPlaneA, src + 2 * g * D::kPlaneA, 2 * D::kPlaneA, &full[s], pol_stream);
       }
       if (*abort) {
         // let the copies in flight land before the CTA leaves (bounded)
@@ -453,10 +482,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       int64_t i = 0, q = 0;
       bool ok = true;
-      int64_t pnext = ptr[row0 + r_begin];   // row pointers loaded one row ahead
+      int64_t pnext = pt(row0 + r_begin);   // row pointers loaded one row ahead
       for (int64_t r = r_begin; r < r_end && ok; ++r) {
         const int64_t b0 = pnext;
-        pnext = ptr[row0 + r + 1];
+        pnext = pt(row0 + r + 1);
         const int64_t nb = pnext - b0;
         for (int64_t s0 = 0; s0 < nb && ok; s0 += kTcSegBlocks, ++q) {
           // accumulator set q mod kSets is free once the epilogue has read its previous use
@@ -481,12 +510,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // first MMA of a segment overwrites the set and all later ones accumulate.
             // K steps (32 bytes, two core matrices) outermost.
             const uint32_t A0 = smem_u32(smem + (size_t)s * kStage), B0 = A0 + kTileA;
-            const uint64_t dA = sdesc(A0), dB = sdesc(B0);
+            const uint64_t dA = sdesc_kb<KB>(A0), dB = sdesc_kb<KB>(B0);
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk)
+            for (int kk = 0; kk < D::kKSteps; ++kk)
 #pragma unroll
               for (int g = 0; g < kTcGroups; ++g)
-                tc_mma(dset + D::col(g), dA + (uint64_t)((2 * g * kSliceA + kk * 256) >> 4),
+                tc_mma(dset + D::col(g), dA + (uint64_t)((2 * g * D::kPlaneA + kk * 256) >> 4),
                        dB + (uint64_t)(kk * 16), tc_idesc(kTcN * D::nx(g)), (t > 0 || kk > 0 || g > 0) ? 1u : 0u);
             tc_commit(&empty[s]);   // the stage is free once these MMAs have read it
           }
@@ -498,13 +527,77 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_wait_bounded(done, 0);
     }
     __syncwarp();
+  } else if (DIAG) {
+    // ---------------- one-block rows: warps 2-5 (group 0) and 6-9 (group 1)
+    // take alternate rows; each reads tensor-memory lanes 32 (warp % 4) ..
+    const int grp = (warp - 2) >> 2;
+    const int quad = warp & 3, tl = quad * 32 + lane, half = tl >> 6, nu = tl & 63;
+    dd *xg = xch + grp * (64 * kTcN);
+    const uint32_t bar_or = 1 + 2 * grp, bar_x = 2 + 2 * grp;
+    int cx[kTcN];
+#pragma unroll
+    for (int j = 0; j < kTcN; ++j) cx[j] = tc_colexp(xmax[j]);
+    int64_t r = r_begin + grp;
+    int Enext = r < r_end ? E[r * kTcK + nu] : 0;   // the row's powers, loaded a row ahead
+    for (; r < r_end; r += 2) {
+      const int64_t q = r - r_begin, t = row0 + r;
+      const int Er = Enext;
+      if (r + 2 < r_end) Enext = E[(r + 2) * kTcK + nu];
+      T *yrow = yhat + (t * kTcK + nu) * rp;
+      const int set = (int)(q % kSets);
+      const bool ready = !*abort && mbar_wait_or_abort(&accf[set], (uint32_t)((q / kSets) & 1), abort);
+      if (named_sync_or_id(bar_or, 128, ready ? 0 : 1)) break;
+      tc_fence_after();
+      dd acc[kTcN];
+#pragma unroll
+      for (int j = 0; j < kTcN; ++j) acc[j] = dd{0.0f, 0.0f};
+      // column block c holds level L = c + 2 + half; blocks c, c + 1 combine as
+      // (32 D_L + D_(L+1)) 2^(2 - 5 (L + 1)), in increasing L
+      const uint32_t tset = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * D::kW;
+#pragma unroll
+      for (int c0 = 0; c0 < ND; c0 += 6) {
+        uint32_t raw[6][16];
+#pragma unroll
+        for (int u = 0; u < 6; ++u)
+          if (c0 + u < ND) tmem_ld16_nw(tset + (uint32_t)((c0 + u) * kTcN), raw[u]);
+        tmem_wait();
+#pragma unroll
+        for (int u = 0; u < 6; u += 2) {
+          const int L = c0 + u + 2 + half;
+          if (c0 + u < ND && L <= D::kTop) {
+            const float w = pow2f(2 - 5 * (L + 1));
+            const float c1 = L + 1 <= D::kTop ? 1.0f : 0.0f;
+#pragma unroll
+            for (int j = 0; j < kTcN; ++j) {
+              const float v = 32.0f * __uint_as_float(raw[u][j]) + c1 * __uint_as_float(raw[u + 1][j]);
+              acc[j] = acc[j] + dd{v * w, 0.0f};
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[set]);
+      if (half == 1)
+#pragma unroll
+        for (int j = 0; j < kTcN; ++j) xg[j * 64 + nu] = acc[j];
+      named_sync_id(bar_x, 128);
+      if (half == 0) {
+#pragma unroll
+        for (int j = 0; j < kTcN; ++j) {
+          if (j >= rp) break;
+          store_as(dd_scale(acc[j] + xg[j * 64 + nu], Er + cx[j]), yrow + j);
+        }
+      }
+      named_sync_id(bar_x, 128);
+    }
   } else {
     // ---------------- epilogue: warps 2-5 read tensor-memory lanes 32 (warp % 4) ..
     const int quad = warp & 3, tl = quad * 32 + lane, half = tl >> 6, nu = tl & 63;
     int64_t q = 0;
     for (int64_t r = r_begin; r < r_end; ++r) {
       const int64_t t = row0 + r;
-      const int64_t nb = ptr[t + 1] - ptr[t];
+      const int64_t nb = pt(t + 1) - pt(t);
       T *yrow = yhat + (t * kTcK + nu) * rp;
       if (nb == 0) {
         if (half == 0)
@@ -703,6 +796,52 @@ __global__ void __launch_bounds__(128) k_ntc_slice_x(const dd *__restrict__ xpad
   __syncthreads();
   for (int w = threadIdx.x; w < (int)(kNtX / 16); w += blockDim.x)
     reinterpret_cast<uint4 *>(xnt + s * (int64_t)kNtX)[w] = reinterpret_cast<const uint4 *>(tile)[w];
+}
+
+// Leaf forward step on the tensor cores (Algorithm 1 at the leaves,
+// x^_t = V_t^T x|t, FP64-accurate handles of order 4 with leaves of at most
+// 32 triangles): the blocks are V_t^T (64 rows nu, the leaf's triangles r as
+// the contraction index, zero padded to 32 bytes), cut once into the ten
+// digit planes of the coupling with a power of two per row,
+// Ev[t][nu] = 1 + floor(log2 max_r |V_t[r][nu]|); the coefficients are the
+// input digit planes of leaf t that the nearfield cuts (k_ntc_slice_x).
+__global__ void k_tcv_rowexp(const dd *__restrict__ V, int64_t nleaf, int L, int kp, int32_t *__restrict__ Ev) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nleaf * kTcK) return;
+  const int64_t t = e / kTcK;
+  const int nu = (int)(e % kTcK);
+  float mx = 0.0f;
+  for (int r = 0; r < L; ++r) mx = fmaxf(mx, fabsf(V[(t * L + r) * kp + nu].hi));
+  Ev[e] = mx > 0.0f ? ilogbf(mx) + 1 : 0;
+}
+
+// the ten digit planes of V_t^T, row nu, contraction indices 16 cg .. 16 cg + 15
+__global__ void k_tcv_slice(const dd *__restrict__ V, const int32_t *__restrict__ Ev, int64_t nleaf, int L, int kp,
+                            unsigned char *__restrict__ Vtc) {
+  using D = Dig<kTcSlices, 32>;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nleaf * kTcK * 2) return;
+  const int64_t t = e / (kTcK * 2);
+  const int nu = (int)((e / 2) % kTcK), cg = (int)(e % 2);
+  const int sc = kTcFixBits - Ev[t * kTcK + nu];
+  __align__(16) unsigned char out[kTcSlices][16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int r = 16 * cg + q;
+    long long X = 0;
+    if (r < L) {
+      const dd v = V[(t * L + r) * kp + nu];
+      X = llrint(ldexp((double)v.hi + (double)v.lo, sc));
+    }
+    int sl[kTcSlices];
+    split_digits(X, sl);
+#pragma unroll
+    for (int i = 0; i < kTcSlices; ++i) out[i][q] = e4m3(sl[i]);
+  }
+  unsigned char *base = Vtc + t * (int64_t)D::kTileA + core_off32(nu, 16 * cg);
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i)
+    *reinterpret_cast<uint4 *>(base + i * D::kPlaneA) = *reinterpret_cast<const uint4 *>(out[i]);
 }
 
 // The nearfield kernel: rows t in [0, nrows) (leaves), each CTA a contiguous
@@ -984,9 +1123,11 @@ int tc_build_nd(Ctx &c, const int32_t *arow_dev) {
 }
 
 // Upward pass of a product on the tensor-core path: the transfers of
-// Algorithm 1, each level's column maxima taken on the way (k_up_reg; the
-// leaves' by k_tc_levmax), then the coefficient digits of every far-field
-// level in one launch (k_tc_slice_x, each cluster with its level's maxima).
+// Algorithm 1, each level's column maxima taken on the way (k_up_reg /
+// k_up_split; the leaves' by k_tc_levmax), then the coefficient digits of
+// every far-field level in one launch (k_tc_slice_x, each cluster with its
+// level's maxima).  Cutting a level's digits inside the next level's
+// transfer launch was slower: the transfer threads are latency bound.
 // Returns the launches made.
 template <class T, int ND>
 int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
@@ -1003,8 +1144,12 @@ int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
   for (int l = D - 1; l >= lmin; --l) {
     // level l from level l + 1, with the column maxima of level l
     const int64_t np = (int64_t)1 << l;
-    k_up_reg<T, T, 4><<<(unsigned)((np + kRegParents - 1) / kRegParents), 256, 0, st>>>(
-        (const T *)d.Ef, rp, np - 1, np, xhat, d.tc_xmax + l * kTcN);
+    if (np <= kUpSplitMax)
+      k_up_split<T, T, 4><<<(unsigned)((np + kSplitParents - 1) / kSplitParents), 256, 0, st>>>(
+          (const T *)d.Ef, rp, np - 1, np, xhat, d.tc_xmax + l * kTcN);
+    else
+      k_up_reg<T, T, 4><<<(unsigned)((np + kRegParents - 1) / kRegParents), 256, 0, st>>>(
+          (const T *)d.Ef, rp, np - 1, np, xhat, d.tc_xmax + l * kTcN);
     ++nl;
   }
   // the digits of every level at once (all maxima are complete)
@@ -1082,17 +1227,27 @@ int ntc_build(Ctx &c, const int32_t *nrow_dev) {
   k_ntc_slice<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>((const dd *)d.near, nrow_dev, d.ntc_E, d.nnear, L, Lp,
                                                             ablk, (unsigned char *)d.Ntc);
   H2_CUDA_TRY(cudaGetLastError());
+  if (d.tc && d.tc_nd == kTcSlices && d.k == kTcK && d.kp == kTcK && L <= 32) {
+    // the V_t^T digit planes of the tensor-core leaf forward step
+    using DV = Dig<kTcSlices, 32>;
+    if ((rc = dev_alloc(d, (void **)&d.tcv_E, sizeof(int32_t) * (size_t)d.nleaf * kTcK))) return rc;
+    if ((rc = dev_alloc(d, &d.Vtc, (size_t)d.nleaf * DV::kTileA))) return rc;
+    const int64_t nv = d.nleaf * kTcK;
+    k_tcv_rowexp<<<(unsigned)((nv + 127) / 128), 128, 0, st>>>((const dd *)d.V, d.nleaf, L, (int)d.kp, d.tcv_E);
+    k_tcv_slice<<<(unsigned)((2 * nv + 255) / 256), 256, 0, st>>>((const dd *)d.V, d.tcv_E, d.nleaf, L, (int)d.kp,
+                                                                  (unsigned char *)d.Vtc);
+    H2_CUDA_TRY(cudaGetLastError());
+  }
   H2_CUDA_TRY(cudaStreamSynchronize(st));
   d.ntc_ablk = ablk;
   d.ntc = true;
   return H2_OK;
 }
 
-// the nearfield phase on the tensor cores: the input's column maxima, its
-// digit planes per leaf, then the block rows (y_pad += or = the near sums)
-int ntc_near(Ctx &c, const void *xpad_v, void *ypad_v, int rp, int accumulate, int64_t *launches) {
+// the input's column maxima and its digit planes per leaf (read by the
+// nearfield and by the tensor-core leaf forward step)
+int ntc_input(Ctx &c, const void *xpad_v, int rp, int64_t *launches) {
   const dd *xpad = static_cast<const dd *>(xpad_v);
-  dd *ypad = static_cast<dd *>(ypad_v);
   Dev &d = c.d;
   cudaStream_t st = c.stream;
   if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core nearfield takes at most 16 right-hand sides");
@@ -1101,6 +1256,44 @@ int ntc_near(Ctx &c, const void *xpad_v, void *ypad_v, int rp, int accumulate, i
   const int64_t rows = d.nleaf * L;
   k_tc_levmax<dd><<<levmax_grid(rows), 256, 0, st>>>(xpad, rows, rp, d.ntc_xmax);
   k_ntc_slice_x<<<(unsigned)d.nleaf, 128, 0, st>>>(xpad, L, rp, d.ntc_xmax, (unsigned char *)d.xnt);
+  H2_CUDA_TRY(cudaGetLastError());
+  if (launches) *launches = 2;
+  return H2_OK;
+}
+
+// the leaf forward step on the tensor cores: x^ of the leaf clusters from the
+// input digits (ntc_input) and the stored V_t^T digits
+int tc_leaf_forward(Ctx &c, void *xhat_v, int rp) {
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  if (rp > kTcN || !d.Vtc) return fail(H2_EINVAL, "no tensor-core leaf forward step for this handle");
+  constexpr int KB = 32;
+  constexpr uint32_t sm = tc_smem<kTcSlices, KB, 2>();
+  static_assert(sm <= 227 * 1024, "tensor-core leaf step does not fit in shared memory");
+  H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_coupling_tc<kTcSlices, dd, KB, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024)));
+  int sms = 0, dev = 0;
+  H2_CUDA_TRY(cudaGetDevice(&dev));
+  H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = (int)std::min<int64_t>(sms, d.nleaf);
+  k_coupling_tc<kTcSlices, dd, KB, true><<<grid, 64 + 2 * 128, sm, st>>>(
+      (const unsigned char *)d.Vtc, (const unsigned char *)d.xnt, nullptr, nullptr, d.tcv_E, d.ntc_xmax,
+      d.nleaf - 1, d.nleaf, rp, static_cast<dd *>(xhat_v));
+  H2_CUDA_TRY(cudaGetLastError());
+  return H2_OK;
+}
+
+// the nearfield phase on the tensor cores: the input's column maxima, its
+// digit planes per leaf, then the block rows (y_pad += or = the near sums)
+int ntc_near(Ctx &c, const void *xpad_v, void *ypad_v, int rp, int accumulate, int64_t *launches, bool have_input) {
+  dd *ypad = static_cast<dd *>(ypad_v);
+  Dev &d = c.d;
+  cudaStream_t st = c.stream;
+  if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core nearfield takes at most 16 right-hand sides");
+  const int L = (int)d.lmax;
+  int64_t nin = 0;
+  int rc;
+  if (!have_input && (rc = ntc_input(c, xpad_v, rp, &nin))) return rc;
   H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(227 * 1024)));
   int sms = 0, dev = 0;
@@ -1111,7 +1304,7 @@ int ntc_near(Ctx &c, const void *xpad_v, void *ypad_v, int rp, int accumulate, i
                                                (const unsigned char *)d.xnt, d.near_ptr, d.near_col, d.ntc_E,
                                                d.ntc_xmax, d.nleaf, L, rp, accumulate, ypad);
   H2_CUDA_TRY(cudaGetLastError());
-  if (launches) *launches = 3;
+  if (launches) *launches = nin + 1;
   return H2_OK;
 }
 

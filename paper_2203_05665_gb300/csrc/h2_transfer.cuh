@@ -203,73 +203,18 @@ __device__ __forceinline__ T modem_out(const T *F, const T (&in)[M], int a) {
 }
 
 // the transfer factors of the children of this CTA's parents: F[q][ch][axis][M x M]
-template <class TS, class T, int M>
+template <class TS, class T, int M, int P = kRegParents>
 __device__ __forceinline__ void load_factors(const TS *__restrict__ Ef, int64_t par0, int64_t npar,
                                              T (*F)[2][3][M * M]) {
   constexpr int kPer = 6 * M * M, kChild = 3 * M * M;
-  for (int i = threadIdx.x; i < kRegParents * kPer; i += blockDim.x) {
+  for (int i = threadIdx.x; i < P * kPer; i += blockDim.x) {
     const int q = i / kPer, o = i % kPer;
-    const int64_t pi = (int64_t)blockIdx.x * kRegParents + q;
+    const int64_t pi = (int64_t)blockIdx.x * P + q;
     const int64_t pp = par0 + pi;
     F[q][o / kChild][(o % kChild) / (M * M)][o % (M * M)] =
         pi < npar ? to_compute<T>(Ef[(2 * pp + 1) * kChild + o]) : zero_of<T>();
   }
   __syncthreads();
-}
-
-// Downward (Algorithm 2): y^_c += E_c y^_parent for both children of parents
-// par0 .. par0 + npar - 1.
-template <class TS, class T, int M>
-__global__ void __launch_bounds__(256, 2) k_down_reg(const TS *__restrict__ Ef, int rp, int64_t par0, int64_t npar,
-                                                     T *__restrict__ yhat) {
-  constexpr int K = M * M * M;
-  __shared__ T F[kRegParents][2][3][M * M];
-  load_factors<TS, T, M>(Ef, par0, npar, F);
-  const int pl = threadIdx.x >> 6, t = threadIdx.x & 63, j = (t >> 2) + 16 * blockIdx.y, jz = t & 3;
-  const int64_t pi = (int64_t)blockIdx.x * kRegParents + pl, par = par0 + pi;
-  const bool act = pi < npar && j < rp && jz < M;
-  const int base = (threadIdx.x & 31) & ~3;
-  const int zq = jz < M ? jz : 0;   // the idle fourth lane of m = 3 computes a copy of lane 0
-  T v[M][M];
-#pragma unroll
-  for (int jy = 0; jy < M; ++jy)
-#pragma unroll
-    for (int jx = 0; jx < M; ++jx) v[jy][jx] = act ? yhat[(par * K + jx + M * jy + M * M * jz) * rp + j] : zero_of<T>();
-#pragma unroll 1
-  for (int ch = 0; ch < 2; ++ch) {
-    const T *Fx = F[pl][ch][0], *Fy = F[pl][ch][1], *Fz = F[pl][ch][2];
-    const int64_t c = 2 * par + 1 + ch;
-    // the child's current values, loaded before the arithmetic
-    T yc[M][M];
-#pragma unroll
-    for (int jy = 0; jy < M; ++jy)
-#pragma unroll
-      for (int jx = 0; jx < M; ++jx)
-        yc[jy][jx] = act ? yhat[(c * K + jx + M * jy + M * M * jz) * rp + j] : zero_of<T>();
-    T a[M][M], b[M][M];
-#pragma unroll
-    for (int jy = 0; jy < M; ++jy)
-#pragma unroll
-      for (int jx = 0; jx < M; ++jx) a[jy][jx] = modem_out<T, false, M>(Fx, v[jy], jx);
-#pragma unroll
-    for (int jx = 0; jx < M; ++jx) {
-      T col[M];
-#pragma unroll
-      for (int jy = 0; jy < M; ++jy) col[jy] = a[jy][jx];
-#pragma unroll
-      for (int jy = 0; jy < M; ++jy) b[jy][jx] = modem_out<T, false, M>(Fy, col, jy);
-    }
-#pragma unroll
-    for (int jy = 0; jy < M; ++jy)
-#pragma unroll
-      for (int jx = 0; jx < M; ++jx) {
-        T in[M];
-#pragma unroll
-        for (int q = 0; q < M; ++q) in[q] = shfl_t(b[jy][jx], base + q);
-        const T r = modem_out<T, false, M>(Fz, in, zq);
-        if (act) yhat[(c * K + jx + M * jy + M * M * jz) * rp + j] = yc[jy][jx] + r;
-      }
-  }
 }
 
 // Upward (Algorithm 1): x^_parent = sum over both children of E_c^T x^_c.
@@ -338,6 +283,138 @@ __global__ void __launch_bounds__(256, 2) k_up_reg(const TS *__restrict__ Ef, in
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
     if (act && jz == 0 && mx > 0.0f) atomicMax(&loc[j & 15], __float_as_uint(mx));
+    __syncthreads();
+    if (threadIdx.x < 16 && loc[threadIdx.x]) atomicMax(&xmax[threadIdx.x], loc[threadIdx.x]);
+  }
+}
+
+// Child-split variants: 128 threads per parent, the two 64-thread halves
+// taking one child each (two parents per 256-thread CTA), so every thread
+// forms half the mode products.  On levels with few parents a CTA's time is
+// the latency of one thread's chain of double-float operations, which this
+// halves.  The upward step adds the second child's part to the first through
+// shared memory in the order of k_up_reg (same bits).
+//
+// Downward (Algorithm 2): y^_c += E_c y^_parent for both children of parents
+// par0 .. par0 + npar - 1, the children independent.
+constexpr int kSplitParents = 2;   // parents per 256-thread CTA
+// upward levels of at most this many parents take the split kernel (the
+// downward pass takes it at every level; both measured at level 7, 16 RHS)
+constexpr int64_t kUpSplitMax = 4096;
+
+template <class TS, class T, int M>
+__global__ void __launch_bounds__(256, 2) k_down_split(const TS *__restrict__ Ef, int rp, int64_t par0, int64_t npar,
+                                                       T *__restrict__ yhat) {
+  constexpr int K = M * M * M;
+  __shared__ T F[kSplitParents][2][3][M * M];
+  load_factors<TS, T, M, kSplitParents>(Ef, par0, npar, F);
+  const int pl = threadIdx.x >> 7, ch = (threadIdx.x >> 6) & 1, t = threadIdx.x & 63;
+  const int j = (t >> 2) + 16 * blockIdx.y, jz = t & 3;
+  const int64_t pi = (int64_t)blockIdx.x * kSplitParents + pl, par = par0 + pi;
+  const bool act = pi < npar && j < rp && jz < M;
+  const int base = (threadIdx.x & 31) & ~3;
+  const int zq = jz < M ? jz : 0;
+  const T *Fx = F[pl][ch][0], *Fy = F[pl][ch][1], *Fz = F[pl][ch][2];
+  const int64_t c = 2 * par + 1 + ch;
+  T v[M][M], yc[M][M];
+#pragma unroll
+  for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < M; ++jx) {
+      const int64_t nu = jx + M * jy + M * M * jz;
+      v[jy][jx] = act ? yhat[(par * K + nu) * rp + j] : zero_of<T>();
+      yc[jy][jx] = act ? yhat[(c * K + nu) * rp + j] : zero_of<T>();
+    }
+  T a[M][M], b[M][M];
+#pragma unroll
+  for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < M; ++jx) a[jy][jx] = modem_out<T, false, M>(Fx, v[jy], jx);
+#pragma unroll
+  for (int jx = 0; jx < M; ++jx) {
+    T col[M];
+#pragma unroll
+    for (int jy = 0; jy < M; ++jy) col[jy] = a[jy][jx];
+#pragma unroll
+    for (int jy = 0; jy < M; ++jy) b[jy][jx] = modem_out<T, false, M>(Fy, col, jy);
+  }
+#pragma unroll
+  for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < M; ++jx) {
+      T in[M];
+#pragma unroll
+      for (int q = 0; q < M; ++q) in[q] = shfl_t(b[jy][jx], base + q);
+      const T r = modem_out<T, false, M>(Fz, in, zq);
+      if (act) yhat[(c * K + jx + M * jy + M * M * jz) * rp + j] = yc[jy][jx] + r;
+    }
+}
+
+template <class TS, class T, int M>
+__global__ void __launch_bounds__(256, 2) k_up_split(const TS *__restrict__ Ef, int rp, int64_t par0, int64_t npar,
+                                                     T *__restrict__ xhat, unsigned *__restrict__ xmax) {
+  constexpr int K = M * M * M;
+  __shared__ T F[kSplitParents][2][3][M * M];
+  __shared__ T R[kSplitParents][M * M][64];   // the second child's part
+  __shared__ unsigned loc[16];
+  if (threadIdx.x < 16) loc[threadIdx.x] = 0u;
+  load_factors<TS, T, M, kSplitParents>(Ef, par0, npar, F);
+  const int pl = threadIdx.x >> 7, ch = (threadIdx.x >> 6) & 1, t = threadIdx.x & 63;
+  const int j = (t >> 2) + 16 * blockIdx.y, jz = t & 3;
+  const int64_t pi = (int64_t)blockIdx.x * kSplitParents + pl, par = par0 + pi;
+  const bool act = pi < npar && j < rp && jz < M;
+  const int base = (threadIdx.x & 31) & ~3;
+  const int zq = jz < M ? jz : 0;
+  const int64_t c = 2 * par + 1 + ch;
+  const T *Fx = F[pl][ch][0], *Fy = F[pl][ch][1], *Fz = F[pl][ch][2];
+  T v[M][M], a[M][M], b[M][M];
+#pragma unroll
+  for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < M; ++jx)
+      v[jy][jx] = act ? xhat[(c * K + jx + M * jy + M * M * jz) * rp + j] : zero_of<T>();
+#pragma unroll
+  for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < M; ++jx) a[jy][jx] = modem_out<T, true, M>(Fx, v[jy], jx);
+#pragma unroll
+  for (int jx = 0; jx < M; ++jx) {
+    T col[M];
+#pragma unroll
+    for (int jy = 0; jy < M; ++jy) col[jy] = a[jy][jx];
+#pragma unroll
+    for (int jy = 0; jy < M; ++jy) b[jy][jx] = modem_out<T, true, M>(Fy, col, jy);
+  }
+  // the z mode product into a (the slab is free again)
+#pragma unroll
+  for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < M; ++jx) {
+      T in[M];
+#pragma unroll
+      for (int q = 0; q < M; ++q) in[q] = shfl_t(b[jy][jx], base + q);
+      a[jy][jx] = modem_out<T, true, M>(Fz, in, zq);
+    }
+  if (ch == 1)
+#pragma unroll
+    for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+      for (int jx = 0; jx < M; ++jx) R[pl][jx + M * jy][t] = a[jy][jx];
+  __syncthreads();
+  float mx = 0.0f;
+  if (ch == 0)
+#pragma unroll
+    for (int jy = 0; jy < M; ++jy)
+#pragma unroll
+      for (int jx = 0; jx < M; ++jx) {
+        const T o = (zero_of<T>() + a[jy][jx]) + R[pl][jx + M * jy][t];
+        if (act) xhat[(par * K + jx + M * jy + M * M * jz) * rp + j] = o;
+        if (act) mx = fmaxf(mx, mag_of(o));
+      }
+  if (xmax) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    if (ch == 0 && act && jz == 0 && mx > 0.0f) atomicMax(&loc[j & 15], __float_as_uint(mx));
     __syncthreads();
     if (threadIdx.x < 16 && loc[threadIdx.x]) atomicMax(&xmax[threadIdx.x], loc[threadIdx.x]);
   }

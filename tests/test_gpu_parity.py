@@ -390,8 +390,40 @@ def test_tensor_core_nearfield_needs_small_leaves(require_gpu):
     """Leaves of more than 21 triangles keep the double-float nearfield."""
     v, f = I.icosphere(2)   # 320 triangles, leaf 40: leaves of 40
     h = H2Matrix(v, f, leaf_size=40, eta=2.0, order=3, prec="f64")
-    assert h.stats["leaf_max"] > 21 and h.stats["tensor_near"] == 0
+    assert h.stats["leaf_max"] > 21 and h.stats["tensor_near"] == 0 and h.stats["tensor_leaf"] == 0
     h.close()
+
+
+@pytest.mark.parametrize("name", ["ico3_m4", "ell3_m4", "cube30_m4"])
+def test_f64_tensor_core_leaf_forward(require_gpu, name):
+    """Leaf forward step x^_t = V_t^T x|t (Algorithm 1 at the leaves) from the E4M3
+    digits of V_t^T and of the input on the tensor cores (FP64-accurate handles with
+    the tensor-core coupling and nearfield): the leaf coefficients and every far-field
+    level against the oracle's FP64 coefficients, columns of very different scales;
+    more than 16 right-hand sides take the double-float step."""
+    v, f, o = _oracle_any(name)
+    make, leaf, eta, m = CASES[name] if name in CASES else TENSOR_CASES[name]
+    h = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64")
+    hd = H2Matrix(v, f, leaf_size=leaf, eta=eta, order=m, prec="f64", tensor="off")
+    assert h.stats["tensor_leaf"] == 1 and hd.stats["tensor_leaf"] == 0
+    n = f.shape[0]
+    first = 2 ** h.stats["first_adm_level"] - 1
+    leaf0 = 2 ** h.stats["depth"] - 1
+    for nrhs in (1, 7, 16, 17):
+        x = I.uniform_rhs(n, nrhs, 3500 + nrhs)
+        _, xh, _ = o.matvec(x, coeffs=True)
+        h.matvec_host(x)
+        xg = h.coefficients(0, nrhs)
+        assert _rel(xg[leaf0:], xh[leaf0:]) <= 1e-13, (nrhs, _rel(xg[leaf0:], xh[leaf0:]))
+        assert _rel(xg[first:], xh[first:]) <= 1e-13
+    x = np.concatenate([np.ones((n, 1)), 1e-9 * I.uniform_rhs(n, 1, 3600), 1e6 * I.uniform_rhs(n, 1, 3601)], axis=1)
+    _, xh, _ = o.matvec(x, coeffs=True)
+    h.matvec_host(x)
+    xg = h.coefficients(0, 3)
+    for c in range(3):
+        assert _rel(xg[leaf0:, :, c], xh[leaf0:, :, c]) <= 1e-13, c
+    h.close()
+    hd.close()
 
 
 @pytest.mark.parametrize("name", ["ico3_m4", "ell3_m4", "cube30_m4"])

@@ -16,6 +16,12 @@
 #endif
 #endif
 
+#include <cstdint>
+#ifndef __CUDA_ARCH__
+#include <cmath>
+#include <cstring>
+#endif
+
 namespace h2 {
 
 // split X (|X| <= 2^49) into ten signed 5-bit digits, most significant
@@ -55,6 +61,56 @@ __host__ __device__ __forceinline__ void split_digits(long long X, int (&s)[ND])
       a = (a - d) >> 5;
     }
     s[0] = a;
+  }
+}
+
+// The same digits, as exact FP32 values, of X = rint(hs) + rint(ls) (hs, ls
+// the two words of a double-float value, or an FP32 value and 0, already
+// scaled by 2^sc: power-of-two products, exact), formed with 32-bit
+// operations only.  For ten digits: H = rint(hs) is an integer-valued float,
+// A = rint(H 2^-25) and B = H - A 2^25 (|B| <= 2^24, an exact float
+// difference) split it, and L = rint(ls) fits in 32 bits, so X = A 2^25 + bt
+// with bt = B + L, whose low 25 bits are those of X: the halves (a, b) of
+// split_digits follow from (A, bt) with 32-bit integer arithmetic.  A digit
+// d = (w & 31) - 16 (w = v + 16) becomes a float by placing w & 31 in the
+// significand of 2^23 and subtracting 2^23 + 16; the next v is w >> 5.
+__host__ __device__ __forceinline__ float bits_float(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ float digit_f(int &v) {
+  const int w = v + 16;
+  v = w >> 5;
+  return bits_float(0x4B000000u | (uint32_t)(w & 31)) - 8388624.0f;
+}
+
+template <int ND>
+__host__ __device__ __forceinline__ void split_digits_f(float hs, float ls, float (&f)[ND]) {
+  static_assert(ND == 10 || ND == 6, "digit counts");
+  if (ND == 10) {
+    const float H = rintf(hs);
+    const float A = rintf(H * 0x1p-25f);
+    const float B = fmaf(-A, 0x1p25f, H);
+    const int bt = (int)B + (int)rintf(ls);
+    int b = ((bt + (1 << 24)) & ((1 << 25) - 1)) - (1 << 24);
+    int a = (int)A + ((bt - b) >> 25);
+#pragma unroll
+    for (int i = ND - 1; i >= ND / 2; --i) f[i] = digit_f(b);
+    a += b;
+#pragma unroll
+    for (int i = ND / 2 - 1; i >= 1; --i) f[i] = digit_f(a);
+    f[0] = (float)a;
+  } else {
+    int a = (int)rintf(hs) + (int)rintf(ls);
+#pragma unroll
+    for (int i = ND - 1; i >= 1; --i) f[i] = digit_f(a);
+    f[0] = (float)a;
   }
 }
 

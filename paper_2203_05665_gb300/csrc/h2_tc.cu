@@ -311,11 +311,6 @@ __device__ __forceinline__ int tc_colexp(unsigned bits) {
   return bits ? (int)((bits >> 23) & 0xFF) - 127 + 2 : 0;
 }
 
-// The ND E4M3 digit planes of the coefficients of cluster c (x^_c
-// [64][rp]): cut in registers, assembled in shared memory (tile: ND x 16 x
-// 64 bytes) in the MMA layout (16 columns x 64 contraction values per
-// plane) and written out with 16-byte stores.  All threads of the CTA take
-// part; the caller synchronises before and after.
 // v 2^sc for the coefficient scalings (|v 2^sc| <= 2^49, |sc| < 252): two
 // power-of-two factors that are normal floats, so the product is exact
 // unless it is far below 1/2, where it rounds to the integer 0 anyway
@@ -323,39 +318,65 @@ __device__ __forceinline__ float scale2(float v, int sc) {
   const int h = sc >> 1;
   return v * pow2f(h) * pow2f(sc - h);
 }
-__device__ __forceinline__ long long fixed_of(dd v, int sc) {
-  return llrintf(scale2(v.hi, sc)) + llrintf(scale2(v.lo, sc));
-}
-__device__ __forceinline__ long long fixed_of(float v, int sc) { return llrintf(scale2(v, sc)); }
 
-template <class T, int ND>
-__device__ __forceinline__ void slice_cluster(const T *__restrict__ xc, int rp, int lvl,
-                                              const unsigned *__restrict__ xmax, unsigned char *tile,
-                                              unsigned char *__restrict__ dst) {
-  for (int e = threadIdx.x; e < kTcN * kTcK; e += blockDim.x) {
-    const int mu = e / kTcN, j = e % kTcN;
-    long long X = 0;
-    if (j < rp) X = fixed_of(xc[mu * rp + j], Dig<ND>::kFix - tc_colexp(xmax[lvl * kTcN + j]));
-    int sl[ND];
-    split_digits<ND>(X, sl);
-    const int o = core_off(j, mu);
+// the ND digits (exact floats) of round(v 2^sc) for a double-float or FP32 value
+template <int ND>
+__device__ __forceinline__ void digits_of(dd v, int sc, float (&f)[ND]) {
+  split_digits_f<ND>(scale2(v.hi, sc), scale2(v.lo, sc), f);
+}
+template <int ND>
+__device__ __forceinline__ void digits_of(float v, int sc, float (&f)[ND]) {
+  split_digits_f<ND>(scale2(v, sc), 0.0f, f);
+}
+
+// two digits as their E4M3 bytes, the first in the low byte
+__device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+
+// The digit planes of 16 consecutive values v[0..15] of one column, each
+// scaled by 2^sc: plane i as one 16-byte word (the bytes in value order), a
+// row of one core matrix of the MMA layout.
+template <int ND, class T>
+__device__ __forceinline__ void cut_row16(const T (&v)[16], int sc, uint4 (&w)[ND]) {
+  uint32_t u[ND][4];
 #pragma unroll
-    for (int i = 0; i < ND; ++i) tile[i * kSliceB + o] = e4m3(sl[i]);
+  for (int q = 0; q < 8; ++q) {
+    float f0[ND], f1[ND];
+    digits_of<ND>(v[2 * q], sc, f0);
+    digits_of<ND>(v[2 * q + 1], sc, f1);
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      const uint32_t h = e4m3x2(f0[i], f1[i]);
+      u[i][q >> 1] = (q & 1) ? (u[i][q >> 1] | (h << 16)) : h;
+    }
   }
-  __syncthreads();
-  constexpr int kWords = Dig<ND>::kTileB / 16;   // 16-byte words of the planes
-  for (int w = threadIdx.x; w < kWords; w += blockDim.x)
-    reinterpret_cast<uint4 *>(dst)[w] = reinterpret_cast<const uint4 *>(tile)[w];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) w[i] = make_uint4(u[i][0], u[i][1], u[i][2], u[i][3]);
 }
 
-// the slices of clusters c0, c0 + 1, ... (one cluster per CTA), each with the
-// column maxima of its own tree level
+// The ND E4M3 digit planes of the coefficients x^_c ([64][rp]) of clusters
+// c0 .. c0 + ncl - 1, each with the column maxima of its own tree level:
+// 64 threads per cluster (four per CTA), thread (g, j) cuts the values
+// mu = 16 g .. 16 g + 15 of column j in registers and writes one 16-byte row
+// of a core matrix per plane (zero digits for the columns j >= rp).
 template <class T, int ND>
-__global__ void __launch_bounds__(256) k_tc_slice_x(const T *__restrict__ xhat, int64_t c0, int rp,
+__global__ void __launch_bounds__(256) k_tc_slice_x(const T *__restrict__ xhat, int64_t c0, int64_t ncl, int rp,
                                                     const unsigned *__restrict__ xmax, unsigned char *__restrict__ xtc) {
-  __shared__ __align__(16) unsigned char tile[Dig<ND>::kTileB];
-  const int64_t c = c0 + blockIdx.x;
-  slice_cluster<T, ND>(xhat + c * kTcK * rp, rp, tc_level(c), xmax, tile, xtc + c * (int64_t)Dig<ND>::kTileB);
+  const int64_t ci = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 6);
+  if (ci >= ncl) return;
+  const int64_t c = c0 + ci;
+  const int g = (threadIdx.x >> 4) & 3, j = threadIdx.x & 15;
+  const T *xc = xhat + c * kTcK * rp;
+  const int sc = Dig<ND>::kFix - tc_colexp(xmax[tc_level(c) * kTcN + j]);
+  T v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = j < rp ? xc[(16 * g + q) * rp + j] : T{};
+  uint4 w[ND];
+  cut_row16<ND>(v, sc, w);
+  unsigned char *dst = xtc + c * (int64_t)Dig<ND>::kTileB + core_off(j, 16 * g);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) *reinterpret_cast<uint4 *>(dst + i * Dig<ND>::kPlaneB) = w[i];
 }
 
 __device__ __forceinline__ dd dd_scale(dd v, int e) {
@@ -773,29 +794,27 @@ __global__ void k_ntc_slice(const dd *__restrict__ near, const int32_t *__restri
   }
 }
 
-// the digit planes of the input of leaf s (x_pad rows s L .. s L + L - 1): 16 rows j x 32 bytes each
-__global__ void __launch_bounds__(128) k_ntc_slice_x(const dd *__restrict__ xpad, int L, int rp,
+// the digit planes of the input of leaf s (x_pad rows s L .. s L + L - 1): 16
+// rows j x 32 bytes each; 32 threads per leaf (four per CTA), thread (g, j)
+// cuts rows mu = 16 g .. 16 g + 15 of column j (zero beyond L and rp)
+__global__ void __launch_bounds__(128) k_ntc_slice_x(const dd *__restrict__ xpad, int64_t nleaf, int L, int rp,
                                                      const unsigned *__restrict__ xmax,
                                                      unsigned char *__restrict__ xnt) {
-  __shared__ __align__(16) unsigned char tile[kNtX];
-  const int64_t s = blockIdx.x;
-  for (int e = threadIdx.x; e < kTcN * 32; e += blockDim.x) {
-    const int j = e & (kTcN - 1), mu = e >> 4;
-    long long X = 0;
-    if (mu < L && j < rp) {
-      const int sc = kTcFixBits - tc_colexp(xmax[j]);
-      const dd v = xpad[(s * L + mu) * rp + j];
-      X = fixed_of(v, sc);
-    }
-    int sl[kTcSlices];
-    split_digits(X, sl);
-    const int o = core_off32(j, mu);
+  const int64_t t = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (t >= nleaf) return;
+  const int g = (threadIdx.x >> 4) & 1, j = threadIdx.x & 15;
+  const int sc = kTcFixBits - tc_colexp(xmax[j]);
+  dd v[16];
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) tile[i * (kTcN * kNtRowB) + o] = e4m3(sl[i]);
+  for (int q = 0; q < 16; ++q) {
+    const int mu = 16 * g + q;
+    v[q] = mu < L && j < rp ? xpad[(t * L + mu) * rp + j] : dd{0.0f, 0.0f};
   }
-  __syncthreads();
-  for (int w = threadIdx.x; w < (int)(kNtX / 16); w += blockDim.x)
-    reinterpret_cast<uint4 *>(xnt + s * (int64_t)kNtX)[w] = reinterpret_cast<const uint4 *>(tile)[w];
+  uint4 w[kTcSlices];
+  cut_row16<kTcSlices>(v, sc, w);
+  unsigned char *dst = xnt + t * (int64_t)kNtX + core_off32(j, 16 * g);
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i) *reinterpret_cast<uint4 *>(dst + i * (kTcN * kNtRowB)) = w[i];
 }
 
 // Leaf forward step on the tensor cores (Algorithm 1 at the leaves,
@@ -1154,7 +1173,8 @@ int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
   }
   // the digits of every level at once (all maxima are complete)
   const int64_t c0 = ((int64_t)1 << lmin) - 1, ncl = d.nclu - c0;
-  k_tc_slice_x<T, ND><<<(unsigned)ncl, 256, 0, st>>>(xhat, c0, rp, d.tc_xmax, (unsigned char *)d.xtc);
+  k_tc_slice_x<T, ND><<<(unsigned)((ncl + 3) / 4), 256, 0, st>>>(xhat, c0, ncl, rp, d.tc_xmax,
+                                                                 (unsigned char *)d.xtc);
   ++nl;
   H2_CUDA_TRY(cudaGetLastError());
   if (launches) *launches = nl;
@@ -1255,7 +1275,8 @@ int ntc_input(Ctx &c, const void *xpad_v, int rp, int64_t *launches) {
   H2_CUDA_TRY(cudaMemsetAsync(d.ntc_xmax, 0, sizeof(unsigned) * kTcN, st));
   const int64_t rows = d.nleaf * L;
   k_tc_levmax<dd><<<levmax_grid(rows), 256, 0, st>>>(xpad, rows, rp, d.ntc_xmax);
-  k_ntc_slice_x<<<(unsigned)d.nleaf, 128, 0, st>>>(xpad, L, rp, d.ntc_xmax, (unsigned char *)d.xnt);
+  k_ntc_slice_x<<<(unsigned)((d.nleaf + 3) / 4), 128, 0, st>>>(xpad, d.nleaf, L, rp, d.ntc_xmax,
+                                                               (unsigned char *)d.xnt);
   H2_CUDA_TRY(cudaGetLastError());
   if (launches) *launches = 2;
   return H2_OK;

@@ -7,6 +7,7 @@
 // success.
 #include <cuda_fp8.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <random>
@@ -51,6 +52,54 @@ static int check(long long lim, int samples, long long bound) {
   return bad;
 }
 
+// split_digits_f (32-bit operations, float digits) against split_digits of
+// the 64-bit integer rint(hs) + rint(ls), for double-float pairs (hi, lo) and
+// FP32 values scaled as the kernels scale them (|hs| < 2^(5 ND - 2)), on
+// boundary values and random samples
+template <int ND>
+static int check_f(int samples) {
+  std::mt19937_64 g(4242 + ND);
+  int bad = 0;
+  auto one = [&](float hs, float ls) {
+    float f[ND];
+    int s[ND];
+    h2::split_digits_f<ND>(hs, ls, f);
+    h2::split_digits<ND>(llrintf(hs) + llrintf(ls), s);
+    for (int i = 0; i < ND; ++i)
+      if (f[i] != (float)s[i]) ++bad;
+  };
+  const float top = std::ldexp(1.0f, 5 * ND - 2);
+  const float edge[] = {0.0f, 0.5f, 1.5f, 2.5f, 15.5f, 16.5f, 8388607.5f, 16777216.0f, 33554431.0f,
+                        33554432.0f, 50331648.0f, std::nextafter(top, 0.0f), top / 3};
+  for (float a : edge)
+    for (float b : {0.0f, 0.5f, -0.5f, 1.5f, -2.5f, 16777216.0f, -33554430.0f}) {
+      if (ND == 6) b = 0.0f;
+      one(a, b);
+      one(-a, -b);
+      one(a, -b);
+    }
+  std::uniform_real_distribution<float> u(-1.0f, 1.0f);
+  std::uniform_int_distribution<int> ex(-30, 5 * ND - 3);
+  for (int n = 0; n < samples; ++n) {
+    const float hi = std::ldexp(u(g), ex(g));   // |hi| < 2^(5 ND - 2)
+    float lo = 0.0f;
+    if (ND == 10) {
+      const float ul = std::nextafter(std::fabs(hi), INFINITY) - std::fabs(hi);
+      lo = u(g) * ul * 0.5f;
+    }
+    one(hi, lo);
+  }
+  // the packed conversion: the first element in the low byte
+  for (int a = -16; a <= 16; ++a)
+    for (int b = -16; b <= 16; ++b) {
+      const __nv_fp8x2_storage_t p = __nv_cvt_float2_to_fp8x2(float2{(float)a, (float)b}, __NV_SATFINITE, __NV_E4M3);
+      const unsigned lo8 = __nv_cvt_float_to_fp8((float)a, __NV_SATFINITE, __NV_E4M3);
+      const unsigned hi8 = __nv_cvt_float_to_fp8((float)b, __NV_SATFINITE, __NV_E4M3);
+      if (p != (__nv_fp8x2_storage_t)(lo8 | (hi8 << 8))) ++bad;
+    }
+  return bad;
+}
+
 int main() {
   int bad = 0;
   for (int s = -16; s <= 16; ++s) {
@@ -60,6 +109,8 @@ int main() {
   }
   const int b10 = check<10>(1LL << 49, 2000000, 1LL << 52);
   const int b6 = check<6>(1LL << 29, 2000000, 1LL << 31);
-  std::printf("e4m3 %d, ten digits %d, six digits %d\n", bad, b10, b6);
-  return bad + b10 + b6 != 0;
+  const int f10 = check_f<10>(2000000);
+  const int f6 = check_f<6>(2000000);
+  std::printf("e4m3 %d, ten digits %d, six digits %d, 32-bit cut %d / %d\n", bad, b10, b6, f10, f6);
+  return bad + b10 + b6 + f10 + f6 != 0;
 }

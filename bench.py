@@ -226,7 +226,7 @@ def run_ours(args):
     # profiles/k_blockrow_coupling_icosphere_L5_m4_16rhs_f64.md), scaled by
     # admissible blocks; None where no capture of the current kernel exists
     tc = args.prec == "f64" and st.get("tensor", 0)
-    traffic_per_block = {"f64": 691.93e6 / 18876, "f64-tc": (794.696448e6 + 8.761344e6) / 18876}
+    traffic_per_block = {"f64": 691.93e6 / 18876, "f64-tc": (794.690048e6 + 7.657472e6) / 18876}
     key = "f64-tc" if tc else args.prec
     roof["traffic"] = (traffic_per_block[key] * st["adm_blocks"]
                        if key in traffic_per_block and args.order == 4 and args.nrhs == 16 else None)

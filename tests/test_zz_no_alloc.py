@@ -42,15 +42,20 @@ def _dirty_shared_array(lib, dt):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_noalloc_matches_oracle_and_matvec_twice(require_gpu, prec):
+@pytest.mark.parametrize("order", [3, 4])
+def test_noalloc_matches_oracle_and_matvec_twice(require_gpu, prec, order):
+    """Order 4 takes the tensor-core phases (coupling digits; for f64 also the
+    nearfield and leaf-basis digits), whose digit buffers the handle owns."""
     import torch
     lib = load()
     dt = torch.float64 if prec == "f64" else torch.float32
     _dirty_shared_array(lib, dt)
     v, f = I.icosphere(4)
     n = f.shape[0]
-    o = oracle.Oracle(v, f, leaf_size=32, eta=2.0, order=3)
-    h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=3, prec=prec)   # fresh: no work buffers yet
+    o = oracle.Oracle(v, f, leaf_size=32, eta=2.0, order=order)
+    h = H2Matrix(v, f, leaf_size=32, eta=2.0, order=order, prec=prec)   # fresh: no work buffers yet
+    if order == 4:
+        assert h.stats["tensor"] == 1 and (prec == "f32" or h.stats["tensor_leaf"] == 1)
     for call, nrhs in enumerate((3, 3)):
         xh = I.uniform_rhs(n, nrhs, 31 + call)
         x = colmajor(torch.from_numpy(xh).to(device="cuda", dtype=dt))
@@ -60,12 +65,12 @@ def test_noalloc_matches_oracle_and_matvec_twice(require_gpu, prec):
         a = y.cpu().double().numpy()
         assert np.all(np.isfinite(a))
         ref = o.matvec(x.cpu().double().numpy())
-        assert np.linalg.norm(a - ref) <= TOL[prec] * np.linalg.norm(ref), (call, prec)
+        assert np.linalg.norm(a - ref) <= TOL[prec] * np.linalg.norm(ref), (call, prec, order)
         y_ref = colmajor(torch.empty_like(x))
         h.matvec(x, y_ref)
         torch.cuda.synchronize()
         r = y_ref.cpu().double().numpy()
-        assert np.linalg.norm(a - r) <= TOL[prec] * np.linalg.norm(r), (call, prec)
+        assert np.linalg.norm(a - r) <= TOL[prec] * np.linalg.norm(r), (call, prec, order)
     h.close()
 
 

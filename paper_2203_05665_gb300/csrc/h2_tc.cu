@@ -395,7 +395,7 @@ __device__ __forceinline__ dd dd_scale(dd v, int e) {
 // row powers of two are E[r][nu] and the column powers xmax[j] (one level):
 // the leaf forward step x^_t = V_t^T x|t with KB = 32, the V_t^T digit
 // planes as the blocks and the input digit planes of leaf t as the
-// coefficients.  Two epilogue warp groups then take alternate rows, and two
+// coefficients.  Three epilogue warp groups then take every third row, and two
 // neighbouring digit levels are combined exactly in FP32 before entering
 // double-float: a level sum of one block is at most 5 x 32 x 16^2 < 2^15.4,
 // so 32 D_L + D_(L+1) < 2^21.
@@ -404,8 +404,9 @@ __device__ __forceinline__ dd to_dd(float v) { return dd{v, 0.0f}; }
 __device__ __forceinline__ void store_as(dd v, dd *p) { *p = v; }
 __device__ __forceinline__ void store_as(dd v, float *p) { *p = v.hi + v.lo; }
 
+constexpr int kDiagGroups = 3;   // epilogue warp groups of one-block rows
 template <int ND, class T, int KB = kTcK, bool DIAG = false>
-__global__ void __launch_bounds__(DIAG ? 64 + 2 * 128 : kTcThreads, 1)
+__global__ void __launch_bounds__(DIAG ? 64 + kDiagGroups * 128 : kTcThreads, 1)
     k_coupling_tc(const unsigned char *__restrict__ Stc, const unsigned char *__restrict__ xtc,
                   const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const int32_t *__restrict__ E,
                   const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, T *__restrict__ yhat) {
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(DIAG ? 64 + 2 * 128 : kTcThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   dd *xch = reinterpret_cast<dd *>(smem + kTcStages * kStage);
   constexpr int kSets = D::kSets;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + tc_bar_off<ND, KB, DIAG ? 2 : 1>());
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + tc_bar_off<ND, KB, DIAG ? kDiagGroups : 1>());
   uint64_t *empty = full + kTcStages;
   uint64_t *accf = empty + kTcStages;   // [kSets]: the MMAs of a segment have completed
   uint64_t *acce = accf + kSets;        // [kSets]: the epilogue has read the set
@@ -549,8 +550,9 @@ __global__ void __launch_bounds__(DIAG ? 64 + 2 * 128 : kTcThreads, 1)
     }
     __syncwarp();
   } else if (DIAG) {
-    // ---------------- one-block rows: warps 2-5 (group 0) and 6-9 (group 1)
-    // take alternate rows; each reads tensor-memory lanes 32 (warp % 4) ..
+    // ---------------- one-block rows: warps 2-5 (group 0), 6-9 (group 1) and
+    // 10-13 (group 2) take every third row; each reads tensor-memory lanes
+    // 32 (warp % 4) ..
     const int grp = (warp - 2) >> 2;
     const int quad = warp & 3, tl = quad * 32 + lane, half = tl >> 6, nu = tl & 63;
     dd *xg = xch + grp * (64 * kTcN);
@@ -560,10 +562,10 @@ __global__ void __launch_bounds__(DIAG ? 64 + 2 * 128 : kTcThreads, 1)
     for (int j = 0; j < kTcN; ++j) cx[j] = tc_colexp(xmax[j]);
     int64_t r = r_begin + grp;
     int Enext = r < r_end ? E[r * kTcK + nu] : 0;   // the row's powers, loaded a row ahead
-    for (; r < r_end; r += 2) {
+    for (; r < r_end; r += kDiagGroups) {
       const int64_t q = r - r_begin, t = row0 + r;
       const int Er = Enext;
-      if (r + 2 < r_end) Enext = E[(r + 2) * kTcK + nu];
+      if (r + kDiagGroups < r_end) Enext = E[(r + kDiagGroups) * kTcK + nu];
       T *yrow = yhat + (t * kTcK + nu) * rp;
       const int set = (int)(q % kSets);
       const bool ready = !*abort && mbar_wait_or_abort(&accf[set], (uint32_t)((q / kSets) & 1), abort);
@@ -576,14 +578,14 @@ __global__ void __launch_bounds__(DIAG ? 64 + 2 * 128 : kTcThreads, 1)
       // (32 D_L + D_(L+1)) 2^(2 - 5 (L + 1)), in increasing L
       const uint32_t tset = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * D::kW;
 #pragma unroll
-      for (int c0 = 0; c0 < ND; c0 += 6) {
-        uint32_t raw[6][16];
+      for (int c0 = 0; c0 < ND; c0 += 4) {
+        uint32_t raw[4][16];
 #pragma unroll
-        for (int u = 0; u < 6; ++u)
+        for (int u = 0; u < 4; ++u)
           if (c0 + u < ND) tmem_ld16_nw(tset + (uint32_t)((c0 + u) * kTcN), raw[u]);
         tmem_wait();
 #pragma unroll
-        for (int u = 0; u < 6; u += 2) {
+        for (int u = 0; u < 4; u += 2) {
           const int L = c0 + u + 2 + half;
           if (c0 + u < ND && L <= D::kTop) {
             const float w = pow2f(2 - 5 * (L + 1));
@@ -1289,7 +1291,7 @@ int tc_leaf_forward(Ctx &c, void *xhat_v, int rp) {
   cudaStream_t st = c.stream;
   if (rp > kTcN || !d.Vtc) return fail(H2_EINVAL, "no tensor-core leaf forward step for this handle");
   constexpr int KB = 32;
-  constexpr uint32_t sm = tc_smem<kTcSlices, KB, 2>();
+  constexpr uint32_t sm = tc_smem<kTcSlices, KB, kDiagGroups>();
   static_assert(sm <= 227 * 1024, "tensor-core leaf step does not fit in shared memory");
   H2_CUDA_TRY(cudaFuncSetAttribute((const void *)k_coupling_tc<kTcSlices, dd, KB, true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024)));
@@ -1297,7 +1299,7 @@ int tc_leaf_forward(Ctx &c, void *xhat_v, int rp) {
   H2_CUDA_TRY(cudaGetDevice(&dev));
   H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = (int)std::min<int64_t>(sms, d.nleaf);
-  k_coupling_tc<kTcSlices, dd, KB, true><<<grid, 64 + 2 * 128, sm, st>>>(
+  k_coupling_tc<kTcSlices, dd, KB, true><<<grid, 64 + kDiagGroups * 128, sm, st>>>(
       (const unsigned char *)d.Vtc, (const unsigned char *)d.xnt, nullptr, nullptr, d.tcv_E, d.ntc_xmax,
       d.nleaf - 1, d.nleaf, rp, static_cast<dd *>(xhat_v));
   H2_CUDA_TRY(cudaGetLastError());

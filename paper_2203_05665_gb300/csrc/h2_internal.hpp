@@ -240,7 +240,9 @@ int wait_selftest(Ctx &c, int withhold, uint32_t limit, int *stages_seen);
 // coefficient arrays [clusters][k][rp]) and that file's device error word
 bool tc_eligible(const Dev &d);
 int tc_build(Ctx &c, const int32_t *arow_dev);
-int tc_upward(Ctx &c, void *xhat, int rp, int64_t *launches);
+// leaf_max: the leaf coefficients' column maxima are in place (written by
+// the tensor-core leaf forward step)
+int tc_upward(Ctx &c, void *xhat, int rp, int64_t *launches, bool leaf_max = false);
 int tc_coupling(Ctx &c, const void *xhat, void *yhat, int rp);
 int tc_take_error(cudaStream_t st);
 bool ntc_eligible(const Dev &d);
@@ -248,7 +250,8 @@ int ntc_build(Ctx &c, const int32_t *nrow_dev);
 int ntc_near(Ctx &c, const void *xpad, void *ypad, int rp, int accumulate, int64_t *launches,
              bool have_input = false);
 // input column maxima and digit planes per leaf (nearfield, tensor-core leaf step)
-int ntc_input(Ctx &c, const void *xpad, int rp, int64_t *launches);
+// have_max: the column maxima are in place (taken by the permutation)
+int ntc_input(Ctx &c, const void *xpad, int rp, int64_t *launches, bool have_max = false);
 // leaf forward step on the tensor cores (after ntc_input); requires d.Vtc
 int tc_leaf_forward(Ctx &c, void *xhat, int rp);
 

@@ -85,16 +85,20 @@ __host__ __device__ inline int range_shift(unsigned long long bits) {
 constexpr int kPermRows = 64;
 
 // xpad[p][c] (zero beyond nrhs and for padding rows) from x[src][c], scaled by
-// the column's range-guard power of two
+// the column's range-guard power of two; with xmax also the largest |xpad|
+// (|hi| for double-float) of every column, as float bits (atomicMax), the
+// maxima the nearfield's input digits are cut with
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(256) k_permute_in(const Tin *__restrict__ x, int64_t n, int nrhs, int rp,
                                                     const int32_t *__restrict__ pad_src, int64_t npad,
                                                     const unsigned long long *__restrict__ colmax,
-                                                    Tout *__restrict__ xpad) {
+                                                    Tout *__restrict__ xpad, unsigned *__restrict__ xmax = nullptr) {
   extern __shared__ __align__(16) unsigned char perm_smem[];
   Tout *tile = reinterpret_cast<Tout *>(perm_smem);
   __shared__ int shift[64];
+  __shared__ unsigned smax[64];
   __shared__ int32_t src[kPermRows];
+  if (threadIdx.x < 64) smax[threadIdx.x] = 0u;
   const int w = rp + 1;
   const int64_t p0 = (int64_t)blockIdx.x * kPermRows;
   if (threadIdx.x < kPermRows) src[threadIdx.x] = p0 + threadIdx.x < npad ? pad_src[p0 + threadIdx.x] : -1;
@@ -124,7 +128,16 @@ __global__ void __launch_bounds__(256) k_permute_in(const Tin *__restrict__ x, i
   const int64_t rows = npad - p0 < kPermRows ? npad - p0 : kPermRows;
   for (int i = threadIdx.x; i < rows * rp; i += blockDim.x) {
     const int q = i / rp, c = i - q * rp;
-    xpad[(p0 + q) * rp + c] = tile[q * w + c];
+    const Tout v = tile[q * w + c];
+    xpad[(p0 + q) * rp + c] = v;
+    if (xmax) {
+      const float m = mag_of(v);
+      if (m > 0.0f) atomicMax(&smax[c], __float_as_uint(m));
+    }
+  }
+  if (xmax) {
+    __syncthreads();
+    if ((int)threadIdx.x < rp && smax[threadIdx.x]) atomicMax(&xmax[threadIdx.x], smax[threadIdx.x]);
   }
 }
 
@@ -1086,18 +1099,20 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
     mk.count(H2_PH_PERMUTE_IN);
   }
   const unsigned perm_grid = (unsigned)((d.npad + kPermRows - 1) / kPermRows);
-  k_permute_in<Tio, T><<<perm_grid, 256, (size_t)kPermRows * (rp + 1) * sizeof(T), st>>>(x, d.n, nrhs, rp, d.pad_src,
-                                                                                        d.npad, cmx, xpad);
+  // FP64-accurate with the tensor-core nearfield and coupling: the leaf
+  // forward step from the input digits the nearfield reads anyway; the
+  // permutation takes the input's column maxima on the way
+  const bool leaf_tc = std::is_same<T, dd>::value && far && d.ntc && d.Vtc && rp <= 16;
+  if (leaf_tc) H2_CUDA_TRY(cudaMemsetAsync(d.ntc_xmax, 0, sizeof(unsigned) * 16, st));
+  k_permute_in<Tio, T><<<perm_grid, 256, (size_t)kPermRows * (rp + 1) * sizeof(T), st>>>(
+      x, d.n, nrhs, rp, d.pad_src, d.npad, cmx, xpad, leaf_tc ? d.ntc_xmax : nullptr);
   mk.count(H2_PH_PERMUTE_IN);
   mk.mark(H2_PH_LEAF_FORWARD);
   // leaf steps with one CTA per leaf when the stored values are in the arithmetic type
   const bool leaf_reg = L <= 32 && k <= 64 && rp <= 16;
-  // FP64-accurate with the tensor-core nearfield and coupling: the leaf
-  // forward step from the input digits the nearfield reads anyway
-  const bool leaf_tc = std::is_same<T, dd>::value && far && d.ntc && d.Vtc && rp <= 16;
   if (leaf_tc) {
     int64_t nl = 0;
-    if ((rc = ntc_input(c, xpad, rp, &nl))) return rc;
+    if ((rc = ntc_input(c, xpad, rp, &nl, true))) return rc;
     if ((rc = tc_leaf_forward(c, xhat, rp))) return rc;
     mk.count(H2_PH_LEAF_FORWARD, nl + 1);
   } else if (far && leaf_reg) {
@@ -1117,7 +1132,7 @@ int matvec_typed(Ctx &c, const Tio *x, Tio *y, int nrhs, bool acc) {
   if (far && tcpath) {
     // with the column maxima and coefficient slices of the tensor-core coupling
     int64_t nl = 0;
-    if ((rc = tc_upward(c, xhat, rp, &nl))) return rc;
+    if ((rc = tc_upward(c, xhat, rp, &nl, leaf_tc))) return rc;
     mk.count(H2_PH_UPWARD, nl);
   } else if (far && (m == 3 || m == 4)) {
     // orders 3 and 4: register kernels (the z mode product by warp shuffles)

@@ -395,7 +395,9 @@ __device__ __forceinline__ dd dd_scale(dd v, int e) {
 // row powers of two are E[r][nu] and the column powers xmax[j] (one level):
 // the leaf forward step x^_t = V_t^T x|t with KB = 32, the V_t^T digit
 // planes as the blocks and the input digit planes of leaf t as the
-// coefficients.  Three epilogue warp groups then take every third row, and two
+// coefficients (with ymax, the largest |hi| of every column of the results
+// is taken too, as float bits).  Three epilogue warp groups then take every
+// third row, and two
 // neighbouring digit levels are combined exactly in FP32 before entering
 // double-float: a level sum of one block is at most 5 x 32 x 16^2 < 2^15.4,
 // so 32 D_L + D_(L+1) < 2^21.
@@ -409,7 +411,8 @@ template <int ND, class T, int KB = kTcK, bool DIAG = false>
 __global__ void __launch_bounds__(DIAG ? 64 + kDiagGroups * 128 : kTcThreads, 1)
     k_coupling_tc(const unsigned char *__restrict__ Stc, const unsigned char *__restrict__ xtc,
                   const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const int32_t *__restrict__ E,
-                  const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, T *__restrict__ yhat) {
+                  const unsigned *__restrict__ xmax, int64_t row0, int64_t nrows, int rp, T *__restrict__ yhat,
+                  unsigned *__restrict__ ymax = nullptr) {
   using D = Dig<ND, KB>;
   // first block of row t (t = row0 + r); one block per row without ptr
   auto pt = [&](int64_t t) -> int64_t { return DIAG ? t - row0 : ptr[t]; };
@@ -558,8 +561,12 @@ __global__ void __launch_bounds__(DIAG ? 64 + kDiagGroups * 128 : kTcThreads, 1)
     dd *xg = xch + grp * (64 * kTcN);
     const uint32_t bar_or = 1 + 2 * grp, bar_x = 2 + 2 * grp;
     int cx[kTcN];
+    float cm[kTcN];   // column maxima of the rows this thread writes
 #pragma unroll
-    for (int j = 0; j < kTcN; ++j) cx[j] = tc_colexp(xmax[j]);
+    for (int j = 0; j < kTcN; ++j) {
+      cx[j] = tc_colexp(xmax[j]);
+      cm[j] = 0.0f;
+    }
     int64_t r = r_begin + grp;
     int Enext = r < r_end ? E[r * kTcK + nu] : 0;   // the row's powers, loaded a row ahead
     for (; r < r_end; r += kDiagGroups) {
@@ -609,10 +616,21 @@ __global__ void __launch_bounds__(DIAG ? 64 + kDiagGroups * 128 : kTcThreads, 1)
 #pragma unroll
         for (int j = 0; j < kTcN; ++j) {
           if (j >= rp) break;
-          store_as(dd_scale(acc[j] + xg[j * 64 + nu], Er + cx[j]), yrow + j);
+          const dd v = dd_scale(acc[j] + xg[j * 64 + nu], Er + cx[j]);
+          store_as(v, yrow + j);
+          cm[j] = fmaxf(cm[j], fabsf(v.hi));
         }
       }
       named_sync_id(bar_x, 128);
+    }
+    if (ymax && half == 0) {
+#pragma unroll
+      for (int j = 0; j < kTcN; ++j) {
+        float m = cm[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && j < rp && m > 0.0f) atomicMax(&ymax[j], __float_as_uint(m));
+      }
     }
   } else {
     // ---------------- epilogue: warps 2-5 read tensor-memory lanes 32 (warp % 4) ..
@@ -1151,17 +1169,19 @@ int tc_build_nd(Ctx &c, const int32_t *arow_dev) {
 // transfer launch was slower: the transfer threads are latency bound.
 // Returns the launches made.
 template <class T, int ND>
-int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches) {
+int tc_upward_t(Ctx &c, T *xhat, int rp, int64_t *launches, bool leaf_max) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
   const int D = d.depth, lmin = d.first_adm_level;
   if (lmin > D) return H2_OK;
   const int64_t leaf0 = d.nleaf - 1;
   int64_t nl = 0;
-  H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
-  const int64_t lrows = d.nleaf * kTcK;
-  k_tc_levmax<T><<<levmax_grid(lrows), 256, 0, st>>>(xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
-  ++nl;
+  if (!leaf_max) {
+    H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
+    const int64_t lrows = d.nleaf * kTcK;
+    k_tc_levmax<T><<<levmax_grid(lrows), 256, 0, st>>>(xhat + leaf0 * kTcK * rp, lrows, rp, d.tc_xmax + D * kTcN);
+    ++nl;
+  }
   for (int l = D - 1; l >= lmin; --l) {
     // level l from level l + 1, with the column maxima of level l
     const int64_t np = (int64_t)1 << l;
@@ -1211,10 +1231,10 @@ int tc_build(Ctx &c, const int32_t *arow_dev) {
   return d.prec == H2_F64 ? tc_build_nd<10>(c, arow_dev) : tc_build_nd<6>(c, arow_dev);
 }
 
-int tc_upward(Ctx &c, void *xhat, int rp, int64_t *launches) {
+int tc_upward(Ctx &c, void *xhat, int rp, int64_t *launches, bool leaf_max) {
   if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core coupling takes at most 16 right-hand sides");
-  if (c.d.tc_nd == 10) return tc_upward_t<dd, 10>(c, static_cast<dd *>(xhat), rp, launches);
-  return tc_upward_t<float, 6>(c, static_cast<float *>(xhat), rp, launches);
+  if (c.d.tc_nd == 10) return tc_upward_t<dd, 10>(c, static_cast<dd *>(xhat), rp, launches, leaf_max);
+  return tc_upward_t<float, 6>(c, static_cast<float *>(xhat), rp, launches, leaf_max);
 }
 
 // the coupling phase: the coefficient digits exist (tc_upward)
@@ -1268,24 +1288,27 @@ int ntc_build(Ctx &c, const int32_t *nrow_dev) {
 
 // the input's column maxima and its digit planes per leaf (read by the
 // nearfield and by the tensor-core leaf forward step)
-int ntc_input(Ctx &c, const void *xpad_v, int rp, int64_t *launches) {
+int ntc_input(Ctx &c, const void *xpad_v, int rp, int64_t *launches, bool have_max) {
   const dd *xpad = static_cast<const dd *>(xpad_v);
   Dev &d = c.d;
   cudaStream_t st = c.stream;
   if (rp > kTcN) return fail(H2_EINVAL, "the tensor-core nearfield takes at most 16 right-hand sides");
   const int L = (int)d.lmax;
-  H2_CUDA_TRY(cudaMemsetAsync(d.ntc_xmax, 0, sizeof(unsigned) * kTcN, st));
-  const int64_t rows = d.nleaf * L;
-  k_tc_levmax<dd><<<levmax_grid(rows), 256, 0, st>>>(xpad, rows, rp, d.ntc_xmax);
+  if (!have_max) {
+    H2_CUDA_TRY(cudaMemsetAsync(d.ntc_xmax, 0, sizeof(unsigned) * kTcN, st));
+    const int64_t rows = d.nleaf * L;
+    k_tc_levmax<dd><<<levmax_grid(rows), 256, 0, st>>>(xpad, rows, rp, d.ntc_xmax);
+  }
   k_ntc_slice_x<<<(unsigned)((d.nleaf + 3) / 4), 128, 0, st>>>(xpad, d.nleaf, L, rp, d.ntc_xmax,
                                                                (unsigned char *)d.xnt);
   H2_CUDA_TRY(cudaGetLastError());
-  if (launches) *launches = 2;
+  if (launches) *launches = have_max ? 1 : 2;
   return H2_OK;
 }
 
 // the leaf forward step on the tensor cores: x^ of the leaf clusters from the
-// input digits (ntc_input) and the stored V_t^T digits
+// input digits (ntc_input) and the stored V_t^T digits, with their column
+// maxima for the upward pass
 int tc_leaf_forward(Ctx &c, void *xhat_v, int rp) {
   Dev &d = c.d;
   cudaStream_t st = c.stream;
@@ -1299,9 +1322,12 @@ int tc_leaf_forward(Ctx &c, void *xhat_v, int rp) {
   H2_CUDA_TRY(cudaGetDevice(&dev));
   H2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = (int)std::min<int64_t>(sms, d.nleaf);
+  // the leaf level's column maxima of the upward pass are taken here
+  // (tc_upward with leaf_max); every level's maxima start from zero
+  H2_CUDA_TRY(cudaMemsetAsync(d.tc_xmax, 0, sizeof(unsigned) * 32 * kTcN, st));
   k_coupling_tc<kTcSlices, dd, KB, true><<<grid, 64 + kDiagGroups * 128, sm, st>>>(
       (const unsigned char *)d.Vtc, (const unsigned char *)d.xnt, nullptr, nullptr, d.tcv_E, d.ntc_xmax,
-      d.nleaf - 1, d.nleaf, rp, static_cast<dd *>(xhat_v));
+      d.nleaf - 1, d.nleaf, rp, static_cast<dd *>(xhat_v), d.tc_xmax + d.depth * kTcN);
   H2_CUDA_TRY(cudaGetLastError());
   return H2_OK;
 }
